@@ -1,0 +1,218 @@
+"""CPU oracle for hierarchical Jacobi (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path
+(``paper_2006_16465_gb300``) never imports it, and it never imports the
+product path: the two share no code.
+
+Everything is computed by ``hj_oracle.c`` (plain C, binary64, no fused
+multiply-add); this module only marshals numpy arrays through ctypes.
+Grid arrays are C-contiguous float64 numpy arrays of shape (rows, nx + 2)
+with the Dirichlet ghost ring (see ``workloads``).
+
+Parity status: every function is pinned by the not-gpu tests in
+``tests/test_oracle_pins.py`` (closed-form Jacobi decay, Thomas vs banded LU,
+DST and dense direct solves, per-subdomain direct solves, k = 1 equivalence,
+central finite differences for the adjoint).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "hj_oracle.c"
+_LIB = _HERE / "libhj_oracle.so"
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (-O2, no FMA contraction, no fast-math)."""
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", str(_SRC), "-o", str(_LIB) + ".tmp", "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(str(_LIB) + ".tmp", _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+                ("cW", C.c_double), ("cE", C.c_double), ("cS", C.c_double),
+                ("cN", C.c_double), ("cD", C.c_double), ("sigma_const", C.c_double),
+                ("sigma", C.c_void_p)]
+
+
+_lib = None
+_D = C.POINTER(C.c_double)
+_F = C.POINTER(C.c_float)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(str(build()))
+        P = C.POINTER(_Problem)
+        L.hjo_apply.argtypes = [P, _D, _D]
+        L.hjo_residual_sq.argtypes = [P, _D, _D]
+        L.hjo_residual_sq.restype = C.c_double
+        L.hjo_jacobi_sweep.argtypes = [P, _D, _D, _D]
+        L.hjo_hier_cycle.argtypes = [P, _D, _D, _D, C.c_int, C.c_int, C.c_int]
+        L.hjo_solve.argtypes = [P, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                C.c_long, _D, C.c_long, C.POINTER(C.c_int)]
+        L.hjo_solve.restype = C.c_long
+        L.hjo_run_fixed.argtypes = [P, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_long]
+        L.hjo_thomas.argtypes = [C.c_long, _D, _D, _D, _D, _D]
+        L.hjo_bf16_round.argtypes = [C.c_float]
+        L.hjo_bf16_round.restype = C.c_float
+        L.hjo_hier_cycle_f32.argtypes = [P, _F, _F, _F, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.hjo_residual_sq_f32.argtypes = [P, _F, _F]
+        L.hjo_residual_sq_f32.restype = C.c_double
+        L.hjo_ir_solve.argtypes = [P, _D, _D, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                   C.c_long, C.c_long, C.c_int, _D, C.c_long,
+                                   C.POINTER(C.c_long), C.POINTER(C.c_int)]
+        L.hjo_ir_solve.restype = C.c_long
+        L.hjo_adjoint.argtypes = [P, _D, _D, _D, _D, C.c_int, C.c_int, C.c_int, C.c_double,
+                                  C.c_long, C.POINTER(C.c_int)]
+        L.hjo_adjoint.restype = C.c_long
+        L.hjo_paper_smem_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+        L.hjo_paper_smem_bytes.restype = C.c_long
+        _lib = L
+    return _lib
+
+
+def _grid(a, dtype=np.float64) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def _fp(a):
+    return a.ctypes.data_as(_F)
+
+
+class Problem:
+    """Oracle-side view of a stencil problem (duck-typed from workloads.Stencil)."""
+
+    def __init__(self, st):
+        self.st = st
+        self.sigma = None if st.sigma is None else _grid(st.sigma)
+        self.c = _Problem(st.dim, st.nx, st.ny, st.cW, st.cE, st.cS, st.cN, st.cD,
+                          float(st.sigma_const),
+                          None if self.sigma is None else self.sigma.ctypes.data)
+        self.shape = (st.rows, st.nx + 2)
+
+    @property
+    def ref(self):
+        return C.byref(self.c)
+
+
+def _prob(st) -> Problem:
+    return st if isinstance(st, Problem) else Problem(st)
+
+
+def apply(st, u):
+    p = _prob(st)
+    u = _grid(u)
+    out = np.zeros(p.shape)
+    lib().hjo_apply(p.ref, _dp(u), _dp(out))
+    return out
+
+
+def residual(st, f, u) -> float:
+    """||f - A u||_2 over interior points (binary64, row-major summation)."""
+    p = _prob(st)
+    return float(np.sqrt(lib().hjo_residual_sq(p.ref, _dp(_grid(f)), _dp(_grid(u)))))
+
+
+def jacobi_sweep(st, f, u):
+    p = _prob(st)
+    out = np.zeros(p.shape)
+    lib().hjo_jacobi_sweep(p.ref, _dp(_grid(f)), _dp(_grid(u)), _dp(out))
+    return out
+
+
+def hier_cycle(st, f, u, tx, ty, k):
+    p = _prob(st)
+    out = np.zeros(p.shape)
+    lib().hjo_hier_cycle(p.ref, _dp(_grid(f)), _dp(_grid(u)), _dp(out), tx, ty, k)
+    return out
+
+
+def run_fixed(st, f, u0, ncycles, tx=32, ty=32, k=1, classic=False):
+    """u after exactly ncycles hierarchical cycles (or classic sweeps)."""
+    p = _prob(st)
+    u = _grid(u0).copy()
+    lib().hjo_run_fixed(p.ref, _dp(_grid(f)), _dp(u), int(classic), tx, ty, k, int(ncycles))
+    return u
+
+
+def solve(st, f, u0, tol, max_cycles, tx=32, ty=32, k=1, classic=False, hist_cap=0):
+    """Returns (u_c, c, status, hist): c = first cycle with ||r_c|| <= tol ||r_0||."""
+    p = _prob(st)
+    u = _grid(u0).copy()
+    hist = np.zeros(max(hist_cap, 1))
+    status = C.c_int(0)
+    c = lib().hjo_solve(p.ref, _dp(_grid(f)), _dp(u), int(classic), tx, ty, k, float(tol),
+                        int(max_cycles), _dp(hist), int(hist_cap), C.byref(status))
+    return u, int(c), int(status.value), hist[:min(hist_cap, c + 1)]
+
+
+def thomas(a, d, c, b):
+    n = len(d)
+    x = np.zeros(n)
+    lib().hjo_thomas(n, _dp(_grid(a)), _dp(_grid(d)), _dp(_grid(c)), _dp(_grid(b)), _dp(x))
+    return x
+
+
+def bf16_round(x: float) -> float:
+    return float(lib().hjo_bf16_round(float(x)))
+
+
+def hier_cycle_f32(st, rhs, d, tx, ty, k, bf16=False):
+    p = _prob(st)
+    out = np.zeros(p.shape, dtype=np.float32)
+    lib().hjo_hier_cycle_f32(p.ref, _fp(_grid(rhs, np.float32)), _fp(_grid(d, np.float32)),
+                             _fp(out), tx, ty, k, int(bf16))
+    return out
+
+
+def residual_f32(st, rhs, d) -> float:
+    p = _prob(st)
+    return float(np.sqrt(lib().hjo_residual_sq_f32(p.ref, _fp(_grid(rhs, np.float32)),
+                                                    _fp(_grid(d, np.float32)))))
+
+
+def ir_solve(st, f, u0, tol, tx=32, ty=32, k=16, inner_tol=1e-4, inner_max=100000,
+             max_outer=50, bf16=False):
+    """Iterative refinement (binary64 residual/update, binary32 inner cycles).
+    Returns (u, outer_steps, inner_cycles, status, hist)."""
+    p = _prob(st)
+    u = _grid(u0).copy()
+    hist = np.zeros(max_outer + 1)
+    tot = C.c_long(0)
+    status = C.c_int(0)
+    o = lib().hjo_ir_solve(p.ref, _dp(_grid(f)), _dp(u), tx, ty, k, float(tol), float(inner_tol),
+                           int(inner_max), int(max_outer), int(bf16), _dp(hist), max_outer + 1,
+                           C.byref(tot), C.byref(status))
+    return u, int(o), int(tot.value), int(status.value), hist[:o + 1]
+
+
+def adjoint(st, g, u, tol=1e-13, max_cycles=10_000_000, tx=32, ty=32, k=16):
+    """(lambda, dL/dsigma) for dL/du = g: A^T lambda = g, dL/dsigma = -lambda*u."""
+    p = _prob(st)
+    lam = np.zeros(p.shape)
+    dsig = np.zeros(p.shape)
+    status = C.c_int(0)
+    lib().hjo_adjoint(p.ref, _dp(_grid(g)), _dp(_grid(u)), _dp(lam), _dp(dsig), tx, ty, k,
+                      float(tol), int(max_cycles), C.byref(status))
+    return lam, dsig, int(status.value)
+
+
+def paper_smem_bytes(dim, tx, ty, esize) -> int:
+    return int(lib().hjo_paper_smem_bytes(dim, tx, ty, esize))
