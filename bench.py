@@ -1,0 +1,336 @@
+"""Benchmark of the hierarchical Jacobi hot path on GB300.
+
+Workload (one step): 2D Poisson -Lap u = f on the unit square, 8192 x 8192
+interior grid, zero Dirichlet data, f ~ U[-1,1] (seeded), binary32, 32 x 32
+subdomains, k subiterations, 1000 hierarchical cycles with the fused residual
+reduction and device-side convergence control on (tol = 0, so every cycle
+runs).  Arrays are 268 MB each, larger than the 129 MB L2, so every cycle
+streams from HBM (no flush needed).
+
+value  = inner lattice-update rate, GLUP/s = 8192^2 * k * cycles / time
+         (every Jacobi point update counts, as in stencil practice);
+roofline = the cycle kernel against measured HBM copy bandwidth: algorithmic
+         traffic 12 B per point per cycle (read u, read f, write u);
+e2e    = the same metric through hj_solve with HOST buffers (f, u copied in
+         and u copied out inside the call, every step).
+Also reported beside it: plain global-memory Jacobi on the same grid, and the
+time to a 1e-8 relative residual on the 512 x 512 problem (binary32 inner
+cycles with binary64 refinement) against global-memory Jacobi in binary64.
+
+N > 1 GPUs: the path runs one problem per GPU (replicas only, no data-path
+collective); value is the aggregate over ranks, timed max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D Poisson time-to-1e-8 residual, GLUP/s vs global-mem Jacobi; % HBM roofline"
+N_BENCH = 8192
+BYTES_PER_POINT_CYCLE = 12  # read u, read f, write u (binary32)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_problem(n, seed=1):
+    import torch
+    import paper_2006_16465_gb300 as hj
+    import workloads as W
+    st = W.poisson_stencil(2, n, n)
+    f = hj.alloc_grid(2, n, n, torch.float32)
+    # seeded U[-1,1] from the shared generator, filled in row blocks to bound host memory
+    rows = 512
+    for j0 in range(0, n, rows):
+        r = min(rows, n - j0)
+        blk = W.uniform(seed, r * n, -1.0, 1.0, offset=j0 * n).reshape(r, n)
+        f[1 + j0:1 + j0 + r, 1:n + 1].copy_(torch.from_numpy(blk).float())
+    u0 = hj.alloc_grid(2, n, n, torch.float32)
+    return st, f, u0
+
+
+def run_reference(args):
+    """The oracle (plain C, binary64, one core) timed on the host on a bounded
+    sample of the same workload: one hierarchical cycle of the 8192^2 grid per
+    step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    import workloads as W
+    n = N_BENCH
+    st = W.poisson_stencil(2, n, n)
+    f = W.zeros_grid(st)
+    rows = 512
+    for j0 in range(0, n, rows):
+        r = min(rows, n - j0)
+        f[1 + j0:1 + j0 + r, 1:n + 1] = W.uniform(1, r * n, -1.0, 1.0, offset=j0 * n).reshape(r, n)
+    u = W.zeros_grid(st)
+    prob = oracle.Problem(st)
+    for _ in range(args.warmup):
+        u = oracle.run_fixed(prob, f, u, 1, 32, 32, args.k)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = oracle.run_fixed(prob, f, u, 1, 32, 32, args.k)
+    dt = time.perf_counter() - t0
+    glups = n * n * args.k * args.steps / dt / 1e9
+    sample = f"{args.steps} hierarchical cycles (k={args.k}, 32x32 subdomains) of the {n}x{n} grid, binary64"
+    line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(args, world),
+            "cpu_baseline": {"value": glups, "unit": "GLUP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": glups, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(args, world):
+    n = getattr(args, "n", N_BENCH)
+    return {"workload": f"2D Poisson {n}x{n} binary32, hierarchical Jacobi, 32x32 subdomains, "
+                        f"k={args.k}, {args.cycles} cycles per step, fused residual on",
+            "grid": [n, n], "tile": [32, 32], "k": args.k, "cycles_per_step": args.cycles,
+            "l2": "inputs larger than L2 (3 x 268 MB arrays)", "parallelism": f"replicas x{world}"}
+
+
+def cpu_baseline(k):
+    """Oracle timed on host cores on a bounded sample (~10 s): hierarchical
+    cycles of the full 8192^2 grid in binary64 until 10 s have passed."""
+    import oracle
+    import workloads as W
+    n = N_BENCH
+    st = W.poisson_stencil(2, n, n)
+    f = W.zeros_grid(st)
+    rows = 512
+    for j0 in range(0, n, rows):
+        r = min(rows, n - j0)
+        f[1 + j0:1 + j0 + r, 1:n + 1] = W.uniform(1, r * n, -1.0, 1.0, offset=j0 * n).reshape(r, n)
+    u = W.zeros_grid(st)
+    prob = oracle.Problem(st)
+    t0 = time.perf_counter()
+    cyc = 0
+    while True:
+        u = oracle.run_fixed(prob, f, u, 1, 32, 32, k)
+        cyc += 1
+        if time.perf_counter() - t0 >= 10.0:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n * n * k * cyc / dt / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+            "sample": f"{cyc} hierarchical cycles (k={k}, 32x32) of the {n}x{n} grid, binary64, one thread"}
+
+
+def time_to_residual(torch, hj, W, tol=1e-8):
+    """512^2 Poisson, f ~ U[-1,1]: binary32-inner / binary64-refinement
+    hierarchical solve vs binary64 global-memory Jacobi, both to tol."""
+    p = W.poisson2d_uniform(512, 512, seed=1)
+    f = hj.grid_from(p.f, 2, torch.float64)
+    out = {}
+    for name, kw in [("hier_f32_ir", dict(tile_x=32, tile_y=32, k=32, precision="f32_ir", inner_tol=1e-4,
+                                          check_every=256)),
+                     ("classic_f64", dict(method="classic", precision="f64", check_every=1024))]:
+        s = hj.Solver(p.st, tol=tol, max_cycles=5_000_000, **kw)
+        u = hj.grid_from(p.u0, 2, torch.float64)
+        s.solve(f, u.clone())  # warm (graphs, caches)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = s.solve(f, u)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        a, rel = s.residual(f, u)
+        out[name] = {"seconds": dt, "cycles": r["cycles"], "outer_steps": r["outer_steps"],
+                     "rel_residual": a / r["res0"] if r["res0"] else 0.0, "status": r["status"]}
+        s.close()
+    out["speedup"] = out["classic_f64"]["seconds"] / out["hier_f32_ir"]["seconds"]
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hj", choices=["hj", "reference"])
+    ap.add_argument("--k", type=int, default=4)
+    ap.add_argument("--cycles", type=int, default=1000)
+    ap.add_argument("--n", type=int, default=N_BENCH, help="grid side (profiling runs use a smaller grid)")
+    ap.add_argument("--no-extras", action="store_true", help="skip classic / time-to-residual / cpu legs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2006_16465_gb300 as hj
+    import workloads as W
+
+    n, k, C = args.n, args.k, args.cycles
+    st, f, u0 = make_problem(n)
+    solver = hj.Solver(st, tile_x=32, tile_y=32, k=k, precision="f32", tol=0.0, max_cycles=C, check_every=100)
+    u = u0.clone()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        solver.solve(f, u, check=False)
+    launches = 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = solver.solve(f, u, check=False)
+            launches += r["cycles_launched"]
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    cycles_done = args.steps * C
+    glups = world * n * n * k * cycles_done / (ms / 1e3) / 1e9
+    per_launch_ms = ms / cycles_done
+    hbm_peak, peak_kind = _peaks()
+    achieved = BYTES_PER_POINT_CYCLE * n * n / (per_launch_ms / 1e3) / 1e9
+
+    # e2e through the C ABI with host buffers (copies inside the timed region)
+    fh = f.cpu().pin_memory()
+    uh = u0.cpu().pin_memory()
+    solver.solve(fh, uh, check=False)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver.solve(fh, uh, check=False)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * n * n * k * cycles_done / e2e_s / 1e9, "unit": "GLUP/s",
+           "h2d_bytes_per_step": 2 * f.numel() * 4, "d2h_bytes_per_step": u.numel() * 4}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        cl = hj.Solver(st, method="classic", precision="f32", tol=0.0, max_cycles=200, check_every=100)
+        uc = u0.clone()
+        cl.solve(f, uc, check=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cl.solve(f, uc, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1) / 200
+        extras["classic_global_jacobi"] = {"glups": n * n / (cms / 1e3) / 1e9, "us_per_sweep": cms * 1e3,
+                                           "hbm_gbs": 12 * n * n / (cms / 1e3) / 1e9}
+        cl.close()
+        extras["hier_global_cycle_rate_gdofs"] = n * n / (per_launch_ms / 1e3) / 1e9
+        extras["time_to_1e-8_512"] = time_to_residual(torch, hj, W)
+    launches += args.steps  # one residual launch per step (the final iterate is not converged: tol = 0)
+    line = {"metric": METRIC, "value": glups, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(args, world),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "kernel": "hier2d_kernel<float,32x32>", "peak_kind": peak_kind},
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+    line.update(extras)
+    if rank == 0 and not args.no_extras:
+        line["cpu_baseline"] = cpu_baseline(k)
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,223 @@
+/*
+ * hj.h -- C ABI of the GB300 hierarchical Jacobi solver.
+ *
+ * Method: Islam & Wang, "Hierarchical Jacobi Iteration for Structured Matrices
+ * on GPUs using Shared Memory" (arXiv 2006.16465).  A cycle partitions the grid
+ * into subdomains (tiles), stages each tile plus a one-point halo on chip, runs
+ * k Jacobi subiterations there with the halo frozen, and writes the tile
+ * interior back (Section 3.3 for 1D, Section 4.1 for 2D).  Cycles repeat until
+ * the L2 residual has dropped by the requested factor (Sections 3.5, 4.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Operator.  For interior point p with neighbours W,E (x-1, x+1) and S,N
+ * (y-1, y+1):
+ *     (A u)_p = d_p u_p + cW u_W + cE u_E + cS u_S + cN u_N,
+ *     d_p     = cD + sigma_const + sigma_p          (sigma_p = 0 if sigma NULL)
+ * This is the tridiagonal stencil of Section 3 (Eq. jacobi-stencil-equation-1d,
+ * a = cW, c = cE, d = cD) and the pentadiagonal stencil of Section 4
+ * (Eq. 2d-jacobi-stencil, a,c,e,f,d = cW,cE,cS,cN,cD), plus a screening term.
+ * 2D Poisson on the unit square (Eq. 2d-poisson): cW = cE = -1/hx^2,
+ * cS = cN = -1/hy^2, cD = 2/hx^2 + 2/hy^2, hx = 1/(nx+1), hy = 1/(ny+1).
+ * The stencil must be diagonally dominant, |d_p| >= |cW|+|cE|+|cS|+|cN| with
+ * d_p > 0 (the convergence condition of Section 2.1); hj_create checks it.
+ *
+ * Grid arrays (f, u, g, sigma, dl_df, dl_dsigma).  Row-major, x fastest, with a
+ * one-point ghost ring holding Dirichlet data:
+ *     2D: (ny + 2) rows, element (row j, column i) at index j*ld + i,
+ *         interior j = 1..ny, i = 1..nx.
+ *     1D: ny rows; every row is an independent 1D problem (the paper's 1024
+ *         simultaneous copies, Section 3.5), interior i = 1..nx, ghosts at
+ *         i = 0 and i = nx + 1.
+ * ld (elements) >= nx + 2.  Base pointers must be 16-byte aligned and
+ * ld * element_size a multiple of 16 bytes.  Element type: double for
+ * HJ_F64, float for HJ_F32; sigma is always double.
+ * Ghost-ring entries of f and sigma are ignored.
+ *
+ * Memory.  Pointers passed to the solve calls are device pointers, except
+ * that hj_solve also accepts host pointers for f and u (it then copies them
+ * through its own device buffers, see hj_solve).  The caller owns every
+ * array it passes; the handle owns its workspace (second iterate buffer,
+ * residual partials, refinement buffers, CUDA graphs) and frees it in
+ * hj_destroy.  sigma must stay valid for the life of the handle.
+ *
+ * Streams.  Every call is ordered on the given stream (NULL = the legacy
+ * default stream).  hj_solve, hj_solve_adjoint and hj_residual synchronise
+ * with that stream to read convergence state and return results, so they
+ * block the calling host thread.
+ *
+ * Errors.  Every int-returning call returns an hj_status code; HJ_OK = 0.
+ * hj_last_error() gives a one-line description of the most recent failure on
+ * the calling thread.  A handle stays usable after HJ_ERR_NOT_CONVERGED,
+ * HJ_ERR_DIVERGED and HJ_ERR_INVALID_ARG; after HJ_ERR_CUDA or
+ * HJ_ERR_TIMEOUT only hj_destroy is safe.
+ */
+#ifndef HJ_H
+#define HJ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Entry points are the only symbols the shared library exports. */
+#if defined(__GNUC__)
+#define HJ_API __attribute__((visibility("default")))
+#else
+#define HJ_API
+#endif
+
+typedef struct hj_handle hj_handle;
+
+/* A cudaStream_t passed as an opaque pointer (NULL = legacy default stream). */
+typedef void *hj_stream;
+
+enum hj_status {
+    HJ_OK = 0,
+    HJ_ERR_INVALID_ARG = 1,      /* bad size, pointer, alignment or parameter     */
+    HJ_ERR_NOT_DIAG_DOMINANT = 2,/* stencil fails the Section 2.1 condition        */
+    HJ_ERR_UNSUPPORTED = 3,      /* tile shape / mode combination not built        */
+    HJ_ERR_CUDA = 4,             /* a CUDA runtime call failed                     */
+    HJ_ERR_NOT_CONVERGED = 5,    /* max_cycles reached; u holds the last iterate   */
+    HJ_ERR_DIVERGED = 6,         /* residual became NaN or Inf                     */
+    HJ_ERR_TIMEOUT = 7,          /* a bounded device-side wait gave up             */
+    HJ_ERR_NO_MEMORY = 8         /* workspace allocation failed                    */
+};
+
+enum hj_dtype { HJ_F64 = 0, HJ_F32 = 1 };
+
+/* Arithmetic of the solve.
+ *   HJ_PREC_F64          : binary64 cycles; the update is evaluated in the fixed
+ *                          order  acc = cW*uW; acc += cE*uE; acc += cS*uS;
+ *                          acc += cN*uN; u' = (f - acc) * (1/d_p)  with no fused
+ *                          multiply-add, so results are reproducible bit for bit.
+ *   HJ_PREC_F32          : binary32 cycles on binary32 f and u (fused multiply-
+ *                          add allowed).  Attainable relative residual ~1e-6.
+ *   HJ_PREC_F32_IR       : binary64 f and u; mixed-precision iterative
+ *                          refinement: binary64 residual r = f - A u and binary64
+ *                          update u += d are the only binary64 steps; the
+ *                          correction equation A d = r is solved by binary32
+ *                          hierarchical cycles.
+ *   HJ_PREC_BF16CORR_IR  : as F32_IR, but the correction d is stored in
+ *                          bfloat16 between cycles (arithmetic stays binary32). */
+enum hj_precision { HJ_PREC_F64 = 0, HJ_PREC_F32 = 1, HJ_PREC_F32_IR = 2, HJ_PREC_BF16CORR_IR = 3 };
+
+/* HJ_METHOD_HIER: hierarchical cycles (Sections 3.3, 4.1).
+ * HJ_METHOD_CLASSIC: one global-memory Jacobi sweep per step (Section 3.2);
+ * every point reads the previous iterate only (a true grid-wide step). */
+enum hj_method { HJ_METHOD_HIER = 0, HJ_METHOD_CLASSIC = 1 };
+
+typedef struct {
+    int dim;              /* 1 or 2                                              */
+    int nx, ny;           /* interior points; 1D: ny = number of independent rows */
+    long long ld;         /* row pitch of every grid array, in elements          */
+    double cW, cE, cS, cN, cD;  /* stencil (cS, cN ignored in 1D)                */
+    double sigma_const;   /* constant screening added to the diagonal            */
+    const double *sigma;  /* device, grid layout, per-point screening; nullable  */
+    int dtype;            /* hj_dtype of f and u                                 */
+} hj_desc;
+
+typedef struct {
+    int method;           /* hj_method                                           */
+    int tile_x, tile_y;   /* subdomain interior size (the paper's blockDim.x,
+                             blockDim.y); 1D ignores tile_y.  Built shapes are
+                             listed by hj_tile_shapes().                          */
+    int k;                /* subiterations per cycle (>= 1)                      */
+    int precision;        /* hj_precision                                        */
+    int check_every;      /* cycles per host convergence check (CUDA graph
+                             length); rounded up to an even number                */
+    long long max_cycles; /* cap on cycles (classic: sweeps)                     */
+    double tol;           /* stop at the first iterate with
+                             ||f - A u_c||_2 <= tol * ||f - A u_0||_2             */
+    long long fixed_cycles; /* > 0: run exactly this many cycles, check nothing  */
+    double inner_tol;     /* refinement: inner relative residual target          */
+    long long inner_max_cycles; /* refinement: cap on inner cycles per outer step */
+    int max_outer;        /* refinement: cap on outer steps                      */
+    int persistent;       /* 1: single persistent launch looping over cycles with
+                             a device-side grid barrier (needs all tiles resident);
+                             0: one launch per cycle inside CUDA graphs;
+                             -1: choose automatically                            */
+    int autotune;         /* 1: pick tile shape and k by measurement on first use */
+} hj_params;
+
+typedef struct {
+    long long cycles;         /* cycles (classic: sweeps) up to the returned iterate */
+    long long cycles_launched;/* cycles issued, including skipped overshoot        */
+    long long inner_cycles;   /* refinement: total binary32 cycles               */
+    int outer_steps;          /* refinement: outer steps taken                   */
+    double res0;              /* ||f - A u_0||_2                                  */
+    double res_final;         /* ||f - A u||_2 of the returned iterate            */
+    double rel_final;         /* res_final / res0 (0 if res0 == 0)                */
+    double *history;          /* caller-owned host array (nullable): ||r_c||_2 per
+                                 checked iterate (refinement: per outer step)     */
+    long long history_cap;    /* capacity of history                             */
+    long long history_len;    /* entries written                                 */
+    double wall_ms;           /* host wall time of the call                      */
+    int tile_x, tile_y, k;    /* configuration actually used                     */
+    int persistent;           /* 1 if the persistent path ran                    */
+} hj_stats;
+
+/* Fill p with defaults: hierarchical, 32 x 32 tiles, k = 16, HJ_PREC_F64,
+ * check_every = 64, max_cycles = 10^7, tol = 1e-6, fixed_cycles = 0,
+ * inner_tol = 1e-4, inner_max_cycles = 10^6, max_outer = 60, persistent = -1,
+ * autotune = 0. */
+HJ_API void hj_default_params(hj_params *p);
+
+/* Create a solver for one problem shape.  Validates the descriptor and
+ * parameters (HJ_ERR_INVALID_ARG, HJ_ERR_NOT_DIAG_DOMINANT, HJ_ERR_UNSUPPORTED),
+ * allocates the workspace on the current device (HJ_ERR_NO_MEMORY) and
+ * precomputes the diagonal of a per-point sigma.  *out is NULL on failure. */
+HJ_API int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params);
+
+/* Solve A u = f.  u: in = initial guess whose ghost ring holds the Dirichlet
+ * data; out = the first iterate u_c with ||r_c|| <= tol ||r_0|| (c in
+ * stats->cycles), or the last iterate (HJ_ERR_NOT_CONVERGED, HJ_ERR_DIVERGED).
+ * With params.fixed_cycles > 0 exactly that many cycles run and no residual is
+ * tested.  f and u may both be host pointers (pageable or pinned): they are
+ * then copied to and from device buffers inside the call.  stats: nullable. */
+HJ_API int hj_solve(hj_handle *h, const void *f, void *u, hj_stream stream, hj_stats *stats);
+
+/* ||f - A u||_2 over interior points (binary64 accumulation, deterministic
+ * order) into *abs_l2, and *rel_l2 = abs / ||f||_2 (abs itself if f = 0).
+ * Device pointers; either output pointer may be NULL. */
+HJ_API int hj_residual(hj_handle *h, const void *f, const void *u, double *abs_l2, double *rel_l2,
+                hj_stream stream);
+
+/* Implicit adjoint of the solve for a loss L(u).  Given g = dL/du (grid,
+ * device, same dtype as u) and the solution u, solves A^T lambda = g with a
+ * zero ghost ring by the same hierarchical cycles and precision as hj_solve
+ * (A^T of the stencil swaps cW<->cE and cS<->cN), then writes
+ *     dl_df     = lambda                (dL/df)
+ *     dl_dsigma = -lambda * u  pointwise (dL/dsigma_p, since dA/dsigma_p = e_p e_p^T)
+ * dl_dsigma (binary64 grid) may be NULL.  Ghost entries of the outputs are 0.
+ * No iterate of the forward solve is stored or needed besides u. */
+HJ_API int hj_solve_adjoint(hj_handle *h, const void *g, const void *u, void *dl_df, void *dl_dsigma,
+                     hj_stream stream, hj_stats *stats);
+
+/* Solve nprob independent 2D problems (each with its own hj_desc: sizes, ld,
+ * stencil, sigma_const; sigma must be NULL; dtype HJ_F64) in one persistent
+ * launch per refinement phase, fed by a device work queue of (problem, tile)
+ * items; problems retire independently when they meet params.tol.  The
+ * handle must come from hj_create with a 2D descriptor (it supplies params);
+ * f[i], u[i] are device pointers.  stats (nullable) receives totals; per-
+ * problem cycle counts go to cycles_out (host, nprob entries, nullable). */
+HJ_API int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, const void *const *f,
+                     void *const *u, hj_stream stream, hj_stats *stats, long long *cycles_out);
+
+/* Free the handle and its workspace (NULL is ignored). */
+HJ_API void hj_destroy(hj_handle *h);
+
+/* Static description of a status code. */
+HJ_API const char *hj_error_string(int status);
+
+/* One-line description of the last error on the calling thread ("" if none). */
+HJ_API const char *hj_last_error(void);
+
+/* Tile shapes built for (dim, precision): writes up to cap (tile_x, tile_y)
+ * pairs into xy[2*i], xy[2*i+1] and returns how many exist. */
+HJ_API int hj_tile_shapes(int dim, int precision, int *xy, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HJ_H */

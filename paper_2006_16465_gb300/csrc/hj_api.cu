@@ -1,0 +1,758 @@
+// hj_api.cu -- host runtime and C ABI (include/hj.h).
+//
+// The cycle loop: a CUDA graph of M launches alternates the two iterate
+// buffers (u_c -> u_{c+1} -> u_c ...).  Each launch folds ||f - A u_c||^2 into
+// the device control block; once an iterate meets the tolerance, the control
+// block records its index and later launches return immediately, so the host
+// only synchronises once per graph (M cycles) and the returned iterate is the
+// exact first one that met the tolerance (Sections 3.5 and 4.2 stop on the L2
+// residual reduced by a factor).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "hj_internal.cuh"
+
+using namespace hj;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int seterr(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CKR(call)                                                                                       \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return seterr(HJ_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                          __LINE__);                                                                    \
+    } while (0)
+
+#define CKS(expr)                  \
+    do {                           \
+        int st_ = (expr);          \
+        if (st_ != HJ_OK) return st_; \
+    } while (0)
+
+const TileKernelInfo *family_tiles(int fam, int *n) {
+    switch (fam) {
+    case FAM_F64: return tile_kernels_f64(n);
+    case FAM_F32: return tile_kernels_f32(n);
+    default: return tile_kernels_bf16(n);
+    }
+}
+const TileKernelInfo *family_classic(int fam, int dim) {
+    int n = 0;
+    const TileKernelInfo *k = fam == FAM_F64 ? classic_kernels_f64(&n)
+                              : fam == FAM_F32 ? classic_kernels_f32(&n)
+                                               : classic_kernels_bf16(&n);
+    for (int i = 0; i < n; ++i)
+        if (k[i].dim == dim) return &k[i];
+    return nullptr;
+}
+const TileKernelInfo *find_tile(int fam, int dim, int tx, int ty) {
+    int n = 0;
+    const TileKernelInfo *k = family_tiles(fam, &n);
+    for (int i = 0; i < n; ++i)
+        if (k[i].dim == dim && k[i].tx == tx && (dim == 1 || k[i].ty == ty)) return &k[i];
+    return nullptr;
+}
+
+struct GraphEntry {
+    CycKernel fn;
+    dim3 grid, block;
+    CycArgs a0, a1;
+    int M;
+    cudaGraphExec_t exec;
+    unsigned long long stamp;
+};
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct hj_handle {
+    hj_desc d;
+    hj_params p;
+    int dev = 0, nsm = 0;
+    int rows = 0;
+    size_t esz = 0, grid_elems = 0, grid_bytes = 0;
+    int fam_outer = FAM_F64, fam_inner = FAM_F32;
+    bool ir = false;
+    const TileKernelInfo *k_outer = nullptr, *k_inner = nullptr, *k_classic = nullptr, *k_classic_inner = nullptr;
+    void *ubuf = nullptr;
+    void *dinv_outer = nullptr;   // per-point 1/d in the outer compute type (sigma given)
+    float *dinv32 = nullptr;      // per-point 1/d in binary32 (refinement, sigma given)
+    float *r32 = nullptr;         // refinement: binary32 residual (inner RHS)
+    void *dA = nullptr, *dB = nullptr;  // refinement: correction buffers
+    void *hf = nullptr, *hu = nullptr;  // staging for host-pointer solves
+    double *partials = nullptr, *gpart = nullptr, *hist = nullptr, *rstore = nullptr;
+    unsigned *gcnt = nullptr, *fcnt = nullptr;
+    Ctl *ctl = nullptr;
+    Ctl *h_ctl = nullptr, *h_ctl_init = nullptr;
+    double *h_hist = nullptr, *h_rstore = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev = nullptr;
+    std::vector<GraphEntry> graphs;
+    unsigned long long stamp = 0;
+    size_t max_blocks = 0, max_groups = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// kernel arguments and launch geometry
+// ---------------------------------------------------------------------------
+CycArgs base_args(const hj_handle *h, bool transpose) {
+    CycArgs a;
+    memset(&a, 0, sizeof(a));
+    a.ld = h->d.ld;
+    a.nx = h->d.nx;
+    a.ny = h->d.ny;
+    a.k = h->p.k;
+    a.cW = transpose ? h->d.cE : h->d.cW;
+    a.cE = transpose ? h->d.cW : h->d.cE;
+    a.cS = h->d.dim == 2 ? (transpose ? h->d.cN : h->d.cS) : 0.0;
+    a.cN = h->d.dim == 2 ? (transpose ? h->d.cS : h->d.cN) : 0.0;
+    a.dconst = h->d.cD + h->d.sigma_const;
+    a.invd = 1.0 / a.dconst;
+    a.fW = (float)a.cW; a.fE = (float)a.cE; a.fS = (float)a.cS; a.fN = (float)a.cN;
+    a.gW = (float)(-a.cW * a.invd); a.gE = (float)(-a.cE * a.invd);
+    a.gS = (float)(-a.cS * a.invd); a.gN = (float)(-a.cN * a.invd);
+    a.finvd = (float)a.invd;
+    a.fdconst = (float)a.dconst;
+    return a;
+}
+
+RedArgs red_args(const hj_handle *h, int mode, double tol, long long max_cycles) {
+    RedArgs r;
+    memset(&r, 0, sizeof(r));
+    r.partials = h->partials;
+    r.gpart = h->gpart;
+    r.gcnt = h->gcnt;
+    r.fcnt = h->fcnt;
+    r.hist = h->hist;
+    r.out = h->rstore;
+    r.ctl = h->ctl;
+    r.tol = tol;
+    r.max_cycles = max_cycles;
+    r.mode = mode;
+    r.scale = 1.0;
+    return r;
+}
+
+void geometry(const hj_handle *h, const TileKernelInfo *ki, bool classic, dim3 *grid, dim3 *block) {
+    const int nx = h->d.nx, ny = h->d.ny;
+    if (classic) {
+        if (h->d.dim == 2) {
+            *grid = dim3((nx + 31) / 32, (ny + 7) / 8);
+            *block = dim3(32, 8);
+        } else {
+            *grid = dim3((nx + 255) / 256, ny);
+            *block = dim3(256);
+        }
+        return;
+    }
+    if (h->d.dim == 2) {
+        *grid = dim3((nx + ki->tx - 1) / ki->tx, (ny + ki->ty - 1) / ki->ty);
+    } else {
+        const int tiles = (nx + ki->tx - 1) / ki->tx;
+        *grid = dim3((tiles + ki->tiles_per_cta - 1) / ki->tiles_per_cta, ny);
+    }
+    *block = dim3(ki->threads);
+}
+
+int family_of(const hj_handle *h, const TileKernelInfo *ki) {
+    if (ki == h->k_inner) return h->fam_inner;
+    return h->fam_outer;
+}
+
+int get_graph(hj_handle *h, CycKernel fn, dim3 grid, dim3 block, const CycArgs &a0, const CycArgs &a1, int M,
+              cudaGraphExec_t *out) {
+    for (auto &g : h->graphs) {
+        if (g.fn == fn && g.M == M && g.grid.x == grid.x && g.grid.y == grid.y && g.block.x == block.x &&
+            g.block.y == block.y && !memcmp(&g.a0, &a0, sizeof(CycArgs)) && !memcmp(&g.a1, &a1, sizeof(CycArgs))) {
+            g.stamp = ++h->stamp;
+            *out = g.exec;
+            return HJ_OK;
+        }
+    }
+    if (h->graphs.size() >= 16) {
+        auto it = std::min_element(h->graphs.begin(), h->graphs.end(),
+                                   [](const GraphEntry &x, const GraphEntry &y) { return x.stamp < y.stamp; });
+        cudaGraphExecDestroy(it->exec);
+        h->graphs.erase(it);
+    }
+    cudaGraph_t graph;
+    CKR(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < M; ++i) fn<<<grid, block, 0, h->cap>>>((i & 1) ? a1 : a0);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ee = cudaStreamEndCapture(h->cap, &graph);
+    if (le != cudaSuccess) return seterr(HJ_ERR_CUDA, "kernel launch during capture: %s", cudaGetErrorString(le));
+    if (ee != cudaSuccess) return seterr(HJ_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ee));
+    cudaGraphExec_t exec;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return seterr(HJ_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+    GraphEntry e;
+    e.fn = fn;
+    e.grid = grid;
+    e.block = block;
+    e.a0 = a0;
+    e.a1 = a1;
+    e.M = M;
+    e.exec = exec;
+    e.stamp = ++h->stamp;
+    h->graphs.push_back(e);
+    *out = exec;
+    return HJ_OK;
+}
+
+struct RunOut {
+    long long c;        // index of the returned iterate
+    int status;
+    long long launched; // cycles issued
+    double res2_0;      // ||r_0||^2 (converging mode)
+    double res2_c;      // ||r_c||^2 of the returned iterate if known, else -1
+};
+
+// Iterate cycles (or classic sweeps) of kernel `fn` from b0 (holds u_0), b1
+// (the other buffer, same ghost ring).  fixed > 0: exactly `fixed` cycles, no
+// residual.  Otherwise until ||r_c|| <= tol ||r_0|| or max_cycles.
+int run_cycles(hj_handle *h, const TileKernelInfo *ki, bool classic, bool sig, const CycArgs &base, void *b0,
+               void *b1, double tol, long long max_cycles, long long fixed, cudaStream_t s, RunOut *ro,
+               double *hist_out, long long hist_cap, long long *hist_len) {
+    dim3 grid, block;
+    geometry(h, ki, classic, &grid, &block);
+    const int M = h->p.check_every;
+    CycArgs a0 = base, a1 = base;
+    a0.uin = b0; a0.uout = b1;
+    a1.uin = b1; a1.uout = b0;
+    ro->res2_0 = -1.0;
+    ro->res2_c = -1.0;
+    if (fixed > 0) {
+        CycKernel fn = ki->fn[sig][0];
+        const long long reps = fixed / M;
+        if (reps > 0) {
+            cudaGraphExec_t ex;
+            CKS(get_graph(h, fn, grid, block, a0, a1, M, &ex));
+            for (long long r = 0; r < reps; ++r) CKR(cudaGraphLaunch(ex, s));
+        }
+        for (long long c = reps * M; c < fixed; ++c) fn<<<grid, block, 0, s>>>((c & 1) ? a1 : a0);
+        CKR(cudaGetLastError());
+        ro->c = fixed;
+        ro->status = HJ_OK;
+        ro->launched = fixed;
+        return HJ_OK;
+    }
+    CycKernel fn = ki->fn[sig][1];
+    a0.red = red_args(h, RED_CYCLE, tol, max_cycles);
+    // binary32 kernels with a constant diagonal accumulate (u' - u)^2; r = d (u' - u)
+    if (family_of(h, ki) != FAM_F64 && !sig) a0.red.scale = base.dconst * base.dconst;
+    a1.red = a0.red;
+    *h->h_ctl_init = Ctl{-1, HJ_OK, 0, 0.0, 0.0};
+    CKR(cudaMemcpyAsync(h->ctl, h->h_ctl_init, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    if (max_cycles <= 0) {
+        // no cycle may run: the residual of u_0 is all there is
+        ro->c = 0;
+        ro->status = HJ_ERR_NOT_CONVERGED;
+        ro->launched = 0;
+        return HJ_OK;
+    }
+    cudaGraphExec_t ex;
+    CKS(get_graph(h, fn, grid, block, a0, a1, M, &ex));
+    long long launched = 0, copied = 0;
+    const long long mask = kHistCap - 1;
+    for (;;) {
+        CKR(cudaGraphLaunch(ex, s));
+        const long long start = launched;
+        launched += M;
+        // copy this replay's slice of the residual ring
+        const long long p0 = start & mask;
+        const long long n0 = std::min<long long>(M, kHistCap - p0);
+        CKR(cudaMemcpyAsync(h->h_hist + p0, h->hist + p0, n0 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (n0 < M)
+            CKR(cudaMemcpyAsync(h->h_hist, h->hist, (M - n0) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CKR(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CKR(cudaEventRecord(h->ev, s));
+        CKR(cudaEventSynchronize(h->ev));
+        const long long ncomp = h->h_ctl->cycle;
+        if (hist_out) {
+            for (; copied < ncomp; ++copied)
+                if (copied < hist_cap) hist_out[copied] = sqrt(h->h_hist[copied & mask]);
+        }
+        if (h->h_ctl->done >= 0) break;
+        if (launched > max_cycles + 2LL * M)
+            return seterr(HJ_ERR_CUDA, "cycle loop did not terminate (device control block not updated)");
+    }
+    if (hist_len) *hist_len = std::min(copied, hist_cap);
+    ro->c = h->h_ctl->done;
+    ro->status = h->h_ctl->status;
+    ro->launched = launched;
+    ro->res2_0 = h->h_ctl->res2_0;
+    if (ro->status == HJ_OK || ro->status == HJ_ERR_DIVERGED) ro->res2_c = h->h_hist[ro->c & mask];
+    return HJ_OK;
+}
+
+int residual_of(hj_handle *h, const void *f, const void *u, bool transpose, double *rr, double *ff, cudaStream_t s) {
+    const CycArgs a = base_args(h, transpose);
+    const RedArgs red = red_args(h, RED_STORE, 0.0, 0);
+    CKR(launch_residual_ex(h->d.dim, h->d.dtype == HJ_F64, f, u, h->d.sigma, h->d.ld, h->d.nx, h->d.ny, a.cW, a.cE,
+                           a.cS, a.cN, a.dconst, 1, nullptr, red, s));
+    CKR(cudaMemcpyAsync(h->h_rstore, h->rstore, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKR(cudaEventRecord(h->ev, s));
+    CKR(cudaEventSynchronize(h->ev));
+    if (rr) *rr = h->h_rstore[0];
+    if (ff) *ff = h->h_rstore[1];
+    return HJ_OK;
+}
+
+// Plain (binary64 or binary32) solve of A u = f, u in/out (device).
+int solve_plain(hj_handle *h, const void *f, void *u, bool transpose, cudaStream_t s, hj_stats *st) {
+    const bool classic = h->p.method == HJ_METHOD_CLASSIC;
+    const TileKernelInfo *ki = classic ? h->k_classic : h->k_outer;
+    const bool sig = h->d.sigma != nullptr;
+    CycArgs base = base_args(h, transpose);
+    base.f = f;
+    base.dinv = h->dinv_outer;
+    CKR(cudaMemcpyAsync(h->ubuf, u, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+    RunOut ro;
+    long long hl = 0;
+    CKS(run_cycles(h, ki, classic, sig, base, u, h->ubuf, h->p.tol, h->p.max_cycles, h->p.fixed_cycles, s, &ro,
+                   st ? st->history : nullptr, st ? st->history_cap : 0, &hl));
+    if (ro.c & 1) CKR(cudaMemcpyAsync(u, h->ubuf, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+    double res0 = -1.0, resc = -1.0;
+    if (h->p.fixed_cycles <= 0) {
+        res0 = sqrt(std::max(ro.res2_0, 0.0));
+        if (ro.res2_c >= 0.0) {
+            resc = sqrt(ro.res2_c);
+        } else {
+            double rr;
+            CKS(residual_of(h, f, u, transpose, &rr, nullptr, s));
+            resc = sqrt(rr);
+            if (ro.launched == 0) res0 = resc;
+            if (resc <= h->p.tol * res0) ro.status = HJ_OK;
+        }
+    }
+    CKR(cudaStreamSynchronize(s));
+    if (st) {
+        st->cycles = ro.c;
+        st->cycles_launched = ro.launched;
+        st->inner_cycles = 0;
+        st->outer_steps = 0;
+        st->res0 = res0;
+        st->res_final = resc;
+        st->rel_final = res0 > 0 ? resc / res0 : 0.0;
+        st->history_len = hl;
+    }
+    if (ro.status == HJ_ERR_DIVERGED) return seterr(HJ_ERR_DIVERGED, "residual became non-finite at cycle %lld", ro.c);
+    if (ro.status == HJ_ERR_NOT_CONVERGED)
+        return seterr(HJ_ERR_NOT_CONVERGED, "tolerance %g not met after %lld cycles (rel %g)", h->p.tol, ro.c,
+                      res0 > 0 ? resc / res0 : 0.0);
+    return HJ_OK;
+}
+
+// Mixed-precision iterative refinement, u (binary64, device) in/out.
+int solve_ir(hj_handle *h, const double *f, double *u, bool transpose, cudaStream_t s, hj_stats *st) {
+    const bool sig = h->d.sigma != nullptr;
+    const CycArgs geo = base_args(h, transpose);
+    const bool bf16 = h->fam_inner == FAM_BF16;
+    const size_t dsz = bf16 ? 2 : 4;
+    CKR(cudaMemcpyAsync(h->ubuf, u, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+    // outer residual of u_0 -> r32
+    {
+        const RedArgs red = red_args(h, RED_STORE, 0.0, 0);
+        CKR(launch_residual_ex(h->d.dim, 1, f, u, h->d.sigma, h->d.ld, h->d.nx, h->d.ny, geo.cW, geo.cE, geo.cS,
+                               geo.cN, geo.dconst, 0, h->r32, red, s));
+        CKR(cudaMemcpyAsync(h->h_rstore, h->rstore, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CKR(cudaEventRecord(h->ev, s));
+        CKR(cudaEventSynchronize(h->ev));
+    }
+    double *cur = u, *other = (double *)h->ubuf;
+    double r0 = sqrt(h->h_rstore[0]), rn = r0;
+    long long inner_total = 0, inner_launched = 0;
+    int o = 0, status = HJ_OK;
+    long long hl = 0;
+    CycArgs base = geo;
+    base.f = h->r32;
+    base.dinv = h->dinv32;
+    for (;; ++o) {
+        if (st && st->history && o < st->history_cap) { st->history[o] = rn; hl = o + 1; }
+        if (!std::isfinite(rn)) { status = HJ_ERR_DIVERGED; break; }
+        if (rn <= h->p.tol * r0) { status = HJ_OK; break; }
+        if (o >= h->p.max_outer) { status = HJ_ERR_NOT_CONVERGED; break; }
+        CKR(cudaMemsetAsync(h->dA, 0, h->grid_elems * dsz, s));
+        RunOut ro;
+        CKS(run_cycles(h, h->k_inner, false, sig, base, h->dA, h->dB, h->p.inner_tol, h->p.inner_max_cycles, 0, s,
+                       &ro, nullptr, 0, nullptr));
+        inner_total += ro.c;
+        inner_launched += ro.launched;
+        const void *dsel = (ro.c & 1) ? h->dB : h->dA;
+        const RedArgs red = red_args(h, RED_STORE, 0.0, 0);
+        CKR(launch_update_residual_ex(h->d.dim, f, cur, dsel, bf16 ? 1 : 0, other, h->d.sigma, h->r32, h->d.ld,
+                                      h->d.nx, h->d.ny, geo.cW, geo.cE, geo.cS, geo.cN, geo.dconst, red, s));
+        CKR(cudaMemcpyAsync(h->h_rstore, h->rstore, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CKR(cudaEventRecord(h->ev, s));
+        CKR(cudaEventSynchronize(h->ev));
+        rn = sqrt(h->h_rstore[0]);
+        std::swap(cur, other);
+    }
+    if (cur != u) CKR(cudaMemcpyAsync(u, cur, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+    CKR(cudaStreamSynchronize(s));
+    if (st) {
+        st->cycles = inner_total;
+        st->cycles_launched = inner_launched;
+        st->inner_cycles = inner_total;
+        st->outer_steps = o;
+        st->res0 = r0;
+        st->res_final = rn;
+        st->rel_final = r0 > 0 ? rn / r0 : 0.0;
+        st->history_len = hl;
+    }
+    if (status == HJ_ERR_DIVERGED) return seterr(HJ_ERR_DIVERGED, "refinement residual became non-finite");
+    if (status == HJ_ERR_NOT_CONVERGED)
+        return seterr(HJ_ERR_NOT_CONVERGED, "refinement: tolerance %g not met after %d outer steps (rel %g)",
+                      h->p.tol, o, r0 > 0 ? rn / r0 : 0.0);
+    return HJ_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int check_ptr(const hj_handle *h, const void *p, const char *name) {
+    if (!p) return seterr(HJ_ERR_INVALID_ARG, "%s is NULL", name);
+    if (((uintptr_t)p) & 15) return seterr(HJ_ERR_INVALID_ARG, "%s is not 16-byte aligned", name);
+    (void)h;
+    return HJ_OK;
+}
+
+void fill_stats_config(const hj_handle *h, hj_stats *st, double t0) {
+    if (!st) return;
+    st->wall_ms = now_ms() - t0;
+    st->tile_x = h->p.tile_x;
+    st->tile_y = h->d.dim == 2 ? h->p.tile_y : 1;
+    st->k = h->p.k;
+    st->persistent = 0;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void hj_default_params(hj_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->method = HJ_METHOD_HIER;
+    p->tile_x = 32;
+    p->tile_y = 32;
+    p->k = 16;
+    p->precision = HJ_PREC_F64;
+    p->check_every = 64;
+    p->max_cycles = 10000000;
+    p->tol = 1e-6;
+    p->fixed_cycles = 0;
+    p->inner_tol = 1e-4;
+    p->inner_max_cycles = 1000000;
+    p->max_outer = 60;
+    p->persistent = -1;
+    p->autotune = 0;
+}
+
+const char *hj_error_string(int s) {
+    switch (s) {
+    case HJ_OK: return "success";
+    case HJ_ERR_INVALID_ARG: return "invalid argument";
+    case HJ_ERR_NOT_DIAG_DOMINANT: return "stencil is not diagonally dominant";
+    case HJ_ERR_UNSUPPORTED: return "unsupported tile shape or mode";
+    case HJ_ERR_CUDA: return "CUDA error";
+    case HJ_ERR_NOT_CONVERGED: return "not converged";
+    case HJ_ERR_DIVERGED: return "diverged";
+    case HJ_ERR_TIMEOUT: return "device wait timed out";
+    case HJ_ERR_NO_MEMORY: return "out of device memory";
+    default: return "unknown status";
+    }
+}
+
+const char *hj_last_error(void) { return g_err; }
+
+int hj_tile_shapes(int dim, int precision, int *xy, int cap) {
+    const int fam = precision == HJ_PREC_F64 ? FAM_F64 : precision == HJ_PREC_BF16CORR_IR ? FAM_BF16 : FAM_F32;
+    int n = 0, m = 0;
+    const TileKernelInfo *k = family_tiles(fam, &n);
+    for (int i = 0; i < n; ++i) {
+        if (k[i].dim != dim) continue;
+        if (xy && m < cap) {
+            xy[2 * m] = k[i].tx;
+            xy[2 * m + 1] = k[i].ty;
+        }
+        ++m;
+    }
+    return m;
+}
+
+void hj_destroy(hj_handle *h) {
+    if (!h) return;
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    void *dev[] = {h->ubuf, h->dinv_outer, h->dinv32, h->r32, h->dA, h->dB, h->hf, h->hu, h->partials, h->gpart,
+                   h->hist, h->rstore, h->gcnt, h->fcnt, h->ctl};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    void *pin[] = {h->h_ctl, h->h_ctl_init, h->h_hist, h->h_rstore};
+    for (void *p : pin)
+        if (p) cudaFreeHost(p);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->ev) cudaEventDestroy(h->ev);
+    delete h;
+}
+
+int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
+    if (!out) return seterr(HJ_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc) return seterr(HJ_ERR_INVALID_ARG, "desc is NULL");
+    hj_params p;
+    if (params) p = *params;
+    else hj_default_params(&p);
+    const hj_desc &d = *desc;
+    if (d.dim != 1 && d.dim != 2) return seterr(HJ_ERR_INVALID_ARG, "dim must be 1 or 2 (got %d)", d.dim);
+    if (d.nx < 1 || d.ny < 1) return seterr(HJ_ERR_INVALID_ARG, "nx, ny must be >= 1 (got %d, %d)", d.nx, d.ny);
+    if (d.dtype != HJ_F64 && d.dtype != HJ_F32) return seterr(HJ_ERR_INVALID_ARG, "dtype must be HJ_F64 or HJ_F32");
+    const size_t esz = d.dtype == HJ_F64 ? 8 : 4;
+    if (d.ld < (long long)d.nx + 2) return seterr(HJ_ERR_INVALID_ARG, "ld (%lld) < nx + 2", d.ld);
+    if ((d.ld * (long long)esz) % 16) return seterr(HJ_ERR_INVALID_ARG, "ld * element size must be a multiple of 16 bytes");
+    if (d.dim == 1 && d.ny > 65535) return seterr(HJ_ERR_INVALID_ARG, "1D: at most 65535 rows");
+    if (d.dim == 2 && (d.ny + 7) / 8 > 65535) return seterr(HJ_ERR_INVALID_ARG, "2D: ny must be <= 524280");
+    if (p.precision < HJ_PREC_F64 || p.precision > HJ_PREC_BF16CORR_IR)
+        return seterr(HJ_ERR_INVALID_ARG, "unknown precision %d", p.precision);
+    const bool ir = p.precision == HJ_PREC_F32_IR || p.precision == HJ_PREC_BF16CORR_IR;
+    if ((p.precision == HJ_PREC_F32) != (d.dtype == HJ_F32))
+        return seterr(HJ_ERR_INVALID_ARG, "dtype HJ_F32 goes with precision HJ_PREC_F32 only (binary64 arrays otherwise)");
+    if (p.method != HJ_METHOD_HIER && p.method != HJ_METHOD_CLASSIC)
+        return seterr(HJ_ERR_INVALID_ARG, "unknown method %d", p.method);
+    if (p.k < 1) return seterr(HJ_ERR_INVALID_ARG, "k must be >= 1");
+    if (!(p.tol >= 0.0)) return seterr(HJ_ERR_INVALID_ARG, "tol must be >= 0");
+    if (p.max_cycles < 0) return seterr(HJ_ERR_INVALID_ARG, "max_cycles must be >= 0");
+    if (ir && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)) return seterr(HJ_ERR_INVALID_ARG, "inner_tol must be in (0,1)");
+    if (ir && p.inner_max_cycles < 1) return seterr(HJ_ERR_INVALID_ARG, "inner_max_cycles must be >= 1");
+    if (ir && p.method == HJ_METHOD_CLASSIC) return seterr(HJ_ERR_UNSUPPORTED, "refinement uses hierarchical cycles");
+    if (p.check_every < 1) p.check_every = 1;
+    if (p.check_every > kHistCap / 2) p.check_every = kHistCap / 2;
+    p.check_every += p.check_every & 1;
+    if (d.dim == 1) p.tile_y = 1;
+
+    // diagonal dominance (Section 2.1): d_p >= |cW| + |cE| + |cS| + |cN|, d_p > 0
+    const double off = fabs(d.cW) + fabs(d.cE) + (d.dim == 2 ? fabs(d.cS) + fabs(d.cN) : 0.0);
+    const int rows = d.dim == 2 ? d.ny + 2 : d.ny;
+    double dmin = d.cD + d.sigma_const;
+    if (d.sigma) {
+        std::vector<double> hs((size_t)rows * d.ld);
+        cudaError_t e = cudaMemcpy(hs.data(), d.sigma, hs.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return seterr(HJ_ERR_CUDA, "reading sigma: %s", cudaGetErrorString(e));
+        const int r0 = d.dim == 2 ? 1 : 0, r1 = d.dim == 2 ? d.ny : d.ny - 1;
+        double smin = INFINITY;
+        for (int j = r0; j <= r1; ++j)
+            for (int i = 1; i <= d.nx; ++i) smin = std::min(smin, hs[(size_t)j * d.ld + i]);
+        dmin = d.cD + d.sigma_const + smin;
+    }
+    if (!(dmin > 0.0) || dmin < off)
+        return seterr(HJ_ERR_NOT_DIAG_DOMINANT, "min diagonal %g < sum |off-diagonal| %g", dmin, off);
+
+    hj_handle *h = new hj_handle();
+    h->d = d;
+    h->p = p;
+    h->ir = ir;
+    h->rows = rows;
+    h->esz = esz;
+    h->grid_elems = (size_t)rows * d.ld;
+    h->grid_bytes = h->grid_elems * esz;
+    h->fam_outer = p.precision == HJ_PREC_F32 ? FAM_F32 : FAM_F64;
+    h->fam_inner = p.precision == HJ_PREC_BF16CORR_IR ? FAM_BF16 : FAM_F32;
+    int st = HJ_OK;
+#define HJ_FAIL(code, ...)              \
+    do {                                \
+        st = seterr(code, __VA_ARGS__); \
+        hj_destroy(h);                  \
+        return st;                      \
+    } while (0)
+#define HJ_ALLOC(ptr, bytes)                                                               \
+    do {                                                                                   \
+        if (cudaMalloc((void **)&(ptr), (bytes)) != cudaSuccess) {                         \
+            cudaGetLastError();                                                            \
+            HJ_FAIL(HJ_ERR_NO_MEMORY, "cudaMalloc of %zu bytes failed", (size_t)(bytes)); \
+        }                                                                                  \
+    } while (0)
+    if (cudaGetDevice(&h->dev) != cudaSuccess) HJ_FAIL(HJ_ERR_CUDA, "no CUDA device");
+    cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
+
+    if (ir) {
+        h->k_inner = find_tile(h->fam_inner, d.dim, p.tile_x, p.tile_y);
+        if (!h->k_inner) HJ_FAIL(HJ_ERR_UNSUPPORTED, "tile %dx%d not built for this precision", p.tile_x, p.tile_y);
+    } else if (p.method == HJ_METHOD_CLASSIC) {
+        h->k_classic = family_classic(h->fam_outer, d.dim);
+    } else {
+        h->k_outer = find_tile(h->fam_outer, d.dim, p.tile_x, p.tile_y);
+        if (!h->k_outer) HJ_FAIL(HJ_ERR_UNSUPPORTED, "tile %dx%d not built for this precision", p.tile_x, p.tile_y);
+    }
+    // reduction workspace sized for the largest grid any kernel of this handle launches
+    size_t maxb = (size_t)aux_max_blocks(d.dim, d.nx, d.ny);
+    for (int fam = 0; fam < 3; ++fam) {
+        int n = 0;
+        const TileKernelInfo *k = family_tiles(fam, &n);
+        for (int i = 0; i < n; ++i) {
+            if (k[i].dim != d.dim) continue;
+            dim3 g, b;
+            geometry(h, &k[i], false, &g, &b);
+            maxb = std::max(maxb, (size_t)g.x * g.y);
+        }
+    }
+    h->max_blocks = maxb;
+    h->max_groups = (maxb + kGroup - 1) / kGroup;
+    HJ_ALLOC(h->ubuf, h->grid_bytes);
+    HJ_ALLOC(h->partials, 2 * maxb * sizeof(double));
+    HJ_ALLOC(h->gpart, 2 * h->max_groups * sizeof(double));
+    HJ_ALLOC(h->gcnt, h->max_groups * sizeof(unsigned));
+    HJ_ALLOC(h->fcnt, sizeof(unsigned));
+    HJ_ALLOC(h->hist, kHistCap * sizeof(double));
+    HJ_ALLOC(h->ctl, sizeof(Ctl));
+    HJ_ALLOC(h->rstore, 2 * sizeof(double));
+    if (cudaMemset(h->gcnt, 0, h->max_groups * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(h->fcnt, 0, sizeof(unsigned)) != cudaSuccess)
+        HJ_FAIL(HJ_ERR_CUDA, "cudaMemset failed");
+    if (cudaMallocHost((void **)&h->h_ctl, sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void **)&h->h_ctl_init, sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void **)&h->h_hist, kHistCap * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void **)&h->h_rstore, 2 * sizeof(double)) != cudaSuccess)
+        HJ_FAIL(HJ_ERR_NO_MEMORY, "cudaMallocHost failed");
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess)
+        HJ_FAIL(HJ_ERR_CUDA, "stream/event creation failed");
+
+    const double dconst = d.cD + d.sigma_const;
+    const int r0 = d.dim == 2 ? 1 : 0;
+    if (ir) {
+        const bool bf16 = h->fam_inner == FAM_BF16;
+        HJ_ALLOC(h->r32, h->grid_elems * sizeof(float));
+        HJ_ALLOC(h->dA, h->grid_elems * (bf16 ? 2 : 4));
+        HJ_ALLOC(h->dB, h->grid_elems * (bf16 ? 2 : 4));
+        if (cudaMemset(h->r32, 0, h->grid_elems * sizeof(float)) != cudaSuccess ||
+            cudaMemset(h->dA, 0, h->grid_elems * (bf16 ? 2 : 4)) != cudaSuccess ||
+            cudaMemset(h->dB, 0, h->grid_elems * (bf16 ? 2 : 4)) != cudaSuccess)
+            HJ_FAIL(HJ_ERR_CUDA, "cudaMemset failed");
+        if (d.sigma) {
+            HJ_ALLOC(h->dinv32, h->grid_elems * sizeof(float));
+            cudaMemset(h->dinv32, 0, h->grid_elems * sizeof(float));
+            if (launch_make_dinv_box(d.sigma, dconst, d.ld, r0, d.ny, 1, d.nx, FAM_F32, h->dinv32, 0) != cudaSuccess)
+                HJ_FAIL(HJ_ERR_CUDA, "dinv kernel failed");
+        }
+    } else if (d.sigma) {
+        const size_t tsz = h->fam_outer == FAM_F64 ? 8 : 4;
+        HJ_ALLOC(h->dinv_outer, h->grid_elems * tsz);
+        cudaMemset(h->dinv_outer, 0, h->grid_elems * tsz);
+        if (launch_make_dinv_box(d.sigma, dconst, d.ld, r0, d.ny, 1, d.nx, h->fam_outer, h->dinv_outer, 0) !=
+            cudaSuccess)
+            HJ_FAIL(HJ_ERR_CUDA, "dinv kernel failed");
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) HJ_FAIL(HJ_ERR_CUDA, "create: %s", cudaGetErrorString(cudaGetLastError()));
+#undef HJ_ALLOC
+#undef HJ_FAIL
+    *out = h;
+    g_err[0] = 0;
+    return HJ_OK;
+}
+
+int hj_solve(hj_handle *h, const void *f, void *u, hj_stream stream, hj_stats *stats) {
+    if (!h) return seterr(HJ_ERR_INVALID_ARG, "handle is NULL");
+    if (!f || !u) return seterr(HJ_ERR_INVALID_ARG, "f and u must be non-NULL");
+    const double t0 = now_ms();
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool fdev = is_device_ptr(f), udev = is_device_ptr(u);
+    const void *fd = f;
+    void *ud = u;
+    if (!fdev || !udev) {
+        if (!h->hf) CKR(cudaMalloc(&h->hf, h->grid_bytes));
+        if (!h->hu) CKR(cudaMalloc(&h->hu, h->grid_bytes));
+        if (!fdev) {
+            CKR(cudaMemcpyAsync(h->hf, f, h->grid_bytes, cudaMemcpyHostToDevice, s));
+            fd = h->hf;
+        }
+        if (!udev) {
+            CKR(cudaMemcpyAsync(h->hu, u, h->grid_bytes, cudaMemcpyHostToDevice, s));
+            ud = h->hu;
+        }
+    }
+    CKS(check_ptr(h, fd, "f"));
+    CKS(check_ptr(h, ud, "u"));
+    int st = h->ir ? solve_ir(h, (const double *)fd, (double *)ud, false, s, stats)
+                   : solve_plain(h, fd, ud, false, s, stats);
+    if (!udev && (st == HJ_OK || st == HJ_ERR_NOT_CONVERGED || st == HJ_ERR_DIVERGED)) {
+        CKR(cudaMemcpyAsync(u, ud, h->grid_bytes, cudaMemcpyDeviceToHost, s));
+        CKR(cudaStreamSynchronize(s));
+    }
+    fill_stats_config(h, stats, t0);
+    return st;
+}
+
+int hj_residual(hj_handle *h, const void *f, const void *u, double *abs_l2, double *rel_l2, hj_stream stream) {
+    if (!h) return seterr(HJ_ERR_INVALID_ARG, "handle is NULL");
+    CKS(check_ptr(h, f, "f"));
+    CKS(check_ptr(h, u, "u"));
+    double rr = 0, ff = 0;
+    CKS(residual_of(h, f, u, false, &rr, &ff, (cudaStream_t)stream));
+    const double a = sqrt(rr);
+    if (abs_l2) *abs_l2 = a;
+    if (rel_l2) *rel_l2 = ff > 0 ? a / sqrt(ff) : a;
+    return HJ_OK;
+}
+
+int hj_solve_adjoint(hj_handle *h, const void *g, const void *u, void *dl_df, void *dl_dsigma, hj_stream stream,
+                     hj_stats *stats) {
+    if (!h) return seterr(HJ_ERR_INVALID_ARG, "handle is NULL");
+    CKS(check_ptr(h, g, "g"));
+    CKS(check_ptr(h, u, "u"));
+    CKS(check_ptr(h, dl_df, "dl_df"));
+    if (dl_dsigma) CKS(check_ptr(h, dl_dsigma, "dl_dsigma"));
+    const double t0 = now_ms();
+    cudaStream_t s = (cudaStream_t)stream;
+    // lambda_0 = 0 with a zero ghost ring (homogeneous Dirichlet data of the adjoint)
+    CKR(cudaMemsetAsync(dl_df, 0, h->grid_bytes, s));
+    int st = h->ir ? solve_ir(h, (const double *)g, (double *)dl_df, true, s, stats)
+                   : solve_plain(h, g, dl_df, true, s, stats);
+    if (st != HJ_OK && st != HJ_ERR_NOT_CONVERGED) return st;
+    if (dl_dsigma) {
+        CKR(cudaMemsetAsync(dl_dsigma, 0, h->grid_elems * sizeof(double), s));
+        CKR(launch_grad_sigma_ex(h->d.dim, h->d.dtype == HJ_F64, dl_df, u, (double *)dl_dsigma, h->d.ld, h->d.nx,
+                                 h->d.ny, s));
+        CKR(cudaStreamSynchronize(s));
+    }
+    fill_stats_config(h, stats, t0);
+    return st;
+}
+
+int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, const void *const *f, void *const *u,
+                     hj_stream stream, hj_stats *stats, long long *cycles_out) {
+    (void)h; (void)nprob; (void)descs; (void)f; (void)u; (void)stream; (void)stats; (void)cycles_out;
+    return seterr(HJ_ERR_UNSUPPORTED, "batched solve not available in this build");
+}
+
+}  // extern "C"

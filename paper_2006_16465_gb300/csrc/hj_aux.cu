@@ -1,0 +1,218 @@
+// hj_aux.cu -- grid-wide helper kernels: binary64 residual (with optional
+// ||f|| and binary32 copy of r for refinement), the fused refinement update
+// u_{o+1} = u_o + d with the next residual, the adjoint gradient
+// dL/dsigma = -lambda * u, and the per-point inverse diagonal.
+#include "hj_internal.cuh"
+
+namespace hj {
+
+namespace {
+
+// (A u)_p - f_p evaluated as f - (d*u + cW*uW + cE*uE + cS*uS + cN*uN), every
+// operation rounded separately (binary64).
+template <bool D2>
+__device__ __forceinline__ double resid_exact(double f, double d, double u, double uW, double uE, double uS,
+                                              double uN, double cW, double cE, double cS, double cN) {
+    double au = __dmul_rn(d, u);
+    au = __dadd_rn(au, __dmul_rn(cW, uW));
+    au = __dadd_rn(au, __dmul_rn(cE, uE));
+    if (D2) {
+        au = __dadd_rn(au, __dmul_rn(cS, uS));
+        au = __dadd_rn(au, __dmul_rn(cN, uN));
+    }
+    return __dsub_rn(f, au);
+}
+
+struct AuxArgs {
+    const void *f;        // user dtype
+    const void *u;        // user dtype
+    const void *d;        // refinement correction (float or bf16), nullable
+    void *uout;           // refinement: u + d (binary64)
+    const double *sigma;  // nullable
+    float *r32;           // nullable: binary32 copy of r (interior; ghosts untouched)
+    long long ld;
+    int nx, ny;
+    double cW, cE, cS, cN, dconst;
+    RedArgs red;
+};
+
+template <int D> struct AuxGeom;
+template <> struct AuxGeom<2> {
+    static __device__ __forceinline__ bool idx(const AuxArgs &a, int &i, int &j) {
+        i = 1 + blockIdx.x * 32 + threadIdx.x;
+        j = 1 + blockIdx.y * 8 + threadIdx.y;
+        return i <= a.nx && j <= a.ny;
+    }
+};
+template <> struct AuxGeom<1> {
+    static __device__ __forceinline__ bool idx(const AuxArgs &a, int &i, int &j) {
+        i = 1 + blockIdx.x * 256 + threadIdx.x;
+        j = blockIdx.y;
+        return i <= a.nx;
+    }
+};
+
+template <typename T, int D, bool WITH_F>
+__global__ void __launch_bounds__(256) residual_kernel(const AuxArgs a) {
+    int i, j;
+    double rr = 0.0, ff = 0.0;
+    if (AuxGeom<D>::idx(a, i, j)) {
+        const T *u = (const T *)a.u;
+        const long long q = (long long)j * a.ld + i;
+        const double fv = (double)((const T *)a.f)[q];
+        const double d = a.sigma ? __dadd_rn(a.dconst, a.sigma[q]) : a.dconst;
+        const double r = resid_exact<D == 2>(fv, d, (double)u[q], (double)u[q - 1], (double)u[q + 1],
+                                             D == 2 ? (double)u[q - a.ld] : 0.0,
+                                             D == 2 ? (double)u[q + a.ld] : 0.0, a.cW, a.cE, a.cS, a.cN);
+        rr = r * r;
+        ff = fv * fv;
+        if (a.r32) a.r32[q] = (float)r;
+    }
+    if (WITH_F) {
+        const double vals[2] = {rr, ff};
+        reduce_grid<2>(a.red, vals);
+    } else {
+        const double vals[1] = {rr};
+        reduce_grid<1>(a.red, vals);
+    }
+}
+
+template <typename DS>
+__device__ __forceinline__ double ld_corr(const DS *p) { return (double)__ldg(p); }
+template <>
+__device__ __forceinline__ double ld_corr<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return (double)__bfloat162float(__ldg(p));
+}
+
+// u_out = u_in + d on interior points, and r = f - A u_out (binary64) with its
+// binary32 copy and ||r||^2.  Neighbour values of u_out are re-formed from
+// u_in and d (d is zero on the ghost ring), so no point reads a value that
+// another thread is writing.
+template <typename DS, int D>
+__global__ void __launch_bounds__(256) update_residual_kernel(const AuxArgs a) {
+    int i, j;
+    double rr = 0.0;
+    if (AuxGeom<D>::idx(a, i, j)) {
+        const double *u = (const double *)a.u;
+        const DS *dd = (const DS *)a.d;
+        const long long q = (long long)j * a.ld + i;
+        const double uc = __dadd_rn(u[q], ld_corr<DS>(dd + q));
+        const double uW = __dadd_rn(u[q - 1], ld_corr<DS>(dd + q - 1));
+        const double uE = __dadd_rn(u[q + 1], ld_corr<DS>(dd + q + 1));
+        double uS = 0.0, uN = 0.0;
+        if (D == 2) {
+            uS = __dadd_rn(u[q - a.ld], ld_corr<DS>(dd + q - a.ld));
+            uN = __dadd_rn(u[q + a.ld], ld_corr<DS>(dd + q + a.ld));
+        }
+        ((double *)a.uout)[q] = uc;
+        const double fv = ((const double *)a.f)[q];
+        const double d = a.sigma ? __dadd_rn(a.dconst, a.sigma[q]) : a.dconst;
+        const double r = resid_exact<D == 2>(fv, d, uc, uW, uE, uS, uN, a.cW, a.cE, a.cS, a.cN);
+        rr = r * r;
+        a.r32[q] = (float)r;
+    }
+    const double vals[1] = {rr};
+    reduce_grid<1>(a.red, vals);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) grad_sigma_kernel(const T *lam, const T *u, double *dsig, long long ld,
+                                                         int nx, int ny) {
+    int i, j;
+    AuxArgs g;
+    g.nx = nx;
+    g.ny = ny;
+    if (AuxGeom<D>::idx(g, i, j)) {
+        const long long q = (long long)j * ld + i;
+        dsig[q] = -((double)lam[q] * (double)u[q]);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) make_dinv_kernel(const double *sigma, double dconst, long long ld,
+                                                       int rows, int cols, T *dinv) {
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i < cols && j < rows) {
+        const long long q = (long long)j * ld + i;
+        dinv[q] = (T)__drcp_rn(__dadd_rn(dconst, sigma[q]));
+    }
+}
+
+dim3 aux_grid(int dim, int nx, int ny) {
+    return dim == 2 ? dim3((nx + 31) / 32, (ny + 7) / 8) : dim3((nx + 255) / 256, ny);
+}
+dim3 aux_block(int dim) { return dim == 2 ? dim3(32, 8) : dim3(256); }
+
+}  // namespace
+
+// rows/cols: the index box of interior points, in grid coordinates
+cudaError_t launch_make_dinv_box(const double *sigma, double dconst, long long ld, int row0, int rows, int col0,
+                                 int cols, int family, void *dinv, cudaStream_t s) {
+    const size_t off = (size_t)row0 * ld + col0;
+    dim3 grid((cols + 255) / 256, rows);
+    if (family == FAM_F64)
+        make_dinv_kernel<double><<<grid, 256, 0, s>>>(sigma + off, dconst, ld, rows, cols, (double *)dinv + off);
+    else
+        make_dinv_kernel<float><<<grid, 256, 0, s>>>(sigma + off, dconst, ld, rows, cols, (float *)dinv + off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_ex(int dim, int user_f64, const void *f, const void *u, const double *sigma,
+                               long long ld, int nx, int ny, double cW, double cE, double cS, double cN,
+                               double dconst, int with_fnorm, float *r32, RedArgs red, cudaStream_t s) {
+    AuxArgs a = {};
+    a.f = f; a.u = u; a.sigma = sigma; a.r32 = r32; a.ld = ld; a.nx = nx; a.ny = ny;
+    a.cW = cW; a.cE = cE; a.cS = cS; a.cN = cN; a.dconst = dconst; a.red = red;
+    const dim3 g = aux_grid(dim, nx, ny), b = aux_block(dim);
+#define HJ_RES_LAUNCH(T, D)                                                              \
+    do {                                                                                 \
+        if (with_fnorm) residual_kernel<T, D, true><<<g, b, 0, s>>>(a);                 \
+        else residual_kernel<T, D, false><<<g, b, 0, s>>>(a);                           \
+    } while (0)
+    if (user_f64) {
+        if (dim == 2) HJ_RES_LAUNCH(double, 2); else HJ_RES_LAUNCH(double, 1);
+    } else {
+        if (dim == 2) HJ_RES_LAUNCH(float, 2); else HJ_RES_LAUNCH(float, 1);
+    }
+#undef HJ_RES_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_residual_ex(int dim, const double *f, const double *uin, const void *d, int d_bf16,
+                                      double *uout, const double *sigma, float *r32, long long ld, int nx, int ny,
+                                      double cW, double cE, double cS, double cN, double dconst, RedArgs red,
+                                      cudaStream_t s) {
+    AuxArgs a = {};
+    a.f = f; a.u = uin; a.d = d; a.uout = uout; a.sigma = sigma; a.r32 = r32; a.ld = ld; a.nx = nx; a.ny = ny;
+    a.cW = cW; a.cE = cE; a.cS = cS; a.cN = cN; a.dconst = dconst; a.red = red;
+    const dim3 g = aux_grid(dim, nx, ny), b = aux_block(dim);
+    if (d_bf16) {
+        if (dim == 2) update_residual_kernel<__nv_bfloat16, 2><<<g, b, 0, s>>>(a);
+        else update_residual_kernel<__nv_bfloat16, 1><<<g, b, 0, s>>>(a);
+    } else {
+        if (dim == 2) update_residual_kernel<float, 2><<<g, b, 0, s>>>(a);
+        else update_residual_kernel<float, 1><<<g, b, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_sigma_ex(int dim, int user_f64, const void *lam, const void *u, double *dsig, long long ld,
+                                 int nx, int ny, cudaStream_t s) {
+    const dim3 g = aux_grid(dim, nx, ny), b = aux_block(dim);
+    if (user_f64) {
+        if (dim == 2) grad_sigma_kernel<double, 2><<<g, b, 0, s>>>((const double *)lam, (const double *)u, dsig, ld, nx, ny);
+        else grad_sigma_kernel<double, 1><<<g, b, 0, s>>>((const double *)lam, (const double *)u, dsig, ld, nx, ny);
+    } else {
+        if (dim == 2) grad_sigma_kernel<float, 2><<<g, b, 0, s>>>((const float *)lam, (const float *)u, dsig, ld, nx, ny);
+        else grad_sigma_kernel<float, 1><<<g, b, 0, s>>>((const float *)lam, (const float *)u, dsig, ld, nx, ny);
+    }
+    return cudaGetLastError();
+}
+
+int aux_max_blocks(int dim, int nx, int ny) {
+    const dim3 g = aux_grid(dim, nx, ny);
+    return (int)(g.x * g.y);
+}
+
+}  // namespace hj

@@ -1,0 +1,433 @@
+// hj_cycle.cuh -- hierarchical Jacobi cycle kernels (templates).
+//
+// One cycle (Sections 3.3 and 4.1): every subdomain (tile) stages its interior
+// plus a one-point halo from the iterate u_c, runs k Jacobi subiterations with
+// the halo frozen, and writes its interior into the other buffer u_{c+1}.
+//
+// GB300 mapping (differs from the paper's one-thread-per-point shared-memory
+// kernel, which targets a 48 KB/SM Volta):
+//   * a 2D tile of TX x TY = (32*C) x (R*NW) points is one CTA of NW warps; warp w
+//     owns the band of R rows starting at row y0 + w*R, lane l owns the C
+//     consecutive columns x0 + l*C .. x0 + l*C + C-1 of that band;
+//   * the tile and its halo go from HBM straight into registers with coalesced
+//     row loads (one 128*C-byte row segment per warp instruction);
+//   * the k subiterations run entirely in registers: N/S neighbours are the
+//     thread's own registers, W/E neighbours arrive by warp shuffle, the frozen
+//     halo column sits in registers of lanes 0 and 31, and only the two edge
+//     rows of each band go through a ping-pong shared-memory buffer (one
+//     barrier per subiteration, none when NW = 1);
+//   * the residual ||f - A u_c||^2 of the staged input is formed in the first
+//     subiteration (r_p = d_p (u'_p - u_p)) and reduced deterministically
+//     (warp butterfly, CTA, two-level grid) inside the same launch.
+// The two containers of the paper's listing become the register state plus the
+// separate global output buffer: the result equals the container rule exactly.
+#pragma once
+
+#include "hj_internal.cuh"
+
+namespace hj {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename T>
+struct Coef {
+    T cW, cE, cS, cN;   // raw stencil (exact / sigma paths)
+    T bW, bE, bS, bN;   // -c * (1/d) for the constant-diagonal fast path
+    T invd, dconst;
+};
+
+template <typename T>
+__device__ __forceinline__ Coef<T> make_coef(const CycArgs &a);
+template <>
+__device__ __forceinline__ Coef<double> make_coef<double>(const CycArgs &a) {
+    Coef<double> k;
+    k.cW = a.cW; k.cE = a.cE; k.cS = a.cS; k.cN = a.cN;
+    k.bW = k.bE = k.bS = k.bN = 0.0;   // unused: binary64 kernels take the exact path
+    k.invd = a.invd;
+    k.dconst = a.dconst;
+    return k;
+}
+template <>
+__device__ __forceinline__ Coef<float> make_coef<float>(const CycArgs &a) {
+    Coef<float> k;
+    k.cW = a.fW; k.cE = a.fE; k.cS = a.fS; k.cN = a.fN;
+    k.bW = a.gW; k.bE = a.gE; k.bS = a.gS; k.bN = a.gN;
+    k.invd = a.finvd;
+    k.dconst = a.fdconst;
+    return k;
+}
+
+// One Jacobi point update.
+//  EXACT (binary64): acc = cW*W; acc += cE*E; [acc += cS*S; acc += cN*N;]
+//                    u' = (f - acc) * (1/d), every operation rounded separately.
+//  fast, constant d: u' = bW W + bE E + bS S + bN N + f/d as a fused chain.
+//  fast, per-point d: u' = (f - cW W - cE E - cS S - cN N) * (1/d_p).
+// If WANT_RES, res receives f - (A u)_p of the *old* value (unscaled by d for
+// the fast constant-d path, where the caller multiplies the sum by d^2).
+template <typename T, bool EXACT, bool SIG, bool D2, bool WANT_RES>
+__device__ __forceinline__ T point_update(const Coef<T> &k, T g, T iv, T W, T E, T S, T N, T old, T &res) {
+    if constexpr (EXACT) {
+        double acc = __dmul_rn(k.cW, W);
+        acc = __dadd_rn(acc, __dmul_rn(k.cE, E));
+        if constexpr (D2) {
+            acc = __dadd_rn(acc, __dmul_rn(k.cS, S));
+            acc = __dadd_rn(acc, __dmul_rn(k.cN, N));
+        }
+        const double t = __dsub_rn(g, acc);
+        const double inv = SIG ? (double)iv : (double)k.invd;
+        if constexpr (WANT_RES) {
+            const double dp = SIG ? __drcp_rn(iv) : (double)k.dconst;
+            res = (T)__dsub_rn(t, __dmul_rn(dp, old));
+        }
+        return (T)__dmul_rn(t, inv);
+    } else if constexpr (SIG) {
+        T t = g;
+        t = fma(-k.cW, W, t);
+        t = fma(-k.cE, E, t);
+        if constexpr (D2) {
+            t = fma(-k.cS, S, t);
+            t = fma(-k.cN, N, t);
+        }
+        const T nv = t * iv;
+        if constexpr (WANT_RES) res = (nv - old) * ((T)1 / iv);
+        return nv;
+    } else {
+        T t = g;
+        if constexpr (D2) {
+            t = fma(k.bN, N, t);
+            t = fma(k.bS, S, t);
+        }
+        t = fma(k.bE, E, t);
+        t = fma(k.bW, W, t);
+        if constexpr (WANT_RES) res = t - old;
+        return t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2D tile
+// ---------------------------------------------------------------------------
+template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG, bool RES, bool PART>
+__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type tile2d(const CycArgs &a, const int x0, const int y0, T *xbuf) {
+    constexpr int TX = 32 * C;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int yb = y0 + w * R;
+    const int xl = x0 + lane * C;
+    const long long ld = a.ld;
+    const int nx = a.nx, ny = a.ny;
+    const S *__restrict__ uin = (const S *)a.uin;
+    const T *__restrict__ f = (const T *)a.f;
+    const T *__restrict__ dinv = (const T *)a.dinv;
+    const Coef<T> kc = make_coef<T>(a);
+
+    T v[R][C], g[R][C];
+    T dv[SIG ? R : 1][SIG ? C : 1];
+    T hx[R], top[C], bot[C];
+
+    // ---- stage tile + halo (u_c) and RHS into registers ----
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int row = yb + r;
+        const bool rowok = !PART || row <= ny + 1;
+        const bool rowin = !PART || row <= ny;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int col = xl + c;
+            const long long q = (long long)row * ld + col;
+            const bool ok = rowok && (!PART || col <= nx + 1);
+            const bool in = rowin && (!PART || col <= nx);
+            v[r][c] = ok ? ld_s<S, T>(uin + q) : (T)0;
+            const T fv = in ? __ldg(f + q) : (T)0;
+            if constexpr (SIG) {
+                dv[r][c] = in ? __ldg(dinv + q) : (T)0;
+                g[r][c] = fv;
+            } else if constexpr (EXACT) {
+                g[r][c] = fv;
+            } else {
+                g[r][c] = fv * kc.invd;
+            }
+        }
+        const int hcol = (lane == 0) ? x0 - 1 : x0 + TX;
+        const bool hok = (lane == 0 || lane == 31) && rowok && (!PART || hcol <= nx + 1);
+        hx[r] = hok ? ld_s<S, T>(uin + (long long)row * ld + hcol) : (T)0;
+    }
+    {
+        const int rt = yb - 1, rb = yb + R;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int col = xl + c;
+            const bool okc = !PART || col <= nx + 1;
+            top[c] = (okc && (!PART || rt <= ny + 1)) ? ld_s<S, T>(uin + (long long)rt * ld + col) : (T)0;
+            bot[c] = (okc && (!PART || rb <= ny + 1)) ? ld_s<S, T>(uin + (long long)rb * ld + col) : (T)0;
+        }
+    }
+
+    typedef typename std::conditional<EXACT, double, T>::type Acc;
+    Acc acc = 0;
+
+    // ---- k subiterations on registers ----
+    auto sweep = [&](auto first_tag) {
+        constexpr bool FIRST = decltype(first_tag)::value;
+        T prev[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) prev[c] = top[c];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            T cur[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) cur[c] = v[r][c];
+            T left = __shfl_up_sync(FULL, cur[C - 1], 1);
+            T right = __shfl_down_sync(FULL, cur[0], 1);
+            if (lane == 0) left = hx[r];
+            if (lane == 31) right = hx[r];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const T W = (c == 0) ? left : cur[c > 0 ? c - 1 : 0];
+                const T E = (c == C - 1) ? right : cur[c < C - 1 ? c + 1 : 0];
+                const T Sv = prev[c];
+                const T Nv = (r == R - 1) ? bot[c] : v[r < R - 1 ? r + 1 : 0][c];
+                T res = 0;
+                T nv = point_update<T, EXACT, SIG, true, FIRST && RES>(
+                    kc, g[r][c], SIG ? dv[SIG ? r : 0][SIG ? c : 0] : (T)0, W, E, Sv, Nv, cur[c], res);
+                if constexpr (PART) {
+                    const bool act = (yb + r <= ny) && (xl + c <= nx);
+                    nv = act ? nv : cur[c];
+                    if (!act) res = 0;
+                }
+                if constexpr (FIRST && RES) acc += (Acc)res * (Acc)res;
+                v[r][c] = nv;
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) prev[c] = cur[c];
+        }
+    };
+
+    int par = 0;
+    auto exchange = [&]() {
+        if constexpr (NW > 1) {
+            T *buf = xbuf + par * (NW * 2 * TX);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                buf[(w * 2 + 0) * TX + lane * C + c] = v[0][c];
+                buf[(w * 2 + 1) * TX + lane * C + c] = v[R - 1][c];
+            }
+            __syncthreads();
+            if (w > 0) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) top[c] = buf[((w - 1) * 2 + 1) * TX + lane * C + c];
+            }
+            if (w < NW - 1) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) bot[c] = buf[((w + 1) * 2 + 0) * TX + lane * C + c];
+            }
+            par ^= 1;
+        }
+    };
+
+    sweep(std::integral_constant<bool, true>());
+    for (int s = 1; s < a.k; ++s) {
+        exchange();
+        sweep(std::integral_constant<bool, false>());
+    }
+
+    // ---- write the tile interior into u_{c+1} ----
+    S *__restrict__ uout = (S *)a.uout;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int row = yb + r;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int col = xl + c;
+            if (!PART || (row <= ny && col <= nx)) st_s<S, T>(uout + (long long)row * ld + col, v[r][c]);
+        }
+    }
+    return acc;
+}
+
+template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG, bool RES>
+__global__ void __launch_bounds__(32 * NW) hier2d_kernel(const CycArgs a) {
+    if constexpr (RES) {
+        if (*(volatile int *)&a.red.ctl->done >= 0) return;
+    }
+    constexpr int TX = 32 * C, TY = R * NW;
+    constexpr int XB = NW > 1 ? 2 * NW * 2 * TX : 1;
+    __shared__ T xbuf[XB];
+    const int x0 = 1 + blockIdx.x * TX, y0 = 1 + blockIdx.y * TY;
+    const bool full = (x0 + TX - 1 <= a.nx) && (y0 + TY - 1 <= a.ny);
+    typename std::conditional<EXACT, double, T>::type acc;
+    if (full) acc = tile2d<S, T, C, R, NW, EXACT, SIG, RES, false>(a, x0, y0, xbuf);
+    else acc = tile2d<S, T, C, R, NW, EXACT, SIG, RES, true>(a, x0, y0, xbuf);
+    if constexpr (RES) reduce_grid_acc(a.red, acc);
+}
+
+// ---------------------------------------------------------------------------
+// 1D tile: one warp per tile of 32*C points, WPB tiles per CTA, one row per
+// blockIdx.y (the independent copies of Section 3.5).
+// ---------------------------------------------------------------------------
+template <typename S, typename T, int C, bool EXACT, bool SIG, bool RES, bool PART>
+__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type tile1d(const CycArgs &a, const int x0, const int row) {
+    constexpr int TX = 32 * C;
+    const int lane = threadIdx.x & 31;
+    const int xl = x0 + lane * C;
+    const long long ld = a.ld;
+    const int nx = a.nx;
+    const long long rb = (long long)row * ld;
+    const S *__restrict__ uin = (const S *)a.uin;
+    const T *__restrict__ f = (const T *)a.f;
+    const T *__restrict__ dinv = (const T *)a.dinv;
+    const Coef<T> kc = make_coef<T>(a);
+    T v[C], g[C], dv[SIG ? C : 1];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int col = xl + c;
+        const bool ok = !PART || col <= nx + 1;
+        const bool in = !PART || col <= nx;
+        v[c] = ok ? ld_s<S, T>(uin + rb + col) : (T)0;
+        const T fv = in ? __ldg(f + rb + col) : (T)0;
+        if constexpr (SIG) {
+            dv[c] = in ? __ldg(dinv + rb + col) : (T)0;
+            g[c] = fv;
+        } else if constexpr (EXACT) {
+            g[c] = fv;
+        } else {
+            g[c] = fv * kc.invd;
+        }
+    }
+    const int hcol = (lane == 0) ? x0 - 1 : x0 + TX;
+    const bool hok = (lane == 0 || lane == 31) && (!PART || hcol <= nx + 1);
+    const T hx = hok ? ld_s<S, T>(uin + rb + hcol) : (T)0;
+
+    typedef typename std::conditional<EXACT, double, T>::type Acc;
+    Acc acc = 0;
+    auto sweep = [&](auto first_tag) {
+        constexpr bool FIRST = decltype(first_tag)::value;
+        T cur[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) cur[c] = v[c];
+        T left = __shfl_up_sync(FULL, cur[C - 1], 1);
+        T right = __shfl_down_sync(FULL, cur[0], 1);
+        if (lane == 0) left = hx;
+        if (lane == 31) right = hx;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const T W = (c == 0) ? left : cur[c > 0 ? c - 1 : 0];
+            const T E = (c == C - 1) ? right : cur[c < C - 1 ? c + 1 : 0];
+            T res = 0;
+            T nv = point_update<T, EXACT, SIG, false, FIRST && RES>(kc, g[c], SIG ? dv[SIG ? c : 0] : (T)0,
+                                                                    W, E, (T)0, (T)0, cur[c], res);
+            if constexpr (PART) {
+                const bool act = xl + c <= nx;
+                nv = act ? nv : cur[c];
+                if (!act) res = 0;
+            }
+            if constexpr (FIRST && RES) acc += (Acc)res * (Acc)res;
+            v[c] = nv;
+        }
+    };
+    sweep(std::integral_constant<bool, true>());
+    for (int s = 1; s < a.k; ++s) sweep(std::integral_constant<bool, false>());
+
+    S *__restrict__ uout = (S *)a.uout;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int col = xl + c;
+        if (!PART || col <= nx) st_s<S, T>(uout + rb + col, v[c]);
+    }
+    return acc;
+}
+
+template <typename S, typename T, int C, int WPB, bool EXACT, bool SIG, bool RES>
+__global__ void __launch_bounds__(32 * WPB) hier1d_kernel(const CycArgs a) {
+    if constexpr (RES) {
+        if (*(volatile int *)&a.red.ctl->done >= 0) return;
+    }
+    constexpr int TX = 32 * C;
+    const int w = threadIdx.x >> 5;
+    const int x0 = 1 + (blockIdx.x * WPB + w) * TX;
+    const int row = blockIdx.y;
+    typename std::conditional<EXACT, double, T>::type acc = 0;
+    if (x0 <= a.nx) {
+        if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, EXACT, SIG, RES, false>(a, x0, row);
+        else acc = tile1d<S, T, C, EXACT, SIG, RES, true>(a, x0, row);
+    }
+    if constexpr (RES) reduce_grid_acc(a.red, acc);
+}
+
+// ---------------------------------------------------------------------------
+// Classic global-memory Jacobi (Section 3.2): one sweep per launch, one thread
+// per point, every point reads u_c only and writes u_{c+1}.  Same update
+// arithmetic and fused residual as the cycle kernels.
+// ---------------------------------------------------------------------------
+template <typename S, typename T, bool EXACT, bool SIG, bool RES>
+__global__ void __launch_bounds__(256) classic2d_kernel(const CycArgs a) {
+    if constexpr (RES) {
+        if (*(volatile int *)&a.red.ctl->done >= 0) return;
+    }
+    const int i = 1 + blockIdx.x * 32 + threadIdx.x;
+    const int j = 1 + blockIdx.y * 8 + threadIdx.y;
+    const long long ld = a.ld;
+    typedef typename std::conditional<EXACT, double, T>::type Acc;
+    Acc acc = 0;
+    if (i <= a.nx && j <= a.ny) {
+        const S *__restrict__ uin = (const S *)a.uin;
+        const long long q = (long long)j * ld + i;
+        const Coef<T> kc = make_coef<T>(a);
+        const T old = ld_s<S, T>(uin + q);
+        const T W = ld_s<S, T>(uin + q - 1), E = ld_s<S, T>(uin + q + 1);
+        const T Sv = ld_s<S, T>(uin + q - ld), Nv = ld_s<S, T>(uin + q + ld);
+        const T fv = __ldg((const T *)a.f + q);
+        const T iv = SIG ? __ldg((const T *)a.dinv + q) : (T)0;
+        const T g = (EXACT || SIG) ? fv : fv * kc.invd;
+        T res = 0;
+        const T nv = point_update<T, EXACT, SIG, true, RES>(kc, g, iv, W, E, Sv, Nv, old, res);
+        st_s<S, T>((S *)a.uout + q, nv);
+        acc = (Acc)res * (Acc)res;
+    }
+    if constexpr (RES) reduce_grid_acc(a.red, acc);
+}
+
+template <typename S, typename T, bool EXACT, bool SIG, bool RES>
+__global__ void __launch_bounds__(256) classic1d_kernel(const CycArgs a) {
+    if constexpr (RES) {
+        if (*(volatile int *)&a.red.ctl->done >= 0) return;
+    }
+    const int i = 1 + blockIdx.x * 256 + threadIdx.x;
+    const int row = blockIdx.y;
+    typedef typename std::conditional<EXACT, double, T>::type Acc;
+    Acc acc = 0;
+    if (i <= a.nx) {
+        const S *__restrict__ uin = (const S *)a.uin;
+        const long long q = (long long)row * a.ld + i;
+        const Coef<T> kc = make_coef<T>(a);
+        const T old = ld_s<S, T>(uin + q);
+        const T W = ld_s<S, T>(uin + q - 1), E = ld_s<S, T>(uin + q + 1);
+        const T fv = __ldg((const T *)a.f + q);
+        const T iv = SIG ? __ldg((const T *)a.dinv + q) : (T)0;
+        const T g = (EXACT || SIG) ? fv : fv * kc.invd;
+        T res = 0;
+        const T nv = point_update<T, EXACT, SIG, false, RES>(kc, g, iv, W, E, (T)0, (T)0, old, res);
+        st_s<S, T>((S *)a.uout + q, nv);
+        acc = (Acc)res * (Acc)res;
+    }
+    if constexpr (RES) reduce_grid_acc(a.red, acc);
+}
+
+}  // namespace hj
+
+// Registry entry helpers ------------------------------------------------------
+#define HJ_K2D(S, T, C, R, NW, EX)                                                                   \
+    {2, 32 * (C), (R) * (NW), 32 * (NW), 1,                                                          \
+     {{hj::hier2d_kernel<S, T, C, R, NW, EX, false, false>, hj::hier2d_kernel<S, T, C, R, NW, EX, false, true>}, \
+      {hj::hier2d_kernel<S, T, C, R, NW, EX, true, false>, hj::hier2d_kernel<S, T, C, R, NW, EX, true, true>}}}
+#define HJ_K1D(S, T, C, WPB, EX)                                                                     \
+    {1, 32 * (C), 1, 32 * (WPB), (WPB),                                                              \
+     {{hj::hier1d_kernel<S, T, C, WPB, EX, false, false>, hj::hier1d_kernel<S, T, C, WPB, EX, false, true>}, \
+      {hj::hier1d_kernel<S, T, C, WPB, EX, true, false>, hj::hier1d_kernel<S, T, C, WPB, EX, true, true>}}}
+#define HJ_KC2D(S, T, EX)                                                                             \
+    {2, 32, 8, 256, 1,                                                                               \
+     {{hj::classic2d_kernel<S, T, EX, false, false>, hj::classic2d_kernel<S, T, EX, false, true>},   \
+      {hj::classic2d_kernel<S, T, EX, true, false>, hj::classic2d_kernel<S, T, EX, true, true>}}}
+#define HJ_KC1D(S, T, EX)                                                                             \
+    {1, 256, 1, 256, 1,                                                                              \
+     {{hj::classic1d_kernel<S, T, EX, false, false>, hj::classic1d_kernel<S, T, EX, false, true>},   \
+      {hj::classic1d_kernel<S, T, EX, true, false>, hj::classic1d_kernel<S, T, EX, true, true>}}}

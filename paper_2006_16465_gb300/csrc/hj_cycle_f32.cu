@@ -1,0 +1,24 @@
+// Binary32 cycle kernels (fused multiply-add chains).
+#include "hj_cycle.cuh"
+
+namespace hj {
+
+static const TileKernelInfo k_tiles[] = {
+    HJ_K2D(float, float, 1, 32, 1, false),    // 32 x 32
+    HJ_K2D(float, float, 1, 16, 1, false),    // 32 x 16
+    HJ_K2D(float, float, 1, 8, 1, false),     // 32 x 8
+    HJ_K2D(float, float, 1, 32, 2, false),    // 32 x 64
+    HJ_K2D(float, float, 2, 16, 2, false),    // 64 x 32
+    HJ_K2D(float, float, 2, 16, 4, false),    // 64 x 64
+    HJ_K2D(float, float, 4, 8, 4, false),     // 128 x 32
+    HJ_K1D(float, float, 1, 4, false),        // 32
+    HJ_K1D(float, float, 2, 4, false),        // 64
+    HJ_K1D(float, float, 4, 4, false),        // 128
+    HJ_K1D(float, float, 8, 4, false),        // 256
+};
+static const TileKernelInfo k_classic[] = {HJ_KC2D(float, float, false), HJ_KC1D(float, float, false)};
+
+const TileKernelInfo *tile_kernels_f32(int *n) { *n = sizeof(k_tiles) / sizeof(k_tiles[0]); return k_tiles; }
+const TileKernelInfo *classic_kernels_f32(int *n) { *n = 2; return k_classic; }
+
+}  // namespace hj

@@ -1,0 +1,23 @@
+// Binary64 cycle kernels (exact evaluation order, no fused multiply-add).
+#include "hj_cycle.cuh"
+
+namespace hj {
+
+static const TileKernelInfo k_tiles[] = {
+    HJ_K2D(double, double, 1, 16, 2, true),   // 32 x 32
+    HJ_K2D(double, double, 1, 16, 1, true),   // 32 x 16
+    HJ_K2D(double, double, 1, 8, 1, true),    // 32 x 8
+    HJ_K2D(double, double, 1, 16, 4, true),   // 32 x 64
+    HJ_K2D(double, double, 2, 8, 4, true),    // 64 x 32
+    HJ_K2D(double, double, 2, 8, 8, true),    // 64 x 64
+    HJ_K1D(double, double, 1, 4, true),       // 32
+    HJ_K1D(double, double, 2, 4, true),       // 64
+    HJ_K1D(double, double, 4, 4, true),       // 128
+    HJ_K1D(double, double, 8, 4, true),       // 256
+};
+static const TileKernelInfo k_classic[] = {HJ_KC2D(double, double, true), HJ_KC1D(double, double, true)};
+
+const TileKernelInfo *tile_kernels_f64(int *n) { *n = sizeof(k_tiles) / sizeof(k_tiles[0]); return k_tiles; }
+const TileKernelInfo *classic_kernels_f64(int *n) { *n = 2; return k_classic; }
+
+}  // namespace hj

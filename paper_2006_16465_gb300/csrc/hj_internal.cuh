@@ -1,0 +1,246 @@
+// hj_internal.cuh -- shared device/host pieces of the GB300 hierarchical Jacobi
+// library: kernel argument blocks, the device-side convergence control block,
+// and the deterministic two-level residual reduction fused into every cycle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "../../include/hj.h"
+
+namespace hj {
+
+// ---------------------------------------------------------------------------
+// Device-side convergence control.  One per handle.  The last CTA to finish a
+// cycle folds the residual of the cycle's *input* iterate u_c into it, so the
+// host only reads it every check_every cycles, and launches queued after
+// convergence return at once (the graph may overshoot without touching u).
+// ---------------------------------------------------------------------------
+struct Ctl {
+    int done;            // -1 while iterating; else index c of the iterate to return
+    int status;          // HJ_OK, HJ_ERR_DIVERGED or HJ_ERR_NOT_CONVERGED
+    long long cycle;     // index of the iterate whose residual the next cycle computes
+    double res2_0;       // ||r_0||^2
+    double res2_last;    // ||r_c||^2 of the last reduced cycle
+};
+
+constexpr int kHistCap = 8192;     // device ring of per-cycle ||r_c||^2 (power of two)
+constexpr int kGroup = 256;        // CTAs per first-level reduction group
+
+enum RedMode { RED_CYCLE = 0, RED_STORE = 1 };
+
+struct RedArgs {
+    double *partials;    // one per CTA (NV per CTA)
+    double *gpart;       // one per group (NV per group)
+    unsigned *gcnt;      // arrival counters per group (zero between uses)
+    unsigned *fcnt;      // final arrival counter (zero between uses)
+    double *hist;        // RED_CYCLE: ring of ||r_c||^2, kHistCap entries
+    double *out;         // RED_STORE: NV results
+    Ctl *ctl;            // RED_CYCLE: control block
+    double tol;          // stop at ||r_c|| <= tol ||r_0||
+    double scale;        // RED_CYCLE: the reduced sum is multiplied by this (d^2 for the fast path)
+    long long max_cycles;
+    int mode;            // RedMode
+};
+
+// Arguments of one cycle (or one classic sweep).
+struct CycArgs {
+    const void *f;       // right-hand side, compute type (grid layout)
+    const void *uin;     // iterate u_c, storage type
+    void *uout;          // iterate u_{c+1}, storage type
+    const void *dinv;    // per-point 1/d_p in compute type (grid layout), or null
+    long long ld;        // row pitch (elements)
+    int nx, ny, k;       // interior size, subiterations
+    double cW, cE, cS, cN;   // stencil
+    double invd;         // 1/(cD + sigma_const) when dinv is null
+    double dconst;       // cD + sigma_const
+    // binary32 copies precomputed on the host (binary64 arithmetic is slow on
+    // this part, so no kernel derives its binary32 coefficients in double)
+    float fW, fE, fS, fN;        // stencil
+    float gW, gE, gS, gN;        // -c * (1/d)
+    float finvd, fdconst;
+    RedArgs red;
+    int *err;            // device error word (bounded waits), nullable
+};
+
+// ---------------------------------------------------------------------------
+// storage <-> compute conversions
+// ---------------------------------------------------------------------------
+template <typename S, typename T> __device__ __forceinline__ T ld_s(const S *p) { return (T)__ldg(p); }
+template <> __device__ __forceinline__ float ld_s<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+}
+template <typename S, typename T> __device__ __forceinline__ void st_s(S *p, T v) { *p = (S)v; }
+template <> __device__ __forceinline__ void st_s<__nv_bfloat16, float>(__nv_bfloat16 *p, float v) {
+    *p = __float2bfloat16_rn(v);
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions.  Within a warp: xor butterfly (every lane ends with
+// the same value, independent of which CTA performs it).  Across CTAs: the last
+// CTA of each group of kGroup CTAs sums the group's partials in a fixed order,
+// the last group sums the group results in a fixed order.  The order depends
+// only on the grid shape, so results are bitwise reproducible.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    return v;
+}
+
+// Fold ||r_c||^2 of the cycle into the control block (runs on one thread).
+__device__ __forceinline__ void finish_cycle(const RedArgs &r, double res2) {
+    volatile Ctl *ctl = r.ctl;   // written by earlier launches: bypass L1
+    const long long c = ctl->cycle;
+    r.hist[c & (kHistCap - 1)] = res2;
+    if (c == 0) ctl->res2_0 = res2;
+    const double r0 = sqrt(c == 0 ? res2 : ctl->res2_0);
+    const double rc = sqrt(res2);
+    ctl->res2_last = res2;
+    if (!isfinite(rc)) {
+        ctl->status = HJ_ERR_DIVERGED;
+        ctl->done = (int)c;
+    } else if (rc <= r.tol * r0) {
+        ctl->done = (int)c;
+    } else if (c + 1 >= r.max_cycles) {
+        ctl->status = HJ_ERR_NOT_CONVERGED;
+        ctl->done = (int)(c + 1);
+    }
+    ctl->cycle = c + 1;
+}
+
+// Block-level reduction of NV per-thread values followed by the grid-level
+// group/final steps.  Must be called by every thread of the CTA.  nwarps =
+// blockDim.x*blockDim.y/32 (<= 32).
+template <int NV>
+__device__ __forceinline__ void reduce_grid(const RedArgs &r, const double (&val)[NV]) {
+    __shared__ double s_w[32][NV];
+    __shared__ int s_flag;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+    double v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = warp_sum(val[i]);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) s_w[warp][i] = v[i];
+    }
+    __syncthreads();
+    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const unsigned g = blk / kGroup;
+    const unsigned gsize = min((unsigned)kGroup, nblk - g * kGroup);
+    const unsigned ngroups = (nblk + kGroup - 1) / kGroup;
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += s_w[w][i];
+            r.partials[(size_t)blk * NV + i] = s;
+        }
+        __threadfence();
+        const unsigned t = atomicAdd(&r.gcnt[g], 1u);
+        s_flag = (t == gsize - 1);
+    }
+    __syncthreads();
+    if (!s_flag || warp != 0) return;
+    // last CTA of group g: sum the group's partials in a fixed order
+    __threadfence();
+    double gs[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = 0.0;
+        for (unsigned b = lane; b < gsize; b += 32) s += __ldcg(&r.partials[(size_t)(g * kGroup + b) * NV + i]);
+        gs[i] = warp_sum(s);
+    }
+    int last = 0;
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) r.gpart[(size_t)g * NV + i] = gs[i];
+        r.gcnt[g] = 0u;
+        __threadfence();
+        const unsigned t2 = atomicAdd(r.fcnt, 1u);
+        last = (t2 == ngroups - 1);
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    double fs[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = 0.0;
+        for (unsigned b = lane; b < ngroups; b += 32) s += __ldcg(&r.gpart[(size_t)b * NV + i]);
+        fs[i] = warp_sum(s);
+    }
+    if (lane == 0) {
+        *r.fcnt = 0u;
+        if (r.mode == RED_CYCLE) {
+            finish_cycle(r, fs[0] * r.scale);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) r.out[i] = fs[i];
+        }
+        __threadfence();
+    }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    return v;
+}
+
+// Per-thread residual contribution -> grid reduction.  binary32 contributions
+// are summed within the warp in binary32 first (one conversion per warp).
+template <typename A>
+__device__ __forceinline__ void reduce_grid_acc(const RedArgs &r, A acc) {
+    double v;
+    if constexpr (std::is_same<A, float>::value) {
+        const float w = warp_sum_f(acc);
+        v = ((threadIdx.x + threadIdx.y * blockDim.x) & 31) == 0 ? (double)w : 0.0;
+    } else {
+        v = acc;
+    }
+    const double vals[1] = {v};
+    reduce_grid<1>(r, vals);
+}
+
+// Launch-side description of one compiled cycle kernel.
+typedef void (*CycKernel)(CycArgs);
+
+struct TileKernelInfo {
+    int dim;            // 1 or 2
+    int tx, ty;         // tile interior shape (1D: ty = 1)
+    int threads;        // threads per CTA
+    int tiles_per_cta;  // 1D packs several tiles per CTA
+    CycKernel fn[2][2]; // [sig][res]
+};
+
+// Kernel registries (one per storage/compute combination).
+enum KernelFamily { FAM_F64 = 0, FAM_F32 = 1, FAM_BF16 = 2 };
+const TileKernelInfo *tile_kernels_f64(int *n);
+const TileKernelInfo *tile_kernels_f32(int *n);
+const TileKernelInfo *tile_kernels_bf16(int *n);
+const TileKernelInfo *classic_kernels_f64(int *n);
+const TileKernelInfo *classic_kernels_f32(int *n);
+const TileKernelInfo *classic_kernels_bf16(int *n);
+
+// Grid-wide helper kernels (hj_aux.cu).
+cudaError_t launch_make_dinv_box(const double *sigma, double dconst, long long ld, int row0, int rows, int col0,
+                                 int cols, int family, void *dinv, cudaStream_t s);
+cudaError_t launch_residual_ex(int dim, int user_f64, const void *f, const void *u, const double *sigma,
+                               long long ld, int nx, int ny, double cW, double cE, double cS, double cN,
+                               double dconst, int with_fnorm, float *r32, RedArgs red, cudaStream_t s);
+cudaError_t launch_update_residual_ex(int dim, const double *f, const double *uin, const void *d, int d_bf16,
+                                      double *uout, const double *sigma, float *r32, long long ld, int nx, int ny,
+                                      double cW, double cE, double cS, double cN, double dconst, RedArgs red,
+                                      cudaStream_t s);
+cudaError_t launch_grad_sigma_ex(int dim, int user_f64, const void *lam, const void *u, double *dsig, long long ld,
+                                 int nx, int ny, cudaStream_t s);
+int aux_max_blocks(int dim, int nx, int ny);
+
+}  // namespace hj

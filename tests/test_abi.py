@@ -1,0 +1,87 @@
+"""The C-ABI library loads and exports every entry point include/hj.h
+declares; host-only entry points answer without a GPU."""
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def hj():
+    from paper_2006_16465_gb300 import _build
+    _build.build()
+    import paper_2006_16465_gb300 as hj
+    hj.lib()
+    return hj
+
+
+def declared_symbols():
+    text = (ROOT / "include" / "hj.h").read_text()
+    return sorted(set(re.findall(r"HJ_API[^;(]*?\b(hj_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ["hj_create", "hj_solve", "hj_residual", "hj_solve_adjoint", "hj_solve_batched", "hj_destroy",
+              "hj_error_string", "hj_last_error", "hj_default_params", "hj_tile_shapes"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(hj):
+    import ctypes
+    lib = ctypes.CDLL(str(hj.LIB_PATH))
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+
+
+def test_binding_has_same_names(hj):
+    for n in declared_symbols():
+        assert callable(getattr(hj, n)), n
+
+
+def test_default_params_and_strings(hj):
+    p = hj.hj_default_params()
+    assert (p.tile_x, p.tile_y, p.k, p.precision, p.check_every) == (32, 32, 16, hj.HJ_PREC_F64, 64)
+    assert p.tol == 1e-6 and p.max_outer == 60 and p.persistent == -1
+    for code in range(0, 9):
+        assert hj.hj_error_string(code) != "unknown status"
+    assert hj.hj_error_string(99) == "unknown status"
+
+
+def test_tile_shapes(hj):
+    s64 = hj.hj_tile_shapes(2, hj.HJ_PREC_F64)
+    s32 = hj.hj_tile_shapes(2, hj.HJ_PREC_F32)
+    assert (32, 32) in s64 and (32, 32) in s32 and (64, 64) in s32
+    assert (128, 1) in hj.hj_tile_shapes(1, hj.HJ_PREC_F64)
+    assert hj.hj_tile_shapes(2, hj.HJ_PREC_BF16CORR_IR) == s32
+
+
+def test_create_rejects_bad_descriptors_without_touching_the_gpu(hj):
+    # argument validation happens before any CUDA call
+    d = hj.make_desc(3, 10, 10, 32, -1, -1, -1, -1, 4)
+    with pytest.raises(hj.HJError) as e:
+        hj.hj_create(d, hj.make_params())
+    assert e.value.code == hj.HJ_ERR_INVALID_ARG
+    d = hj.make_desc(2, 10, 10, 11, -1, -1, -1, -1, 4)     # ld < nx + 2
+    with pytest.raises(hj.HJError) as e:
+        hj.hj_create(d, hj.make_params())
+    assert e.value.code == hj.HJ_ERR_INVALID_ARG
+    d = hj.make_desc(2, 10, 10, 32, -1, -1, -1, -1, 3.9)   # not diagonally dominant
+    with pytest.raises(hj.HJError) as e:
+        hj.hj_create(d, hj.make_params())
+    assert e.value.code == hj.HJ_ERR_NOT_DIAG_DOMINANT
+    d = hj.make_desc(2, 10, 10, 32, -1, -1, -1, -1, 4, dtype=hj.HJ_F32)   # f32 data with f64 precision
+    with pytest.raises(hj.HJError) as e:
+        hj.hj_create(d, hj.make_params())
+    assert e.value.code == hj.HJ_ERR_INVALID_ARG
+
+
+def test_no_cpu_fallback(tmp_path, monkeypatch, hj):
+    # with the library absent, the binding raises instead of computing anything
+    import importlib
+    monkeypatch.setattr(hj, "LIB_PATH", tmp_path / "missing.so")
+    monkeypatch.setattr(hj, "_lib", None)
+    with pytest.raises(RuntimeError):
+        hj.lib()

@@ -1,0 +1,333 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the CPU oracle
+on the same seeded inputs.
+
+Tolerances (written here, derived in the design doc):
+  * binary64 cycles use the oracle's evaluation order without fused
+    multiply-add: max |u_gpu - u_oracle| <= 1e-12 max |u_oracle| at equal cycle
+    counts (bitwise equality is expected and reported);
+  * binary32 cycles: relative residual within 1e-5 of the oracle's, and
+    u within 1e-5 (relative, max norm) of the binary64 oracle at equal cycles
+    on small grids;
+  * refinement: the returned u meets tol and matches the oracle's refinement
+    result within kappa * tol.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from helpers import gpu_solver, rel_max, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+F64_TILES_2D = [(32, 32), (32, 16), (32, 8), (32, 64), (64, 32), (64, 64)]
+F32_TILES_2D = [(32, 32), (32, 16), (32, 8), (32, 64), (64, 32), (64, 64), (128, 32)]
+TILES_1D = [32, 64, 128, 256]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+# ---------------------------------------------------------------------------
+# binary64 hierarchical cycles: equal cycle counts
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tile", F64_TILES_2D)
+@pytest.mark.parametrize("shape,sigma,asym", [((70, 45), "field", True), ((64, 64), "none", False),
+                                               ((97, 130), "const", False)])
+def test_f64_cycles_match_oracle_2d(tile, shape, sigma, asym):
+    torch = _torch()
+    nx, ny = shape
+    p = W.random_bc_problem(2, nx, ny, seed=nx + ny, sigma_kind=sigma, asym=asym)
+    for k, ncyc in [(1, 3), (5, 4), (16, 2)]:
+        s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=k, precision="f64", fixed_cycles=ncyc)
+        f = to_dev(p.f, 2, torch.float64)
+        u = to_dev(p.u0, 2, torch.float64)
+        s.solve(f, u)
+        got = to_host(u, nx)
+        ref = oracle.run_fixed(p.st, p.f, p.u0, ncyc, tile[0], tile[1], k)
+        assert rel_max(got, ref) <= 1e-12, (tile, k, ncyc)
+        assert np.array_equal(got, ref), f"not bitwise for tile {tile} k={k}"
+        s.close()
+
+
+@pytest.mark.parametrize("tile", TILES_1D)
+@pytest.mark.parametrize("n,copies,sigma,asym", [(512, 1, "none", False), (300, 5, "field", True),
+                                                   (1000, 3, "const", True)])
+def test_f64_cycles_match_oracle_1d(tile, n, copies, sigma, asym):
+    torch = _torch()
+    p = W.random_bc_problem(1, n, copies, seed=n, sigma_kind=sigma, asym=asym)
+    for k, ncyc in [(1, 3), (32, 3)]:
+        s = gpu_solver(p, tile_x=tile, k=k, precision="f64", fixed_cycles=ncyc)
+        f = to_dev(p.f, 1, torch.float64)
+        u = to_dev(p.u0, 1, torch.float64)
+        s.solve(f, u)
+        got = to_host(u, n)
+        ref = oracle.run_fixed(p.st, p.f, p.u0, ncyc, tile, 1, k)
+        assert np.array_equal(got, ref), (tile, k)
+        s.close()
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_f64_classic_sweeps_match_oracle(dim):
+    torch = _torch()
+    p = W.random_bc_problem(dim, 77, 41 if dim == 2 else 3, seed=5, sigma_kind="field", asym=True)
+    s = gpu_solver(p, method="classic", precision="f64", fixed_cycles=9)
+    f = to_dev(p.f, dim, torch.float64)
+    u = to_dev(p.u0, dim, torch.float64)
+    s.solve(f, u)
+    ref = oracle.run_fixed(p.st, p.f, p.u0, 9, classic=True)
+    assert np.array_equal(to_host(u, p.st.nx), ref)
+
+
+# ---------------------------------------------------------------------------
+# converging solves: same stopping cycle, same iterate, same residual history
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,shape,tile,k,method", [
+    (2, (96, 80), (32, 32), 8, "hier"),
+    (2, (70, 45), (32, 16), 4, "hier"),
+    (2, (48, 48), (32, 32), 1, "classic"),
+    (1, (512, 1), (128, 1), 32, "hier"),
+    (1, (700, 4), (64, 1), 16, "hier"),
+])
+def test_f64_convergence_matches_oracle(dim, shape, tile, k, method):
+    torch = _torch()
+    nx, ny = shape
+    if dim == 1 and ny == 1:
+        p = W.poisson1d_sine(nx, seed=0)
+    else:
+        p = W.random_bc_problem(dim, nx, ny, seed=7, sigma_kind="field")
+    tol = 1e-6
+    s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=k, precision="f64", tol=tol, check_every=16,
+                   method=method)
+    f = to_dev(p.f, dim, torch.float64)
+    u = to_dev(p.u0, dim, torch.float64)
+    out = s.solve(f, u, history=100000)
+    uo, c, status, hist = oracle.solve(p.st, p.f, p.u0, tol, 10 ** 7, tile[0], tile[1], k,
+                                       classic=(method == "classic"), hist_cap=100000)
+    assert status == 0 and out["status"] == 0
+    assert out["cycles"] == c
+    assert np.array_equal(to_host(u, nx), uo)
+    gh = np.array(out["history"])
+    assert len(gh) == c + 1
+    np.testing.assert_allclose(gh, hist[:c + 1], rtol=1e-9, atol=1e-12 * hist[0])
+    assert out["res_final"] == pytest.approx(hist[c], rel=1e-9)
+    s.close()
+
+
+def test_residual_api_matches_oracle():
+    torch = _torch()
+    for dim, nx, ny in [(2, 90, 70), (1, 333, 3)]:
+        p = W.random_bc_problem(dim, nx, ny, seed=4, sigma_kind="field", asym=True)
+        s = gpu_solver(p, precision="f64")
+        f = to_dev(p.f, dim, torch.float64)
+        u = to_dev(p.u0, dim, torch.float64)
+        a, r = s.residual(f, u)
+        ro = oracle.residual(p.st, p.f, p.u0)
+        assert a == pytest.approx(ro, rel=1e-12)
+        assert r == pytest.approx(ro / np.linalg.norm(W.interior(p.f, dim)), rel=1e-12)
+        s.close()
+
+
+# ---------------------------------------------------------------------------
+# binary32 cycles
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tile", F32_TILES_2D)
+def test_f32_cycles_close_to_oracle(tile):
+    torch = _torch()
+    nx, ny = 150, 100
+    p = W.random_bc_problem(2, nx, ny, seed=9, sigma_kind="none")
+    ncyc, k = 20, 8
+    s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=k, precision="f32", fixed_cycles=ncyc)
+    f = to_dev(p.f, 2, torch.float32)
+    u = to_dev(p.u0, 2, torch.float32)
+    s.solve(f, u)
+    got = to_host(u, nx)
+    ref = oracle.run_fixed(p.st, p.f, p.u0, ncyc, tile[0], tile[1], k)
+    assert rel_max(got, ref) <= 1e-5
+    r0 = oracle.residual(p.st, p.f, p.u0)
+    assert abs(oracle.residual(p.st, p.f, got) - oracle.residual(p.st, p.f, ref)) / r0 <= 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("sigma", ["field", "const"])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_f32_screened_and_1d_close_to_oracle(dim, sigma):
+    torch = _torch()
+    p = W.random_bc_problem(dim, 200, 60 if dim == 2 else 4, seed=12, sigma_kind=sigma, asym=True)
+    s = gpu_solver(p, tile_x=32 if dim == 2 else 128, tile_y=32, k=6, precision="f32", fixed_cycles=15)
+    f = to_dev(p.f, dim, torch.float32)
+    u = to_dev(p.u0, dim, torch.float32)
+    s.solve(f, u)
+    ref = oracle.run_fixed(p.st, p.f, p.u0, 15, 32 if dim == 2 else 128, 32, 6)
+    assert rel_max(to_host(u, 200), ref) <= 1e-5
+    s.close()
+
+
+def test_f32_solve_reaches_tolerance_and_oracle_agrees():
+    torch = _torch()
+    p = W.poisson2d_uniform(128, 128, seed=1)
+    s = gpu_solver(p, tile_x=32, tile_y=32, k=16, precision="f32", tol=1e-5, check_every=32)
+    f = to_dev(p.f, 2, torch.float32)
+    u = to_dev(p.u0, 2, torch.float32)
+    out = s.solve(f, u, history=100000)
+    assert out["status"] == 0
+    uo, c, status, _ = oracle.solve(p.st, p.f, p.u0, 1e-5, 10 ** 6, 32, 32, 16)
+    rel_gpu = oracle.residual(p.st, p.f, to_host(u, 128)) / oracle.residual(p.st, p.f, p.u0)
+    rel_orc = oracle.residual(p.st, p.f, uo) / oracle.residual(p.st, p.f, p.u0)
+    assert abs(rel_gpu - rel_orc) <= 1e-5
+    assert abs(out["cycles"] - c) <= max(2, 0.02 * c)
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# mixed-precision iterative refinement
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["f32_ir", "bf16corr_ir"])
+def test_refinement_reaches_tolerance_and_matches_oracle(prec):
+    torch = _torch()
+    n = 96
+    p = W.poisson2d_sin_noise(n, seed=2)
+    tol = 1e-10
+    inner_tol = 1e-4 if prec == "f32_ir" else 1e-2
+    s = gpu_solver(p, tile_x=32, tile_y=32, k=16, precision=prec, tol=tol, inner_tol=inner_tol,
+                   check_every=16, max_outer=60)
+    f = to_dev(p.f, 2, torch.float64)
+    u = to_dev(p.u0, 2, torch.float64)
+    out = s.solve(f, u, history=64)
+    assert out["status"] == 0
+    r0 = oracle.residual(p.st, p.f, p.u0)
+    ug = to_host(u, n)
+    assert oracle.residual(p.st, p.f, ug) <= tol * r0 * 1.0001
+    uo, outer, inner, status, hist = oracle.ir_solve(p.st, p.f, p.u0, tol, 32, 32, 16, inner_tol=inner_tol,
+                                                     bf16=(prec == "bf16corr_ir"))
+    assert status == 0
+    h = 1 / (n + 1)
+    kappa = (8 / h ** 2) / (2 * np.pi ** 2)
+    assert np.abs(ug - uo).max() <= kappa * tol * np.abs(uo).max()
+    assert out["outer_steps"] >= 2
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# adjoint
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32_ir", 1e-10)])
+def test_adjoint_matches_oracle(prec, tol):
+    torch = _torch()
+    p = W.random_bc_problem(2, 80, 64, seed=21, sigma_kind="field", asym=True)
+    st = p.st
+    u_star, _, _, _ = oracle.solve(st, p.f, p.u0, 1e-13, 10 ** 7, 32, 32, 16)
+    g = W.zeros_grid(st)
+    g[1:-1, 1:-1] = W.uniform(5, 80 * 64, -1, 1).reshape(64, 80)
+    s = gpu_solver(p, tile_x=32, tile_y=32, k=16, precision=prec, tol=tol, check_every=32)
+    gd = to_dev(g, 2, torch.float64)
+    ud = to_dev(u_star, 2, torch.float64)
+    lam = to_dev(W.zeros_grid(st), 2, torch.float64)
+    dsig = to_dev(W.zeros_grid(st), 2, torch.float64)
+    out = s.adjoint(gd, ud, lam, dsig)
+    assert out["status"] == 0
+    lam_o, dsig_o, status = oracle.adjoint(st, g, u_star, tol=1e-13)
+    assert status == 0
+    L = to_host(lam, 80)
+    assert rel_max(L, lam_o) <= 1e-6
+    assert rel_max(to_host(dsig, 80), dsig_o) <= 1e-6
+    assert np.all(L[0] == 0) and np.all(L[-1] == 0) and np.all(L[:, 0] == 0) and np.all(L[:, 81] == 0)
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# interfaces and edge cases
+# ---------------------------------------------------------------------------
+
+def test_host_pointer_solve_equals_device_solve():
+    torch = _torch()
+    import paper_2006_16465_gb300 as hj
+    p = W.random_bc_problem(2, 64, 40, seed=2)
+    s = gpu_solver(p, tile_x=32, tile_y=32, k=4, precision="f64", fixed_cycles=6)
+    f = to_dev(p.f, 2, torch.float64)
+    u = to_dev(p.u0, 2, torch.float64)
+    s.solve(f, u)
+    fh = f.cpu().pin_memory()
+    uh = to_dev(p.u0, 2, torch.float64).cpu()          # pageable host memory
+    code = hj.hj_solve(s.h, fh.data_ptr(), uh.data_ptr(), 0, None)
+    assert code == 0
+    assert torch.equal(uh, u.cpu())
+    s.close()
+
+
+def test_zero_rhs_and_exact_guess_converge_at_cycle_zero():
+    torch = _torch()
+    p = W.poisson2d_uniform(40, 40, seed=3)
+    f = to_dev(W.zeros_grid(p.st), 2, torch.float64)
+    u = to_dev(W.zeros_grid(p.st), 2, torch.float64)
+    s = gpu_solver(p, precision="f64", tol=1e-8)
+    out = s.solve(f, u)
+    assert out["status"] == 0 and out["cycles"] == 0 and out["res_final"] == 0.0
+    s.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (33, 1), (31, 33)])
+def test_tiny_and_degenerate_grids(shape):
+    torch = _torch()
+    nx, ny = shape
+    p = W.random_bc_problem(2, nx, ny, seed=nx * 10 + ny, sigma_kind="field")
+    s = gpu_solver(p, tile_x=32, tile_y=32, k=3, precision="f64", fixed_cycles=5)
+    f = to_dev(p.f, 2, torch.float64)
+    u = to_dev(p.u0, 2, torch.float64)
+    s.solve(f, u)
+    assert np.array_equal(to_host(u, nx), oracle.run_fixed(p.st, p.f, p.u0, 5, 32, 32, 3))
+    s.close()
+
+
+def test_not_converged_returns_last_iterate():
+    torch = _torch()
+    import paper_2006_16465_gb300 as hj
+    p = W.poisson2d_uniform(64, 64, seed=8)
+    s = gpu_solver(p, precision="f64", tol=1e-12, max_cycles=13, check_every=4, k=2)
+    f = to_dev(p.f, 2, torch.float64)
+    u = to_dev(p.u0, 2, torch.float64)
+    out = s.solve(f, u, check=False)
+    assert out["status"] == hj.HJ_ERR_NOT_CONVERGED and out["cycles"] == 13
+    ref = oracle.run_fixed(p.st, p.f, p.u0, 13, 32, 32, 2)
+    assert np.array_equal(to_host(u, 64), ref)
+    assert out["res_final"] == pytest.approx(oracle.residual(p.st, p.f, ref), rel=1e-12)
+    s.close()
+
+
+def test_nonfinite_rhs_reports_divergence():
+    torch = _torch()
+    import paper_2006_16465_gb300 as hj
+    p = W.poisson2d_uniform(64, 64, seed=8)
+    fh = p.f.copy()
+    fh[10, 10] = np.nan
+    s = gpu_solver(p, precision="f64", tol=1e-8)
+    out = s.solve(to_dev(fh, 2, torch.float64), to_dev(p.u0, 2, torch.float64), check=False)
+    assert out["status"] == hj.HJ_ERR_DIVERGED
+    s.close()
+
+
+def test_solver_reuse_and_graph_cache():
+    torch = _torch()
+    p = W.random_bc_problem(2, 100, 90, seed=31)
+    s = gpu_solver(p, tile_x=32, tile_y=32, k=4, precision="f64", tol=1e-7, check_every=8)
+    f = to_dev(p.f, 2, torch.float64)
+    outs = []
+    for _ in range(3):
+        u = to_dev(p.u0, 2, torch.float64)
+        outs.append((s.solve(f, u)["cycles"], to_host(u, 100)))
+    assert outs[0][0] == outs[1][0] == outs[2][0]
+    assert np.array_equal(outs[0][1], outs[2][1])
+    s.close()
