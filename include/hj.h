@@ -137,6 +137,13 @@ typedef struct {
                              0: one launch per cycle inside CUDA graphs;
                              -1: choose automatically                            */
     int autotune;         /* 1: pick tile shape and k by measurement on first use */
+    int pipeline;         /* 2D cycles: 1 = TMA-pipelined kernel (CTAs walk tile
+                             lists, next tile staged while the current one
+                             sweeps), 0 = one CTA per tile, -1 = automatic      */
+    int inner_stall;      /* refinement: an inner solve also stops when ||r|| has
+                             changed by <= 1e-3 (relative) over this many cycles,
+                             i.e. the correction has reached the fixed point its
+                             storage precision allows; 0 = off                 */
 } hj_params;
 
 typedef struct {
@@ -159,7 +166,7 @@ typedef struct {
 /* Fill p with defaults: hierarchical, 32 x 32 tiles, k = 16, HJ_PREC_F64,
  * check_every = 64, max_cycles = 10^7, tol = 1e-6, fixed_cycles = 0,
  * inner_tol = 1e-4, inner_max_cycles = 10^6, max_outer = 60, persistent = -1,
- * autotune = 0. */
+ * autotune = 0, pipeline = -1, inner_stall = 32. */
 HJ_API void hj_default_params(hj_params *p);
 
 /* Create a solver for one problem shape.  Validates the descriptor and

@@ -72,7 +72,7 @@ def lib():
         L.hjo_residual_sq_f32.argtypes = [P, _F, _F]
         L.hjo_residual_sq_f32.restype = C.c_double
         L.hjo_ir_solve.argtypes = [P, _D, _D, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
-                                   C.c_long, C.c_long, C.c_int, _D, C.c_long,
+                                   C.c_long, C.c_long, C.c_int, C.c_long, C.c_double, _D, C.c_long,
                                    C.POINTER(C.c_long), C.POINTER(C.c_int)]
         L.hjo_ir_solve.restype = C.c_long
         L.hjo_adjoint.argtypes = [P, _D, _D, _D, _D, C.c_int, C.c_int, C.c_int, C.c_double,
@@ -189,8 +189,9 @@ def residual_f32(st, rhs, d) -> float:
 
 
 def ir_solve(st, f, u0, tol, tx=32, ty=32, k=16, inner_tol=1e-4, inner_max=100000,
-             max_outer=50, bf16=False):
-    """Iterative refinement (binary64 residual/update, binary32 inner cycles).
+             max_outer=50, bf16=False, stall_window=32, stall_rtol=1e-3):
+    """Iterative refinement (binary64 residual/update, binary32 inner cycles,
+    inner stop on inner_tol, stagnation or inner_max).
     Returns (u, outer_steps, inner_cycles, status, hist)."""
     p = _prob(st)
     u = _grid(u0).copy()
@@ -198,7 +199,8 @@ def ir_solve(st, f, u0, tol, tx=32, ty=32, k=16, inner_tol=1e-4, inner_max=10000
     tot = C.c_long(0)
     status = C.c_int(0)
     o = lib().hjo_ir_solve(p.ref, _dp(_grid(f)), _dp(u), tx, ty, k, float(tol), float(inner_tol),
-                           int(inner_max), int(max_outer), int(bf16), _dp(hist), max_outer + 1,
+                           int(inner_max), int(max_outer), int(bf16), int(stall_window), float(stall_rtol),
+                           _dp(hist), max_outer + 1,
                            C.byref(tot), C.byref(status))
     return u, int(o), int(tot.value), int(status.value), hist[:o + 1]
 

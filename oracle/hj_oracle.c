@@ -383,14 +383,18 @@ double hjo_residual_sq_f32(const hjo_problem *p, const float *rhs, const float *
  *   outer step: r = f - A u (binary64); stop if ||r|| <= tol ||r_0||;
  *               rhs = (float) r; d = 0;
  *               inner: binary32 hierarchical cycles on A d = rhs until
- *                      ||rhs - A d|| <= inner_tol ||rhs|| or inner_max cycles;
+ *                      ||rhs - A d|| <= inner_tol ||rhs||, or (stall_window > 0)
+ *                      ||rhs - A d_c|| differs by at most stall_rtol (relative)
+ *                      from its value stall_window cycles earlier (checked at
+ *                      c = W, 2W, ...: the stored correction has reached its
+ *                      fixed point), or inner_max cycles;
  *               u = u + (double) d   (interior points).
  * Returns the number of outer steps taken (== max_outer if not converged,
  * *status = 1).  hist[o] = ||r_o||; *inner_total = total inner cycles. */
 long hjo_ir_solve(const hjo_problem *p, const double *f, double *u,
                   int tx, int ty, int k, double tol, double inner_tol, long inner_max,
-                  long max_outer, int bf16, double *hist, long hist_cap,
-                  long *inner_total, int *status)
+                  long max_outer, int bf16, long stall_window, double stall_rtol,
+                  double *hist, long hist_cap, long *inner_total, int *status)
 {
     const long W = width_of(p), R = rows_of(p);
     const size_t n = (size_t)(W * R);
@@ -421,9 +425,17 @@ long hjo_ir_solve(const hjo_problem *p, const double *f, double *u,
         memset(d1, 0, n * sizeof(float));
         float *cur = d0, *nxt = d1;
         const double ri0 = sqrt(hjo_residual_sq_f32(p, rhs, cur));
+        double mark = ri0;
+        long mark_c = 0;
         for (long c = 0; c < inner_max; ++c) {
             const double ri = (c == 0) ? ri0 : sqrt(hjo_residual_sq_f32(p, rhs, cur));
             if (ri <= inner_tol * ri0) break;
+            if (stall_window > 0 && c > 0 && c - mark_c >= stall_window) {
+                const int stop = fabs(ri - mark) <= stall_rtol * ri;
+                mark = ri;
+                mark_c = c;
+                if (stop) break;
+            }
             hjo_hier_cycle_f32(p, rhs, cur, nxt, tx, ty, k, bf16);
             float *t = cur; cur = nxt; nxt = t;
             ++total;

@@ -48,7 +48,7 @@ class hj_params(C.Structure):
                 ("precision", C.c_int), ("check_every", C.c_int), ("max_cycles", C.c_longlong),
                 ("tol", C.c_double), ("fixed_cycles", C.c_longlong), ("inner_tol", C.c_double),
                 ("inner_max_cycles", C.c_longlong), ("max_outer", C.c_int), ("persistent", C.c_int),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("pipeline", C.c_int), ("inner_stall", C.c_int)]
 
 
 class hj_stats(C.Structure):

@@ -15,11 +15,14 @@
 #include <cstring>
 #include <vector>
 
-#include "hj_internal.cuh"
+#include <cudaTypedefs.h>
+
+#include "hj_runtime.cuh"
+#include "hj_tma.cuh"
 
 using namespace hj;
 
-namespace {
+namespace hj {
 
 thread_local char g_err[512] = "";
 
@@ -31,27 +34,37 @@ int seterr(int code, const char *fmt, ...) {
     return code;
 }
 
-#define CKR(call)                                                                                       \
-    do {                                                                                                \
-        cudaError_t e_ = (call);                                                                        \
-        if (e_ != cudaSuccess)                                                                          \
-            return seterr(HJ_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
-                          __LINE__);                                                                    \
-    } while (0)
+const char *last_error_text() { return g_err; }
 
-#define CKS(expr)                  \
-    do {                           \
-        int st_ = (expr);          \
-        if (st_ != HJ_OK) return st_; \
-    } while (0)
+}  // namespace hj
 
-const TileKernelInfo *family_tiles(int fam, int *n) {
+namespace {
+
+}  // namespace
+
+const TileKernelInfo *hj::family_tiles(int fam, int *n) {
     switch (fam) {
     case FAM_F64: return tile_kernels_f64(n);
     case FAM_F32: return tile_kernels_f32(n);
     default: return tile_kernels_bf16(n);
     }
 }
+const PersistKernelInfo *hj::family_persist(int fam, int *n) {
+    switch (fam) {
+    case FAM_F64: return persist_kernels_f64(n);
+    case FAM_F32: return persist_kernels_f32(n);
+    default: return persist_kernels_bf16(n);
+    }
+}
+const PersistKernelInfo *hj::find_persist(int fam, int dim, int tx, int ty) {
+    int n = 0;
+    const PersistKernelInfo *k = family_persist(fam, &n);
+    for (int i = 0; i < n; ++i)
+        if (k[i].dim == dim && k[i].tx == tx && (dim == 1 || k[i].ty == ty)) return &k[i];
+    return nullptr;
+}
+
+namespace {
 const TileKernelInfo *family_classic(int fam, int dim) {
     int n = 0;
     const TileKernelInfo *k = fam == FAM_F64 ? classic_kernels_f64(&n)
@@ -61,6 +74,51 @@ const TileKernelInfo *family_classic(int fam, int dim) {
         if (k[i].dim == dim) return &k[i];
     return nullptr;
 }
+const PpcKernelInfo *family_ppc(int fam, int *n) {
+    switch (fam) {
+    case FAM_F64: return ppc_kernels_f64(n);
+    case FAM_F32: return ppc_kernels_f32(n);
+    default: return ppc_kernels_bf16(n);
+    }
+}
+const PpcKernelInfo *find_ppc(int fam, int tx, int ty) {
+    int n = 0;
+    const PpcKernelInfo *k = family_ppc(fam, &n);
+    for (int i = 0; i < n; ++i)
+        if (k[i].tx == tx && k[i].ty == ty) return &k[i];
+    return nullptr;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2D tiled map over a grid array: dims (cols, rows), row stride ld*esz bytes,
+// box (bw, bh); out-of-bounds elements read as zero.
+bool make_tmap(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int esz, long long ld, int cols, int rows,
+               int bw, int bh) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
+    cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    cuuint32_t estr[2] = {1, 1};
+    memset(m, 0, sizeof(*m));
+    return enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 const TileKernelInfo *find_tile(int fam, int dim, int tx, int ty) {
     int n = 0;
     const TileKernelInfo *k = family_tiles(fam, &n);
@@ -69,14 +127,7 @@ const TileKernelInfo *find_tile(int fam, int dim, int tx, int ty) {
     return nullptr;
 }
 
-struct GraphEntry {
-    CycKernel fn;
-    dim3 grid, block;
-    CycArgs a0, a1;
-    int M;
-    cudaGraphExec_t exec;
-    unsigned long long stamp;
-};
+
 
 double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -84,32 +135,7 @@ double now_ms() {
 
 }  // namespace
 
-struct hj_handle {
-    hj_desc d;
-    hj_params p;
-    int dev = 0, nsm = 0;
-    int rows = 0;
-    size_t esz = 0, grid_elems = 0, grid_bytes = 0;
-    int fam_outer = FAM_F64, fam_inner = FAM_F32;
-    bool ir = false;
-    const TileKernelInfo *k_outer = nullptr, *k_inner = nullptr, *k_classic = nullptr, *k_classic_inner = nullptr;
-    void *ubuf = nullptr;
-    void *dinv_outer = nullptr;   // per-point 1/d in the outer compute type (sigma given)
-    float *dinv32 = nullptr;      // per-point 1/d in binary32 (refinement, sigma given)
-    float *r32 = nullptr;         // refinement: binary32 residual (inner RHS)
-    void *dA = nullptr, *dB = nullptr;  // refinement: correction buffers
-    void *hf = nullptr, *hu = nullptr;  // staging for host-pointer solves
-    double *partials = nullptr, *gpart = nullptr, *hist = nullptr, *rstore = nullptr;
-    unsigned *gcnt = nullptr, *fcnt = nullptr;
-    Ctl *ctl = nullptr;
-    Ctl *h_ctl = nullptr, *h_ctl_init = nullptr;
-    double *h_hist = nullptr, *h_rstore = nullptr;
-    cudaStream_t cap = nullptr;
-    cudaEvent_t ev = nullptr;
-    std::vector<GraphEntry> graphs;
-    unsigned long long stamp = 0;
-    size_t max_blocks = 0, max_groups = 0;
-};
+
 
 namespace {
 
@@ -175,16 +201,15 @@ void geometry(const hj_handle *h, const TileKernelInfo *ki, bool classic, dim3 *
     *block = dim3(ki->threads);
 }
 
-int family_of(const hj_handle *h, const TileKernelInfo *ki) {
-    if (ki == h->k_inner) return h->fam_inner;
-    return h->fam_outer;
-}
-
-int get_graph(hj_handle *h, CycKernel fn, dim3 grid, dim3 block, const CycArgs &a0, const CycArgs &a1, int M,
-              cudaGraphExec_t *out) {
+template <typename Args>
+int get_graph(hj_handle *h, void (*fn)(Args), dim3 grid, dim3 block, int smem, const Args &a0, const Args &a1,
+              int M, cudaGraphExec_t *out) {
+    std::vector<unsigned char> key(2 * sizeof(Args));
+    memcpy(key.data(), &a0, sizeof(Args));
+    memcpy(key.data() + sizeof(Args), &a1, sizeof(Args));
     for (auto &g : h->graphs) {
-        if (g.fn == fn && g.M == M && g.grid.x == grid.x && g.grid.y == grid.y && g.block.x == block.x &&
-            g.block.y == block.y && !memcmp(&g.a0, &a0, sizeof(CycArgs)) && !memcmp(&g.a1, &a1, sizeof(CycArgs))) {
+        if (g.fn == (const void *)fn && g.M == M && g.smem == smem && g.grid.x == grid.x && g.grid.y == grid.y &&
+            g.block.x == block.x && g.block.y == block.y && g.key == key) {
             g.stamp = ++h->stamp;
             *out = g.exec;
             return HJ_OK;
@@ -198,7 +223,7 @@ int get_graph(hj_handle *h, CycKernel fn, dim3 grid, dim3 block, const CycArgs &
     }
     cudaGraph_t graph;
     CKR(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < M; ++i) fn<<<grid, block, 0, h->cap>>>((i & 1) ? a1 : a0);
+    for (int i = 0; i < M; ++i) fn<<<grid, block, smem, h->cap>>>((i & 1) ? a1 : a0);
     cudaError_t le = cudaGetLastError();
     cudaError_t ee = cudaStreamEndCapture(h->cap, &graph);
     if (le != cudaSuccess) return seterr(HJ_ERR_CUDA, "kernel launch during capture: %s", cudaGetErrorString(le));
@@ -208,17 +233,103 @@ int get_graph(hj_handle *h, CycKernel fn, dim3 grid, dim3 block, const CycArgs &
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) return seterr(HJ_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
     GraphEntry e;
-    e.fn = fn;
+    e.fn = (const void *)fn;
     e.grid = grid;
     e.block = block;
-    e.a0 = a0;
-    e.a1 = a1;
+    e.smem = smem;
+    e.key = std::move(key);
     e.M = M;
     e.exec = exec;
     e.stamp = ++h->stamp;
-    h->graphs.push_back(e);
+    h->graphs.push_back(std::move(e));
     *out = exec;
     return HJ_OK;
+}
+
+// Launch plan for one iteration kernel: either the one-CTA-per-tile kernel
+// (CycArgs) or the TMA-pipelined kernel (PpcArgs) with its two argument blocks.
+struct Plan {
+    bool ppc = false;
+    CycKernel fn = nullptr;
+    PpcKernel pfn = nullptr;
+    dim3 grid, block;
+    int smem = 0;
+    CycArgs a0, a1;
+    PpcArgs p0, p1;
+};
+
+CUtensorMapDataType tmap_type(int fam, bool storage) {
+    if (fam == FAM_F64) return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    if (fam == FAM_BF16 && storage) return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+}
+
+int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int fam, bool classic, bool sig,
+              bool res, const CycArgs &base, void *b0, void *b1, Plan *pl) {
+    pl->a0 = base;
+    pl->a1 = base;
+    pl->a0.uin = b0; pl->a0.uout = b1;
+    pl->a1.uin = b1; pl->a1.uout = b0;
+    const int nx = h->d.nx, ny = h->d.ny;
+    bool use_ppc = false;
+    if (!classic && pi && h->d.dim == 2) {
+        const long long ntiles = (long long)((nx + pi->tx - 1) / pi->tx) * ((ny + pi->ty - 1) / pi->ty);
+        if (h->p.pipeline == 1) use_ppc = true;
+        else if (h->p.pipeline == -1) use_ppc = ntiles >= 8LL * h->nsm;
+    }
+    if (!use_ppc) {
+        geometry(h, ki, classic, &pl->grid, &pl->block);
+        pl->fn = ki->fn[sig][res];
+        pl->ppc = false;
+        return HJ_OK;
+    }
+    PpcKernel fn = pi->fn[sig][res];
+    const int smem = pi->smem[sig];
+    static thread_local const void *configured[64];
+    static thread_local int nconf = 0;
+    bool done_attr = false;
+    for (int i = 0; i < nconf; ++i) done_attr |= configured[i] == (const void *)fn;
+    if (!done_attr) {
+        CKR(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        if (nconf < 64) configured[nconf++] = (const void *)fn;
+    }
+    int occ = 0;
+    CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, pi->threads, smem));
+    if (occ < 1) return seterr(HJ_ERR_UNSUPPORTED, "pipelined kernel does not fit on an SM");
+    const int tiles_x = (nx + pi->tx - 1) / pi->tx;
+    const int ntiles = tiles_x * ((ny + pi->ty - 1) / pi->ty);
+    const int ssz = fam == FAM_F64 ? 8 : fam == FAM_BF16 ? 2 : 4;
+    const int tsz = fam == FAM_F64 ? 8 : 4;
+    const long long ld = base.ld;
+    for (int which = 0; which < 2; ++which) {
+        PpcArgs &P = which ? pl->p1 : pl->p0;
+        memset(&P, 0, sizeof(P));
+        P.a = which ? pl->a1 : pl->a0;
+        P.tiles_x = tiles_x;
+        P.ntiles = ntiles;
+        P.spin_limit = 1LL << 26;
+        if (!make_tmap(&P.mu, P.a.uin, tmap_type(fam, true), ssz, ld, nx + 2, ny + 2, pi->bwu, pi->ty + 2) ||
+            !make_tmap(&P.mf, P.a.f, tmap_type(fam, false), tsz, ld, nx + 2, ny + 2, pi->bwf, pi->ty))
+            return seterr(HJ_ERR_CUDA, "cuTensorMapEncodeTiled failed (pointer alignment or pitch)");
+        if (sig && !make_tmap(&P.md, P.a.dinv, tmap_type(fam, false), tsz, ld, nx + 2, ny + 2, pi->bwf, pi->ty))
+            return seterr(HJ_ERR_CUDA, "cuTensorMapEncodeTiled failed for 1/d");
+    }
+    pl->ppc = true;
+    pl->pfn = fn;
+    pl->smem = smem;
+    pl->grid = dim3(std::min(ntiles, occ * h->nsm));
+    pl->block = dim3(pi->threads);
+    return HJ_OK;
+}
+
+int plan_graph(hj_handle *h, const Plan &pl, int M, cudaGraphExec_t *ex) {
+    if (pl.ppc) return get_graph<PpcArgs>(h, pl.pfn, pl.grid, pl.block, pl.smem, pl.p0, pl.p1, M, ex);
+    return get_graph<CycArgs>(h, pl.fn, pl.grid, pl.block, 0, pl.a0, pl.a1, M, ex);
+}
+
+void plan_launch(const Plan &pl, long long c, cudaStream_t s) {
+    if (pl.ppc) pl.pfn<<<pl.grid, pl.block, pl.smem, s>>>((c & 1) ? pl.p1 : pl.p0);
+    else pl.fn<<<pl.grid, pl.block, 0, s>>>((c & 1) ? pl.a1 : pl.a0);
 }
 
 struct RunOut {
@@ -229,42 +340,47 @@ struct RunOut {
     double res2_c;      // ||r_c||^2 of the returned iterate if known, else -1
 };
 
-// Iterate cycles (or classic sweeps) of kernel `fn` from b0 (holds u_0), b1
-// (the other buffer, same ghost ring).  fixed > 0: exactly `fixed` cycles, no
-// residual.  Otherwise until ||r_c|| <= tol ||r_0|| or max_cycles.
-int run_cycles(hj_handle *h, const TileKernelInfo *ki, bool classic, bool sig, const CycArgs &base, void *b0,
-               void *b1, double tol, long long max_cycles, long long fixed, cudaStream_t s, RunOut *ro,
-               double *hist_out, long long hist_cap, long long *hist_len) {
-    dim3 grid, block;
-    geometry(h, ki, classic, &grid, &block);
+// Iterate cycles (or classic sweeps) from b0 (holds u_0) and b1 (the other
+// buffer, same ghost ring).  fixed > 0: exactly `fixed` cycles, no residual.
+// Otherwise until ||r_c|| <= tol ||r_0|| or max_cycles.
+int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int fam, bool classic, bool sig,
+               const CycArgs &base_in, void *b0, void *b1, double tol, long long max_cycles, long long fixed,
+               cudaStream_t s, RunOut *ro, double *hist_out, long long hist_cap, long long *hist_len) {
     const int M = h->p.check_every;
-    CycArgs a0 = base, a1 = base;
-    a0.uin = b0; a0.uout = b1;
-    a1.uin = b1; a1.uout = b0;
     ro->res2_0 = -1.0;
     ro->res2_c = -1.0;
+    CycArgs base = base_in;
+    base.err = &h->ctl->err;
+    *h->h_ctl_init = Ctl{-1, HJ_OK, 0, 0.0, 0.0, 0, 0, 0.0, 0};
+    CKR(cudaMemcpyAsync(h->ctl, h->h_ctl_init, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     if (fixed > 0) {
-        CycKernel fn = ki->fn[sig][0];
+        Plan pl;
+        CKS(make_plan(h, ki, pi, fam, classic, sig, false, base, b0, b1, &pl));
         const long long reps = fixed / M;
         if (reps > 0) {
             cudaGraphExec_t ex;
-            CKS(get_graph(h, fn, grid, block, a0, a1, M, &ex));
+            CKS(plan_graph(h, pl, M, &ex));
             for (long long r = 0; r < reps; ++r) CKR(cudaGraphLaunch(ex, s));
         }
-        for (long long c = reps * M; c < fixed; ++c) fn<<<grid, block, 0, s>>>((c & 1) ? a1 : a0);
+        for (long long c = reps * M; c < fixed; ++c) plan_launch(pl, c, s);
         CKR(cudaGetLastError());
+        CKR(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CKR(cudaEventRecord(h->ev, s));
+        CKR(cudaEventSynchronize(h->ev));
+        if (h->h_ctl->err) return seterr(HJ_ERR_TIMEOUT, "a bounded device wait expired (tile pipeline)");
         ro->c = fixed;
         ro->status = HJ_OK;
         ro->launched = fixed;
         return HJ_OK;
     }
-    CycKernel fn = ki->fn[sig][1];
-    a0.red = red_args(h, RED_CYCLE, tol, max_cycles);
+    {
+        const long long sw = base.red.stall_window;
+        base.red = red_args(h, RED_CYCLE, tol, max_cycles);
+        base.red.stall_window = sw;
+        base.red.stall_rtol = 1e-3;
+    }
     // binary32 kernels with a constant diagonal accumulate (u' - u)^2; r = d (u' - u)
-    if (family_of(h, ki) != FAM_F64 && !sig) a0.red.scale = base.dconst * base.dconst;
-    a1.red = a0.red;
-    *h->h_ctl_init = Ctl{-1, HJ_OK, 0, 0.0, 0.0};
-    CKR(cudaMemcpyAsync(h->ctl, h->h_ctl_init, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    if (fam != FAM_F64 && !sig) base.red.scale = base.dconst * base.dconst;
     if (max_cycles <= 0) {
         // no cycle may run: the residual of u_0 is all there is
         ro->c = 0;
@@ -272,8 +388,10 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, bool classic, bool sig, c
         ro->launched = 0;
         return HJ_OK;
     }
+    Plan pl;
+    CKS(make_plan(h, ki, pi, fam, classic, sig, true, base, b0, b1, &pl));
     cudaGraphExec_t ex;
-    CKS(get_graph(h, fn, grid, block, a0, a1, M, &ex));
+    CKS(plan_graph(h, pl, M, &ex));
     long long launched = 0, copied = 0;
     const long long mask = kHistCap - 1;
     for (;;) {
@@ -289,6 +407,7 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, bool classic, bool sig, c
         CKR(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         CKR(cudaEventRecord(h->ev, s));
         CKR(cudaEventSynchronize(h->ev));
+        if (h->h_ctl->err) return seterr(HJ_ERR_TIMEOUT, "a bounded device wait expired (tile pipeline)");
         const long long ncomp = h->h_ctl->cycle;
         if (hist_out) {
             for (; copied < ncomp; ++copied)
@@ -307,11 +426,65 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, bool classic, bool sig, c
     return HJ_OK;
 }
 
+// Iterate with the persistent engine when every block of the grid can be
+// resident at once (or when forced), else with graph-captured launches.
+int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int fam, bool classic, bool sig,
+            const CycArgs &base, void *b0, void *b1, double tol, long long max_cycles, long long fixed, cudaStream_t s,
+            RunOut *ro, double *hist_out, long long hist_cap, long long *hist_len, int *used_persistent) {
+    const PersistKernelInfo *pk = classic ? nullptr : find_persist(fam, h->d.dim, ki->tx, ki->ty);
+    dim3 g, bb;
+    geometry(h, ki, classic, &g, &bb);
+    bool use = false;
+    if (pk && fixed <= 0 && max_cycles > 0 && h->p.persistent != 0) {
+        int cap = 0;
+        CKS(persist_capacity(h, pk, sig, &cap));
+        const long long blocks = (long long)g.x * g.y;
+        if (h->p.persistent == 1) {
+            if (blocks > 64LL * cap) return seterr(HJ_ERR_UNSUPPORTED, "grid too large for the persistent engine");
+            use = true;
+        } else {
+            use = blocks <= cap;
+        }
+    }
+    if (used_persistent) *used_persistent = use ? 1 : 0;
+    if (!use)
+        return run_cycles(h, ki, pi, fam, classic, sig, base, b0, b1, tol, max_cycles, fixed, s, ro, hist_out,
+                          hist_cap, hist_len);
+    std::vector<PersistProblem> v(1);
+    PersistProblem &q = v[0];
+    q.a = base;
+    q.a.uin = b0;
+    q.a.uout = b1;
+    q.a.red = red_args(h, RED_CYCLE, tol, max_cycles);
+    q.a.red.stall_window = base.red.stall_window;
+    q.a.red.stall_rtol = 1e-3;
+    if (fam != FAM_F64 && !sig) q.a.red.scale = base.dconst * base.dconst;
+    q.blocks_x = g.x;
+    q.blocks = g.x * g.y;
+    std::vector<ProbState> st;
+    CKS(run_persistent(h, pk, sig, v, s, &st));
+    ro->c = st[0].done;
+    ro->status = st[0].status;
+    ro->launched = st[0].cycle;
+    ro->res2_0 = st[0].res2_0;
+    ro->res2_c = (ro->status == HJ_OK || ro->status == HJ_ERR_DIVERGED) ? st[0].res2_last : -1.0;
+    if (hist_out) {
+        const long long ncomp = st[0].cycle;
+        const long long lo = std::max(0LL, ncomp - (long long)kHistCap);
+        const long long mask = kHistCap - 1;
+        CKR(cudaMemcpyAsync(h->h_hist, h->hist, kHistCap * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CKR(cudaStreamSynchronize(s));
+        for (long long c = lo; c < ncomp && c < hist_cap; ++c) hist_out[c] = sqrt(h->h_hist[c & mask]);
+        if (hist_len) *hist_len = std::min(ncomp, hist_cap);
+    }
+    return HJ_OK;
+}
+
 int residual_of(hj_handle *h, const void *f, const void *u, bool transpose, double *rr, double *ff, cudaStream_t s) {
     const CycArgs a = base_args(h, transpose);
     const RedArgs red = red_args(h, RED_STORE, 0.0, 0);
-    CKR(launch_residual_ex(h->d.dim, h->d.dtype == HJ_F64, f, u, h->d.sigma, h->d.ld, h->d.nx, h->d.ny, a.cW, a.cE,
-                           a.cS, a.cN, a.dconst, 1, nullptr, red, s));
+    CKR(launch_residual_ex(h->d.dim, h->d.dtype == HJ_F64, f, u, h->d.sigma, h->d.ld, h->d.ld, h->d.nx, h->d.ny,
+                           a.cW, a.cE, a.cS, a.cN, a.dconst, 1, nullptr, red, s));
     CKR(cudaMemcpyAsync(h->h_rstore, h->rstore, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CKR(cudaEventRecord(h->ev, s));
     CKR(cudaEventSynchronize(h->ev));
@@ -331,8 +504,10 @@ int solve_plain(hj_handle *h, const void *f, void *u, bool transpose, cudaStream
     CKR(cudaMemcpyAsync(h->ubuf, u, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
     RunOut ro;
     long long hl = 0;
-    CKS(run_cycles(h, ki, classic, sig, base, u, h->ubuf, h->p.tol, h->p.max_cycles, h->p.fixed_cycles, s, &ro,
-                   st ? st->history : nullptr, st ? st->history_cap : 0, &hl));
+    int persist = 0;
+    CKS(iterate(h, ki, classic ? nullptr : h->p_outer, h->fam_outer, classic, sig, base, u, h->ubuf, h->p.tol,
+                h->p.max_cycles, h->p.fixed_cycles, s, &ro, st ? st->history : nullptr, st ? st->history_cap : 0,
+                &hl, &persist));
     if (ro.c & 1) CKR(cudaMemcpyAsync(u, h->ubuf, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
     double res0 = -1.0, resc = -1.0;
     if (h->p.fixed_cycles <= 0) {
@@ -357,6 +532,7 @@ int solve_plain(hj_handle *h, const void *f, void *u, bool transpose, cudaStream
         st->res_final = resc;
         st->rel_final = res0 > 0 ? resc / res0 : 0.0;
         st->history_len = hl;
+        st->persistent = persist;
     }
     if (ro.status == HJ_ERR_DIVERGED) return seterr(HJ_ERR_DIVERGED, "residual became non-finite at cycle %lld", ro.c);
     if (ro.status == HJ_ERR_NOT_CONVERGED)
@@ -375,8 +551,8 @@ int solve_ir(hj_handle *h, const double *f, double *u, bool transpose, cudaStrea
     // outer residual of u_0 -> r32
     {
         const RedArgs red = red_args(h, RED_STORE, 0.0, 0);
-        CKR(launch_residual_ex(h->d.dim, 1, f, u, h->d.sigma, h->d.ld, h->d.nx, h->d.ny, geo.cW, geo.cE, geo.cS,
-                               geo.cN, geo.dconst, 0, h->r32, red, s));
+        CKR(launch_residual_ex(h->d.dim, 1, f, u, h->d.sigma, h->d.ld, h->ld_in, h->d.nx, h->d.ny, geo.cW, geo.cE,
+                               geo.cS, geo.cN, geo.dconst, 0, h->r32, red, s));
         CKR(cudaMemcpyAsync(h->h_rstore, h->rstore, sizeof(double), cudaMemcpyDeviceToHost, s));
         CKR(cudaEventRecord(h->ev, s));
         CKR(cudaEventSynchronize(h->ev));
@@ -384,26 +560,29 @@ int solve_ir(hj_handle *h, const double *f, double *u, bool transpose, cudaStrea
     double *cur = u, *other = (double *)h->ubuf;
     double r0 = sqrt(h->h_rstore[0]), rn = r0;
     long long inner_total = 0, inner_launched = 0;
-    int o = 0, status = HJ_OK;
+    int o = 0, status = HJ_OK, persist = 0;
     long long hl = 0;
     CycArgs base = geo;
+    base.ld = h->ld_in;
     base.f = h->r32;
     base.dinv = h->dinv32;
+    base.red.stall_window = h->p.inner_stall;
     for (;; ++o) {
         if (st && st->history && o < st->history_cap) { st->history[o] = rn; hl = o + 1; }
         if (!std::isfinite(rn)) { status = HJ_ERR_DIVERGED; break; }
         if (rn <= h->p.tol * r0) { status = HJ_OK; break; }
         if (o >= h->p.max_outer) { status = HJ_ERR_NOT_CONVERGED; break; }
-        CKR(cudaMemsetAsync(h->dA, 0, h->grid_elems * dsz, s));
+        CKR(cudaMemsetAsync(h->dA, 0, (size_t)h->rows * h->ld_in * dsz, s));
         RunOut ro;
-        CKS(run_cycles(h, h->k_inner, false, sig, base, h->dA, h->dB, h->p.inner_tol, h->p.inner_max_cycles, 0, s,
-                       &ro, nullptr, 0, nullptr));
+        CKS(iterate(h, h->k_inner, h->p_inner, h->fam_inner, false, sig, base, h->dA, h->dB, h->p.inner_tol,
+                    h->p.inner_max_cycles, 0, s, &ro, nullptr, 0, nullptr, &persist));
         inner_total += ro.c;
         inner_launched += ro.launched;
         const void *dsel = (ro.c & 1) ? h->dB : h->dA;
         const RedArgs red = red_args(h, RED_STORE, 0.0, 0);
         CKR(launch_update_residual_ex(h->d.dim, f, cur, dsel, bf16 ? 1 : 0, other, h->d.sigma, h->r32, h->d.ld,
-                                      h->d.nx, h->d.ny, geo.cW, geo.cE, geo.cS, geo.cN, geo.dconst, red, s));
+                                      h->ld_in, h->d.nx, h->d.ny, geo.cW, geo.cE, geo.cS, geo.cN, geo.dconst, red,
+                                      s));
         CKR(cudaMemcpyAsync(h->h_rstore, h->rstore, sizeof(double), cudaMemcpyDeviceToHost, s));
         CKR(cudaEventRecord(h->ev, s));
         CKR(cudaEventSynchronize(h->ev));
@@ -421,6 +600,7 @@ int solve_ir(hj_handle *h, const double *f, double *u, bool transpose, cudaStrea
         st->res_final = rn;
         st->rel_final = r0 > 0 ? rn / r0 : 0.0;
         st->history_len = hl;
+        st->persistent = persist;
     }
     if (status == HJ_ERR_DIVERGED) return seterr(HJ_ERR_DIVERGED, "refinement residual became non-finite");
     if (status == HJ_ERR_NOT_CONVERGED)
@@ -451,7 +631,6 @@ void fill_stats_config(const hj_handle *h, hj_stats *st, double t0) {
     st->tile_x = h->p.tile_x;
     st->tile_y = h->d.dim == 2 ? h->p.tile_y : 1;
     st->k = h->p.k;
-    st->persistent = 0;
 }
 
 }  // namespace
@@ -478,6 +657,8 @@ void hj_default_params(hj_params *p) {
     p->max_outer = 60;
     p->persistent = -1;
     p->autotune = 0;
+    p->pipeline = -1;
+    p->inner_stall = 32;
 }
 
 const char *hj_error_string(int s) {
@@ -516,10 +697,10 @@ void hj_destroy(hj_handle *h) {
     if (!h) return;
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     void *dev[] = {h->ubuf, h->dinv_outer, h->dinv32, h->r32, h->dA, h->dB, h->hf, h->hu, h->partials, h->gpart,
-                   h->hist, h->rstore, h->gcnt, h->fcnt, h->ctl};
+                   h->hist, h->rstore, h->gcnt, h->fcnt, h->ctl, h->pscratch, h->barena, h->rs};
     for (void *p : dev)
         if (p) cudaFree(p);
-    void *pin[] = {h->h_ctl, h->h_ctl_init, h->h_hist, h->h_rstore};
+    void *pin[] = {h->h_ctl, h->h_ctl_init, h->h_hist, h->h_rstore, h->h_pstage, h->h_rs};
     for (void *p : pin)
         if (p) cudaFreeHost(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -555,6 +736,7 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     if (p.max_cycles < 0) return seterr(HJ_ERR_INVALID_ARG, "max_cycles must be >= 0");
     if (ir && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)) return seterr(HJ_ERR_INVALID_ARG, "inner_tol must be in (0,1)");
     if (ir && p.inner_max_cycles < 1) return seterr(HJ_ERR_INVALID_ARG, "inner_max_cycles must be >= 1");
+    if (p.inner_stall < 0) return seterr(HJ_ERR_INVALID_ARG, "inner_stall must be >= 0");
     if (ir && p.method == HJ_METHOD_CLASSIC) return seterr(HJ_ERR_UNSUPPORTED, "refinement uses hierarchical cycles");
     if (p.check_every < 1) p.check_every = 1;
     if (p.check_every > kHistCap / 2) p.check_every = kHistCap / 2;
@@ -605,15 +787,20 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     if (cudaGetDevice(&h->dev) != cudaSuccess) HJ_FAIL(HJ_ERR_CUDA, "no CUDA device");
     cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
 
+    h->ld_in = ((long long)d.nx + 2 + 31) / 32 * 32;
     if (ir) {
         h->k_inner = find_tile(h->fam_inner, d.dim, p.tile_x, p.tile_y);
         if (!h->k_inner) HJ_FAIL(HJ_ERR_UNSUPPORTED, "tile %dx%d not built for this precision", p.tile_x, p.tile_y);
+        if (d.dim == 2) h->p_inner = find_ppc(h->fam_inner, p.tile_x, p.tile_y);
     } else if (p.method == HJ_METHOD_CLASSIC) {
         h->k_classic = family_classic(h->fam_outer, d.dim);
     } else {
         h->k_outer = find_tile(h->fam_outer, d.dim, p.tile_x, p.tile_y);
         if (!h->k_outer) HJ_FAIL(HJ_ERR_UNSUPPORTED, "tile %dx%d not built for this precision", p.tile_x, p.tile_y);
+        if (d.dim == 2) h->p_outer = find_ppc(h->fam_outer, p.tile_x, p.tile_y);
     }
+    if (p.pipeline == 1 && d.dim == 2 && p.method == HJ_METHOD_HIER && !(ir ? h->p_inner : h->p_outer))
+        HJ_FAIL(HJ_ERR_UNSUPPORTED, "no pipelined kernel for tile %dx%d", p.tile_x, p.tile_y);
     // reduction workspace sized for the largest grid any kernel of this handle launches
     size_t maxb = (size_t)aux_max_blocks(d.dim, d.nx, d.ny);
     for (int fam = 0; fam < 3; ++fam) {
@@ -652,24 +839,26 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     const int r0 = d.dim == 2 ? 1 : 0;
     if (ir) {
         const bool bf16 = h->fam_inner == FAM_BF16;
-        HJ_ALLOC(h->r32, h->grid_elems * sizeof(float));
-        HJ_ALLOC(h->dA, h->grid_elems * (bf16 ? 2 : 4));
-        HJ_ALLOC(h->dB, h->grid_elems * (bf16 ? 2 : 4));
-        if (cudaMemset(h->r32, 0, h->grid_elems * sizeof(float)) != cudaSuccess ||
-            cudaMemset(h->dA, 0, h->grid_elems * (bf16 ? 2 : 4)) != cudaSuccess ||
-            cudaMemset(h->dB, 0, h->grid_elems * (bf16 ? 2 : 4)) != cudaSuccess)
+        const size_t nin = (size_t)rows * h->ld_in;
+        HJ_ALLOC(h->r32, nin * sizeof(float));
+        HJ_ALLOC(h->dA, nin * (bf16 ? 2 : 4));
+        HJ_ALLOC(h->dB, nin * (bf16 ? 2 : 4));
+        if (cudaMemset(h->r32, 0, nin * sizeof(float)) != cudaSuccess ||
+            cudaMemset(h->dA, 0, nin * (bf16 ? 2 : 4)) != cudaSuccess ||
+            cudaMemset(h->dB, 0, nin * (bf16 ? 2 : 4)) != cudaSuccess)
             HJ_FAIL(HJ_ERR_CUDA, "cudaMemset failed");
         if (d.sigma) {
-            HJ_ALLOC(h->dinv32, h->grid_elems * sizeof(float));
-            cudaMemset(h->dinv32, 0, h->grid_elems * sizeof(float));
-            if (launch_make_dinv_box(d.sigma, dconst, d.ld, r0, d.ny, 1, d.nx, FAM_F32, h->dinv32, 0) != cudaSuccess)
+            HJ_ALLOC(h->dinv32, nin * sizeof(float));
+            cudaMemset(h->dinv32, 0, nin * sizeof(float));
+            if (launch_make_dinv_box(d.sigma, dconst, d.ld, h->ld_in, r0, d.ny, 1, d.nx, FAM_F32, h->dinv32, 0) !=
+                cudaSuccess)
                 HJ_FAIL(HJ_ERR_CUDA, "dinv kernel failed");
         }
     } else if (d.sigma) {
         const size_t tsz = h->fam_outer == FAM_F64 ? 8 : 4;
         HJ_ALLOC(h->dinv_outer, h->grid_elems * tsz);
         cudaMemset(h->dinv_outer, 0, h->grid_elems * tsz);
-        if (launch_make_dinv_box(d.sigma, dconst, d.ld, r0, d.ny, 1, d.nx, h->fam_outer, h->dinv_outer, 0) !=
+        if (launch_make_dinv_box(d.sigma, dconst, d.ld, d.ld, r0, d.ny, 1, d.nx, h->fam_outer, h->dinv_outer, 0) !=
             cudaSuccess)
             HJ_FAIL(HJ_ERR_CUDA, "dinv kernel failed");
     }
@@ -749,10 +938,6 @@ int hj_solve_adjoint(hj_handle *h, const void *g, const void *u, void *dl_df, vo
     return st;
 }
 
-int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, const void *const *f, void *const *u,
-                     hj_stream stream, hj_stats *stats, long long *cycles_out) {
-    (void)h; (void)nprob; (void)descs; (void)f; (void)u; (void)stream; (void)stats; (void)cycles_out;
-    return seterr(HJ_ERR_UNSUPPORTED, "batched solve not available in this build");
-}
+
 
 }  // extern "C"

@@ -30,7 +30,8 @@ struct AuxArgs {
     void *uout;           // refinement: u + d (binary64)
     const double *sigma;  // nullable
     float *r32;           // nullable: binary32 copy of r (interior; ghosts untouched)
-    long long ld;
+    long long ld;         // pitch of f, u, uout, sigma
+    long long ld2;        // pitch of r32 and d
     int nx, ny;
     double cW, cE, cS, cN, dconst;
     RedArgs red;
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const AuxArgs a) {
                                              D == 2 ? (double)u[q + a.ld] : 0.0, a.cW, a.cE, a.cS, a.cN);
         rr = r * r;
         ff = fv * fv;
-        if (a.r32) a.r32[q] = (float)r;
+        if (a.r32) a.r32[(long long)j * a.ld2 + i] = (float)r;
     }
     if (WITH_F) {
         const double vals[2] = {rr, ff};
@@ -96,20 +97,21 @@ __global__ void __launch_bounds__(256) update_residual_kernel(const AuxArgs a) {
         const double *u = (const double *)a.u;
         const DS *dd = (const DS *)a.d;
         const long long q = (long long)j * a.ld + i;
-        const double uc = __dadd_rn(u[q], ld_corr<DS>(dd + q));
-        const double uW = __dadd_rn(u[q - 1], ld_corr<DS>(dd + q - 1));
-        const double uE = __dadd_rn(u[q + 1], ld_corr<DS>(dd + q + 1));
+        const long long q2 = (long long)j * a.ld2 + i;
+        const double uc = __dadd_rn(u[q], ld_corr<DS>(dd + q2));
+        const double uW = __dadd_rn(u[q - 1], ld_corr<DS>(dd + q2 - 1));
+        const double uE = __dadd_rn(u[q + 1], ld_corr<DS>(dd + q2 + 1));
         double uS = 0.0, uN = 0.0;
         if (D == 2) {
-            uS = __dadd_rn(u[q - a.ld], ld_corr<DS>(dd + q - a.ld));
-            uN = __dadd_rn(u[q + a.ld], ld_corr<DS>(dd + q + a.ld));
+            uS = __dadd_rn(u[q - a.ld], ld_corr<DS>(dd + q2 - a.ld2));
+            uN = __dadd_rn(u[q + a.ld], ld_corr<DS>(dd + q2 + a.ld2));
         }
         ((double *)a.uout)[q] = uc;
         const double fv = ((const double *)a.f)[q];
         const double d = a.sigma ? __dadd_rn(a.dconst, a.sigma[q]) : a.dconst;
         const double r = resid_exact<D == 2>(fv, d, uc, uW, uE, uS, uN, a.cW, a.cE, a.cS, a.cN);
         rr = r * r;
-        a.r32[q] = (float)r;
+        a.r32[q2] = (float)r;
     }
     const double vals[1] = {rr};
     reduce_grid<1>(a.red, vals);
@@ -130,13 +132,10 @@ __global__ void __launch_bounds__(256) grad_sigma_kernel(const T *lam, const T *
 
 template <typename T>
 __global__ void __launch_bounds__(256) make_dinv_kernel(const double *sigma, double dconst, long long ld,
-                                                       int rows, int cols, T *dinv) {
+                                                       long long ld2, int rows, int cols, T *dinv) {
     const int i = blockIdx.x * 256 + threadIdx.x;
     const int j = blockIdx.y;
-    if (i < cols && j < rows) {
-        const long long q = (long long)j * ld + i;
-        dinv[q] = (T)__drcp_rn(__dadd_rn(dconst, sigma[q]));
-    }
+    if (i < cols && j < rows) dinv[(long long)j * ld2 + i] = (T)__drcp_rn(__dadd_rn(dconst, sigma[(long long)j * ld + i]));
 }
 
 dim3 aux_grid(int dim, int nx, int ny) {
@@ -147,22 +146,22 @@ dim3 aux_block(int dim) { return dim == 2 ? dim3(32, 8) : dim3(256); }
 }  // namespace
 
 // rows/cols: the index box of interior points, in grid coordinates
-cudaError_t launch_make_dinv_box(const double *sigma, double dconst, long long ld, int row0, int rows, int col0,
-                                 int cols, int family, void *dinv, cudaStream_t s) {
-    const size_t off = (size_t)row0 * ld + col0;
+cudaError_t launch_make_dinv_box(const double *sigma, double dconst, long long ld, long long ld2, int row0, int rows,
+                                 int col0, int cols, int family, void *dinv, cudaStream_t s) {
+    const size_t off = (size_t)row0 * ld + col0, off2 = (size_t)row0 * ld2 + col0;
     dim3 grid((cols + 255) / 256, rows);
     if (family == FAM_F64)
-        make_dinv_kernel<double><<<grid, 256, 0, s>>>(sigma + off, dconst, ld, rows, cols, (double *)dinv + off);
+        make_dinv_kernel<double><<<grid, 256, 0, s>>>(sigma + off, dconst, ld, ld2, rows, cols, (double *)dinv + off2);
     else
-        make_dinv_kernel<float><<<grid, 256, 0, s>>>(sigma + off, dconst, ld, rows, cols, (float *)dinv + off);
+        make_dinv_kernel<float><<<grid, 256, 0, s>>>(sigma + off, dconst, ld, ld2, rows, cols, (float *)dinv + off2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual_ex(int dim, int user_f64, const void *f, const void *u, const double *sigma,
-                               long long ld, int nx, int ny, double cW, double cE, double cS, double cN,
-                               double dconst, int with_fnorm, float *r32, RedArgs red, cudaStream_t s) {
+                               long long ld, long long ld2, int nx, int ny, double cW, double cE, double cS,
+                               double cN, double dconst, int with_fnorm, float *r32, RedArgs red, cudaStream_t s) {
     AuxArgs a = {};
-    a.f = f; a.u = u; a.sigma = sigma; a.r32 = r32; a.ld = ld; a.nx = nx; a.ny = ny;
+    a.f = f; a.u = u; a.sigma = sigma; a.r32 = r32; a.ld = ld; a.ld2 = ld2; a.nx = nx; a.ny = ny;
     a.cW = cW; a.cE = cE; a.cS = cS; a.cN = cN; a.dconst = dconst; a.red = red;
     const dim3 g = aux_grid(dim, nx, ny), b = aux_block(dim);
 #define HJ_RES_LAUNCH(T, D)                                                              \
@@ -180,11 +179,12 @@ cudaError_t launch_residual_ex(int dim, int user_f64, const void *f, const void 
 }
 
 cudaError_t launch_update_residual_ex(int dim, const double *f, const double *uin, const void *d, int d_bf16,
-                                      double *uout, const double *sigma, float *r32, long long ld, int nx, int ny,
-                                      double cW, double cE, double cS, double cN, double dconst, RedArgs red,
-                                      cudaStream_t s) {
+                                      double *uout, const double *sigma, float *r32, long long ld, long long ld2,
+                                      int nx, int ny, double cW, double cE, double cS, double cN, double dconst,
+                                      RedArgs red, cudaStream_t s) {
     AuxArgs a = {};
-    a.f = f; a.u = uin; a.d = d; a.uout = uout; a.sigma = sigma; a.r32 = r32; a.ld = ld; a.nx = nx; a.ny = ny;
+    a.f = f; a.u = uin; a.d = d; a.uout = uout; a.sigma = sigma; a.r32 = r32; a.ld = ld; a.ld2 = ld2;
+    a.nx = nx; a.ny = ny;
     a.cW = cW; a.cE = cE; a.cS = cS; a.cN = cN; a.dconst = dconst; a.red = red;
     const dim3 g = aux_grid(dim, nx, ny), b = aux_block(dim);
     if (d_bf16) {

@@ -105,26 +105,36 @@ __device__ __forceinline__ T point_update(const Coef<T> &k, T g, T iv, T W, T E,
 }
 
 // ---------------------------------------------------------------------------
-// 2D tile
+// 2D tile: register state, staging (from global or from a TMA-filled shared
+// box), the k subiterations, and the write-back.
 // ---------------------------------------------------------------------------
-template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG, bool RES, bool PART>
-__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type tile2d(const CycArgs &a, const int x0, const int y0, T *xbuf) {
+template <typename T, int C, int R, bool SIG>
+struct Tile2D {
+    T v[R][C];                       // band values (current iterate)
+    T g[R][C];                       // RHS term: f (exact / sigma) or f/d (fast)
+    T dv[SIG ? R : 1][SIG ? C : 1];  // per-point 1/d_p
+    T hx[R];                         // frozen halo column: lane 0 -> W, lane 31 -> E
+    T top[C], bot[C];                // row above / below the band
+};
+
+template <typename T, bool EXACT, bool SIG>
+__device__ __forceinline__ T rhs_term(const Coef<T> &kc, T fv) {
+    if constexpr (EXACT || SIG) return fv;
+    else return fv * kc.invd;
+}
+
+// Stage from global memory with predicated loads (zero beyond the ghost ring).
+template <typename S, typename T, int C, int R, bool EXACT, bool SIG, bool PART>
+__device__ __forceinline__ void stage2d_global(Tile2D<T, C, R, SIG> &t, const CycArgs &a, const Coef<T> &kc,
+                                               const int x0, const int yb) {
     constexpr int TX = 32 * C;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int yb = y0 + w * R;
+    const int lane = threadIdx.x & 31;
     const int xl = x0 + lane * C;
     const long long ld = a.ld;
     const int nx = a.nx, ny = a.ny;
     const S *__restrict__ uin = (const S *)a.uin;
     const T *__restrict__ f = (const T *)a.f;
     const T *__restrict__ dinv = (const T *)a.dinv;
-    const Coef<T> kc = make_coef<T>(a);
-
-    T v[R][C], g[R][C];
-    T dv[SIG ? R : 1][SIG ? C : 1];
-    T hx[R], top[C], bot[C];
-
-    // ---- stage tile + halo (u_c) and RHS into registers ----
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int row = yb + r;
@@ -136,101 +146,139 @@ __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type til
             const long long q = (long long)row * ld + col;
             const bool ok = rowok && (!PART || col <= nx + 1);
             const bool in = rowin && (!PART || col <= nx);
-            v[r][c] = ok ? ld_s<S, T>(uin + q) : (T)0;
-            const T fv = in ? __ldg(f + q) : (T)0;
-            if constexpr (SIG) {
-                dv[r][c] = in ? __ldg(dinv + q) : (T)0;
-                g[r][c] = fv;
-            } else if constexpr (EXACT) {
-                g[r][c] = fv;
-            } else {
-                g[r][c] = fv * kc.invd;
-            }
+            t.v[r][c] = ok ? ld_s<S, T>(uin + q) : (T)0;
+            t.g[r][c] = rhs_term<T, EXACT, SIG>(kc, in ? __ldg(f + q) : (T)0);
+            if constexpr (SIG) t.dv[r][c] = in ? __ldg(dinv + q) : (T)0;
         }
         const int hcol = (lane == 0) ? x0 - 1 : x0 + TX;
         const bool hok = (lane == 0 || lane == 31) && rowok && (!PART || hcol <= nx + 1);
-        hx[r] = hok ? ld_s<S, T>(uin + (long long)row * ld + hcol) : (T)0;
+        t.hx[r] = hok ? ld_s<S, T>(uin + (long long)row * ld + hcol) : (T)0;
     }
-    {
-        const int rt = yb - 1, rb = yb + R;
+    const int rt = yb - 1, rb = yb + R;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int col = xl + c;
+        const bool okc = !PART || col <= nx + 1;
+        t.top[c] = (okc && (!PART || rt <= ny + 1)) ? ld_s<S, T>(uin + (long long)rt * ld + col) : (T)0;
+        t.bot[c] = (okc && (!PART || rb <= ny + 1)) ? ld_s<S, T>(uin + (long long)rb * ld + col) : (T)0;
+    }
+}
+
+template <typename S, typename T> __device__ __forceinline__ T sm_s(const S *p) { return (T)*p; }
+template <> __device__ __forceinline__ float sm_s<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
+    return __bfloat162float(*p);
+}
+
+// Stage from shared-memory boxes filled by TMA.  su: (TY+2) rows of the
+// iterate starting at (x0-1, y0-1); sf / sd: TY rows of f / (1/d) starting at
+// (x0-1, y0); all with row pitch bw elements.  Out-of-bounds box elements
+// were zero-filled by the copy engine, exactly like the predicated path.
+template <typename S, typename T, int C, int R, bool EXACT, bool SIG>
+__device__ __forceinline__ void stage2d_smem(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const S *su, const T *sf,
+                                             const T *sd, const int bwu, const int bwf, const int band_row0) {
+    constexpr int TX = 32 * C;
+    const int lane = threadIdx.x & 31;
+    const int xc = 1 + lane * C;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int sr = band_row0 + r;   // tile-interior row index
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            const int col = xl + c;
-            const bool okc = !PART || col <= nx + 1;
-            top[c] = (okc && (!PART || rt <= ny + 1)) ? ld_s<S, T>(uin + (long long)rt * ld + col) : (T)0;
-            bot[c] = (okc && (!PART || rb <= ny + 1)) ? ld_s<S, T>(uin + (long long)rb * ld + col) : (T)0;
+            t.v[r][c] = sm_s<S, T>(su + (sr + 1) * bwu + xc + c);
+            t.g[r][c] = rhs_term<T, EXACT, SIG>(kc, sf[sr * bwf + xc + c]);
+            if constexpr (SIG) t.dv[r][c] = sd[sr * bwf + xc + c];
         }
+        const int hcol = (lane == 0) ? 0 : TX + 1;
+        t.hx[r] = sm_s<S, T>(su + (sr + 1) * bwu + hcol);
     }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        t.top[c] = sm_s<S, T>(su + band_row0 * bwu + xc + c);
+        t.bot[c] = sm_s<S, T>(su + (band_row0 + R + 1) * bwu + xc + c);
+    }
+}
 
+// k subiterations on registers.  Returns this thread's share of
+// ||f - A u_c||^2 (unscaled by d^2 on the fast constant-diagonal path).
+template <typename T, int C, int R, int NW, bool EXACT, bool SIG, bool RES, bool PART>
+__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type
+sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, const int yb, const int nx,
+         const int ny, T *xbuf) {
+    constexpr int TX = 32 * C;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int xl = x0 + lane * C;
     typedef typename std::conditional<EXACT, double, T>::type Acc;
     Acc acc = 0;
-
-    // ---- k subiterations on registers ----
     auto sweep = [&](auto first_tag) {
         constexpr bool FIRST = decltype(first_tag)::value;
         T prev[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) prev[c] = top[c];
+        for (int c = 0; c < C; ++c) prev[c] = t.top[c];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             T cur[C];
 #pragma unroll
-            for (int c = 0; c < C; ++c) cur[c] = v[r][c];
+            for (int c = 0; c < C; ++c) cur[c] = t.v[r][c];
             T left = __shfl_up_sync(FULL, cur[C - 1], 1);
             T right = __shfl_down_sync(FULL, cur[0], 1);
-            if (lane == 0) left = hx[r];
-            if (lane == 31) right = hx[r];
+            if (lane == 0) left = t.hx[r];
+            if (lane == 31) right = t.hx[r];
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 const T W = (c == 0) ? left : cur[c > 0 ? c - 1 : 0];
                 const T E = (c == C - 1) ? right : cur[c < C - 1 ? c + 1 : 0];
                 const T Sv = prev[c];
-                const T Nv = (r == R - 1) ? bot[c] : v[r < R - 1 ? r + 1 : 0][c];
+                const T Nv = (r == R - 1) ? t.bot[c] : t.v[r < R - 1 ? r + 1 : 0][c];
                 T res = 0;
                 T nv = point_update<T, EXACT, SIG, true, FIRST && RES>(
-                    kc, g[r][c], SIG ? dv[SIG ? r : 0][SIG ? c : 0] : (T)0, W, E, Sv, Nv, cur[c], res);
+                    kc, t.g[r][c], SIG ? t.dv[SIG ? r : 0][SIG ? c : 0] : (T)0, W, E, Sv, Nv, cur[c], res);
                 if constexpr (PART) {
                     const bool act = (yb + r <= ny) && (xl + c <= nx);
                     nv = act ? nv : cur[c];
                     if (!act) res = 0;
                 }
                 if constexpr (FIRST && RES) acc += (Acc)res * (Acc)res;
-                v[r][c] = nv;
+                t.v[r][c] = nv;
             }
 #pragma unroll
             for (int c = 0; c < C; ++c) prev[c] = cur[c];
         }
     };
-
     int par = 0;
     auto exchange = [&]() {
         if constexpr (NW > 1) {
             T *buf = xbuf + par * (NW * 2 * TX);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                buf[(w * 2 + 0) * TX + lane * C + c] = v[0][c];
-                buf[(w * 2 + 1) * TX + lane * C + c] = v[R - 1][c];
+                buf[(w * 2 + 0) * TX + lane * C + c] = t.v[0][c];
+                buf[(w * 2 + 1) * TX + lane * C + c] = t.v[R - 1][c];
             }
             __syncthreads();
             if (w > 0) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) top[c] = buf[((w - 1) * 2 + 1) * TX + lane * C + c];
+                for (int c = 0; c < C; ++c) t.top[c] = buf[((w - 1) * 2 + 1) * TX + lane * C + c];
             }
             if (w < NW - 1) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) bot[c] = buf[((w + 1) * 2 + 0) * TX + lane * C + c];
+                for (int c = 0; c < C; ++c) t.bot[c] = buf[((w + 1) * 2 + 0) * TX + lane * C + c];
             }
             par ^= 1;
         }
     };
-
     sweep(std::integral_constant<bool, true>());
-    for (int s = 1; s < a.k; ++s) {
+    for (int s = 1; s < k; ++s) {
         exchange();
         sweep(std::integral_constant<bool, false>());
     }
+    return acc;
+}
 
-    // ---- write the tile interior into u_{c+1} ----
+// Write the band's interior points into u_{c+1}.
+template <typename S, typename T, int C, int R, bool SIG, bool PART>
+__device__ __forceinline__ void store2d(const Tile2D<T, C, R, SIG> &t, const CycArgs &a, const int x0,
+                                        const int yb) {
+    const int lane = threadIdx.x & 31;
+    const int xl = x0 + lane * C;
     S *__restrict__ uout = (S *)a.uout;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -238,9 +286,21 @@ __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type til
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const int col = xl + c;
-            if (!PART || (row <= ny && col <= nx)) st_s<S, T>(uout + (long long)row * ld + col, v[r][c]);
+            if (!PART || (row <= a.ny && col <= a.nx)) st_s<S, T>(uout + (long long)row * a.ld + col, t.v[r][c]);
         }
     }
+}
+
+template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG, bool RES, bool PART>
+__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type tile2d(const CycArgs &a, const int x0,
+                                                                                    const int y0, T *xbuf) {
+    const int w = threadIdx.x >> 5;
+    const int yb = y0 + w * R;
+    const Coef<T> kc = make_coef<T>(a);
+    Tile2D<T, C, R, SIG> t;
+    stage2d_global<S, T, C, R, EXACT, SIG, PART>(t, a, kc, x0, yb);
+    auto acc = sweeps2d<T, C, R, NW, EXACT, SIG, RES, PART>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
+    store2d<S, T, C, R, SIG, PART>(t, a, x0, yb);
     return acc;
 }
 

@@ -1,5 +1,6 @@
 // Binary64 cycle kernels (exact evaluation order, no fused multiply-add).
-#include "hj_cycle.cuh"
+#include "hj_persist.cuh"
+#include "hj_tma.cuh"
 
 namespace hj {
 
@@ -19,5 +20,27 @@ static const TileKernelInfo k_classic[] = {HJ_KC2D(double, double, true), HJ_KC1
 
 const TileKernelInfo *tile_kernels_f64(int *n) { *n = sizeof(k_tiles) / sizeof(k_tiles[0]); return k_tiles; }
 const TileKernelInfo *classic_kernels_f64(int *n) { *n = 2; return k_classic; }
+
+static const PpcKernelInfo k_ppc[] = {
+    HJ_KPPC(double, double, 1, 16, 2, true, 2),   // 32 x 32
+    HJ_KPPC(double, double, 1, 16, 1, true, 2),   // 32 x 16
+    HJ_KPPC(double, double, 1, 8, 1, true, 2),   // 32 x 8
+    HJ_KPPC(double, double, 1, 16, 4, true, 2),   // 32 x 64
+    HJ_KPPC(double, double, 2, 8, 4, true, 2),   // 64 x 32
+    HJ_KPPC(double, double, 2, 8, 8, true, 2),   // 64 x 64
+};
+const PpcKernelInfo *ppc_kernels_f64(int *n) { *n = sizeof(k_ppc) / sizeof(k_ppc[0]); return k_ppc; }
+
+static const PersistKernelInfo k_persist[] = {
+    HJ_KP2D(double, double, 1, 16, 2, true),
+    HJ_KP2D(double, double, 1, 16, 1, true),
+    HJ_KP2D(double, double, 1, 8, 1, true),
+    HJ_KP2D(double, double, 2, 8, 4, true),
+    HJ_KP1D(double, double, 1, 4, true),
+    HJ_KP1D(double, double, 2, 4, true),
+    HJ_KP1D(double, double, 4, 4, true),
+    HJ_KP1D(double, double, 8, 4, true),
+};
+const PersistKernelInfo *persist_kernels_f64(int *n) { *n = sizeof(k_persist) / sizeof(k_persist[0]); return k_persist; }
 
 }  // namespace hj

@@ -25,6 +25,10 @@ struct Ctl {
     long long cycle;     // index of the iterate whose residual the next cycle computes
     double res2_0;       // ||r_0||^2
     double res2_last;    // ||r_c||^2 of the last reduced cycle
+    int err;             // HJ_ERR_TIMEOUT if a bounded device wait expired
+    int pad;
+    double res2_mark;    // stagnation rule: ||r||^2 at cycle mark_cycle
+    long long mark_cycle;
 };
 
 constexpr int kHistCap = 8192;     // device ring of per-cycle ||r_c||^2 (power of two)
@@ -42,6 +46,8 @@ struct RedArgs {
     Ctl *ctl;            // RED_CYCLE: control block
     double tol;          // stop at ||r_c|| <= tol ||r_0||
     double scale;        // RED_CYCLE: the reduced sum is multiplied by this (d^2 for the fast path)
+    long long stall_window;  // > 0: also stop when ||r|| moved by <= stall_rtol relative over this many cycles
+    double stall_rtol;
     long long max_cycles;
     int mode;            // RedMode
 };
@@ -91,6 +97,25 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Stagnation rule of the refinement's inner solves: every stall_window cycles,
+// compare ||r_c|| with its value stall_window cycles earlier; a relative change
+// of at most stall_rtol means the iterate has reached the fixed point that its
+// storage precision allows (bitwise, in practice), so further cycles are wasted.
+__device__ __forceinline__ bool stalled(const RedArgs &r, long long c, double res2, volatile double *mark,
+                                        volatile long long *mark_c) {
+    if (r.stall_window <= 0) return false;
+    if (c == 0) {
+        *mark = res2;
+        *mark_c = 0;
+        return false;
+    }
+    if (c - *mark_c < r.stall_window) return false;
+    const double a = sqrt(res2), b = sqrt(*mark);
+    *mark = res2;
+    *mark_c = c;
+    return fabs(a - b) <= r.stall_rtol * a;
+}
+
 // Fold ||r_c||^2 of the cycle into the control block (runs on one thread).
 __device__ __forceinline__ void finish_cycle(const RedArgs &r, double res2) {
     volatile Ctl *ctl = r.ctl;   // written by earlier launches: bypass L1
@@ -104,6 +129,8 @@ __device__ __forceinline__ void finish_cycle(const RedArgs &r, double res2) {
         ctl->status = HJ_ERR_DIVERGED;
         ctl->done = (int)c;
     } else if (rc <= r.tol * r0) {
+        ctl->done = (int)c;
+    } else if (stalled(r, c, res2, &ctl->res2_mark, &ctl->mark_cycle)) {
         ctl->done = (int)c;
     } else if (c + 1 >= r.max_cycles) {
         ctl->status = HJ_ERR_NOT_CONVERGED;
@@ -212,6 +239,17 @@ __device__ __forceinline__ void reduce_grid_acc(const RedArgs &r, A acc) {
 // Launch-side description of one compiled cycle kernel.
 typedef void (*CycKernel)(CycArgs);
 
+struct PpcArgs;
+typedef void (*PpcKernel)(PpcArgs);
+
+// TMA-pipelined 2D cycle kernel (hj_tma.cuh).
+struct PpcKernelInfo {
+    int tx, ty, threads;
+    int smem[2];        // dynamic shared memory bytes [sig]
+    int bwu, bwf;       // box widths (elements) of the iterate / RHS boxes
+    PpcKernel fn[2][2]; // [sig][res]
+};
+
 struct TileKernelInfo {
     int dim;            // 1 or 2
     int tx, ty;         // tile interior shape (1D: ty = 1)
@@ -228,17 +266,20 @@ const TileKernelInfo *tile_kernels_bf16(int *n);
 const TileKernelInfo *classic_kernels_f64(int *n);
 const TileKernelInfo *classic_kernels_f32(int *n);
 const TileKernelInfo *classic_kernels_bf16(int *n);
+const PpcKernelInfo *ppc_kernels_f64(int *n);
+const PpcKernelInfo *ppc_kernels_f32(int *n);
+const PpcKernelInfo *ppc_kernels_bf16(int *n);
 
 // Grid-wide helper kernels (hj_aux.cu).
-cudaError_t launch_make_dinv_box(const double *sigma, double dconst, long long ld, int row0, int rows, int col0,
-                                 int cols, int family, void *dinv, cudaStream_t s);
+cudaError_t launch_make_dinv_box(const double *sigma, double dconst, long long ld, long long ld2, int row0, int rows,
+                                 int col0, int cols, int family, void *dinv, cudaStream_t s);
 cudaError_t launch_residual_ex(int dim, int user_f64, const void *f, const void *u, const double *sigma,
-                               long long ld, int nx, int ny, double cW, double cE, double cS, double cN,
-                               double dconst, int with_fnorm, float *r32, RedArgs red, cudaStream_t s);
+                               long long ld, long long ld2, int nx, int ny, double cW, double cE, double cS,
+                               double cN, double dconst, int with_fnorm, float *r32, RedArgs red, cudaStream_t s);
 cudaError_t launch_update_residual_ex(int dim, const double *f, const double *uin, const void *d, int d_bf16,
-                                      double *uout, const double *sigma, float *r32, long long ld, int nx, int ny,
-                                      double cW, double cE, double cS, double cN, double dconst, RedArgs red,
-                                      cudaStream_t s);
+                                      double *uout, const double *sigma, float *r32, long long ld, long long ld2,
+                                      int nx, int ny, double cW, double cE, double cS, double cN, double dconst,
+                                      RedArgs red, cudaStream_t s);
 cudaError_t launch_grad_sigma_ex(int dim, int user_f64, const void *lam, const void *u, double *dsig, long long ld,
                                  int nx, int ny, cudaStream_t s);
 int aux_max_blocks(int dim, int nx, int ny);

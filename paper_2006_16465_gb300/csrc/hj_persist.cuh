@@ -1,0 +1,235 @@
+// hj_persist.cuh -- persistent multi-cycle kernel: one cooperative launch runs
+// the cycles of one or many problems until each meets its tolerance.
+//
+// Work items are (problem, block) pairs in a flat list; every CTA walks the
+// list with a static stride.  A cycle is:
+//   phase A  every item of an active problem runs one hierarchical cycle of
+//            its tile(s) (stage u_c + halo, k subiterations, write u_{c+1})
+//            and stores its share of ||f - A u_c||^2;
+//   barrier  (grid-wide, bounded)
+//   phase B  CTA b reduces problems b, b + G, ... in a fixed order, records
+//            ||r_c||, and retires the problem when it meets its tolerance
+//            (its iterate u_c is still intact in buffer c mod 2), diverges, or
+//            reaches its cycle cap;
+//   barrier  (grid-wide, bounded); stop when no problem is active.
+// Problems of different sizes, stencils, k and tolerances share the launch.
+// Every barrier wait is bounded by wall time (%globaltimer); on expiry the
+// kernel records HJ_ERR_TIMEOUT in the error word and every CTA returns.
+#pragma once
+
+#include "hj_cycle.cuh"
+
+namespace hj {
+
+struct ProbState {
+    int done;           // -1 while active; else index of the returned iterate
+    int status;         // HJ_OK / HJ_ERR_DIVERGED / HJ_ERR_NOT_CONVERGED
+    long long cycle;    // cycles completed
+    double res2_0;      // ||r_0||^2
+    double res2_last;   // ||r_c||^2 of the last reduced cycle
+    double res2_mark;   // stagnation rule state
+    long long mark_cycle;
+};
+
+struct PersistArgs {
+    const CycArgs *probs;    // per problem: f, b0 (=uin), b1 (=uout), dinv, geometry, k, coefficients,
+                             // red.tol, red.max_cycles, red.scale
+    ProbState *state;        // per problem
+    const int *item_prob;    // per item: problem index
+    const int *item_blk;     // per item: block index within the problem (bx + tiles_x * by)
+    const int *prob_item0;   // per problem: first item index (items of a problem are contiguous)
+    const int *prob_nitems;  // per problem: number of items
+    const int *prob_tiles_x; // per problem: blocks along x
+    double *partial;         // [2][nitems]
+    unsigned *bar;           // [0] arrival count, [1] generation (zero before launch)
+    int *active;             // number of active problems (set before launch)
+    int *err;                // error word
+    int nprob, nitems;
+    long long max_iters;     // cap on cycles in this launch
+    unsigned long long timeout_ns;
+    int skip_barrier_cta;    // test hook: this CTA leaves before the first barrier (-1 = none)
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  Returns
+// false if the wait expired or another CTA already recorded an error.
+__device__ __forceinline__ bool grid_barrier(const PersistArgs &P) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = P.bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(P.bar, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(P.bar, 0u);
+            __threadfence();
+            atomicAdd(P.bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*vgen == gen) {
+                if (*(volatile int *)P.err) { ok = 0; break; }
+                if (global_ns() - t0 > P.timeout_ns) {
+                    atomicExch(P.err, HJ_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && (*(volatile int *)P.err == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename A>
+__device__ __forceinline__ double cta_sum(A acc) {
+    __shared__ double s_w[32];
+    double v;
+    if constexpr (std::is_same<A, float>::value) v = (double)warp_sum_f(acc);
+    else v = warp_sum(acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) s_w[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += s_w[i];
+    return s;
+}
+
+// Phase B for problem p (run by warp 0 of one CTA).
+__device__ __forceinline__ void retire_check(const PersistArgs &P, int p, int parity) {
+    const int lane = threadIdx.x & 31;
+    const int i0 = P.prob_item0[p], n = P.prob_nitems[p];
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += __ldcg(&P.partial[(size_t)parity * P.nitems + i0 + i]);
+    s = warp_sum(s);
+    if (lane == 0) {
+        volatile ProbState *st = P.state + p;
+        const RedArgs &r = P.probs[p].red;
+        const double res2 = s * r.scale;
+        const long long c = st->cycle;
+        if (r.hist) r.hist[c & (kHistCap - 1)] = res2;
+        if (c == 0) st->res2_0 = res2;
+        const double r0 = sqrt(c == 0 ? res2 : st->res2_0);
+        const double rc = sqrt(res2);
+        st->res2_last = res2;
+        int retire = 1;
+        if (!isfinite(rc)) {
+            st->status = HJ_ERR_DIVERGED;
+            st->done = (int)c;
+        } else if (rc <= r.tol * r0) {
+            st->done = (int)c;
+        } else if (stalled(r, c, res2, &st->res2_mark, &st->mark_cycle)) {
+            st->done = (int)c;
+        } else if (c + 1 >= r.max_cycles) {
+            st->status = HJ_ERR_NOT_CONVERGED;
+            st->done = (int)(c + 1);
+        } else {
+            retire = 0;
+        }
+        st->cycle = c + 1;
+        if (retire) atomicSub(P.active, 1);
+    }
+}
+
+template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG>
+__global__ void __launch_bounds__(32 * NW) persist2d_kernel(const PersistArgs P) {
+    constexpr int TX = 32 * C, TY = R * NW;
+    constexpr int XB = NW > 1 ? 2 * NW * 2 * TX : 1;
+    __shared__ T xbuf[XB];
+    for (long long it = 0; it < P.max_iters; ++it) {
+        const int parity = (int)(it & 1);
+        for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
+            const int p = P.item_prob[item];
+            volatile ProbState *st = P.state + p;
+            if (st->done >= 0) continue;
+            CycArgs a = P.probs[p];
+            if (st->cycle & 1) {
+                const void *t = a.uin;
+                a.uin = a.uout;
+                a.uout = const_cast<void *>(t);
+            }
+            const int blk = P.item_blk[item], tx = P.prob_tiles_x[p];
+            const int x0 = 1 + (blk % tx) * TX, y0 = 1 + (blk / tx) * TY;
+            typename std::conditional<EXACT, double, T>::type acc;
+            if (x0 + TX - 1 <= a.nx && y0 + TY - 1 <= a.ny)
+                acc = tile2d<S, T, C, R, NW, EXACT, SIG, true, false>(a, x0, y0, xbuf);
+            else
+                acc = tile2d<S, T, C, R, NW, EXACT, SIG, true, true>(a, x0, y0, xbuf);
+            const double s = cta_sum(acc);
+            if (threadIdx.x == 0) P.partial[(size_t)parity * P.nitems + item] = s;
+        }
+        if ((int)blockIdx.x == P.skip_barrier_cta) return;
+        if (!grid_barrier(P)) return;
+        if (threadIdx.x < 32) {
+            for (int p = blockIdx.x; p < P.nprob; p += gridDim.x)
+                if (((volatile ProbState *)P.state + p)->done < 0) retire_check(P, p, parity);
+        }
+        if (!grid_barrier(P)) return;
+        if (*(volatile int *)P.active <= 0) return;
+    }
+}
+
+template <typename S, typename T, int C, int WPB, bool EXACT, bool SIG>
+__global__ void __launch_bounds__(32 * WPB) persist1d_kernel(const PersistArgs P) {
+    constexpr int TX = 32 * C;
+    for (long long it = 0; it < P.max_iters; ++it) {
+        const int parity = (int)(it & 1);
+        for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
+            const int p = P.item_prob[item];
+            volatile ProbState *st = P.state + p;
+            if (st->done >= 0) continue;
+            CycArgs a = P.probs[p];
+            if (st->cycle & 1) {
+                const void *t = a.uin;
+                a.uin = a.uout;
+                a.uout = const_cast<void *>(t);
+            }
+            const int blk = P.item_blk[item], bxn = P.prob_tiles_x[p];
+            const int w = threadIdx.x >> 5;
+            const int x0 = 1 + ((blk % bxn) * WPB + w) * TX;
+            const int row = blk / bxn;
+            typename std::conditional<EXACT, double, T>::type acc = 0;
+            if (x0 <= a.nx) {
+                if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, EXACT, SIG, true, false>(a, x0, row);
+                else acc = tile1d<S, T, C, EXACT, SIG, true, true>(a, x0, row);
+            }
+            const double s = cta_sum(acc);
+            if (threadIdx.x == 0) P.partial[(size_t)parity * P.nitems + item] = s;
+        }
+        if ((int)blockIdx.x == P.skip_barrier_cta) return;
+        if (!grid_barrier(P)) return;
+        if (threadIdx.x < 32) {
+            for (int p = blockIdx.x; p < P.nprob; p += gridDim.x)
+                if (((volatile ProbState *)P.state + p)->done < 0) retire_check(P, p, parity);
+        }
+        if (!grid_barrier(P)) return;
+        if (*(volatile int *)P.active <= 0) return;
+    }
+}
+
+typedef void (*PersistKernel)(PersistArgs);
+
+struct PersistKernelInfo {
+    int dim, tx, ty, threads, tiles_per_cta;
+    PersistKernel fn[2];   // [sig]
+};
+
+}  // namespace hj
+
+#define HJ_KP2D(S, T, C, R, NW, EX) \
+    {2, 32 * (C), (R) * (NW), 32 * (NW), 1, \
+     {hj::persist2d_kernel<S, T, C, R, NW, EX, false>, hj::persist2d_kernel<S, T, C, R, NW, EX, true>}}
+#define HJ_KP1D(S, T, C, WPB, EX) \
+    {1, 32 * (C), 1, 32 * (WPB), (WPB), \
+     {hj::persist1d_kernel<S, T, C, WPB, EX, false>, hj::persist1d_kernel<S, T, C, WPB, EX, true>}}

@@ -1,0 +1,108 @@
+// hj_runtime.cuh -- host runtime internals shared by the C-ABI translation
+// units: the handle, error reporting, and the engines the solve calls use.
+#pragma once
+
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "hj_internal.cuh"
+#include "hj_persist.cuh"
+
+namespace hj {
+
+int seterr(int code, const char *fmt, ...);
+const char *last_error_text();
+
+#define CKR(call)                                                                                           \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess)                                                                              \
+            return ::hj::seterr(HJ_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                                __LINE__);                                                                  \
+    } while (0)
+
+#define CKS(expr)                     \
+    do {                              \
+        int st_ = (expr);             \
+        if (st_ != HJ_OK) return st_; \
+    } while (0)
+
+// A captured graph of M alternating launches, keyed by the kernel, the launch
+// shape and the bytes of both argument blocks.
+struct GraphEntry {
+    const void *fn;
+    dim3 grid, block;
+    int smem;
+    std::vector<unsigned char> key;
+    int M;
+    cudaGraphExec_t exec;
+    unsigned long long stamp;
+};
+
+const TileKernelInfo *family_tiles(int fam, int *n);
+const PersistKernelInfo *family_persist(int fam, int *n);
+const PersistKernelInfo *find_persist(int fam, int dim, int tx, int ty);
+const PersistKernelInfo *persist_kernels_f64(int *n);
+const PersistKernelInfo *persist_kernels_f32(int *n);
+const PersistKernelInfo *persist_kernels_bf16(int *n);
+
+}  // namespace hj
+
+struct hj_handle {
+    hj_desc d;
+    hj_params p;
+    int dev = 0, nsm = 0;
+    int rows = 0;
+    size_t esz = 0, grid_elems = 0, grid_bytes = 0;
+    int fam_outer = hj::FAM_F64, fam_inner = hj::FAM_F32;
+    bool ir = false;
+    const hj::TileKernelInfo *k_outer = nullptr, *k_inner = nullptr, *k_classic = nullptr, *k_classic_inner = nullptr;
+    const hj::PpcKernelInfo *p_outer = nullptr, *p_inner = nullptr;   // TMA-pipelined variants (2D)
+    long long ld_in = 0;          // row pitch of the refinement's binary32 / bfloat16 arrays
+    void *ubuf = nullptr;
+    void *dinv_outer = nullptr;   // per-point 1/d in the outer compute type (sigma given)
+    float *dinv32 = nullptr;      // per-point 1/d in binary32 (refinement, sigma given)
+    float *r32 = nullptr;         // refinement: binary32 residual (inner RHS)
+    void *dA = nullptr, *dB = nullptr;  // refinement: correction buffers
+    void *hf = nullptr, *hu = nullptr;  // staging for host-pointer solves
+    double *partials = nullptr, *gpart = nullptr, *hist = nullptr, *rstore = nullptr;
+    unsigned *gcnt = nullptr, *fcnt = nullptr;
+    hj::Ctl *ctl = nullptr;
+    hj::Ctl *h_ctl = nullptr, *h_ctl_init = nullptr;
+    double *h_hist = nullptr, *h_rstore = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev = nullptr;
+    std::vector<hj::GraphEntry> graphs;
+    unsigned long long stamp = 0;
+    size_t max_blocks = 0, max_groups = 0;
+    // persistent engine scratch (device) and its pinned staging copy
+    void *pscratch = nullptr;
+    unsigned char *h_pstage = nullptr;
+    size_t pscratch_bytes = 0;
+    // batched solves: per-problem arrays and norms
+    void *barena = nullptr;
+    size_t barena_bytes = 0;
+    double *rs = nullptr, *h_rs = nullptr;
+    size_t nrs = 0;
+};
+
+namespace hj {
+
+// Grow the grid-reduction workspace so that a launch of `blocks` CTAs fits.
+int ensure_reduction(hj_handle *h, size_t blocks);
+// Grow the persistent-engine scratch (items, states, partials, barrier words).
+int ensure_scratch(hj_handle *h, size_t bytes);
+
+// Persistent engine: run cycles of several problems in one cooperative launch.
+struct PersistProblem {
+    CycArgs a;        // f, uin (= u_0 buffer), uout (= other buffer), dinv, geometry, k, coefficients,
+                      // red.tol, red.max_cycles, red.scale (red.hist for a single problem)
+    int blocks_x;     // CTAs along x (2D tiles, or 1D groups of tiles)
+    int blocks;       // CTAs in total
+};
+int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vector<PersistProblem> &probs,
+                   cudaStream_t s, std::vector<ProbState> *out);
+int persist_capacity(hj_handle *h, const PersistKernelInfo *ki, bool sig, int *ctas);
+
+}  // namespace hj

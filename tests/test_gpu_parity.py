@@ -40,15 +40,18 @@ def _torch():
 # binary64 hierarchical cycles: equal cycle counts
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("pipeline", [0, 1])
 @pytest.mark.parametrize("tile", F64_TILES_2D)
 @pytest.mark.parametrize("shape,sigma,asym", [((70, 45), "field", True), ((64, 64), "none", False),
                                                ((97, 130), "const", False)])
-def test_f64_cycles_match_oracle_2d(tile, shape, sigma, asym):
+def test_f64_cycles_match_oracle_2d(tile, shape, sigma, asym, pipeline):
+    """pipeline=1: TMA-staged kernel (CTAs walk tile lists); 0: one CTA per tile."""
     torch = _torch()
     nx, ny = shape
     p = W.random_bc_problem(2, nx, ny, seed=nx + ny, sigma_kind=sigma, asym=asym)
     for k, ncyc in [(1, 3), (5, 4), (16, 2)]:
-        s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=k, precision="f64", fixed_cycles=ncyc)
+        s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=k, precision="f64", fixed_cycles=ncyc,
+                       pipeline=pipeline)
         f = to_dev(p.f, 2, torch.float64)
         u = to_dev(p.u0, 2, torch.float64)
         s.solve(f, u)
@@ -92,6 +95,7 @@ def test_f64_classic_sweeps_match_oracle(dim):
 # converging solves: same stopping cycle, same iterate, same residual history
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("persistent", [0, 1])
 @pytest.mark.parametrize("dim,shape,tile,k,method", [
     (2, (96, 80), (32, 32), 8, "hier"),
     (2, (70, 45), (32, 16), 4, "hier"),
@@ -99,7 +103,9 @@ def test_f64_classic_sweeps_match_oracle(dim):
     (1, (512, 1), (128, 1), 32, "hier"),
     (1, (700, 4), (64, 1), 16, "hier"),
 ])
-def test_f64_convergence_matches_oracle(dim, shape, tile, k, method):
+def test_f64_convergence_matches_oracle(dim, shape, tile, k, method, persistent):
+    """persistent=1: one cooperative launch iterates all cycles (device-side
+    grid barrier); 0: CUDA graphs of check_every launches."""
     torch = _torch()
     nx, ny = shape
     if dim == 1 and ny == 1:
@@ -108,10 +114,11 @@ def test_f64_convergence_matches_oracle(dim, shape, tile, k, method):
         p = W.random_bc_problem(dim, nx, ny, seed=7, sigma_kind="field")
     tol = 1e-6
     s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=k, precision="f64", tol=tol, check_every=16,
-                   method=method)
+                   method=method, persistent=persistent)
     f = to_dev(p.f, dim, torch.float64)
     u = to_dev(p.u0, dim, torch.float64)
     out = s.solve(f, u, history=100000)
+    assert out["persistent"] == (persistent if method == "hier" else 0)
     uo, c, status, hist = oracle.solve(p.st, p.f, p.u0, tol, 10 ** 7, tile[0], tile[1], k,
                                        classic=(method == "classic"), hist_cap=100000)
     assert status == 0 and out["status"] == 0
@@ -142,13 +149,15 @@ def test_residual_api_matches_oracle():
 # binary32 cycles
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("pipeline", [0, 1])
 @pytest.mark.parametrize("tile", F32_TILES_2D)
-def test_f32_cycles_close_to_oracle(tile):
+def test_f32_cycles_close_to_oracle(tile, pipeline):
     torch = _torch()
     nx, ny = 150, 100
     p = W.random_bc_problem(2, nx, ny, seed=9, sigma_kind="none")
     ncyc, k = 20, 8
-    s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=k, precision="f32", fixed_cycles=ncyc)
+    s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=k, precision="f32", fixed_cycles=ncyc,
+                   pipeline=pipeline)
     f = to_dev(p.f, 2, torch.float32)
     u = to_dev(p.u0, 2, torch.float32)
     s.solve(f, u)
@@ -160,12 +169,16 @@ def test_f32_cycles_close_to_oracle(tile):
     s.close()
 
 
+@pytest.mark.parametrize("pipeline", [0, 1])
 @pytest.mark.parametrize("sigma", ["field", "const"])
 @pytest.mark.parametrize("dim", [1, 2])
-def test_f32_screened_and_1d_close_to_oracle(dim, sigma):
+def test_f32_screened_and_1d_close_to_oracle(dim, sigma, pipeline):
     torch = _torch()
+    if dim == 1 and pipeline == 1:
+        pytest.skip("the TMA pipeline is a 2D kernel")
     p = W.random_bc_problem(dim, 200, 60 if dim == 2 else 4, seed=12, sigma_kind=sigma, asym=True)
-    s = gpu_solver(p, tile_x=32 if dim == 2 else 128, tile_y=32, k=6, precision="f32", fixed_cycles=15)
+    s = gpu_solver(p, tile_x=32 if dim == 2 else 128, tile_y=32, k=6, precision="f32", fixed_cycles=15,
+                   pipeline=pipeline)
     f = to_dev(p.f, dim, torch.float32)
     u = to_dev(p.u0, dim, torch.float32)
     s.solve(f, u)
@@ -194,15 +207,18 @@ def test_f32_solve_reaches_tolerance_and_oracle_agrees():
 # mixed-precision iterative refinement
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("engine", ["persistent", "graph", "pipeline"])
 @pytest.mark.parametrize("prec", ["f32_ir", "bf16corr_ir"])
-def test_refinement_reaches_tolerance_and_matches_oracle(prec):
+def test_refinement_reaches_tolerance_and_matches_oracle(prec, engine):
     torch = _torch()
     n = 96
     p = W.poisson2d_sin_noise(n, seed=2)
     tol = 1e-10
     inner_tol = 1e-4 if prec == "f32_ir" else 1e-2
+    eng = {"persistent": dict(persistent=1, pipeline=0), "graph": dict(persistent=0, pipeline=0),
+           "pipeline": dict(persistent=0, pipeline=1)}[engine]
     s = gpu_solver(p, tile_x=32, tile_y=32, k=16, precision=prec, tol=tol, inner_tol=inner_tol,
-                   check_every=16, max_outer=60)
+                   check_every=16, max_outer=60, **eng)
     f = to_dev(p.f, 2, torch.float64)
     u = to_dev(p.u0, 2, torch.float64)
     out = s.solve(f, u, history=64)
@@ -331,3 +347,89 @@ def test_solver_reuse_and_graph_cache():
     assert outs[0][0] == outs[1][0] == outs[2][0]
     assert np.array_equal(outs[0][1], outs[2][1])
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# batched persistent scheduler
+# ---------------------------------------------------------------------------
+
+def _batch(nprob=7, seed=11):
+    sides = [64, 96, 128, 160]
+    out = []
+    for i in range(nprob):
+        nx, ny = sides[i % 4], sides[(i * 3 + 1) % 4]
+        st = W.poisson_stencil(2, nx, ny, sigma_const=float(W.uniform(seed, nprob, 0.0, 100.0)[i]))
+        f = W.zeros_grid(st)
+        f[1:-1, 1:-1] = W.uniform(seed * 100 + i, nx * ny, -1, 1).reshape(ny, nx)
+        out.append(W.Problem(st, f, W.zeros_grid(st)))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["f32_ir", "bf16corr_ir"])
+def test_batched_equals_individual_solves_and_oracle(prec):
+    torch = _torch()
+    import paper_2006_16465_gb300 as hj
+    probs = _batch()
+    tol = 1e-8
+    params = dict(tile_x=32, tile_y=32, k=16, precision=prec, tol=tol, inner_tol=1e-4, max_outer=60)
+    # batched
+    s = gpu_solver(probs[0], **params)
+    fs = [to_dev(q.f, 2, torch.float64) for q in probs]
+    us = [to_dev(q.u0, 2, torch.float64) for q in probs]
+    descs = [hj.make_desc(2, q.st.nx, q.st.ny, f.shape[1], q.st.cW, q.st.cE, q.st.cS, q.st.cN, q.st.cD,
+                          q.st.sigma_const) for q, f in zip(probs, fs)]
+    cyc = (hj.C.c_longlong * len(probs))()
+    code = hj.hj_solve_batched(s.h, descs, [f.data_ptr() for f in fs], [u.data_ptr() for u in us], 0, None, cyc)
+    assert code == 0, hj.hj_last_error()
+    s.close()
+    for i, q in enumerate(probs):
+        # one problem alone through the same persistent engine: bitwise identical
+        si = gpu_solver(q, persistent=1, **params)
+        ui = to_dev(q.u0, 2, torch.float64)
+        out = si.solve(to_dev(q.f, 2, torch.float64), ui)
+        assert out["status"] == 0
+        assert torch.equal(ui, us[i]), f"problem {i}"
+        assert out["inner_cycles"] == cyc[i]
+        si.close()
+        ug = to_host(us[i], q.st.nx)
+        r0 = oracle.residual(q.st, q.f, q.u0)
+        assert oracle.residual(q.st, q.f, ug) <= tol * r0 * 1.0001
+        uo, _, _, st, _ = oracle.ir_solve(q.st, q.f, q.u0, tol, 32, 32, 16, inner_tol=1e-4,
+                                          bf16=(prec == "bf16corr_ir"))
+        assert st == 0
+        hx, hy = 1 / (q.st.nx + 1), 1 / (q.st.ny + 1)
+        kappa = (4 / hx ** 2 + 4 / hy ** 2 + q.st.sigma_const) / (np.pi ** 2 * 2 + q.st.sigma_const)
+        assert np.abs(ug - uo).max() <= 2 * kappa * tol * np.abs(uo).max()
+
+
+_TIMEOUT_SCRIPT = r"""
+import os, sys
+sys.path.insert(0, os.getcwd())
+os.environ["HJ_TEST_SKIP_BARRIER_CTA"] = "0"
+os.environ["HJ_TEST_BARRIER_TIMEOUT_NS"] = "50000000"
+import torch
+import paper_2006_16465_gb300 as hj
+import workloads as W
+p = W.poisson2d_uniform(128, 128, seed=1)
+s = hj.Solver(p.st, tile_x=32, tile_y=32, k=4, precision="f64", tol=1e-8, persistent=1)
+out = s.solve(hj.grid_from(p.f, 2, torch.float64), hj.grid_from(p.u0, 2, torch.float64), check=False)
+print("STATUS", out["status"], hj.hj_last_error())
+s.close()
+"""
+
+
+def test_bounded_grid_barrier_reports_timeout():
+    """One CTA of the persistent launch leaves before the grid barrier (test
+    hook); the others give up after 50 ms and the call returns HJ_ERR_TIMEOUT
+    instead of hanging.  Runs in a child process (the handle is unusable
+    afterwards)."""
+    import subprocess
+    import sys
+    import os
+    import paper_2006_16465_gb300 as hj
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _TIMEOUT_SCRIPT], cwd=root, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("STATUS")][0]
+    assert int(line.split()[1]) == hj.HJ_ERR_TIMEOUT, line
