@@ -136,7 +136,10 @@ typedef struct {
                              a device-side grid barrier (needs all tiles resident);
                              0: one launch per cycle inside CUDA graphs;
                              -1: choose automatically                            */
-    int autotune;         /* 1: pick tile shape and k by measurement on first use */
+    int autotune;         /* 1: pick tile shape and k by measurement (hj_autotune)
+                             at hj_create; 2: keep tile_x, tile_y and tune k only;
+                             hj_solve_batched: tile from the largest problem,
+                             k per size class                                   */
     int pipeline;         /* 2D cycles: 1 = TMA-pipelined kernel (CTAs walk tile
                              lists, next tile staged while the current one
                              sweeps), 0 = one CTA per tile, -1 = automatic      */
@@ -218,6 +221,19 @@ HJ_API const char *hj_error_string(int status);
 
 /* One-line description of the last error on the calling thread ("" if none). */
 HJ_API const char *hj_last_error(void);
+
+/* Pick the subdomain shape (tile_x, tile_y; threads per subdomain follow from
+ * it) and the subiteration count k for desc and params->precision/tol by
+ * measurement on the device, and write them into *params (other fields are
+ * left alone).  k trades in-chip work against halo staleness (Section 3.3);
+ * each candidate is scored by its measured time per cycle times the cycles
+ * its measured contraction rate needs to reach tol.  Results are cached per
+ * process and, when the environment variable HJ_AUTOTUNE_CACHE names a file,
+ * in that file.  *predicted_ms (nullable) receives the predicted time to
+ * tolerance, or -1 for a cache hit.  hj_create runs this when
+ * params->autotune is 1; params->autotune = 2 keeps tile_x, tile_y and tunes
+ * k only. */
+HJ_API int hj_autotune(const hj_desc *desc, hj_params *params, double *predicted_ms);
 
 /* Tile shapes built for (dim, precision): writes up to cap (tile_x, tile_y)
  * pairs into xy[2*i], xy[2*i+1] and returns how many exist. */

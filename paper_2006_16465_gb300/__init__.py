@@ -103,8 +103,9 @@ def lib():
         L.hj_last_error.argtypes = []
         L.hj_last_error.restype = C.c_char_p
         L.hj_tile_shapes.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]
+        L.hj_autotune.argtypes = [C.POINTER(hj_desc), C.POINTER(hj_params), C.POINTER(C.c_double)]
         for name in ("hj_create", "hj_solve", "hj_residual", "hj_solve_adjoint", "hj_solve_batched",
-                     "hj_tile_shapes"):
+                     "hj_tile_shapes", "hj_autotune"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -170,6 +171,16 @@ def hj_error_string(code: int) -> str:
 
 def hj_last_error() -> str:
     return lib().hj_last_error().decode()
+
+
+def hj_autotune(desc: hj_desc, params: hj_params):
+    """Measure and write the best tile_x, tile_y, k into params; returns the
+    predicted milliseconds to tolerance (-1 for a cache hit)."""
+    ms = C.c_double()
+    st = lib().hj_autotune(C.byref(desc), C.byref(params), C.byref(ms))
+    if st != HJ_OK:
+        raise HJError(st, "hj_autotune")
+    return ms.value
 
 
 def hj_tile_shapes(dim: int, precision: int):

@@ -183,13 +183,12 @@ RedArgs red_args(const hj_handle *h, int mode, double tol, long long max_cycles)
 void geometry(const hj_handle *h, const TileKernelInfo *ki, bool classic, dim3 *grid, dim3 *block) {
     const int nx = h->d.nx, ny = h->d.ny;
     if (classic) {
-        if (h->d.dim == 2) {
-            *grid = dim3((nx + 31) / 32, (ny + 7) / 8);
-            *block = dim3(32, 8);
-        } else {
-            *grid = dim3((nx + 255) / 256, ny);
-            *block = dim3(256);
-        }
+        // grid-stride kernels over blocks of 32 x 8 (2D) or 256 (1D) points,
+        // bounded to 8 CTAs per SM so the residual is reduced once per CTA
+        const long long nb = h->d.dim == 2 ? (long long)((nx + 31) / 32) * ((ny + 7) / 8)
+                                           : (long long)((nx + 255) / 256) * ny;
+        *grid = dim3((unsigned)std::min<long long>(nb, 8LL * h->nsm));
+        *block = h->d.dim == 2 ? dim3(32, 8) : dim3(256);
         return;
     }
     if (h->d.dim == 2) {
@@ -739,9 +738,17 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     if (p.inner_stall < 0) return seterr(HJ_ERR_INVALID_ARG, "inner_stall must be >= 0");
     if (ir && p.method == HJ_METHOD_CLASSIC) return seterr(HJ_ERR_UNSUPPORTED, "refinement uses hierarchical cycles");
     if (p.check_every < 1) p.check_every = 1;
-    if (p.check_every > kHistCap / 2) p.check_every = kHistCap / 2;
+    if (p.check_every > 4096) p.check_every = 4096;
     p.check_every += p.check_every & 1;
     if (d.dim == 1) p.tile_y = 1;
+    if (p.autotune == 1 || p.autotune == 2) {
+        hj_params tp = p;
+        const int st = hj_autotune(&d, &tp, nullptr);
+        if (st != HJ_OK) return st;
+        p.tile_x = tp.tile_x;
+        p.tile_y = tp.tile_y;
+        p.k = tp.k;
+    }
 
     // diagonal dominance (Section 2.1): d_p >= |cW| + |cE| + |cS| + |cN|, d_p > 0
     const double off = fabs(d.cW) + fabs(d.cE) + (d.dim == 2 ? fabs(d.cS) + fabs(d.cN) : 0.0);

@@ -2,25 +2,28 @@
 // ||f|| and binary32 copy of r for refinement), the fused refinement update
 // u_{o+1} = u_o + d with the next residual, the adjoint gradient
 // dL/dsigma = -lambda * u, and the per-point inverse diagonal.
+#include <algorithm>
+
 #include "hj_internal.cuh"
 
 namespace hj {
 
 namespace {
 
-// (A u)_p - f_p evaluated as f - (d*u + cW*uW + cE*uE + cS*uS + cN*uN), every
-// operation rounded separately (binary64).
+// r_p = f_p - (A u)_p in binary64 as a fused multiply-add chain,
+// r = f - d u - cW uW - cE uE - cS uS - cN uN (binary64 throughput is low on
+// this part; the residual needs no particular rounding order, only binary64).
 template <bool D2>
 __device__ __forceinline__ double resid_exact(double f, double d, double u, double uW, double uE, double uS,
                                               double uN, double cW, double cE, double cS, double cN) {
-    double au = __dmul_rn(d, u);
-    au = __dadd_rn(au, __dmul_rn(cW, uW));
-    au = __dadd_rn(au, __dmul_rn(cE, uE));
+    double r = fma(-d, u, f);
+    r = fma(-cW, uW, r);
+    r = fma(-cE, uE, r);
     if (D2) {
-        au = __dadd_rn(au, __dmul_rn(cS, uS));
-        au = __dadd_rn(au, __dmul_rn(cN, uN));
+        r = fma(-cS, uS, r);
+        r = fma(-cN, uN, r);
     }
-    return __dsub_rn(f, au);
+    return r;
 }
 
 struct AuxArgs {
@@ -37,19 +40,28 @@ struct AuxArgs {
     RedArgs red;
 };
 
+// Grid-stride walk over blocks of points: 2D blocks of 32 x 8 points (one
+// thread each, x fastest), 1D blocks of 256 points of one row.  The grid is
+// bounded (a few CTAs per SM), so every CTA reduces its sums once.
 template <int D> struct AuxGeom;
 template <> struct AuxGeom<2> {
-    static __device__ __forceinline__ bool idx(const AuxArgs &a, int &i, int &j) {
-        i = 1 + blockIdx.x * 32 + threadIdx.x;
-        j = 1 + blockIdx.y * 8 + threadIdx.y;
-        return i <= a.nx && j <= a.ny;
+    static __device__ __forceinline__ long long nblocks(int nx, int ny) {
+        return (long long)((nx + 31) / 32) * ((ny + 7) / 8);
+    }
+    static __device__ __forceinline__ bool idx(int nx, int ny, long long b, int &i, int &j) {
+        const int bxn = (nx + 31) / 32;
+        i = 1 + (int)(b % bxn) * 32 + (int)threadIdx.x;
+        j = 1 + (int)(b / bxn) * 8 + (int)threadIdx.y;
+        return i <= nx && j <= ny;
     }
 };
 template <> struct AuxGeom<1> {
-    static __device__ __forceinline__ bool idx(const AuxArgs &a, int &i, int &j) {
-        i = 1 + blockIdx.x * 256 + threadIdx.x;
-        j = blockIdx.y;
-        return i <= a.nx;
+    static __device__ __forceinline__ long long nblocks(int nx, int ny) { return (long long)((nx + 255) / 256) * ny; }
+    static __device__ __forceinline__ bool idx(int nx, int ny, long long b, int &i, int &j) {
+        const int bxn = (nx + 255) / 256;
+        i = 1 + (int)(b % bxn) * 256 + (int)threadIdx.x;
+        j = (int)(b / bxn);
+        return i <= nx;
     }
 };
 
@@ -57,7 +69,9 @@ template <typename T, int D, bool WITH_F>
 __global__ void __launch_bounds__(256) residual_kernel(const AuxArgs a) {
     int i, j;
     double rr = 0.0, ff = 0.0;
-    if (AuxGeom<D>::idx(a, i, j)) {
+    const long long nb = AuxGeom<D>::nblocks(a.nx, a.ny);
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        if (!AuxGeom<D>::idx(a.nx, a.ny, b, i, j)) continue;
         const T *u = (const T *)a.u;
         const long long q = (long long)j * a.ld + i;
         const double fv = (double)((const T *)a.f)[q];
@@ -65,8 +79,8 @@ __global__ void __launch_bounds__(256) residual_kernel(const AuxArgs a) {
         const double r = resid_exact<D == 2>(fv, d, (double)u[q], (double)u[q - 1], (double)u[q + 1],
                                              D == 2 ? (double)u[q - a.ld] : 0.0,
                                              D == 2 ? (double)u[q + a.ld] : 0.0, a.cW, a.cE, a.cS, a.cN);
-        rr = r * r;
-        ff = fv * fv;
+        rr += r * r;
+        ff += fv * fv;
         if (a.r32) a.r32[(long long)j * a.ld2 + i] = (float)r;
     }
     if (WITH_F) {
@@ -93,7 +107,9 @@ template <typename DS, int D>
 __global__ void __launch_bounds__(256) update_residual_kernel(const AuxArgs a) {
     int i, j;
     double rr = 0.0;
-    if (AuxGeom<D>::idx(a, i, j)) {
+    const long long nb = AuxGeom<D>::nblocks(a.nx, a.ny);
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        if (!AuxGeom<D>::idx(a.nx, a.ny, b, i, j)) continue;
         const double *u = (const double *)a.u;
         const DS *dd = (const DS *)a.d;
         const long long q = (long long)j * a.ld + i;
@@ -110,7 +126,7 @@ __global__ void __launch_bounds__(256) update_residual_kernel(const AuxArgs a) {
         const double fv = ((const double *)a.f)[q];
         const double d = a.sigma ? __dadd_rn(a.dconst, a.sigma[q]) : a.dconst;
         const double r = resid_exact<D == 2>(fv, d, uc, uW, uE, uS, uN, a.cW, a.cE, a.cS, a.cN);
-        rr = r * r;
+        rr += r * r;
         a.r32[q2] = (float)r;
     }
     const double vals[1] = {rr};
@@ -121,10 +137,9 @@ template <typename T, int D>
 __global__ void __launch_bounds__(256) grad_sigma_kernel(const T *lam, const T *u, double *dsig, long long ld,
                                                          int nx, int ny) {
     int i, j;
-    AuxArgs g;
-    g.nx = nx;
-    g.ny = ny;
-    if (AuxGeom<D>::idx(g, i, j)) {
+    const long long nb = AuxGeom<D>::nblocks(nx, ny);
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        if (!AuxGeom<D>::idx(nx, ny, b, i, j)) continue;
         const long long q = (long long)j * ld + i;
         dsig[q] = -((double)lam[q] * (double)u[q]);
     }
@@ -138,8 +153,22 @@ __global__ void __launch_bounds__(256) make_dinv_kernel(const double *sigma, dou
     if (i < cols && j < rows) dinv[(long long)j * ld2 + i] = (T)__drcp_rn(__dadd_rn(dconst, sigma[(long long)j * ld + i]));
 }
 
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n < 1) n = 1;
+    }
+    return n;
+}
+
+// bounded grid: at most 8 CTAs of 256 threads per SM
 dim3 aux_grid(int dim, int nx, int ny) {
-    return dim == 2 ? dim3((nx + 31) / 32, (ny + 7) / 8) : dim3((nx + 255) / 256, ny);
+    const long long nb = dim == 2 ? (long long)((nx + 31) / 32) * ((ny + 7) / 8)
+                                  : (long long)((nx + 255) / 256) * ny;
+    return dim3((unsigned)std::min<long long>(nb, 8LL * sm_count()));
 }
 dim3 aux_block(int dim) { return dim == 2 ? dim3(32, 8) : dim3(256); }
 
@@ -214,5 +243,7 @@ int aux_max_blocks(int dim, int nx, int ny) {
     const dim3 g = aux_grid(dim, nx, ny);
     return (int)(g.x * g.y);
 }
+
+int aux_sm_count() { return sm_count(); }
 
 }  // namespace hj

@@ -52,9 +52,10 @@ int ensure_scratch(hj_handle *h, size_t bytes) {
 }
 
 int persist_capacity(hj_handle *h, const PersistKernelInfo *ki, bool sig, int *ctas) {
-    int occ = 0;
+    int occ = 0, occ1 = 0;
     CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ki->fn[sig], ki->threads, 0));
-    *ctas = occ * h->nsm;
+    CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, ki->one[sig], ki->threads, 0));
+    *ctas = std::min(occ, occ1) * h->nsm;
     return HJ_OK;
 }
 
@@ -136,7 +137,9 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
     if (cap < 1) return seterr(HJ_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
     const int grid = (int)std::min<long long>(nitems, cap);
     void *args[] = {&P};
-    CKR(cudaLaunchCooperativeKernel((const void *)ki->fn[sig], dim3(grid), dim3(ki->threads), args, 0, s));
+    // one problem: one grid barrier per cycle; several: two (reduce, then retire)
+    const void *fn = nprob == 1 ? (const void *)ki->one[sig] : (const void *)ki->fn[sig];
+    CKR(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(ki->threads), args, 0, s));
     CKR(cudaMemcpyAsync(hb + o_state, db + o_state, nprob * sizeof(ProbState), cudaMemcpyDeviceToHost, s));
     CKR(cudaMemcpyAsync(hb + o_bar, db + o_bar, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CKR(cudaEventRecord(h->ev, s));
@@ -209,8 +212,35 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
     if (nprob < 1 || !descs || !f || !u) return seterr(HJ_ERR_INVALID_ARG, "nprob, descs, f, u");
     if (!h->ir) return seterr(HJ_ERR_UNSUPPORTED, "batched solves use HJ_PREC_F32_IR or HJ_PREC_BF16CORR_IR");
     cudaStream_t s = (cudaStream_t)stream;
-    const hj_params &par = h->p;
+    hj_params par = h->p;
     const int fam = h->fam_inner;
+    for (int i = 0; i < nprob; ++i) CKS(validate_desc(descs[i], i));
+    // autotune: the tile shape (common to a launch) on the largest problem, then
+    // k per size class (largest side up to 128, 256, 384, beyond) on the largest
+    // problem of each class with that tile fixed
+    std::vector<int> kprob(nprob, par.k);
+    if (par.autotune == 1 || par.autotune == 2) {
+        int big = 0;
+        for (int i = 1; i < nprob; ++i)
+            if ((long long)descs[i].nx * descs[i].ny > (long long)descs[big].nx * descs[big].ny) big = i;
+        hj_params tp = par;
+        if (par.autotune == 1) CKS(hj_autotune(&descs[big], &tp, nullptr));
+        par.tile_x = tp.tile_x;
+        par.tile_y = tp.tile_y;
+        auto bucket = [&](int i) { const int m = std::max(descs[i].nx, descs[i].ny); return m <= 128 ? 0 : m <= 256 ? 1 : m <= 384 ? 2 : 3; };
+        for (int b = 0; b < 4; ++b) {
+            int rep = -1;
+            for (int i = 0; i < nprob; ++i)
+                if (bucket(i) == b && (rep < 0 || (long long)descs[i].nx * descs[i].ny > (long long)descs[rep].nx * descs[rep].ny))
+                    rep = i;
+            if (rep < 0) continue;
+            hj_params kp = par;
+            kp.autotune = 2;
+            CKS(hj_autotune(&descs[rep], &kp, nullptr));
+            for (int i = 0; i < nprob; ++i)
+                if (bucket(i) == b) kprob[i] = kp.k;
+        }
+    }
     const PersistKernelInfo *ki = find_persist(fam, 2, par.tile_x, par.tile_y);
     if (!ki) return seterr(HJ_ERR_UNSUPPORTED, "no persistent kernel for tile %dx%d", par.tile_x, par.tile_y);
     const bool bf16 = fam == FAM_BF16;
@@ -218,7 +248,6 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
     std::vector<BProb> P(nprob);
     size_t arena = 0, maxaux = 0;
     for (int i = 0; i < nprob; ++i) {
-        CKS(validate_desc(descs[i], i));
         if (!f[i] || !u[i] || ((uintptr_t)f[i] & 15) || ((uintptr_t)u[i] & 15))
             return seterr(HJ_ERR_INVALID_ARG, "problem %d: f/u NULL or not 16-byte aligned", i);
         BProb &b = P[i];
@@ -321,6 +350,7 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
             CKR(cudaMemsetAsync(b.dA, 0, b.nin * dsz, s));
             PersistProblem q;
             q.a = prob_args(b.d, par);
+            q.a.k = kprob[i];
             q.a.ld = b.ld_in;
             q.a.f = b.r32;
             q.a.uin = b.dA;
@@ -363,7 +393,7 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
         stats->history_len = 0;
         stats->tile_x = ki->tx;
         stats->tile_y = ki->ty;
-        stats->k = par.k;
+        stats->k = *std::max_element(kprob.begin(), kprob.end());
         stats->persistent = 1;
     }
     if (status == HJ_ERR_DIVERGED) return seterr(HJ_ERR_DIVERGED, "a problem of the batch diverged");

@@ -423,15 +423,18 @@ __global__ void __launch_bounds__(256) classic2d_kernel(const CycArgs a) {
     if constexpr (RES) {
         if (*(volatile int *)&a.red.ctl->done >= 0) return;
     }
-    const int i = 1 + blockIdx.x * 32 + threadIdx.x;
-    const int j = 1 + blockIdx.y * 8 + threadIdx.y;
     const long long ld = a.ld;
+    const int bxn = (a.nx + 31) / 32;
+    const long long nb = (long long)bxn * ((a.ny + 7) / 8);
+    const Coef<T> kc = make_coef<T>(a);
+    const S *__restrict__ uin = (const S *)a.uin;
     typedef typename std::conditional<EXACT, double, T>::type Acc;
     Acc acc = 0;
-    if (i <= a.nx && j <= a.ny) {
-        const S *__restrict__ uin = (const S *)a.uin;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int i = 1 + (int)(b % bxn) * 32 + threadIdx.x;
+        const int j = 1 + (int)(b / bxn) * 8 + threadIdx.y;
+        if (i > a.nx || j > a.ny) continue;
         const long long q = (long long)j * ld + i;
-        const Coef<T> kc = make_coef<T>(a);
         const T old = ld_s<S, T>(uin + q);
         const T W = ld_s<S, T>(uin + q - 1), E = ld_s<S, T>(uin + q + 1);
         const T Sv = ld_s<S, T>(uin + q - ld), Nv = ld_s<S, T>(uin + q + ld);
@@ -441,7 +444,7 @@ __global__ void __launch_bounds__(256) classic2d_kernel(const CycArgs a) {
         T res = 0;
         const T nv = point_update<T, EXACT, SIG, true, RES>(kc, g, iv, W, E, Sv, Nv, old, res);
         st_s<S, T>((S *)a.uout + q, nv);
-        acc = (Acc)res * (Acc)res;
+        acc += (Acc)res * (Acc)res;
     }
     if constexpr (RES) reduce_grid_acc(a.red, acc);
 }
@@ -451,14 +454,17 @@ __global__ void __launch_bounds__(256) classic1d_kernel(const CycArgs a) {
     if constexpr (RES) {
         if (*(volatile int *)&a.red.ctl->done >= 0) return;
     }
-    const int i = 1 + blockIdx.x * 256 + threadIdx.x;
-    const int row = blockIdx.y;
+    const int bxn = (a.nx + 255) / 256;
+    const long long nb = (long long)bxn * a.ny;
+    const Coef<T> kc = make_coef<T>(a);
+    const S *__restrict__ uin = (const S *)a.uin;
     typedef typename std::conditional<EXACT, double, T>::type Acc;
     Acc acc = 0;
-    if (i <= a.nx) {
-        const S *__restrict__ uin = (const S *)a.uin;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int i = 1 + (int)(b % bxn) * 256 + threadIdx.x;
+        const int row = (int)(b / bxn);
+        if (i > a.nx) continue;
         const long long q = (long long)row * a.ld + i;
-        const Coef<T> kc = make_coef<T>(a);
         const T old = ld_s<S, T>(uin + q);
         const T W = ld_s<S, T>(uin + q - 1), E = ld_s<S, T>(uin + q + 1);
         const T fv = __ldg((const T *)a.f + q);
@@ -467,7 +473,7 @@ __global__ void __launch_bounds__(256) classic1d_kernel(const CycArgs a) {
         T res = 0;
         const T nv = point_update<T, EXACT, SIG, false, RES>(kc, g, iv, W, E, (T)0, (T)0, old, res);
         st_s<S, T>((S *)a.uout + q, nv);
-        acc = (Acc)res * (Acc)res;
+        acc += (Acc)res * (Acc)res;
     }
     if constexpr (RES) reduce_grid_acc(a.red, acc);
 }

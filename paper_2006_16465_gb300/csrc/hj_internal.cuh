@@ -31,7 +31,7 @@ struct Ctl {
     long long mark_cycle;
 };
 
-constexpr int kHistCap = 8192;     // device ring of per-cycle ||r_c||^2 (power of two)
+constexpr int kHistCap = 1 << 17;  // device ring of per-cycle ||r_c||^2 (power of two)
 constexpr int kGroup = 256;        // CTAs per first-level reduction group
 
 enum RedMode { RED_CYCLE = 0, RED_STORE = 1 };
@@ -283,5 +283,6 @@ cudaError_t launch_update_residual_ex(int dim, const double *f, const double *ui
 cudaError_t launch_grad_sigma_ex(int dim, int user_f64, const void *lam, const void *u, double *dsig, long long ld,
                                  int nx, int ny, cudaStream_t s);
 int aux_max_blocks(int dim, int nx, int ny);
+int aux_sm_count();
 
 }  // namespace hj

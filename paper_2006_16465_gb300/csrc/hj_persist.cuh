@@ -218,18 +218,140 @@ __global__ void __launch_bounds__(32 * WPB) persist1d_kernel(const PersistArgs P
     }
 }
 
+// Single-problem variant with ONE grid barrier per cycle: after the barrier
+// every CTA sums all partials of the cycle in the same fixed order, so every
+// CTA reaches the same stopping decision on its own; CTA 0 publishes the
+// state and the residual history.  Partials are double-buffered by cycle
+// parity, so a CTA that runs ahead cannot overwrite values another CTA is
+// still summing.
+struct OneState {
+    int done, status;
+    long long cycle;
+    double res2_0, res2_last, mark;
+    long long mark_c;
+};
+
+__device__ __forceinline__ bool one_decide(const PersistArgs &P, OneState &ls, int parity) {
+    const int lane = threadIdx.x & 31;
+    __shared__ OneState s_ls;
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int i = lane; i < P.nitems; i += 32) s += __ldcg(&P.partial[(size_t)parity * P.nitems + i]);
+        s = warp_sum(s);
+        if (lane == 0) {
+            const RedArgs &r = P.probs[0].red;
+            const double res2 = s * r.scale;
+            const long long c = ls.cycle;
+            if (blockIdx.x == 0 && r.hist) r.hist[c & (kHistCap - 1)] = res2;
+            if (c == 0) ls.res2_0 = res2;
+            const double r0 = sqrt(ls.res2_0), rc = sqrt(res2);
+            ls.res2_last = res2;
+            if (!isfinite(rc)) {
+                ls.status = HJ_ERR_DIVERGED;
+                ls.done = (int)c;
+            } else if (rc <= r.tol * r0) {
+                ls.done = (int)c;
+            } else if (stalled(r, c, res2, &ls.mark, &ls.mark_c)) {
+                ls.done = (int)c;
+            } else if (c + 1 >= r.max_cycles) {
+                ls.status = HJ_ERR_NOT_CONVERGED;
+                ls.done = (int)(c + 1);
+            }
+            ls.cycle = c + 1;
+            s_ls = ls;
+            if (blockIdx.x == 0 && ls.done >= 0) {
+                ProbState *st = P.state;
+                st->status = ls.status;
+                st->cycle = ls.cycle;
+                st->res2_0 = ls.res2_0;
+                st->res2_last = ls.res2_last;
+                __threadfence();
+                st->done = ls.done;
+            }
+        }
+    }
+    __syncthreads();
+    ls = s_ls;
+    return ls.done >= 0;
+}
+
+template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG>
+__global__ void __launch_bounds__(32 * NW) persist2d_one_kernel(const PersistArgs P) {
+    constexpr int TX = 32 * C, TY = R * NW;
+    constexpr int XB = NW > 1 ? 2 * NW * 2 * TX : 1;
+    __shared__ T xbuf[XB];
+    OneState ls{-1, HJ_OK, 0, 0.0, 0.0, 0.0, 0};
+    const int tx = P.prob_tiles_x[0];
+    for (long long it = 0; it < P.max_iters; ++it) {
+        const int parity = (int)(it & 1);
+        CycArgs a = P.probs[0];
+        if (ls.cycle & 1) {
+            const void *t = a.uin;
+            a.uin = a.uout;
+            a.uout = const_cast<void *>(t);
+        }
+        for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
+            const int x0 = 1 + (item % tx) * TX, y0 = 1 + (item / tx) * TY;
+            typename std::conditional<EXACT, double, T>::type acc;
+            if (x0 + TX - 1 <= a.nx && y0 + TY - 1 <= a.ny)
+                acc = tile2d<S, T, C, R, NW, EXACT, SIG, true, false>(a, x0, y0, xbuf);
+            else
+                acc = tile2d<S, T, C, R, NW, EXACT, SIG, true, true>(a, x0, y0, xbuf);
+            const double s = cta_sum(acc);
+            if (threadIdx.x == 0) P.partial[(size_t)parity * P.nitems + item] = s;
+        }
+        if ((int)blockIdx.x == P.skip_barrier_cta) return;
+        if (!grid_barrier(P)) return;
+        if (one_decide(P, ls, parity)) return;
+    }
+}
+
+template <typename S, typename T, int C, int WPB, bool EXACT, bool SIG>
+__global__ void __launch_bounds__(32 * WPB) persist1d_one_kernel(const PersistArgs P) {
+    constexpr int TX = 32 * C;
+    OneState ls{-1, HJ_OK, 0, 0.0, 0.0, 0.0, 0};
+    const int bxn = P.prob_tiles_x[0];
+    for (long long it = 0; it < P.max_iters; ++it) {
+        const int parity = (int)(it & 1);
+        CycArgs a = P.probs[0];
+        if (ls.cycle & 1) {
+            const void *t = a.uin;
+            a.uin = a.uout;
+            a.uout = const_cast<void *>(t);
+        }
+        for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
+            const int w = threadIdx.x >> 5;
+            const int x0 = 1 + ((item % bxn) * WPB + w) * TX;
+            const int row = item / bxn;
+            typename std::conditional<EXACT, double, T>::type acc = 0;
+            if (x0 <= a.nx) {
+                if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, EXACT, SIG, true, false>(a, x0, row);
+                else acc = tile1d<S, T, C, EXACT, SIG, true, true>(a, x0, row);
+            }
+            const double s = cta_sum(acc);
+            if (threadIdx.x == 0) P.partial[(size_t)parity * P.nitems + item] = s;
+        }
+        if ((int)blockIdx.x == P.skip_barrier_cta) return;
+        if (!grid_barrier(P)) return;
+        if (one_decide(P, ls, parity)) return;
+    }
+}
+
 typedef void (*PersistKernel)(PersistArgs);
 
 struct PersistKernelInfo {
     int dim, tx, ty, threads, tiles_per_cta;
-    PersistKernel fn[2];   // [sig]
+    PersistKernel fn[2];      // [sig]  many problems, two barriers per cycle
+    PersistKernel one[2];     // [sig]  one problem, one barrier per cycle
 };
 
 }  // namespace hj
 
 #define HJ_KP2D(S, T, C, R, NW, EX) \
     {2, 32 * (C), (R) * (NW), 32 * (NW), 1, \
-     {hj::persist2d_kernel<S, T, C, R, NW, EX, false>, hj::persist2d_kernel<S, T, C, R, NW, EX, true>}}
+     {hj::persist2d_kernel<S, T, C, R, NW, EX, false>, hj::persist2d_kernel<S, T, C, R, NW, EX, true>}, \
+     {hj::persist2d_one_kernel<S, T, C, R, NW, EX, false>, hj::persist2d_one_kernel<S, T, C, R, NW, EX, true>}}
 #define HJ_KP1D(S, T, C, WPB, EX) \
     {1, 32 * (C), 1, 32 * (WPB), (WPB), \
-     {hj::persist1d_kernel<S, T, C, WPB, EX, false>, hj::persist1d_kernel<S, T, C, WPB, EX, true>}}
+     {hj::persist1d_kernel<S, T, C, WPB, EX, false>, hj::persist1d_kernel<S, T, C, WPB, EX, true>}, \
+     {hj::persist1d_one_kernel<S, T, C, WPB, EX, false>, hj::persist1d_one_kernel<S, T, C, WPB, EX, true>}}
