@@ -222,6 +222,75 @@ def time_to_residual(torch, hj, W, tol=1e-8):
     return out
 
 
+def time_1d(torch, hj, W):
+    """cfg1: 1D Poisson N = 512, f = sum of 8 sine modes, binary64, to 1e-6:
+    hierarchical (128-point subdomains, k = 32) vs classic."""
+    q = W.poisson1d_sine(512, seed=0)
+    f = hj.grid_from(q.f, 1, torch.float64)
+    out = {}
+    for name, kw in [("hier_f64", dict(tile_x=128, k=32)), ("classic_f64", dict(method="classic"))]:
+        s = hj.Solver(q.st, precision="f64", tol=1e-6, check_every=512, **kw)
+        u = hj.grid_from(q.u0, 1, torch.float64)
+        s.solve(f, u.clone())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = s.solve(f, u)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "cycles": r["cycles"], "status": r["status"]}
+        s.close()
+    out["speedup"] = out["classic_f64"]["seconds"] / out["hier_f64"]["seconds"]
+    return out
+
+
+def time_batched(torch, hj, W):
+    """cfg4: 256 screened problems, sides from {64..512}, binary32 inner cycles
+    with binary64 refinement to 1e-8, one persistent launch per inner phase,
+    autotuned tile and per-size-class k (second call timed: tuning is cached)."""
+    probs = W.batched_screened(256, seed=3)
+    s = hj.Solver(probs[0].st, tile_x=32, tile_y=32, k=16, precision="f32_ir", tol=1e-8, autotune=1)
+    fs = [hj.grid_from(q.f, 2, torch.float64) for q in probs]
+    descs = [hj.make_desc(2, q.st.nx, q.st.ny, f.shape[1], q.st.cW, q.st.cE, q.st.cS, q.st.cN, q.st.cD,
+                          q.st.sigma_const) for q, f in zip(probs, fs)]
+    res = {}
+    for rep in range(2):
+        us = [hj.grid_from(q.u0, 2, torch.float64) for q in probs]
+        st = hj.hj_stats()
+        cyc = (hj.C.c_longlong * len(probs))()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        code = hj.hj_solve_batched(s.h, descs, [f.data_ptr() for f in fs], [u.data_ptr() for u in us], 0, st, cyc)
+        torch.cuda.synchronize()
+        res = {"seconds": time.perf_counter() - t0, "status": code, "worst_rel_residual": st.rel_final,
+               "outer_steps": st.outer_steps, "inner_cycles_total": st.inner_cycles,
+               "inner_cycles_max": max(cyc), "unknowns": sum(q.st.nx * q.st.ny for q in probs),
+               "tile": [st.tile_x, st.tile_y]}
+    s.close()
+    return res
+
+
+def time_differentiation(torch, hj, W):
+    """cfg5: screened Poisson 1024^2, Fourier sigma field, 16 RHS, loss
+    0.5 ||u - u*||^2; forward solves and implicit-adjoint backward (binary32
+    inner cycles, binary64 refinement to 1e-10)."""
+    from paper_2006_16465_gb300.autograd import solve_screened
+    st, fs, ustar = W.differentiation_problem(1024, 16, seed=7)
+    f = torch.stack([hj.grid_from(x, 2, torch.float64) for x in fs]).requires_grad_(True)
+    sigma = hj.grid_from(st.sigma, 2, torch.float64).requires_grad_(True)
+    target = hj.grid_from(ustar, 2, torch.float64)
+    params = dict(tile_x=64, tile_y=64, k=32, precision="f32_ir", tol=1e-10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u = solve_screened(f, sigma, st, **params)
+    loss = 0.5 * ((u - target)[:, 1:-1, 1:1025] ** 2).sum()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"forward_seconds": t1 - t0, "backward_seconds": t2 - t1, "rhs": 16, "grid": [1024, 1024],
+            "loss": float(loss), "grad_sigma_norm": float(sigma.grad.norm()), "grad_f_norm": float(f.grad.norm())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,14 +381,20 @@ def main():
         cl.close()
         extras["hier_global_cycle_rate_gdofs"] = n * n / (per_launch_ms / 1e3) / 1e9
         extras["time_to_1e-8_512"] = time_to_residual(torch, hj, W)
+        extras["cfg1_1d_to_1e-6"] = time_1d(torch, hj, W)
+        extras["cfg4_batched_256_to_1e-8"] = time_batched(torch, hj, W)
+        extras["cfg5_differentiation_1024"] = time_differentiation(torch, hj, W)
     launches += args.steps  # one residual launch per step (the final iterate is not converged: tol = 0)
+    ntiles = ((n + 31) // 32) ** 2
+    pipelined = ntiles >= 8 * torch.cuda.get_device_properties(local).multi_processor_count
+    kernel_name = ("ppc2d_kernel" if pipelined else "hier2d_kernel") + "<float, 32x32 tiles, fused residual>"
     line = {"metric": METRIC, "value": glups, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _config(args, world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None,
-                         "kernel": "hier2d_kernel<float,32x32>", "peak_kind": peak_kind},
+                         "kernel": kernel_name, "peak_kind": peak_kind},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
     line.update(extras)
     if rank == 0 and not args.no_extras:
