@@ -143,6 +143,11 @@ typedef struct {
     int pipeline;         /* 2D cycles: 1 = TMA-pipelined kernel (CTAs walk tile
                              lists, next tile staged while the current one
                              sweeps), 0 = one CTA per tile, -1 = automatic      */
+    int tile_threads;     /* threads per subdomain (one warp per band of rows);
+                             0 = the default for the tile shape; the built
+                             combinations are listed by hj_tile_variants()      */
+    int pipeline_stages;  /* TMA-pipelined kernel: tiles in flight per CTA (2 or
+                             3; 0 = default 2)                                 */
     int inner_stall;      /* refinement: an inner solve also stops when ||r|| has
                              changed by <= 1e-3 (relative) over this many cycles,
                              i.e. the correction has reached the fixed point its
@@ -163,13 +168,15 @@ typedef struct {
     long long history_len;    /* entries written                                 */
     double wall_ms;           /* host wall time of the call                      */
     int tile_x, tile_y, k;    /* configuration actually used                     */
+    int tile_threads;         /* threads per subdomain actually used             */
     int persistent;           /* 1 if the persistent path ran                    */
 } hj_stats;
 
 /* Fill p with defaults: hierarchical, 32 x 32 tiles, k = 16, HJ_PREC_F64,
  * check_every = 64, max_cycles = 10^7, tol = 1e-6, fixed_cycles = 0,
  * inner_tol = 1e-4, inner_max_cycles = 10^6, max_outer = 60, persistent = -1,
- * autotune = 0, pipeline = -1, inner_stall = 32. */
+ * autotune = 0, pipeline = -1, tile_threads = 0, pipeline_stages = 0,
+ * inner_stall = 32. */
 HJ_API void hj_default_params(hj_params *p);
 
 /* Create a solver for one problem shape.  Validates the descriptor and
@@ -234,6 +241,10 @@ HJ_API const char *hj_last_error(void);
  * params->autotune is 1; params->autotune = 2 keeps tile_x, tile_y and tunes
  * k only. */
 HJ_API int hj_autotune(const hj_desc *desc, hj_params *params, double *predicted_ms);
+
+/* Built (tile_x, tile_y, threads) combinations for (dim, precision): writes
+ * up to cap triples into txt[3*i .. 3*i+2] and returns how many exist. */
+HJ_API int hj_tile_variants(int dim, int precision, int *txt, int cap);
 
 /* Tile shapes built for (dim, precision): writes up to cap (tile_x, tile_y)
  * pairs into xy[2*i], xy[2*i+1] and returns how many exist. */

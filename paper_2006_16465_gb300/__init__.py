@@ -48,7 +48,8 @@ class hj_params(C.Structure):
                 ("precision", C.c_int), ("check_every", C.c_int), ("max_cycles", C.c_longlong),
                 ("tol", C.c_double), ("fixed_cycles", C.c_longlong), ("inner_tol", C.c_double),
                 ("inner_max_cycles", C.c_longlong), ("max_outer", C.c_int), ("persistent", C.c_int),
-                ("autotune", C.c_int), ("pipeline", C.c_int), ("inner_stall", C.c_int)]
+                ("autotune", C.c_int), ("pipeline", C.c_int), ("tile_threads", C.c_int),
+                ("pipeline_stages", C.c_int), ("inner_stall", C.c_int)]
 
 
 class hj_stats(C.Structure):
@@ -57,7 +58,7 @@ class hj_stats(C.Structure):
                 ("res_final", C.c_double), ("rel_final", C.c_double),
                 ("history", C.POINTER(C.c_double)), ("history_cap", C.c_longlong),
                 ("history_len", C.c_longlong), ("wall_ms", C.c_double), ("tile_x", C.c_int),
-                ("tile_y", C.c_int), ("k", C.c_int), ("persistent", C.c_int)]
+                ("tile_y", C.c_int), ("k", C.c_int), ("tile_threads", C.c_int), ("persistent", C.c_int)]
 
 
 class HJError(RuntimeError):
@@ -103,9 +104,10 @@ def lib():
         L.hj_last_error.argtypes = []
         L.hj_last_error.restype = C.c_char_p
         L.hj_tile_shapes.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]
+        L.hj_tile_variants.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]
         L.hj_autotune.argtypes = [C.POINTER(hj_desc), C.POINTER(hj_params), C.POINTER(C.c_double)]
         for name in ("hj_create", "hj_solve", "hj_residual", "hj_solve_adjoint", "hj_solve_batched",
-                     "hj_tile_shapes", "hj_autotune"):
+                     "hj_tile_shapes", "hj_tile_variants", "hj_autotune"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -181,6 +183,13 @@ def hj_autotune(desc: hj_desc, params: hj_params):
     if st != HJ_OK:
         raise HJError(st, "hj_autotune")
     return ms.value
+
+
+def hj_tile_variants(dim: int, precision: int):
+    n = lib().hj_tile_variants(dim, precision, None, 0)
+    buf = (C.c_int * (3 * n))()
+    lib().hj_tile_variants(dim, precision, buf, n)
+    return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(n)]
 
 
 def hj_tile_shapes(dim: int, precision: int):

@@ -56,11 +56,12 @@ const PersistKernelInfo *hj::family_persist(int fam, int *n) {
     default: return persist_kernels_bf16(n);
     }
 }
-const PersistKernelInfo *hj::find_persist(int fam, int dim, int tx, int ty) {
+const PersistKernelInfo *hj::find_persist(int fam, int dim, int tx, int ty, int threads) {
     int n = 0;
     const PersistKernelInfo *k = family_persist(fam, &n);
     for (int i = 0; i < n; ++i)
-        if (k[i].dim == dim && k[i].tx == tx && (dim == 1 || k[i].ty == ty)) return &k[i];
+        if (k[i].dim == dim && k[i].tx == tx && (dim == 1 || k[i].ty == ty) && (!threads || k[i].threads == threads))
+            return &k[i];
     return nullptr;
 }
 
@@ -81,11 +82,14 @@ const PpcKernelInfo *family_ppc(int fam, int *n) {
     default: return ppc_kernels_bf16(n);
     }
 }
-const PpcKernelInfo *find_ppc(int fam, int tx, int ty) {
+// threads / stages 0 = the first (default) entry for the shape
+const PpcKernelInfo *find_ppc(int fam, int tx, int ty, int threads, int stages) {
     int n = 0;
     const PpcKernelInfo *k = family_ppc(fam, &n);
     for (int i = 0; i < n; ++i)
-        if (k[i].tx == tx && k[i].ty == ty) return &k[i];
+        if (k[i].tx == tx && k[i].ty == ty && (!threads || k[i].threads == threads) &&
+            (!stages || k[i].stages == stages))
+            return &k[i];
     return nullptr;
 }
 
@@ -119,11 +123,12 @@ bool make_tmap(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int esz
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-const TileKernelInfo *find_tile(int fam, int dim, int tx, int ty) {
+const TileKernelInfo *find_tile(int fam, int dim, int tx, int ty, int threads = 0) {
     int n = 0;
     const TileKernelInfo *k = family_tiles(fam, &n);
     for (int i = 0; i < n; ++i)
-        if (k[i].dim == dim && k[i].tx == tx && (dim == 1 || k[i].ty == ty)) return &k[i];
+        if (k[i].dim == dim && k[i].tx == tx && (dim == 1 || k[i].ty == ty) && (!threads || k[i].threads == threads))
+            return &k[i];
     return nullptr;
 }
 
@@ -430,7 +435,7 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, 
 int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int fam, bool classic, bool sig,
             const CycArgs &base, void *b0, void *b1, double tol, long long max_cycles, long long fixed, cudaStream_t s,
             RunOut *ro, double *hist_out, long long hist_cap, long long *hist_len, int *used_persistent) {
-    const PersistKernelInfo *pk = classic ? nullptr : find_persist(fam, h->d.dim, ki->tx, ki->ty);
+    const PersistKernelInfo *pk = classic ? nullptr : find_persist(fam, h->d.dim, ki->tx, ki->ty, ki->threads);
     dim3 g, bb;
     geometry(h, ki, classic, &g, &bb);
     bool use = false;
@@ -630,6 +635,7 @@ void fill_stats_config(const hj_handle *h, hj_stats *st, double t0) {
     st->tile_x = h->p.tile_x;
     st->tile_y = h->d.dim == 2 ? h->p.tile_y : 1;
     st->k = h->p.k;
+    st->tile_threads = h->ir ? h->k_inner->threads : h->k_outer ? h->k_outer->threads : 0;
 }
 
 }  // namespace
@@ -677,12 +683,31 @@ const char *hj_error_string(int s) {
 
 const char *hj_last_error(void) { return g_err; }
 
+int hj_tile_variants(int dim, int precision, int *txt, int cap) {
+    const int fam = precision == HJ_PREC_F64 ? FAM_F64 : precision == HJ_PREC_BF16CORR_IR ? FAM_BF16 : FAM_F32;
+    int n = 0, m = 0;
+    const TileKernelInfo *k = family_tiles(fam, &n);
+    for (int i = 0; i < n; ++i) {
+        if (k[i].dim != dim) continue;
+        if (txt && m < cap) {
+            txt[3 * m] = k[i].tx;
+            txt[3 * m + 1] = k[i].ty;
+            txt[3 * m + 2] = k[i].threads;
+        }
+        ++m;
+    }
+    return m;
+}
+
 int hj_tile_shapes(int dim, int precision, int *xy, int cap) {
     const int fam = precision == HJ_PREC_F64 ? FAM_F64 : precision == HJ_PREC_BF16CORR_IR ? FAM_BF16 : FAM_F32;
     int n = 0, m = 0;
     const TileKernelInfo *k = family_tiles(fam, &n);
     for (int i = 0; i < n; ++i) {
         if (k[i].dim != dim) continue;
+        bool dup = false;
+        for (int j = 0; j < i; ++j) dup |= k[j].dim == dim && k[j].tx == k[i].tx && k[j].ty == k[i].ty;
+        if (dup) continue;
         if (xy && m < cap) {
             xy[2 * m] = k[i].tx;
             xy[2 * m + 1] = k[i].ty;
@@ -747,6 +772,7 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
         if (st != HJ_OK) return st;
         p.tile_x = tp.tile_x;
         p.tile_y = tp.tile_y;
+        p.tile_threads = tp.tile_threads;
         p.k = tp.k;
     }
 
@@ -796,15 +822,19 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
 
     h->ld_in = ((long long)d.nx + 2 + 31) / 32 * 32;
     if (ir) {
-        h->k_inner = find_tile(h->fam_inner, d.dim, p.tile_x, p.tile_y);
-        if (!h->k_inner) HJ_FAIL(HJ_ERR_UNSUPPORTED, "tile %dx%d not built for this precision", p.tile_x, p.tile_y);
-        if (d.dim == 2) h->p_inner = find_ppc(h->fam_inner, p.tile_x, p.tile_y);
+        h->k_inner = find_tile(h->fam_inner, d.dim, p.tile_x, p.tile_y, p.tile_threads);
+        if (!h->k_inner)
+            HJ_FAIL(HJ_ERR_UNSUPPORTED, "tile %dx%d (%d threads) not built for this precision", p.tile_x, p.tile_y,
+                    p.tile_threads);
+        if (d.dim == 2) h->p_inner = find_ppc(h->fam_inner, p.tile_x, p.tile_y, h->k_inner->threads, p.pipeline_stages);
     } else if (p.method == HJ_METHOD_CLASSIC) {
         h->k_classic = family_classic(h->fam_outer, d.dim);
     } else {
-        h->k_outer = find_tile(h->fam_outer, d.dim, p.tile_x, p.tile_y);
-        if (!h->k_outer) HJ_FAIL(HJ_ERR_UNSUPPORTED, "tile %dx%d not built for this precision", p.tile_x, p.tile_y);
-        if (d.dim == 2) h->p_outer = find_ppc(h->fam_outer, p.tile_x, p.tile_y);
+        h->k_outer = find_tile(h->fam_outer, d.dim, p.tile_x, p.tile_y, p.tile_threads);
+        if (!h->k_outer)
+            HJ_FAIL(HJ_ERR_UNSUPPORTED, "tile %dx%d (%d threads) not built for this precision", p.tile_x, p.tile_y,
+                    p.tile_threads);
+        if (d.dim == 2) h->p_outer = find_ppc(h->fam_outer, p.tile_x, p.tile_y, h->k_outer->threads, p.pipeline_stages);
     }
     if (p.pipeline == 1 && d.dim == 2 && p.method == HJ_METHOD_HIER && !(ir ? h->p_inner : h->p_outer))
         HJ_FAIL(HJ_ERR_UNSUPPORTED, "no pipelined kernel for tile %dx%d", p.tile_x, p.tile_y);

@@ -13,7 +13,7 @@
 //   * predicted time to the tolerance: ln(tol) / ln(rho) * t.
 // The candidate with the smallest prediction wins.  Results are cached per
 // process and, if HJ_AUTOTUNE_CACHE names a file, in that file (one line per
-// key: "key tile_x tile_y k").
+// key: "key tile_x tile_y threads k").
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -68,17 +68,17 @@ void load_cache_file() {
     FILE *fp = fopen(path, "r");
     if (!fp) return;
     char key[512];
-    int tx, ty, k;
-    while (fscanf(fp, "%511s %d %d %d", key, &tx, &ty, &k) == 4) g_cache[key] = {tx, ty, k};
+    int tx, ty, th, k;
+    while (fscanf(fp, "%511s %d %d %d %d", key, &tx, &ty, &th, &k) == 5) g_cache[key] = {tx, ty, th, k};
     fclose(fp);
 }
 
-void store_cache_file(const std::string &key, int tx, int ty, int k) {
+void store_cache_file(const std::string &key, int tx, int ty, int th, int k) {
     const char *path = getenv("HJ_AUTOTUNE_CACHE");
     if (!path || !*path) return;
     FILE *fp = fopen(path, "a");
     if (!fp) return;
-    fprintf(fp, "%s %d %d %d\n", key.c_str(), tx, ty, k);
+    fprintf(fp, "%s %d %d %d %d\n", key.c_str(), tx, ty, th, k);
     fclose(fp);
 }
 
@@ -93,7 +93,7 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
     std::string key = make_key(d, params->precision, tol);
     if (params->autotune == 2) {
         char extra[64];
-        snprintf(extra, sizeof(extra), "_fixed%dx%d", params->tile_x, params->tile_y);
+        snprintf(extra, sizeof(extra), "_fixed%dx%dt%d", params->tile_x, params->tile_y, params->tile_threads);
         key += extra;
     }
     {
@@ -103,7 +103,8 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
         if (it != g_cache.end()) {
             params->tile_x = it->second[0];
             params->tile_y = it->second[1];
-            params->k = it->second[2];
+            params->tile_threads = it->second[2];
+            params->k = it->second[3];
             if (predicted_ms) *predicted_ms = -1.0;
             return HJ_OK;
         }
@@ -142,21 +143,23 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
         cleanup();
         return seterr(HJ_ERR_CUDA, "autotune memset");
     }
-    // candidate tile shapes
-    int xy[64];
-    const int nshape = std::min(32, hj_tile_shapes(d.dim, prec, xy, 32));
+    // candidate (tile shape, threads per tile) variants
+    int xy[3 * 64];
+    const int nshape = std::min(64, hj_tile_variants(d.dim, prec, xy, 64));
     const int ks[] = {4, 8, 16, 32, 64};
     const int C = 24;
     double best = INFINITY;
-    int btx = params->tile_x, bty = params->tile_y, bk = params->k;
+    int btx = params->tile_x, bty = params->tile_y, bth = params->tile_threads, bk = params->k;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     double hist[C + 1];
     for (int si = 0; si < nshape; ++si) {
-        const int tx = xy[2 * si], ty = xy[2 * si + 1];
-        // autotune == 2: the tile shape is fixed by the caller, tune k only
-        if (params->autotune == 2 && (tx != params->tile_x || (d.dim == 2 && ty != params->tile_y))) continue;
+        const int tx = xy[3 * si], ty = xy[3 * si + 1], th = xy[3 * si + 2];
+        // autotune == 2: the tile variant is fixed by the caller, tune k only
+        if (params->autotune == 2 && (tx != params->tile_x || (d.dim == 2 && ty != params->tile_y) ||
+                                      (params->tile_threads && th != params->tile_threads)))
+            continue;
         // skip shapes far larger than the grid
         if (tx > 2 * std::max(d.nx, 32) || (d.dim == 2 && ty > 2 * std::max(d.ny, 8))) continue;
         for (int k : ks) {
@@ -164,6 +167,8 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
             hj_default_params(&tp);
             tp.tile_x = tx;
             tp.tile_y = ty;
+            tp.tile_threads = th;
+            tp.pipeline_stages = params->pipeline_stages;
             tp.k = k;
             tp.precision = prec;
             tp.tol = 0.0;
@@ -206,6 +211,7 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
                 best = pred;
                 btx = tx;
                 bty = ty;
+                bth = th;
                 bk = k;
             }
         }
@@ -217,12 +223,13 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
     if (!std::isfinite(best)) return seterr(HJ_ERR_UNSUPPORTED, "autotune found no usable candidate");
     params->tile_x = btx;
     params->tile_y = d.dim == 2 ? bty : 1;
+    params->tile_threads = bth;
     params->k = bk;
     if (predicted_ms) *predicted_ms = best;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        g_cache[key] = {btx, bty, bk};
-        store_cache_file(key, btx, bty, bk);
+        g_cache[key] = {btx, bty, bth, bk};
+        store_cache_file(key, btx, bty, bth, bk);
     }
     return HJ_OK;
 }

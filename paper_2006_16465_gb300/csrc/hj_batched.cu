@@ -227,6 +227,7 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
         if (par.autotune == 1) CKS(hj_autotune(&descs[big], &tp, nullptr));
         par.tile_x = tp.tile_x;
         par.tile_y = tp.tile_y;
+        par.tile_threads = tp.tile_threads;
         auto bucket = [&](int i) { const int m = std::max(descs[i].nx, descs[i].ny); return m <= 128 ? 0 : m <= 256 ? 1 : m <= 384 ? 2 : 3; };
         for (int b = 0; b < 4; ++b) {
             int rep = -1;
@@ -241,7 +242,7 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
                 if (bucket(i) == b) kprob[i] = kp.k;
         }
     }
-    const PersistKernelInfo *ki = find_persist(fam, 2, par.tile_x, par.tile_y);
+    const PersistKernelInfo *ki = find_persist(fam, 2, par.tile_x, par.tile_y, par.tile_threads);
     if (!ki) return seterr(HJ_ERR_UNSUPPORTED, "no persistent kernel for tile %dx%d", par.tile_x, par.tile_y);
     const bool bf16 = fam == FAM_BF16;
     const size_t dsz = bf16 ? 2 : 4;
@@ -393,6 +394,7 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
         stats->history_len = 0;
         stats->tile_x = ki->tx;
         stats->tile_y = ki->ty;
+        stats->tile_threads = ki->threads;
         stats->k = *std::max_element(kprob.begin(), kprob.end());
         stats->persistent = 1;
     }

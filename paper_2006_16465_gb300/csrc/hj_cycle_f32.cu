@@ -6,6 +6,7 @@ namespace hj {
 
 static const TileKernelInfo k_tiles[] = {
     HJ_K2D(float, float, 1, 32, 1, false),    // 32 x 32
+    HJ_K2D(float, float, 1, 16, 2, false),    // 32 x 32, two warps
     HJ_K2D(float, float, 1, 16, 1, false),    // 32 x 16
     HJ_K2D(float, float, 1, 8, 1, false),     // 32 x 8
     HJ_K2D(float, float, 1, 32, 2, false),    // 32 x 64
@@ -24,6 +25,9 @@ const TileKernelInfo *classic_kernels_f32(int *n) { *n = 2; return k_classic; }
 
 static const PpcKernelInfo k_ppc[] = {
     HJ_KPPC(float, float, 1, 32, 1, false, 2),   // 32 x 32
+    HJ_KPPC(float, float, 1, 16, 2, false, 2),   // 32 x 32, two warps
+    HJ_KPPC(float, float, 1, 32, 1, false, 3),   // 32 x 32, three stages
+    HJ_KPPC(float, float, 1, 16, 2, false, 3),   // 32 x 32, two warps, three stages
     HJ_KPPC(float, float, 1, 16, 1, false, 2),   // 32 x 16
     HJ_KPPC(float, float, 1, 8, 1, false, 2),   // 32 x 8
     HJ_KPPC(float, float, 1, 32, 2, false, 2),   // 32 x 64
@@ -35,6 +39,7 @@ const PpcKernelInfo *ppc_kernels_f32(int *n) { *n = sizeof(k_ppc) / sizeof(k_ppc
 
 static const PersistKernelInfo k_persist[] = {
     HJ_KP2D(float, float, 1, 32, 1, false),
+    HJ_KP2D(float, float, 1, 16, 2, false),
     HJ_KP2D(float, float, 1, 16, 1, false),
     HJ_KP2D(float, float, 1, 8, 1, false),
     HJ_KP2D(float, float, 2, 16, 2, false),

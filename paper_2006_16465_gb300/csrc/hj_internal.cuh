@@ -244,7 +244,7 @@ typedef void (*PpcKernel)(PpcArgs);
 
 // TMA-pipelined 2D cycle kernel (hj_tma.cuh).
 struct PpcKernelInfo {
-    int tx, ty, threads;
+    int tx, ty, threads, stages;
     int smem[2];        // dynamic shared memory bytes [sig]
     int bwu, bwf;       // box widths (elements) of the iterate / RHS boxes
     PpcKernel fn[2][2]; // [sig][res]

@@ -42,7 +42,7 @@ struct GraphEntry {
 
 const TileKernelInfo *family_tiles(int fam, int *n);
 const PersistKernelInfo *family_persist(int fam, int *n);
-const PersistKernelInfo *find_persist(int fam, int dim, int tx, int ty);
+const PersistKernelInfo *find_persist(int fam, int dim, int tx, int ty, int threads = 0);
 const PersistKernelInfo *persist_kernels_f64(int *n);
 const PersistKernelInfo *persist_kernels_f32(int *n);
 const PersistKernelInfo *persist_kernels_bf16(int *n);

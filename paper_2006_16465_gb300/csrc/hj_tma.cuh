@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ 
 }  // namespace hj
 
 #define HJ_KPPC(S, T, C, R, NW, EX, NST)                                                                   \
-    {32 * (C), (R) * (NW), 32 * (NW), hj::PpcLayout<S, T, C, R, NW, false, NST>::SMEM,                     \
+    {32 * (C), (R) * (NW), 32 * (NW), (NST), hj::PpcLayout<S, T, C, R, NW, false, NST>::SMEM,              \
      hj::PpcLayout<S, T, C, R, NW, true, NST>::SMEM,                                                        \
      hj::PpcLayout<S, T, C, R, NW, false, NST>::BWU, hj::PpcLayout<S, T, C, R, NW, false, NST>::BWF,        \
      {{hj::ppc2d_kernel<S, T, C, R, NW, EX, false, false, NST>, hj::ppc2d_kernel<S, T, C, R, NW, EX, false, true, NST>}, \
