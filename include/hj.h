@@ -242,6 +242,25 @@ HJ_API const char *hj_last_error(void);
  * k only. */
 HJ_API int hj_autotune(const hj_desc *desc, hj_params *params, double *predicted_ms);
 
+/* Runs params->fixed_cycles cycles (hierarchical, or classic sweeps with
+ * params->method) on u in place, like hj_solve with fixed_cycles, but
+ * allocates nothing: no handle, no workspace, no graph.  The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory
+ * when they need cycles (a device-memory budget fixed at start-up, a real-time
+ * loop that cannot afford cudaMalloc, memory owned by another allocator).
+ * The second iterate buffer comes from a static 16 MiB device array inside
+ * the library, so the grid must satisfy rows * ld * element size <= 16 MiB
+ * (2D: rows = ny + 2), else HJ_ERR_INVALID_ARG.  desc->sigma must be NULL
+ * (sigma_const is fine); params->precision is HJ_PREC_F64 or HJ_PREC_F32 to
+ * match desc->dtype; tile_x, tile_y, k, method as for hj_create.  f and u are
+ * device pointers (same layout rules).  Stream-ordered; does not wait.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and corrupt each other's results. */
+HJ_API int hj_cycles_noalloc(const hj_desc *desc, const hj_params *params, const void *f, void *u,
+                             hj_stream stream);
+
 /* Built (tile_x, tile_y, threads) combinations for (dim, precision): writes
  * up to cap triples into txt[3*i .. 3*i+2] and returns how many exist. */
 HJ_API int hj_tile_variants(int dim, int precision, int *txt, int cap);

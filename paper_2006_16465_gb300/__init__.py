@@ -106,8 +106,10 @@ def lib():
         L.hj_tile_shapes.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]
         L.hj_tile_variants.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]
         L.hj_autotune.argtypes = [C.POINTER(hj_desc), C.POINTER(hj_params), C.POINTER(C.c_double)]
+        L.hj_cycles_noalloc.argtypes = [C.POINTER(hj_desc), C.POINTER(hj_params), C.c_void_p, C.c_void_p,
+                                        C.c_void_p]
         for name in ("hj_create", "hj_solve", "hj_residual", "hj_solve_adjoint", "hj_solve_batched",
-                     "hj_tile_shapes", "hj_tile_variants", "hj_autotune"):
+                     "hj_tile_shapes", "hj_tile_variants", "hj_autotune", "hj_cycles_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -183,6 +185,13 @@ def hj_autotune(desc: hj_desc, params: hj_params):
     if st != HJ_OK:
         raise HJError(st, "hj_autotune")
     return ms.value
+
+
+def hj_cycles_noalloc(desc: hj_desc, params: hj_params, f_ptr: int, u_ptr: int, stream: int = 0) -> int:
+    """params.fixed_cycles cycles on u in place without any allocation (the
+    second iterate buffer is a static 16 MiB array in the library)."""
+    return lib().hj_cycles_noalloc(C.byref(desc), C.byref(params), C.c_void_p(f_ptr), C.c_void_p(u_ptr),
+                                   C.c_void_p(stream))
 
 
 def hj_tile_variants(dim: int, precision: int):
