@@ -211,14 +211,27 @@ HJ_API int hj_solve_adjoint(hj_handle *h, const void *g, const void *u, void *dl
                      hj_stream stream, hj_stats *stats);
 
 /* Solve nprob independent 2D problems (each with its own hj_desc: sizes, ld,
- * stencil, sigma_const; sigma must be NULL; dtype HJ_F64) in one persistent
- * launch per refinement phase, fed by a device work queue of (problem, tile)
- * items; problems retire independently when they meet params.tol.  The
- * handle must come from hj_create with a 2D descriptor (it supplies params);
- * f[i], u[i] are device pointers.  stats (nullable) receives totals; per-
- * problem cycle counts go to cycles_out (host, nprob entries, nullable). */
+ * stencil, sigma_const, per-point sigma or NULL; dtype HJ_F64) in one
+ * persistent launch per refinement phase, fed by a device work queue of
+ * (problem, tile) items; problems retire independently when they meet
+ * params.tol.  The handle must come from hj_create with a 2D descriptor and
+ * HJ_PREC_F32_IR or HJ_PREC_BF16CORR_IR (it supplies params; autotune = 1
+ * tunes one tile variant for the launch and k per size class).  f[i], u[i]
+ * are device pointers.  stats (nullable) receives totals (rel_final = the
+ * worst relative residual); per-problem inner cycle counts go to cycles_out
+ * (host, nprob entries, nullable). */
 HJ_API int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, const void *const *f,
                      void *const *u, hj_stream stream, hj_stats *stats, long long *cycles_out);
+
+/* Adjoint of a batch of nrhs solves that share the handle's operator A(sigma)
+ * (the handle's descriptor, sigma included): solves A^T lambda_b = g_b for
+ * every b in one persistent launch per refinement phase (handle precision
+ * HJ_PREC_F32_IR or HJ_PREC_BF16CORR_IR, 2D), writes dl_df[b] = lambda_b and
+ * accumulates dl_dsigma = -sum_b lambda_b * u_b (binary64 grid, nullable) by
+ * the fused gradient kernel.  g, u, dl_df: device grids in the handle's layout.
+ * Same errors as hj_solve_batched. */
+HJ_API int hj_solve_adjoint_batched(hj_handle *h, int nrhs, const void *const *g, const void *const *u,
+                                    void *const *dl_df, void *dl_dsigma, hj_stream stream, hj_stats *stats);
 
 /* Free the handle and its workspace (NULL is ignored). */
 HJ_API void hj_destroy(hj_handle *h);

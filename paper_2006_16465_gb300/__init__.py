@@ -97,6 +97,8 @@ def lib():
         L.hj_solve_batched.argtypes = [H, C.c_int, C.POINTER(hj_desc), C.POINTER(C.c_void_p),
                                        C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(hj_stats),
                                        C.POINTER(C.c_longlong)]
+        L.hj_solve_adjoint_batched.argtypes = [H, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                               C.POINTER(C.c_void_p), C.c_void_p, C.c_void_p, C.POINTER(hj_stats)]
         L.hj_destroy.argtypes = [H]
         L.hj_destroy.restype = None
         L.hj_error_string.argtypes = [C.c_int]
@@ -109,6 +111,7 @@ def lib():
         L.hj_cycles_noalloc.argtypes = [C.POINTER(hj_desc), C.POINTER(hj_params), C.c_void_p, C.c_void_p,
                                         C.c_void_p]
         for name in ("hj_create", "hj_solve", "hj_residual", "hj_solve_adjoint", "hj_solve_batched",
+                     "hj_solve_adjoint_batched",
                      "hj_tile_shapes", "hj_tile_variants", "hj_autotune", "hj_cycles_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -162,6 +165,16 @@ def hj_solve_batched(h, descs, f_ptrs, u_ptrs, stream: int = 0, stats: hj_stats 
     U = (C.c_void_p * n)(*u_ptrs)
     return lib().hj_solve_batched(h, n, D, F, U, C.c_void_p(stream),
                                   C.byref(stats) if stats is not None else None, cycles_out)
+
+
+def hj_solve_adjoint_batched(h, g_ptrs, u_ptrs, dl_df_ptrs, dl_dsigma_ptr: int = 0, stream: int = 0,
+                             stats: hj_stats | None = None) -> int:
+    n = len(g_ptrs)
+    G = (C.c_void_p * n)(*g_ptrs)
+    U = (C.c_void_p * n)(*u_ptrs)
+    L = (C.c_void_p * n)(*dl_df_ptrs)
+    return lib().hj_solve_adjoint_batched(h, n, G, U, L, C.c_void_p(dl_dsigma_ptr or None), C.c_void_p(stream),
+                                          C.byref(stats) if stats is not None else None)
 
 
 def hj_destroy(h) -> None:

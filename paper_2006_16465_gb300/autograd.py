@@ -14,7 +14,13 @@ from __future__ import annotations
 
 import torch
 
-from . import HJ_ERR_NOT_CONVERGED, HJ_OK, HJError, Solver, make_params
+from . import (HJ_ERR_NOT_CONVERGED, HJ_OK, HJ_PREC_BF16CORR_IR, HJ_PREC_F32_IR, HJError, Solver,
+               _stream_handle, hj_solve_adjoint_batched, hj_solve_batched, make_params)
+
+
+def _batchable(solver, nrhs):
+    # several right-hand sides of one 2D refinement solve share persistent launches
+    return nrhs > 1 and solver.dim == 2 and solver.params.precision in (HJ_PREC_F32_IR, HJ_PREC_BF16CORR_IR)
 
 
 class HJSolve(torch.autograd.Function):
@@ -30,10 +36,17 @@ class HJSolve(torch.autograd.Function):
         fb = f if batched else f.unsqueeze(0)
         solver = Solver(stencil, params, sigma=None if sigma is None else sigma.detach().contiguous())
         u = torch.zeros_like(fb)
-        for b in range(fb.shape[0]):
-            out = solver.solve(fb[b].detach().contiguous(), u[b], check=False)
-            if out["status"] not in (HJ_OK, HJ_ERR_NOT_CONVERGED):
-                raise HJError(out["status"], "HJSolve forward")
+        fd = fb.detach().contiguous()
+        if _batchable(solver, fb.shape[0]):
+            code = hj_solve_batched(solver.h, [solver.desc] * fb.shape[0], [fd[b].data_ptr() for b in range(fb.shape[0])],
+                                    [u[b].data_ptr() for b in range(fb.shape[0])], _stream_handle(None))
+            if code not in (HJ_OK, HJ_ERR_NOT_CONVERGED):
+                raise HJError(code, "HJSolve forward (batched)")
+        else:
+            for b in range(fb.shape[0]):
+                out = solver.solve(fd[b], u[b], check=False)
+                if out["status"] not in (HJ_OK, HJ_ERR_NOT_CONVERGED):
+                    raise HJError(out["status"], "HJSolve forward")
         ctx.solver = solver
         ctx.batched = batched
         ctx.has_sigma = sigma is not None
@@ -52,12 +65,21 @@ class HJSolve(torch.autograd.Function):
         if ctx.has_sigma and ctx.needs_input_grad[1]:
             dl_dsig = torch.zeros_like(u[0])
             dsig_b = torch.zeros_like(u[0])
-        for b in range(u.shape[0]):
-            out = solver.adjoint(g[b], u[b], dl_df[b], dsig_b, check=False)
-            if out["status"] not in (HJ_OK, HJ_ERR_NOT_CONVERGED):
-                raise HJError(out["status"], "HJSolve backward")
-            if dsig_b is not None:
-                dl_dsig += dsig_b
+        B = u.shape[0]
+        if _batchable(solver, B):
+            code = hj_solve_adjoint_batched(solver.h, [g[b].data_ptr() for b in range(B)],
+                                            [u[b].data_ptr() for b in range(B)],
+                                            [dl_df[b].data_ptr() for b in range(B)],
+                                            0 if dl_dsig is None else dl_dsig.data_ptr(), _stream_handle(None))
+            if code not in (HJ_OK, HJ_ERR_NOT_CONVERGED):
+                raise HJError(code, "HJSolve backward (batched)")
+        else:
+            for b in range(B):
+                out = solver.adjoint(g[b], u[b], dl_df[b], dsig_b, check=False)
+                if out["status"] not in (HJ_OK, HJ_ERR_NOT_CONVERGED):
+                    raise HJError(out["status"], "HJSolve backward")
+                if dsig_b is not None:
+                    dl_dsig += dsig_b
         solver.close()
         ctx.solver = None
         grad_f = dl_df if ctx.batched else dl_df[0]

@@ -396,36 +396,53 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, 
     CKS(make_plan(h, ki, pi, fam, classic, sig, true, base, b0, b1, &pl));
     cudaGraphExec_t ex;
     CKS(plan_graph(h, pl, M, &ex));
-    long long launched = 0, copied = 0;
     const long long mask = kHistCap - 1;
-    for (;;) {
+    // Replays are pipelined two deep: replay i+1 is queued before the host
+    // waits for replay i's control block, so the GPU does not idle while the
+    // host checks.  Replay r copies its control block into slot r % 2 and its
+    // slice of the residual ring into the pinned ring.  No replay starts at or
+    // beyond max_cycles, and launches after convergence return at once.
+    long long issued = 0;   // replays queued
+    auto issue = [&]() -> int {
+        const long long r = issued;
         CKR(cudaGraphLaunch(ex, s));
-        const long long start = launched;
-        launched += M;
-        // copy this replay's slice of the residual ring
-        const long long p0 = start & mask;
+        const long long p0 = (r * M) & mask;
         const long long n0 = std::min<long long>(M, kHistCap - p0);
         CKR(cudaMemcpyAsync(h->h_hist + p0, h->hist + p0, n0 * sizeof(double), cudaMemcpyDeviceToHost, s));
         if (n0 < M)
             CKR(cudaMemcpyAsync(h->h_hist, h->hist, (M - n0) * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CKR(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-        CKR(cudaEventRecord(h->ev, s));
-        CKR(cudaEventSynchronize(h->ev));
-        if (h->h_ctl->err) return seterr(HJ_ERR_TIMEOUT, "a bounded device wait expired (tile pipeline)");
-        const long long ncomp = h->h_ctl->cycle;
+        CKR(cudaMemcpyAsync(h->h_ctl + (r & 1), h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CKR(cudaEventRecord(h->evs[r & 1], s));
+        ++issued;
+        return HJ_OK;
+    };
+    CKS(issue());
+    long long copied = 0, checked = 0;
+    const Ctl *last = nullptr;
+    for (;;) {
+        if (issued * M < max_cycles) CKS(issue());
+        CKR(cudaEventSynchronize(h->evs[checked & 1]));
+        last = h->h_ctl + (checked & 1);
+        ++checked;
+        if (last->err) return seterr(HJ_ERR_TIMEOUT, "a bounded device wait expired (tile pipeline)");
+        const long long ncomp = last->cycle;
         if (hist_out) {
             for (; copied < ncomp; ++copied)
                 if (copied < hist_cap) hist_out[copied] = sqrt(h->h_hist[copied & mask]);
         }
-        if (h->h_ctl->done >= 0) break;
-        if (launched > max_cycles + 2LL * M)
+        if (last->done >= 0) break;
+        if (checked >= issued)
             return seterr(HJ_ERR_CUDA, "cycle loop did not terminate (device control block not updated)");
     }
+    // the replay queued behind the converged one returns at once; wait for it
+    // so that no copy into the pinned slots is still pending when we return
+    if (issued > checked) CKR(cudaEventSynchronize(h->evs[(issued - 1) & 1]));
+    const long long launched = issued * M;   // kernels launched, including returns-at-once overshoot
     if (hist_len) *hist_len = std::min(copied, hist_cap);
-    ro->c = h->h_ctl->done;
-    ro->status = h->h_ctl->status;
+    ro->c = last->done;
+    ro->status = last->status;
     ro->launched = launched;
-    ro->res2_0 = h->h_ctl->res2_0;
+    ro->res2_0 = last->res2_0;
     if (ro->status == HJ_OK || ro->status == HJ_ERR_DIVERGED) ro->res2_c = h->h_hist[ro->c & mask];
     return HJ_OK;
 }
@@ -729,6 +746,8 @@ void hj_destroy(hj_handle *h) {
         if (p) cudaFreeHost(p);
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->ev) cudaEventDestroy(h->ev);
+    for (cudaEvent_t e : h->evs)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 
@@ -863,13 +882,15 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     if (cudaMemset(h->gcnt, 0, h->max_groups * sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(h->fcnt, 0, sizeof(unsigned)) != cudaSuccess)
         HJ_FAIL(HJ_ERR_CUDA, "cudaMemset failed");
-    if (cudaMallocHost((void **)&h->h_ctl, sizeof(Ctl)) != cudaSuccess ||
+    if (cudaMallocHost((void **)&h->h_ctl, 2 * sizeof(Ctl)) != cudaSuccess ||
         cudaMallocHost((void **)&h->h_ctl_init, sizeof(Ctl)) != cudaSuccess ||
         cudaMallocHost((void **)&h->h_hist, kHistCap * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void **)&h->h_rstore, 2 * sizeof(double)) != cudaSuccess)
         HJ_FAIL(HJ_ERR_NO_MEMORY, "cudaMallocHost failed");
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->evs[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->evs[1], cudaEventDisableTiming) != cudaSuccess)
         HJ_FAIL(HJ_ERR_CUDA, "stream/event creation failed");
 
     const double dconst = d.cD + d.sigma_const;
@@ -968,7 +989,7 @@ int hj_solve_adjoint(hj_handle *h, const void *g, const void *u, void *dl_df, vo
     if (dl_dsigma) {
         CKR(cudaMemsetAsync(dl_dsigma, 0, h->grid_elems * sizeof(double), s));
         CKR(launch_grad_sigma_ex(h->d.dim, h->d.dtype == HJ_F64, dl_df, u, (double *)dl_dsigma, h->d.ld, h->d.nx,
-                                 h->d.ny, s));
+                                 h->d.ny, 0, s));
         CKR(cudaStreamSynchronize(s));
     }
     fill_stats_config(h, stats, t0);

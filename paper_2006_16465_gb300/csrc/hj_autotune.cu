@@ -7,7 +7,9 @@
 // For every candidate (tile, k):
 //   * contraction rho per cycle: start from the lowest discrete sine mode with
 //     f = 0 and zero Dirichlet data (the slowest-converging error component),
-//     run C cycles and take rho = (||r_C|| / ||r_{C/2}||)^(2/C);
+//     run 128 cycles and take the mean rate over the last 32 (earlier windows
+//     are biased by the transient at subdomain edges: the residual may even
+//     grow during the first cycles);
 //   * time per cycle t: CUDA events around the same run (graph path with the
 //     fused residual, as a real solve runs);
 //   * predicted time to the tolerance: ln(tol) / ln(rho) * t.
@@ -82,6 +84,107 @@ void store_cache_file(const std::string &key, int tx, int ty, int th, int k) {
     fclose(fp);
 }
 
+// Scratch copy of a problem in the tuned precision (same stencil and sigma).
+struct Scratch {
+    void *u = nullptr, *f = nullptr;
+    double *sig = nullptr;
+    hj_desc td;
+    long long ld = 0;
+    int esz = 4;
+    ~Scratch() {
+        if (u) cudaFree(u);
+        if (f) cudaFree(f);
+        if (sig) cudaFree(sig);
+    }
+    int init(const hj_desc &d, int prec) {
+        esz = prec == HJ_PREC_F64 ? 8 : 4;
+        ld = ((long long)d.nx + 2 + 31) / 32 * 32;
+        const int rows = d.dim == 2 ? d.ny + 2 : d.ny;
+        const size_t bytes = (size_t)rows * ld * esz;
+        if (cudaMalloc(&u, bytes) != cudaSuccess || cudaMalloc(&f, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return seterr(HJ_ERR_NO_MEMORY, "autotune scratch");
+        }
+        td = d;
+        td.ld = ld;
+        td.dtype = prec == HJ_PREC_F64 ? HJ_F64 : HJ_F32;
+        if (d.sigma) {
+            if (cudaMalloc((void **)&sig, (size_t)rows * ld * 8) != cudaSuccess ||
+                cudaMemcpy2D(sig, ld * 8, d.sigma, d.ld * 8, (size_t)(d.nx + 2) * 8, rows, cudaMemcpyDeviceToDevice) !=
+                    cudaSuccess) {
+                cudaGetLastError();
+                return seterr(HJ_ERR_NO_MEMORY, "autotune sigma copy");
+            }
+            td.sigma = sig;
+        }
+        if (cudaMemset(f, 0, bytes) != cudaSuccess) return seterr(HJ_ERR_CUDA, "autotune memset");
+        return HJ_OK;
+    }
+};
+
+constexpr int kCyc = 128;   // cycles per measurement
+constexpr int kWin = 32;    // contraction measured over the last kWin cycles
+
+// Run kCyc cycles of (tile, threads, k) from the lowest sine mode with f = 0.
+// *rho: contraction per cycle over the second half; *ms: time of the kCyc
+// cycles without the closing residual pass.  fixed: time fixed cycles instead
+// (no residual, no rho).
+bool measure(Scratch &sc, int prec, int tx, int ty, int th, int k, const hj_params &base, double *rho, double *ms) {
+    hj_params tp;
+    hj_default_params(&tp);
+    tp.tile_x = tx;
+    tp.tile_y = ty;
+    tp.tile_threads = th;
+    tp.pipeline_stages = base.pipeline_stages;
+    tp.k = k;
+    tp.precision = prec;
+    tp.tol = 0.0;
+    tp.max_cycles = kCyc;
+    tp.check_every = kCyc;
+    tp.persistent = base.persistent;
+    tp.pipeline = base.pipeline;
+    hj_handle *h = nullptr;
+    if (hj_create(&h, &sc.td, &tp) != HJ_OK) return false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double hist[kCyc + 1];
+    double best = INFINITY, r = 1.0;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {   // the first run warms graphs and caches
+        if (sc.esz == 8) fill_mode_kernel<double><<<256, 256>>>((double *)sc.u, sc.ld, sc.td.nx, sc.td.ny, sc.td.dim);
+        else fill_mode_kernel<float><<<256, 256>>>((float *)sc.u, sc.ld, sc.td.nx, sc.td.ny, sc.td.dim);
+        hj_stats st;
+        memset(&st, 0, sizeof(st));
+        st.history = hist;
+        st.history_cap = kCyc + 1;
+        cudaEventRecord(e0, 0);
+        const int code = hj_solve(h, sc.f, sc.u, nullptr, &st);
+        cudaEventRecord(e1, 0);
+        cudaEventSynchronize(e1);
+        if (code != HJ_OK && code != HJ_ERR_NOT_CONVERGED) { ok = false; break; }
+        float t = 0.f, tr = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        // the solve ends with one residual pass of the last iterate (it did not
+        // converge at tol = 0): time it alone and subtract it
+        cudaEventRecord(e0, 0);
+        hj_residual(h, sc.f, sc.u, nullptr, nullptr, nullptr);
+        cudaEventRecord(e1, 0);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&tr, e0, e1);
+        best = std::min(best, (double)std::max(t - tr, 1e-3f));
+        if (st.history_len >= kCyc && hist[kCyc - 1 - kWin] > 0 && hist[kCyc - 1] > 0)
+            r = pow(hist[kCyc - 1] / hist[kCyc - 1 - kWin], 1.0 / kWin);
+    }
+    hj_destroy(h);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    *rho = r;
+    *ms = best;
+    return ok && std::isfinite(best);
+}
+
 }  // namespace
 
 extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predicted_ms) {
@@ -109,51 +212,13 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
             return HJ_OK;
         }
     }
-    // scratch problem in the tuned precision, same stencil and sigma
-    const int esz = prec == HJ_PREC_F64 ? 8 : 4;
-    const long long ld = ((long long)d.nx + 2 + 31) / 32 * 32;
-    const int rows = d.dim == 2 ? d.ny + 2 : d.ny;
-    const size_t bytes = (size_t)rows * ld * esz;
-    void *u = nullptr, *f = nullptr;
-    double *sig = nullptr;
-    auto cleanup = [&]() {
-        if (u) cudaFree(u);
-        if (f) cudaFree(f);
-        if (sig) cudaFree(sig);
-    };
-    if (cudaMalloc(&u, bytes) != cudaSuccess || cudaMalloc(&f, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        cleanup();
-        return seterr(HJ_ERR_NO_MEMORY, "autotune scratch");
-    }
-    hj_desc td = d;
-    td.ld = ld;
-    td.dtype = prec == HJ_PREC_F64 ? HJ_F64 : HJ_F32;
-    if (d.sigma) {
-        if (cudaMalloc((void **)&sig, (size_t)rows * ld * 8) != cudaSuccess ||
-            cudaMemcpy2D(sig, ld * 8, d.sigma, d.ld * 8, (size_t)(d.nx + 2) * 8, rows, cudaMemcpyDeviceToDevice) !=
-                cudaSuccess) {
-            cudaGetLastError();
-            cleanup();
-            return seterr(HJ_ERR_NO_MEMORY, "autotune sigma copy");
-        }
-        td.sigma = sig;
-    }
-    if (cudaMemset(f, 0, bytes) != cudaSuccess) {
-        cleanup();
-        return seterr(HJ_ERR_CUDA, "autotune memset");
-    }
-    // candidate (tile shape, threads per tile) variants
+    Scratch sc;
+    CKS(sc.init(d, prec));
     int xy[3 * 64];
     const int nshape = std::min(64, hj_tile_variants(d.dim, prec, xy, 64));
     const int ks[] = {4, 8, 16, 32, 64};
-    const int C = 24;
     double best = INFINITY;
     int btx = params->tile_x, bty = params->tile_y, bth = params->tile_threads, bk = params->k;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    double hist[C + 1];
     for (int si = 0; si < nshape; ++si) {
         const int tx = xy[3 * si], ty = xy[3 * si + 1], th = xy[3 * si + 2];
         // autotune == 2: the tile variant is fixed by the caller, tune k only
@@ -163,50 +228,10 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
         // skip shapes far larger than the grid
         if (tx > 2 * std::max(d.nx, 32) || (d.dim == 2 && ty > 2 * std::max(d.ny, 8))) continue;
         for (int k : ks) {
-            hj_params tp;
-            hj_default_params(&tp);
-            tp.tile_x = tx;
-            tp.tile_y = ty;
-            tp.tile_threads = th;
-            tp.pipeline_stages = params->pipeline_stages;
-            tp.k = k;
-            tp.precision = prec;
-            tp.tol = 0.0;
-            tp.max_cycles = C;
-            tp.check_every = C;
-            tp.persistent = params->persistent;
-            tp.pipeline = params->pipeline;
-            hj_handle *h = nullptr;
-            if (hj_create(&h, &td, &tp) != HJ_OK) continue;
-            double ms = INFINITY, rho = 1.0;
-            for (int rep = 0; rep < 2; ++rep) {   // first run warms graphs and caches
-                if (esz == 8) fill_mode_kernel<double><<<256, 256>>>((double *)u, ld, d.nx, d.ny, d.dim);
-                else fill_mode_kernel<float><<<256, 256>>>((float *)u, ld, d.nx, d.ny, d.dim);
-                hj_stats st;
-                memset(&st, 0, sizeof(st));
-                st.history = hist;
-                st.history_cap = C + 1;
-                cudaEventRecord(e0, 0);
-                const int code = hj_solve(h, f, u, nullptr, &st);
-                cudaEventRecord(e1, 0);
-                cudaEventSynchronize(e1);
-                if (code != HJ_OK && code != HJ_ERR_NOT_CONVERGED) break;
-                float t = 0.f, tr = 0.f;
-                cudaEventElapsedTime(&t, e0, e1);
-                // the solve ends with one residual pass of the last iterate (it
-                // did not converge at tol = 0): time it alone and subtract it
-                cudaEventRecord(e0, 0);
-                hj_residual(h, f, u, nullptr, nullptr, nullptr);
-                cudaEventRecord(e1, 0);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&tr, e0, e1);
-                ms = std::min(ms, (double)std::max(t - tr, 1e-3f));
-                if (st.history_len >= C && hist[C / 2] > 0 && hist[C - 1] > 0)
-                    rho = pow(hist[C - 1] / hist[C / 2], 1.0 / (C - 1 - C / 2));
-            }
-            hj_destroy(h);
-            if (!(rho > 0.0 && rho < 1.0) || !std::isfinite(ms)) continue;
-            const double pred = log(std::max(tol, 1e-300)) / log(rho) * (ms / C);
+            double rho = 1.0, ms = INFINITY;
+            if (!measure(sc, prec, tx, ty, th, k, *params, &rho, &ms)) continue;
+            if (!(rho > 0.0 && rho < 1.0)) continue;
+            const double pred = log(std::max(tol, 1e-300)) / log(rho) * (ms / kCyc);
             if (pred < best) {
                 best = pred;
                 btx = tx;
@@ -216,10 +241,6 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cleanup();
-    cudaGetLastError();
     if (!std::isfinite(best)) return seterr(HJ_ERR_UNSUPPORTED, "autotune found no usable candidate");
     params->tile_x = btx;
     params->tile_y = d.dim == 2 ? bty : 1;
@@ -233,3 +254,143 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
     }
     return HJ_OK;
 }
+
+namespace hj {
+
+// Batched scheduler tuning.  In a batch, cycles are throughput-bound (all
+// active problems share each launch), so a candidate's cost per point per
+// cycle c(t, k) is measured on a throughput-sized synthetic grid, while its
+// contraction rho(t, k) is measured on the largest problem of each size
+// class.  The tile variant t (one per launch, persistent kernels only)
+// minimises  sum_p points_p * cycles(rho_class(p)(t, k_class)) * c(t, k_class),
+// with k per class chosen the same way.  cls[p] is the class of problem p.
+int autotune_batched(const hj_desc *descs, int nprob, const std::vector<int> &cls, int ncls, hj_params *par,
+                     std::vector<int> *kcls) {
+    // per-process cache keyed by the whole batch description
+    static std::mutex mu;
+    static std::map<std::string, std::vector<int>> cache;
+    std::string key;
+    {
+        char buf[128];
+        snprintf(buf, sizeof(buf), "p%d_tol%.3g_a%d_t%dx%dt%d:", par->precision, par->tol, par->autotune,
+                 par->tile_x, par->tile_y, par->tile_threads);
+        key = buf;
+        for (int i = 0; i < nprob; ++i) {
+            snprintf(buf, sizeof(buf), "%dx%d,%.9g,%.9g;", descs[i].nx, descs[i].ny, descs[i].cD, descs[i].sigma_const);
+            key += buf;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            par->tile_x = it->second[0];
+            par->tile_y = it->second[1];
+            par->tile_threads = it->second[2];
+            kcls->assign(it->second.begin() + 3, it->second.end());
+            return HJ_OK;
+        }
+    }
+    const int fam = par->precision == HJ_PREC_BF16CORR_IR ? FAM_BF16 : FAM_F32;
+    const int prec = HJ_PREC_F32;
+    const double tol = par->tol;
+    std::vector<int> rep(ncls, -1);
+    std::vector<double> pts(ncls, 0.0);
+    for (int i = 0; i < nprob; ++i) {
+        const int c = cls[i];
+        pts[c] += (double)descs[i].nx * descs[i].ny;
+        if (rep[c] < 0 || (long long)descs[i].nx * descs[i].ny > (long long)descs[rep[c]].nx * descs[rep[c]].ny)
+            rep[c] = i;
+    }
+    // throughput grid: Poisson 2048^2 with the largest problem's screening
+    hj_desc big = descs[0];
+    big.nx = big.ny = 2048;
+    big.sigma = nullptr;
+    Scratch thr;
+    CKS(thr.init(big, prec));
+    int xy[3 * 64];
+    const int nv = std::min(64, hj_tile_variants(2, prec, xy, 64));
+    const int ks[] = {4, 8, 16, 32, 64};
+    const int nk = 5;
+    double best = INFINITY;
+    std::vector<int> bestk(ncls, par->k);
+    int btx = par->tile_x, bty = par->tile_y, bth = par->tile_threads;
+    std::vector<Scratch> reps(ncls);
+    for (int c = 0; c < ncls; ++c)
+        if (rep[c] >= 0) CKS(reps[c].init(descs[rep[c]], prec));
+    hj_params thp = *par;
+    thp.persistent = 0;   // fixed-cycle throughput of the tile code on a large grid
+    thp.pipeline = 0;
+    hj_params solo = *par;
+    solo.persistent = 1;  // a problem alone: the latency floor of a persistent cycle
+    for (int v = 0; v < nv; ++v) {
+        const int tx = xy[3 * v], ty = xy[3 * v + 1], th = xy[3 * v + 2];
+        if (!find_persist(fam, 2, tx, ty, th)) continue;
+        if (par->autotune == 2 && (tx != par->tile_x || ty != par->tile_y || (par->tile_threads && th != par->tile_threads)))
+            continue;
+        // measured per class and k: cycles to tol and solo cycle time; per k: throughput cost per point
+        std::vector<double> cyc(ncls * nk, INFINITY), tau(ncls * nk, INFINITY), theta(nk, INFINITY);
+        for (int j = 0; j < nk; ++j) {
+            double rho_t = 0.0, ms_thr = 0.0;
+            if (measure(thr, prec, tx, ty, th, ks[j], thp, &rho_t, &ms_thr))
+                theta[j] = ms_thr / kCyc / (2048.0 * 2048.0);
+            for (int c = 0; c < ncls; ++c) {
+                if (rep[c] < 0) continue;
+                double rho = 1.0, ms = 0.0;
+                if (!measure(reps[c], prec, tx, ty, th, ks[j], solo, &rho, &ms)) continue;
+                if (!(rho > 0.0 && rho < 1.0)) continue;
+                cyc[c * nk + j] = log(std::max(tol, 1e-300)) / log(rho);
+                tau[c * nk + j] = ms / kCyc;
+            }
+        }
+        // simulate the batch for every choice of k per class: all classes run
+        // together; a cycle costs max(latency floor of the active classes,
+        // active points x throughput cost); classes retire after their cycles
+        std::vector<int> choice(ncls, 0);
+        const int ncomb = (int)pow(nk, ncls);
+        for (int comb = 0; comb < ncomb; ++comb) {
+            int t = comb;
+            for (int c = 0; c < ncls; ++c) { choice[c] = t % nk; t /= nk; }
+            std::vector<std::pair<double, int>> ord;
+            bool okc = true;
+            for (int c = 0; c < ncls; ++c) {
+                if (rep[c] < 0) continue;
+                const double n = cyc[c * nk + choice[c]];
+                if (!std::isfinite(n) || !std::isfinite(theta[choice[c]])) { okc = false; break; }
+                ord.push_back({n, c});
+            }
+            if (!okc || ord.empty()) continue;
+            std::sort(ord.begin(), ord.end());
+            double total = 0.0, done = 0.0;
+            for (size_t a2 = 0; a2 < ord.size(); ++a2) {
+                double floor_t = 0.0, work = 0.0;
+                for (size_t b2 = a2; b2 < ord.size(); ++b2) {
+                    const int c = ord[b2].second;
+                    floor_t = std::max(floor_t, tau[c * nk + choice[c]]);
+                    work += pts[c] * theta[choice[c]];
+                }
+                total += (ord[a2].first - done) * std::max(floor_t, work);
+                done = ord[a2].first;
+            }
+            if (total < best) {
+                best = total;
+                btx = tx;
+                bty = ty;
+                bth = th;
+                for (int c = 0; c < ncls; ++c) bestk[c] = ks[choice[c]];
+            }
+        }
+    }
+    if (!std::isfinite(best)) return seterr(HJ_ERR_UNSUPPORTED, "batched autotune found no usable candidate");
+    par->tile_x = btx;
+    par->tile_y = bty;
+    par->tile_threads = bth;
+    *kcls = bestk;
+    {
+        std::vector<int> v = {btx, bty, bth};
+        v.insert(v.end(), bestk.begin(), bestk.end());
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = v;
+    }
+    return HJ_OK;
+}
+
+}  // namespace hj

@@ -133,15 +133,20 @@ __global__ void __launch_bounds__(256) update_residual_kernel(const AuxArgs a) {
     reduce_grid<1>(a.red, vals);
 }
 
+// dL/dsigma_p = -lambda_p u_p (accumulate != 0: added to dsig, for a batch of
+// right-hand sides sharing sigma)
 template <typename T, int D>
 __global__ void __launch_bounds__(256) grad_sigma_kernel(const T *lam, const T *u, double *dsig, long long ld,
-                                                         int nx, int ny) {
+                                                         int nx, int ny, int accumulate) {
     int i, j;
     const long long nb = AuxGeom<D>::nblocks(nx, ny);
     for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
         if (!AuxGeom<D>::idx(nx, ny, b, i, j)) continue;
         const long long q = (long long)j * ld + i;
-        dsig[q] = -((double)lam[q] * (double)u[q]);
+        // separately rounded (no contraction into an FMA), so a batch's sum equals
+        // the sum of the per-right-hand-side gradients bit for bit
+        const double g = -__dmul_rn((double)lam[q], (double)u[q]);
+        dsig[q] = accumulate ? __dadd_rn(dsig[q], g) : g;
     }
 }
 
@@ -150,7 +155,8 @@ __global__ void __launch_bounds__(256) make_dinv_kernel(const double *sigma, dou
                                                        long long ld2, int rows, int cols, T *dinv) {
     const int i = blockIdx.x * 256 + threadIdx.x;
     const int j = blockIdx.y;
-    if (i < cols && j < rows) dinv[(long long)j * ld2 + i] = (T)__drcp_rn(__dadd_rn(dconst, sigma[(long long)j * ld + i]));
+    if (i < cols && j < rows)
+        dinv[(long long)j * ld2 + i] = (T)__drcp_rn(__dadd_rn(dconst, sigma ? sigma[(long long)j * ld + i] : 0.0));
 }
 
 int sm_count() {
@@ -178,11 +184,12 @@ dim3 aux_block(int dim) { return dim == 2 ? dim3(32, 8) : dim3(256); }
 cudaError_t launch_make_dinv_box(const double *sigma, double dconst, long long ld, long long ld2, int row0, int rows,
                                  int col0, int cols, int family, void *dinv, cudaStream_t s) {
     const size_t off = (size_t)row0 * ld + col0, off2 = (size_t)row0 * ld2 + col0;
+    const double *sg = sigma ? sigma + off : nullptr;
     dim3 grid((cols + 255) / 256, rows);
     if (family == FAM_F64)
-        make_dinv_kernel<double><<<grid, 256, 0, s>>>(sigma + off, dconst, ld, ld2, rows, cols, (double *)dinv + off2);
+        make_dinv_kernel<double><<<grid, 256, 0, s>>>(sg, dconst, ld, ld2, rows, cols, (double *)dinv + off2);
     else
-        make_dinv_kernel<float><<<grid, 256, 0, s>>>(sigma + off, dconst, ld, ld2, rows, cols, (float *)dinv + off2);
+        make_dinv_kernel<float><<<grid, 256, 0, s>>>(sg, dconst, ld, ld2, rows, cols, (float *)dinv + off2);
     return cudaGetLastError();
 }
 
@@ -227,14 +234,14 @@ cudaError_t launch_update_residual_ex(int dim, const double *f, const double *ui
 }
 
 cudaError_t launch_grad_sigma_ex(int dim, int user_f64, const void *lam, const void *u, double *dsig, long long ld,
-                                 int nx, int ny, cudaStream_t s) {
+                                 int nx, int ny, int accumulate, cudaStream_t s) {
     const dim3 g = aux_grid(dim, nx, ny), b = aux_block(dim);
     if (user_f64) {
-        if (dim == 2) grad_sigma_kernel<double, 2><<<g, b, 0, s>>>((const double *)lam, (const double *)u, dsig, ld, nx, ny);
-        else grad_sigma_kernel<double, 1><<<g, b, 0, s>>>((const double *)lam, (const double *)u, dsig, ld, nx, ny);
+        if (dim == 2) grad_sigma_kernel<double, 2><<<g, b, 0, s>>>((const double *)lam, (const double *)u, dsig, ld, nx, ny, accumulate);
+        else grad_sigma_kernel<double, 1><<<g, b, 0, s>>>((const double *)lam, (const double *)u, dsig, ld, nx, ny, accumulate);
     } else {
-        if (dim == 2) grad_sigma_kernel<float, 2><<<g, b, 0, s>>>((const float *)lam, (const float *)u, dsig, ld, nx, ny);
-        else grad_sigma_kernel<float, 1><<<g, b, 0, s>>>((const float *)lam, (const float *)u, dsig, ld, nx, ny);
+        if (dim == 2) grad_sigma_kernel<float, 2><<<g, b, 0, s>>>((const float *)lam, (const float *)u, dsig, ld, nx, ny, accumulate);
+        else grad_sigma_kernel<float, 1><<<g, b, 0, s>>>((const float *)lam, (const float *)u, dsig, ld, nx, ny, accumulate);
     }
     return cudaGetLastError();
 }

@@ -158,6 +158,12 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
 // ===========================================================================
 namespace {
 
+struct BProb;
+
+}  // namespace
+
+namespace {
+
 struct BProb {
     hj_desc d;
     int rows;
@@ -169,19 +175,24 @@ struct BProb {
     float *r32;              // binary32 residual (inner RHS)
     void *dA, *dB;           // correction buffers
     double *cur, *other;
+    float *dinv;             // per-point 1/d in binary32 (some problem of the batch has sigma)
     double r0, rn;
     bool active;
     long long inner_cycles;
 };
 
-CycArgs prob_args(const hj_desc &d, const hj_params &p) {
+// transpose: the adjoint operator A^T (cW <-> cE, cS <-> cN)
+CycArgs prob_args(const hj_desc &d, const hj_params &p, bool transpose = false) {
     CycArgs a;
     memset(&a, 0, sizeof(a));
     a.ld = d.ld;
     a.nx = d.nx;
     a.ny = d.ny;
     a.k = p.k;
-    a.cW = d.cW; a.cE = d.cE; a.cS = d.cS; a.cN = d.cN;
+    a.cW = transpose ? d.cE : d.cW;
+    a.cE = transpose ? d.cW : d.cE;
+    a.cS = transpose ? d.cN : d.cS;
+    a.cN = transpose ? d.cS : d.cN;
     a.dconst = d.cD + d.sigma_const;
     a.invd = 1.0 / a.dconst;
     a.fW = (float)a.cW; a.fE = (float)a.cE; a.fS = (float)a.cS; a.fN = (float)a.cN;
@@ -196,18 +207,34 @@ int validate_desc(const hj_desc &d, int i) {
     if (d.dim != 2) return seterr(HJ_ERR_INVALID_ARG, "problem %d: batched solves are 2D", i);
     if (d.nx < 1 || d.ny < 1 || d.ny > 524280) return seterr(HJ_ERR_INVALID_ARG, "problem %d: bad size", i);
     if (d.dtype != HJ_F64) return seterr(HJ_ERR_INVALID_ARG, "problem %d: batched solves take binary64 arrays", i);
-    if (d.sigma) return seterr(HJ_ERR_INVALID_ARG, "problem %d: per-point sigma is not supported in batches", i);
     if (d.ld < (long long)d.nx + 2 || (d.ld * 8) % 16) return seterr(HJ_ERR_INVALID_ARG, "problem %d: bad ld", i);
+    if (d.sigma && ((uintptr_t)d.sigma & 15)) return seterr(HJ_ERR_INVALID_ARG, "problem %d: sigma not aligned", i);
     const double off = fabs(d.cW) + fabs(d.cE) + fabs(d.cS) + fabs(d.cN);
-    const double dd = d.cD + d.sigma_const;
+    double dd = d.cD + d.sigma_const;
+    if (d.sigma) {
+        // smallest per-point screening (read once per distinct sigma array)
+        static thread_local const double *last = nullptr;
+        static thread_local double last_min = 0.0;
+        if (d.sigma != last) {
+            std::vector<double> hs((size_t)(d.ny + 2) * d.ld);
+            if (cudaMemcpy(hs.data(), d.sigma, hs.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return seterr(HJ_ERR_CUDA, "problem %d: reading sigma", i);
+            double m = INFINITY;
+            for (int j = 1; j <= d.ny; ++j)
+                for (int x = 1; x <= d.nx; ++x) m = std::min(m, hs[(size_t)j * d.ld + x]);
+            last = d.sigma;
+            last_min = m;
+        }
+        dd += last_min;
+    }
     if (!(dd > 0.0) || dd < off) return seterr(HJ_ERR_NOT_DIAG_DOMINANT, "problem %d: not diagonally dominant", i);
     return HJ_OK;
 }
 
 }  // namespace
 
-extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, const void *const *f, void *const *u,
-                                hj_stream stream, hj_stats *stats, long long *cycles_out) {
+int batched_core(hj_handle *h, int nprob, const hj_desc *descs, const void *const *f, void *const *u,
+                 hj_stream stream, hj_stats *stats, long long *cycles_out, bool transpose) {
     if (!h) return seterr(HJ_ERR_INVALID_ARG, "handle is NULL");
     if (nprob < 1 || !descs || !f || !u) return seterr(HJ_ERR_INVALID_ARG, "nprob, descs, f, u");
     if (!h->ir) return seterr(HJ_ERR_UNSUPPORTED, "batched solves use HJ_PREC_F32_IR or HJ_PREC_BF16CORR_IR");
@@ -215,37 +242,25 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
     hj_params par = h->p;
     const int fam = h->fam_inner;
     for (int i = 0; i < nprob; ++i) CKS(validate_desc(descs[i], i));
-    // autotune: the tile shape (common to a launch) on the largest problem, then
-    // k per size class (largest side up to 128, 256, 384, beyond) on the largest
-    // problem of each class with that tile fixed
+    // autotune: one tile variant for the launch and k per size class (largest
+    // side up to 128, 256, 384, beyond), by the batched cost model
     std::vector<int> kprob(nprob, par.k);
     if (par.autotune == 1 || par.autotune == 2) {
-        int big = 0;
-        for (int i = 1; i < nprob; ++i)
-            if ((long long)descs[i].nx * descs[i].ny > (long long)descs[big].nx * descs[big].ny) big = i;
-        hj_params tp = par;
-        if (par.autotune == 1) CKS(hj_autotune(&descs[big], &tp, nullptr));
-        par.tile_x = tp.tile_x;
-        par.tile_y = tp.tile_y;
-        par.tile_threads = tp.tile_threads;
-        auto bucket = [&](int i) { const int m = std::max(descs[i].nx, descs[i].ny); return m <= 128 ? 0 : m <= 256 ? 1 : m <= 384 ? 2 : 3; };
-        for (int b = 0; b < 4; ++b) {
-            int rep = -1;
-            for (int i = 0; i < nprob; ++i)
-                if (bucket(i) == b && (rep < 0 || (long long)descs[i].nx * descs[i].ny > (long long)descs[rep].nx * descs[rep].ny))
-                    rep = i;
-            if (rep < 0) continue;
-            hj_params kp = par;
-            kp.autotune = 2;
-            CKS(hj_autotune(&descs[rep], &kp, nullptr));
-            for (int i = 0; i < nprob; ++i)
-                if (bucket(i) == b) kprob[i] = kp.k;
+        std::vector<int> cls(nprob);
+        for (int i = 0; i < nprob; ++i) {
+            const int m = std::max(descs[i].nx, descs[i].ny);
+            cls[i] = m <= 128 ? 0 : m <= 256 ? 1 : m <= 384 ? 2 : 3;
         }
+        std::vector<int> kc;
+        CKS(autotune_batched(descs, nprob, cls, 4, &par, &kc));
+        for (int i = 0; i < nprob; ++i) kprob[i] = kc[cls[i]];
     }
     const PersistKernelInfo *ki = find_persist(fam, 2, par.tile_x, par.tile_y, par.tile_threads);
     if (!ki) return seterr(HJ_ERR_UNSUPPORTED, "no persistent kernel for tile %dx%d", par.tile_x, par.tile_y);
     const bool bf16 = fam == FAM_BF16;
     const size_t dsz = bf16 ? 2 : 4;
+    bool sig_any = false;
+    for (int i = 0; i < nprob; ++i) sig_any |= descs[i].sigma != nullptr;
     std::vector<BProb> P(nprob);
     size_t arena = 0, maxaux = 0;
     for (int i = 0; i < nprob; ++i) {
@@ -261,6 +276,7 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
         arena += ((size_t)b.rows * b.d.ld * 8 + 255) / 256 * 256;    // u2
         arena += (b.nin * 4 + 255) / 256 * 256;                       // r32
         arena += 2 * ((b.nin * dsz + 255) / 256 * 256);               // dA, dB
+        if (sig_any) arena += (b.nin * 4 + 255) / 256 * 256;          // per-point 1/d (binary32)
         maxaux = std::max(maxaux, (size_t)aux_max_blocks(2, b.d.nx, b.d.ny));
     }
     CKS(ensure_reduction(h, maxaux));
@@ -294,6 +310,13 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
         b.r32 = (float *)ap; ap += (b.nin * 4 + 255) / 256 * 256;
         b.dA = ap; ap += (b.nin * dsz + 255) / 256 * 256;
         b.dB = ap; ap += (b.nin * dsz + 255) / 256 * 256;
+        b.dinv = nullptr;
+        if (sig_any) {
+            b.dinv = (float *)ap; ap += (b.nin * 4 + 255) / 256 * 256;
+            CKR(cudaMemsetAsync(b.dinv, 0, b.nin * 4, s));
+            CKR(launch_make_dinv_box(b.d.sigma, b.d.cD + b.d.sigma_const, b.d.ld, b.ld_in, 1, b.d.ny, 1, b.d.nx,
+                                     FAM_F32, b.dinv, s));
+        }
         CKR(cudaMemcpyAsync(b.u2, b.u, (size_t)b.rows * b.d.ld * 8, cudaMemcpyDeviceToDevice, s));
         CKR(cudaMemsetAsync(b.r32, 0, b.nin * 4, s));
         CKR(cudaMemsetAsync(b.dB, 0, b.nin * dsz, s));
@@ -305,7 +328,7 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
     auto norms = [&](bool update, const std::vector<int> &act, const std::vector<ProbState> *st) -> int {
         for (size_t j = 0; j < act.size(); ++j) {
             BProb &b = P[act[j]];
-            const CycArgs g = prob_args(b.d, par);
+            const CycArgs g = prob_args(b.d, par, transpose);
             RedArgs red;
             memset(&red, 0, sizeof(red));
             red.partials = h->partials; red.gpart = h->gpart; red.gcnt = h->gcnt; red.fcnt = h->fcnt;
@@ -313,11 +336,11 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
             red.mode = RED_STORE;
             red.scale = 1.0;
             if (!update) {
-                CKR(launch_residual_ex(2, 1, b.f, b.cur, nullptr, b.d.ld, b.ld_in, b.d.nx, b.d.ny, g.cW, g.cE, g.cS,
-                                       g.cN, g.dconst, 0, b.r32, red, s));
+                CKR(launch_residual_ex(2, 1, b.f, b.cur, b.d.sigma, b.d.ld, b.ld_in, b.d.nx, b.d.ny, g.cW, g.cE,
+                                       g.cS, g.cN, g.dconst, 0, b.r32, red, s));
             } else {
                 const void *dsel = ((*st)[j].done & 1) ? b.dB : b.dA;
-                CKR(launch_update_residual_ex(2, b.f, b.cur, dsel, bf16 ? 1 : 0, b.other, nullptr, b.r32, b.d.ld,
+                CKR(launch_update_residual_ex(2, b.f, b.cur, dsel, bf16 ? 1 : 0, b.other, b.d.sigma, b.r32, b.d.ld,
                                               b.ld_in, b.d.nx, b.d.ny, g.cW, g.cE, g.cS, g.cN, g.dconst, red, s));
                 std::swap(b.cur, b.other);
             }
@@ -350,15 +373,17 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
             BProb &b = P[i];
             CKR(cudaMemsetAsync(b.dA, 0, b.nin * dsz, s));
             PersistProblem q;
-            q.a = prob_args(b.d, par);
+            q.a = prob_args(b.d, par, transpose);
             q.a.k = kprob[i];
             q.a.ld = b.ld_in;
             q.a.f = b.r32;
             q.a.uin = b.dA;
             q.a.uout = b.dB;
+            q.a.dinv = b.dinv;
             q.a.red.tol = par.inner_tol;
             q.a.red.max_cycles = par.inner_max_cycles;
-            q.a.red.scale = q.a.dconst * q.a.dconst;
+            // the per-point-diagonal kernel forms r itself; the constant-diagonal one forms (u' - u)
+            q.a.red.scale = sig_any ? 1.0 : q.a.dconst * q.a.dconst;
             q.a.red.stall_window = par.inner_stall;
             q.a.red.stall_rtol = 1e-3;
             q.blocks_x = (b.d.nx + ki->tx - 1) / ki->tx;
@@ -366,7 +391,7 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
             pp.push_back(q);
         }
         std::vector<ProbState> st;
-        CKS(run_persistent(h, ki, false, pp, s, &st));
+        CKS(run_persistent(h, ki, sig_any, pp, s, &st));
         for (size_t j = 0; j < act.size(); ++j) {
             P[act[j]].inner_cycles += st[j].done;
             total_inner += st[j].done;
@@ -402,4 +427,34 @@ extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, c
     if (status == HJ_ERR_NOT_CONVERGED)
         return seterr(HJ_ERR_NOT_CONVERGED, "%zu problems not converged after %d outer steps", act.size(), o);
     return HJ_OK;
+}
+
+extern "C" int hj_solve_batched(hj_handle *h, int nprob, const hj_desc *descs, const void *const *f, void *const *u,
+                                hj_stream stream, hj_stats *stats, long long *cycles_out) {
+    return batched_core(h, nprob, descs, f, u, stream, stats, cycles_out, false);
+}
+
+extern "C" int hj_solve_adjoint_batched(hj_handle *h, int nrhs, const void *const *g, const void *const *u,
+                                        void *const *dl_df, void *dl_dsigma, hj_stream stream, hj_stats *stats) {
+    if (!h) return seterr(HJ_ERR_INVALID_ARG, "handle is NULL");
+    if (nrhs < 1 || !g || !u || !dl_df) return seterr(HJ_ERR_INVALID_ARG, "nrhs, g, u, dl_df");
+    if (h->d.dim != 2) return seterr(HJ_ERR_UNSUPPORTED, "batched adjoint solves are 2D");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int b = 0; b < nrhs; ++b) {
+        if (!g[b] || !u[b] || !dl_df[b] || ((uintptr_t)g[b] & 15) || ((uintptr_t)u[b] & 15) || ((uintptr_t)dl_df[b] & 15))
+            return seterr(HJ_ERR_INVALID_ARG, "rhs %d: pointers NULL or not 16-byte aligned", b);
+        // lambda_0 = 0 with a zero ghost ring (homogeneous Dirichlet data of the adjoint)
+        CKR(cudaMemsetAsync(dl_df[b], 0, h->grid_bytes, s));
+    }
+    std::vector<hj_desc> descs(nrhs, h->d);
+    const int st = batched_core(h, nrhs, descs.data(), g, dl_df, stream, stats, nullptr, true);
+    if (st != HJ_OK && st != HJ_ERR_NOT_CONVERGED) return st;
+    if (dl_dsigma) {
+        if ((uintptr_t)dl_dsigma & 15) return seterr(HJ_ERR_INVALID_ARG, "dl_dsigma not 16-byte aligned");
+        CKR(cudaMemsetAsync(dl_dsigma, 0, h->grid_elems * sizeof(double), s));
+        for (int b = 0; b < nrhs; ++b)
+            CKR(launch_grad_sigma_ex(2, 1, dl_df[b], u[b], (double *)dl_dsigma, h->d.ld, h->d.nx, h->d.ny, 1, s));
+        CKR(cudaStreamSynchronize(s));
+    }
+    return st;
 }

@@ -281,7 +281,7 @@ cudaError_t launch_update_residual_ex(int dim, const double *f, const double *ui
                                       int nx, int ny, double cW, double cE, double cS, double cN, double dconst,
                                       RedArgs red, cudaStream_t s);
 cudaError_t launch_grad_sigma_ex(int dim, int user_f64, const void *lam, const void *u, double *dsig, long long ld,
-                                 int nx, int ny, cudaStream_t s);
+                                 int nx, int ny, int accumulate, cudaStream_t s);
 int aux_max_blocks(int dim, int nx, int ny);
 int aux_sm_count();
 

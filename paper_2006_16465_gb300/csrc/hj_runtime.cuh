@@ -69,10 +69,11 @@ struct hj_handle {
     double *partials = nullptr, *gpart = nullptr, *hist = nullptr, *rstore = nullptr;
     unsigned *gcnt = nullptr, *fcnt = nullptr;
     hj::Ctl *ctl = nullptr;
-    hj::Ctl *h_ctl = nullptr, *h_ctl_init = nullptr;
+    hj::Ctl *h_ctl = nullptr, *h_ctl_init = nullptr;   // h_ctl: two slots (pipelined checks)
     double *h_hist = nullptr, *h_rstore = nullptr;
     cudaStream_t cap = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t evs[2] = {nullptr, nullptr};
     std::vector<hj::GraphEntry> graphs;
     unsigned long long stamp = 0;
     size_t max_blocks = 0, max_groups = 0;
@@ -104,5 +105,10 @@ struct PersistProblem {
 int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vector<PersistProblem> &probs,
                    cudaStream_t s, std::vector<ProbState> *out);
 int persist_capacity(hj_handle *h, const PersistKernelInfo *ki, bool sig, int *ctas);
+
+// Batched tuning (hj_autotune.cu): tile variant with a persistent kernel and
+// k per size class; cls[p] in [0, ncls).
+int autotune_batched(const hj_desc *descs, int nprob, const std::vector<int> &cls, int ncls, hj_params *par,
+                     std::vector<int> *kcls);
 
 }  // namespace hj
