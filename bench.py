@@ -218,9 +218,11 @@ def time_to_residual(torch, hj, W, tol=1e-8):
     p = W.poisson2d_uniform(512, 512, seed=1)
     f = hj.grid_from(p.f, 2, torch.float64)
     out = {}
-    for name, kw in [("hier_f32_ir", dict(tile_x=32, tile_y=32, k=32, precision="f32_ir", inner_tol=1e-4,
-                                          check_every=256)),
-                     ("classic_f64", dict(method="classic", precision="f64", check_every=1024))]:
+    for name, kw in [("hier_f32_ir_32x32_k32", dict(tile_x=32, tile_y=32, k=32, precision="f32_ir", inner_tol=1e-4,
+                                                    check_every=256)),
+                     ("hier_f32_ir_autotuned", dict(precision="f32_ir", inner_tol=1e-4, autotune=1, check_every=256)),
+                     ("classic_f64_graphs", dict(method="classic", precision="f64", check_every=1024, persistent=0)),
+                     ("classic_f64_gridsync", dict(method="classic", precision="f64", persistent=1))]:
         s = hj.Solver(p.st, tol=tol, max_cycles=5_000_000, **kw)
         u = hj.grid_from(p.u0, 2, torch.float64)
         s.solve(f, u.clone())  # warm (graphs, caches)
@@ -231,9 +233,68 @@ def time_to_residual(torch, hj, W, tol=1e-8):
         dt = time.perf_counter() - t0
         a, rel = s.residual(f, u)
         out[name] = {"seconds": dt, "cycles": r["cycles"], "outer_steps": r["outer_steps"],
-                     "rel_residual": a / r["res0"] if r["res0"] else 0.0, "status": r["status"]}
+                     "rel_residual": a / r["res0"] if r["res0"] else 0.0, "status": r["status"],
+                     "tile": [r["tile_x"], r["tile_y"], r["tile_threads"]], "k": r["k"]}
         s.close()
-    out["speedup"] = out["classic_f64"]["seconds"] / out["hier_f32_ir"]["seconds"]
+    # the faster classic variant is the baseline (the paper takes the best classic configuration)
+    best = min(out["classic_f64_graphs"]["seconds"], out["classic_f64_gridsync"]["seconds"])
+    out["speedup_32x32_vs_best_classic"] = best / out["hier_f32_ir_32x32_k32"]["seconds"]
+    out["speedup_autotuned_vs_best_classic"] = best / out["hier_f32_ir_autotuned"]["seconds"]
+    return out
+
+
+def inner_roofline(torch, hj, W, n, k=16, cycles=100):
+    """Inner sweeps bound by the binary32 FMA pipe: 4 FMAs per point update, so
+    peak = SMs x 128 lanes x max SM clock / 4 point updates per second."""
+    st, f, u0 = make_problem(n)
+    s = hj.Solver(st, tile_x=32, tile_y=32, k=k, precision="f32", fixed_cycles=cycles, check_every=cycles)
+    u = u0.clone()
+    s.solve(f, u)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.solve(f, u)
+    e1.record()
+    torch.cuda.synchronize()
+    s.close()
+    ms = e0.elapsed_time(e1)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sm_max_mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            sm_max_mhz = float(json.load(fh).get("sm_max_mhz", sm_max_mhz))
+    except Exception:
+        pass
+    peak = props.multi_processor_count * 128 * sm_max_mhz * 1e6 / 4 / 1e9
+    achieved = n * n * k * cycles / (ms / 1e3) / 1e9
+    return {"bound": "alu", "k": k, "achieved": achieved, "peak": peak, "unit": "GLUP/s", "frac": achieved / peak,
+            "peak_basis": "SMs x 128 FP32 lanes x max SM clock / 4 FMA per point update"}
+
+
+def paper_replicas(torch, hj, W):
+    """Context: the paper's timing problems (Sections 3.5 and 4.2) in binary64,
+    residual reduced by 1e-4 from x0 = 1 with b = 1: best classic vs
+    hierarchical (tpb 32 / 32x32) for each k of Tables 1 and 3."""
+    out = {}
+    for dim, tile in ((1, (32, 1)), (2, (32, 32))):
+        p = W.paper_replica(dim, 1024, copies=1024)
+        f = hj.grid_from(p.f, dim, torch.float64)
+        res = {}
+        for name, kw in [("classic_graphs", dict(method="classic", persistent=0, check_every=1024)),
+                         ("classic_gridsync", dict(method="classic", persistent=1))] + \
+                        [(f"hier_k{k}", dict(tile_x=tile[0], tile_y=tile[1], k=k)) for k in (4, 8, 16, 32, 64, 128)]:
+            s = hj.Solver(p.st, precision="f64", tol=1e-4, **kw)
+            u = hj.grid_from(p.u0, dim, torch.float64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = s.solve(f, u)
+            torch.cuda.synchronize()
+            res[name] = {"seconds": time.perf_counter() - t0, "cycles": r["cycles"], "status": r["status"]}
+            s.close()
+        best = min(res["classic_graphs"]["seconds"], res["classic_gridsync"]["seconds"])
+        res["speedup_vs_best_classic"] = {k: best / v["seconds"] for k, v in res.items() if k.startswith("hier")}
+        out[f"{dim}d"] = res
     return out
 
 
@@ -317,6 +378,8 @@ def main():
     ap.add_argument("--cycles", type=int, default=1000)
     ap.add_argument("--n", type=int, default=N_BENCH, help="grid side (profiling runs use a smaller grid)")
     ap.add_argument("--no-extras", action="store_true", help="skip classic / time-to-residual / cpu legs")
+    ap.add_argument("--paper-replicas", action="store_true",
+                    help="also time the paper's Section 3.5 / 4.2 problems (binary64, minutes)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -396,6 +459,9 @@ def main():
         extras["cfg1_1d_to_1e-6"] = time_1d(torch, hj, W)
         extras["cfg4_batched_256_to_1e-8"] = time_batched(torch, hj, W)
         extras["cfg5_differentiation_1024"] = time_differentiation(torch, hj, W)
+        extras["inner_sweep_roofline_k16"] = inner_roofline(torch, hj, W, n)
+    if args.paper_replicas and rank == 0:
+        extras["paper_replicas"] = paper_replicas(torch, hj, W)
     launches += args.steps  # one residual launch per step (the final iterate is not converged: tol = 0)
     ntiles = ((n + 31) // 32) ** 2
     pipelined = ntiles >= 8 * torch.cuda.get_device_properties(local).multi_processor_count

@@ -453,13 +453,28 @@ int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int
             const CycArgs &base, void *b0, void *b1, double tol, long long max_cycles, long long fixed, cudaStream_t s,
             RunOut *ro, double *hist_out, long long hist_cap, long long *hist_len, int *used_persistent) {
     const PersistKernelInfo *pk = classic ? nullptr : find_persist(fam, h->d.dim, ki->tx, ki->ty, ki->threads);
+    PersistKernel pclassic = nullptr;
+    if (classic) {
+        const PersistClassicInfo *pc = fam == FAM_F64 ? persist_classic_f64()
+                                       : fam == FAM_F32 ? persist_classic_f32() : persist_classic_bf16();
+        pclassic = pc->fn[h->d.dim - 1][sig ? 1 : 0];
+    }
     dim3 g, bb;
     geometry(h, ki, classic, &g, &bb);
+    // classic: items are blocks of points (the grid-stride launch shape is bounded)
+    const long long cblocks = h->d.dim == 2 ? (long long)((h->d.nx + 31) / 32) * ((h->d.ny + 7) / 8)
+                                            : (long long)((h->d.nx + 255) / 256) * h->d.ny;
     bool use = false;
-    if (pk && fixed <= 0 && max_cycles > 0 && h->p.persistent != 0) {
+    if ((pk || pclassic) && fixed <= 0 && max_cycles > 0 && h->p.persistent != 0) {
         int cap = 0;
-        CKS(persist_capacity(h, pk, sig, &cap));
-        const long long blocks = (long long)g.x * g.y;
+        if (pclassic) {
+            int occ = 0;
+            CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pclassic, 256, 0));
+            cap = occ * h->nsm;
+        } else {
+            CKS(persist_capacity(h, pk, sig, &cap));
+        }
+        const long long blocks = pclassic ? cblocks : (long long)g.x * g.y;
         if (h->p.persistent == 1) {
             if (blocks > 64LL * cap) return seterr(HJ_ERR_UNSUPPORTED, "grid too large for the persistent engine");
             use = true;
@@ -480,10 +495,10 @@ int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int
     q.a.red.stall_window = base.red.stall_window;
     q.a.red.stall_rtol = 1e-3;
     if (fam != FAM_F64 && !sig) q.a.red.scale = base.dconst * base.dconst;
-    q.blocks_x = g.x;
-    q.blocks = g.x * g.y;
+    q.blocks_x = pclassic ? 1 : g.x;
+    q.blocks = pclassic ? (int)cblocks : g.x * g.y;
     std::vector<ProbState> st;
-    CKS(run_persistent(h, pk, sig, v, s, &st));
+    CKS(run_persistent(h, pk, sig, v, s, &st, pclassic));
     ro->c = st[0].done;
     ro->status = st[0].status;
     ro->launched = st[0].cycle;

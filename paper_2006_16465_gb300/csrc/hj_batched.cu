@@ -69,7 +69,7 @@ long long env_ll(const char *name, long long dflt) {
 }  // namespace
 
 int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vector<PersistProblem> &probs,
-                   cudaStream_t s, std::vector<ProbState> *out) {
+                   cudaStream_t s, std::vector<ProbState> *out, PersistKernel classic) {
     const int nprob = (int)probs.size();
     long long nitems = 0, max_iters = 1;
     for (auto &p : probs) {
@@ -132,14 +132,22 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
     // make one CTA leave early, so that the timeout path runs without a fault)
     P.timeout_ns = (unsigned long long)env_ll("HJ_TEST_BARRIER_TIMEOUT_NS", 4000000000LL);
     P.skip_barrier_cta = (int)env_ll("HJ_TEST_SKIP_BARRIER_CTA", -1);
-    int cap = 0;
-    CKS(persist_capacity(h, ki, sig, &cap));
+    int cap = 0, threads = 256;
+    if (classic) {
+        int occ = 0;
+        CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, classic, 256, 0));
+        cap = occ * h->nsm;
+    } else {
+        CKS(persist_capacity(h, ki, sig, &cap));
+        threads = ki->threads;
+    }
     if (cap < 1) return seterr(HJ_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
     const int grid = (int)std::min<long long>(nitems, cap);
     void *args[] = {&P};
     // one problem: one grid barrier per cycle; several: two (reduce, then retire)
-    const void *fn = nprob == 1 ? (const void *)ki->one[sig] : (const void *)ki->fn[sig];
-    CKR(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(ki->threads), args, 0, s));
+    const void *fn = classic ? (const void *)classic
+                     : nprob == 1 ? (const void *)ki->one[sig] : (const void *)ki->fn[sig];
+    CKR(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, 0, s));
     CKR(cudaMemcpyAsync(hb + o_state, db + o_state, nprob * sizeof(ProbState), cudaMemcpyDeviceToHost, s));
     CKR(cudaMemcpyAsync(hb + o_bar, db + o_bar, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CKR(cudaEventRecord(h->ev, s));

@@ -51,4 +51,7 @@ static const PersistKernelInfo k_persist[] = {
 };
 const PersistKernelInfo *persist_kernels_bf16(int *n) { *n = sizeof(k_persist) / sizeof(k_persist[0]); return k_persist; }
 
+static const PersistClassicInfo k_pclassic = HJ_KPC(__nv_bfloat16, float, false);
+const PersistClassicInfo *persist_classic_bf16() { return &k_pclassic; }
+
 }  // namespace hj

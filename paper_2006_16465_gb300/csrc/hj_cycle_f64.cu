@@ -43,4 +43,7 @@ static const PersistKernelInfo k_persist[] = {
 };
 const PersistKernelInfo *persist_kernels_f64(int *n) { *n = sizeof(k_persist) / sizeof(k_persist[0]); return k_persist; }
 
+static const PersistClassicInfo k_pclassic = HJ_KPC(double, double, true);
+const PersistClassicInfo *persist_classic_f64() { return &k_pclassic; }
+
 }  // namespace hj

@@ -231,12 +231,13 @@ struct OneState {
     long long mark_c;
 };
 
-__device__ __forceinline__ bool one_decide(const PersistArgs &P, OneState &ls, int parity) {
+// count: partials written per cycle (one per item, or one per CTA)
+__device__ __forceinline__ bool one_decide(const PersistArgs &P, OneState &ls, int parity, int count) {
     const int lane = threadIdx.x & 31;
     __shared__ OneState s_ls;
     if (threadIdx.x < 32) {
         double s = 0.0;
-        for (int i = lane; i < P.nitems; i += 32) s += __ldcg(&P.partial[(size_t)parity * P.nitems + i]);
+        for (int i = lane; i < count; i += 32) s += __ldcg(&P.partial[(size_t)parity * P.nitems + i]);
         s = warp_sum(s);
         if (lane == 0) {
             const RedArgs &r = P.probs[0].red;
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(32 * NW) persist2d_one_kernel(const PersistArg
         }
         if ((int)blockIdx.x == P.skip_barrier_cta) return;
         if (!grid_barrier(P)) return;
-        if (one_decide(P, ls, parity)) return;
+        if (one_decide(P, ls, parity, P.nitems)) return;
     }
 }
 
@@ -333,7 +334,65 @@ __global__ void __launch_bounds__(32 * WPB) persist1d_one_kernel(const PersistAr
         }
         if ((int)blockIdx.x == P.skip_barrier_cta) return;
         if (!grid_barrier(P)) return;
-        if (one_decide(P, ls, parity)) return;
+        if (one_decide(P, ls, parity, P.nitems)) return;
+    }
+}
+
+// Classic global-memory Jacobi (Section 3.2) as one persistent launch for a
+// single problem: every grid-wide sweep is one cycle of the loop above, with
+// a grid barrier between sweeps instead of a kernel boundary (the grid-sync
+// variant of the classic baseline).  Items are blocks of 32 x 8 points (2D)
+// or 256 points of one row (1D), one thread per point.
+template <typename S, typename T, int D, bool EXACT, bool SIG>
+__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type classic_block(const CycArgs &a,
+                                                                                           int item) {
+    typedef typename std::conditional<EXACT, double, T>::type Acc;
+    Acc acc = 0;
+    const Coef<T> kc = make_coef<T>(a);
+    const S *__restrict__ uin = (const S *)a.uin;
+    int i, j;
+    if constexpr (D == 2) {
+        const int bxn = (a.nx + 31) / 32;
+        i = 1 + (item % bxn) * 32 + (threadIdx.x & 31);
+        j = 1 + (item / bxn) * 8 + (threadIdx.x >> 5);
+        if (i > a.nx || j > a.ny) return acc;
+    } else {
+        const int bxn = (a.nx + 255) / 256;
+        i = 1 + (item % bxn) * 256 + threadIdx.x;
+        j = item / bxn;
+        if (i > a.nx) return acc;
+    }
+    const long long q = (long long)j * a.ld + i;
+    const T old = ld_s<S, T>(uin + q);
+    const T W = ld_s<S, T>(uin + q - 1), E = ld_s<S, T>(uin + q + 1);
+    const T Sv = D == 2 ? ld_s<S, T>(uin + q - a.ld) : (T)0, Nv = D == 2 ? ld_s<S, T>(uin + q + a.ld) : (T)0;
+    const T fv = __ldg((const T *)a.f + q);
+    const T iv = SIG ? __ldg((const T *)a.dinv + q) : (T)0;
+    const T g = (EXACT || SIG) ? fv : fv * kc.invd;
+    T res = 0;
+    const T nv = point_update<T, EXACT, SIG, D == 2, true>(kc, g, iv, W, E, Sv, Nv, old, res);
+    st_s<S, T>((S *)a.uout + q, nv);
+    return (Acc)res * (Acc)res;
+}
+
+template <typename S, typename T, int D, bool EXACT, bool SIG>
+__global__ void __launch_bounds__(256) persist_classic_one_kernel(const PersistArgs P) {
+    OneState ls{-1, HJ_OK, 0, 0.0, 0.0, 0.0, 0};
+    for (long long it = 0; it < P.max_iters; ++it) {
+        const int parity = (int)(it & 1);
+        CycArgs a = P.probs[0];
+        if (ls.cycle & 1) {
+            const void *t = a.uin;
+            a.uin = a.uout;
+            a.uout = const_cast<void *>(t);
+        }
+        typename std::conditional<EXACT, double, T>::type acc = 0;
+        for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) acc += classic_block<S, T, D, EXACT, SIG>(a, item);
+        const double s = cta_sum(acc);
+        if (threadIdx.x == 0) P.partial[(size_t)parity * P.nitems + blockIdx.x] = s;
+        if ((int)blockIdx.x == P.skip_barrier_cta) return;
+        if (!grid_barrier(P)) return;
+        if (one_decide(P, ls, parity, gridDim.x)) return;
     }
 }
 
@@ -345,12 +404,20 @@ struct PersistKernelInfo {
     PersistKernel one[2];     // [sig]  one problem, one barrier per cycle
 };
 
+// Grid-sync classic baseline, one problem ([dim - 1][sig]).
+struct PersistClassicInfo {
+    PersistKernel fn[2][2];
+};
+
 }  // namespace hj
 
 #define HJ_KP2D(S, T, C, R, NW, EX) \
     {2, 32 * (C), (R) * (NW), 32 * (NW), 1, \
      {hj::persist2d_kernel<S, T, C, R, NW, EX, false>, hj::persist2d_kernel<S, T, C, R, NW, EX, true>}, \
      {hj::persist2d_one_kernel<S, T, C, R, NW, EX, false>, hj::persist2d_one_kernel<S, T, C, R, NW, EX, true>}}
+#define HJ_KPC(S, T, EX) \
+    {{{hj::persist_classic_one_kernel<S, T, 1, EX, false>, hj::persist_classic_one_kernel<S, T, 1, EX, true>}, \
+      {hj::persist_classic_one_kernel<S, T, 2, EX, false>, hj::persist_classic_one_kernel<S, T, 2, EX, true>}}}
 #define HJ_KP1D(S, T, C, WPB, EX) \
     {1, 32 * (C), 1, 32 * (WPB), (WPB), \
      {hj::persist1d_kernel<S, T, C, WPB, EX, false>, hj::persist1d_kernel<S, T, C, WPB, EX, true>}, \

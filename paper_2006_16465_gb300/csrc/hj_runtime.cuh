@@ -46,6 +46,9 @@ const PersistKernelInfo *find_persist(int fam, int dim, int tx, int ty, int thre
 const PersistKernelInfo *persist_kernels_f64(int *n);
 const PersistKernelInfo *persist_kernels_f32(int *n);
 const PersistKernelInfo *persist_kernels_bf16(int *n);
+const PersistClassicInfo *persist_classic_f64();
+const PersistClassicInfo *persist_classic_f32();
+const PersistClassicInfo *persist_classic_bf16();
 
 }  // namespace hj
 
@@ -102,8 +105,9 @@ struct PersistProblem {
     int blocks_x;     // CTAs along x (2D tiles, or 1D groups of tiles)
     int blocks;       // CTAs in total
 };
+// classic: run the grid-sync classic kernel (one problem, blocks of points as items)
 int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vector<PersistProblem> &probs,
-                   cudaStream_t s, std::vector<ProbState> *out);
+                   cudaStream_t s, std::vector<ProbState> *out, PersistKernel classic = nullptr);
 int persist_capacity(hj_handle *h, const PersistKernelInfo *ki, bool sig, int *ctas);
 
 // Batched tuning (hj_autotune.cu): tile variant with a persistent kernel and

@@ -105,7 +105,8 @@ def test_f64_classic_sweeps_match_oracle(dim):
 ])
 def test_f64_convergence_matches_oracle(dim, shape, tile, k, method, persistent):
     """persistent=1: one cooperative launch iterates all cycles (device-side
-    grid barrier); 0: CUDA graphs of check_every launches."""
+    grid barrier; for the classic method the grid-sync variant); 0: CUDA
+    graphs of check_every launches."""
     torch = _torch()
     nx, ny = shape
     if dim == 1 and ny == 1:
@@ -118,7 +119,7 @@ def test_f64_convergence_matches_oracle(dim, shape, tile, k, method, persistent)
     f = to_dev(p.f, dim, torch.float64)
     u = to_dev(p.u0, dim, torch.float64)
     out = s.solve(f, u, history=100000)
-    assert out["persistent"] == (persistent if method == "hier" else 0)
+    assert out["persistent"] == persistent
     uo, c, status, hist = oracle.solve(p.st, p.f, p.u0, tol, 10 ** 7, tile[0], tile[1], k,
                                        classic=(method == "classic"), hist_cap=100000)
     assert status == 0 and out["status"] == 0
