@@ -39,6 +39,41 @@ N_BENCH = 8192
 BYTES_PER_POINT_CYCLE = 12  # read u, read f, write u (binary32)
 
 
+# Sources that define the cycle kernel; the DRAM traffic recorded under
+# profiles/ counts only while their hash matches the one recorded with it.
+KERNEL_SOURCES = ["paper_2006_16465_gb300/csrc/hj_tma.cuh", "paper_2006_16465_gb300/csrc/hj_cycle.cuh",
+                  "paper_2006_16465_gb300/csrc/hj_internal.cuh"]
+TRAFFIC_RECORD = "profiles/ppc2d_kernel_f32_32x32_k4_poisson8192_dram.md"
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(n):
+    """DRAM bytes (read + write) per launch of the cycle kernel from the
+    committed ncu record, or None if the kernel changed since, or the record
+    is for another grid size."""
+    try:
+        rec = {}
+        with open(os.path.join(ROOT, TRAFFIC_RECORD)) as fh:
+            for line in fh:
+                if ":" in line and line.split(":")[0].strip() in ("traffic_bytes_per_launch", "kernel_source_hash",
+                                                                   "grid"):
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip().strip("`")
+        if rec.get("kernel_source_hash") != kernel_source_hash() or int(rec.get("grid", 0)) != n:
+            return None
+        return float(rec["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -471,7 +506,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _config(args, world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak, "traffic": recorded_traffic(n),
+                         "algorithmic_bytes_per_launch": BYTES_PER_POINT_CYCLE * n * n,
                          "kernel": kernel_name, "peak_kind": peak_kind},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
     line.update(extras)

@@ -13,6 +13,7 @@ static const TileKernelInfo k_tiles[] = {
     HJ_K2D(float, float, 2, 16, 2, false),    // 64 x 32
     HJ_K2D(float, float, 2, 16, 4, false),    // 64 x 64
     HJ_K2D(float, float, 4, 8, 4, false),     // 128 x 32
+    HJ_K2D(float, float, 4, 8, 8, false),     // 128 x 64
     HJ_K1D(float, float, 1, 4, false),        // 32
     HJ_K1D(float, float, 2, 4, false),        // 64
     HJ_K1D(float, float, 4, 4, false),        // 128
@@ -34,6 +35,7 @@ static const PpcKernelInfo k_ppc[] = {
     HJ_KPPC(float, float, 2, 16, 2, false, 2),   // 64 x 32
     HJ_KPPC(float, float, 2, 16, 4, false, 2),   // 64 x 64
     HJ_KPPC(float, float, 4, 8, 4, false, 2),   // 128 x 32
+    HJ_KPPC(float, float, 4, 8, 8, false, 2),   // 128 x 64
 };
 const PpcKernelInfo *ppc_kernels_f32(int *n) { *n = sizeof(k_ppc) / sizeof(k_ppc[0]); return k_ppc; }
 
@@ -44,6 +46,7 @@ static const PersistKernelInfo k_persist[] = {
     HJ_KP2D(float, float, 1, 8, 1, false),
     HJ_KP2D(float, float, 2, 16, 2, false),
     HJ_KP2D(float, float, 2, 16, 4, false),
+    HJ_KP2D(float, float, 4, 8, 8, false),
     HJ_KP1D(float, float, 1, 4, false),
     HJ_KP1D(float, float, 2, 4, false),
     HJ_KP1D(float, float, 4, 4, false),

@@ -21,7 +21,7 @@ from helpers import gpu_solver, rel_max, to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 F64_TILES_2D = [(32, 32), (32, 16), (32, 8), (32, 64), (64, 32), (64, 64)]
-F32_TILES_2D = [(32, 32), (32, 16), (32, 8), (32, 64), (64, 32), (64, 64), (128, 32)]
+F32_TILES_2D = [(32, 32), (32, 16), (32, 8), (32, 64), (64, 32), (64, 64), (128, 32), (128, 64)]
 TILES_1D = [32, 64, 128, 256]
 
 
