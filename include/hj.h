@@ -146,12 +146,18 @@ typedef struct {
     int tile_threads;     /* threads per subdomain (one warp per band of rows);
                              0 = the default for the tile shape; the built
                              combinations are listed by hj_tile_variants()      */
-    int pipeline_stages;  /* TMA-pipelined kernel: tiles in flight per CTA (2 or
-                             3; 0 = default 2)                                 */
+    int pipeline_stages;  /* TMA-pipelined kernel: shared-memory stages per CTA
+                             (binary32 / bfloat16: 1 or 2, binary64: 2; 0 = the
+                             default, the first built).  With one stage the
+                             next tile is copied in while the current one
+                             sweeps in registers                               */
     int inner_stall;      /* refinement: an inner solve also stops when ||r|| has
                              changed by <= 1e-3 (relative) over this many cycles,
                              i.e. the correction has reached the fixed point its
                              storage precision allows; 0 = off                 */
+    int ctas_per_sm;      /* TMA-pipelined kernel: resident CTAs per SM (0 = as
+                             many as fit).  Fewer CTAs keep fewer copies in
+                             flight, which HBM can serve at a higher rate     */
 } hj_params;
 
 typedef struct {
@@ -176,7 +182,7 @@ typedef struct {
  * check_every = 64, max_cycles = 10^7, tol = 1e-6, fixed_cycles = 0,
  * inner_tol = 1e-4, inner_max_cycles = 10^6, max_outer = 60, persistent = -1,
  * autotune = 0, pipeline = -1, tile_threads = 0, pipeline_stages = 0,
- * inner_stall = 32. */
+ * inner_stall = 32, ctas_per_sm = 0. */
 HJ_API void hj_default_params(hj_params *p);
 
 /* Create a solver for one problem shape.  Validates the descriptor and

@@ -205,12 +205,12 @@ void geometry(const hj_handle *h, const TileKernelInfo *ki, bool classic, dim3 *
     *block = dim3(ki->threads);
 }
 
+// Graph of M launches of fn; launch i takes args[i % period].
 template <typename Args>
-int get_graph(hj_handle *h, void (*fn)(Args), dim3 grid, dim3 block, int smem, const Args &a0, const Args &a1,
+int get_graph(hj_handle *h, void (*fn)(Args), dim3 grid, dim3 block, int smem, const Args *args, int period,
               int M, cudaGraphExec_t *out) {
-    std::vector<unsigned char> key(2 * sizeof(Args));
-    memcpy(key.data(), &a0, sizeof(Args));
-    memcpy(key.data() + sizeof(Args), &a1, sizeof(Args));
+    std::vector<unsigned char> key(period * sizeof(Args));
+    for (int j = 0; j < period; ++j) memcpy(key.data() + j * sizeof(Args), &args[j], sizeof(Args));
     for (auto &g : h->graphs) {
         if (g.fn == (const void *)fn && g.M == M && g.smem == smem && g.grid.x == grid.x && g.grid.y == grid.y &&
             g.block.x == block.x && g.block.y == block.y && g.key == key) {
@@ -227,7 +227,7 @@ int get_graph(hj_handle *h, void (*fn)(Args), dim3 grid, dim3 block, int smem, c
     }
     cudaGraph_t graph;
     CKR(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < M; ++i) fn<<<grid, block, smem, h->cap>>>((i & 1) ? a1 : a0);
+    for (int i = 0; i < M; ++i) fn<<<grid, block, smem, h->cap>>>(args[i % period]);
     cudaError_t le = cudaGetLastError();
     cudaError_t ee = cudaStreamEndCapture(h->cap, &graph);
     if (le != cudaSuccess) return seterr(HJ_ERR_CUDA, "kernel launch during capture: %s", cudaGetErrorString(le));
@@ -252,15 +252,33 @@ int get_graph(hj_handle *h, void (*fn)(Args), dim3 grid, dim3 block, int smem, c
 
 // Launch plan for one iteration kernel: either the one-CTA-per-tile kernel
 // (CycArgs) or the TMA-pipelined kernel (PpcArgs) with its two argument blocks.
+// Converging runs of the pipelined kernel rotate three iterate buffers and
+// two partial slots (period 6): launch c reads B[c % 3], writes B[(c+1) % 3]
+// and its residual partials to slot c % 2.  Its residual is folded by launch
+// c + 1 while that launch writes B[(c+2) % 3], so the iterate u_c whose
+// residual met the tolerance is still intact when the fold decides.
+constexpr int kPpcPeriod = 6;
+
 struct Plan {
     bool ppc = false;
+    bool deferred = false;   // pipelined kernel with deferred residual fold
+    int period = 2;          // argument blocks launches cycle through
     CycKernel fn = nullptr;
     PpcKernel pfn = nullptr;
     dim3 grid, block;
     int smem = 0;
-    CycArgs a0, a1;
-    PpcArgs p0, p1;
+    CycArgs a[2];
+    PpcArgs p[kPpcPeriod];
 };
+
+// Whether the TMA-pipelined kernel runs this plan's cycles.
+bool want_ppc(const hj_handle *h, const PpcKernelInfo *pi, bool classic) {
+    if (classic || !pi || h->d.dim != 2) return false;
+    if (h->p.pipeline == 1) return true;
+    if (h->p.pipeline != -1) return false;
+    const long long ntiles = (long long)((h->d.nx + pi->tx - 1) / pi->tx) * ((h->d.ny + pi->ty - 1) / pi->ty);
+    return ntiles >= 8LL * h->nsm;
+}
 
 CUtensorMapDataType tmap_type(int fam, bool storage) {
     if (fam == FAM_F64) return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
@@ -268,25 +286,24 @@ CUtensorMapDataType tmap_type(int fam, bool storage) {
     return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
 }
 
+// b2: third iterate buffer (same ghost ring as b0), required when the
+// pipelined kernel runs with the fused residual.
 int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int fam, bool classic, bool sig,
-              bool res, const CycArgs &base, void *b0, void *b1, Plan *pl) {
-    pl->a0 = base;
-    pl->a1 = base;
-    pl->a0.uin = b0; pl->a0.uout = b1;
-    pl->a1.uin = b1; pl->a1.uout = b0;
+              bool res, const CycArgs &base, void *b0, void *b1, void *b2, Plan *pl) {
+    pl->a[0] = base;
+    pl->a[1] = base;
+    pl->a[0].uin = b0; pl->a[0].uout = b1;
+    pl->a[1].uin = b1; pl->a[1].uout = b0;
+    pl->period = 2;
+    pl->deferred = false;
     const int nx = h->d.nx, ny = h->d.ny;
-    bool use_ppc = false;
-    if (!classic && pi && h->d.dim == 2) {
-        const long long ntiles = (long long)((nx + pi->tx - 1) / pi->tx) * ((ny + pi->ty - 1) / pi->ty);
-        if (h->p.pipeline == 1) use_ppc = true;
-        else if (h->p.pipeline == -1) use_ppc = ntiles >= 8LL * h->nsm;
-    }
-    if (!use_ppc) {
+    if (!want_ppc(h, pi, classic)) {
         geometry(h, ki, classic, &pl->grid, &pl->block);
         pl->fn = ki->fn[sig][res];
         pl->ppc = false;
         return HJ_OK;
     }
+    if (res && !b2) return seterr(HJ_ERR_CUDA, "internal: pipelined residual runs need a third iterate buffer");
     PpcKernel fn = pi->fn[sig][res];
     const int smem = pi->smem[sig];
     static thread_local const void *configured[64];
@@ -300,18 +317,29 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
     int occ = 0;
     CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, pi->threads, smem));
     if (occ < 1) return seterr(HJ_ERR_UNSUPPORTED, "pipelined kernel does not fit on an SM");
+    if (h->p.ctas_per_sm > 0) occ = std::min(occ, h->p.ctas_per_sm);
     const int tiles_x = (nx + pi->tx - 1) / pi->tx;
     const int ntiles = tiles_x * ((ny + pi->ty - 1) / pi->ty);
     const int ssz = fam == FAM_F64 ? 8 : fam == FAM_BF16 ? 2 : 4;
     const int tsz = fam == FAM_F64 ? 8 : 4;
     const long long ld = base.ld;
-    for (int which = 0; which < 2; ++which) {
-        PpcArgs &P = which ? pl->p1 : pl->p0;
+    const int grid = std::min(ntiles, occ * h->nsm);
+    void *bufs[3] = {b0, b1, b2};
+    pl->deferred = res;
+    pl->period = res ? kPpcPeriod : 2;
+    if (res) CKS(ensure_reduction(h, (size_t)grid));   // two slots of one partial per CTA
+    for (int j = 0; j < pl->period; ++j) {
+        PpcArgs &P = pl->p[j];
         memset(&P, 0, sizeof(P));
-        P.a = which ? pl->a1 : pl->a0;
+        P.a = base;
+        P.a.uin = res ? bufs[j % 3] : bufs[j & 1];
+        P.a.uout = res ? bufs[(j + 1) % 3] : bufs[(j + 1) & 1];
         P.tiles_x = tiles_x;
         P.ntiles = ntiles;
         P.spin_limit = 1LL << 26;
+        P.parity = j & 1;
+        P.part_w = h->partials + (size_t)(j & 1) * grid;
+        P.part_r = h->partials + (size_t)((j + 1) & 1) * grid;
         if (!make_tmap(&P.mu, P.a.uin, tmap_type(fam, true), ssz, ld, nx + 2, ny + 2, pi->bwu, pi->ty + 2) ||
             !make_tmap(&P.mf, P.a.f, tmap_type(fam, false), tsz, ld, nx + 2, ny + 2, pi->bwf, pi->ty))
             return seterr(HJ_ERR_CUDA, "cuTensorMapEncodeTiled failed (pointer alignment or pitch)");
@@ -321,19 +349,19 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
     pl->ppc = true;
     pl->pfn = fn;
     pl->smem = smem;
-    pl->grid = dim3(std::min(ntiles, occ * h->nsm));
+    pl->grid = dim3(grid);
     pl->block = dim3(pi->threads);
     return HJ_OK;
 }
 
 int plan_graph(hj_handle *h, const Plan &pl, int M, cudaGraphExec_t *ex) {
-    if (pl.ppc) return get_graph<PpcArgs>(h, pl.pfn, pl.grid, pl.block, pl.smem, pl.p0, pl.p1, M, ex);
-    return get_graph<CycArgs>(h, pl.fn, pl.grid, pl.block, 0, pl.a0, pl.a1, M, ex);
+    if (pl.ppc) return get_graph<PpcArgs>(h, pl.pfn, pl.grid, pl.block, pl.smem, pl.p, pl.period, M, ex);
+    return get_graph<CycArgs>(h, pl.fn, pl.grid, pl.block, 0, pl.a, 2, M, ex);
 }
 
 void plan_launch(const Plan &pl, long long c, cudaStream_t s) {
-    if (pl.ppc) pl.pfn<<<pl.grid, pl.block, pl.smem, s>>>((c & 1) ? pl.p1 : pl.p0);
-    else pl.fn<<<pl.grid, pl.block, 0, s>>>((c & 1) ? pl.a1 : pl.a0);
+    if (pl.ppc) pl.pfn<<<pl.grid, pl.block, pl.smem, s>>>(pl.p[c % pl.period]);
+    else pl.fn<<<pl.grid, pl.block, 0, s>>>(pl.a[c & 1]);
 }
 
 struct RunOut {
@@ -342,24 +370,33 @@ struct RunOut {
     long long launched; // cycles issued
     double res2_0;      // ||r_0||^2 (converging mode)
     double res2_c;      // ||r_c||^2 of the returned iterate if known, else -1
+    void *buf;          // the buffer that holds iterate c
+};
+
+// Where a converging run keeps its third iterate buffer (allocated on first
+// use: only the pipelined kernel's deferred residual fold needs it).
+struct ThirdBuffer {
+    void **slot;
+    size_t bytes;
 };
 
 // Iterate cycles (or classic sweeps) from b0 (holds u_0) and b1 (the other
 // buffer, same ghost ring).  fixed > 0: exactly `fixed` cycles, no residual.
 // Otherwise until ||r_c|| <= tol ||r_0|| or max_cycles.
 int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int fam, bool classic, bool sig,
-               const CycArgs &base_in, void *b0, void *b1, double tol, long long max_cycles, long long fixed,
-               cudaStream_t s, RunOut *ro, double *hist_out, long long hist_cap, long long *hist_len) {
-    const int M = h->p.check_every;
+               const CycArgs &base_in, void *b0, void *b1, ThirdBuffer third, double tol, long long max_cycles,
+               long long fixed, cudaStream_t s, RunOut *ro, double *hist_out, long long hist_cap,
+               long long *hist_len) {
+    int M = h->p.check_every;
     ro->res2_0 = -1.0;
     ro->res2_c = -1.0;
     CycArgs base = base_in;
     base.err = &h->ctl->err;
-    *h->h_ctl_init = Ctl{-1, HJ_OK, 0, 0.0, 0.0, 0, 0, 0.0, 0};
+    *h->h_ctl_init = Ctl{-1, HJ_OK, 0, 0.0, 0.0, 0, 0, 0.0, 0, 0, {0, 0}};
     CKR(cudaMemcpyAsync(h->ctl, h->h_ctl_init, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     if (fixed > 0) {
         Plan pl;
-        CKS(make_plan(h, ki, pi, fam, classic, sig, false, base, b0, b1, &pl));
+        CKS(make_plan(h, ki, pi, fam, classic, sig, false, base, b0, b1, nullptr, &pl));
         const long long reps = fixed / M;
         if (reps > 0) {
             cudaGraphExec_t ex;
@@ -375,6 +412,7 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, 
         ro->c = fixed;
         ro->status = HJ_OK;
         ro->launched = fixed;
+        ro->buf = (fixed & 1) ? b1 : b0;
         return HJ_OK;
     }
     {
@@ -390,27 +428,54 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, 
         ro->c = 0;
         ro->status = HJ_ERR_NOT_CONVERGED;
         ro->launched = 0;
+        ro->buf = b0;
         return HJ_OK;
     }
+    // the pipelined kernel folds each launch's residual in the next launch:
+    // a third buffer keeps u_c intact until that fold has decided
+    void *b2 = nullptr;
+    if (want_ppc(h, pi, classic)) {
+        if (!third.slot) return seterr(HJ_ERR_CUDA, "internal: no slot for the third iterate buffer");
+        if (!*third.slot) {
+            if (cudaMalloc(third.slot, third.bytes) != cudaSuccess) {
+                cudaGetLastError();
+                *third.slot = nullptr;
+                return seterr(HJ_ERR_NO_MEMORY, "third iterate buffer (%zu bytes)", third.bytes);
+            }
+        }
+        b2 = *third.slot;
+        CKR(cudaMemcpyAsync(b2, b0, third.bytes, cudaMemcpyDeviceToDevice, s));   // same ghost ring
+    }
     Plan pl;
-    CKS(make_plan(h, ki, pi, fam, classic, sig, true, base, b0, b1, &pl));
+    CKS(make_plan(h, ki, pi, fam, classic, sig, true, base, b0, b1, b2, &pl));
+    // residual of launch c's input is known after launch c + 1 (deferred fold)
+    const int lag = pl.deferred ? 1 : 0;
+    if (pl.deferred) M = (M + kPpcPeriod - 1) / kPpcPeriod * kPpcPeriod;
     cudaGraphExec_t ex;
     CKS(plan_graph(h, pl, M, &ex));
     const long long mask = kHistCap - 1;
     // Replays are pipelined two deep: replay i+1 is queued before the host
     // waits for replay i's control block, so the GPU does not idle while the
-    // host checks.  Replay r copies its control block into slot r % 2 and its
-    // slice of the residual ring into the pinned ring.  No replay starts at or
-    // beyond max_cycles, and launches after convergence return at once.
+    // host checks.  Replay r copies its control block into slot r % 2 and the
+    // entries of the residual ring it may have written into the pinned ring.
+    // No replay starts beyond the launch that settles max_cycles, and launches
+    // after convergence return at once.
     long long issued = 0;   // replays queued
+    auto copy_ring = [&](long long lo, long long n) -> int {
+        while (n > 0) {
+            const long long p0 = lo & mask;
+            const long long k = std::min<long long>(n, kHistCap - p0);
+            CKR(cudaMemcpyAsync(h->h_hist + p0, h->hist + p0, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+            lo += k;
+            n -= k;
+        }
+        return HJ_OK;
+    };
     auto issue = [&]() -> int {
         const long long r = issued;
         CKR(cudaGraphLaunch(ex, s));
-        const long long p0 = (r * M) & mask;
-        const long long n0 = std::min<long long>(M, kHistCap - p0);
-        CKR(cudaMemcpyAsync(h->h_hist + p0, h->hist + p0, n0 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        if (n0 < M)
-            CKR(cudaMemcpyAsync(h->h_hist, h->hist, (M - n0) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        const long long lo = std::max(0LL, r * M - lag);
+        CKS(copy_ring(lo, (r + 1) * M - lo));
         CKR(cudaMemcpyAsync(h->h_ctl + (r & 1), h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         CKR(cudaEventRecord(h->evs[r & 1], s));
         ++issued;
@@ -420,7 +485,7 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, 
     long long copied = 0, checked = 0;
     const Ctl *last = nullptr;
     for (;;) {
-        if (issued * M < max_cycles) CKS(issue());
+        if (issued * M < max_cycles + lag) CKS(issue());
         CKR(cudaEventSynchronize(h->evs[checked & 1]));
         last = h->h_ctl + (checked & 1);
         ++checked;
@@ -444,14 +509,21 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, 
     ro->launched = launched;
     ro->res2_0 = last->res2_0;
     if (ro->status == HJ_OK || ro->status == HJ_ERR_DIVERGED) ro->res2_c = h->h_hist[ro->c & mask];
+    if (pl.deferred) {
+        void *bufs[3] = {b0, b1, b2};
+        ro->buf = bufs[ro->c % 3];
+    } else {
+        ro->buf = (ro->c & 1) ? b1 : b0;
+    }
     return HJ_OK;
 }
 
 // Iterate with the persistent engine when every block of the grid can be
 // resident at once (or when forced), else with graph-captured launches.
 int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int fam, bool classic, bool sig,
-            const CycArgs &base, void *b0, void *b1, double tol, long long max_cycles, long long fixed, cudaStream_t s,
-            RunOut *ro, double *hist_out, long long hist_cap, long long *hist_len, int *used_persistent) {
+            const CycArgs &base, void *b0, void *b1, ThirdBuffer third, double tol, long long max_cycles,
+            long long fixed, cudaStream_t s, RunOut *ro, double *hist_out, long long hist_cap, long long *hist_len,
+            int *used_persistent) {
     const PersistKernelInfo *pk = classic ? nullptr : find_persist(fam, h->d.dim, ki->tx, ki->ty, ki->threads);
     PersistKernel pclassic = nullptr;
     if (classic) {
@@ -484,8 +556,8 @@ int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int
     }
     if (used_persistent) *used_persistent = use ? 1 : 0;
     if (!use)
-        return run_cycles(h, ki, pi, fam, classic, sig, base, b0, b1, tol, max_cycles, fixed, s, ro, hist_out,
-                          hist_cap, hist_len);
+        return run_cycles(h, ki, pi, fam, classic, sig, base, b0, b1, third, tol, max_cycles, fixed, s, ro,
+                          hist_out, hist_cap, hist_len);
     std::vector<PersistProblem> v(1);
     PersistProblem &q = v[0];
     q.a = base;
@@ -504,6 +576,7 @@ int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int
     ro->launched = st[0].cycle;
     ro->res2_0 = st[0].res2_0;
     ro->res2_c = (ro->status == HJ_OK || ro->status == HJ_ERR_DIVERGED) ? st[0].res2_last : -1.0;
+    ro->buf = (ro->c & 1) ? b1 : b0;
     if (hist_out) {
         const long long ncomp = st[0].cycle;
         const long long lo = std::max(0LL, ncomp - (long long)kHistCap);
@@ -541,10 +614,10 @@ int solve_plain(hj_handle *h, const void *f, void *u, bool transpose, cudaStream
     RunOut ro;
     long long hl = 0;
     int persist = 0;
-    CKS(iterate(h, ki, classic ? nullptr : h->p_outer, h->fam_outer, classic, sig, base, u, h->ubuf, h->p.tol,
-                h->p.max_cycles, h->p.fixed_cycles, s, &ro, st ? st->history : nullptr, st ? st->history_cap : 0,
-                &hl, &persist));
-    if (ro.c & 1) CKR(cudaMemcpyAsync(u, h->ubuf, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+    CKS(iterate(h, ki, classic ? nullptr : h->p_outer, h->fam_outer, classic, sig, base, u, h->ubuf,
+                ThirdBuffer{&h->ubuf2, h->grid_bytes}, h->p.tol, h->p.max_cycles, h->p.fixed_cycles, s, &ro,
+                st ? st->history : nullptr, st ? st->history_cap : 0, &hl, &persist));
+    if (ro.buf != u) CKR(cudaMemcpyAsync(u, ro.buf, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
     double res0 = -1.0, resc = -1.0;
     if (h->p.fixed_cycles <= 0) {
         res0 = sqrt(std::max(ro.res2_0, 0.0));
@@ -610,11 +683,12 @@ int solve_ir(hj_handle *h, const double *f, double *u, bool transpose, cudaStrea
         if (o >= h->p.max_outer) { status = HJ_ERR_NOT_CONVERGED; break; }
         CKR(cudaMemsetAsync(h->dA, 0, (size_t)h->rows * h->ld_in * dsz, s));
         RunOut ro;
-        CKS(iterate(h, h->k_inner, h->p_inner, h->fam_inner, false, sig, base, h->dA, h->dB, h->p.inner_tol,
-                    h->p.inner_max_cycles, 0, s, &ro, nullptr, 0, nullptr, &persist));
+        CKS(iterate(h, h->k_inner, h->p_inner, h->fam_inner, false, sig, base, h->dA, h->dB,
+                    ThirdBuffer{&h->dC, (size_t)h->rows * h->ld_in * dsz}, h->p.inner_tol, h->p.inner_max_cycles, 0,
+                    s, &ro, nullptr, 0, nullptr, &persist));
         inner_total += ro.c;
         inner_launched += ro.launched;
-        const void *dsel = (ro.c & 1) ? h->dB : h->dA;
+        const void *dsel = ro.buf;
         const RedArgs red = red_args(h, RED_STORE, 0.0, 0);
         CKR(launch_update_residual_ex(h->d.dim, f, cur, dsel, bf16 ? 1 : 0, other, h->d.sigma, h->r32, h->d.ld,
                                       h->ld_in, h->d.nx, h->d.ny, geo.cW, geo.cE, geo.cS, geo.cN, geo.dconst, red,
@@ -696,6 +770,7 @@ void hj_default_params(hj_params *p) {
     p->autotune = 0;
     p->pipeline = -1;
     p->inner_stall = 32;
+    p->ctas_per_sm = 0;
 }
 
 const char *hj_error_string(int s) {
@@ -752,7 +827,7 @@ int hj_tile_shapes(int dim, int precision, int *xy, int cap) {
 void hj_destroy(hj_handle *h) {
     if (!h) return;
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
-    void *dev[] = {h->ubuf, h->dinv_outer, h->dinv32, h->r32, h->dA, h->dB, h->hf, h->hu, h->partials, h->gpart,
+    void *dev[] = {h->ubuf, h->ubuf2, h->dC, h->dinv_outer, h->dinv32, h->r32, h->dA, h->dB, h->hf, h->hu, h->partials, h->gpart,
                    h->hist, h->rstore, h->gcnt, h->fcnt, h->ctl, h->pscratch, h->barena, h->rs};
     for (void *p : dev)
         if (p) cudaFree(p);
@@ -795,6 +870,7 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     if (ir && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)) return seterr(HJ_ERR_INVALID_ARG, "inner_tol must be in (0,1)");
     if (ir && p.inner_max_cycles < 1) return seterr(HJ_ERR_INVALID_ARG, "inner_max_cycles must be >= 1");
     if (p.inner_stall < 0) return seterr(HJ_ERR_INVALID_ARG, "inner_stall must be >= 0");
+    if (p.ctas_per_sm < 0) return seterr(HJ_ERR_INVALID_ARG, "ctas_per_sm must be >= 0");
     if (ir && p.method == HJ_METHOD_CLASSIC) return seterr(HJ_ERR_UNSUPPORTED, "refinement uses hierarchical cycles");
     if (p.check_every < 1) p.check_every = 1;
     if (p.check_every > 4096) p.check_every = 4096;

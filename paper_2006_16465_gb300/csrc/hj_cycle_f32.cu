@@ -1,6 +1,5 @@
 // Binary32 cycle kernels (fused multiply-add chains).
 #include "hj_persist.cuh"
-#include "hj_tma.cuh"
 
 namespace hj {
 
@@ -23,21 +22,6 @@ static const TileKernelInfo k_classic[] = {HJ_KC2D(float, float, false), HJ_KC1D
 
 const TileKernelInfo *tile_kernels_f32(int *n) { *n = sizeof(k_tiles) / sizeof(k_tiles[0]); return k_tiles; }
 const TileKernelInfo *classic_kernels_f32(int *n) { *n = 2; return k_classic; }
-
-static const PpcKernelInfo k_ppc[] = {
-    HJ_KPPC(float, float, 1, 32, 1, false, 2),   // 32 x 32
-    HJ_KPPC(float, float, 1, 16, 2, false, 2),   // 32 x 32, two warps
-    HJ_KPPC(float, float, 1, 32, 1, false, 3),   // 32 x 32, three stages
-    HJ_KPPC(float, float, 1, 16, 2, false, 3),   // 32 x 32, two warps, three stages
-    HJ_KPPC(float, float, 1, 16, 1, false, 2),   // 32 x 16
-    HJ_KPPC(float, float, 1, 8, 1, false, 2),   // 32 x 8
-    HJ_KPPC(float, float, 1, 32, 2, false, 2),   // 32 x 64
-    HJ_KPPC(float, float, 2, 16, 2, false, 2),   // 64 x 32
-    HJ_KPPC(float, float, 2, 16, 4, false, 2),   // 64 x 64
-    HJ_KPPC(float, float, 4, 8, 4, false, 2),   // 128 x 32
-    HJ_KPPC(float, float, 4, 8, 8, false, 2),   // 128 x 64
-};
-const PpcKernelInfo *ppc_kernels_f32(int *n) { *n = sizeof(k_ppc) / sizeof(k_ppc[0]); return k_ppc; }
 
 static const PersistKernelInfo k_persist[] = {
     HJ_KP2D(float, float, 1, 32, 1, false),

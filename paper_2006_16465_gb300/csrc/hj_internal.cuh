@@ -29,6 +29,10 @@ struct Ctl {
     int pad;
     double res2_mark;    // stagnation rule: ||r||^2 at cycle mark_cycle
     long long mark_cycle;
+    // deferred fold (TMA-pipelined kernel): launches started, and per launch
+    // parity whether the launch only folds its predecessor's partials
+    long long launch;
+    int fold_only[2];
 };
 
 constexpr int kHistCap = 1 << 17;  // device ring of per-cycle ||r_c||^2 (power of two)
@@ -213,6 +217,27 @@ __device__ __forceinline__ void reduce_grid(const RedArgs &r, const double (&val
         }
         __threadfence();
     }
+}
+
+// Deferred fold: one warp sums n per-CTA partials written by the previous
+// launch (fixed order: lane-strided, four interleaved accumulators, then the
+// butterfly) and folds ||r||^2 into the control block.  The kernel boundary
+// orders those writes before these loads; __ldcg skips stale L1 lines.
+__device__ __forceinline__ void fold_partials(const RedArgs &r, const double *part, int n) {
+    const int lane = threadIdx.x & 31;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int b = lane;
+    for (; b + 96 < n; b += 128) {
+        const double x0 = __ldcg(part + b), x1 = __ldcg(part + b + 32);
+        const double x2 = __ldcg(part + b + 64), x3 = __ldcg(part + b + 96);
+        s0 += x0;
+        s1 += x1;
+        s2 += x2;
+        s3 += x3;
+    }
+    for (; b < n; b += 32) s0 += __ldcg(part + b);
+    const double s = warp_sum((s0 + s1) + (s2 + s3));
+    if (lane == 0) finish_cycle(r, s * r.scale);
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {

@@ -64,10 +64,12 @@ struct hj_handle {
     const hj::PpcKernelInfo *p_outer = nullptr, *p_inner = nullptr;   // TMA-pipelined variants (2D)
     long long ld_in = 0;          // row pitch of the refinement's binary32 / bfloat16 arrays
     void *ubuf = nullptr;
+    void *ubuf2 = nullptr;        // third iterate buffer (pipelined kernel, deferred residual fold)
     void *dinv_outer = nullptr;   // per-point 1/d in the outer compute type (sigma given)
     float *dinv32 = nullptr;      // per-point 1/d in binary32 (refinement, sigma given)
     float *r32 = nullptr;         // refinement: binary32 residual (inner RHS)
     void *dA = nullptr, *dB = nullptr;  // refinement: correction buffers
+    void *dC = nullptr;                 // refinement: third correction buffer (as ubuf2)
     void *hf = nullptr, *hu = nullptr;  // staging for host-pointer solves
     double *partials = nullptr, *gpart = nullptr, *hist = nullptr, *rstore = nullptr;
     unsigned *gcnt = nullptr, *fcnt = nullptr;

@@ -7,7 +7,8 @@
 // next NST tiles' iterate box (tile + halo) and RHS box into shared memory,
 // completing on an mbarrier, while the warps sweep the current tile in
 // registers; the interior goes back to HBM with plain coalesced stores from
-// registers.  The residual of the whole CTA's tiles is reduced once per CTA.
+// registers.  The residual of the whole CTA's tiles becomes one partial per
+// CTA, folded by the next launch (no atomics or fences at the kernel's end).
 // Every wait on an mbarrier is bounded; on expiry the kernel records the
 // error in the control block, drains its own copies (bounded) and returns.
 #pragma once
@@ -25,6 +26,13 @@ struct PpcArgs {
     CycArgs a;
     int tiles_x, ntiles;
     long long spin_limit;   // polls of an mbarrier before giving up
+    // Fused residual (deferred fold): this launch writes one partial of
+    // ||f - A u_c||^2 per CTA into part_w; the last CTA of the next launch
+    // folds them (part_r there) into the control block.  parity = launch
+    // index mod 2 selects the launch's fold_only flag.
+    double *part_w;
+    const double *part_r;
+    int parity;
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -85,13 +93,56 @@ struct PpcLayout {
     static constexpr int SMEM = XB_OFF + XB_BYTES + 128;   // + room to align the base to 128 bytes
 };
 
+// Deferred fold, run by one warp of the last CTA of a launch: fold the
+// previous launch's partials (residual of the iterate that launch staged),
+// then decide whether the next launch only folds (its iterate would lie
+// beyond max_cycles).  The launch counter and the flags are touched by this
+// warp only, one launch after another.
+__device__ __forceinline__ void deferred_fold(const PpcArgs &P) {
+    volatile Ctl *ctl = P.a.red.ctl;
+    const long long l = ctl->launch;
+    if (l >= 1) fold_partials(P.a.red, P.part_r, (int)gridDim.x);
+    if ((threadIdx.x & 31) == 0) {
+        ctl->fold_only[P.parity ^ 1] = (l + 1 >= P.a.red.max_cycles) ? 1 : 0;
+        ctl->launch = l + 1;
+    }
+}
+
+// One partial of the CTA's residual share, written without atomics: the next
+// launch reads it after this kernel has completed.
+template <int NW, typename A>
+__device__ __forceinline__ void write_cta_partial(double *out, A acc) {
+    double v;
+    if constexpr (std::is_same<A, float>::value) v = (double)warp_sum_f(acc);
+    else v = warp_sum((double)acc);
+    if constexpr (NW == 1) {
+        if (threadIdx.x == 0) out[blockIdx.x] = v;
+    } else {
+        __shared__ double s_w[NW];
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) t += s_w[w];
+            out[blockIdx.x] = t;
+        }
+    }
+}
+
 template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG, bool RES, int NST>
 __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ PpcArgs P) {
     using L = PpcLayout<S, T, C, R, NW, SIG, NST>;
     constexpr int TX = L::TX, TY = L::TY;
     const CycArgs &a = P.a;
+    const bool reducer = blockIdx.x == gridDim.x - 1;
     if constexpr (RES) {
-        if (*(volatile int *)&a.red.ctl->done >= 0) return;
+        volatile Ctl *ctl = a.red.ctl;
+        if (ctl->done >= 0) return;
+        if (ctl->fold_only[P.parity]) {
+            if (reducer && threadIdx.x < 32) deferred_fold(P);
+            return;
+        }
     }
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // copy destinations must be 128-byte aligned: align the dynamic base explicitly
@@ -118,6 +169,11 @@ __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ 
     __syncthreads();
     if (tid == 0) {
         for (int i = 0; i < NST && i < mine; ++i) issue(i, blockIdx.x + i * gridDim.x);
+    }
+    // the last CTA has the fewest tiles when the grid does not divide them:
+    // it folds the previous launch's residual while its first copies land
+    if constexpr (RES) {
+        if (reducer && tid < 32) deferred_fold(P);
     }
     const Coef<T> kc = make_coef<T>(a);
     typedef typename std::conditional<EXACT, double, T>::type Acc;
@@ -167,7 +223,7 @@ __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ 
         __syncthreads();
         return;
     }
-    if constexpr (RES) reduce_grid_acc(a.red, acc);
+    if constexpr (RES) write_cta_partial<NW>(P.part_w, acc);
 }
 
 }  // namespace hj

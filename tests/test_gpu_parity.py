@@ -132,6 +132,107 @@ def test_f64_convergence_matches_oracle(dim, shape, tile, k, method, persistent)
     s.close()
 
 
+# The TMA-pipelined kernel folds each launch's residual partials in the next
+# launch and rotates three iterate buffers; these cases pin that control path
+# (forced with pipeline=1, persistent=0) to the oracle's stopping rule.
+PIPE = dict(pipeline=1, persistent=0)
+
+
+@pytest.mark.parametrize("check_every", [16, 6, 7])
+@pytest.mark.parametrize("shape,tile,k,sigma", [
+    ((96, 80), (32, 32), 8, "field"),
+    ((70, 45), (32, 16), 4, "const"),
+    ((130, 97), (64, 32), 16, "none"),
+])
+def test_f64_pipelined_convergence_matches_oracle(shape, tile, k, sigma, check_every):
+    torch = _torch()
+    nx, ny = shape
+    p = W.random_bc_problem(2, nx, ny, seed=nx + 3, sigma_kind=sigma)
+    tol = 1e-6
+    s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=k, precision="f64", tol=tol, check_every=check_every,
+                   **PIPE)
+    f = to_dev(p.f, 2, torch.float64)
+    u = to_dev(p.u0, 2, torch.float64)
+    out = s.solve(f, u, history=100000)
+    assert out["persistent"] == 0
+    uo, c, status, hist = oracle.solve(p.st, p.f, p.u0, tol, 10 ** 7, tile[0], tile[1], k, hist_cap=100000)
+    assert status == 0 and out["status"] == 0
+    assert out["cycles"] == c
+    assert np.array_equal(to_host(u, nx), uo)
+    gh = np.array(out["history"])
+    assert len(gh) == c + 1
+    np.testing.assert_allclose(gh, hist[:c + 1], rtol=1e-9, atol=1e-12 * hist[0])
+    assert out["res_final"] == pytest.approx(hist[c], rel=1e-9)
+    s.close()
+
+
+@pytest.mark.parametrize("max_cycles", [1, 2, 5, 6, 7, 13])
+def test_pipelined_cycle_cap_returns_last_iterate(max_cycles):
+    torch = _torch()
+    import paper_2006_16465_gb300 as hj
+    p = W.random_bc_problem(2, 72, 66, seed=max_cycles, sigma_kind="field", asym=True)
+    s = gpu_solver(p, tile_x=32, tile_y=32, k=3, precision="f64", tol=1e-14, max_cycles=max_cycles,
+                   check_every=4, **PIPE)
+    f = to_dev(p.f, 2, torch.float64)
+    u = to_dev(p.u0, 2, torch.float64)
+    out = s.solve(f, u, check=False, history=64)
+    assert out["status"] == hj.HJ_ERR_NOT_CONVERGED and out["cycles"] == max_cycles
+    ref = oracle.run_fixed(p.st, p.f, p.u0, max_cycles, 32, 32, 3)
+    assert np.array_equal(to_host(u, 72), ref)
+    assert out["res_final"] == pytest.approx(oracle.residual(p.st, p.f, ref), rel=1e-12)
+    # every folded residual is in the history: ||r_0|| .. ||r_{max_cycles-1}||
+    assert len(out["history"]) == max_cycles
+    s.close()
+
+
+def test_pipelined_zero_rhs_converges_at_cycle_zero_and_nan_diverges():
+    torch = _torch()
+    import paper_2006_16465_gb300 as hj
+    p = W.poisson2d_uniform(64, 64, seed=3)
+    s = gpu_solver(p, precision="f64", tol=1e-8, **PIPE)
+    out = s.solve(to_dev(W.zeros_grid(p.st), 2, torch.float64), to_dev(W.zeros_grid(p.st), 2, torch.float64))
+    assert out["status"] == 0 and out["cycles"] == 0 and out["res_final"] == 0.0
+    fh = p.f.copy()
+    fh[10, 10] = np.nan
+    out = s.solve(to_dev(fh, 2, torch.float64), to_dev(p.u0, 2, torch.float64), check=False)
+    assert out["status"] == hj.HJ_ERR_DIVERGED
+    s.close()
+
+
+def test_pipelined_reuse_with_new_boundary_values():
+    """The third buffer takes each solve's ghost ring (Dirichlet data)."""
+    torch = _torch()
+    s = None
+    for seed in (11, 12, 13):
+        p = W.random_bc_problem(2, 80, 70, seed=seed, sigma_kind="none")
+        if s is None:
+            s = gpu_solver(p, tile_x=32, tile_y=32, k=4, precision="f64", tol=1e-7, check_every=12, **PIPE)
+        u = to_dev(p.u0, 2, torch.float64)
+        out = s.solve(to_dev(p.f, 2, torch.float64), u)
+        uo, c, status, _ = oracle.solve(p.st, p.f, p.u0, 1e-7, 10 ** 7, 32, 32, 4)
+        assert out["cycles"] == c and np.array_equal(to_host(u, 80), uo), seed
+    s.close()
+
+
+def test_f32_pipelined_solve_matches_graph_solve():
+    """Binary32 with the pipelined kernel: same stopping cycle and iterate as
+    the one-CTA-per-tile kernel (same arithmetic per point)."""
+    torch = _torch()
+    p = W.poisson2d_uniform(160, 128, seed=4)
+    outs = []
+    for eng in (PIPE, dict(pipeline=0, persistent=0)):
+        s = gpu_solver(p, tile_x=32, tile_y=32, k=8, precision="f32", tol=1e-5, check_every=10, **eng)
+        u = to_dev(p.u0, 2, torch.float32)
+        out = s.solve(to_dev(p.f, 2, torch.float32), u, history=100000)
+        assert out["status"] == 0
+        outs.append((out, to_host(u, 160)))
+        s.close()
+    (a, ua), (b, ub) = outs
+    assert a["cycles"] == b["cycles"]
+    assert np.array_equal(ua, ub)
+    np.testing.assert_allclose(a["history"], b["history"], rtol=1e-6)
+
+
 def test_residual_api_matches_oracle():
     torch = _torch()
     for dim, nx, ny in [(2, 90, 70), (1, 333, 3)]:
