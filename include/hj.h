@@ -138,6 +138,9 @@ typedef struct {
                              -1: choose automatically                            */
     int autotune;         /* 1: pick tile shape and k by measurement (hj_autotune)
                              at hj_create; 2: keep tile_x, tile_y and tune k only;
+                             3: keep tile and k, tune only the pipelined kernel's
+                             launch (threads per subdomain, copy stages, CTAs
+                             per SM; 1 and 2 tune it too after their pick);
                              hj_solve_batched: tile from the largest problem,
                              k per size class                                   */
     int pipeline;         /* 2D cycles: 1 = TMA-pipelined kernel (CTAs walk tile
@@ -176,6 +179,8 @@ typedef struct {
     int tile_x, tile_y, k;    /* configuration actually used                     */
     int tile_threads;         /* threads per subdomain actually used             */
     int persistent;           /* 1 if the persistent path ran                    */
+    int pipeline_stages;      /* copy stages of the pipelined kernel if it runs, else 0 */
+    int ctas_per_sm;          /* its CTAs-per-SM cap (0 = as many as fit)         */
 } hj_stats;
 
 /* Fill p with defaults: hierarchical, 32 x 32 tiles, k = 16, HJ_PREC_F64,
@@ -258,7 +263,11 @@ HJ_API const char *hj_last_error(void);
  * in that file.  *predicted_ms (nullable) receives the predicted time to
  * tolerance, or -1 for a cache hit.  hj_create runs this when
  * params->autotune is 1; params->autotune = 2 keeps tile_x, tile_y and tunes
- * k only. */
+ * k only.  Where the TMA-pipelined kernel runs the cycles (2D grids of at least
+ * 8 subdomains per SM, or pipeline = 1), every mode then measures its launch
+ * shapes for the chosen subdomain and k (threads per subdomain, copy stages,
+ * CTAs per SM) and writes the fastest into tile_threads, pipeline_stages and
+ * ctas_per_sm; params->autotune = 3 does only that. */
 HJ_API int hj_autotune(const hj_desc *desc, hj_params *params, double *predicted_ms);
 
 /* Runs params->fixed_cycles cycles (hierarchical, or classic sweeps with

@@ -742,6 +742,10 @@ void fill_stats_config(const hj_handle *h, hj_stats *st, double t0) {
     st->tile_y = h->d.dim == 2 ? h->p.tile_y : 1;
     st->k = h->p.k;
     st->tile_threads = h->ir ? h->k_inner->threads : h->k_outer ? h->k_outer->threads : 0;
+    const PpcKernelInfo *pk = h->ir ? h->p_inner : h->p_outer;
+    const bool ppc = want_ppc(h, pk, h->p.method == HJ_METHOD_CLASSIC);
+    st->pipeline_stages = ppc ? pk->stages : 0;
+    st->ctas_per_sm = ppc ? h->p.ctas_per_sm : 0;
 }
 
 }  // namespace
@@ -876,7 +880,8 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     if (p.check_every > 4096) p.check_every = 4096;
     p.check_every += p.check_every & 1;
     if (d.dim == 1) p.tile_y = 1;
-    if (p.autotune == 1 || p.autotune == 2) {
+    if (p.autotune < 0 || p.autotune > 3) return seterr(HJ_ERR_INVALID_ARG, "autotune must be 0, 1, 2 or 3");
+    if (p.autotune != 0) {
         hj_params tp = p;
         const int st = hj_autotune(&d, &tp, nullptr);
         if (st != HJ_OK) return st;
@@ -884,6 +889,8 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
         p.tile_y = tp.tile_y;
         p.tile_threads = tp.tile_threads;
         p.k = tp.k;
+        p.pipeline_stages = tp.pipeline_stages;
+        p.ctas_per_sm = tp.ctas_per_sm;
     }
 
     // diagonal dominance (Section 2.1): d_p >= |cW| + |cE| + |cS| + |cN|, d_p > 0

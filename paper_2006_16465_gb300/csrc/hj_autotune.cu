@@ -13,7 +13,10 @@
 //   * time per cycle t: CUDA events around the same run (graph path with the
 //     fused residual, as a real solve runs);
 //   * predicted time to the tolerance: ln(tol) / ln(rho) * t.
-// The candidate with the smallest prediction wins.  Results are cached per
+// The candidate with the smallest prediction wins.  Where the TMA-pipelined
+// kernel runs the cycles (large 2D grids), its launch shape is tuned next
+// (tune_launch: threads per subdomain, copy stages, CTAs per SM by measured
+// time per cycle); autotune = 3 tunes only that.  Results are cached per
 // process and, if HJ_AUTOTUNE_CACHE names a file, in that file (one line per
 // key: "key tile_x tile_y threads k").
 #include <algorithm>
@@ -185,11 +188,149 @@ bool measure(Scratch &sc, int prec, int tx, int ty, int th, int k, const hj_para
     return ok && std::isfinite(best);
 }
 
+// Time per cycle of the pipelined kernel for one launch shape: threads per
+// subdomain th, copy stages, CTAs per SM (0 = as many as fit); converging
+// mode (fused residual, deferred fold) as a real solve runs.  Best of three
+// runs after a warm-up, minus the closing residual pass.
+bool measure_launch(Scratch &sc, int prec, int tx, int ty, int th, int stages, int cps, int k, double *us) {
+    constexpr int kL = 48;   // cycles per run (a multiple of the pipelined graph period)
+    hj_params tp;
+    hj_default_params(&tp);
+    tp.tile_x = tx;
+    tp.tile_y = ty;
+    tp.tile_threads = th;
+    tp.pipeline_stages = stages;
+    tp.ctas_per_sm = cps;
+    tp.k = k;
+    tp.precision = prec;
+    tp.tol = 0.0;
+    tp.max_cycles = kL;
+    tp.check_every = kL;
+    tp.persistent = 0;
+    tp.pipeline = 1;
+    hj_handle *h = nullptr;
+    if (hj_create(&h, &sc.td, &tp) != HJ_OK) return false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = INFINITY;
+    bool ok = true;
+    for (int rep = 0; rep < 4 && ok; ++rep) {   // run 0 builds the graph and warms caches
+        if (sc.esz == 8) fill_mode_kernel<double><<<256, 256>>>((double *)sc.u, sc.ld, sc.td.nx, sc.td.ny, sc.td.dim);
+        else fill_mode_kernel<float><<<256, 256>>>((float *)sc.u, sc.ld, sc.td.nx, sc.td.ny, sc.td.dim);
+        float t = 0.f, tr = 0.f;
+        cudaEventRecord(e0, 0);
+        const int code = hj_solve(h, sc.f, sc.u, nullptr, nullptr);
+        cudaEventRecord(e1, 0);
+        cudaEventSynchronize(e1);
+        if (code != HJ_OK && code != HJ_ERR_NOT_CONVERGED) { ok = false; break; }
+        cudaEventElapsedTime(&t, e0, e1);
+        cudaEventRecord(e0, 0);
+        hj_residual(h, sc.f, sc.u, nullptr, nullptr, nullptr);
+        cudaEventRecord(e1, 0);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&tr, e0, e1);
+        if (rep > 0) best = std::min(best, 1e3 * (double)std::max(t - tr, 1e-3f) / kL);
+    }
+    hj_destroy(h);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    *us = best;
+    return ok && std::isfinite(best);
+}
+
+// Launch shape of the pipelined kernel for a fixed subdomain shape and k:
+// which threads-per-subdomain variant, how many copy stages, how many CTAs per
+// SM.  How many copies are in flight per SM decides how well HBM serves the
+// staging pattern, and the best residency is not monotonic in the CTA count,
+// so it is measured on the problem's own grid.  Leaves *p unchanged when the
+// pipelined kernel would not run (1D, small grids, pipeline = 0).
+int tune_launch(const hj_desc &d, hj_params *p) {
+    if (d.dim != 2 || p->pipeline == 0 || p->method == HJ_METHOD_CLASSIC) return HJ_OK;
+    const bool ir = p->precision == HJ_PREC_F32_IR || p->precision == HJ_PREC_BF16CORR_IR;
+    const int prec = ir ? HJ_PREC_F32 : p->precision;
+    const int fam = prec == HJ_PREC_F64 ? FAM_F64 : FAM_F32;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long ntiles = (long long)((d.nx + p->tile_x - 1) / p->tile_x) * ((d.ny + p->tile_y - 1) / p->tile_y);
+    if (p->pipeline == -1 && ntiles < 8LL * nsm) return HJ_OK;
+    std::string key = make_key(d, p->precision, p->tol);
+    {
+        char extra[96];
+        snprintf(extra, sizeof(extra), "_launch%dx%dt%dk%d", p->tile_x, p->tile_y, p->tile_threads, p->k);
+        key += extra;
+        std::lock_guard<std::mutex> lk(g_mu);
+        load_cache_file();
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            p->tile_threads = it->second[0];
+            p->pipeline_stages = it->second[1];
+            p->ctas_per_sm = it->second[2];
+            return HJ_OK;
+        }
+    }
+    int n = 0;
+    const PpcKernelInfo *ks = fam == FAM_F64 ? ppc_kernels_f64(&n) : ppc_kernels_f32(&n);
+    const bool sig = d.sigma != nullptr;
+    Scratch sc;
+    CKS(sc.init(d, prec));
+    double best = INFINITY;
+    int bth = p->tile_threads, bst = p->pipeline_stages, bcps = p->ctas_per_sm;
+    for (int i = 0; i < n; ++i) {
+        const PpcKernelInfo &e = ks[i];
+        if (e.tx != p->tile_x || e.ty != p->tile_y) continue;
+        if (p->tile_threads && e.threads != p->tile_threads) continue;
+        // the same threads-per-subdomain variant must exist as a tile kernel
+        int nt = 0;
+        const TileKernelInfo *tk = fam == FAM_F64 ? tile_kernels_f64(&nt) : tile_kernels_f32(&nt);
+        bool have = false;
+        for (int j = 0; j < nt; ++j) have |= tk[j].dim == 2 && tk[j].tx == e.tx && tk[j].ty == e.ty && tk[j].threads == e.threads;
+        if (!have) continue;
+        PpcKernel fn = e.fn[sig][1];
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e.smem[sig]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, e.threads, e.smem[sig]) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        for (int c = occ; c >= std::max(1, occ / 2); --c) {
+            double us = INFINITY;
+            if (!measure_launch(sc, prec, e.tx, e.ty, e.threads, e.stages, c == occ ? 0 : c, p->k, &us)) continue;
+            if (us < best) {
+                best = us;
+                bth = e.threads;
+                bst = e.stages;
+                bcps = c == occ ? 0 : c;
+            }
+        }
+    }
+    if (!std::isfinite(best)) return HJ_OK;   // nothing measurable: keep the defaults
+    p->tile_threads = bth;
+    p->pipeline_stages = bst;
+    p->ctas_per_sm = bcps;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_cache[key] = {bth, bst, bcps, 0};
+        store_cache_file(key, bth, bst, bcps, 0);
+    }
+    return HJ_OK;
+}
+
 }  // namespace
 
 extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predicted_ms) {
     if (!desc || !params) return seterr(HJ_ERR_INVALID_ARG, "desc and params must be non-NULL");
     const hj_desc &d = *desc;
+    if (params->autotune == 3) {
+        // launch shape only: tile_x, tile_y and k are the caller's
+        if (predicted_ms) *predicted_ms = -1.0;
+        return tune_launch(d, params);
+    }
     const bool ir = params->precision == HJ_PREC_F32_IR || params->precision == HJ_PREC_BF16CORR_IR;
     const int prec = ir ? HJ_PREC_F32 : params->precision;   // refinement: tune the binary32 inner cycles
     const double tol = ir ? params->tol : std::max(params->tol, 1e-12);
@@ -209,7 +350,7 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
             params->tile_threads = it->second[2];
             params->k = it->second[3];
             if (predicted_ms) *predicted_ms = -1.0;
-            return HJ_OK;
+            return tune_launch(d, params);
         }
     }
     Scratch sc;
@@ -252,7 +393,7 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
         g_cache[key] = {btx, bty, bth, bk};
         store_cache_file(key, btx, bty, bth, bk);
     }
-    return HJ_OK;
+    return tune_launch(d, params);
 }
 
 namespace hj {

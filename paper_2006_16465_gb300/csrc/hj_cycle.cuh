@@ -6,16 +6,19 @@
 //
 // GB300 mapping (differs from the paper's one-thread-per-point shared-memory
 // kernel, which targets a 48 KB/SM Volta):
-//   * a 2D tile of TX x TY = (32*C) x (R*NW) points is one CTA of NW warps; warp w
-//     owns the band of R rows starting at row y0 + w*R, lane l owns the C
-//     consecutive columns x0 + l*C .. x0 + l*C + C-1 of that band;
-//   * the tile and its halo go from HBM straight into registers with coalesced
-//     row loads (one 128*C-byte row segment per warp instruction);
+//   * a 2D tile of TX x TY = (32*C/H) x (R*NW*H) points is one CTA of NW warps;
+//     each warp owns H bands of R rows, and a lane owns C consecutive columns
+//     of its band (the layout is spelled out above Tile2D below);
+//   * the tile and its halo go into registers, straight from HBM with
+//     coalesced row loads or from a shared-memory box filled by TMA;
 //   * the k subiterations run entirely in registers: N/S neighbours are the
 //     thread's own registers, W/E neighbours arrive by warp shuffle, the frozen
-//     halo column sits in registers of lanes 0 and 31, and only the two edge
-//     rows of each band go through a ping-pong shared-memory buffer (one
+//     halo column sits in registers of the first and last lane of each row,
+//     the two bands of a warp swap their edge rows by shuffle, and only the
+//     edge rows of each warp go through a ping-pong shared-memory buffer (one
 //     barrier per subiteration, none when NW = 1);
+//   * binary32 lanes with an even number of columns update them in packed
+//     pairs (fma.rn.f32x2), which gives the scalar results exactly;
 //   * the residual ||f - A u_c||^2 of the staged input is formed in the first
 //     subiteration (r_p = d_p (u'_p - u_p)) and reduced deterministically
 //     (warp butterfly, CTA, two-level grid) inside the same launch.
@@ -105,15 +108,22 @@ __device__ __forceinline__ T point_update(const Coef<T> &k, T g, T iv, T W, T E,
 }
 
 // ---------------------------------------------------------------------------
-// 2D tile: register state, staging (from global or from a TMA-filled shared
-// box), the k subiterations, and the write-back.
+// 2D tile: register state, staging (from global memory or from a TMA-filled
+// shared box), the k subiterations, and the write-back.
+//
+// A CTA of NW warps owns a TX x TY tile with TX = L*C, L = 32/H lanes per row,
+// TY = R*NW*H.  Each warp holds H bands of R rows (H = 1 or 2): lane l belongs
+// to band hb = l / L of its warp and owns the C consecutive columns
+// x0 + (l % L)*C ... of that band's rows; band b = w*H + hb starts at row
+// y0 + b*R.  Two bands per warp let a 32-wide tile give every lane two
+// neighbouring columns, whose updates then run as packed binary32 pairs.
 // ---------------------------------------------------------------------------
 template <typename T, int C, int R, bool SIG>
 struct Tile2D {
     T v[R][C];                       // band values (current iterate)
     T g[R][C];                       // RHS term: f (exact / sigma) or f/d (fast)
     T dv[SIG ? R : 1][SIG ? C : 1];  // per-point 1/d_p
-    T hx[R];                         // frozen halo column: lane 0 -> W, lane 31 -> E
+    T hx[R];                         // frozen halo column: first lane of a row -> W, last -> E
     T top[C], bot[C];                // row above / below the band
 };
 
@@ -123,13 +133,19 @@ __device__ __forceinline__ T rhs_term(const Coef<T> &kc, T fv) {
     else return fv * kc.invd;
 }
 
+// Band of this lane within its CTA and its first row.
+template <int R, int H>
+__device__ __forceinline__ int band_of_lane() {
+    return (int)(threadIdx.x >> 5) * H + (int)(threadIdx.x & 31) / (32 / H);
+}
+
 // Stage from global memory with predicated loads (zero beyond the ghost ring).
-template <typename S, typename T, int C, int R, bool EXACT, bool SIG, bool PART>
+template <typename S, typename T, int C, int R, int H, bool EXACT, bool SIG, bool PART>
 __device__ __forceinline__ void stage2d_global(Tile2D<T, C, R, SIG> &t, const CycArgs &a, const Coef<T> &kc,
                                                const int x0, const int yb) {
-    constexpr int TX = 32 * C;
-    const int lane = threadIdx.x & 31;
-    const int xl = x0 + lane * C;
+    constexpr int L = 32 / H, TX = L * C;
+    const int li = (threadIdx.x & 31) % L;
+    const int xl = x0 + li * C;
     const long long ld = a.ld;
     const int nx = a.nx, ny = a.ny;
     const S *__restrict__ uin = (const S *)a.uin;
@@ -150,8 +166,8 @@ __device__ __forceinline__ void stage2d_global(Tile2D<T, C, R, SIG> &t, const Cy
             t.g[r][c] = rhs_term<T, EXACT, SIG>(kc, in ? __ldg(f + q) : (T)0);
             if constexpr (SIG) t.dv[r][c] = in ? __ldg(dinv + q) : (T)0;
         }
-        const int hcol = (lane == 0) ? x0 - 1 : x0 + TX;
-        const bool hok = (lane == 0 || lane == 31) && rowok && (!PART || hcol <= nx + 1);
+        const int hcol = (li == 0) ? x0 - 1 : x0 + TX;
+        const bool hok = (li == 0 || li == L - 1) && rowok && (!PART || hcol <= nx + 1);
         t.hx[r] = hok ? ld_s<S, T>(uin + (long long)row * ld + hcol) : (T)0;
     }
     const int rt = yb - 1, rb = yb + R;
@@ -173,12 +189,12 @@ template <> __device__ __forceinline__ float sm_s<__nv_bfloat16, float>(const __
 // iterate starting at (x0-1, y0-1); sf / sd: TY rows of f / (1/d) starting at
 // (x0-1, y0); all with row pitch bw elements.  Out-of-bounds box elements
 // were zero-filled by the copy engine, exactly like the predicated path.
-template <typename S, typename T, int C, int R, bool EXACT, bool SIG>
+template <typename S, typename T, int C, int R, int H, bool EXACT, bool SIG>
 __device__ __forceinline__ void stage2d_smem(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const S *su, const T *sf,
                                              const T *sd, const int bwu, const int bwf, const int band_row0) {
-    constexpr int TX = 32 * C;
-    const int lane = threadIdx.x & 31;
-    const int xc = 1 + lane * C;
+    constexpr int L = 32 / H, TX = L * C;
+    const int li = (threadIdx.x & 31) % L;
+    const int xc = 1 + li * C;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int sr = band_row0 + r;   // tile-interior row index
@@ -188,7 +204,7 @@ __device__ __forceinline__ void stage2d_smem(Tile2D<T, C, R, SIG> &t, const Coef
             t.g[r][c] = rhs_term<T, EXACT, SIG>(kc, sf[sr * bwf + xc + c]);
             if constexpr (SIG) t.dv[r][c] = sd[sr * bwf + xc + c];
         }
-        const int hcol = (lane == 0) ? 0 : TX + 1;
+        const int hcol = (li == 0) ? 0 : TX + 1;
         t.hx[r] = sm_s<S, T>(su + (sr + 1) * bwu + hcol);
     }
 #pragma unroll
@@ -198,15 +214,62 @@ __device__ __forceinline__ void stage2d_smem(Tile2D<T, C, R, SIG> &t, const Coef
     }
 }
 
+// Packed binary32 pairs (fma/mul .f32x2: two independent round-to-nearest
+// operations, so a pair gives exactly the two scalar results).
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long p, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Two neighbouring points of one row (binary32 fast or per-point-d path), in
+// the scalar chain's order: point_update gives the same two values.
+template <bool SIG>
+__device__ __forceinline__ void point_update_pair(const Coef<float> &k, float g0, float g1, float iv0, float iv1,
+                                                  float W0, float W1, float E0, float E1, float S0, float S1,
+                                                  float N0, float N1, float &n0, float &n1) {
+    unsigned long long t = pk2(g0, g1);
+    if constexpr (SIG) {
+        t = ffma2(pk2(-k.cW, -k.cW), pk2(W0, W1), t);
+        t = ffma2(pk2(-k.cE, -k.cE), pk2(E0, E1), t);
+        t = ffma2(pk2(-k.cS, -k.cS), pk2(S0, S1), t);
+        t = ffma2(pk2(-k.cN, -k.cN), pk2(N0, N1), t);
+        t = fmul2(t, pk2(iv0, iv1));
+    } else {
+        t = ffma2(pk2(k.bN, k.bN), pk2(N0, N1), t);
+        t = ffma2(pk2(k.bS, k.bS), pk2(S0, S1), t);
+        t = ffma2(pk2(k.bE, k.bE), pk2(E0, E1), t);
+        t = ffma2(pk2(k.bW, k.bW), pk2(W0, W1), t);
+    }
+    upk2(t, n0, n1);
+}
+
 // k subiterations on registers.  Returns this thread's share of
 // ||f - A u_c||^2 (unscaled by d^2 on the fast constant-diagonal path).
-template <typename T, int C, int R, int NW, bool EXACT, bool SIG, bool RES, bool PART>
+template <typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES, bool PART>
 __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type
 sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, const int yb, const int nx,
          const int ny, T *xbuf) {
-    constexpr int TX = 32 * C;
+    static_assert(H == 1 || H == 2, "one or two bands per warp");
+    constexpr int L = 32 / H, TX = L * C;
+    constexpr bool PACK = std::is_same<T, float>::value && !EXACT && (C % 2 == 0) && !PART;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int xl = x0 + lane * C;
+    const int li = lane % L, hb = lane / L;
+    const int xl = x0 + li * C;
     typedef typename std::conditional<EXACT, double, T>::type Acc;
     Acc acc = 0;
     auto sweep = [&](auto first_tag) {
@@ -221,46 +284,85 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
             for (int c = 0; c < C; ++c) cur[c] = t.v[r][c];
             T left = __shfl_up_sync(FULL, cur[C - 1], 1);
             T right = __shfl_down_sync(FULL, cur[0], 1);
-            if (lane == 0) left = t.hx[r];
-            if (lane == 31) right = t.hx[r];
+            if (li == 0) left = t.hx[r];
+            if (li == L - 1) right = t.hx[r];
+            if constexpr (PACK) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const T W = (c == 0) ? left : cur[c > 0 ? c - 1 : 0];
-                const T E = (c == C - 1) ? right : cur[c < C - 1 ? c + 1 : 0];
-                const T Sv = prev[c];
-                const T Nv = (r == R - 1) ? t.bot[c] : t.v[r < R - 1 ? r + 1 : 0][c];
-                T res = 0;
-                T nv = point_update<T, EXACT, SIG, true, FIRST && RES>(
-                    kc, t.g[r][c], SIG ? t.dv[SIG ? r : 0][SIG ? c : 0] : (T)0, W, E, Sv, Nv, cur[c], res);
-                if constexpr (PART) {
-                    const bool act = (yb + r <= ny) && (xl + c <= nx);
-                    nv = act ? nv : cur[c];
-                    if (!act) res = 0;
+                for (int c = 0; c < C; c += 2) {
+                    const T W0 = (c == 0) ? left : cur[c > 0 ? c - 1 : 0];
+                    const T E1 = (c + 2 == C) ? right : cur[c + 2 < C ? c + 2 : 0];
+                    const T N0 = (r == R - 1) ? t.bot[c] : t.v[r < R - 1 ? r + 1 : 0][c];
+                    const T N1 = (r == R - 1) ? t.bot[c + 1] : t.v[r < R - 1 ? r + 1 : 0][c + 1];
+                    T n0, n1;
+                    point_update_pair<SIG>(kc, t.g[r][c], t.g[r][c + 1], SIG ? t.dv[SIG ? r : 0][SIG ? c : 0] : 0.f,
+                                           SIG ? t.dv[SIG ? r : 0][SIG ? c + 1 : 0] : 0.f, W0, cur[c], cur[c + 1],
+                                           E1, prev[c], prev[c + 1], N0, N1, n0, n1);
+                    if constexpr (FIRST && RES) {
+                        T r0, r1;
+                        if constexpr (SIG) {
+                            r0 = (n0 - cur[c]) * ((T)1 / t.dv[SIG ? r : 0][SIG ? c : 0]);
+                            r1 = (n1 - cur[c + 1]) * ((T)1 / t.dv[SIG ? r : 0][SIG ? c + 1 : 0]);
+                        } else {
+                            r0 = n0 - cur[c];
+                            r1 = n1 - cur[c + 1];
+                        }
+                        acc += (Acc)r0 * (Acc)r0;
+                        acc += (Acc)r1 * (Acc)r1;
+                    }
+                    t.v[r][c] = n0;
+                    t.v[r][c + 1] = n1;
                 }
-                if constexpr (FIRST && RES) acc += (Acc)res * (Acc)res;
-                t.v[r][c] = nv;
+            } else {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const T W = (c == 0) ? left : cur[c > 0 ? c - 1 : 0];
+                    const T E = (c == C - 1) ? right : cur[c < C - 1 ? c + 1 : 0];
+                    const T Sv = prev[c];
+                    const T Nv = (r == R - 1) ? t.bot[c] : t.v[r < R - 1 ? r + 1 : 0][c];
+                    T res = 0;
+                    T nv = point_update<T, EXACT, SIG, true, FIRST && RES>(
+                        kc, t.g[r][c], SIG ? t.dv[SIG ? r : 0][SIG ? c : 0] : (T)0, W, E, Sv, Nv, cur[c], res);
+                    if constexpr (PART) {
+                        const bool act = (yb + r <= ny) && (xl + c <= nx);
+                        nv = act ? nv : cur[c];
+                        if (!act) res = 0;
+                    }
+                    if constexpr (FIRST && RES) acc += (Acc)res * (Acc)res;
+                    t.v[r][c] = nv;
+                }
             }
 #pragma unroll
             for (int c = 0; c < C; ++c) prev[c] = cur[c];
         }
     };
     int par = 0;
+    // before each subiteration after the first: the rows next to each band
+    // become the neighbouring bands' values of the previous subiteration
     auto exchange = [&]() {
+        if constexpr (H == 2) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const T send = hb ? t.v[0][c] : t.v[R - 1][c];
+                const T recv = __shfl_xor_sync(FULL, send, 16);
+                if (hb) t.top[c] = recv;
+                else t.bot[c] = recv;
+            }
+        }
         if constexpr (NW > 1) {
             T *buf = xbuf + par * (NW * 2 * TX);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                buf[(w * 2 + 0) * TX + lane * C + c] = t.v[0][c];
-                buf[(w * 2 + 1) * TX + lane * C + c] = t.v[R - 1][c];
+                if (hb == 0) buf[(w * 2 + 0) * TX + li * C + c] = t.v[0][c];
+                if (hb == H - 1) buf[(w * 2 + 1) * TX + li * C + c] = t.v[R - 1][c];
             }
             __syncthreads();
-            if (w > 0) {
+            if (w > 0 && hb == 0) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) t.top[c] = buf[((w - 1) * 2 + 1) * TX + lane * C + c];
+                for (int c = 0; c < C; ++c) t.top[c] = buf[((w - 1) * 2 + 1) * TX + li * C + c];
             }
-            if (w < NW - 1) {
+            if (w < NW - 1 && hb == H - 1) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) t.bot[c] = buf[((w + 1) * 2 + 0) * TX + lane * C + c];
+                for (int c = 0; c < C; ++c) t.bot[c] = buf[((w + 1) * 2 + 0) * TX + li * C + c];
             }
             par ^= 1;
         }
@@ -274,11 +376,11 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
 }
 
 // Write the band's interior points into u_{c+1}.
-template <typename S, typename T, int C, int R, bool SIG, bool PART>
+template <typename S, typename T, int C, int R, int H, bool SIG, bool PART>
 __device__ __forceinline__ void store2d(const Tile2D<T, C, R, SIG> &t, const CycArgs &a, const int x0,
                                         const int yb) {
-    const int lane = threadIdx.x & 31;
-    const int xl = x0 + lane * C;
+    const int li = (threadIdx.x & 31) % (32 / H);
+    const int xl = x0 + li * C;
     S *__restrict__ uout = (S *)a.uout;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -291,32 +393,31 @@ __device__ __forceinline__ void store2d(const Tile2D<T, C, R, SIG> &t, const Cyc
     }
 }
 
-template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG, bool RES, bool PART>
+template <typename S, typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES, bool PART>
 __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type tile2d(const CycArgs &a, const int x0,
                                                                                     const int y0, T *xbuf) {
-    const int w = threadIdx.x >> 5;
-    const int yb = y0 + w * R;
+    const int yb = y0 + band_of_lane<R, H>() * R;
     const Coef<T> kc = make_coef<T>(a);
     Tile2D<T, C, R, SIG> t;
-    stage2d_global<S, T, C, R, EXACT, SIG, PART>(t, a, kc, x0, yb);
-    auto acc = sweeps2d<T, C, R, NW, EXACT, SIG, RES, PART>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
-    store2d<S, T, C, R, SIG, PART>(t, a, x0, yb);
+    stage2d_global<S, T, C, R, H, EXACT, SIG, PART>(t, a, kc, x0, yb);
+    auto acc = sweeps2d<T, C, R, NW, H, EXACT, SIG, RES, PART>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
+    store2d<S, T, C, R, H, SIG, PART>(t, a, x0, yb);
     return acc;
 }
 
-template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG, bool RES>
+template <typename S, typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES>
 __global__ void __launch_bounds__(32 * NW) hier2d_kernel(const CycArgs a) {
     if constexpr (RES) {
         if (*(volatile int *)&a.red.ctl->done >= 0) return;
     }
-    constexpr int TX = 32 * C, TY = R * NW;
+    constexpr int TX = 32 * C / H, TY = R * NW * H;
     constexpr int XB = NW > 1 ? 2 * NW * 2 * TX : 1;
     __shared__ T xbuf[XB];
     const int x0 = 1 + blockIdx.x * TX, y0 = 1 + blockIdx.y * TY;
     const bool full = (x0 + TX - 1 <= a.nx) && (y0 + TY - 1 <= a.ny);
     typename std::conditional<EXACT, double, T>::type acc;
-    if (full) acc = tile2d<S, T, C, R, NW, EXACT, SIG, RES, false>(a, x0, y0, xbuf);
-    else acc = tile2d<S, T, C, R, NW, EXACT, SIG, RES, true>(a, x0, y0, xbuf);
+    if (full) acc = tile2d<S, T, C, R, NW, H, EXACT, SIG, RES, false>(a, x0, y0, xbuf);
+    else acc = tile2d<S, T, C, R, NW, H, EXACT, SIG, RES, true>(a, x0, y0, xbuf);
     if constexpr (RES) reduce_grid_acc(a.red, acc);
 }
 
@@ -481,10 +582,11 @@ __global__ void __launch_bounds__(256) classic1d_kernel(const CycArgs a) {
 }  // namespace hj
 
 // Registry entry helpers ------------------------------------------------------
-#define HJ_K2D(S, T, C, R, NW, EX)                                                                   \
-    {2, 32 * (C), (R) * (NW), 32 * (NW), 1,                                                          \
-     {{hj::hier2d_kernel<S, T, C, R, NW, EX, false, false>, hj::hier2d_kernel<S, T, C, R, NW, EX, false, true>}, \
-      {hj::hier2d_kernel<S, T, C, R, NW, EX, true, false>, hj::hier2d_kernel<S, T, C, R, NW, EX, true, true>}}}
+#define HJ_K2D(S, T, C, R, NW, H, EX)                                                                \
+    {2, 32 * (C) / (H), (R) * (NW) * (H), 32 * (NW), 1,                                               \
+     {{hj::hier2d_kernel<S, T, C, R, NW, H, EX, false, false>,                                        \
+       hj::hier2d_kernel<S, T, C, R, NW, H, EX, false, true>},                                        \
+      {hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, false>, hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, true>}}}
 #define HJ_K1D(S, T, C, WPB, EX)                                                                     \
     {1, 32 * (C), 1, 32 * (WPB), (WPB),                                                              \
      {{hj::hier1d_kernel<S, T, C, WPB, EX, false, false>, hj::hier1d_kernel<S, T, C, WPB, EX, false, true>}, \

@@ -4,15 +4,15 @@
 namespace hj {
 
 static const TileKernelInfo k_tiles[] = {
-    HJ_K2D(__nv_bfloat16, float, 1, 32, 1, false),    // 32 x 32
-    HJ_K2D(__nv_bfloat16, float, 1, 16, 2, false),    // 32 x 32, two warps
-    HJ_K2D(__nv_bfloat16, float, 1, 16, 1, false),    // 32 x 16
-    HJ_K2D(__nv_bfloat16, float, 1, 8, 1, false),     // 32 x 8
-    HJ_K2D(__nv_bfloat16, float, 1, 32, 2, false),    // 32 x 64
-    HJ_K2D(__nv_bfloat16, float, 2, 16, 2, false),    // 64 x 32
-    HJ_K2D(__nv_bfloat16, float, 2, 16, 4, false),    // 64 x 64
-    HJ_K2D(__nv_bfloat16, float, 4, 8, 4, false),     // 128 x 32
-    HJ_K2D(__nv_bfloat16, float, 4, 8, 8, false),     // 128 x 64
+    HJ_K2D(__nv_bfloat16, float, 2, 16, 1, 2, false),    // 32 x 32
+    HJ_K2D(__nv_bfloat16, float, 2, 8, 2, 2, false),     // 32 x 32, two warps
+    HJ_K2D(__nv_bfloat16, float, 2, 8, 1, 2, false),     // 32 x 16
+    HJ_K2D(__nv_bfloat16, float, 2, 4, 1, 2, false),     // 32 x 8
+    HJ_K2D(__nv_bfloat16, float, 2, 16, 2, 2, false),    // 32 x 64
+    HJ_K2D(__nv_bfloat16, float, 2, 16, 2, 1, false),    // 64 x 32
+    HJ_K2D(__nv_bfloat16, float, 2, 16, 4, 1, false),    // 64 x 64
+    HJ_K2D(__nv_bfloat16, float, 4, 8, 4, 1, false),     // 128 x 32
+    HJ_K2D(__nv_bfloat16, float, 4, 8, 8, 1, false),     // 128 x 64
     HJ_K1D(__nv_bfloat16, float, 1, 4, false),        // 32
     HJ_K1D(__nv_bfloat16, float, 2, 4, false),        // 64
     HJ_K1D(__nv_bfloat16, float, 4, 4, false),        // 128
@@ -24,13 +24,13 @@ const TileKernelInfo *tile_kernels_bf16(int *n) { *n = sizeof(k_tiles) / sizeof(
 const TileKernelInfo *classic_kernels_bf16(int *n) { *n = 2; return k_classic; }
 
 static const PersistKernelInfo k_persist[] = {
-    HJ_KP2D(__nv_bfloat16, float, 1, 32, 1, false),
-    HJ_KP2D(__nv_bfloat16, float, 1, 16, 2, false),
-    HJ_KP2D(__nv_bfloat16, float, 1, 16, 1, false),
-    HJ_KP2D(__nv_bfloat16, float, 1, 8, 1, false),
-    HJ_KP2D(__nv_bfloat16, float, 2, 16, 2, false),
-    HJ_KP2D(__nv_bfloat16, float, 2, 16, 4, false),
-    HJ_KP2D(__nv_bfloat16, float, 4, 8, 8, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 16, 1, 2, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 8, 2, 2, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 8, 1, 2, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 4, 1, 2, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 16, 2, 1, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 16, 4, 1, false),
+    HJ_KP2D(__nv_bfloat16, float, 4, 8, 8, 1, false),
     HJ_KP1D(__nv_bfloat16, float, 1, 4, false),
     HJ_KP1D(__nv_bfloat16, float, 2, 4, false),
     HJ_KP1D(__nv_bfloat16, float, 4, 4, false),

@@ -5,12 +5,12 @@
 namespace hj {
 
 static const TileKernelInfo k_tiles[] = {
-    HJ_K2D(double, double, 1, 16, 2, true),   // 32 x 32
-    HJ_K2D(double, double, 1, 16, 1, true),   // 32 x 16
-    HJ_K2D(double, double, 1, 8, 1, true),    // 32 x 8
-    HJ_K2D(double, double, 1, 16, 4, true),   // 32 x 64
-    HJ_K2D(double, double, 2, 8, 4, true),    // 64 x 32
-    HJ_K2D(double, double, 2, 8, 8, true),    // 64 x 64
+    HJ_K2D(double, double, 1, 16, 2, 1, true),   // 32 x 32
+    HJ_K2D(double, double, 1, 16, 1, 1, true),   // 32 x 16
+    HJ_K2D(double, double, 1, 8, 1, 1, true),    // 32 x 8
+    HJ_K2D(double, double, 1, 16, 4, 1, true),   // 32 x 64
+    HJ_K2D(double, double, 2, 8, 4, 1, true),    // 64 x 32
+    HJ_K2D(double, double, 2, 8, 8, 1, true),    // 64 x 64
     HJ_K1D(double, double, 1, 4, true),       // 32
     HJ_K1D(double, double, 2, 4, true),       // 64
     HJ_K1D(double, double, 4, 4, true),       // 128
@@ -22,20 +22,20 @@ const TileKernelInfo *tile_kernels_f64(int *n) { *n = sizeof(k_tiles) / sizeof(k
 const TileKernelInfo *classic_kernels_f64(int *n) { *n = 2; return k_classic; }
 
 static const PpcKernelInfo k_ppc[] = {
-    HJ_KPPC(double, double, 1, 16, 2, true, 2),   // 32 x 32
-    HJ_KPPC(double, double, 1, 16, 1, true, 2),   // 32 x 16
-    HJ_KPPC(double, double, 1, 8, 1, true, 2),   // 32 x 8
-    HJ_KPPC(double, double, 1, 16, 4, true, 2),   // 32 x 64
-    HJ_KPPC(double, double, 2, 8, 4, true, 2),   // 64 x 32
-    HJ_KPPC(double, double, 2, 8, 8, true, 2),   // 64 x 64
+    HJ_KPPC(double, double, 1, 16, 2, 1, true, 2),   // 32 x 32
+    HJ_KPPC(double, double, 1, 16, 1, 1, true, 2),   // 32 x 16
+    HJ_KPPC(double, double, 1, 8, 1, 1, true, 2),   // 32 x 8
+    HJ_KPPC(double, double, 1, 16, 4, 1, true, 2),   // 32 x 64
+    HJ_KPPC(double, double, 2, 8, 4, 1, true, 2),   // 64 x 32
+    HJ_KPPC(double, double, 2, 8, 8, 1, true, 2),   // 64 x 64
 };
 const PpcKernelInfo *ppc_kernels_f64(int *n) { *n = sizeof(k_ppc) / sizeof(k_ppc[0]); return k_ppc; }
 
 static const PersistKernelInfo k_persist[] = {
-    HJ_KP2D(double, double, 1, 16, 2, true),
-    HJ_KP2D(double, double, 1, 16, 1, true),
-    HJ_KP2D(double, double, 1, 8, 1, true),
-    HJ_KP2D(double, double, 2, 8, 4, true),
+    HJ_KP2D(double, double, 1, 16, 2, 1, true),
+    HJ_KP2D(double, double, 1, 16, 1, 1, true),
+    HJ_KP2D(double, double, 1, 8, 1, 1, true),
+    HJ_KP2D(double, double, 2, 8, 4, 1, true),
     HJ_KP1D(double, double, 1, 4, true),
     HJ_KP1D(double, double, 2, 4, true),
     HJ_KP1D(double, double, 4, 4, true),

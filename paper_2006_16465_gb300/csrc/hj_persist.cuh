@@ -142,9 +142,9 @@ __device__ __forceinline__ void retire_check(const PersistArgs &P, int p, int pa
     }
 }
 
-template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG>
+template <typename S, typename T, int C, int R, int NW, int H, bool EXACT, bool SIG>
 __global__ void __launch_bounds__(32 * NW) persist2d_kernel(const PersistArgs P) {
-    constexpr int TX = 32 * C, TY = R * NW;
+    constexpr int TX = 32 * C / H, TY = R * NW * H;
     constexpr int XB = NW > 1 ? 2 * NW * 2 * TX : 1;
     __shared__ T xbuf[XB];
     for (long long it = 0; it < P.max_iters; ++it) {
@@ -163,9 +163,9 @@ __global__ void __launch_bounds__(32 * NW) persist2d_kernel(const PersistArgs P)
             const int x0 = 1 + (blk % tx) * TX, y0 = 1 + (blk / tx) * TY;
             typename std::conditional<EXACT, double, T>::type acc;
             if (x0 + TX - 1 <= a.nx && y0 + TY - 1 <= a.ny)
-                acc = tile2d<S, T, C, R, NW, EXACT, SIG, true, false>(a, x0, y0, xbuf);
+                acc = tile2d<S, T, C, R, NW, H, EXACT, SIG, true, false>(a, x0, y0, xbuf);
             else
-                acc = tile2d<S, T, C, R, NW, EXACT, SIG, true, true>(a, x0, y0, xbuf);
+                acc = tile2d<S, T, C, R, NW, H, EXACT, SIG, true, true>(a, x0, y0, xbuf);
             const double s = cta_sum(acc);
             if (threadIdx.x == 0) P.partial[(size_t)parity * P.nitems + item] = s;
         }
@@ -276,9 +276,9 @@ __device__ __forceinline__ bool one_decide(const PersistArgs &P, OneState &ls, i
     return ls.done >= 0;
 }
 
-template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG>
+template <typename S, typename T, int C, int R, int NW, int H, bool EXACT, bool SIG>
 __global__ void __launch_bounds__(32 * NW) persist2d_one_kernel(const PersistArgs P) {
-    constexpr int TX = 32 * C, TY = R * NW;
+    constexpr int TX = 32 * C / H, TY = R * NW * H;
     constexpr int XB = NW > 1 ? 2 * NW * 2 * TX : 1;
     __shared__ T xbuf[XB];
     OneState ls{-1, HJ_OK, 0, 0.0, 0.0, 0.0, 0};
@@ -295,9 +295,9 @@ __global__ void __launch_bounds__(32 * NW) persist2d_one_kernel(const PersistArg
             const int x0 = 1 + (item % tx) * TX, y0 = 1 + (item / tx) * TY;
             typename std::conditional<EXACT, double, T>::type acc;
             if (x0 + TX - 1 <= a.nx && y0 + TY - 1 <= a.ny)
-                acc = tile2d<S, T, C, R, NW, EXACT, SIG, true, false>(a, x0, y0, xbuf);
+                acc = tile2d<S, T, C, R, NW, H, EXACT, SIG, true, false>(a, x0, y0, xbuf);
             else
-                acc = tile2d<S, T, C, R, NW, EXACT, SIG, true, true>(a, x0, y0, xbuf);
+                acc = tile2d<S, T, C, R, NW, H, EXACT, SIG, true, true>(a, x0, y0, xbuf);
             const double s = cta_sum(acc);
             if (threadIdx.x == 0) P.partial[(size_t)parity * P.nitems + item] = s;
         }
@@ -411,10 +411,10 @@ struct PersistClassicInfo {
 
 }  // namespace hj
 
-#define HJ_KP2D(S, T, C, R, NW, EX) \
-    {2, 32 * (C), (R) * (NW), 32 * (NW), 1, \
-     {hj::persist2d_kernel<S, T, C, R, NW, EX, false>, hj::persist2d_kernel<S, T, C, R, NW, EX, true>}, \
-     {hj::persist2d_one_kernel<S, T, C, R, NW, EX, false>, hj::persist2d_one_kernel<S, T, C, R, NW, EX, true>}}
+#define HJ_KP2D(S, T, C, R, NW, H, EX) \
+    {2, 32 * (C) / (H), (R) * (NW) * (H), 32 * (NW), 1, \
+     {hj::persist2d_kernel<S, T, C, R, NW, H, EX, false>, hj::persist2d_kernel<S, T, C, R, NW, H, EX, true>}, \
+     {hj::persist2d_one_kernel<S, T, C, R, NW, H, EX, false>, hj::persist2d_one_kernel<S, T, C, R, NW, H, EX, true>}}
 #define HJ_KPC(S, T, EX) \
     {{{hj::persist_classic_one_kernel<S, T, 1, EX, false>, hj::persist_classic_one_kernel<S, T, 1, EX, true>}, \
       {hj::persist_classic_one_kernel<S, T, 2, EX, false>, hj::persist_classic_one_kernel<S, T, 2, EX, true>}}}

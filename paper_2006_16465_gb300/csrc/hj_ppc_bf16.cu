@@ -10,24 +10,24 @@
 namespace hj {
 
 static const PpcKernelInfo k_ppc[] = {
-    HJ_KPPC(__nv_bfloat16, float, 1, 32, 1, false, 1),   // 32 x 32, one stage (default)
-    HJ_KPPC(__nv_bfloat16, float, 1, 32, 1, false, 2),   // 32 x 32, two stages
-    HJ_KPPC(__nv_bfloat16, float, 1, 16, 2, false, 1),   // 32 x 32, two warps, one stage (default)
-    HJ_KPPC(__nv_bfloat16, float, 1, 16, 2, false, 2),   // 32 x 32, two warps, two stages
-    HJ_KPPC(__nv_bfloat16, float, 1, 16, 1, false, 1),   // 32 x 16, one stage (default)
-    HJ_KPPC(__nv_bfloat16, float, 1, 16, 1, false, 2),   // 32 x 16, two stages
-    HJ_KPPC(__nv_bfloat16, float, 1, 8, 1, false, 1),   // 32 x 8, one stage (default)
-    HJ_KPPC(__nv_bfloat16, float, 1, 8, 1, false, 2),   // 32 x 8, two stages
-    HJ_KPPC(__nv_bfloat16, float, 1, 32, 2, false, 1),   // 32 x 64, one stage (default)
-    HJ_KPPC(__nv_bfloat16, float, 1, 32, 2, false, 2),   // 32 x 64, two stages
-    HJ_KPPC(__nv_bfloat16, float, 2, 16, 2, false, 1),   // 64 x 32, one stage (default)
-    HJ_KPPC(__nv_bfloat16, float, 2, 16, 2, false, 2),   // 64 x 32, two stages
-    HJ_KPPC(__nv_bfloat16, float, 2, 16, 4, false, 1),   // 64 x 64, one stage (default)
-    HJ_KPPC(__nv_bfloat16, float, 2, 16, 4, false, 2),   // 64 x 64, two stages
-    HJ_KPPC(__nv_bfloat16, float, 4, 8, 4, false, 1),   // 128 x 32, one stage (default)
-    HJ_KPPC(__nv_bfloat16, float, 4, 8, 4, false, 2),   // 128 x 32, two stages
-    HJ_KPPC(__nv_bfloat16, float, 4, 8, 8, false, 1),   // 128 x 64, one stage (default)
-    HJ_KPPC(__nv_bfloat16, float, 4, 8, 8, false, 2),   // 128 x 64, two stages
+    HJ_KPPC(__nv_bfloat16, float, 2, 16, 1, 2, false, 1),   // 32 x 32, one stage (default)
+    HJ_KPPC(__nv_bfloat16, float, 2, 16, 1, 2, false, 2),   // 32 x 32, two stages
+    HJ_KPPC(__nv_bfloat16, float, 2, 8, 2, 2, false, 1),   // 32 x 32, two warps, one stage (default)
+    HJ_KPPC(__nv_bfloat16, float, 2, 8, 2, 2, false, 2),   // 32 x 32, two warps, two stages
+    HJ_KPPC(__nv_bfloat16, float, 2, 8, 1, 2, false, 1),   // 32 x 16, one stage (default)
+    HJ_KPPC(__nv_bfloat16, float, 2, 8, 1, 2, false, 2),   // 32 x 16, two stages
+    HJ_KPPC(__nv_bfloat16, float, 2, 4, 1, 2, false, 1),   // 32 x 8, one stage (default)
+    HJ_KPPC(__nv_bfloat16, float, 2, 4, 1, 2, false, 2),   // 32 x 8, two stages
+    HJ_KPPC(__nv_bfloat16, float, 2, 16, 2, 2, false, 1),   // 32 x 64, one stage (default)
+    HJ_KPPC(__nv_bfloat16, float, 2, 16, 2, 2, false, 2),   // 32 x 64, two stages
+    HJ_KPPC(__nv_bfloat16, float, 2, 16, 2, 1, false, 1),   // 64 x 32, one stage (default)
+    HJ_KPPC(__nv_bfloat16, float, 2, 16, 2, 1, false, 2),   // 64 x 32, two stages
+    HJ_KPPC(__nv_bfloat16, float, 2, 16, 4, 1, false, 1),   // 64 x 64, one stage (default)
+    HJ_KPPC(__nv_bfloat16, float, 2, 16, 4, 1, false, 2),   // 64 x 64, two stages
+    HJ_KPPC(__nv_bfloat16, float, 4, 8, 4, 1, false, 1),   // 128 x 32, one stage (default)
+    HJ_KPPC(__nv_bfloat16, float, 4, 8, 4, 1, false, 2),   // 128 x 32, two stages
+    HJ_KPPC(__nv_bfloat16, float, 4, 8, 8, 1, false, 1),   // 128 x 64, one stage (default)
+    HJ_KPPC(__nv_bfloat16, float, 4, 8, 8, 1, false, 2),   // 128 x 64, two stages
 };
 const PpcKernelInfo *ppc_kernels_bf16(int *n) { *n = sizeof(k_ppc) / sizeof(k_ppc[0]); return k_ppc; }
 

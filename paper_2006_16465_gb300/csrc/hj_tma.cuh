@@ -77,9 +77,9 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
 
 constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-template <typename S, typename T, int C, int R, int NW, bool SIG, int NST>
+template <typename S, typename T, int C, int R, int NW, int H, bool SIG, int NST>
 struct PpcLayout {
-    static constexpr int TX = 32 * C, TY = R * NW;
+    static constexpr int TX = 32 * C / H, TY = R * NW * H;
     static constexpr int BWU = round_up(TX + 2, 16 / (int)sizeof(S));   // box width, 16-byte multiple
     static constexpr int BWF = round_up(TX + 2, 16 / (int)sizeof(T));
     static constexpr int UB = BWU * (TY + 2) * (int)sizeof(S);
@@ -130,9 +130,9 @@ __device__ __forceinline__ void write_cta_partial(double *out, A acc) {
     }
 }
 
-template <typename S, typename T, int C, int R, int NW, bool EXACT, bool SIG, bool RES, int NST>
+template <typename S, typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES, int NST>
 __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ PpcArgs P) {
-    using L = PpcLayout<S, T, C, R, NW, SIG, NST>;
+    using L = PpcLayout<S, T, C, R, NW, H, SIG, NST>;
     constexpr int TX = L::TX, TY = L::TY;
     const CycArgs &a = P.a;
     const bool reducer = blockIdx.x == gridDim.x - 1;
@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ 
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     uint64_t *bars = (uint64_t *)(smem + L::BAR_OFF);
     T *xbuf = (T *)(smem + L::XB_OFF);
-    const int tid = threadIdx.x, w = tid >> 5;
+    const int tid = threadIdx.x;
+    const int band = band_of_lane<R, H>();
     const int mine = (P.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
     auto su = [&](int s) { return (S *)(smem + s * L::STAGE); };
     auto sf = [&](int s) { return (T *)(smem + s * L::STAGE + L::UB_AL); };
@@ -191,9 +192,9 @@ __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ 
         if (__syncthreads_or(!ok)) { failed = true; break; }
         const int tile = blockIdx.x + i * gridDim.x;
         const int bx = tile % P.tiles_x, by = tile / P.tiles_x;
-        const int x0 = 1 + bx * TX, y0 = 1 + by * TY, yb = y0 + w * R;
+        const int x0 = 1 + bx * TX, y0 = 1 + by * TY, yb = y0 + band * R;
         Tile2D<T, C, R, SIG> t;
-        stage2d_smem<S, T, C, R, EXACT, SIG>(t, kc, su(s), sf(s), sd(s), L::BWU, L::BWF, w * R);
+        stage2d_smem<S, T, C, R, H, EXACT, SIG>(t, kc, su(s), sf(s), sd(s), L::BWU, L::BWF, band * R);
         __syncthreads();   // every thread is done with stage s
         if (tid == 0 && i + NST < mine) {
             fence_proxy_async_smem();
@@ -201,11 +202,11 @@ __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ 
         }
         const bool full = (x0 + TX - 1 <= a.nx) && (y0 + TY - 1 <= a.ny);
         if (full) {
-            acc += sweeps2d<T, C, R, NW, EXACT, SIG, RES, false>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
-            store2d<S, T, C, R, SIG, false>(t, a, x0, yb);
+            acc += sweeps2d<T, C, R, NW, H, EXACT, SIG, RES, false>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
+            store2d<S, T, C, R, H, SIG, false>(t, a, x0, yb);
         } else {
-            acc += sweeps2d<T, C, R, NW, EXACT, SIG, RES, true>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
-            store2d<S, T, C, R, SIG, true>(t, a, x0, yb);
+            acc += sweeps2d<T, C, R, NW, H, EXACT, SIG, RES, true>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
+            store2d<S, T, C, R, H, SIG, true>(t, a, x0, yb);
         }
     }
     if (failed) {
@@ -228,9 +229,9 @@ __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ 
 
 }  // namespace hj
 
-#define HJ_KPPC(S, T, C, R, NW, EX, NST)                                                                   \
-    {32 * (C), (R) * (NW), 32 * (NW), (NST), hj::PpcLayout<S, T, C, R, NW, false, NST>::SMEM,              \
-     hj::PpcLayout<S, T, C, R, NW, true, NST>::SMEM,                                                        \
-     hj::PpcLayout<S, T, C, R, NW, false, NST>::BWU, hj::PpcLayout<S, T, C, R, NW, false, NST>::BWF,        \
-     {{hj::ppc2d_kernel<S, T, C, R, NW, EX, false, false, NST>, hj::ppc2d_kernel<S, T, C, R, NW, EX, false, true, NST>}, \
-      {hj::ppc2d_kernel<S, T, C, R, NW, EX, true, false, NST>, hj::ppc2d_kernel<S, T, C, R, NW, EX, true, true, NST>}}}
+#define HJ_KPPC(S, T, C, R, NW, H, EX, NST)                                                                \
+    {32 * (C) / (H), (R) * (NW) * (H), 32 * (NW), (NST), hj::PpcLayout<S, T, C, R, NW, H, false, NST>::SMEM,    \
+     hj::PpcLayout<S, T, C, R, NW, H, true, NST>::SMEM,                                                      \
+     hj::PpcLayout<S, T, C, R, NW, H, false, NST>::BWU, hj::PpcLayout<S, T, C, R, NW, H, false, NST>::BWF,   \
+     {{hj::ppc2d_kernel<S, T, C, R, NW, H, EX, false, false, NST>, hj::ppc2d_kernel<S, T, C, R, NW, H, EX, false, true, NST>}, \
+      {hj::ppc2d_kernel<S, T, C, R, NW, H, EX, true, false, NST>, hj::ppc2d_kernel<S, T, C, R, NW, H, EX, true, true, NST>}}}

@@ -91,3 +91,27 @@ def test_batched_autotune_converges():
         assert rel <= 1e-8 * 1.0001
         a.close()
     s.close()
+
+
+def test_launch_tuning_keeps_subdomain_and_k_and_the_iterates():
+    """autotune = 3 measures the pipelined kernel's launch shapes (threads per
+    subdomain, copy stages, CTAs per SM) and keeps tile and k; the arithmetic
+    per point is the same in every launch shape, so the iterates are too."""
+    import numpy as np
+    import torch
+    p = W.poisson2d_uniform(640, 512, seed=5)
+    base = dict(tile_x=32, tile_y=32, k=4, precision="f32", tol=1e-5, check_every=12, pipeline=1, persistent=0)
+    outs = []
+    for extra in ({}, {"autotune": 3}):
+        s = gpu_solver(p, **base, **extra)
+        u = to_dev(p.u0, 2, torch.float32)
+        out = s.solve(to_dev(p.f, 2, torch.float32), u)
+        outs.append((out, u.cpu().numpy()))
+        s.close()
+    (a, ua), (b, ub) = outs
+    assert a["status"] == 0 and b["status"] == 0
+    assert (b["tile_x"], b["tile_y"], b["k"]) == (32, 32, 4)
+    assert b["pipeline_stages"] in (1, 2) and b["tile_threads"] in (32, 64) and b["ctas_per_sm"] >= 0
+    assert a["pipeline_stages"] == 1 and a["ctas_per_sm"] == 0
+    assert a["cycles"] == b["cycles"]
+    assert np.array_equal(ua, ub)
