@@ -218,7 +218,7 @@ def _config(args, world):
     return {"workload": f"2D Poisson {n}x{n} binary32, hierarchical Jacobi, 32x32 subdomains, "
                         f"k={args.k}, {args.cycles} cycles per step, fused residual on",
             "grid": [n, n], "tile": [32, 32], "k": args.k, "cycles_per_step": args.cycles,
-            "l2": "inputs larger than L2 (u, f and two more iterate buffers, 268 MB each)",
+            "l2": f"inputs larger than L2 (u, f and two more iterate buffers, {4 * (n + 2) * (n + 32) / 1e6:.0f} MB each)",
             "parallelism": f"replicas x{world}"}
 
 
