@@ -938,6 +938,21 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
 
     h->ld_in = ((long long)d.nx + 2 + 31) / 32 * 32;
+    // 1D with fewer subdomains than SMs: a cycle is the latency of one
+    // subdomain's k sweeps, and binary64 issues slowly per sub-partition, so
+    // split each subdomain over as many warps as a built variant allows
+    if (d.dim == 1 && p.tile_threads == 0 && p.method == HJ_METHOD_HIER) {
+        const long long tiles = (long long)((d.nx + p.tile_x - 1) / p.tile_x) * d.ny;
+        const int fam = ir ? h->fam_inner : h->fam_outer;
+        if (tiles < h->nsm) {
+            int n = 0, best = 0;
+            const TileKernelInfo *k = family_tiles(fam, &n);
+            for (int i = 0; i < n; ++i)
+                if (k[i].dim == 1 && k[i].tx == p.tile_x) best = std::max(best, k[i].threads);
+            p.tile_threads = best;
+            h->p.tile_threads = best;
+        }
+    }
     if (ir) {
         h->k_inner = find_tile(h->fam_inner, d.dim, p.tile_x, p.tile_y, p.tile_threads);
         if (!h->k_inner)

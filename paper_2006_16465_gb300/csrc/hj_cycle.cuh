@@ -422,14 +422,25 @@ __global__ void __launch_bounds__(32 * NW) hier2d_kernel(const CycArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// 1D tile: one warp per tile of 32*C points, WPB tiles per CTA, one row per
-// blockIdx.y (the independent copies of Section 3.5).
+// 1D tile: a subdomain of TX = 32*C*WPT points of one row (the independent
+// copies of Section 3.5, one row per blockIdx.y) is one CTA of WPT warps; warp
+// q owns the 32*C points starting at x0 + q*32*C, lane l the C consecutive
+// points from there + l*C.  Neighbouring warps swap their edge points through
+// a double-buffered shared array (one barrier per subiteration); with WPT > 1
+// binary64 updates run on WPT sub-partitions at once.
 // ---------------------------------------------------------------------------
-template <typename S, typename T, int C, bool EXACT, bool SIG, bool RES, bool PART>
-__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type tile1d(const CycArgs &a, const int x0, const int row) {
-    constexpr int TX = 32 * C;
-    const int lane = threadIdx.x & 31;
-    const int xl = x0 + lane * C;
+template <typename T, int WPT>
+struct Xchg1D {
+    T e[2][WPT > 1 ? WPT : 1][2];   // [parity][warp][first, last]
+};
+
+template <typename S, typename T, int C, int WPT, bool EXACT, bool SIG, bool RES, bool PART>
+__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type tile1d(const CycArgs &a, const int x0,
+                                                                                    const int row,
+                                                                                    Xchg1D<T, WPT> &xb) {
+    constexpr int TX = 32 * C * WPT;
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int xl = x0 + q * 32 * C + lane * C;
     const long long ld = a.ld;
     const int nx = a.nx;
     const long long rb = (long long)row * ld;
@@ -454,12 +465,15 @@ __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type til
             g[c] = fv * kc.invd;
         }
     }
-    const int hcol = (lane == 0) ? x0 - 1 : x0 + TX;
-    const bool hok = (lane == 0 || lane == 31) && (!PART || hcol <= nx + 1);
+    // frozen halo: first lane of warp 0 (W) and last lane of the last warp (E)
+    const bool wl = lane == 0 && q == 0, el = lane == 31 && q == WPT - 1;
+    const int hcol = wl ? x0 - 1 : x0 + TX;
+    const bool hok = (wl || el) && (!PART || hcol <= nx + 1);
     const T hx = hok ? ld_s<S, T>(uin + rb + hcol) : (T)0;
 
     typedef typename std::conditional<EXACT, double, T>::type Acc;
     Acc acc = 0;
+    int par = 0;
     auto sweep = [&](auto first_tag) {
         constexpr bool FIRST = decltype(first_tag)::value;
         T cur[C];
@@ -467,8 +481,17 @@ __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type til
         for (int c = 0; c < C; ++c) cur[c] = v[c];
         T left = __shfl_up_sync(FULL, cur[C - 1], 1);
         T right = __shfl_down_sync(FULL, cur[0], 1);
-        if (lane == 0) left = hx;
-        if (lane == 31) right = hx;
+        if constexpr (WPT > 1) {
+            // the neighbouring warps' edge points of the previous subiterate
+            if (lane == 0) xb.e[par][q][0] = cur[0];
+            if (lane == 31) xb.e[par][q][1] = cur[C - 1];
+            __syncthreads();
+            if (lane == 0 && q > 0) left = xb.e[par][q - 1][1];
+            if (lane == 31 && q < WPT - 1) right = xb.e[par][q + 1][0];
+            par ^= 1;
+        }
+        if (wl) left = hx;
+        if (el) right = hx;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const T W = (c == 0) ? left : cur[c > 0 ? c - 1 : 0];
@@ -497,20 +520,19 @@ __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type til
     return acc;
 }
 
-template <typename S, typename T, int C, int WPB, bool EXACT, bool SIG, bool RES>
-__global__ void __launch_bounds__(32 * WPB) hier1d_kernel(const CycArgs a) {
+template <typename S, typename T, int C, int WPT, bool EXACT, bool SIG, bool RES>
+__global__ void __launch_bounds__(32 * WPT) hier1d_kernel(const CycArgs a) {
     if constexpr (RES) {
         if (*(volatile int *)&a.red.ctl->done >= 0) return;
     }
-    constexpr int TX = 32 * C;
-    const int w = threadIdx.x >> 5;
-    const int x0 = 1 + (blockIdx.x * WPB + w) * TX;
+    constexpr int TX = 32 * C * WPT;
+    __shared__ Xchg1D<T, WPT> xb;
+    const int x0 = 1 + blockIdx.x * TX;
     const int row = blockIdx.y;
     typename std::conditional<EXACT, double, T>::type acc = 0;
-    if (x0 <= a.nx) {
-        if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, EXACT, SIG, RES, false>(a, x0, row);
-        else acc = tile1d<S, T, C, EXACT, SIG, RES, true>(a, x0, row);
-    }
+    // x0 is uniform across the CTA, so the whole CTA takes the same branch
+    if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, WPT, EXACT, SIG, RES, false>(a, x0, row, xb);
+    else acc = tile1d<S, T, C, WPT, EXACT, SIG, RES, true>(a, x0, row, xb);
     if constexpr (RES) reduce_grid_acc(a.red, acc);
 }
 
@@ -587,10 +609,10 @@ __global__ void __launch_bounds__(256) classic1d_kernel(const CycArgs a) {
      {{hj::hier2d_kernel<S, T, C, R, NW, H, EX, false, false>,                                        \
        hj::hier2d_kernel<S, T, C, R, NW, H, EX, false, true>},                                        \
       {hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, false>, hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, true>}}}
-#define HJ_K1D(S, T, C, WPB, EX)                                                                     \
-    {1, 32 * (C), 1, 32 * (WPB), (WPB),                                                              \
-     {{hj::hier1d_kernel<S, T, C, WPB, EX, false, false>, hj::hier1d_kernel<S, T, C, WPB, EX, false, true>}, \
-      {hj::hier1d_kernel<S, T, C, WPB, EX, true, false>, hj::hier1d_kernel<S, T, C, WPB, EX, true, true>}}}
+#define HJ_K1D(S, T, C, WPT, EX)                                                                     \
+    {1, 32 * (C) * (WPT), 1, 32 * (WPT), 1,                                                          \
+     {{hj::hier1d_kernel<S, T, C, WPT, EX, false, false>, hj::hier1d_kernel<S, T, C, WPT, EX, false, true>}, \
+      {hj::hier1d_kernel<S, T, C, WPT, EX, true, false>, hj::hier1d_kernel<S, T, C, WPT, EX, true, true>}}}
 #define HJ_KC2D(S, T, EX)                                                                             \
     {2, 32, 8, 256, 1,                                                                               \
      {{hj::classic2d_kernel<S, T, EX, false, false>, hj::classic2d_kernel<S, T, EX, false, true>},   \

@@ -1,5 +1,5 @@
 // Binary32 arithmetic on bfloat16-stored iterates (the refinement correction).
-#include "hj_persist.cuh"
+#include "hj_cycle.cuh"
 
 namespace hj {
 
@@ -13,32 +13,20 @@ static const TileKernelInfo k_tiles[] = {
     HJ_K2D(__nv_bfloat16, float, 2, 16, 4, 1, false),    // 64 x 64
     HJ_K2D(__nv_bfloat16, float, 4, 8, 4, 1, false),     // 128 x 32
     HJ_K2D(__nv_bfloat16, float, 4, 8, 8, 1, false),     // 128 x 64
-    HJ_K1D(__nv_bfloat16, float, 1, 4, false),        // 32
-    HJ_K1D(__nv_bfloat16, float, 2, 4, false),        // 64
-    HJ_K1D(__nv_bfloat16, float, 4, 4, false),        // 128
-    HJ_K1D(__nv_bfloat16, float, 8, 4, false),        // 256
+    HJ_K1D(__nv_bfloat16, float, 1, 1, false),    // 32
+    HJ_K1D(__nv_bfloat16, float, 2, 1, false),    // 64
+    HJ_K1D(__nv_bfloat16, float, 1, 2, false),    // 64, 2 warps
+    HJ_K1D(__nv_bfloat16, float, 4, 1, false),    // 128
+    HJ_K1D(__nv_bfloat16, float, 2, 2, false),    // 128, 2 warps
+    HJ_K1D(__nv_bfloat16, float, 1, 4, false),    // 128, 4 warps
+    HJ_K1D(__nv_bfloat16, float, 8, 1, false),    // 256
+    HJ_K1D(__nv_bfloat16, float, 4, 2, false),    // 256, 2 warps
+    HJ_K1D(__nv_bfloat16, float, 2, 4, false),    // 256, 4 warps
+    HJ_K1D(__nv_bfloat16, float, 1, 8, false),    // 256, 8 warps
 };
 static const TileKernelInfo k_classic[] = {HJ_KC2D(__nv_bfloat16, float, false), HJ_KC1D(__nv_bfloat16, float, false)};
 
 const TileKernelInfo *tile_kernels_bf16(int *n) { *n = sizeof(k_tiles) / sizeof(k_tiles[0]); return k_tiles; }
 const TileKernelInfo *classic_kernels_bf16(int *n) { *n = 2; return k_classic; }
-
-static const PersistKernelInfo k_persist[] = {
-    HJ_KP2D(__nv_bfloat16, float, 2, 16, 1, 2, false),
-    HJ_KP2D(__nv_bfloat16, float, 2, 8, 2, 2, false),
-    HJ_KP2D(__nv_bfloat16, float, 2, 8, 1, 2, false),
-    HJ_KP2D(__nv_bfloat16, float, 2, 4, 1, 2, false),
-    HJ_KP2D(__nv_bfloat16, float, 2, 16, 2, 1, false),
-    HJ_KP2D(__nv_bfloat16, float, 2, 16, 4, 1, false),
-    HJ_KP2D(__nv_bfloat16, float, 4, 8, 8, 1, false),
-    HJ_KP1D(__nv_bfloat16, float, 1, 4, false),
-    HJ_KP1D(__nv_bfloat16, float, 2, 4, false),
-    HJ_KP1D(__nv_bfloat16, float, 4, 4, false),
-    HJ_KP1D(__nv_bfloat16, float, 8, 4, false),
-};
-const PersistKernelInfo *persist_kernels_bf16(int *n) { *n = sizeof(k_persist) / sizeof(k_persist[0]); return k_persist; }
-
-static const PersistClassicInfo k_pclassic = HJ_KPC(__nv_bfloat16, float, false);
-const PersistClassicInfo *persist_classic_bf16() { return &k_pclassic; }
 
 }  // namespace hj

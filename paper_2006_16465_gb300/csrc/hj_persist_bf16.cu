@@ -1,0 +1,32 @@
+// Binary32 arithmetic on bfloat16-stored iterates: persistent cooperative cycle kernels (hj_persist.cuh), in a
+// translation unit of their own so that the library's kernels compile in
+// parallel.
+#include "hj_persist.cuh"
+
+namespace hj {
+
+static const PersistKernelInfo k_persist[] = {
+    HJ_KP2D(__nv_bfloat16, float, 2, 16, 1, 2, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 8, 2, 2, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 8, 1, 2, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 4, 1, 2, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 16, 2, 1, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 16, 4, 1, false),
+    HJ_KP2D(__nv_bfloat16, float, 4, 8, 8, 1, false),
+    HJ_KP1D(__nv_bfloat16, float, 1, 1, false),
+    HJ_KP1D(__nv_bfloat16, float, 2, 1, false),
+    HJ_KP1D(__nv_bfloat16, float, 1, 2, false),
+    HJ_KP1D(__nv_bfloat16, float, 4, 1, false),
+    HJ_KP1D(__nv_bfloat16, float, 2, 2, false),
+    HJ_KP1D(__nv_bfloat16, float, 1, 4, false),
+    HJ_KP1D(__nv_bfloat16, float, 8, 1, false),
+    HJ_KP1D(__nv_bfloat16, float, 4, 2, false),
+    HJ_KP1D(__nv_bfloat16, float, 2, 4, false),
+    HJ_KP1D(__nv_bfloat16, float, 1, 8, false),
+};
+const PersistKernelInfo *persist_kernels_bf16(int *n) { *n = sizeof(k_persist) / sizeof(k_persist[0]); return k_persist; }
+
+static const PersistClassicInfo k_pclassic = HJ_KPC(__nv_bfloat16, float, false);
+const PersistClassicInfo *persist_classic_bf16() { return &k_pclassic; }
+
+}  // namespace hj

@@ -62,14 +62,17 @@ def test_f64_cycles_match_oracle_2d(tile, shape, sigma, asym, pipeline):
         s.close()
 
 
+@pytest.mark.parametrize("threads", [0, 32])
 @pytest.mark.parametrize("tile", TILES_1D)
 @pytest.mark.parametrize("n,copies,sigma,asym", [(512, 1, "none", False), (300, 5, "field", True),
                                                    (1000, 3, "const", True)])
-def test_f64_cycles_match_oracle_1d(tile, n, copies, sigma, asym):
+def test_f64_cycles_match_oracle_1d(tile, n, copies, sigma, asym, threads):
+    """threads=0 splits each subdomain over the most warps built (fewer
+    subdomains than SMs here); 32 gives every subdomain one warp."""
     torch = _torch()
     p = W.random_bc_problem(1, n, copies, seed=n, sigma_kind=sigma, asym=asym)
     for k, ncyc in [(1, 3), (32, 3)]:
-        s = gpu_solver(p, tile_x=tile, k=k, precision="f64", fixed_cycles=ncyc)
+        s = gpu_solver(p, tile_x=tile, k=k, precision="f64", fixed_cycles=ncyc, tile_threads=threads)
         f = to_dev(p.f, 1, torch.float64)
         u = to_dev(p.u0, 1, torch.float64)
         s.solve(f, u)
