@@ -38,6 +38,46 @@ const char *last_error_text() { return g_err; }
 
 }  // namespace hj
 
+namespace hj {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2D tiled map over a grid array: dims (cols, rows), row stride ld*esz bytes,
+// box (bw, bh); out-of-bounds elements read as zero.
+bool make_tmap(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int esz, long long ld, int cols, int rows,
+               int bw, int bh) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
+    cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    cuuint32_t estr[2] = {1, 1};
+    memset(m, 0, sizeof(*m));
+    return enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+CUtensorMapDataType tmap_type(int fam, bool storage) {
+    if (fam == FAM_F64) return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    if (fam == FAM_BF16 && storage) return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+}
+
+}  // namespace hj
+
 namespace {
 
 }  // namespace
@@ -93,35 +133,7 @@ const PpcKernelInfo *find_ppc(int fam, int tx, int ty, int threads, int stages) 
     return nullptr;
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
-    return fn;
-}
 
-// 2D tiled map over a grid array: dims (cols, rows), row stride ld*esz bytes,
-// box (bw, bh); out-of-bounds elements read as zero.
-bool make_tmap(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int esz, long long ld, int cols, int rows,
-               int bw, int bh) {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
-    cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
-    cuuint32_t estr[2] = {1, 1};
-    memset(m, 0, sizeof(*m));
-    return enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
 
 const TileKernelInfo *find_tile(int fam, int dim, int tx, int ty, int threads = 0) {
     int n = 0;
@@ -280,11 +292,6 @@ bool want_ppc(const hj_handle *h, const PpcKernelInfo *pi, bool classic) {
     return ntiles >= 8LL * h->nsm;
 }
 
-CUtensorMapDataType tmap_type(int fam, bool storage) {
-    if (fam == FAM_F64) return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-    if (fam == FAM_BF16 && storage) return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-}
 
 // b2: third iterate buffer (same ghost ring as b0), required when the
 // pipelined kernel runs with the fused residual.
@@ -570,7 +577,7 @@ int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int
     q.blocks_x = pclassic ? 1 : g.x;
     q.blocks = pclassic ? (int)cblocks : g.x * g.y;
     std::vector<ProbState> st;
-    CKS(run_persistent(h, pk, sig, v, s, &st, pclassic));
+    CKS(run_persistent(h, pk, sig, v, s, &st, pclassic, fam));
     ro->c = st[0].done;
     ro->status = st[0].status;
     ro->launched = st[0].cycle;

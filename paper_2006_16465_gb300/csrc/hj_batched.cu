@@ -8,6 +8,7 @@
 #include <cstring>
 
 #include "hj_runtime.cuh"
+#include "hj_persist_tma.cuh"
 
 using namespace hj;
 
@@ -51,12 +52,31 @@ int ensure_scratch(hj_handle *h, size_t bytes) {
     return HJ_OK;
 }
 
-int persist_capacity(hj_handle *h, const PersistKernelInfo *ki, bool sig, int *ctas) {
+// TMA-staged persistent kernels run unless pipeline = 0 (2D only).
+bool persist_uses_tma(const hj_handle *h, const PersistKernelInfo *ki, bool sig) {
+    return h->p.pipeline != 0 && ki && ki->dim == 2 && ki->tma_fn[sig] && ki->tma_one[sig];
+}
+
+namespace {
+int capacity_of(hj_handle *h, const PersistKernelInfo *ki, bool sig, bool tma, int *ctas) {
     int occ = 0, occ1 = 0;
-    CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ki->fn[sig], ki->threads, 0));
-    CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, ki->one[sig], ki->threads, 0));
+    if (tma) {
+        const int smem = ki->tma_smem[sig];
+        for (PersistKernel fn : {ki->tma_fn[sig], ki->tma_one[sig]})
+            CKR(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ki->tma_fn[sig], ki->threads, smem));
+        CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, ki->tma_one[sig], ki->threads, smem));
+    } else {
+        CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ki->fn[sig], ki->threads, 0));
+        CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, ki->one[sig], ki->threads, 0));
+    }
     *ctas = std::min(occ, occ1) * h->nsm;
     return HJ_OK;
+}
+}  // namespace
+
+int persist_capacity(hj_handle *h, const PersistKernelInfo *ki, bool sig, int *ctas) {
+    return capacity_of(h, ki, sig, persist_uses_tma(h, ki, sig), ctas);
 }
 
 namespace {
@@ -69,8 +89,28 @@ long long env_ll(const char *name, long long dflt) {
 }  // namespace
 
 int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vector<PersistProblem> &probs,
-                   cudaStream_t s, std::vector<ProbState> *out, PersistKernel classic) {
+                   cudaStream_t s, std::vector<ProbState> *out, PersistKernel classic, int fam) {
     const int nprob = (int)probs.size();
+    bool tma = !classic && fam >= 0 && persist_uses_tma(h, ki, sig);
+    // tensor maps of each problem's two iterate buffers, RHS and 1/d; arrays
+    // the encoder rejects (alignment) run the plain-staging kernel instead
+    std::vector<PersistMaps> maps;
+    if (tma) {
+        maps.resize(nprob);
+        const int ssz = fam == FAM_F64 ? 8 : fam == FAM_BF16 ? 2 : 4;
+        const int tsz = fam == FAM_F64 ? 8 : 4;
+        for (int p = 0; p < nprob && tma; ++p) {
+            const CycArgs &a = probs[p].a;
+            PersistMaps &m = maps[p];
+            memset(&m, 0, sizeof(m));
+            const int cols = a.nx + 2, rows = a.ny + 2;
+            tma = make_tmap(&m.mu[0], a.uin, tmap_type(fam, true), ssz, a.ld, cols, rows, ki->bwu, ki->ty + 2) &&
+                  make_tmap(&m.mu[1], a.uout, tmap_type(fam, true), ssz, a.ld, cols, rows, ki->bwu, ki->ty + 2) &&
+                  make_tmap(&m.mf, a.f, tmap_type(fam, false), tsz, a.ld, cols, rows, ki->bwf, ki->ty);
+            if (tma && sig)
+                tma = a.dinv && make_tmap(&m.md, a.dinv, tmap_type(fam, false), tsz, a.ld, cols, rows, ki->bwf, ki->ty);
+        }
+    }
     long long nitems = 0, max_iters = 1;
     for (auto &p : probs) {
         nitems += p.blocks;
@@ -87,7 +127,8 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
     const size_t o_ptx = al(o_pn + nprob * sizeof(int));
     const size_t o_part = al(o_ptx + nprob * sizeof(int));
     const size_t o_bar = al(o_part + 2 * nitems * sizeof(double));
-    const size_t total = al(o_bar + 4 * sizeof(unsigned));
+    const size_t o_maps = al(o_bar + 4 * sizeof(unsigned));
+    const size_t total = al(o_maps + (tma ? nprob * sizeof(PersistMaps) : 0));
     CKS(ensure_scratch(h, total));
     unsigned char *hb = h->h_pstage;
     unsigned char *db = (unsigned char *)h->pscratch;
@@ -107,6 +148,7 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
             hib[it] = b;
         }
     }
+    if (tma) memcpy(hb + o_maps, maps.data(), nprob * sizeof(PersistMaps));
     unsigned *hbar = (unsigned *)(hb + o_bar);
     hbar[0] = hbar[1] = 0u;
     ((int *)hbar)[2] = nprob;   // active
@@ -132,13 +174,15 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
     // make one CTA leave early, so that the timeout path runs without a fault)
     P.timeout_ns = (unsigned long long)env_ll("HJ_TEST_BARRIER_TIMEOUT_NS", 4000000000LL);
     P.skip_barrier_cta = (int)env_ll("HJ_TEST_SKIP_BARRIER_CTA", -1);
+    P.maps = tma ? (const PersistMaps *)(db + o_maps) : nullptr;
+    P.spin_limit = 1LL << 26;
     int cap = 0, threads = 256;
     if (classic) {
         int occ = 0;
         CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, classic, 256, 0));
         cap = occ * h->nsm;
     } else {
-        CKS(persist_capacity(h, ki, sig, &cap));
+        CKS(capacity_of(h, ki, sig, tma, &cap));
         threads = ki->threads;
     }
     if (cap < 1) return seterr(HJ_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
@@ -146,8 +190,9 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
     void *args[] = {&P};
     // one problem: one grid barrier per cycle; several: two (reduce, then retire)
     const void *fn = classic ? (const void *)classic
-                     : nprob == 1 ? (const void *)ki->one[sig] : (const void *)ki->fn[sig];
-    CKR(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, 0, s));
+                     : tma ? (nprob == 1 ? (const void *)ki->tma_one[sig] : (const void *)ki->tma_fn[sig])
+                           : (nprob == 1 ? (const void *)ki->one[sig] : (const void *)ki->fn[sig]);
+    CKR(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, tma ? ki->tma_smem[sig] : 0, s));
     CKR(cudaMemcpyAsync(hb + o_state, db + o_state, nprob * sizeof(ProbState), cudaMemcpyDeviceToHost, s));
     CKR(cudaMemcpyAsync(hb + o_bar, db + o_bar, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CKR(cudaEventRecord(h->ev, s));
@@ -399,7 +444,7 @@ int batched_core(hj_handle *h, int nprob, const hj_desc *descs, const void *cons
             pp.push_back(q);
         }
         std::vector<ProbState> st;
-        CKS(run_persistent(h, ki, sig_any, pp, s, &st));
+        CKS(run_persistent(h, ki, sig_any, pp, s, &st, nullptr, fam));
         for (size_t j = 0; j < act.size(); ++j) {
             P[act[j]].inner_cycles += st[j].done;
             total_inner += st[j].done;

@@ -31,6 +31,8 @@ struct ProbState {
     long long mark_cycle;
 };
 
+struct PersistMaps;   // hj_persist_tma.cuh: per-problem tensor maps
+
 struct PersistArgs {
     const CycArgs *probs;    // per problem: f, b0 (=uin), b1 (=uout), dinv, geometry, k, coefficients,
                              // red.tol, red.max_cycles, red.scale
@@ -48,6 +50,8 @@ struct PersistArgs {
     long long max_iters;     // cap on cycles in this launch
     unsigned long long timeout_ns;
     int skip_barrier_cta;    // test hook: this CTA leaves before the first barrier (-1 = none)
+    const PersistMaps *maps; // per problem (TMA-staging kernels only)
+    long long spin_limit;    // polls of an mbarrier before giving up (TMA-staging kernels)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -398,6 +402,10 @@ struct PersistKernelInfo {
     int dim, tx, ty, threads, tiles_per_cta;
     PersistKernel fn[2];      // [sig]  many problems, two barriers per cycle
     PersistKernel one[2];     // [sig]  one problem, one barrier per cycle
+    // TMA-staged variants (2D; null otherwise) and their dynamic shared memory
+    PersistKernel tma_fn[2], tma_one[2];
+    int tma_smem[2];
+    int bwu, bwf;             // box widths (elements) of the iterate / RHS boxes
 };
 
 // Grid-sync classic baseline, one problem ([dim - 1][sig]).
@@ -407,14 +415,11 @@ struct PersistClassicInfo {
 
 }  // namespace hj
 
-#define HJ_KP2D(S, T, C, R, NW, H, EX) \
-    {2, 32 * (C) / (H), (R) * (NW) * (H), 32 * (NW), 1, \
-     {hj::persist2d_kernel<S, T, C, R, NW, H, EX, false>, hj::persist2d_kernel<S, T, C, R, NW, H, EX, true>}, \
-     {hj::persist2d_one_kernel<S, T, C, R, NW, H, EX, false>, hj::persist2d_one_kernel<S, T, C, R, NW, H, EX, true>}}
 #define HJ_KPC(S, T, EX) \
     {{{hj::persist_classic_one_kernel<S, T, 1, EX, false>, hj::persist_classic_one_kernel<S, T, 1, EX, true>}, \
       {hj::persist_classic_one_kernel<S, T, 2, EX, false>, hj::persist_classic_one_kernel<S, T, 2, EX, true>}}}
 #define HJ_KP1D(S, T, C, WPT, EX) \
     {1, 32 * (C) * (WPT), 1, 32 * (WPT), 1, \
      {hj::persist1d_kernel<S, T, C, WPT, EX, false>, hj::persist1d_kernel<S, T, C, WPT, EX, true>}, \
-     {hj::persist1d_one_kernel<S, T, C, WPT, EX, false>, hj::persist1d_one_kernel<S, T, C, WPT, EX, true>}}
+     {hj::persist1d_one_kernel<S, T, C, WPT, EX, false>, hj::persist1d_one_kernel<S, T, C, WPT, EX, true>}, \
+     {nullptr, nullptr}, {nullptr, nullptr}, {0, 0}, 0, 0}

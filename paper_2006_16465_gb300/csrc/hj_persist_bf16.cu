@@ -1,7 +1,8 @@
-// Binary32 arithmetic on bfloat16-stored iterates: persistent cooperative cycle kernels (hj_persist.cuh), in a
+// Binary32 arithmetic on bfloat16-stored iterates: persistent cooperative cycle kernels (hj_persist.cuh,
+// hj_persist_tma.cuh), in a
 // translation unit of their own so that the library's kernels compile in
 // parallel.
-#include "hj_persist.cuh"
+#include "hj_persist_tma.cuh"
 
 namespace hj {
 

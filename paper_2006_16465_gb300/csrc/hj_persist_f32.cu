@@ -1,7 +1,8 @@
-// Binary32: persistent cooperative cycle kernels (hj_persist.cuh), in a
+// Binary32: persistent cooperative cycle kernels (hj_persist.cuh,
+// hj_persist_tma.cuh), in a
 // translation unit of their own so that the library's kernels compile in
 // parallel.
-#include "hj_persist.cuh"
+#include "hj_persist_tma.cuh"
 
 namespace hj {
 

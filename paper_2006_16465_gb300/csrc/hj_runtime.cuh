@@ -2,6 +2,8 @@
 // units: the handle, error reporting, and the engines the solve calls use.
 #pragma once
 
+#include <cuda.h>
+
 #include <cstdarg>
 #include <cstdio>
 #include <vector>
@@ -95,6 +97,14 @@ struct hj_handle {
 
 namespace hj {
 
+// 2D tiled tensor map over a grid array: dims (cols, rows), row stride
+// ld*esz bytes, box (bw, bh), zero fill out of bounds.  False if the encoder
+// is unavailable or rejects the arguments (alignment, pitch).
+bool make_tmap(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int esz, long long ld, int cols, int rows,
+               int bw, int bh);
+// Element type of a family's storage (iterate) or compute (RHS, 1/d) arrays.
+CUtensorMapDataType tmap_type(int fam, bool storage);
+
 // Grow the grid-reduction workspace so that a launch of `blocks` CTAs fits.
 int ensure_reduction(hj_handle *h, size_t blocks);
 // Grow the persistent-engine scratch (items, states, partials, barrier words).
@@ -108,8 +118,9 @@ struct PersistProblem {
     int blocks;       // CTAs in total
 };
 // classic: run the grid-sync classic kernel (one problem, blocks of points as items)
+// fam >= 0 (the kernels' family) lets 2D problems stage by TMA (pipeline != 0).
 int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vector<PersistProblem> &probs,
-                   cudaStream_t s, std::vector<ProbState> *out, PersistKernel classic = nullptr);
+                   cudaStream_t s, std::vector<ProbState> *out, PersistKernel classic = nullptr, int fam = -1);
 int persist_capacity(hj_handle *h, const PersistKernelInfo *ki, bool sig, int *ctas);
 
 // Batched tuning (hj_autotune.cu): tile variant with a persistent kernel and

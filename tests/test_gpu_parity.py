@@ -507,6 +507,40 @@ def test_batched_equals_individual_solves_and_oracle(prec):
         assert np.abs(ug - uo).max() <= 2 * kappa * tol * np.abs(uo).max()
 
 
+@pytest.mark.parametrize("sigma", [False, True])
+def test_batched_tma_staging_equals_plain_staging(sigma):
+    """The persistent engine stages subdomains by TMA with prefetch unless
+    pipeline = 0; both stagings give the same iterates and cycle counts."""
+    torch = _torch()
+    import paper_2006_16465_gb300 as hj
+    probs = _batch()
+    runs = []
+    for pipeline in (-1, 0):
+        params = dict(tile_x=32, tile_y=32, k=16, precision="f32_ir", tol=1e-8, inner_tol=1e-4, max_outer=60,
+                      pipeline=pipeline)
+        sig = None
+        if sigma:
+            q0 = probs[0]
+            sg = W.zeros_grid(q0.st)
+            sg[1:-1, 1:-1] = W.uniform(77, q0.st.nx * q0.st.ny, 0.0, 40.0).reshape(q0.st.ny, q0.st.nx)
+            sig = to_dev(sg, 2, torch.float64)
+        s = hj.Solver(probs[0].st, **params)
+        fs = [to_dev(q.f, 2, torch.float64) for q in probs]
+        us = [to_dev(q.u0, 2, torch.float64) for q in probs]
+        descs = [hj.make_desc(2, q.st.nx, q.st.ny, f.shape[1], q.st.cW, q.st.cE, q.st.cS, q.st.cN, q.st.cD,
+                              q.st.sigma_const, sig if (sigma and i == 0) else None)
+                 for i, (q, f) in enumerate(zip(probs, fs))]
+        cyc = (hj.C.c_longlong * len(probs))()
+        code = hj.hj_solve_batched(s.h, descs, [f.data_ptr() for f in fs], [u.data_ptr() for u in us], 0, None, cyc)
+        assert code == 0, hj.hj_last_error()
+        runs.append((us, list(cyc)))
+        s.close()
+    (ua, ca), (ub, cb) = runs
+    assert ca == cb
+    for i in range(len(probs)):
+        assert torch.equal(ua[i], ub[i]), f"problem {i}"
+
+
 _TIMEOUT_SCRIPT = r"""
 import os, sys
 sys.path.insert(0, os.getcwd())
