@@ -100,7 +100,8 @@ const PersistKernelInfo *hj::find_persist(int fam, int dim, int tx, int ty, int 
     int n = 0;
     const PersistKernelInfo *k = family_persist(fam, &n);
     for (int i = 0; i < n; ++i)
-        if (k[i].dim == dim && k[i].tx == tx && (dim == 1 || k[i].ty == ty) && (!threads || k[i].threads == threads))
+        if (k[i].dim == dim && k[i].tx == tx && (dim == 1 || k[i].ty == ty) &&
+            (!threads || k[i].threads / k[i].tiles_per_cta == threads))
             return &k[i];
     return nullptr;
 }
@@ -135,11 +136,14 @@ const PpcKernelInfo *find_ppc(int fam, int tx, int ty, int threads, int stages) 
 
 
 
+// threads: threads per subdomain (a CTA of a 1D kernel may hold several
+// subdomains); 0 = the first (default) entry for the shape
 const TileKernelInfo *find_tile(int fam, int dim, int tx, int ty, int threads = 0) {
     int n = 0;
     const TileKernelInfo *k = family_tiles(fam, &n);
     for (int i = 0; i < n; ++i)
-        if (k[i].dim == dim && k[i].tx == tx && (dim == 1 || k[i].ty == ty) && (!threads || k[i].threads == threads))
+        if (k[i].dim == dim && k[i].tx == tx && (dim == 1 || k[i].ty == ty) &&
+            (!threads || k[i].threads / k[i].tiles_per_cta == threads))
             return &k[i];
     return nullptr;
 }
@@ -531,7 +535,8 @@ int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int
             const CycArgs &base, void *b0, void *b1, ThirdBuffer third, double tol, long long max_cycles,
             long long fixed, cudaStream_t s, RunOut *ro, double *hist_out, long long hist_cap, long long *hist_len,
             int *used_persistent) {
-    const PersistKernelInfo *pk = classic ? nullptr : find_persist(fam, h->d.dim, ki->tx, ki->ty, ki->threads);
+    const PersistKernelInfo *pk =
+        classic ? nullptr : find_persist(fam, h->d.dim, ki->tx, ki->ty, ki->threads / ki->tiles_per_cta);
     PersistKernel pclassic = nullptr;
     if (classic) {
         const PersistClassicInfo *pc = fam == FAM_F64 ? persist_classic_f64()
@@ -748,7 +753,8 @@ void fill_stats_config(const hj_handle *h, hj_stats *st, double t0) {
     st->tile_x = h->p.tile_x;
     st->tile_y = h->d.dim == 2 ? h->p.tile_y : 1;
     st->k = h->p.k;
-    st->tile_threads = h->ir ? h->k_inner->threads : h->k_outer ? h->k_outer->threads : 0;
+    const TileKernelInfo *tk = h->ir ? h->k_inner : h->k_outer;
+    st->tile_threads = tk ? tk->threads / tk->tiles_per_cta : 0;
     const PpcKernelInfo *pk = h->ir ? h->p_inner : h->p_outer;
     const bool ppc = want_ppc(h, pk, h->p.method == HJ_METHOD_CLASSIC);
     st->pipeline_stages = ppc ? pk->stages : 0;
@@ -810,7 +816,7 @@ int hj_tile_variants(int dim, int precision, int *txt, int cap) {
         if (txt && m < cap) {
             txt[3 * m] = k[i].tx;
             txt[3 * m + 1] = k[i].ty;
-            txt[3 * m + 2] = k[i].threads;
+            txt[3 * m + 2] = k[i].threads / k[i].tiles_per_cta;
         }
         ++m;
     }
@@ -955,7 +961,7 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
             int n = 0, best = 0;
             const TileKernelInfo *k = family_tiles(fam, &n);
             for (int i = 0; i < n; ++i)
-                if (k[i].dim == 1 && k[i].tx == p.tile_x) best = std::max(best, k[i].threads);
+                if (k[i].dim == 1 && k[i].tx == p.tile_x) best = std::max(best, k[i].threads / k[i].tiles_per_cta);
             p.tile_threads = best;
             h->p.tile_threads = best;
         }

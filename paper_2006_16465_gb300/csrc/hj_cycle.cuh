@@ -423,11 +423,13 @@ __global__ void __launch_bounds__(32 * NW) hier2d_kernel(const CycArgs a) {
 
 // ---------------------------------------------------------------------------
 // 1D tile: a subdomain of TX = 32*C*WPT points of one row (the independent
-// copies of Section 3.5, one row per blockIdx.y) is one CTA of WPT warps; warp
-// q owns the 32*C points starting at x0 + q*32*C, lane l the C consecutive
-// points from there + l*C.  Neighbouring warps swap their edge points through
-// a double-buffered shared array (one barrier per subiteration); with WPT > 1
-// binary64 updates run on WPT sub-partitions at once.
+// copies of Section 3.5, one row per blockIdx.y) is swept by WPT warps; warp
+// q of it owns the 32*C points starting at x0 + q*32*C, lane l the C
+// consecutive points from there + l*C.  Neighbouring warps swap their edge
+// points through a double-buffered shared array (one barrier per
+// subiteration); with WPT > 1 binary64 updates run on WPT sub-partitions at
+// once.  A CTA holds WPB subdomains side by side (WPB > 1 only with WPT = 1,
+// so that no barrier sits in a branch that differs between subdomains).
 // ---------------------------------------------------------------------------
 template <typename T, int WPT>
 struct Xchg1D {
@@ -439,7 +441,7 @@ __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type til
                                                                                     const int row,
                                                                                     Xchg1D<T, WPT> &xb) {
     constexpr int TX = 32 * C * WPT;
-    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, q = (threadIdx.x >> 5) % WPT;
     const int xl = x0 + q * 32 * C + lane * C;
     const long long ld = a.ld;
     const int nx = a.nx;
@@ -520,19 +522,23 @@ __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type til
     return acc;
 }
 
-template <typename S, typename T, int C, int WPT, bool EXACT, bool SIG, bool RES>
-__global__ void __launch_bounds__(32 * WPT) hier1d_kernel(const CycArgs a) {
+template <typename S, typename T, int C, int WPT, int WPB, bool EXACT, bool SIG, bool RES>
+__global__ void __launch_bounds__(32 * WPT * WPB) hier1d_kernel(const CycArgs a) {
+    static_assert(WPT == 1 || WPB == 1, "several subdomains per CTA only with one warp each");
     if constexpr (RES) {
         if (*(volatile int *)&a.red.ctl->done >= 0) return;
     }
     constexpr int TX = 32 * C * WPT;
     __shared__ Xchg1D<T, WPT> xb;
-    const int x0 = 1 + blockIdx.x * TX;
+    const int x0 = 1 + (blockIdx.x * WPB + (int)(threadIdx.x >> 5) / WPT) * TX;
     const int row = blockIdx.y;
     typename std::conditional<EXACT, double, T>::type acc = 0;
-    // x0 is uniform across the CTA, so the whole CTA takes the same branch
-    if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, WPT, EXACT, SIG, RES, false>(a, x0, row, xb);
-    else acc = tile1d<S, T, C, WPT, EXACT, SIG, RES, true>(a, x0, row, xb);
+    // with WPT > 1, x0 is uniform across the CTA and the whole CTA takes the
+    // same branch; with WPB > 1 the branches hold no barrier
+    if (x0 <= a.nx) {
+        if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, WPT, EXACT, SIG, RES, false>(a, x0, row, xb);
+        else acc = tile1d<S, T, C, WPT, EXACT, SIG, RES, true>(a, x0, row, xb);
+    }
     if constexpr (RES) reduce_grid_acc(a.red, acc);
 }
 
@@ -609,10 +615,11 @@ __global__ void __launch_bounds__(256) classic1d_kernel(const CycArgs a) {
      {{hj::hier2d_kernel<S, T, C, R, NW, H, EX, false, false>,                                        \
        hj::hier2d_kernel<S, T, C, R, NW, H, EX, false, true>},                                        \
       {hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, false>, hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, true>}}}
-#define HJ_K1D(S, T, C, WPT, EX)                                                                     \
-    {1, 32 * (C) * (WPT), 1, 32 * (WPT), 1,                                                          \
-     {{hj::hier1d_kernel<S, T, C, WPT, EX, false, false>, hj::hier1d_kernel<S, T, C, WPT, EX, false, true>}, \
-      {hj::hier1d_kernel<S, T, C, WPT, EX, true, false>, hj::hier1d_kernel<S, T, C, WPT, EX, true, true>}}}
+#define HJ_K1D(S, T, C, WPT, WPB, EX)                                                                \
+    {1, 32 * (C) * (WPT), 1, 32 * (WPT) * (WPB), (WPB),                                              \
+     {{hj::hier1d_kernel<S, T, C, WPT, WPB, EX, false, false>,                                       \
+       hj::hier1d_kernel<S, T, C, WPT, WPB, EX, false, true>},                                       \
+      {hj::hier1d_kernel<S, T, C, WPT, WPB, EX, true, false>, hj::hier1d_kernel<S, T, C, WPT, WPB, EX, true, true>}}}
 #define HJ_KC2D(S, T, EX)                                                                             \
     {2, 32, 8, 256, 1,                                                                               \
      {{hj::classic2d_kernel<S, T, EX, false, false>, hj::classic2d_kernel<S, T, EX, false, true>},   \

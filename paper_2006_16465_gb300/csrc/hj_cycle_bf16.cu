@@ -13,16 +13,16 @@ static const TileKernelInfo k_tiles[] = {
     HJ_K2D(__nv_bfloat16, float, 2, 16, 4, 1, false),    // 64 x 64
     HJ_K2D(__nv_bfloat16, float, 4, 8, 4, 1, false),     // 128 x 32
     HJ_K2D(__nv_bfloat16, float, 4, 8, 8, 1, false),     // 128 x 64
-    HJ_K1D(__nv_bfloat16, float, 1, 1, false),    // 32
-    HJ_K1D(__nv_bfloat16, float, 2, 1, false),    // 64
-    HJ_K1D(__nv_bfloat16, float, 1, 2, false),    // 64, 2 warps
-    HJ_K1D(__nv_bfloat16, float, 4, 1, false),    // 128
-    HJ_K1D(__nv_bfloat16, float, 2, 2, false),    // 128, 2 warps
-    HJ_K1D(__nv_bfloat16, float, 1, 4, false),    // 128, 4 warps
-    HJ_K1D(__nv_bfloat16, float, 8, 1, false),    // 256
-    HJ_K1D(__nv_bfloat16, float, 4, 2, false),    // 256, 2 warps
-    HJ_K1D(__nv_bfloat16, float, 2, 4, false),    // 256, 4 warps
-    HJ_K1D(__nv_bfloat16, float, 1, 8, false),    // 256, 8 warps
+    HJ_K1D(__nv_bfloat16, float, 1, 1, 4, false),    // 32
+    HJ_K1D(__nv_bfloat16, float, 2, 1, 4, false),    // 64
+    HJ_K1D(__nv_bfloat16, float, 1, 2, 1, false),    // 64, 2 warps
+    HJ_K1D(__nv_bfloat16, float, 4, 1, 4, false),    // 128
+    HJ_K1D(__nv_bfloat16, float, 2, 2, 1, false),    // 128, 2 warps
+    HJ_K1D(__nv_bfloat16, float, 1, 4, 1, false),    // 128, 4 warps
+    HJ_K1D(__nv_bfloat16, float, 8, 1, 4, false),    // 256
+    HJ_K1D(__nv_bfloat16, float, 4, 2, 1, false),    // 256, 2 warps
+    HJ_K1D(__nv_bfloat16, float, 2, 4, 1, false),    // 256, 4 warps
+    HJ_K1D(__nv_bfloat16, float, 1, 8, 1, false),    // 256, 8 warps
 };
 static const TileKernelInfo k_classic[] = {HJ_KC2D(__nv_bfloat16, float, false), HJ_KC1D(__nv_bfloat16, float, false)};
 

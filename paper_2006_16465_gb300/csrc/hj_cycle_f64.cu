@@ -11,16 +11,16 @@ static const TileKernelInfo k_tiles[] = {
     HJ_K2D(double, double, 1, 16, 4, 1, true),   // 32 x 64
     HJ_K2D(double, double, 2, 8, 4, 1, true),    // 64 x 32
     HJ_K2D(double, double, 2, 8, 8, 1, true),    // 64 x 64
-    HJ_K1D(double, double, 1, 1, true),    // 32
-    HJ_K1D(double, double, 2, 1, true),    // 64
-    HJ_K1D(double, double, 1, 2, true),    // 64, 2 warps
-    HJ_K1D(double, double, 4, 1, true),    // 128
-    HJ_K1D(double, double, 2, 2, true),    // 128, 2 warps
-    HJ_K1D(double, double, 1, 4, true),    // 128, 4 warps
-    HJ_K1D(double, double, 8, 1, true),    // 256
-    HJ_K1D(double, double, 4, 2, true),    // 256, 2 warps
-    HJ_K1D(double, double, 2, 4, true),    // 256, 4 warps
-    HJ_K1D(double, double, 1, 8, true),    // 256, 8 warps
+    HJ_K1D(double, double, 1, 1, 4, true),    // 32
+    HJ_K1D(double, double, 2, 1, 4, true),    // 64
+    HJ_K1D(double, double, 1, 2, 1, true),    // 64, 2 warps
+    HJ_K1D(double, double, 4, 1, 4, true),    // 128
+    HJ_K1D(double, double, 2, 2, 1, true),    // 128, 2 warps
+    HJ_K1D(double, double, 1, 4, 1, true),    // 128, 4 warps
+    HJ_K1D(double, double, 8, 1, 4, true),    // 256
+    HJ_K1D(double, double, 4, 2, 1, true),    // 256, 2 warps
+    HJ_K1D(double, double, 2, 4, 1, true),    // 256, 4 warps
+    HJ_K1D(double, double, 1, 8, 1, true),    // 256, 8 warps
 };
 static const TileKernelInfo k_classic[] = {HJ_KC2D(double, double, true), HJ_KC1D(double, double, true)};
 

@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(32 * NW) persist2d_kernel(const PersistArgs P)
     }
 }
 
-template <typename S, typename T, int C, int WPT, bool EXACT, bool SIG>
-__global__ void __launch_bounds__(32 * WPT) persist1d_kernel(const PersistArgs P) {
+template <typename S, typename T, int C, int WPT, int WPB, bool EXACT, bool SIG>
+__global__ void __launch_bounds__(32 * WPT * WPB) persist1d_kernel(const PersistArgs P) {
     constexpr int TX = 32 * C * WPT;
     __shared__ Xchg1D<T, WPT> xb;
     for (long long it = 0; it < P.max_iters; ++it) {
@@ -201,11 +201,13 @@ __global__ void __launch_bounds__(32 * WPT) persist1d_kernel(const PersistArgs P
                 a.uout = const_cast<void *>(t);
             }
             const int blk = P.item_blk[item], bxn = P.prob_tiles_x[p];
-            const int x0 = 1 + (blk % bxn) * TX;
+            const int x0 = 1 + ((blk % bxn) * WPB + (int)(threadIdx.x >> 5) / WPT) * TX;
             const int row = blk / bxn;
             typename std::conditional<EXACT, double, T>::type acc = 0;
-            if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, WPT, EXACT, SIG, true, false>(a, x0, row, xb);
-            else acc = tile1d<S, T, C, WPT, EXACT, SIG, true, true>(a, x0, row, xb);
+            if (x0 <= a.nx) {
+                if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, WPT, EXACT, SIG, true, false>(a, x0, row, xb);
+                else acc = tile1d<S, T, C, WPT, EXACT, SIG, true, true>(a, x0, row, xb);
+            }
             const double s = cta_sum(acc);
             if (threadIdx.x == 0) P.partial[(size_t)parity * P.nitems + item] = s;
         }
@@ -309,8 +311,8 @@ __global__ void __launch_bounds__(32 * NW) persist2d_one_kernel(const PersistArg
     }
 }
 
-template <typename S, typename T, int C, int WPT, bool EXACT, bool SIG>
-__global__ void __launch_bounds__(32 * WPT) persist1d_one_kernel(const PersistArgs P) {
+template <typename S, typename T, int C, int WPT, int WPB, bool EXACT, bool SIG>
+__global__ void __launch_bounds__(32 * WPT * WPB) persist1d_one_kernel(const PersistArgs P) {
     constexpr int TX = 32 * C * WPT;
     __shared__ Xchg1D<T, WPT> xb;
     OneState ls{-1, HJ_OK, 0, 0.0, 0.0, 0.0, 0};
@@ -324,11 +326,13 @@ __global__ void __launch_bounds__(32 * WPT) persist1d_one_kernel(const PersistAr
             a.uout = const_cast<void *>(t);
         }
         for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
-            const int x0 = 1 + (item % bxn) * TX;
+            const int x0 = 1 + ((item % bxn) * WPB + (int)(threadIdx.x >> 5) / WPT) * TX;
             const int row = item / bxn;
             typename std::conditional<EXACT, double, T>::type acc = 0;
-            if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, WPT, EXACT, SIG, true, false>(a, x0, row, xb);
-            else acc = tile1d<S, T, C, WPT, EXACT, SIG, true, true>(a, x0, row, xb);
+            if (x0 <= a.nx) {
+                if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, WPT, EXACT, SIG, true, false>(a, x0, row, xb);
+                else acc = tile1d<S, T, C, WPT, EXACT, SIG, true, true>(a, x0, row, xb);
+            }
             const double s = cta_sum(acc);
             if (threadIdx.x == 0) P.partial[(size_t)parity * P.nitems + item] = s;
         }
@@ -418,8 +422,8 @@ struct PersistClassicInfo {
 #define HJ_KPC(S, T, EX) \
     {{{hj::persist_classic_one_kernel<S, T, 1, EX, false>, hj::persist_classic_one_kernel<S, T, 1, EX, true>}, \
       {hj::persist_classic_one_kernel<S, T, 2, EX, false>, hj::persist_classic_one_kernel<S, T, 2, EX, true>}}}
-#define HJ_KP1D(S, T, C, WPT, EX) \
-    {1, 32 * (C) * (WPT), 1, 32 * (WPT), 1, \
-     {hj::persist1d_kernel<S, T, C, WPT, EX, false>, hj::persist1d_kernel<S, T, C, WPT, EX, true>}, \
-     {hj::persist1d_one_kernel<S, T, C, WPT, EX, false>, hj::persist1d_one_kernel<S, T, C, WPT, EX, true>}, \
+#define HJ_KP1D(S, T, C, WPT, WPB, EX) \
+    {1, 32 * (C) * (WPT), 1, 32 * (WPT) * (WPB), (WPB), \
+     {hj::persist1d_kernel<S, T, C, WPT, WPB, EX, false>, hj::persist1d_kernel<S, T, C, WPT, WPB, EX, true>}, \
+     {hj::persist1d_one_kernel<S, T, C, WPT, WPB, EX, false>, hj::persist1d_one_kernel<S, T, C, WPT, WPB, EX, true>}, \
      {nullptr, nullptr}, {nullptr, nullptr}, {0, 0}, 0, 0}

@@ -14,16 +14,16 @@ static const PersistKernelInfo k_persist[] = {
     HJ_KP2D(__nv_bfloat16, float, 2, 16, 2, 1, false),
     HJ_KP2D(__nv_bfloat16, float, 2, 16, 4, 1, false),
     HJ_KP2D(__nv_bfloat16, float, 4, 8, 8, 1, false),
-    HJ_KP1D(__nv_bfloat16, float, 1, 1, false),
-    HJ_KP1D(__nv_bfloat16, float, 2, 1, false),
-    HJ_KP1D(__nv_bfloat16, float, 1, 2, false),
-    HJ_KP1D(__nv_bfloat16, float, 4, 1, false),
-    HJ_KP1D(__nv_bfloat16, float, 2, 2, false),
-    HJ_KP1D(__nv_bfloat16, float, 1, 4, false),
-    HJ_KP1D(__nv_bfloat16, float, 8, 1, false),
-    HJ_KP1D(__nv_bfloat16, float, 4, 2, false),
-    HJ_KP1D(__nv_bfloat16, float, 2, 4, false),
-    HJ_KP1D(__nv_bfloat16, float, 1, 8, false),
+    HJ_KP1D(__nv_bfloat16, float, 1, 1, 4, false),
+    HJ_KP1D(__nv_bfloat16, float, 2, 1, 4, false),
+    HJ_KP1D(__nv_bfloat16, float, 1, 2, 1, false),
+    HJ_KP1D(__nv_bfloat16, float, 4, 1, 4, false),
+    HJ_KP1D(__nv_bfloat16, float, 2, 2, 1, false),
+    HJ_KP1D(__nv_bfloat16, float, 1, 4, 1, false),
+    HJ_KP1D(__nv_bfloat16, float, 8, 1, 4, false),
+    HJ_KP1D(__nv_bfloat16, float, 4, 2, 1, false),
+    HJ_KP1D(__nv_bfloat16, float, 2, 4, 1, false),
+    HJ_KP1D(__nv_bfloat16, float, 1, 8, 1, false),
 };
 const PersistKernelInfo *persist_kernels_bf16(int *n) { *n = sizeof(k_persist) / sizeof(k_persist[0]); return k_persist; }
 

@@ -236,6 +236,28 @@ def test_f32_pipelined_solve_matches_graph_solve():
     np.testing.assert_allclose(a["history"], b["history"], rtol=1e-6)
 
 
+def test_pipelined_launch_shapes_give_the_same_iterates():
+    """Threads per subdomain, copy stages and CTAs per SM change the launch,
+    not the arithmetic: every shape stops at the same cycle with the same
+    iterate."""
+    torch = _torch()
+    p = W.random_bc_problem(2, 200, 170, seed=9, sigma_kind="field", asym=True)
+    sig = to_dev(p.st.sigma, 2, torch.float64)
+    import paper_2006_16465_gb300 as hj
+    outs = []
+    for th, stg, cps in [(32, 1, 0), (32, 2, 0), (64, 1, 3), (32, 1, 2), (64, 2, 1)]:
+        s = hj.Solver(p.st, sigma=sig, tile_x=32, tile_y=32, k=6, precision="f32", tol=1e-5, check_every=10,
+                      tile_threads=th, pipeline_stages=stg, ctas_per_sm=cps, **PIPE)
+        u = to_dev(p.u0, 2, torch.float32)
+        out = s.solve(to_dev(p.f, 2, torch.float32), u)
+        assert out["status"] == 0 and out["pipeline_stages"] == stg and out["ctas_per_sm"] == cps
+        outs.append((out["cycles"], to_host(u, 200)))
+        s.close()
+    for c, u in outs[1:]:
+        assert c == outs[0][0]
+        assert np.array_equal(u, outs[0][1])
+
+
 def test_residual_api_matches_oracle():
     torch = _torch()
     for dim, nx, ny in [(2, 90, 70), (1, 333, 3)]:
