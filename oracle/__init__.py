@@ -78,6 +78,11 @@ def lib():
         L.hjo_adjoint.argtypes = [P, _D, _D, _D, _D, C.c_int, C.c_int, C.c_int, C.c_double,
                                   C.c_long, C.POINTER(C.c_int)]
         L.hjo_adjoint.restype = C.c_long
+        L.hjo_hier_cycle_ovl.argtypes = [P, _D, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.hjo_solve_ovl.argtypes = [P, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                    C.c_double, C.c_long, _D, C.c_long, C.POINTER(C.c_int)]
+        L.hjo_solve_ovl.restype = C.c_long
+        L.hjo_run_fixed_ovl.argtypes = [P, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_long]
         L.hjo_paper_smem_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
         L.hjo_paper_smem_bytes.restype = C.c_long
         _lib = L
@@ -144,22 +149,41 @@ def hier_cycle(st, f, u, tx, ty, k):
     return out
 
 
-def run_fixed(st, f, u0, ncycles, tx=32, ty=32, k=1, classic=False):
-    """u after exactly ncycles hierarchical cycles (or classic sweeps)."""
+def hier_cycle_ovl(st, f, u, tx, ty, k, ox, oy=0):
+    """One cycle with overlapping subdomains (ox, oy shared points between
+    neighbours; Sections 3.4, 4.3)."""
+    p = _prob(st)
+    out = np.zeros(p.shape)
+    lib().hjo_hier_cycle_ovl(p.ref, _dp(_grid(f)), _dp(_grid(u)), _dp(out), tx, ty, k, int(ox), int(oy))
+    return out
+
+
+def run_fixed(st, f, u0, ncycles, tx=32, ty=32, k=1, classic=False, overlap=(0, 0)):
+    """u after exactly ncycles hierarchical cycles (or classic sweeps);
+    overlap = (ox, oy) points shared by neighbouring subdomains."""
     p = _prob(st)
     u = _grid(u0).copy()
-    lib().hjo_run_fixed(p.ref, _dp(_grid(f)), _dp(u), int(classic), tx, ty, k, int(ncycles))
+    if overlap != (0, 0) and not classic:
+        lib().hjo_run_fixed_ovl(p.ref, _dp(_grid(f)), _dp(u), tx, ty, k, int(overlap[0]), int(overlap[1]),
+                                int(ncycles))
+    else:
+        lib().hjo_run_fixed(p.ref, _dp(_grid(f)), _dp(u), int(classic), tx, ty, k, int(ncycles))
     return u
 
 
-def solve(st, f, u0, tol, max_cycles, tx=32, ty=32, k=1, classic=False, hist_cap=0):
+def solve(st, f, u0, tol, max_cycles, tx=32, ty=32, k=1, classic=False, hist_cap=0, overlap=(0, 0)):
     """Returns (u_c, c, status, hist): c = first cycle with ||r_c|| <= tol ||r_0||."""
     p = _prob(st)
     u = _grid(u0).copy()
     hist = np.zeros(max(hist_cap, 1))
     status = C.c_int(0)
-    c = lib().hjo_solve(p.ref, _dp(_grid(f)), _dp(u), int(classic), tx, ty, k, float(tol),
-                        int(max_cycles), _dp(hist), int(hist_cap), C.byref(status))
+    if overlap != (0, 0) and not classic:
+        c = lib().hjo_solve_ovl(p.ref, _dp(_grid(f)), _dp(u), int(classic), tx, ty, k, int(overlap[0]),
+                                int(overlap[1]), float(tol), int(max_cycles), _dp(hist), int(hist_cap),
+                                C.byref(status))
+    else:
+        c = lib().hjo_solve(p.ref, _dp(_grid(f)), _dp(u), int(classic), tx, ty, k, float(tol),
+                            int(max_cycles), _dp(hist), int(hist_cap), C.byref(status))
     return u, int(c), int(status.value), hist[:min(hist_cap, c + 1)]
 
 

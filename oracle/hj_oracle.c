@@ -201,12 +201,113 @@ void hjo_hier_cycle(const hjo_problem *p, const double *f, const double *uin, do
     free(L[1]);
 }
 
+/* Subdomains along one dimension with overlap (Sections 3.4 and 4.3).
+ * Subdomain j of J spans [start, end] of the interior 1..n: T points at
+ * stride S = T - o, the last one clamped so that it ends at n (with o = 0 the
+ * last one is truncated instead, as in hjo_hier_cycle).  Neighbouring
+ * subdomains share the points of their overlap; the left one keeps the left
+ * half of them and the right one the right half (with an odd count the right
+ * one keeps the middle point), so every interior point is owned by exactly
+ * one subdomain: [own_lo, own_hi]. */
+static long ovl_count(long n, long T, long o)
+{
+    if (n <= T) return 1;
+    if (o == 0) return (n + T - 1) / T;
+    return (n - T + (T - o) - 1) / (T - o) + 1;
+}
+
+static void ovl_span(long j, long J, long n, long T, long o, long *start, long *end, long *own_lo, long *own_hi)
+{
+    const long S = T - o;
+    long st = 1 + j * S;
+    if (o > 0 && J > 1 && j == J - 1) st = n - T + 1;
+    *start = st;
+    *end = st + T - 1 < n ? st + T - 1 : n;
+    if (j == 0) {
+        *own_lo = 1;
+    } else {
+        long ps, pe, d1, d2;
+        ovl_span(j - 1, J, n, T, o, &ps, &pe, &d1, &d2);   /* previous subdomain's span only */
+        *own_lo = st + (pe - st + 1) / 2;
+    }
+    if (j == J - 1) {
+        *own_hi = n;
+    } else {
+        const long ns = (o > 0 && J > 1 && j + 1 == J - 1) ? n - T + 1 : 1 + (j + 1) * S;
+        *own_hi = ns + (*end - ns + 1) / 2 - 1;
+    }
+}
+
+/* One hierarchical cycle with overlapping subdomains (Sections 3.4 and 4.3):
+ * every subdomain stages its points plus the one-point halo from u_in, runs k
+ * Jacobi subiterations on all its points with the halo frozen, and writes
+ * only the points it owns (ovl_span) to u_out.  ox = oy = 0 is the cycle of
+ * hjo_hier_cycle.  Parity: pinned (ox = oy = 0 equals hjo_hier_cycle; k = 1
+ * equals a classic sweep for any overlap; large k equals restricted additive
+ * Schwarz with dense subdomain solves; the overlap count of SURVEY's probe). */
+void hjo_hier_cycle_ovl(const hjo_problem *p, const double *f, const double *uin, double *uout,
+                        int tx, int ty, int k, int ox, int oy)
+{
+    const long W = width_of(p);
+    if (p->dim == 1) { ty = 1; oy = 0; }
+    copy_ghosts(p, uin, uout);
+    const long lw = tx + 2, lh = (p->dim == 2) ? ty + 2 : 1;
+    double *L[2];
+    L[0] = (double *)malloc(sizeof(double) * (size_t)(lw * lh));
+    L[1] = (double *)malloc(sizeof(double) * (size_t)(lw * lh));
+    const long Jx = ovl_count(p->nx, tx, ox);
+    /* 2D: subdomains in y as in x; 1D: every copy (row) on its own */
+    const long Jy = (p->dim == 2) ? ovl_count(p->ny, ty, oy) : p->ny;
+    for (long jy = 0; jy < Jy; ++jy) {
+        long j0, j1, oj0, oj1;
+        if (p->dim == 2) {
+            ovl_span(jy, Jy, p->ny, ty, oy, &j0, &j1, &oj0, &oj1);
+        } else {
+            j0 = j1 = oj0 = oj1 = jy;
+        }
+        for (long jx = 0; jx < Jx; ++jx) {
+            long i0, i1, oi0, oi1;
+            ovl_span(jx, Jx, p->nx, tx, ox, &i0, &i1, &oi0, &oi1);
+            const long hj0 = (p->dim == 2) ? j0 - 1 : j0;
+            const long hj1 = (p->dim == 2) ? j1 + 1 : j1;
+            for (long j = hj0; j <= hj1; ++j)
+                for (long i = i0 - 1; i <= i1 + 1; ++i) {
+                    const long l = (j - hj0) * lw + (i - (i0 - 1));
+                    L[0][l] = uin[j * W + i];
+                    L[1][l] = uin[j * W + i];
+                }
+            for (int s = 0; s < k; ++s) {
+                const double *src = L[s % 2];
+                double *dst = L[(s + 1) % 2];
+                for (long j = j0; j <= j1; ++j)
+                    for (long i = i0; i <= i1; ++i) {
+                        const long l = (j - hj0) * lw + (i - (i0 - 1));
+                        const double uS = p->dim == 2 ? src[l - lw] : 0.0;
+                        const double uN = p->dim == 2 ? src[l + lw] : 0.0;
+                        dst[l] = jacobi_point(p, f[j * W + i], diag_at(p, j * W + i),
+                                              src[l - 1], src[l + 1], uS, uN);
+                    }
+            }
+            const double *fin = L[k % 2];
+            for (long j = oj0; j <= oj1; ++j)
+                for (long i = oi0; i <= oi1; ++i)
+                    uout[j * W + i] = fin[(j - hj0) * lw + (i - (i0 - 1))];
+        }
+    }
+    free(L[0]);
+    free(L[1]);
+}
+
 /* Iterate classic sweeps (classic != 0) or hierarchical cycles from u (in/out)
  * until ||r_c|| <= tol * ||r_0|| (L2 residual reduced by the factor tol,
  * Sections 3.5 and 4.2), or max_cycles.  On return u holds u_c for the
  * returned c (the first iterate that met the tolerance, else the last one);
  * hist[c] = ||r_c|| for c < hist_cap.  *status: 0 converged, 1 not converged,
  * 2 diverged (non-finite residual).  Parity: pinned through its parts. */
+long hjo_solve_ovl(const hjo_problem *p, const double *f, double *u, int classic,
+                   int tx, int ty, int k, int ox, int oy, double tol, long max_cycles,
+                   double *hist, long hist_cap, int *status);
+
 long hjo_solve(const hjo_problem *p, const double *f, double *u, int classic,
                int tx, int ty, int k, double tol, long max_cycles,
                double *hist, long hist_cap, int *status)
@@ -245,6 +346,49 @@ void hjo_run_fixed(const hjo_problem *p, const double *f, double *u, int classic
     for (long c = 0; c < ncycles; ++c) {
         if (classic) hjo_jacobi_sweep(p, f, cur, nxt);
         else hjo_hier_cycle(p, f, cur, nxt, tx, ty, k);
+        double *t = cur; cur = nxt; nxt = t;
+    }
+    if (cur != u) memcpy(u, cur, sizeof(double) * n);
+    free(v);
+}
+
+/* hjo_solve / hjo_run_fixed with overlapping subdomains (ox, oy points). */
+long hjo_solve_ovl(const hjo_problem *p, const double *f, double *u, int classic,
+                   int tx, int ty, int k, int ox, int oy, double tol, long max_cycles,
+                   double *hist, long hist_cap, int *status)
+{
+    const size_t n = (size_t)(rows_of(p) * width_of(p));
+    double *v = (double *)malloc(sizeof(double) * n);
+    memcpy(v, u, sizeof(double) * n);
+    const double r0 = sqrt(hjo_residual_sq(p, f, u));
+    long c = 0;
+    int st = 1;
+    double *cur = u, *nxt = v;
+    for (;;) {
+        const double rc = (c == 0) ? r0 : sqrt(hjo_residual_sq(p, f, cur));
+        if (hist && c < hist_cap) hist[c] = rc;
+        if (!isfinite(rc)) { st = 2; break; }
+        if (rc <= tol * r0) { st = 0; break; }
+        if (c >= max_cycles) { st = 1; break; }
+        if (classic) hjo_jacobi_sweep(p, f, cur, nxt);
+        else hjo_hier_cycle_ovl(p, f, cur, nxt, tx, ty, k, ox, oy);
+        double *t = cur; cur = nxt; nxt = t;
+        ++c;
+    }
+    if (cur != u) memcpy(u, cur, sizeof(double) * n);
+    free(v);
+    if (status) *status = st;
+    return c;
+}
+
+void hjo_run_fixed_ovl(const hjo_problem *p, const double *f, double *u, int tx, int ty, int k, int ox, int oy,
+                       long ncycles)
+{
+    const size_t n = (size_t)(rows_of(p) * width_of(p));
+    double *v = (double *)malloc(sizeof(double) * n);
+    double *cur = u, *nxt = v;
+    for (long c = 0; c < ncycles; ++c) {
+        hjo_hier_cycle_ovl(p, f, cur, nxt, tx, ty, k, ox, oy);
         double *t = cur; cur = nxt; nxt = t;
     }
     if (cur != u) memcpy(u, cur, sizeof(double) * n);
