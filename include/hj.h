@@ -161,6 +161,16 @@ typedef struct {
     int ctas_per_sm;      /* TMA-pipelined kernel: resident CTAs per SM (0 = as
                              many as fit).  Fewer CTAs keep fewer copies in
                              flight, which HBM can serve at a higher rate     */
+    int overlap_x;        /* overlapping subdomains (Sections 3.4 and 4.3):
+                             points shared by neighbouring subdomains along x
+                             (0 <= overlap_x < tile_x).  Starts advance by
+                             tile_x - overlap_x, the last subdomain ends at nx,
+                             and each shared point is written by the subdomain
+                             in which it lies further from an edge (an overlap
+                             is split at its midpoint).  Runs on CUDA graphs of
+                             the one-CTA-per-subdomain kernels; persistent = 1,
+                             pipeline = 1, classic and batched solves reject it */
+    int overlap_y;        /* the same along y (2D; 0 <= overlap_y < tile_y)   */
 } hj_params;
 
 typedef struct {
@@ -187,7 +197,7 @@ typedef struct {
  * check_every = 64, max_cycles = 10^7, tol = 1e-6, fixed_cycles = 0,
  * inner_tol = 1e-4, inner_max_cycles = 10^6, max_outer = 60, persistent = -1,
  * autotune = 0, pipeline = -1, tile_threads = 0, pipeline_stages = 0,
- * inner_stall = 32, ctas_per_sm = 0. */
+ * inner_stall = 32, ctas_per_sm = 0, overlap_x = overlap_y = 0. */
 HJ_API void hj_default_params(hj_params *p);
 
 /* Create a solver for one problem shape.  Validates the descriptor and

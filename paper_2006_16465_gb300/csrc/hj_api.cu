@@ -181,8 +181,14 @@ CycArgs base_args(const hj_handle *h, bool transpose) {
     a.gS = (float)(-a.cS * a.invd); a.gN = (float)(-a.cN * a.invd);
     a.finvd = (float)a.invd;
     a.fdconst = (float)a.dconst;
+    a.ox = h->p.overlap_x;
+    a.oy = h->d.dim == 2 ? h->p.overlap_y : 0;
+    a.jx = subdomain_count(h->d.nx, h->p.tile_x, a.ox);
+    a.jy = h->d.dim == 2 ? subdomain_count(h->d.ny, h->p.tile_y, a.oy) : h->d.ny;
     return a;
 }
+
+bool overlapped(const hj_handle *h) { return h->p.overlap_x > 0 || (h->d.dim == 2 && h->p.overlap_y > 0); }
 
 RedArgs red_args(const hj_handle *h, int mode, double tol, long long max_cycles) {
     RedArgs r;
@@ -212,10 +218,12 @@ void geometry(const hj_handle *h, const TileKernelInfo *ki, bool classic, dim3 *
         *block = h->d.dim == 2 ? dim3(32, 8) : dim3(256);
         return;
     }
+    const bool ovl = overlapped(h);
     if (h->d.dim == 2) {
-        *grid = dim3((nx + ki->tx - 1) / ki->tx, (ny + ki->ty - 1) / ki->ty);
+        *grid = ovl ? dim3(subdomain_count(nx, ki->tx, h->p.overlap_x), subdomain_count(ny, ki->ty, h->p.overlap_y))
+                    : dim3((nx + ki->tx - 1) / ki->tx, (ny + ki->ty - 1) / ki->ty);
     } else {
-        const int tiles = (nx + ki->tx - 1) / ki->tx;
+        const int tiles = ovl ? subdomain_count(nx, ki->tx, h->p.overlap_x) : (nx + ki->tx - 1) / ki->tx;
         *grid = dim3((tiles + ki->tiles_per_cta - 1) / ki->tiles_per_cta, ny);
     }
     *block = dim3(ki->threads);
@@ -289,7 +297,7 @@ struct Plan {
 
 // Whether the TMA-pipelined kernel runs this plan's cycles.
 bool want_ppc(const hj_handle *h, const PpcKernelInfo *pi, bool classic) {
-    if (classic || !pi || h->d.dim != 2) return false;
+    if (classic || !pi || h->d.dim != 2 || overlapped(h)) return false;
     if (h->p.pipeline == 1) return true;
     if (h->p.pipeline != -1) return false;
     const long long ntiles = (long long)((h->d.nx + pi->tx - 1) / pi->tx) * ((h->d.ny + pi->ty - 1) / pi->ty);
@@ -310,7 +318,7 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
     const int nx = h->d.nx, ny = h->d.ny;
     if (!want_ppc(h, pi, classic)) {
         geometry(h, ki, classic, &pl->grid, &pl->block);
-        pl->fn = ki->fn[sig][res];
+        pl->fn = (!classic && overlapped(h)) ? ki->ovl[sig][res] : ki->fn[sig][res];
         pl->ppc = false;
         return HJ_OK;
     }
@@ -549,7 +557,7 @@ int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int
     const long long cblocks = h->d.dim == 2 ? (long long)((h->d.nx + 31) / 32) * ((h->d.ny + 7) / 8)
                                             : (long long)((h->d.nx + 255) / 256) * h->d.ny;
     bool use = false;
-    if ((pk || pclassic) && fixed <= 0 && max_cycles > 0 && h->p.persistent != 0) {
+    if ((pk || pclassic) && fixed <= 0 && max_cycles > 0 && h->p.persistent != 0 && !overlapped(h)) {
         int cap = 0;
         if (pclassic) {
             int occ = 0;
@@ -888,6 +896,14 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     if (ir && p.inner_max_cycles < 1) return seterr(HJ_ERR_INVALID_ARG, "inner_max_cycles must be >= 1");
     if (p.inner_stall < 0) return seterr(HJ_ERR_INVALID_ARG, "inner_stall must be >= 0");
     if (p.ctas_per_sm < 0) return seterr(HJ_ERR_INVALID_ARG, "ctas_per_sm must be >= 0");
+    if (d.dim == 1) p.overlap_y = 0;
+    if (p.overlap_x < 0 || p.overlap_y < 0) return seterr(HJ_ERR_INVALID_ARG, "overlaps must be >= 0");
+    if (p.overlap_x > 0 || p.overlap_y > 0) {
+        if (p.method == HJ_METHOD_CLASSIC) return seterr(HJ_ERR_INVALID_ARG, "overlap applies to hierarchical cycles");
+        if (p.persistent == 1 || p.pipeline == 1)
+            return seterr(HJ_ERR_UNSUPPORTED, "overlapping subdomains run on graphs (persistent and pipeline must not be 1)");
+        if (p.autotune == 1) return seterr(HJ_ERR_UNSUPPORTED, "autotune = 1 picks the subdomain shape: use overlap with a fixed shape");
+    }
     if (ir && p.method == HJ_METHOD_CLASSIC) return seterr(HJ_ERR_UNSUPPORTED, "refinement uses hierarchical cycles");
     if (p.check_every < 1) p.check_every = 1;
     if (p.check_every > 4096) p.check_every = 4096;
@@ -905,6 +921,9 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
         p.pipeline_stages = tp.pipeline_stages;
         p.ctas_per_sm = tp.ctas_per_sm;
     }
+    if (p.overlap_x >= p.tile_x || (d.dim == 2 && p.overlap_y >= p.tile_y))
+        return seterr(HJ_ERR_INVALID_ARG, "overlap (%d, %d) must be smaller than the subdomain (%d, %d)", p.overlap_x,
+                      p.overlap_y, p.tile_x, p.tile_y);
 
     // diagonal dominance (Section 2.1): d_p >= |cW| + |cE| + |cS| + |cN|, d_p > 0
     const double off = fabs(d.cW) + fabs(d.cE) + (d.dim == 2 ? fabs(d.cS) + fabs(d.cN) : 0.0);

@@ -247,7 +247,8 @@ bool measure_launch(Scratch &sc, int prec, int tx, int ty, int th, int stages, i
 // so it is measured on the problem's own grid.  Leaves *p unchanged when the
 // pipelined kernel would not run (1D, small grids, pipeline = 0).
 int tune_launch(const hj_desc &d, hj_params *p) {
-    if (d.dim != 2 || p->pipeline == 0 || p->method == HJ_METHOD_CLASSIC) return HJ_OK;
+    if (d.dim != 2 || p->pipeline == 0 || p->method == HJ_METHOD_CLASSIC || p->overlap_x > 0 || p->overlap_y > 0)
+        return HJ_OK;
     const bool ir = p->precision == HJ_PREC_F32_IR || p->precision == HJ_PREC_BF16CORR_IR;
     const int prec = ir ? HJ_PREC_F32 : p->precision;
     const int fam = prec == HJ_PREC_F64 ? FAM_F64 : FAM_F32;

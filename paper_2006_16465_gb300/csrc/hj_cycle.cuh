@@ -260,10 +260,16 @@ __device__ __forceinline__ void point_update_pair(const Coef<float> &k, float g0
 
 // k subiterations on registers.  Returns this thread's share of
 // ||f - A u_c||^2 (unscaled by d^2 on the fast constant-diagonal path).
-template <typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES, bool PART>
+// Points a subdomain owns (overlapping subdomains write back and count in the
+// residual only these): columns [xlo, xhi], rows [ylo, yhi].
+struct Own {
+    int xlo, xhi, ylo, yhi;
+};
+
+template <typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES, bool PART, bool OVL = false>
 __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type
 sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, const int yb, const int nx,
-         const int ny, T *xbuf) {
+         const int ny, T *xbuf, const Own own = Own{0, 0, 0, 0}) {
     static_assert(H == 1 || H == 2, "one or two bands per warp");
     constexpr int L = 32 / H, TX = L * C;
     constexpr bool PACK = std::is_same<T, float>::value && !EXACT && (C % 2 == 0) && !PART;
@@ -306,6 +312,11 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
                             r0 = n0 - cur[c];
                             r1 = n1 - cur[c + 1];
                         }
+                        if constexpr (OVL) {
+                            const bool orow = yb + r >= own.ylo && yb + r <= own.yhi;
+                            if (!(orow && xl + c >= own.xlo && xl + c <= own.xhi)) r0 = 0;
+                            if (!(orow && xl + c + 1 >= own.xlo && xl + c + 1 <= own.xhi)) r1 = 0;
+                        }
                         acc += (Acc)r0 * (Acc)r0;
                         acc += (Acc)r1 * (Acc)r1;
                     }
@@ -326,6 +337,10 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
                         const bool act = (yb + r <= ny) && (xl + c <= nx);
                         nv = act ? nv : cur[c];
                         if (!act) res = 0;
+                    }
+                    if constexpr (OVL && FIRST && RES) {
+                        if (!(yb + r >= own.ylo && yb + r <= own.yhi && xl + c >= own.xlo && xl + c <= own.xhi))
+                            res = 0;
                     }
                     if constexpr (FIRST && RES) acc += (Acc)res * (Acc)res;
                     t.v[r][c] = nv;
@@ -376,9 +391,9 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
 }
 
 // Write the band's interior points into u_{c+1}.
-template <typename S, typename T, int C, int R, int H, bool SIG, bool PART>
+template <typename S, typename T, int C, int R, int H, bool SIG, bool PART, bool OVL = false>
 __device__ __forceinline__ void store2d(const Tile2D<T, C, R, SIG> &t, const CycArgs &a, const int x0,
-                                        const int yb) {
+                                        const int yb, const Own own = Own{0, 0, 0, 0}) {
     const int li = (threadIdx.x & 31) % (32 / H);
     const int xl = x0 + li * C;
     S *__restrict__ uout = (S *)a.uout;
@@ -388,24 +403,29 @@ __device__ __forceinline__ void store2d(const Tile2D<T, C, R, SIG> &t, const Cyc
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const int col = xl + c;
-            if (!PART || (row <= a.ny && col <= a.nx)) st_s<S, T>(uout + (long long)row * a.ld + col, t.v[r][c]);
+            bool w = !PART || (row <= a.ny && col <= a.nx);
+            if constexpr (OVL) w = w && row >= own.ylo && row <= own.yhi && col >= own.xlo && col <= own.xhi;
+            if (w) st_s<S, T>(uout + (long long)row * a.ld + col, t.v[r][c]);
         }
     }
 }
 
-template <typename S, typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES, bool PART>
-__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type tile2d(const CycArgs &a, const int x0,
-                                                                                    const int y0, T *xbuf) {
+template <typename S, typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES, bool PART,
+          bool OVL = false>
+__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type
+tile2d(const CycArgs &a, const int x0, const int y0, T *xbuf, const Own own = Own{0, 0, 0, 0}) {
     const int yb = y0 + band_of_lane<R, H>() * R;
     const Coef<T> kc = make_coef<T>(a);
     Tile2D<T, C, R, SIG> t;
     stage2d_global<S, T, C, R, H, EXACT, SIG, PART>(t, a, kc, x0, yb);
-    auto acc = sweeps2d<T, C, R, NW, H, EXACT, SIG, RES, PART>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
-    store2d<S, T, C, R, H, SIG, PART>(t, a, x0, yb);
+    auto acc = sweeps2d<T, C, R, NW, H, EXACT, SIG, RES, PART, OVL>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf, own);
+    store2d<S, T, C, R, H, SIG, PART, OVL>(t, a, x0, yb, own);
     return acc;
 }
 
-template <typename S, typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES>
+// OVL: overlapping subdomains (Sections 3.4, 4.3): block (bx, by) is subdomain
+// (bx, by) of a.jx x a.jy, placed and owning points as subdomain_span says.
+template <typename S, typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES, bool OVL = false>
 __global__ void __launch_bounds__(32 * NW) hier2d_kernel(const CycArgs a) {
     if constexpr (RES) {
         if (*(volatile int *)&a.red.ctl->done >= 0) return;
@@ -413,11 +433,19 @@ __global__ void __launch_bounds__(32 * NW) hier2d_kernel(const CycArgs a) {
     constexpr int TX = 32 * C / H, TY = R * NW * H;
     constexpr int XB = NW > 1 ? 2 * NW * 2 * TX : 1;
     __shared__ T xbuf[XB];
-    const int x0 = 1 + blockIdx.x * TX, y0 = 1 + blockIdx.y * TY;
+    int x0 = 1 + blockIdx.x * TX, y0 = 1 + blockIdx.y * TY;
+    Own own{0, 0, 0, 0};
+    if constexpr (OVL) {
+        const Span sx = subdomain_span(blockIdx.x, a.jx, a.nx, TX, a.ox);
+        const Span sy = subdomain_span(blockIdx.y, a.jy, a.ny, TY, a.oy);
+        x0 = sx.start;
+        y0 = sy.start;
+        own = Own{sx.lo, sx.hi, sy.lo, sy.hi};
+    }
     const bool full = (x0 + TX - 1 <= a.nx) && (y0 + TY - 1 <= a.ny);
     typename std::conditional<EXACT, double, T>::type acc;
-    if (full) acc = tile2d<S, T, C, R, NW, H, EXACT, SIG, RES, false>(a, x0, y0, xbuf);
-    else acc = tile2d<S, T, C, R, NW, H, EXACT, SIG, RES, true>(a, x0, y0, xbuf);
+    if (full) acc = tile2d<S, T, C, R, NW, H, EXACT, SIG, RES, false, OVL>(a, x0, y0, xbuf, own);
+    else acc = tile2d<S, T, C, R, NW, H, EXACT, SIG, RES, true, OVL>(a, x0, y0, xbuf, own);
     if constexpr (RES) reduce_grid_acc(a.red, acc);
 }
 
@@ -436,10 +464,9 @@ struct Xchg1D {
     T e[2][WPT > 1 ? WPT : 1][2];   // [parity][warp][first, last]
 };
 
-template <typename S, typename T, int C, int WPT, bool EXACT, bool SIG, bool RES, bool PART>
-__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type tile1d(const CycArgs &a, const int x0,
-                                                                                    const int row,
-                                                                                    Xchg1D<T, WPT> &xb) {
+template <typename S, typename T, int C, int WPT, bool EXACT, bool SIG, bool RES, bool PART, bool OVL = false>
+__device__ __forceinline__ typename std::conditional<EXACT, double, T>::type
+tile1d(const CycArgs &a, const int x0, const int row, Xchg1D<T, WPT> &xb, const int own_lo = 0, const int own_hi = 0) {
     constexpr int TX = 32 * C * WPT;
     const int lane = threadIdx.x & 31, q = (threadIdx.x >> 5) % WPT;
     const int xl = x0 + q * 32 * C + lane * C;
@@ -506,6 +533,9 @@ __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type til
                 nv = act ? nv : cur[c];
                 if (!act) res = 0;
             }
+            if constexpr (OVL && FIRST && RES) {
+                if (!(xl + c >= own_lo && xl + c <= own_hi)) res = 0;
+            }
             if constexpr (FIRST && RES) acc += (Acc)res * (Acc)res;
             v[c] = nv;
         }
@@ -517,12 +547,14 @@ __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type til
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int col = xl + c;
-        if (!PART || col <= nx) st_s<S, T>(uout + rb + col, v[c]);
+        bool w = !PART || col <= nx;
+        if constexpr (OVL) w = w && col >= own_lo && col <= own_hi;
+        if (w) st_s<S, T>(uout + rb + col, v[c]);
     }
     return acc;
 }
 
-template <typename S, typename T, int C, int WPT, int WPB, bool EXACT, bool SIG, bool RES>
+template <typename S, typename T, int C, int WPT, int WPB, bool EXACT, bool SIG, bool RES, bool OVL = false>
 __global__ void __launch_bounds__(32 * WPT * WPB) hier1d_kernel(const CycArgs a) {
     static_assert(WPT == 1 || WPB == 1, "several subdomains per CTA only with one warp each");
     if constexpr (RES) {
@@ -530,14 +562,25 @@ __global__ void __launch_bounds__(32 * WPT * WPB) hier1d_kernel(const CycArgs a)
     }
     constexpr int TX = 32 * C * WPT;
     __shared__ Xchg1D<T, WPT> xb;
-    const int x0 = 1 + (blockIdx.x * WPB + (int)(threadIdx.x >> 5) / WPT) * TX;
+    const int j = blockIdx.x * WPB + (int)(threadIdx.x >> 5) / WPT;   // subdomain along the row
+    int x0 = 1 + j * TX, lo = 0, hi = 0;
+    bool here = x0 <= a.nx;
+    if constexpr (OVL) {
+        here = j < a.jx;
+        if (here) {
+            const Span sp = subdomain_span(j, a.jx, a.nx, TX, a.ox);
+            x0 = sp.start;
+            lo = sp.lo;
+            hi = sp.hi;
+        }
+    }
     const int row = blockIdx.y;
     typename std::conditional<EXACT, double, T>::type acc = 0;
-    // with WPT > 1, x0 is uniform across the CTA and the whole CTA takes the
-    // same branch; with WPB > 1 the branches hold no barrier
-    if (x0 <= a.nx) {
-        if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, WPT, EXACT, SIG, RES, false>(a, x0, row, xb);
-        else acc = tile1d<S, T, C, WPT, EXACT, SIG, RES, true>(a, x0, row, xb);
+    // with WPT > 1, the subdomain is uniform across the CTA and the whole CTA
+    // takes the same branch; with WPB > 1 the branches hold no barrier
+    if (here) {
+        if (x0 + TX - 1 <= a.nx) acc = tile1d<S, T, C, WPT, EXACT, SIG, RES, false, OVL>(a, x0, row, xb, lo, hi);
+        else acc = tile1d<S, T, C, WPT, EXACT, SIG, RES, true, OVL>(a, x0, row, xb, lo, hi);
     }
     if constexpr (RES) reduce_grid_acc(a.red, acc);
 }
@@ -614,17 +657,27 @@ __global__ void __launch_bounds__(256) classic1d_kernel(const CycArgs a) {
     {2, 32 * (C) / (H), (R) * (NW) * (H), 32 * (NW), 1,                                               \
      {{hj::hier2d_kernel<S, T, C, R, NW, H, EX, false, false>,                                        \
        hj::hier2d_kernel<S, T, C, R, NW, H, EX, false, true>},                                        \
-      {hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, false>, hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, true>}}}
+      {hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, false>, hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, true>}}, \
+     {{hj::hier2d_kernel<S, T, C, R, NW, H, EX, false, false, true>,                                  \
+       hj::hier2d_kernel<S, T, C, R, NW, H, EX, false, true, true>},                                  \
+      {hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, false, true>,                                   \
+       hj::hier2d_kernel<S, T, C, R, NW, H, EX, true, true, true>}}}
 #define HJ_K1D(S, T, C, WPT, WPB, EX)                                                                \
     {1, 32 * (C) * (WPT), 1, 32 * (WPT) * (WPB), (WPB),                                              \
      {{hj::hier1d_kernel<S, T, C, WPT, WPB, EX, false, false>,                                       \
        hj::hier1d_kernel<S, T, C, WPT, WPB, EX, false, true>},                                       \
-      {hj::hier1d_kernel<S, T, C, WPT, WPB, EX, true, false>, hj::hier1d_kernel<S, T, C, WPT, WPB, EX, true, true>}}}
+      {hj::hier1d_kernel<S, T, C, WPT, WPB, EX, true, false>, hj::hier1d_kernel<S, T, C, WPT, WPB, EX, true, true>}}, \
+     {{hj::hier1d_kernel<S, T, C, WPT, WPB, EX, false, false, true>,                                 \
+       hj::hier1d_kernel<S, T, C, WPT, WPB, EX, false, true, true>},                                 \
+      {hj::hier1d_kernel<S, T, C, WPT, WPB, EX, true, false, true>,                                  \
+       hj::hier1d_kernel<S, T, C, WPT, WPB, EX, true, true, true>}}}
 #define HJ_KC2D(S, T, EX)                                                                             \
     {2, 32, 8, 256, 1,                                                                               \
      {{hj::classic2d_kernel<S, T, EX, false, false>, hj::classic2d_kernel<S, T, EX, false, true>},   \
-      {hj::classic2d_kernel<S, T, EX, true, false>, hj::classic2d_kernel<S, T, EX, true, true>}}}
+      {hj::classic2d_kernel<S, T, EX, true, false>, hj::classic2d_kernel<S, T, EX, true, true>}},     \
+     {{nullptr, nullptr}, {nullptr, nullptr}}}
 #define HJ_KC1D(S, T, EX)                                                                             \
     {1, 256, 1, 256, 1,                                                                              \
      {{hj::classic1d_kernel<S, T, EX, false, false>, hj::classic1d_kernel<S, T, EX, false, true>},   \
-      {hj::classic1d_kernel<S, T, EX, true, false>, hj::classic1d_kernel<S, T, EX, true, true>}}}
+      {hj::classic1d_kernel<S, T, EX, true, false>, hj::classic1d_kernel<S, T, EX, true, true>}},     \
+     {{nullptr, nullptr}, {nullptr, nullptr}}}

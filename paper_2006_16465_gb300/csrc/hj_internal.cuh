@@ -74,7 +74,49 @@ struct CycArgs {
     float finvd, fdconst;
     RedArgs red;
     int *err;            // device error word (bounded waits), nullable
+    // overlapping subdomains (Sections 3.4, 4.3): points shared with each
+    // neighbour along x / y, and subdomains along x / y (2D; 1D: along x)
+    int ox, oy, jx, jy;
 };
+
+// Subdomain j of J along one dimension of n interior points, T points each,
+// overlapping its neighbours by o points: it spans [start, end] and owns
+// [lo, hi].  Starts advance by T - o; with o > 0 the last subdomain is moved
+// back to end at n (o = 0: truncated at n).  Each overlap is split at its
+// midpoint, the left subdomain keeping the left half (the right one keeps the
+// middle point of an odd overlap), so every point has exactly one owner: the
+// subdomain in which it lies further from an edge.
+struct Span {
+    int start, end, lo, hi;
+};
+__host__ __device__ __forceinline__ int span_start(int j, int J, int n, int T, int o) {
+    return (o > 0 && J > 1 && j == J - 1) ? n - T + 1 : 1 + j * (T - o);
+}
+__host__ __device__ __forceinline__ Span subdomain_span(int j, int J, int n, int T, int o) {
+    Span s;
+    s.start = span_start(j, J, n, T, o);
+    s.end = s.start + T - 1 < n ? s.start + T - 1 : n;
+    if (j == 0) {
+        s.lo = 1;
+    } else {
+        const int ps = span_start(j - 1, J, n, T, o);
+        const int pe = ps + T - 1 < n ? ps + T - 1 : n;
+        s.lo = s.start + (pe - s.start + 1) / 2;
+    }
+    if (j == J - 1) {
+        s.hi = n;
+    } else {
+        const int ns = span_start(j + 1, J, n, T, o);
+        s.hi = ns + (s.end - ns + 1) / 2 - 1;
+    }
+    return s;
+}
+// Subdomains along a dimension of n points.
+__host__ __device__ __forceinline__ int subdomain_count(int n, int T, int o) {
+    if (n <= T) return 1;
+    if (o == 0) return (n + T - 1) / T;
+    return (n - T + (T - o) - 1) / (T - o) + 1;
+}
 
 // ---------------------------------------------------------------------------
 // storage <-> compute conversions
@@ -281,6 +323,7 @@ struct TileKernelInfo {
     int threads;        // threads per CTA
     int tiles_per_cta;  // 1D packs several tiles per CTA
     CycKernel fn[2][2]; // [sig][res]
+    CycKernel ovl[2][2];// [sig][res] overlapping subdomains (null for classic kernels)
 };
 
 // Kernel registries (one per storage/compute combination).

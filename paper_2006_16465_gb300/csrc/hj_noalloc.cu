@@ -91,6 +91,8 @@ extern "C" int hj_cycles_noalloc(const hj_desc *desc, const hj_params *params, c
         return seterr(HJ_ERR_INVALID_ARG, "precision must be HJ_PREC_F64 (binary64 data) or HJ_PREC_F32 (binary32 data)");
     if (p.method != HJ_METHOD_HIER && p.method != HJ_METHOD_CLASSIC) return seterr(HJ_ERR_INVALID_ARG, "unknown method");
     if (p.k < 1) return seterr(HJ_ERR_INVALID_ARG, "k must be >= 1");
+    if (p.overlap_x > 0 || (d.dim == 2 && p.overlap_y > 0))
+        return seterr(HJ_ERR_UNSUPPORTED, "hj_cycles_noalloc does not take overlapping subdomains");
     if (p.fixed_cycles < 0) return seterr(HJ_ERR_INVALID_ARG, "fixed_cycles (the cycle count) must be >= 0");
     const double off = fabs(d.cW) + fabs(d.cE) + (d.dim == 2 ? fabs(d.cS) + fabs(d.cN) : 0.0);
     const double dc = d.cD + d.sigma_const;

@@ -632,3 +632,100 @@ def test_batched_with_sigma_field_and_batched_adjoint_equal_single_calls():
         dsum += ds
     assert torch.equal(dsum, dsig)
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# overlapping subdomains (Sections 3.4, 4.3)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tile,ovl", [((32, 32), (2, 2)), ((32, 32), (4, 4)), ((32, 16), (6, 3)),
+                                      ((64, 32), (10, 2)), ((32, 8), (4, 0))])
+@pytest.mark.parametrize("shape,sigma,asym", [((97, 130), "field", True), ((70, 45), "const", False)])
+def test_f64_overlap_cycles_match_oracle_2d(tile, ovl, shape, sigma, asym):
+    torch = _torch()
+    nx, ny = shape
+    p = W.random_bc_problem(2, nx, ny, seed=nx + ovl[0], sigma_kind=sigma, asym=asym)
+    for k, ncyc in [(1, 2), (5, 3), (16, 2)]:
+        s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=k, precision="f64", fixed_cycles=ncyc,
+                       overlap_x=ovl[0], overlap_y=ovl[1], persistent=0)
+        u = to_dev(p.u0, 2, torch.float64)
+        s.solve(to_dev(p.f, 2, torch.float64), u)
+        ref = oracle.run_fixed(p.st, p.f, p.u0, ncyc, tile[0], tile[1], k, overlap=ovl)
+        assert np.array_equal(to_host(u, nx), ref), (tile, ovl, k)
+        s.close()
+
+
+@pytest.mark.parametrize("tile,ovl,threads", [(32, 2, 0), (64, 4, 0), (128, 8, 0), (128, 4, 32), (256, 12, 0)])
+def test_f64_overlap_cycles_match_oracle_1d(tile, ovl, threads):
+    torch = _torch()
+    p = W.random_bc_problem(1, 700, 3, seed=ovl, sigma_kind="field", asym=True)
+    for k, ncyc in [(1, 2), (32, 3)]:
+        s = gpu_solver(p, tile_x=tile, k=k, precision="f64", fixed_cycles=ncyc, overlap_x=ovl, tile_threads=threads,
+                       persistent=0)
+        u = to_dev(p.u0, 1, torch.float64)
+        s.solve(to_dev(p.f, 1, torch.float64), u)
+        ref = oracle.run_fixed(p.st, p.f, p.u0, ncyc, tile, 1, k, overlap=(ovl, 0))
+        assert np.array_equal(to_host(u, 700), ref), (tile, ovl, k)
+        s.close()
+
+
+@pytest.mark.parametrize("dim,shape,tile,k,ovl", [(2, (96, 80), (32, 32), 16, (4, 4)),
+                                                  (2, (130, 97), (32, 16), 8, (2, 6)),
+                                                  (1, (1024, 1), (32, 1), 16, (4, 0))])
+def test_f64_overlap_convergence_matches_oracle(dim, shape, tile, k, ovl):
+    """Same stopping cycle, iterate and residual history as the oracle; the
+    1D case is the Section 3.5 problem (one copy) at k = 16, o = 4."""
+    torch = _torch()
+    nx, ny = shape
+    if dim == 1:
+        p = W.paper_replica(1, 1024, copies=1)
+        tol = 1e-4
+    else:
+        p = W.random_bc_problem(2, nx, ny, seed=17, sigma_kind="field")
+        tol = 1e-6
+    s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=k, precision="f64", tol=tol, check_every=32,
+                   overlap_x=ovl[0], overlap_y=ovl[1])
+    u = to_dev(p.u0, dim, torch.float64)
+    out = s.solve(to_dev(p.f, dim, torch.float64), u, history=100000)
+    uo, c, status, hist = oracle.solve(p.st, p.f, p.u0, tol, 10 ** 7, tile[0], tile[1], k, hist_cap=100000,
+                                       overlap=ovl)
+    assert status == 0 and out["status"] == 0 and out["persistent"] == 0
+    assert out["cycles"] == c
+    if dim == 1:
+        assert c == 8093
+    assert np.array_equal(to_host(u, nx), uo)
+    np.testing.assert_allclose(np.array(out["history"]), hist[:c + 1], rtol=1e-9, atol=1e-12 * hist[0])
+    s.close()
+
+
+def test_f32_overlap_cycles_close_to_oracle_and_refinement_converges():
+    torch = _torch()
+    p = W.random_bc_problem(2, 150, 120, seed=23, sigma_kind="field", asym=True)
+    for tile, ovl in [((32, 32), (4, 4)), ((64, 64), (8, 6)), ((32, 16), (2, 2))]:
+        s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], k=8, precision="f32", fixed_cycles=6,
+                       overlap_x=ovl[0], overlap_y=ovl[1])
+        u = to_dev(p.u0, 2, torch.float32)
+        s.solve(to_dev(p.f, 2, torch.float32), u)
+        ref = oracle.run_fixed(p.st, p.f, p.u0, 6, tile[0], tile[1], 8, overlap=ovl)
+        assert rel_max(to_host(u, 150), ref) <= 1e-5, (tile, ovl)
+        s.close()
+    q = W.poisson2d_sin_noise(96, seed=2)
+    s = gpu_solver(q, tile_x=32, tile_y=32, k=16, precision="f32_ir", tol=1e-10, inner_tol=1e-4, overlap_x=4,
+                   overlap_y=4)
+    u = to_dev(q.u0, 2, torch.float64)
+    out = s.solve(to_dev(q.f, 2, torch.float64), u)
+    assert out["status"] == 0
+    assert oracle.residual(q.st, q.f, to_host(u, 96)) <= 1e-10 * oracle.residual(q.st, q.f, q.u0) * 1.0001
+    s.close()
+
+
+def test_overlap_is_rejected_where_unsupported():
+    import paper_2006_16465_gb300 as hj
+    p = W.poisson2d_uniform(64, 64, seed=1)
+    for kw, code in [(dict(overlap_x=32), hj.HJ_ERR_INVALID_ARG), (dict(overlap_x=4, persistent=1), hj.HJ_ERR_UNSUPPORTED),
+                     (dict(overlap_x=4, pipeline=1), hj.HJ_ERR_UNSUPPORTED),
+                     (dict(overlap_x=4, method="classic"), hj.HJ_ERR_INVALID_ARG),
+                     (dict(overlap_x=-2), hj.HJ_ERR_INVALID_ARG)]:
+        with pytest.raises(hj.HJError) as e:
+            gpu_solver(p, tile_x=32, tile_y=32, precision="f64", **kw)
+        assert e.value.code == code, kw
