@@ -137,7 +137,8 @@ typedef struct {
                              0: one launch per cycle inside CUDA graphs;
                              -1: choose automatically                            */
     int autotune;         /* 1: pick tile shape and k by measurement (hj_autotune)
-                             at hj_create; 2: keep tile_x, tile_y and tune k only;
+                             at hj_create; 2: keep tile_x, tile_y and tune k only
+                             (both also pick the overlap, replacing overlap_x/y);
                              3: keep tile and k, tune only the pipelined kernel's
                              launch (threads per subdomain, copy stages, CTAs
                              per SM; 1 and 2 tune it too after their pick);
@@ -169,7 +170,8 @@ typedef struct {
                              in which it lies further from an edge (an overlap
                              is split at its midpoint).  Runs on CUDA graphs of
                              the one-CTA-per-subdomain kernels; persistent = 1,
-                             pipeline = 1, classic and batched solves reject it */
+                             pipeline = 1 and classic reject it; batched
+                             solves run without overlap                      */
     int overlap_y;        /* the same along y (2D; 0 <= overlap_y < tile_y)   */
 } hj_params;
 
@@ -191,6 +193,7 @@ typedef struct {
     int persistent;           /* 1 if the persistent path ran                    */
     int pipeline_stages;      /* copy stages of the pipelined kernel if it runs, else 0 */
     int ctas_per_sm;          /* its CTAs-per-SM cap (0 = as many as fit)         */
+    int overlap_x, overlap_y; /* overlapping points used (Sections 3.4, 4.3)      */
 } hj_stats;
 
 /* Fill p with defaults: hierarchical, 32 x 32 tiles, k = 16, HJ_PREC_F64,
@@ -273,7 +276,9 @@ HJ_API const char *hj_last_error(void);
  * in that file.  *predicted_ms (nullable) receives the predicted time to
  * tolerance, or -1 for a cache hit.  hj_create runs this when
  * params->autotune is 1; params->autotune = 2 keeps tile_x, tile_y and tunes
- * k only.  Where the TMA-pipelined kernel runs the cycles (2D grids of at least
+ * k only.  Modes 1 and 2 also pick the overlap of neighbouring subdomains
+ * (Sections 3.4, 4.3) from {0, 2, 4, 8} points (below half the subdomain
+ * side) and write it into overlap_x (and overlap_y in 2D).  Where the TMA-pipelined kernel runs the cycles (2D grids of at least
  * 8 subdomains per SM, or pipeline = 1), every mode then measures its launch
  * shapes for the chosen subdomain and k (threads per subdomain, copy stages,
  * CTAs per SM) and writes the fastest into tile_threads, pipeline_stages and

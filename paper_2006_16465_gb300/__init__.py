@@ -60,7 +60,8 @@ class hj_stats(C.Structure):
                 ("history", C.POINTER(C.c_double)), ("history_cap", C.c_longlong),
                 ("history_len", C.c_longlong), ("wall_ms", C.c_double), ("tile_x", C.c_int),
                 ("tile_y", C.c_int), ("k", C.c_int), ("tile_threads", C.c_int), ("persistent", C.c_int),
-                ("pipeline_stages", C.c_int), ("ctas_per_sm", C.c_int)]
+                ("pipeline_stages", C.c_int), ("ctas_per_sm", C.c_int), ("overlap_x", C.c_int),
+                ("overlap_y", C.c_int)]
 
 
 class HJError(RuntimeError):

@@ -767,6 +767,8 @@ void fill_stats_config(const hj_handle *h, hj_stats *st, double t0) {
     const bool ppc = want_ppc(h, pk, h->p.method == HJ_METHOD_CLASSIC);
     st->pipeline_stages = ppc ? pk->stages : 0;
     st->ctas_per_sm = ppc ? h->p.ctas_per_sm : 0;
+    st->overlap_x = h->p.overlap_x;
+    st->overlap_y = h->d.dim == 2 ? h->p.overlap_y : 0;
 }
 
 }  // namespace
@@ -902,7 +904,6 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
         if (p.method == HJ_METHOD_CLASSIC) return seterr(HJ_ERR_INVALID_ARG, "overlap applies to hierarchical cycles");
         if (p.persistent == 1 || p.pipeline == 1)
             return seterr(HJ_ERR_UNSUPPORTED, "overlapping subdomains run on graphs (persistent and pipeline must not be 1)");
-        if (p.autotune == 1) return seterr(HJ_ERR_UNSUPPORTED, "autotune = 1 picks the subdomain shape: use overlap with a fixed shape");
     }
     if (ir && p.method == HJ_METHOD_CLASSIC) return seterr(HJ_ERR_UNSUPPORTED, "refinement uses hierarchical cycles");
     if (p.check_every < 1) p.check_every = 1;
@@ -920,6 +921,8 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
         p.k = tp.k;
         p.pipeline_stages = tp.pipeline_stages;
         p.ctas_per_sm = tp.ctas_per_sm;
+        p.overlap_x = tp.overlap_x;
+        p.overlap_y = tp.overlap_y;
     }
     if (p.overlap_x >= p.tile_x || (d.dim == 2 && p.overlap_y >= p.tile_y))
         return seterr(HJ_ERR_INVALID_ARG, "overlap (%d, %d) must be smaller than the subdomain (%d, %d)", p.overlap_x,

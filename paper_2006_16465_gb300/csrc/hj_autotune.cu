@@ -18,7 +18,7 @@
 // (tune_launch: threads per subdomain, copy stages, CTAs per SM by measured
 // time per cycle); autotune = 3 tunes only that.  Results are cached per
 // process and, if HJ_AUTOTUNE_CACHE names a file, in that file (one line per
-// key: "key tile_x tile_y threads k").
+// key: "key tile_x tile_y threads k overlap").
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -60,11 +60,12 @@ bool g_loaded = false;
 
 std::string make_key(const hj_desc &d, int precision, double tol) {
     char buf[512];
-    snprintf(buf, sizeof(buf), "d%d_n%dx%d_p%d_c%.9g,%.9g,%.9g,%.9g,%.9g_s%.9g_sig%d_tol%.3g", d.dim, d.nx, d.ny,
+    snprintf(buf, sizeof(buf), "v2_d%d_n%dx%d_p%d_c%.9g,%.9g,%.9g,%.9g,%.9g_s%.9g_sig%d_tol%.3g", d.dim, d.nx, d.ny,
              precision, d.cW, d.cE, d.cS, d.cN, d.cD, d.sigma_const, d.sigma ? 1 : 0, tol);
     return buf;
 }
 
+// One line per key: "key v0 v1 v2 v3 v4"; lines that do not parse are skipped.
 void load_cache_file() {
     if (g_loaded) return;
     g_loaded = true;
@@ -72,18 +73,20 @@ void load_cache_file() {
     if (!path || !*path) return;
     FILE *fp = fopen(path, "r");
     if (!fp) return;
-    char key[512];
-    int tx, ty, th, k;
-    while (fscanf(fp, "%511s %d %d %d %d", key, &tx, &ty, &th, &k) == 5) g_cache[key] = {tx, ty, th, k};
+    char line[768], key[512];
+    int v[5];
+    while (fgets(line, sizeof(line), fp))
+        if (sscanf(line, "%511s %d %d %d %d %d", key, &v[0], &v[1], &v[2], &v[3], &v[4]) == 6)
+            g_cache[key] = {v[0], v[1], v[2], v[3], v[4]};
     fclose(fp);
 }
 
-void store_cache_file(const std::string &key, int tx, int ty, int th, int k) {
+void store_cache_file(const std::string &key, const std::vector<int> &v) {
     const char *path = getenv("HJ_AUTOTUNE_CACHE");
     if (!path || !*path) return;
     FILE *fp = fopen(path, "a");
     if (!fp) return;
-    fprintf(fp, "%s %d %d %d %d\n", key.c_str(), tx, ty, th, k);
+    fprintf(fp, "%s %d %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3], v[4]);
     fclose(fp);
 }
 
@@ -132,7 +135,8 @@ constexpr int kWin = 32;    // contraction measured over the last kWin cycles
 // *rho: contraction per cycle over the second half; *ms: time of the kCyc
 // cycles without the closing residual pass.  fixed: time fixed cycles instead
 // (no residual, no rho).
-bool measure(Scratch &sc, int prec, int tx, int ty, int th, int k, const hj_params &base, double *rho, double *ms) {
+bool measure(Scratch &sc, int prec, int tx, int ty, int th, int k, const hj_params &base, double *rho, double *ms,
+             int ovl = 0) {
     hj_params tp;
     hj_default_params(&tp);
     tp.tile_x = tx;
@@ -146,6 +150,13 @@ bool measure(Scratch &sc, int prec, int tx, int ty, int th, int k, const hj_para
     tp.check_every = kCyc;
     tp.persistent = base.persistent;
     tp.pipeline = base.pipeline;
+    // overlapping subdomains run on graphs of the one-CTA-per-subdomain kernels
+    tp.overlap_x = ovl;
+    tp.overlap_y = sc.td.dim == 2 ? ovl : 0;
+    if (ovl > 0) {
+        if (tp.persistent == 1) tp.persistent = -1;
+        if (tp.pipeline == 1) tp.pipeline = -1;
+    }
     hj_handle *h = nullptr;
     if (hj_create(&h, &sc.td, &tp) != HJ_OK) return false;
     cudaEvent_t e0, e1;
@@ -316,8 +327,8 @@ int tune_launch(const hj_desc &d, hj_params *p) {
     p->ctas_per_sm = bcps;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        g_cache[key] = {bth, bst, bcps, 0};
-        store_cache_file(key, bth, bst, bcps, 0);
+        g_cache[key] = {bth, bst, bcps, 0, 0};
+        store_cache_file(key, g_cache[key]);
     }
     return HJ_OK;
 }
@@ -350,6 +361,8 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
             params->tile_y = it->second[1];
             params->tile_threads = it->second[2];
             params->k = it->second[3];
+            params->overlap_x = it->second[4];
+            params->overlap_y = d.dim == 2 ? it->second[4] : 0;
             if (predicted_ms) *predicted_ms = -1.0;
             return tune_launch(d, params);
         }
@@ -359,8 +372,9 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
     int xy[3 * 64];
     const int nshape = std::min(64, hj_tile_variants(d.dim, prec, xy, 64));
     const int ks[] = {4, 8, 16, 32, 64};
+    const int os[] = {0, 2, 4, 8};   // overlapping points per side (Sections 3.4, 4.3)
     double best = INFINITY;
-    int btx = params->tile_x, bty = params->tile_y, bth = params->tile_threads, bk = params->k;
+    int btx = params->tile_x, bty = params->tile_y, bth = params->tile_threads, bk = params->k, bo = 0;
     for (int si = 0; si < nshape; ++si) {
         const int tx = xy[3 * si], ty = xy[3 * si + 1], th = xy[3 * si + 2];
         // autotune == 2: the tile variant is fixed by the caller, tune k only
@@ -369,17 +383,22 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
             continue;
         // skip shapes far larger than the grid
         if (tx > 2 * std::max(d.nx, 32) || (d.dim == 2 && ty > 2 * std::max(d.ny, 8))) continue;
+        const int tmin = d.dim == 2 ? std::min(tx, ty) : tx;
         for (int k : ks) {
-            double rho = 1.0, ms = INFINITY;
-            if (!measure(sc, prec, tx, ty, th, k, *params, &rho, &ms)) continue;
-            if (!(rho > 0.0 && rho < 1.0)) continue;
-            const double pred = log(std::max(tol, 1e-300)) / log(rho) * (ms / kCyc);
-            if (pred < best) {
-                best = pred;
-                btx = tx;
-                bty = ty;
-                bth = th;
-                bk = k;
+            for (int o : os) {
+                if (2 * o >= tmin) continue;
+                double rho = 1.0, ms = INFINITY;
+                if (!measure(sc, prec, tx, ty, th, k, *params, &rho, &ms, o)) continue;
+                if (!(rho > 0.0 && rho < 1.0)) continue;
+                const double pred = log(std::max(tol, 1e-300)) / log(rho) * (ms / kCyc);
+                if (pred < best) {
+                    best = pred;
+                    btx = tx;
+                    bty = ty;
+                    bth = th;
+                    bk = k;
+                    bo = o;
+                }
             }
         }
     }
@@ -388,11 +407,13 @@ extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predi
     params->tile_y = d.dim == 2 ? bty : 1;
     params->tile_threads = bth;
     params->k = bk;
+    params->overlap_x = bo;
+    params->overlap_y = d.dim == 2 ? bo : 0;
     if (predicted_ms) *predicted_ms = best;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        g_cache[key] = {btx, bty, bth, bk};
-        store_cache_file(key, btx, bty, bth, bk);
+        g_cache[key] = {btx, bty, bth, bk, bo};
+        store_cache_file(key, g_cache[key]);
     }
     return tune_launch(d, params);
 }

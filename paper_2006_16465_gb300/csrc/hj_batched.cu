@@ -289,8 +289,6 @@ int validate_desc(const hj_desc &d, int i) {
 int batched_core(hj_handle *h, int nprob, const hj_desc *descs, const void *const *f, void *const *u,
                  hj_stream stream, hj_stats *stats, long long *cycles_out, bool transpose) {
     if (!h) return seterr(HJ_ERR_INVALID_ARG, "handle is NULL");
-    if (h->p.overlap_x > 0 || h->p.overlap_y > 0)
-        return seterr(HJ_ERR_UNSUPPORTED, "batched solves do not take overlapping subdomains");
     if (nprob < 1 || !descs || !f || !u) return seterr(HJ_ERR_INVALID_ARG, "nprob, descs, f, u");
     if (!h->ir) return seterr(HJ_ERR_UNSUPPORTED, "batched solves use HJ_PREC_F32_IR or HJ_PREC_BF16CORR_IR");
     cudaStream_t s = (cudaStream_t)stream;

@@ -30,9 +30,10 @@ def test_autotune_picks_a_built_configuration_and_caches_it():
     assert ms > 0
     assert (p.tile_x, p.tile_y) in hj.hj_tile_shapes(2, hj.HJ_PREC_F32)
     assert p.k in (4, 8, 16, 32, 64)
+    assert p.overlap_x in (0, 2, 4, 8) and p.overlap_y == p.overlap_x and 2 * p.overlap_x < min(p.tile_x, p.tile_y)
     q = hj.make_params(precision="f32", tol=1e-5)
     assert hj.hj_autotune(d, q) == -1.0          # cache hit
-    assert (q.tile_x, q.tile_y, q.k) == (p.tile_x, p.tile_y, p.k)
+    assert (q.tile_x, q.tile_y, q.k, q.overlap_x) == (p.tile_x, p.tile_y, p.k, p.overlap_x)
 
 
 def test_autotuned_handle_solves_to_tolerance():
