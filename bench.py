@@ -342,6 +342,8 @@ def paper_replicas(torch, hj, W, precision="f64"):
         runs += [(f"hier_k{k}_o{best_o[k]}", dict(tile_x=tile[0], tile_y=tile[1], k=k, overlap_x=best_o[k],
                                                   overlap_y=best_o[k] if dim == 2 else 0, persistent=0))
                  for k in (4, 8, 16, 32, 64, 128) if best_o[k] > 0]
+        # one global array (Appendix A taken literally): convergence and speed
+        runs += [(f"hier_k{k}_in_place", dict(tile_x=tile[0], tile_y=tile[1], k=k, in_place=1)) for k in (4, 16, 64)]
         for name, kw in runs:
             s = hj.Solver(p.st, precision=precision, tol=1e-4, **kw)
             u = hj.grid_from(p.u0, dim, dt)

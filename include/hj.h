@@ -173,6 +173,16 @@ typedef struct {
                              pipeline = 1 and classic reject it; batched
                              solves run without overlap                      */
     int overlap_y;        /* the same along y (2D; 0 <= overlap_y < tile_y)   */
+    int in_place;         /* 1: one global iterate array, as the listing of
+                             Appendix A has it: a subdomain may stage halo
+                             values that a neighbour already overwrote in the
+                             same cycle, so results depend on scheduling and
+                             are not reproducible bit for bit.  The stopping
+                             test uses the fused residual of the staged data;
+                             res0 and res_final are exact residuals of the
+                             initial and the returned array (which may be one
+                             cycle past the checked one).  0 (default): u_c
+                             and u_{c+1} in separate arrays, deterministic   */
 } hj_params;
 
 typedef struct {
@@ -200,7 +210,7 @@ typedef struct {
  * check_every = 64, max_cycles = 10^7, tol = 1e-6, fixed_cycles = 0,
  * inner_tol = 1e-4, inner_max_cycles = 10^6, max_outer = 60, persistent = -1,
  * autotune = 0, pipeline = -1, tile_threads = 0, pipeline_stages = 0,
- * inner_stall = 32, ctas_per_sm = 0, overlap_x = overlap_y = 0. */
+ * inner_stall = 32, ctas_per_sm = 0, overlap_x = overlap_y = 0, in_place = 0. */
 HJ_API void hj_default_params(hj_params *p);
 
 /* Create a solver for one problem shape.  Validates the descriptor and

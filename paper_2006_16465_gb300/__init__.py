@@ -50,7 +50,7 @@ class hj_params(C.Structure):
                 ("inner_max_cycles", C.c_longlong), ("max_outer", C.c_int), ("persistent", C.c_int),
                 ("autotune", C.c_int), ("pipeline", C.c_int), ("tile_threads", C.c_int),
                 ("pipeline_stages", C.c_int), ("inner_stall", C.c_int), ("ctas_per_sm", C.c_int),
-                ("overlap_x", C.c_int), ("overlap_y", C.c_int)]
+                ("overlap_x", C.c_int), ("overlap_y", C.c_int), ("in_place", C.c_int)]
 
 
 class hj_stats(C.Structure):

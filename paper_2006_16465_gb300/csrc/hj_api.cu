@@ -397,6 +397,7 @@ struct RunOut {
 struct ThirdBuffer {
     void **slot;
     size_t bytes;
+    void *alias;   // in-place runs: every iterate buffer is this array
 };
 
 // Iterate cycles (or classic sweeps) from b0 (holds u_0) and b1 (the other
@@ -453,7 +454,9 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, 
     // the pipelined kernel folds each launch's residual in the next launch:
     // a third buffer keeps u_c intact until that fold has decided
     void *b2 = nullptr;
-    if (want_ppc(h, pi, classic)) {
+    if (third.alias) {
+        b2 = third.alias;
+    } else if (want_ppc(h, pi, classic)) {
         if (!third.slot) return seterr(HJ_ERR_CUDA, "internal: no slot for the third iterate buffer");
         if (!*third.slot) {
             if (cudaMalloc(third.slot, third.bytes) != cudaSuccess) {
@@ -630,25 +633,36 @@ int solve_plain(hj_handle *h, const void *f, void *u, bool transpose, cudaStream
     CycArgs base = base_args(h, transpose);
     base.f = f;
     base.dinv = h->dinv_outer;
-    CKR(cudaMemcpyAsync(h->ubuf, u, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+    const bool inplace = h->p.in_place != 0;
+    if (!inplace) CKR(cudaMemcpyAsync(h->ubuf, u, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+    // in place, even the first cycle's staged data may mix u_0 and u_1: take
+    // ||r_0|| exactly for the final status
+    double r0_exact = -1.0;
+    if (inplace && h->p.fixed_cycles <= 0) {
+        double rr;
+        CKS(residual_of(h, f, u, transpose, &rr, nullptr, s));
+        r0_exact = sqrt(rr);
+    }
     RunOut ro;
     long long hl = 0;
     int persist = 0;
-    CKS(iterate(h, ki, classic ? nullptr : h->p_outer, h->fam_outer, classic, sig, base, u, h->ubuf,
-                ThirdBuffer{&h->ubuf2, h->grid_bytes}, h->p.tol, h->p.max_cycles, h->p.fixed_cycles, s, &ro,
-                st ? st->history : nullptr, st ? st->history_cap : 0, &hl, &persist));
+    CKS(iterate(h, ki, classic ? nullptr : h->p_outer, h->fam_outer, classic, sig, base, u, inplace ? u : h->ubuf,
+                ThirdBuffer{&h->ubuf2, h->grid_bytes, inplace ? u : nullptr}, h->p.tol, h->p.max_cycles,
+                h->p.fixed_cycles, s, &ro, st ? st->history : nullptr, st ? st->history_cap : 0, &hl, &persist));
     if (ro.buf != u) CKR(cudaMemcpyAsync(u, ro.buf, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
     double res0 = -1.0, resc = -1.0;
     if (h->p.fixed_cycles <= 0) {
-        res0 = sqrt(std::max(ro.res2_0, 0.0));
-        if (ro.res2_c >= 0.0) {
+        res0 = inplace ? r0_exact : sqrt(std::max(ro.res2_0, 0.0));
+        if (ro.res2_c >= 0.0 && !inplace) {
             resc = sqrt(ro.res2_c);
         } else {
+            // in place, the fused residuals belong to staged data, not to one
+            // iterate: the exact residual of the returned array decides
             double rr;
             CKS(residual_of(h, f, u, transpose, &rr, nullptr, s));
             resc = sqrt(rr);
             if (ro.launched == 0) res0 = resc;
-            if (resc <= h->p.tol * res0) ro.status = HJ_OK;
+            if (resc <= h->p.tol * res0 && ro.status != HJ_ERR_DIVERGED) ro.status = HJ_OK;
         }
     }
     CKR(cudaStreamSynchronize(s));
@@ -703,9 +717,10 @@ int solve_ir(hj_handle *h, const double *f, double *u, bool transpose, cudaStrea
         if (o >= h->p.max_outer) { status = HJ_ERR_NOT_CONVERGED; break; }
         CKR(cudaMemsetAsync(h->dA, 0, (size_t)h->rows * h->ld_in * dsz, s));
         RunOut ro;
-        CKS(iterate(h, h->k_inner, h->p_inner, h->fam_inner, false, sig, base, h->dA, h->dB,
-                    ThirdBuffer{&h->dC, (size_t)h->rows * h->ld_in * dsz}, h->p.inner_tol, h->p.inner_max_cycles, 0,
-                    s, &ro, nullptr, 0, nullptr, &persist));
+        const bool inplace = h->p.in_place != 0;
+        CKS(iterate(h, h->k_inner, h->p_inner, h->fam_inner, false, sig, base, h->dA, inplace ? h->dA : h->dB,
+                    ThirdBuffer{&h->dC, (size_t)h->rows * h->ld_in * dsz, inplace ? h->dA : nullptr},
+                    h->p.inner_tol, h->p.inner_max_cycles, 0, s, &ro, nullptr, 0, nullptr, &persist));
         inner_total += ro.c;
         inner_launched += ro.launched;
         const void *dsel = ro.buf;
@@ -898,6 +913,7 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     if (ir && p.inner_max_cycles < 1) return seterr(HJ_ERR_INVALID_ARG, "inner_max_cycles must be >= 1");
     if (p.inner_stall < 0) return seterr(HJ_ERR_INVALID_ARG, "inner_stall must be >= 0");
     if (p.ctas_per_sm < 0) return seterr(HJ_ERR_INVALID_ARG, "ctas_per_sm must be >= 0");
+    if (p.in_place != 0 && p.in_place != 1) return seterr(HJ_ERR_INVALID_ARG, "in_place must be 0 or 1");
     if (d.dim == 1) p.overlap_y = 0;
     if (p.overlap_x < 0 || p.overlap_y < 0) return seterr(HJ_ERR_INVALID_ARG, "overlaps must be >= 0");
     if (p.overlap_x > 0 || p.overlap_y > 0) {
