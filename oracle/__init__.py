@@ -43,7 +43,7 @@ class _Problem(C.Structure):
     _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
                 ("cW", C.c_double), ("cE", C.c_double), ("cS", C.c_double),
                 ("cN", C.c_double), ("cD", C.c_double), ("sigma_const", C.c_double),
-                ("sigma", C.c_void_p)]
+                ("sigma", C.c_void_p), ("coef", C.c_void_p)]
 
 
 _lib = None
@@ -107,9 +107,12 @@ class Problem:
     def __init__(self, st):
         self.st = st
         self.sigma = None if st.sigma is None else _grid(st.sigma)
+        coef = getattr(st, "coef", None)
+        self.coef = None if coef is None else _grid(coef)   # planes W, E[, S, N] x rows x (nx + 2)
         self.c = _Problem(st.dim, st.nx, st.ny, st.cW, st.cE, st.cS, st.cN, st.cD,
                           float(st.sigma_const),
-                          None if self.sigma is None else self.sigma.ctypes.data)
+                          None if self.sigma is None else self.sigma.ctypes.data,
+                          None if self.coef is None else self.coef.ctypes.data)
         self.shape = (st.rows, st.nx + 2)
 
     @property

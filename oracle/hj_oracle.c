@@ -44,6 +44,9 @@ typedef struct {
     double cW, cE, cS, cN, cD;
     double sigma_const; /* constant screening added to every diagonal entry */
     const double *sigma;/* nullable, grid-shaped, per-point screening */
+    const double *coef; /* nullable: per-point neighbour coefficients, grid-shaped
+                           planes W, E (1D) or W, E, S, N (2D) that replace cW..cN;
+                           the general tridiagonal a_i, c_i of Section 3 */
 } hjo_problem;
 
 static long rows_of(const hjo_problem *p) { return p->dim == 2 ? (long)p->ny + 2 : (long)p->ny; }
@@ -59,15 +62,23 @@ static double diag_at(const hjo_problem *p, long q)
     return d;
 }
 
-/* One Jacobi point update from the four (two in 1D) neighbour values. */
-static double jacobi_point(const hjo_problem *p, double f, double d,
+/* neighbour coefficient m (0 = W, 1 = E, 2 = S, 3 = N) of grid index q */
+static double coef_at(const hjo_problem *p, int m, long q)
+{
+    if (p->coef) return p->coef[(long)m * rows_of(p) * width_of(p) + q];
+    return m == 0 ? p->cW : m == 1 ? p->cE : m == 2 ? p->cS : p->cN;
+}
+
+/* One Jacobi point update of grid index q from the four (two in 1D)
+ * neighbour values. */
+static double jacobi_point(const hjo_problem *p, long q, double f, double d,
                            double uW, double uE, double uS, double uN)
 {
-    double acc = p->cW * uW;
-    acc = acc + p->cE * uE;
+    double acc = coef_at(p, 0, q) * uW;
+    acc = acc + coef_at(p, 1, q) * uE;
     if (p->dim == 2) {
-        acc = acc + p->cS * uS;
-        acc = acc + p->cN * uN;
+        acc = acc + coef_at(p, 2, q) * uS;
+        acc = acc + coef_at(p, 3, q) * uN;
     }
     return (f - acc) * (1.0 / d);
 }
@@ -77,11 +88,11 @@ static double apply_point(const hjo_problem *p, const double *u, long q)
 {
     const long W = width_of(p);
     double au = diag_at(p, q) * u[q];
-    au = au + p->cW * u[q - 1];
-    au = au + p->cE * u[q + 1];
+    au = au + coef_at(p, 0, q) * u[q - 1];
+    au = au + coef_at(p, 1, q) * u[q + 1];
     if (p->dim == 2) {
-        au = au + p->cS * u[q - W];
-        au = au + p->cN * u[q + W];
+        au = au + coef_at(p, 2, q) * u[q - W];
+        au = au + coef_at(p, 3, q) * u[q + W];
     }
     return au;
 }
@@ -138,7 +149,7 @@ void hjo_jacobi_sweep(const hjo_problem *p, const double *f, const double *uin, 
             const long q = j * W + i;
             const double uS = p->dim == 2 ? uin[q - W] : 0.0;
             const double uN = p->dim == 2 ? uin[q + W] : 0.0;
-            uout[q] = jacobi_point(p, f[q], diag_at(p, q), uin[q - 1], uin[q + 1], uS, uN);
+            uout[q] = jacobi_point(p, q, f[q], diag_at(p, q), uin[q - 1], uin[q + 1], uS, uN);
         }
 }
 
@@ -186,7 +197,7 @@ void hjo_hier_cycle(const hjo_problem *p, const double *f, const double *uin, do
                         const long l = (j - hj0) * lw + (i - (i0 - 1));
                         const double uS = p->dim == 2 ? src[l - lw] : 0.0;
                         const double uN = p->dim == 2 ? src[l + lw] : 0.0;
-                        dst[l] = jacobi_point(p, f[j * W + i], diag_at(p, j * W + i),
+                        dst[l] = jacobi_point(p, j * W + i, f[j * W + i], diag_at(p, j * W + i),
                                               src[l - 1], src[l + 1], uS, uN);
                     }
             }
@@ -284,7 +295,7 @@ void hjo_hier_cycle_ovl(const hjo_problem *p, const double *f, const double *uin
                         const long l = (j - hj0) * lw + (i - (i0 - 1));
                         const double uS = p->dim == 2 ? src[l - lw] : 0.0;
                         const double uN = p->dim == 2 ? src[l + lw] : 0.0;
-                        dst[l] = jacobi_point(p, f[j * W + i], diag_at(p, j * W + i),
+                        dst[l] = jacobi_point(p, j * W + i, f[j * W + i], diag_at(p, j * W + i),
                                               src[l - 1], src[l + 1], uS, uN);
                     }
             }
@@ -540,6 +551,10 @@ long hjo_ir_solve(const hjo_problem *p, const double *f, double *u,
                   long max_outer, int bf16, long stall_window, double stall_rtol,
                   double *hist, long hist_cap, long *inner_total, int *status)
 {
+    if (p->coef) {   /* refinement is defined here for constant neighbour coefficients */
+        if (status) *status = 3;
+        return -1;
+    }
     const long W = width_of(p), R = rows_of(p);
     const size_t n = (size_t)(W * R);
     float *rhs = (float *)calloc(n, sizeof(float));
@@ -611,6 +626,10 @@ long hjo_adjoint(const hjo_problem *p, const double *g, const double *u,
                  double *lam, double *dl_dsigma, int tx, int ty, int k,
                  double tol, long max_cycles, int *status)
 {
+    if (p->coef) {   /* the transposed stencil is built for constant neighbour coefficients */
+        if (status) *status = 3;
+        return -1;
+    }
     const long W = width_of(p), R = rows_of(p);
     hjo_problem pt = *p;
     pt.cW = p->cE; pt.cE = p->cW;

@@ -51,9 +51,12 @@ def dense_system(st, f, u):
             sig = st.sigma_const + (st.sigma[j, i] if st.sigma is not None else 0.0)
             A[m, m] = st.cD + sig
             b[m] = f[j, i]
-            nbrs = [(j, i - 1, st.cW), (j, i + 1, st.cE)]
+            cf = getattr(st, "coef", None)
+            cw, ce = (st.cW, st.cE) if cf is None else (cf[0][j, i], cf[1][j, i])
+            nbrs = [(j, i - 1, cw), (j, i + 1, ce)]
             if st.dim == 2:
-                nbrs += [(j - 1, i, st.cS), (j + 1, i, st.cN)]
+                cs, cn = (st.cS, st.cN) if cf is None else (cf[2][j, i], cf[3][j, i])
+                nbrs += [(j - 1, i, cs), (j + 1, i, cn)]
             for (jj, ii, c) in nbrs:
                 ghost = ii == 0 or ii == nx + 1 or (st.dim == 2 and (jj == 0 or jj == st.ny + 1))
                 if ghost:
@@ -533,3 +536,68 @@ def test_overlap_cycle_count_of_the_paper_1d_problem():
     assert s4 == 0 and s0 == 0
     assert c4 == 8093
     assert c0 == 19555
+
+
+# ---------------------------------------------------------------------------
+# Variable neighbour coefficients (the general tridiagonal matrix of Section 3
+# and its 2D pentadiagonal analogue)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,nx,ny", [(1, 13, 3), (2, 9, 7)])
+def test_variable_coefficients_apply_matches_dense(dim, nx, ny):
+    p = W.variable_coef_problem(dim, nx, ny, seed=nx, contrast=20.0, screening=3.0)
+    A, b = dense_system(p.st, p.f, p.u0)
+    x = W.interior(p.u0, dim).ravel()
+    r_dense = b - A @ x
+    r = W.interior(p.f - oracle.apply(p.st, p.u0), dim).ravel()
+    # apply() sees the ghost ring through u0: move those terms like dense_system does
+    np.testing.assert_allclose(r, r_dense, rtol=1e-12, atol=1e-9 * np.abs(b).max())
+    assert oracle.residual(p.st, p.f, p.u0) == pytest.approx(np.linalg.norm(r_dense), rel=1e-12)
+
+
+@pytest.mark.parametrize("dim,nx,ny,tx,ty", [(1, 45, 2, 8, 1), (2, 23, 17, 8, 6)])
+def test_variable_coefficients_k1_cycle_is_classic_sweep(dim, nx, ny, tx, ty):
+    p = W.variable_coef_problem(dim, nx, ny, seed=5)
+    for ovl in ((0, 0), (2, 2 if dim == 2 else 0)):
+        a = oracle.hier_cycle_ovl(p.st, p.f, p.u0, tx, ty, 1, *ovl)
+        assert np.array_equal(a, oracle.jacobi_sweep(p.st, p.f, p.u0))
+
+
+def test_variable_coefficients_1d_converges_to_thomas():
+    """The general tridiagonal system of Section 3 (a_i, d_i, c_i per row)
+    solved by hierarchical cycles agrees with the Thomas algorithm."""
+    n = 96
+    p = W.variable_coef_problem(1, n, 1, seed=9, contrast=50.0)
+    st = p.st
+    a = st.coef[0][0, 1:n + 1].copy()
+    c = st.coef[1][0, 1:n + 1].copy()
+    d = st.sigma[0, 1:n + 1].copy()
+    b = p.f[0, 1:n + 1].copy()
+    b[0] -= a[0] * p.u0[0, 0]
+    b[-1] -= c[-1] * p.u0[0, n + 1]
+    x = oracle.thomas(a, d, c, b)
+    u, cyc, status, _ = oracle.solve(st, p.f, p.u0, 1e-13, 10 ** 7, 16, 1, 12)
+    assert status == 0
+    kappa = 4 * 50.0 * (n + 1) ** 2 / (np.pi ** 2)
+    assert np.abs(u[0, 1:n + 1] - x).max() <= kappa * 1e-13 * np.abs(x).max()
+
+
+def test_variable_coefficients_large_k_and_fixed_point_2d():
+    p = W.variable_coef_problem(2, 11, 9, seed=4, contrast=30.0, screening=5.0)
+    st, f, u0 = p.st, p.f, p.u0
+    tx, ty = 4, 3
+    out = oracle.hier_cycle(st, f, u0, tx, ty, 4000)
+    ref = u0.copy()
+    for j0 in range(1, st.ny + 1, ty):
+        for i0 in range(1, st.nx + 1, tx):
+            j1, i1 = min(j0 + ty - 1, st.ny), min(i0 + tx - 1, st.nx)
+            loc = W.Stencil(2, i1 - i0 + 1, j1 - j0 + 1, st.cW, st.cE, st.cS, st.cN, st.cD,
+                            sigma=st.sigma[j0 - 1:j1 + 2, i0 - 1:i1 + 2],
+                            coef=st.coef[:, j0 - 1:j1 + 2, i0 - 1:i1 + 2])
+            A, b = dense_system(loc, f[j0 - 1:j1 + 2, i0 - 1:i1 + 2], u0[j0 - 1:j1 + 2, i0 - 1:i1 + 2])
+            ref[j0:j1 + 1, i0:i1 + 1] = np.linalg.solve(A, b).reshape(j1 - j0 + 1, i1 - i0 + 1)
+    np.testing.assert_allclose(out, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+    A, b = dense_system(st, f, u0)
+    ex = u0.copy()
+    ex[1:-1, 1:-1] = np.linalg.solve(A, b).reshape(st.ny, st.nx)
+    np.testing.assert_allclose(oracle.hier_cycle(st, f, ex, 5, 4, 6), ex, rtol=1e-12, atol=1e-13)

@@ -90,6 +90,10 @@ class Stencil:
     cD: float = 0.0
     sigma: np.ndarray | None = None   # grid-shaped array (ghost entries ignored) or None
     sigma_const: float = 0.0          # constant screening added to the diagonal
+    # per-point neighbour coefficients (planes W, E in 1D; W, E, S, N in 2D,
+    # each grid-shaped) replacing cW..cN: the general tridiagonal a_i, c_i of
+    # Section 3 and its 2D analogue; None = constant coefficients
+    coef: np.ndarray | None = None
 
     @property
     def rows(self) -> int:
@@ -197,6 +201,44 @@ def random_bc_problem(dim: int, nx: int, ny: int, seed: int, sigma_kind: str = "
     interior(f, dim)[...] = uniform(seed, interior(f, dim).size, -1.0, 1.0).reshape(interior(f, dim).shape)
     u0 = uniform(seed + 7, rows * (nx + 2), -0.5, 0.5).reshape(rows, nx + 2)
     return Problem(st, f, u0, {"seed": seed})
+
+
+def variable_coef_problem(dim: int, nx: int, ny: int, seed: int, contrast: float = 10.0,
+                          screening: float = 0.0) -> Problem:
+    """Heterogeneous diffusion -div(kappa grad u) + s u = f on the unit square
+    (or interval) with the 5-point (3-point) flux form: kappa is a smooth
+    positive field with max/min about `contrast`, face values are arithmetic
+    means of the two cell values, cW = -kappa_{i-1/2}/h^2 etc., and the
+    diagonal (sum of the neighbour magnitudes, plus s) goes in sigma with
+    cD = 0.  Random RHS, random Dirichlet ring and initial guess."""
+    rows = ny + 2 if dim == 2 else ny
+    hx = 1.0 / (nx + 1)
+    hy = 1.0 / (ny + 1) if dim == 2 else 1.0
+    x = np.arange(nx + 2) * hx
+    y = (np.arange(rows) * hy) if dim == 2 else np.zeros(rows)
+    ph = uniform(seed + 31, 4, 0.0, 2 * np.pi)
+    g = np.sin(2 * np.pi * x[None, :] + ph[0]) * np.cos(2 * np.pi * y[:, None] + ph[1]) + \
+        0.5 * np.sin(6 * np.pi * x[None, :] + ph[2])
+    kappa = np.exp(np.log(contrast) * 0.5 * (g / 1.5 + 1.0))   # in [1, contrast]
+    planes = 4 if dim == 2 else 2
+    coef = np.zeros((planes, rows, nx + 2))
+    kW = 0.5 * (kappa[:, 1:-1] + kappa[:, :-2])
+    kE = 0.5 * (kappa[:, 1:-1] + kappa[:, 2:])
+    coef[0][:, 1:-1] = -kW / hx ** 2
+    coef[1][:, 1:-1] = -kE / hx ** 2
+    if dim == 2:
+        kS = 0.5 * (kappa[1:-1, :] + kappa[:-2, :])
+        kN = 0.5 * (kappa[1:-1, :] + kappa[2:, :])
+        coef[2][1:-1, :] = -kS / hy ** 2
+        coef[3][1:-1, :] = -kN / hy ** 2
+    sigma = np.abs(coef).sum(axis=0) + screening
+    st = Stencil(dim, nx, ny, cW=-1.0 / hx ** 2, cE=-1.0 / hx ** 2,
+                 cS=(-1.0 / hy ** 2) if dim == 2 else 0.0, cN=(-1.0 / hy ** 2) if dim == 2 else 0.0,
+                 cD=0.0, sigma=sigma, coef=coef)
+    f = zeros_grid(st)
+    interior(f, dim)[...] = uniform(seed, interior(f, dim).size, -1.0, 1.0).reshape(interior(f, dim).shape)
+    u0 = uniform(seed + 7, rows * (nx + 2), -0.5, 0.5).reshape(rows, nx + 2)
+    return Problem(st, f, u0, {"seed": seed, "contrast": contrast})
 
 
 BATCH_SIDES = tuple(range(64, 513, 32))   # {64, 96, ..., 512}: 15 values
