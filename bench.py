@@ -320,6 +320,69 @@ def inner_roofline(torch, hj, W, n, k=16, cycles=100):
             "peak_basis": "SMs x 128 FP32 lanes x max SM clock / 4 FMA per point update"}
 
 
+def variable_coefficients(torch, hj, W, n=4096, hbm_peak=None):
+    """Per-point neighbour coefficients (heterogeneous diffusion, kappa
+    contrast 10): the thread-per-point kernel's cycle rate and its HBM
+    roofline at n^2, and time to a 1e-6 residual reduction at 256^2,
+    hierarchical vs classic (both binary64).  Algorithmic bytes per point
+    and cycle: binary32 u in/out, f, four -c/d planes and 1/d = 32 B;
+    binary64 u in/out, f, four coefficient planes and sigma = 64 B."""
+    out = {}
+    p = W.variable_coef_problem(2, n, n, seed=5, contrast=10.0)
+    st = p.st
+    ld = hj.padded_ld(n, torch.float32)
+    planes = torch.zeros((4, n + 2, ld), dtype=torch.float64, device="cuda")
+    planes[:, :, :n + 2] = torch.as_tensor(st.coef)
+    sig = hj.grid_from(st.sigma, 2, torch.float64)
+    for prec, dt, bpp in (("f32", torch.float32, 32), ("f64", torch.float64, 64)):
+        f = hj.grid_from(p.f, 2, dt)
+        for k in ((1, 4, 16) if prec == "f32" else (4,)):
+            t = []
+            for ncyc in (4, 24):
+                s = hj.Solver(st, sigma=sig, coef=planes, tile_x=32, tile_y=32, k=k, precision=prec,
+                              fixed_cycles=ncyc)
+                u = hj.grid_from(p.u0, 2, dt)
+                s.solve(f, u)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.solve(f, u)
+                e1.record()
+                torch.cuda.synchronize()
+                t.append(e0.elapsed_time(e1))
+                s.close()
+            us = (t[1] - t[0]) / 20 * 1e3
+            gbs = bpp * n * n / (us / 1e6) / 1e9
+            out[f"{prec}_32x32_k{k}"] = {"us_per_cycle": us, "glups": n * n / (us / 1e6) / 1e9,
+                                         "hbm_gbs": gbs, "frac": gbs / hbm_peak if hbm_peak else None,
+                                         "bytes_per_point": bpp}
+        del f
+    del planes, sig
+    q = W.variable_coef_problem(2, 256, 256, seed=6, contrast=10.0)
+    qpl = torch.zeros((4, 258, hj.padded_ld(256, torch.float64)), dtype=torch.float64, device="cuda")
+    qpl[:, :, :258] = torch.as_tensor(q.st.coef)
+    qsig = hj.grid_from(q.st.sigma, 2, torch.float64)
+    f = hj.grid_from(q.f, 2, torch.float64)
+    ttr = {}
+    for name, kw in [("hier_f64_32x32_k16", dict(tile_x=32, tile_y=32, k=16, check_every=64)),
+                     ("hier_f64_32x32_k64", dict(tile_x=32, tile_y=32, k=64, check_every=64)),
+                     ("classic_f64", dict(method="classic", check_every=1024))]:
+        s = hj.Solver(q.st, sigma=qsig, coef=qpl, precision="f64", tol=1e-6, max_cycles=20_000_000, **kw)
+        u = hj.grid_from(q.u0, 2, torch.float64)
+        s.solve(f, u.clone())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = s.solve(f, u)
+        torch.cuda.synchronize()
+        ttr[name] = {"seconds": time.perf_counter() - t0, "cycles": r["cycles"], "status": r["status"]}
+        s.close()
+    for name in ("hier_f64_32x32_k16", "hier_f64_32x32_k64"):
+        ttr[f"speedup_{name}_vs_classic"] = ttr["classic_f64"]["seconds"] / ttr[name]["seconds"]
+    out["time_to_1e-6_256_kappa10"] = ttr
+    return out
+
+
 def paper_replicas(torch, hj, W, precision="f64"):
     """Context: the paper's timing problems (Sections 3.5 and 4.2), residual
     reduced by 1e-4 from x0 = 1 with b = 1: best classic vs hierarchical
@@ -562,6 +625,7 @@ def main():
         extras["cfg4_batched_256_to_1e-8"] = time_batched(torch, hj, W)
         extras["cfg5_differentiation_1024"] = time_differentiation(torch, hj, W)
         extras["inner_sweep_roofline_k16"] = inner_roofline(torch, hj, W, n)
+        extras["variable_coefficients_4096"] = variable_coefficients(torch, hj, W, hbm_peak=hbm_peak)
     if args.paper_replicas and rank == 0:
         extras["paper_replicas"] = paper_replicas(torch, hj, W)
         extras["paper_replicas_f32"] = paper_replicas(torch, hj, W, "f32")

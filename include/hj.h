@@ -114,6 +114,15 @@ typedef struct {
     double sigma_const;   /* constant screening added to the diagonal            */
     const double *sigma;  /* device, grid layout, per-point screening; nullable  */
     int dtype;            /* hj_dtype of f and u                                 */
+    const double *coef;   /* device, nullable: per-point neighbour coefficients
+                             replacing cW..cN (the general tridiagonal a_i, c_i
+                             of Section 3 and its 2D analogue): planes W, E
+                             (1D) or W, E, S, N (2D), each rows x ld binary64 in
+                             the grid layout, one after another.  The diagonal
+                             stays cD + sigma_const + sigma_p.  Runs on the
+                             one-thread-per-point kernels under CUDA graphs;
+                             HJ_PREC_F64 and HJ_PREC_F32 only, no overlap, no
+                             adjoint, no batched solves (HJ_ERR_UNSUPPORTED)  */
 } hj_desc;
 
 typedef struct {

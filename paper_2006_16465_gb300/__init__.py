@@ -40,7 +40,7 @@ class hj_desc(C.Structure):
     _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("ld", C.c_longlong),
                 ("cW", C.c_double), ("cE", C.c_double), ("cS", C.c_double), ("cN", C.c_double),
                 ("cD", C.c_double), ("sigma_const", C.c_double), ("sigma", C.c_void_p),
-                ("dtype", C.c_int)]
+                ("dtype", C.c_int), ("coef", C.c_void_p)]
 
 
 class hj_params(C.Structure):
@@ -261,9 +261,12 @@ def _stream_handle(stream) -> int:
 
 
 def make_desc(dim, nx, ny, ld, cW, cE, cS=0.0, cN=0.0, cD=0.0, sigma_const=0.0, sigma=None,
-              dtype=HJ_F64) -> hj_desc:
+              dtype=HJ_F64, coef=None) -> hj_desc:
+    """coef: optional device tensor (planes, rows, ld) float64 of per-point
+    neighbour coefficients W, E[, S, N]."""
     return hj_desc(dim, nx, ny, ld, cW, cE, cS, cN, cD, sigma_const,
-                   None if sigma is None else int(sigma.data_ptr()), dtype)
+                   None if sigma is None else int(sigma.data_ptr()), dtype,
+                   None if coef is None else int(coef.data_ptr()))
 
 
 def make_params(**kw) -> hj_params:
@@ -281,10 +284,12 @@ class Solver:
     """One hj handle for a fixed grid shape, stencil and parameter set.
 
     stencil: any object with dim, nx, ny, cW, cE, cS, cN, cD, sigma_const
-    attributes; sigma: optional (rows, ld) float64 device tensor (kept alive
-    by the Solver as the ABI requires)."""
+    attributes; sigma: optional (rows, ld) float64 device tensor; coef:
+    optional (planes, rows, ld) float64 device tensor of per-point neighbour
+    coefficients W, E[, S, N] (both kept alive by the Solver as the ABI
+    requires)."""
 
-    def __init__(self, stencil, params: hj_params | None = None, sigma=None, dtype=None, **kw):
+    def __init__(self, stencil, params: hj_params | None = None, sigma=None, dtype=None, coef=None, **kw):
         import torch
         self.params = params if params is not None else make_params(**kw)
         self.dim, self.nx, self.ny = stencil.dim, stencil.nx, stencil.ny
@@ -295,9 +300,13 @@ class Solver:
         self.sigma = sigma
         if sigma is not None and sigma.shape[1] != self.ld:
             raise ValueError("sigma must be a padded grid with the solver's ld")
+        self.coef = coef
+        if coef is not None and (coef.dim() != 3 or coef.shape[2] != self.ld or coef.dtype != torch.float64
+                                 or not coef.is_contiguous()):
+            raise ValueError("coef must be a contiguous float64 (planes, rows, ld) tensor with the solver's ld")
         self.desc = make_desc(self.dim, self.nx, self.ny, self.ld, stencil.cW, stencil.cE, stencil.cS,
                               stencil.cN, stencil.cD, getattr(stencil, "sigma_const", 0.0), sigma,
-                              HJ_F64 if dtype == torch.float64 else HJ_F32)
+                              HJ_F64 if dtype == torch.float64 else HJ_F32, coef)
         self.h = hj_create(self.desc, self.params)
 
     def _check(self, t, name):

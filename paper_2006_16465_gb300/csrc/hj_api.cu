@@ -185,6 +185,11 @@ CycArgs base_args(const hj_handle *h, bool transpose) {
     a.oy = h->d.dim == 2 ? h->p.overlap_y : 0;
     a.jx = subdomain_count(h->d.nx, h->p.tile_x, a.ox);
     a.jy = h->d.dim == 2 ? subdomain_count(h->d.ny, h->p.tile_y, a.oy) : h->d.ny;
+    if (h->d.coef) {
+        a.vc = h->fam_outer == FAM_F64 ? (const void *)h->d.coef : (const void *)h->vcf;
+        a.vsig = h->d.sigma;
+        a.vcs = (long long)h->rows * h->d.ld;
+    }
     return a;
 }
 
@@ -297,7 +302,7 @@ struct Plan {
 
 // Whether the TMA-pipelined kernel runs this plan's cycles.
 bool want_ppc(const hj_handle *h, const PpcKernelInfo *pi, bool classic) {
-    if (classic || !pi || h->d.dim != 2 || overlapped(h)) return false;
+    if (classic || !pi || h->d.dim != 2 || overlapped(h) || h->d.coef) return false;
     if (h->p.pipeline == 1) return true;
     if (h->p.pipeline != -1) return false;
     const long long ntiles = (long long)((h->d.nx + pi->tx - 1) / pi->tx) * ((h->d.ny + pi->ty - 1) / pi->ty);
@@ -316,6 +321,19 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
     pl->period = 2;
     pl->deferred = false;
     const int nx = h->d.nx, ny = h->d.ny;
+    if (h->d.coef) {
+        // variable coefficients: one thread per point; classic Jacobi is the
+        // same kernel with one subiteration (a k = 1 cycle is a classic sweep)
+        const VcKernelInfo *vk = fam == FAM_F64 ? vc_kernels_f64() : vc_kernels_f32();
+        const int tx = h->p.tile_x, ty = h->d.dim == 2 ? h->p.tile_y : 1;
+        pl->fn = vk->fn[h->d.dim - 1][res];
+        pl->grid = h->d.dim == 2 ? dim3((nx + tx - 1) / tx, (ny + ty - 1) / ty) : dim3((nx + tx - 1) / tx, ny);
+        pl->block = h->d.dim == 2 ? dim3(tx, ty) : dim3(tx);
+        pl->smem = 2 * (tx + 2) * (h->d.dim == 2 ? ty + 2 : 1) * (fam == FAM_F64 ? 8 : 4);
+        if (classic) pl->a[0].k = pl->a[1].k = 1;
+        pl->ppc = false;
+        return HJ_OK;
+    }
     if (!want_ppc(h, pi, classic)) {
         geometry(h, ki, classic, &pl->grid, &pl->block);
         pl->fn = (!classic && overlapped(h)) ? ki->ovl[sig][res] : ki->fn[sig][res];
@@ -375,12 +393,12 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
 
 int plan_graph(hj_handle *h, const Plan &pl, int M, cudaGraphExec_t *ex) {
     if (pl.ppc) return get_graph<PpcArgs>(h, pl.pfn, pl.grid, pl.block, pl.smem, pl.p, pl.period, M, ex);
-    return get_graph<CycArgs>(h, pl.fn, pl.grid, pl.block, 0, pl.a, 2, M, ex);
+    return get_graph<CycArgs>(h, pl.fn, pl.grid, pl.block, pl.smem, pl.a, 2, M, ex);
 }
 
 void plan_launch(const Plan &pl, long long c, cudaStream_t s) {
     if (pl.ppc) pl.pfn<<<pl.grid, pl.block, pl.smem, s>>>(pl.p[c % pl.period]);
-    else pl.fn<<<pl.grid, pl.block, 0, s>>>(pl.a[c & 1]);
+    else pl.fn<<<pl.grid, pl.block, pl.smem, s>>>(pl.a[c & 1]);
 }
 
 struct RunOut {
@@ -546,6 +564,11 @@ int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int
             const CycArgs &base, void *b0, void *b1, ThirdBuffer third, double tol, long long max_cycles,
             long long fixed, cudaStream_t s, RunOut *ro, double *hist_out, long long hist_cap, long long *hist_len,
             int *used_persistent) {
+    if (h->d.coef) {   // variable coefficients: graph-captured launches only
+        if (used_persistent) *used_persistent = 0;
+        return run_cycles(h, ki, pi, fam, classic, sig, base, b0, b1, third, tol, max_cycles, fixed, s, ro,
+                          hist_out, hist_cap, hist_len);
+    }
     const PersistKernelInfo *pk =
         classic ? nullptr : find_persist(fam, h->d.dim, ki->tx, ki->ty, ki->threads / ki->tiles_per_cta);
     PersistKernel pclassic = nullptr;
@@ -560,7 +583,7 @@ int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int
     const long long cblocks = h->d.dim == 2 ? (long long)((h->d.nx + 31) / 32) * ((h->d.ny + 7) / 8)
                                             : (long long)((h->d.nx + 255) / 256) * h->d.ny;
     bool use = false;
-    if ((pk || pclassic) && fixed <= 0 && max_cycles > 0 && h->p.persistent != 0 && !overlapped(h)) {
+    if ((pk || pclassic) && fixed <= 0 && max_cycles > 0 && h->p.persistent != 0 && !overlapped(h) && !h->d.coef) {
         int cap = 0;
         if (pclassic) {
             int occ = 0;
@@ -616,7 +639,8 @@ int residual_of(hj_handle *h, const void *f, const void *u, bool transpose, doub
     const CycArgs a = base_args(h, transpose);
     const RedArgs red = red_args(h, RED_STORE, 0.0, 0);
     CKR(launch_residual_ex(h->d.dim, h->d.dtype == HJ_F64, f, u, h->d.sigma, h->d.ld, h->d.ld, h->d.nx, h->d.ny,
-                           a.cW, a.cE, a.cS, a.cN, a.dconst, 1, nullptr, red, s));
+                           a.cW, a.cE, a.cS, a.cN, a.dconst, 1, nullptr, red, s, h->d.coef,
+                           (long long)h->rows * h->d.ld));
     CKR(cudaMemcpyAsync(h->h_rstore, h->rstore, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CKR(cudaEventRecord(h->ev, s));
     CKR(cudaEventSynchronize(h->ev));
@@ -777,7 +801,8 @@ void fill_stats_config(const hj_handle *h, hj_stats *st, double t0) {
     st->tile_y = h->d.dim == 2 ? h->p.tile_y : 1;
     st->k = h->p.k;
     const TileKernelInfo *tk = h->ir ? h->k_inner : h->k_outer;
-    st->tile_threads = tk ? tk->threads / tk->tiles_per_cta : 0;
+    st->tile_threads = tk ? tk->threads / tk->tiles_per_cta
+                          : h->d.coef ? h->p.tile_x * (h->d.dim == 2 ? h->p.tile_y : 1) : 0;
     const PpcKernelInfo *pk = h->ir ? h->p_inner : h->p_outer;
     const bool ppc = want_ppc(h, pk, h->p.method == HJ_METHOD_CLASSIC);
     st->pipeline_stages = ppc ? pk->stages : 0;
@@ -869,7 +894,7 @@ int hj_tile_shapes(int dim, int precision, int *xy, int cap) {
 void hj_destroy(hj_handle *h) {
     if (!h) return;
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
-    void *dev[] = {h->ubuf, h->ubuf2, h->dC, h->dinv_outer, h->dinv32, h->r32, h->dA, h->dB, h->hf, h->hu, h->partials, h->gpart,
+    void *dev[] = {h->ubuf, h->ubuf2, h->dC, h->vcf, h->dinv_outer, h->dinv32, h->r32, h->dA, h->dB, h->hf, h->hu, h->partials, h->gpart,
                    h->hist, h->rstore, h->gcnt, h->fcnt, h->ctl, h->pscratch, h->barena, h->rs};
     for (void *p : dev)
         if (p) cudaFree(p);
@@ -927,7 +952,7 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     p.check_every += p.check_every & 1;
     if (d.dim == 1) p.tile_y = 1;
     if (p.autotune < 0 || p.autotune > 3) return seterr(HJ_ERR_INVALID_ARG, "autotune must be 0, 1, 2 or 3");
-    if (p.autotune != 0) {
+    if (p.autotune != 0 && !d.coef) {   // (variable coefficients: kept as given)
         hj_params tp = p;
         const int st = hj_autotune(&d, &tp, nullptr);
         if (st != HJ_OK) return st;
@@ -944,22 +969,53 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
         return seterr(HJ_ERR_INVALID_ARG, "overlap (%d, %d) must be smaller than the subdomain (%d, %d)", p.overlap_x,
                       p.overlap_y, p.tile_x, p.tile_y);
 
-    // diagonal dominance (Section 2.1): d_p >= |cW| + |cE| + |cS| + |cN|, d_p > 0
-    const double off = fabs(d.cW) + fabs(d.cE) + (d.dim == 2 ? fabs(d.cS) + fabs(d.cN) : 0.0);
     const int rows = d.dim == 2 ? d.ny + 2 : d.ny;
-    double dmin = d.cD + d.sigma_const;
-    if (d.sigma) {
-        std::vector<double> hs((size_t)rows * d.ld);
-        cudaError_t e = cudaMemcpy(hs.data(), d.sigma, hs.size() * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return seterr(HJ_ERR_CUDA, "reading sigma: %s", cudaGetErrorString(e));
-        const int r0 = d.dim == 2 ? 1 : 0, r1 = d.dim == 2 ? d.ny : d.ny - 1;
-        double smin = INFINITY;
-        for (int j = r0; j <= r1; ++j)
-            for (int i = 1; i <= d.nx; ++i) smin = std::min(smin, hs[(size_t)j * d.ld + i]);
-        dmin = d.cD + d.sigma_const + smin;
+    if (d.coef) {
+        if (ir) return seterr(HJ_ERR_UNSUPPORTED, "variable coefficients: HJ_PREC_F64 or HJ_PREC_F32 only");
+        if (p.overlap_x > 0 || p.overlap_y > 0)
+            return seterr(HJ_ERR_UNSUPPORTED, "variable coefficients do not take overlapping subdomains");
+        if (p.persistent == 1 || p.pipeline == 1)
+            return seterr(HJ_ERR_UNSUPPORTED, "variable coefficients run on graphs (persistent and pipeline must not be 1)");
+        if (p.tile_x < 1 || p.tile_y < 1) return seterr(HJ_ERR_INVALID_ARG, "tile sizes must be >= 1");
+        if ((long long)p.tile_x * (d.dim == 2 ? p.tile_y : 1) > 1024)
+            return seterr(HJ_ERR_UNSUPPORTED, "variable coefficients: one thread per point, at most 1024 per subdomain");
     }
-    if (!(dmin > 0.0) || dmin < off)
-        return seterr(HJ_ERR_NOT_DIAG_DOMINANT, "min diagonal %g < sum |off-diagonal| %g", dmin, off);
+    // diagonal dominance (Section 2.1): d_p >= |cW| + |cE| + |cS| + |cN|, d_p > 0
+    {
+        const int r0 = d.dim == 2 ? 1 : 0, r1 = d.dim == 2 ? d.ny : d.ny - 1;
+        std::vector<double> hs, hc;
+        if (d.sigma) {
+            hs.resize((size_t)rows * d.ld);
+            cudaError_t e = cudaMemcpy(hs.data(), d.sigma, hs.size() * sizeof(double), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return seterr(HJ_ERR_CUDA, "reading sigma: %s", cudaGetErrorString(e));
+        }
+        const int planes = d.dim == 2 ? 4 : 2;
+        const size_t ps = (size_t)rows * d.ld;
+        if (d.coef) {
+            hc.resize(ps * planes);
+            cudaError_t e = cudaMemcpy(hc.data(), d.coef, hc.size() * sizeof(double), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return seterr(HJ_ERR_CUDA, "reading coef: %s", cudaGetErrorString(e));
+        }
+        const double off_c = fabs(d.cW) + fabs(d.cE) + (d.dim == 2 ? fabs(d.cS) + fabs(d.cN) : 0.0);
+        double worst = INFINITY, wd = 0.0, wo = 0.0;   // smallest d_p - sum |off|
+        for (int j = r0; j <= r1; ++j)
+            for (int i = 1; i <= d.nx; ++i) {
+                const size_t q = (size_t)j * d.ld + i;
+                const double dp = d.cD + d.sigma_const + (d.sigma ? hs[q] : 0.0);
+                double off = off_c;
+                if (d.coef) {
+                    off = 0.0;
+                    for (int m = 0; m < planes; ++m) off += fabs(hc[m * ps + q]);
+                }
+                if (!(dp > 0.0) || dp - off < worst) {
+                    worst = dp > 0.0 ? dp - off : -INFINITY;
+                    wd = dp;
+                    wo = off;
+                }
+            }
+        if (!(worst >= 0.0))
+            return seterr(HJ_ERR_NOT_DIAG_DOMINANT, "diagonal %g < sum |off-diagonal| %g", wd, wo);
+    }
 
     hj_handle *h = new hj_handle();
     h->d = d;
@@ -1013,11 +1069,14 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     } else if (p.method == HJ_METHOD_CLASSIC) {
         h->k_classic = family_classic(h->fam_outer, d.dim);
     } else {
-        h->k_outer = find_tile(h->fam_outer, d.dim, p.tile_x, p.tile_y, p.tile_threads);
-        if (!h->k_outer)
+        // (variable coefficients run their own thread-per-point kernel: any
+        // subdomain of at most 1024 points)
+        h->k_outer = d.coef ? nullptr : find_tile(h->fam_outer, d.dim, p.tile_x, p.tile_y, p.tile_threads);
+        if (!h->k_outer && !d.coef)
             HJ_FAIL(HJ_ERR_UNSUPPORTED, "tile %dx%d (%d threads) not built for this precision", p.tile_x, p.tile_y,
                     p.tile_threads);
-        if (d.dim == 2) h->p_outer = find_ppc(h->fam_outer, p.tile_x, p.tile_y, h->k_outer->threads, p.pipeline_stages);
+        if (d.dim == 2 && h->k_outer)
+            h->p_outer = find_ppc(h->fam_outer, p.tile_x, p.tile_y, h->k_outer->threads, p.pipeline_stages);
     }
     if (p.pipeline == 1 && d.dim == 2 && p.method == HJ_METHOD_HIER && !(ir ? h->p_inner : h->p_outer))
         HJ_FAIL(HJ_ERR_UNSUPPORTED, "no pipelined kernel for tile %dx%d", p.tile_x, p.tile_y);
@@ -1033,9 +1092,24 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
             maxb = std::max(maxb, (size_t)g.x * g.y);
         }
     }
+    if (d.coef) {   // thread-per-point kernel: one block per subdomain
+        const long long gx = (d.nx + p.tile_x - 1) / p.tile_x;
+        maxb = std::max(maxb, (size_t)(d.dim == 2 ? gx * ((d.ny + p.tile_y - 1) / p.tile_y) : gx * d.ny));
+    }
     h->max_blocks = maxb;
     h->max_groups = (maxb + kGroup - 1) / kGroup;
     HJ_ALLOC(h->ubuf, h->grid_bytes);
+    if (d.coef && h->fam_outer == FAM_F32) {
+        // -c/d per neighbour, 1/d and d per point, in binary32
+        const int np = (d.dim == 2 ? 4 : 2) + 2;
+        const long long ps = (long long)rows * d.ld;
+        HJ_ALLOC(h->vcf, (size_t)np * ps * sizeof(float));
+        if (cudaMemset(h->vcf, 0, (size_t)np * ps * sizeof(float)) != cudaSuccess ||
+            launch_vc_prep(d.dim, d.coef, d.sigma, d.cD + d.sigma_const, d.ld, ps, d.nx, d.ny, h->vcf, 0) !=
+                cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess)
+            HJ_FAIL(HJ_ERR_CUDA, "preparing variable coefficients");
+    }
     HJ_ALLOC(h->partials, 2 * maxb * sizeof(double));
     HJ_ALLOC(h->gpart, 2 * h->max_groups * sizeof(double));
     HJ_ALLOC(h->gcnt, h->max_groups * sizeof(unsigned));
@@ -1139,6 +1213,7 @@ int hj_residual(hj_handle *h, const void *f, const void *u, double *abs_l2, doub
 int hj_solve_adjoint(hj_handle *h, const void *g, const void *u, void *dl_df, void *dl_dsigma, hj_stream stream,
                      hj_stats *stats) {
     if (!h) return seterr(HJ_ERR_INVALID_ARG, "handle is NULL");
+    if (h->d.coef) return seterr(HJ_ERR_UNSUPPORTED, "the adjoint is built for constant neighbour coefficients");
     CKS(check_ptr(h, g, "g"));
     CKS(check_ptr(h, u, "u"));
     CKS(check_ptr(h, dl_df, "dl_df"));

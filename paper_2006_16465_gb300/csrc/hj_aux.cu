@@ -38,6 +38,8 @@ struct AuxArgs {
     int nx, ny;
     double cW, cE, cS, cN, dconst;
     RedArgs red;
+    const double *coef;   // nullable: per-point W, E[, S, N] coefficient planes, cps apart
+    long long cps;
 };
 
 // Grid-stride walk over blocks of points: 2D blocks of 32 x 8 points (one
@@ -76,9 +78,18 @@ __global__ void __launch_bounds__(256) residual_kernel(const AuxArgs a) {
         const long long q = (long long)j * a.ld + i;
         const double fv = (double)((const T *)a.f)[q];
         const double d = a.sigma ? __dadd_rn(a.dconst, a.sigma[q]) : a.dconst;
+        double cW = a.cW, cE = a.cE, cS = a.cS, cN = a.cN;
+        if (a.coef) {
+            cW = a.coef[q];
+            cE = a.coef[a.cps + q];
+            if (D == 2) {
+                cS = a.coef[2 * a.cps + q];
+                cN = a.coef[3 * a.cps + q];
+            }
+        }
         const double r = resid_exact<D == 2>(fv, d, (double)u[q], (double)u[q - 1], (double)u[q + 1],
                                              D == 2 ? (double)u[q - a.ld] : 0.0,
-                                             D == 2 ? (double)u[q + a.ld] : 0.0, a.cW, a.cE, a.cS, a.cN);
+                                             D == 2 ? (double)u[q + a.ld] : 0.0, cW, cE, cS, cN);
         rr += r * r;
         ff += fv * fv;
         if (a.r32) a.r32[(long long)j * a.ld2 + i] = (float)r;
@@ -89,6 +100,26 @@ __global__ void __launch_bounds__(256) residual_kernel(const AuxArgs a) {
     } else {
         const double vals[1] = {rr};
         reduce_grid<1>(a.red, vals);
+    }
+}
+
+// Binary32 factors of the variable-coefficient kernels from the caller's
+// binary64 coefficients: planes -cW/d, -cE/d[, -cS/d, -cN/d], 1/d, d with
+// d_p = dconst + sigma_p (each computed in binary64, then rounded once).
+template <int D>
+__global__ void __launch_bounds__(256) vc_prep_kernel(const double *coef, const double *sigma, double dconst,
+                                                     long long ld, long long ps, int nx, int ny, float *out) {
+    int i, j;
+    const long long nb = AuxGeom<D>::nblocks(nx, ny);
+    constexpr int NP = D == 2 ? 4 : 2;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        if (!AuxGeom<D>::idx(nx, ny, b, i, j)) continue;
+        const long long q = (long long)j * ld + i;
+        const double d = sigma ? __dadd_rn(dconst, sigma[q]) : dconst;
+        const double iv = __drcp_rn(d);
+        for (int m = 0; m < NP; ++m) out[m * ps + q] = (float)(-coef[m * ps + q] * iv);
+        out[NP * ps + q] = (float)iv;
+        out[(NP + 1) * ps + q] = (float)d;
     }
 }
 
@@ -195,10 +226,12 @@ cudaError_t launch_make_dinv_box(const double *sigma, double dconst, long long l
 
 cudaError_t launch_residual_ex(int dim, int user_f64, const void *f, const void *u, const double *sigma,
                                long long ld, long long ld2, int nx, int ny, double cW, double cE, double cS,
-                               double cN, double dconst, int with_fnorm, float *r32, RedArgs red, cudaStream_t s) {
+                               double cN, double dconst, int with_fnorm, float *r32, RedArgs red, cudaStream_t s,
+                               const double *coef, long long cps) {
     AuxArgs a = {};
     a.f = f; a.u = u; a.sigma = sigma; a.r32 = r32; a.ld = ld; a.ld2 = ld2; a.nx = nx; a.ny = ny;
     a.cW = cW; a.cE = cE; a.cS = cS; a.cN = cN; a.dconst = dconst; a.red = red;
+    a.coef = coef; a.cps = cps;
     const dim3 g = aux_grid(dim, nx, ny), b = aux_block(dim);
 #define HJ_RES_LAUNCH(T, D)                                                              \
     do {                                                                                 \
@@ -243,6 +276,14 @@ cudaError_t launch_grad_sigma_ex(int dim, int user_f64, const void *lam, const v
         if (dim == 2) grad_sigma_kernel<float, 2><<<g, b, 0, s>>>((const float *)lam, (const float *)u, dsig, ld, nx, ny, accumulate);
         else grad_sigma_kernel<float, 1><<<g, b, 0, s>>>((const float *)lam, (const float *)u, dsig, ld, nx, ny, accumulate);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vc_prep(int dim, const double *coef, const double *sigma, double dconst, long long ld,
+                           long long ps, int nx, int ny, float *out, cudaStream_t s) {
+    const dim3 g = aux_grid(dim, nx, ny), b = aux_block(dim);
+    if (dim == 2) vc_prep_kernel<2><<<g, b, 0, s>>>(coef, sigma, dconst, ld, ps, nx, ny, out);
+    else vc_prep_kernel<1><<<g, b, 0, s>>>(coef, sigma, dconst, ld, ps, nx, ny, out);
     return cudaGetLastError();
 }
 

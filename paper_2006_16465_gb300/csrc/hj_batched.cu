@@ -260,6 +260,7 @@ int validate_desc(const hj_desc &d, int i) {
     if (d.dim != 2) return seterr(HJ_ERR_INVALID_ARG, "problem %d: batched solves are 2D", i);
     if (d.nx < 1 || d.ny < 1 || d.ny > 524280) return seterr(HJ_ERR_INVALID_ARG, "problem %d: bad size", i);
     if (d.dtype != HJ_F64) return seterr(HJ_ERR_INVALID_ARG, "problem %d: batched solves take binary64 arrays", i);
+    if (d.coef) return seterr(HJ_ERR_UNSUPPORTED, "problem %d: batched solves take constant neighbour coefficients", i);
     if (d.ld < (long long)d.nx + 2 || (d.ld * 8) % 16) return seterr(HJ_ERR_INVALID_ARG, "problem %d: bad ld", i);
     if (d.sigma && ((uintptr_t)d.sigma & 15)) return seterr(HJ_ERR_INVALID_ARG, "problem %d: sigma not aligned", i);
     const double off = fabs(d.cW) + fabs(d.cE) + fabs(d.cS) + fabs(d.cN);

@@ -586,6 +586,121 @@ __global__ void __launch_bounds__(32 * WPT * WPB) hier1d_kernel(const CycArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// Variable neighbour coefficients (the general tridiagonal a_i, d_i, c_i of
+// Section 3 and its 2D analogue): one thread per point, the subdomain plus its
+// halo in two shared-memory containers used in turn (the paper's own kernel
+// layout, Appendix A), one barrier per subiteration.  A thread keeps its
+// point's coefficients in registers.  blockDim = (tile_x, tile_y) in 2D,
+// (tile_x) in 1D with one copy per blockIdx.y.
+//   binary64: acc = cW*uW; acc += cE*uE; [acc += cS*uS; acc += cN*uN;]
+//             u' = (f - acc) * (1/d_p), d_p = dconst + sigma_p, each operation
+//             rounded separately (the oracle's order);
+//   binary32: u' = f/d + (-cN/d) uN + (-cS/d) uS + (-cE/d) uE + (-cW/d) uW as a
+//             fused chain from precomputed per-point factors.
+// ---------------------------------------------------------------------------
+template <typename S, typename T, int DIM, bool EXACT, bool RES>
+__global__ void vc_kernel(const CycArgs a) {
+    if constexpr (RES) {
+        if (*(volatile int *)&a.red.ctl->done >= 0) return;
+    }
+    extern __shared__ __align__(16) unsigned char vc_smem[];
+    const int TX = blockDim.x, TY = DIM == 2 ? blockDim.y : 1;
+    const int lw = TX + 2, lh = DIM == 2 ? TY + 2 : 1;
+    T *buf0 = (T *)vc_smem, *buf1 = buf0 + lw * lh;
+    const int tx = threadIdx.x, ty = DIM == 2 ? threadIdx.y : 0;
+    const int i = 1 + blockIdx.x * TX + tx;
+    const int j = DIM == 2 ? 1 + blockIdx.y * TY + ty : blockIdx.y;
+    const int nx = a.nx, ny = a.ny;
+    const long long ld = a.ld;
+    const bool in = i <= nx && (DIM == 1 || j <= ny);
+    const S *__restrict__ uin = (const S *)a.uin;
+    const T *__restrict__ f = (const T *)a.f;
+    const int me = (ty + (DIM == 2 ? 1 : 0)) * lw + tx + 1;
+    auto ld_u = [&](int jj, int ii) -> T {
+        const bool ok = ii <= nx + 1 && (DIM == 1 || jj <= ny + 1);
+        return ok ? ld_s<S, T>(uin + (long long)jj * ld + ii) : (T)0;
+    };
+    // stage the point and the halo cells next to it into both containers
+    const T v0 = ld_u(j, i);
+    buf0[me] = v0;
+    buf1[me] = v0;
+    if (tx == 0) { const T h = ld_u(j, i - 1); buf0[me - 1] = h; buf1[me - 1] = h; }
+    if (tx == TX - 1) { const T h = ld_u(j, i + 1); buf0[me + 1] = h; buf1[me + 1] = h; }
+    if constexpr (DIM == 2) {
+        if (ty == 0) { const T h = ld_u(j - 1, i); buf0[me - lw] = h; buf1[me - lw] = h; }
+        if (ty == TY - 1) { const T h = ld_u(j + 1, i); buf0[me + lw] = h; buf1[me + lw] = h; }
+    }
+    // this point's factors
+    const long long q = (long long)j * ld + i;
+    const long long ps = a.vcs;
+    T cw = 0, ce = 0, cs = 0, cn = 0, g = 0, dpt = 0, iv = 0;
+    if (in) {
+        if constexpr (EXACT) {
+            const double *c = (const double *)a.vc;
+            cw = c[q];
+            ce = c[ps + q];
+            if constexpr (DIM == 2) {
+                cs = c[2 * ps + q];
+                cn = c[3 * ps + q];
+            }
+            dpt = a.vsig ? __dadd_rn(a.dconst, a.vsig[q]) : a.dconst;
+            iv = __drcp_rn(dpt);
+            g = f[q];
+        } else {
+            const float *c = (const float *)a.vc;
+            constexpr int NP = DIM == 2 ? 4 : 2;   // planes before 1/d and d
+            cw = c[q];
+            ce = c[ps + q];
+            if constexpr (DIM == 2) {
+                cs = c[2 * ps + q];
+                cn = c[3 * ps + q];
+            }
+            iv = c[NP * ps + q];
+            dpt = c[(NP + 1) * ps + q];
+            g = f[q] * iv;
+        }
+    }
+    __syncthreads();
+    typedef typename std::conditional<EXACT, double, T>::type Acc;
+    Acc acc = 0;
+    for (int s = 0; s < a.k; ++s) {
+        const T *src = (s & 1) ? buf1 : buf0;
+        T *dst = (s & 1) ? buf0 : buf1;
+        if (in) {
+            const T old = src[me], W = src[me - 1], E = src[me + 1];
+            const T Sv = DIM == 2 ? src[me - lw] : (T)0, Nv = DIM == 2 ? src[me + lw] : (T)0;
+            T nv, res = 0;
+            if constexpr (EXACT) {
+                double t = __dmul_rn(cw, W);
+                t = __dadd_rn(t, __dmul_rn(ce, E));
+                if constexpr (DIM == 2) {
+                    t = __dadd_rn(t, __dmul_rn(cs, Sv));
+                    t = __dadd_rn(t, __dmul_rn(cn, Nv));
+                }
+                const double tt = __dsub_rn(g, t);
+                nv = __dmul_rn(tt, iv);
+                if (RES && s == 0) res = __dsub_rn(tt, __dmul_rn(dpt, old));
+            } else {
+                T t = g;
+                if constexpr (DIM == 2) {
+                    t = fma(cn, Nv, t);
+                    t = fma(cs, Sv, t);
+                }
+                t = fma(ce, E, t);
+                t = fma(cw, W, t);
+                nv = t;
+                if (RES && s == 0) res = (t - old) * dpt;
+            }
+            if constexpr (RES) acc += (Acc)res * (Acc)res;
+            dst[me] = nv;
+        }
+        __syncthreads();
+    }
+    if (in) st_s<S, T>((S *)a.uout + q, ((a.k & 1) ? buf1 : buf0)[me]);
+    if constexpr (RES) reduce_grid_acc(a.red, acc);
+}
+
+// ---------------------------------------------------------------------------
 // Classic global-memory Jacobi (Section 3.2): one sweep per launch, one thread
 // per point, every point reads u_c only and writes u_{c+1}.  Same update
 // arithmetic and fused residual as the cycle kernels.
@@ -681,3 +796,6 @@ __global__ void __launch_bounds__(256) classic1d_kernel(const CycArgs a) {
      {{hj::classic1d_kernel<S, T, EX, false, false>, hj::classic1d_kernel<S, T, EX, false, true>},   \
       {hj::classic1d_kernel<S, T, EX, true, false>, hj::classic1d_kernel<S, T, EX, true, true>}},     \
      {{nullptr, nullptr}, {nullptr, nullptr}}}
+#define HJ_KVC(S, T, EX)                                                                              \
+    {{{hj::vc_kernel<S, T, 1, EX, false>, hj::vc_kernel<S, T, 1, EX, true>},                          \
+      {hj::vc_kernel<S, T, 2, EX, false>, hj::vc_kernel<S, T, 2, EX, true>}}}

@@ -29,4 +29,7 @@ static const TileKernelInfo k_classic[] = {HJ_KC2D(float, float, false), HJ_KC1D
 const TileKernelInfo *tile_kernels_f32(int *n) { *n = sizeof(k_tiles) / sizeof(k_tiles[0]); return k_tiles; }
 const TileKernelInfo *classic_kernels_f32(int *n) { *n = 2; return k_classic; }
 
+static const VcKernelInfo k_vc = HJ_KVC(float, float, false);
+const VcKernelInfo *vc_kernels_f32() { return &k_vc; }
+
 }  // namespace hj

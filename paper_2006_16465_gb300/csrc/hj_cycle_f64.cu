@@ -37,4 +37,7 @@ static const PpcKernelInfo k_ppc[] = {
 };
 const PpcKernelInfo *ppc_kernels_f64(int *n) { *n = sizeof(k_ppc) / sizeof(k_ppc[0]); return k_ppc; }
 
+static const VcKernelInfo k_vc = HJ_KVC(double, double, true);
+const VcKernelInfo *vc_kernels_f64() { return &k_vc; }
+
 }  // namespace hj

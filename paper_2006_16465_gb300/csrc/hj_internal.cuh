@@ -77,6 +77,13 @@ struct CycArgs {
     // overlapping subdomains (Sections 3.4, 4.3): points shared with each
     // neighbour along x / y, and subdomains along x / y (2D; 1D: along x)
     int ox, oy, jx, jy;
+    // variable neighbour coefficients (null: constant cW..cN above): planes of
+    // rows * ld elements, vcs apart.  binary64: the caller's W, E[, S, N]
+    // coefficients, with d_p = dconst + sigma_p (vsig, nullable); binary32:
+    // -cW/d, -cE/d[, -cS/d, -cN/d], 1/d, d per point, precomputed
+    const void *vc;
+    const double *vsig;
+    long long vcs;
 };
 
 // Subdomain j of J along one dimension of n interior points, T points each,
@@ -326,6 +333,14 @@ struct TileKernelInfo {
     CycKernel ovl[2][2];// [sig][res] overlapping subdomains (null for classic kernels)
 };
 
+// Variable-coefficient kernels: [dim - 1][res], one thread per point, dynamic
+// shared memory 2 * (tile_x + 2) * (tile_y + 2) elements of the compute type.
+struct VcKernelInfo {
+    CycKernel fn[2][2];
+};
+const VcKernelInfo *vc_kernels_f64();
+const VcKernelInfo *vc_kernels_f32();
+
 // Kernel registries (one per storage/compute combination).
 enum KernelFamily { FAM_F64 = 0, FAM_F32 = 1, FAM_BF16 = 2 };
 const TileKernelInfo *tile_kernels_f64(int *n);
@@ -341,9 +356,14 @@ const PpcKernelInfo *ppc_kernels_bf16(int *n);
 // Grid-wide helper kernels (hj_aux.cu).
 cudaError_t launch_make_dinv_box(const double *sigma, double dconst, long long ld, long long ld2, int row0, int rows,
                                  int col0, int cols, int family, void *dinv, cudaStream_t s);
+// coef (nullable): per-point W, E[, S, N] coefficient planes cps elements apart
 cudaError_t launch_residual_ex(int dim, int user_f64, const void *f, const void *u, const double *sigma,
                                long long ld, long long ld2, int nx, int ny, double cW, double cE, double cS,
-                               double cN, double dconst, int with_fnorm, float *r32, RedArgs red, cudaStream_t s);
+                               double cN, double dconst, int with_fnorm, float *r32, RedArgs red, cudaStream_t s,
+                               const double *coef = nullptr, long long cps = 0);
+// binary32 factors of the variable-coefficient kernels (vc_kernel)
+cudaError_t launch_vc_prep(int dim, const double *coef, const double *sigma, double dconst, long long ld,
+                           long long ps, int nx, int ny, float *out, cudaStream_t s);
 cudaError_t launch_update_residual_ex(int dim, const double *f, const double *uin, const void *d, int d_bf16,
                                       double *uout, const double *sigma, float *r32, long long ld, long long ld2,
                                       int nx, int ny, double cW, double cE, double cS, double cN, double dconst,

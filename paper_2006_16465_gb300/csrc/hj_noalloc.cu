@@ -86,6 +86,7 @@ extern "C" int hj_cycles_noalloc(const hj_desc *desc, const hj_params *params, c
     if (d.dim == 1 && d.ny > 65535) return seterr(HJ_ERR_INVALID_ARG, "1D: at most 65535 rows");
     if (d.dim == 2 && (d.ny + 7) / 8 > 65535) return seterr(HJ_ERR_INVALID_ARG, "2D: ny must be <= 524280");
     if (d.sigma) return seterr(HJ_ERR_UNSUPPORTED, "per-point sigma needs workspace; use sigma_const or hj_create");
+    if (d.coef) return seterr(HJ_ERR_UNSUPPORTED, "per-point neighbour coefficients need workspace; use hj_create");
     const bool f64 = p.precision == HJ_PREC_F64;
     if (!(f64 || p.precision == HJ_PREC_F32) || f64 != (d.dtype == HJ_F64))
         return seterr(HJ_ERR_INVALID_ARG, "precision must be HJ_PREC_F64 (binary64 data) or HJ_PREC_F32 (binary32 data)");

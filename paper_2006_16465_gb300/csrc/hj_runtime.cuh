@@ -67,6 +67,7 @@ struct hj_handle {
     long long ld_in = 0;          // row pitch of the refinement's binary32 / bfloat16 arrays
     void *ubuf = nullptr;
     void *ubuf2 = nullptr;        // third iterate buffer (pipelined kernel, deferred residual fold)
+    float *vcf = nullptr;         // binary32 factors of the variable-coefficient kernels
     void *dinv_outer = nullptr;   // per-point 1/d in the outer compute type (sigma given)
     float *dinv32 = nullptr;      // per-point 1/d in binary32 (refinement, sigma given)
     float *r32 = nullptr;         // refinement: binary32 residual (inner RHS)

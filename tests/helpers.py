@@ -10,6 +10,16 @@ def gpu_solver(prob_or_st, **params):
     sig = None
     if st.sigma is not None:
         sig = hj.grid_from(st.sigma, st.dim, torch.float64)
+    coef = None
+    if getattr(st, "coef", None) is not None and "coef" not in params:
+        # per-point neighbour coefficients, padded to the solver's ld
+        dtype = torch.float32 if params.get("precision") == "f32" else torch.float64
+        ld = hj.padded_ld(st.nx, dtype)
+        c = np.asarray(st.coef)
+        coef = torch.zeros((c.shape[0], c.shape[1], ld), dtype=torch.float64, device="cuda")
+        coef[:, :, :st.nx + 2] = torch.as_tensor(c)
+    if coef is not None:
+        params["coef"] = coef
     return hj.Solver(st, sigma=sig, **params)
 
 
