@@ -322,11 +322,13 @@ def inner_roofline(torch, hj, W, n, k=16, cycles=100):
 
 def variable_coefficients(torch, hj, W, n=4096, hbm_peak=None):
     """Per-point neighbour coefficients (heterogeneous diffusion, kappa
-    contrast 10): the thread-per-point kernel's cycle rate and its HBM
-    roofline at n^2, and time to a 1e-6 residual reduction at 256^2,
-    hierarchical vs classic (both binary64).  Algorithmic bytes per point
-    and cycle: binary32 u in/out, f, four -c/d planes and 1/d = 32 B;
-    binary64 u in/out, f, four coefficient planes and sigma = 64 B."""
+    contrast 10): the thread-per-point kernel's cycle rate and its roofline
+    at n^2, and time to a 1e-6 residual reduction at 256^2, hierarchical vs
+    classic (both binary64).  Algorithmic bytes per point and cycle: binary32
+    u in/out, f, four -c/d planes and 1/d = 32 B; binary64 u in/out, f, four
+    coefficient planes and 1/d = 64 B.  Binary64 is bound by the FP64 pipe:
+    9 separately rounded operations per point update against the part's
+    nominal 1.25 TFLOP/s FP64 = 0.625 T operations/s."""
     out = {}
     p = W.variable_coef_problem(2, n, n, seed=5, contrast=10.0)
     st = p.st
@@ -334,29 +336,35 @@ def variable_coefficients(torch, hj, W, n=4096, hbm_peak=None):
     planes = torch.zeros((4, n + 2, ld), dtype=torch.float64, device="cuda")
     planes[:, :, :n + 2] = torch.as_tensor(st.coef)
     sig = hj.grid_from(st.sigma, 2, torch.float64)
-    for prec, dt, bpp in (("f32", torch.float32, 32), ("f64", torch.float64, 64)):
+    runs = [("f32", (32, 32), 4), ("f32", (32, 8), 1), ("f32", (32, 8), 4), ("f32", (32, 8), 16),
+            ("f64", (32, 8), 1), ("f64", (32, 8), 4)]
+    for prec, tile, k in runs:
+        dt = torch.float32 if prec == "f32" else torch.float64
+        bpp = 32 if prec == "f32" else 64
         f = hj.grid_from(p.f, 2, dt)
-        for k in ((1, 4, 16) if prec == "f32" else (4,)):
-            t = []
-            for ncyc in (4, 24):
-                s = hj.Solver(st, sigma=sig, coef=planes, tile_x=32, tile_y=32, k=k, precision=prec,
-                              fixed_cycles=ncyc)
-                u = hj.grid_from(p.u0, 2, dt)
-                s.solve(f, u)
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                s.solve(f, u)
-                e1.record()
-                torch.cuda.synchronize()
-                t.append(e0.elapsed_time(e1))
-                s.close()
-            us = (t[1] - t[0]) / 20 * 1e3
-            gbs = bpp * n * n / (us / 1e6) / 1e9
-            out[f"{prec}_32x32_k{k}"] = {"us_per_cycle": us, "glups": n * n / (us / 1e6) / 1e9,
-                                         "hbm_gbs": gbs, "frac": gbs / hbm_peak if hbm_peak else None,
-                                         "bytes_per_point": bpp}
+        t = []
+        for ncyc in (4, 24):
+            s = hj.Solver(st, sigma=sig, coef=planes, tile_x=tile[0], tile_y=tile[1], k=k, precision=prec,
+                          fixed_cycles=ncyc)
+            u = hj.grid_from(p.u0, 2, dt)
+            s.solve(f, u)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.solve(f, u)
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+            s.close()
+        us = (t[1] - t[0]) / 20 * 1e3
+        gbs = bpp * n * n / (us / 1e6) / 1e9
+        row = {"us_per_cycle": us, "glups": n * n / (us / 1e6) / 1e9, "hbm_gbs": gbs,
+               "hbm_frac": gbs / hbm_peak if hbm_peak else None, "bytes_per_point": bpp}
+        if prec == "f64":
+            row["fp64_ops_per_s"] = 9.0 * k * n * n / (us / 1e6)
+            row["fp64_frac"] = row["fp64_ops_per_s"] / 0.625e12
+        out[f"{prec}_{tile[0]}x{tile[1]}_k{k}"] = row
         del f
     del planes, sig
     q = W.variable_coef_problem(2, 256, 256, seed=6, contrast=10.0)

@@ -594,12 +594,13 @@ __global__ void __launch_bounds__(32 * WPT * WPB) hier1d_kernel(const CycArgs a)
 // (tile_x) in 1D with one copy per blockIdx.y.
 //   binary64: acc = cW*uW; acc += cE*uE; [acc += cS*uS; acc += cN*uN;]
 //             u' = (f - acc) * (1/d_p), d_p = dconst + sigma_p, each operation
-//             rounded separately (the oracle's order);
+//             rounded separately (the oracle's order); 1/d_p comes from the
+//             handle's dinv plane when sigma is a field;
 //   binary32: u' = f/d + (-cN/d) uN + (-cS/d) uS + (-cE/d) uE + (-cW/d) uW as a
 //             fused chain from precomputed per-point factors.
 // ---------------------------------------------------------------------------
 template <typename S, typename T, int DIM, bool EXACT, bool RES>
-__global__ void vc_kernel(const CycArgs a) {
+__global__ void __launch_bounds__(1024, 2) vc_kernel(const CycArgs a) {
     if constexpr (RES) {
         if (*(volatile int *)&a.red.ctl->done >= 0) return;
     }
@@ -620,45 +621,56 @@ __global__ void vc_kernel(const CycArgs a) {
         const bool ok = ii <= nx + 1 && (DIM == 1 || jj <= ny + 1);
         return ok ? ld_s<S, T>(uin + (long long)jj * ld + ii) : (T)0;
     };
-    // stage the point and the halo cells next to it into both containers
+    // Every global load first (the point, the halo cells next to it, f and
+    // the point's factors), then the shared-memory stores: one round of
+    // memory latency per subdomain instead of one per kind of operand.
     const T v0 = ld_u(j, i);
-    buf0[me] = v0;
-    buf1[me] = v0;
-    if (tx == 0) { const T h = ld_u(j, i - 1); buf0[me - 1] = h; buf1[me - 1] = h; }
-    if (tx == TX - 1) { const T h = ld_u(j, i + 1); buf0[me + 1] = h; buf1[me + 1] = h; }
+    const T hw = tx == 0 ? ld_u(j, i - 1) : (T)0;
+    const T he = tx == TX - 1 ? ld_u(j, i + 1) : (T)0;
+    T hs = 0, hn = 0;
     if constexpr (DIM == 2) {
-        if (ty == 0) { const T h = ld_u(j - 1, i); buf0[me - lw] = h; buf1[me - lw] = h; }
-        if (ty == TY - 1) { const T h = ld_u(j + 1, i); buf0[me + lw] = h; buf1[me + lw] = h; }
+        hs = ty == 0 ? ld_u(j - 1, i) : (T)0;
+        hn = ty == TY - 1 ? ld_u(j + 1, i) : (T)0;
     }
-    // this point's factors
     const long long q = (long long)j * ld + i;
     const long long ps = a.vcs;
     T cw = 0, ce = 0, cs = 0, cn = 0, g = 0, dpt = 0, iv = 0;
     if (in) {
         if constexpr (EXACT) {
-            const double *c = (const double *)a.vc;
-            cw = c[q];
-            ce = c[ps + q];
+            const double *__restrict__ c = (const double *)a.vc;
+            cw = __ldg(c + q);
+            ce = __ldg(c + ps + q);
             if constexpr (DIM == 2) {
-                cs = c[2 * ps + q];
-                cn = c[3 * ps + q];
+                cs = __ldg(c + 2 * ps + q);
+                cn = __ldg(c + 3 * ps + q);
             }
-            dpt = a.vsig ? __dadd_rn(a.dconst, a.vsig[q]) : a.dconst;
-            iv = __drcp_rn(dpt);
-            g = f[q];
+            // 1/d_p from the handle's plane (the same correctly rounded
+            // reciprocal of dconst + sigma_p): binary64 arithmetic is the
+            // scarce resource here, bytes are not
+            if constexpr (RES) dpt = a.vsig ? __dadd_rn(a.dconst, __ldg(a.vsig + q)) : a.dconst;
+            iv = a.dinv ? __ldg((const double *)a.dinv + q) : __drcp_rn(a.dconst);
+            g = __ldg(f + q);
         } else {
-            const float *c = (const float *)a.vc;
+            const float *__restrict__ c = (const float *)a.vc;
             constexpr int NP = DIM == 2 ? 4 : 2;   // planes before 1/d and d
-            cw = c[q];
-            ce = c[ps + q];
+            cw = __ldg(c + q);
+            ce = __ldg(c + ps + q);
             if constexpr (DIM == 2) {
-                cs = c[2 * ps + q];
-                cn = c[3 * ps + q];
+                cs = __ldg(c + 2 * ps + q);
+                cn = __ldg(c + 3 * ps + q);
             }
-            iv = c[NP * ps + q];
-            dpt = c[(NP + 1) * ps + q];
-            g = f[q] * iv;
+            iv = __ldg(c + NP * ps + q);
+            if constexpr (RES) dpt = __ldg(c + (NP + 1) * ps + q);
+            g = __ldg(f + q) * iv;
         }
+    }
+    buf0[me] = v0;
+    buf1[me] = v0;
+    if (tx == 0) { buf0[me - 1] = hw; buf1[me - 1] = hw; }
+    if (tx == TX - 1) { buf0[me + 1] = he; buf1[me + 1] = he; }
+    if constexpr (DIM == 2) {
+        if (ty == 0) { buf0[me - lw] = hs; buf1[me - lw] = hs; }
+        if (ty == TY - 1) { buf0[me + lw] = hn; buf1[me + lw] = hn; }
     }
     __syncthreads();
     typedef typename std::conditional<EXACT, double, T>::type Acc;
