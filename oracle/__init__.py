@@ -25,15 +25,16 @@ from pathlib import Path
 import numpy as np
 
 _HERE = Path(__file__).resolve().parent
-_SRC = _HERE / "hj_oracle.c"
+_SRCS = [_HERE / "hj_oracle.c", _HERE / "hj_oracle3d.c"]
 _LIB = _HERE / "libhj_oracle.so"
 
 
 def build(force: bool = False) -> Path:
     """Compile the oracle with gcc (-O2, no FMA contraction, no fast-math)."""
-    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+    newest = max(s.stat().st_mtime for s in _SRCS)
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < newest:
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", str(_SRC), "-o", str(_LIB) + ".tmp", "-lm"]
+               "-shared"] + [str(s) for s in _SRCS] + ["-o", str(_LIB) + ".tmp", "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(str(_LIB) + ".tmp", _LIB)
     return _LIB
@@ -44,6 +45,13 @@ class _Problem(C.Structure):
                 ("cW", C.c_double), ("cE", C.c_double), ("cS", C.c_double),
                 ("cN", C.c_double), ("cD", C.c_double), ("sigma_const", C.c_double),
                 ("sigma", C.c_void_p), ("coef", C.c_void_p)]
+
+
+class _Problem3(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("cW", C.c_double), ("cE", C.c_double), ("cS", C.c_double), ("cN", C.c_double),
+                ("cB", C.c_double), ("cT", C.c_double), ("cD", C.c_double),
+                ("sigma_const", C.c_double), ("sigma", C.c_void_p)]
 
 
 _lib = None
@@ -83,6 +91,16 @@ def lib():
                                     C.c_double, C.c_long, _D, C.c_long, C.POINTER(C.c_int)]
         L.hjo_solve_ovl.restype = C.c_long
         L.hjo_run_fixed_ovl.argtypes = [P, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_long]
+        P3 = C.POINTER(_Problem3)
+        L.hjo3_apply.argtypes = [P3, _D, _D]
+        L.hjo3_residual_sq.argtypes = [P3, _D, _D]
+        L.hjo3_residual_sq.restype = C.c_double
+        L.hjo3_jacobi_sweep.argtypes = [P3, _D, _D, _D]
+        L.hjo3_hier_cycle.argtypes = [P3, _D, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.hjo3_solve.argtypes = [P3, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                 C.c_long, _D, C.c_long, C.POINTER(C.c_int)]
+        L.hjo3_solve.restype = C.c_long
+        L.hjo3_run_fixed.argtypes = [P3, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_long]
         L.hjo_paper_smem_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
         L.hjo_paper_smem_bytes.restype = C.c_long
         _lib = L
@@ -107,6 +125,13 @@ class Problem:
     def __init__(self, st):
         self.st = st
         self.sigma = None if st.sigma is None else _grid(st.sigma)
+        if st.dim == 3:
+            if getattr(st, "coef", None) is not None:
+                raise ValueError("the 3D oracle takes constant neighbour coefficients")
+            self.c = _Problem3(st.nx, st.ny, st.nz, st.cW, st.cE, st.cS, st.cN, st.cB, st.cT, st.cD,
+                               float(st.sigma_const), None if self.sigma is None else self.sigma.ctypes.data)
+            self.shape = (st.nz + 2, st.ny + 2, st.nx + 2)
+            return
         coef = getattr(st, "coef", None)
         self.coef = None if coef is None else _grid(coef)   # planes W, E[, S, N] x rows x (nx + 2)
         self.c = _Problem(st.dim, st.nx, st.ny, st.cW, st.cE, st.cS, st.cN, st.cD,
@@ -124,31 +149,41 @@ def _prob(st) -> Problem:
     return st if isinstance(st, Problem) else Problem(st)
 
 
+def _is3(p) -> bool:
+    return p.st.dim == 3
+
+
 def apply(st, u):
     p = _prob(st)
     u = _grid(u)
     out = np.zeros(p.shape)
-    lib().hjo_apply(p.ref, _dp(u), _dp(out))
+    (lib().hjo3_apply if _is3(p) else lib().hjo_apply)(p.ref, _dp(u), _dp(out))
     return out
 
 
 def residual(st, f, u) -> float:
-    """||f - A u||_2 over interior points (binary64, row-major summation)."""
+    """||f - A u||_2 over interior points (binary64, x-fastest summation)."""
     p = _prob(st)
-    return float(np.sqrt(lib().hjo_residual_sq(p.ref, _dp(_grid(f)), _dp(_grid(u)))))
+    fn = lib().hjo3_residual_sq if _is3(p) else lib().hjo_residual_sq
+    return float(np.sqrt(fn(p.ref, _dp(_grid(f)), _dp(_grid(u)))))
 
 
 def jacobi_sweep(st, f, u):
     p = _prob(st)
     out = np.zeros(p.shape)
-    lib().hjo_jacobi_sweep(p.ref, _dp(_grid(f)), _dp(_grid(u)), _dp(out))
+    fn = lib().hjo3_jacobi_sweep if _is3(p) else lib().hjo_jacobi_sweep
+    fn(p.ref, _dp(_grid(f)), _dp(_grid(u)), _dp(out))
     return out
 
 
-def hier_cycle(st, f, u, tx, ty, k):
+def hier_cycle(st, f, u, tx, ty, k, tz=1):
+    """One hierarchical cycle on tx (x ty (x tz)) subdomains."""
     p = _prob(st)
     out = np.zeros(p.shape)
-    lib().hjo_hier_cycle(p.ref, _dp(_grid(f)), _dp(_grid(u)), _dp(out), tx, ty, k)
+    if _is3(p):
+        lib().hjo3_hier_cycle(p.ref, _dp(_grid(f)), _dp(_grid(u)), _dp(out), tx, ty, tz, k)
+    else:
+        lib().hjo_hier_cycle(p.ref, _dp(_grid(f)), _dp(_grid(u)), _dp(out), tx, ty, k)
     return out
 
 
@@ -161,12 +196,15 @@ def hier_cycle_ovl(st, f, u, tx, ty, k, ox, oy=0):
     return out
 
 
-def run_fixed(st, f, u0, ncycles, tx=32, ty=32, k=1, classic=False, overlap=(0, 0)):
+def run_fixed(st, f, u0, ncycles, tx=32, ty=32, k=1, classic=False, overlap=(0, 0), tz=1):
     """u after exactly ncycles hierarchical cycles (or classic sweeps);
-    overlap = (ox, oy) points shared by neighbouring subdomains."""
+    overlap = (ox, oy) points shared by neighbouring subdomains; tz: the
+    subdomain depth of 3D problems."""
     p = _prob(st)
     u = _grid(u0).copy()
-    if overlap != (0, 0) and not classic:
+    if _is3(p):
+        lib().hjo3_run_fixed(p.ref, _dp(_grid(f)), _dp(u), int(classic), tx, ty, tz, k, int(ncycles))
+    elif overlap != (0, 0) and not classic:
         lib().hjo_run_fixed_ovl(p.ref, _dp(_grid(f)), _dp(u), tx, ty, k, int(overlap[0]), int(overlap[1]),
                                 int(ncycles))
     else:
@@ -174,13 +212,16 @@ def run_fixed(st, f, u0, ncycles, tx=32, ty=32, k=1, classic=False, overlap=(0, 
     return u
 
 
-def solve(st, f, u0, tol, max_cycles, tx=32, ty=32, k=1, classic=False, hist_cap=0, overlap=(0, 0)):
+def solve(st, f, u0, tol, max_cycles, tx=32, ty=32, k=1, classic=False, hist_cap=0, overlap=(0, 0), tz=1):
     """Returns (u_c, c, status, hist): c = first cycle with ||r_c|| <= tol ||r_0||."""
     p = _prob(st)
     u = _grid(u0).copy()
     hist = np.zeros(max(hist_cap, 1))
     status = C.c_int(0)
-    if overlap != (0, 0) and not classic:
+    if _is3(p):
+        c = lib().hjo3_solve(p.ref, _dp(_grid(f)), _dp(u), int(classic), tx, ty, tz, k, float(tol),
+                             int(max_cycles), _dp(hist), int(hist_cap), C.byref(status))
+    elif overlap != (0, 0) and not classic:
         c = lib().hjo_solve_ovl(p.ref, _dp(_grid(f)), _dp(u), int(classic), tx, ty, k, int(overlap[0]),
                                 int(overlap[1]), float(tol), int(max_cycles), _dp(hist), int(hist_cap),
                                 C.byref(status))

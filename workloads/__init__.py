@@ -94,10 +94,22 @@ class Stencil:
     # each grid-shaped) replacing cW..cN: the general tridiagonal a_i, c_i of
     # Section 3 and its 2D analogue; None = constant coefficients
     coef: np.ndarray | None = None
+    # 3D seven-point extension (dim = 3): nz interior planes, bottom (z - 1)
+    # and top (z + 1) neighbour coefficients
+    nz: int = 1
+    cB: float = 0.0
+    cT: float = 0.0
 
     @property
     def rows(self) -> int:
-        return self.ny + 2 if self.dim == 2 else self.ny
+        return self.ny + 2 if self.dim >= 2 else self.ny
+
+    @property
+    def shape(self) -> tuple:
+        """Shape of a grid array: (rows, nx + 2), or (nz + 2, ny + 2, nx + 2) in 3D."""
+        if self.dim == 3:
+            return (self.nz + 2, self.ny + 2, self.nx + 2)
+        return (self.rows, self.nx + 2)
 
 
 def poisson_stencil(dim: int, nx: int, ny: int = 1, sigma=None, sigma_const: float = 0.0) -> Stencil:
@@ -114,11 +126,22 @@ def poisson_stencil(dim: int, nx: int, ny: int = 1, sigma=None, sigma_const: flo
     return Stencil(2, nx, ny, -ix2, -ix2, -iy2, -iy2, 2.0 * ix2 + 2.0 * iy2, sigma, sigma_const)
 
 
+def poisson_stencil3d(nx: int, ny: int, nz: int, sigma=None, sigma_const: float = 0.0) -> Stencil:
+    """Seven-point -Lap u on the unit cube (h = 1/(n+1) per axis), the 2D
+    stencil of Eq. 2d-poisson extended by the z pair; diagonal 2/hx^2 +
+    2/hy^2 + 2/hz^2."""
+    ix2, iy2, iz2 = (nx + 1.0) ** 2, (ny + 1.0) ** 2, (nz + 1.0) ** 2
+    return Stencil(3, nx, ny, -ix2, -ix2, -iy2, -iy2, 2.0 * (ix2 + iy2 + iz2), sigma, sigma_const,
+                   None, nz, -iz2, -iz2)
+
+
 def zeros_grid(st: Stencil, dtype=np.float64) -> np.ndarray:
-    return np.zeros((st.rows, st.nx + 2), dtype=dtype)
+    return np.zeros(st.shape, dtype=dtype)
 
 
 def interior(a: np.ndarray, dim: int) -> np.ndarray:
+    if dim == 3:
+        return a[1:-1, 1:-1, 1:-1]
     return a[1:-1, 1:-1] if dim == 2 else a[:, 1:-1]
 
 
@@ -239,6 +262,42 @@ def variable_coef_problem(dim: int, nx: int, ny: int, seed: int, contrast: float
     interior(f, dim)[...] = uniform(seed, interior(f, dim).size, -1.0, 1.0).reshape(interior(f, dim).shape)
     u0 = uniform(seed + 7, rows * (nx + 2), -0.5, 0.5).reshape(rows, nx + 2)
     return Problem(st, f, u0, {"seed": seed, "contrast": contrast})
+
+
+def poisson3d_uniform(nx: int, ny: int | None = None, nz: int | None = None, seed: int = 1,
+                      sigma_const: float = 0.0) -> Problem:
+    """3D -Lap u + s u = f on the unit cube, zero Dirichlet, f ~ U[-1,1], u0 = 0."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    st = poisson_stencil3d(nx, ny, nz, sigma_const=sigma_const)
+    f = zeros_grid(st)
+    f[1:-1, 1:-1, 1:-1] = uniform(seed, nx * ny * nz, -1.0, 1.0).reshape(nz, ny, nx)
+    return Problem(st, f, zeros_grid(st), {"seed": seed})
+
+
+def random_bc_problem3d(nx: int, ny: int, nz: int, seed: int, sigma_kind: str = "none",
+                        asym: bool = False) -> Problem:
+    """Small general 3D test problem: random RHS, random Dirichlet shell and
+    initial guess, optional constant or per-point screening and an optional
+    non-symmetric (diagonally dominant) stencil."""
+    st = poisson_stencil3d(nx, ny, nz)
+    if asym:
+        st.cW *= 1.3
+        st.cE *= 0.7
+        st.cS *= 0.8
+        st.cN *= 1.2
+        st.cB *= 1.1
+        st.cT *= 0.9
+    if sigma_kind == "field":
+        st.sigma = zeros_grid(st)
+        st.sigma[1:-1, 1:-1, 1:-1] = uniform(seed + 101, nx * ny * nz, 0.0, 50.0).reshape(nz, ny, nx)
+    elif sigma_kind == "const":
+        st.sigma_const = 37.5
+    f = zeros_grid(st)
+    f[1:-1, 1:-1, 1:-1] = uniform(seed, nx * ny * nz, -1.0, 1.0).reshape(nz, ny, nx)
+    size = int(np.prod(st.shape))
+    u0 = uniform(seed + 7, size, -0.5, 0.5).reshape(st.shape)
+    return Problem(st, f, u0, {"seed": seed})
 
 
 BATCH_SIDES = tuple(range(64, 513, 32))   # {64, 96, ..., 512}: 15 values
