@@ -391,6 +391,68 @@ def variable_coefficients(torch, hj, W, n=4096, hbm_peak=None):
     return out
 
 
+def three_d(torch, hj, W, n=512, hbm_peak=None):
+    """3D seven-point extension: cycle rate and HBM roofline of the
+    warp-per-subdomain kernel and of the classic sweep at n^3 (binary32: 12 B
+    per point and cycle, u in/out and f; binary64 is bound by the FP64 pipe,
+    13 separately rounded operations per update), and time to a 1e-5
+    residual reduction at 128^3 (binary32), hierarchical vs classic."""
+    out = {}
+    st = W.poisson_stencil3d(n, n, n)
+    runs = [("f32", (16, 8, 4), 1), ("f32", (16, 8, 4), 4), ("f32", (16, 8, 8), 4), ("f32", None, 1),
+            ("f64", (16, 4, 8), 1), ("f64", (16, 4, 8), 4)]
+    for prec, tile, k in runs:
+        dt = torch.float32 if prec == "f32" else torch.float64
+        bpp = 12 if prec == "f32" else 24
+        f = hj.alloc_grid(3, n, n, dt, nz=n, fill=1.0)
+        t = []
+        for ncyc in (4, 24):
+            kw = dict(method="classic") if tile is None else dict(tile_x=tile[0], tile_y=tile[1], tile_z=tile[2], k=k)
+            s = hj.Solver(st, precision=prec, fixed_cycles=ncyc, **kw)
+            u = hj.alloc_grid(3, n, n, dt, nz=n)
+            s.solve(f, u)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.solve(f, u)
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+            s.close()
+            del u
+        us = (t[1] - t[0]) / 20 * 1e3
+        gbs = bpp * n ** 3 / (us / 1e6) / 1e9
+        row = {"us_per_cycle": us, "glups": n ** 3 / (us / 1e6) / 1e9, "hbm_gbs": gbs,
+               "hbm_frac": gbs / hbm_peak if hbm_peak else None}
+        if prec == "f64":
+            row["fp64_frac"] = 13.0 * k * n ** 3 / (us / 1e6) / 0.625e12
+        name = "classic" if tile is None else f"{tile[0]}x{tile[1]}x{tile[2]}_k{k}"
+        out[f"{prec}_{name}"] = row
+        del f
+    q = W.poisson3d_uniform(128, seed=4)
+    f = hj.grid_from(q.f, 3, torch.float32)
+    ttr = {}
+    for name, kw in [("hier_16x8x8_k8", dict(tile_x=16, tile_y=8, tile_z=8, k=8, check_every=64)),
+                     ("hier_16x8x8_k16", dict(tile_x=16, tile_y=8, tile_z=8, k=16, check_every=64)),
+                     ("hier_16x8x4_k8", dict(tile_x=16, tile_y=8, tile_z=4, k=8, check_every=64)),
+                     ("classic", dict(method="classic", check_every=1024))]:
+        s = hj.Solver(q.st, precision="f32", tol=1e-5, max_cycles=10_000_000, **kw)
+        u = hj.grid_from(q.u0, 3, torch.float32)
+        s.solve(f, u.clone())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = s.solve(f, u)
+        torch.cuda.synchronize()
+        ttr[name] = {"seconds": time.perf_counter() - t0, "cycles": r["cycles"], "status": r["status"]}
+        s.close()
+    for name in list(ttr):
+        if name != "classic":
+            ttr[f"speedup_{name}_vs_classic"] = ttr["classic"]["seconds"] / ttr[name]["seconds"]
+    out["time_to_1e-5_128_f32"] = ttr
+    return out
+
+
 def paper_replicas(torch, hj, W, precision="f64"):
     """Context: the paper's timing problems (Sections 3.5 and 4.2), residual
     reduced by 1e-4 from x0 = 1 with b = 1: best classic vs hierarchical
@@ -634,6 +696,7 @@ def main():
         extras["cfg5_differentiation_1024"] = time_differentiation(torch, hj, W)
         extras["inner_sweep_roofline_k16"] = inner_roofline(torch, hj, W, n)
         extras["variable_coefficients_4096"] = variable_coefficients(torch, hj, W, hbm_peak=hbm_peak)
+        extras["three_d_512"] = three_d(torch, hj, W, hbm_peak=hbm_peak)
     if args.paper_replicas and rank == 0:
         extras["paper_replicas"] = paper_replicas(torch, hj, W)
         extras["paper_replicas_f32"] = paper_replicas(torch, hj, W, "f32")

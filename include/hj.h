@@ -107,7 +107,7 @@ enum hj_precision { HJ_PREC_F64 = 0, HJ_PREC_F32 = 1, HJ_PREC_F32_IR = 2, HJ_PRE
 enum hj_method { HJ_METHOD_HIER = 0, HJ_METHOD_CLASSIC = 1 };
 
 typedef struct {
-    int dim;              /* 1 or 2                                              */
+    int dim;              /* 1, 2 or 3 (3: the seven-point extension, see nz)    */
     int nx, ny;           /* interior points; 1D: ny = number of independent rows */
     long long ld;         /* row pitch of every grid array, in elements          */
     double cW, cE, cS, cN, cD;  /* stencil (cS, cN ignored in 1D)                */
@@ -123,6 +123,18 @@ typedef struct {
                              one-thread-per-point kernels under CUDA graphs;
                              HJ_PREC_F64 and HJ_PREC_F32 only, no overlap, no
                              adjoint, no batched solves (HJ_ERR_UNSUPPORTED)  */
+    int nz;               /* dim = 3: interior planes (1 <= nz <= 65535).  A 3D
+                             grid array is (nz + 2) planes of (ny + 2) rows of
+                             ld elements (x fastest, then y, then z) with a
+                             one-point ghost shell of Dirichlet data; the
+                             operator is Section 4's five-point stencil plus
+                             cB u_{z-1} + cT u_{z+1} (an extension: the paper
+                             stops at 2D).  3D takes constant coefficients and
+                             sigma_const only (sigma, coef NULL), HJ_PREC_F64
+                             or HJ_PREC_F32, hierarchical or classic, on CUDA
+                             graphs; no refinement, overlap, in-place, adjoint,
+                             autotune or batched solves (HJ_ERR_UNSUPPORTED)  */
+    double cB, cT;        /* dim = 3: bottom (z - 1) and top (z + 1) coefficients */
 } hj_desc;
 
 typedef struct {
@@ -192,6 +204,10 @@ typedef struct {
                              initial and the returned array (which may be one
                              cycle past the checked one).  0 (default): u_c
                              and u_{c+1} in separate arrays, deterministic   */
+    int tile_z;           /* 3D: subdomain depth; 0 = the default 3D shape of
+                             the precision (binary32 16 x 8 x 8, binary64
+                             16 x 4 x 8), which replaces tile_x and tile_y.
+                             Built shapes are listed by hj_tile_shapes3d()    */
 } hj_params;
 
 typedef struct {
@@ -213,13 +229,15 @@ typedef struct {
     int pipeline_stages;      /* copy stages of the pipelined kernel if it runs, else 0 */
     int ctas_per_sm;          /* its CTAs-per-SM cap (0 = as many as fit)         */
     int overlap_x, overlap_y; /* overlapping points used (Sections 3.4, 4.3)      */
+    int tile_z;               /* 3D: subdomain depth used (1 otherwise)           */
 } hj_stats;
 
 /* Fill p with defaults: hierarchical, 32 x 32 tiles, k = 16, HJ_PREC_F64,
  * check_every = 64, max_cycles = 10^7, tol = 1e-6, fixed_cycles = 0,
  * inner_tol = 1e-4, inner_max_cycles = 10^6, max_outer = 60, persistent = -1,
  * autotune = 0, pipeline = -1, tile_threads = 0, pipeline_stages = 0,
- * inner_stall = 32, ctas_per_sm = 0, overlap_x = overlap_y = 0, in_place = 0. */
+ * inner_stall = 32, ctas_per_sm = 0, overlap_x = overlap_y = 0, in_place = 0,
+ * tile_z = 0. */
 HJ_API void hj_default_params(hj_params *p);
 
 /* Create a solver for one problem shape.  Validates the descriptor and
@@ -330,6 +348,11 @@ HJ_API int hj_tile_variants(int dim, int precision, int *txt, int cap);
 /* Tile shapes built for (dim, precision): writes up to cap (tile_x, tile_y)
  * pairs into xy[2*i], xy[2*i+1] and returns how many exist. */
 HJ_API int hj_tile_shapes(int dim, int precision, int *xy, int cap);
+
+/* 3D subdomain shapes built for a precision (HJ_PREC_F64 or HJ_PREC_F32):
+ * writes up to cap (tile_x, tile_y, tile_z) triples into xyz[3*i .. 3*i+2]
+ * and returns how many exist (0 for other precisions). */
+HJ_API int hj_tile_shapes3d(int precision, int *xyz, int cap);
 
 #ifdef __cplusplus
 }

@@ -40,7 +40,8 @@ class hj_desc(C.Structure):
     _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("ld", C.c_longlong),
                 ("cW", C.c_double), ("cE", C.c_double), ("cS", C.c_double), ("cN", C.c_double),
                 ("cD", C.c_double), ("sigma_const", C.c_double), ("sigma", C.c_void_p),
-                ("dtype", C.c_int), ("coef", C.c_void_p)]
+                ("dtype", C.c_int), ("coef", C.c_void_p), ("nz", C.c_int), ("cB", C.c_double),
+                ("cT", C.c_double)]
 
 
 class hj_params(C.Structure):
@@ -50,7 +51,7 @@ class hj_params(C.Structure):
                 ("inner_max_cycles", C.c_longlong), ("max_outer", C.c_int), ("persistent", C.c_int),
                 ("autotune", C.c_int), ("pipeline", C.c_int), ("tile_threads", C.c_int),
                 ("pipeline_stages", C.c_int), ("inner_stall", C.c_int), ("ctas_per_sm", C.c_int),
-                ("overlap_x", C.c_int), ("overlap_y", C.c_int), ("in_place", C.c_int)]
+                ("overlap_x", C.c_int), ("overlap_y", C.c_int), ("in_place", C.c_int), ("tile_z", C.c_int)]
 
 
 class hj_stats(C.Structure):
@@ -61,7 +62,7 @@ class hj_stats(C.Structure):
                 ("history_len", C.c_longlong), ("wall_ms", C.c_double), ("tile_x", C.c_int),
                 ("tile_y", C.c_int), ("k", C.c_int), ("tile_threads", C.c_int), ("persistent", C.c_int),
                 ("pipeline_stages", C.c_int), ("ctas_per_sm", C.c_int), ("overlap_x", C.c_int),
-                ("overlap_y", C.c_int)]
+                ("overlap_y", C.c_int), ("tile_z", C.c_int)]
 
 
 class HJError(RuntimeError):
@@ -109,6 +110,7 @@ def lib():
         L.hj_last_error.argtypes = []
         L.hj_last_error.restype = C.c_char_p
         L.hj_tile_shapes.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]
+        L.hj_tile_shapes3d.argtypes = [C.c_int, C.POINTER(C.c_int), C.c_int]
         L.hj_tile_variants.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]
         L.hj_autotune.argtypes = [C.POINTER(hj_desc), C.POINTER(hj_params), C.POINTER(C.c_double)]
         L.hj_cycles_noalloc.argtypes = [C.POINTER(hj_desc), C.POINTER(hj_params), C.c_void_p, C.c_void_p,
@@ -224,6 +226,13 @@ def hj_tile_shapes(dim: int, precision: int):
     return [(buf[2 * i], buf[2 * i + 1]) for i in range(n)]
 
 
+def hj_tile_shapes3d(precision: int):
+    n = lib().hj_tile_shapes3d(precision, None, 0)
+    buf = (C.c_int * (3 * n))()
+    lib().hj_tile_shapes3d(precision, buf, n)
+    return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(n)]
+
+
 # ---------------------------------------------------------------------------
 # torch-tensor convenience layer (memory and streams only)
 # ---------------------------------------------------------------------------
@@ -233,24 +242,30 @@ def padded_ld(nx: int, dtype) -> int:
     return ((nx + 2 + 31) // 32) * 32
 
 
-def alloc_grid(dim: int, nx: int, ny: int, dtype, device="cuda", fill: float = 0.0):
-    """A (rows, ld) device tensor meeting the ABI's alignment rules; use
-    ``t[:, :nx+2]`` as the logical grid."""
+def alloc_grid(dim: int, nx: int, ny: int, dtype, device="cuda", fill: float = 0.0, nz: int = 1):
+    """A (rows, ld) device tensor meeting the ABI's alignment rules, or
+    (nz + 2, ny + 2, ld) in 3D; use ``t[..., :nx+2]`` as the logical grid."""
     import torch
+    if dim == 3:
+        return torch.full((nz + 2, ny + 2, padded_ld(nx, dtype)), fill, dtype=dtype, device=device)
     rows = ny + 2 if dim == 2 else ny
     t = torch.full((rows, padded_ld(nx, dtype)), fill, dtype=dtype, device=device)
     return t
 
 
 def grid_from(a, dim: int, dtype=None, device="cuda"):
-    """Copy a logical (rows, nx+2) array (numpy or torch) into a padded device grid."""
+    """Copy a logical (rows, nx+2) (3D: (nz+2, ny+2, nx+2)) array (numpy or
+    torch) into a padded device grid."""
     import torch
     src = torch.as_tensor(a)
     dtype = dtype or src.dtype
-    nx = src.shape[1] - 2
-    ny = src.shape[0] - 2 if dim == 2 else src.shape[0]
-    t = alloc_grid(dim, nx, ny, dtype, device)
-    t[:, :nx + 2].copy_(src.to(dtype))
+    nx = src.shape[-1] - 2
+    if dim == 3:
+        t = alloc_grid(3, nx, src.shape[1] - 2, dtype, device, nz=src.shape[0] - 2)
+    else:
+        ny = src.shape[0] - 2 if dim == 2 else src.shape[0]
+        t = alloc_grid(dim, nx, ny, dtype, device)
+    t[..., :nx + 2].copy_(src.to(dtype))
     return t
 
 
@@ -261,12 +276,12 @@ def _stream_handle(stream) -> int:
 
 
 def make_desc(dim, nx, ny, ld, cW, cE, cS=0.0, cN=0.0, cD=0.0, sigma_const=0.0, sigma=None,
-              dtype=HJ_F64, coef=None) -> hj_desc:
+              dtype=HJ_F64, coef=None, nz=1, cB=0.0, cT=0.0) -> hj_desc:
     """coef: optional device tensor (planes, rows, ld) float64 of per-point
-    neighbour coefficients W, E[, S, N]."""
+    neighbour coefficients W, E[, S, N]; nz, cB, cT: the 3D extension."""
     return hj_desc(dim, nx, ny, ld, cW, cE, cS, cN, cD, sigma_const,
                    None if sigma is None else int(sigma.data_ptr()), dtype,
-                   None if coef is None else int(coef.data_ptr()))
+                   None if coef is None else int(coef.data_ptr()), nz, cB, cT)
 
 
 def make_params(**kw) -> hj_params:
@@ -293,12 +308,13 @@ class Solver:
         import torch
         self.params = params if params is not None else make_params(**kw)
         self.dim, self.nx, self.ny = stencil.dim, stencil.nx, stencil.ny
+        self.nz = getattr(stencil, "nz", 1) if self.dim == 3 else 1
         if dtype is None:
             dtype = torch.float32 if self.params.precision == HJ_PREC_F32 else torch.float64
         self.dtype = dtype
         self.ld = padded_ld(self.nx, dtype)
         self.sigma = sigma
-        if sigma is not None and sigma.shape[1] != self.ld:
+        if sigma is not None and sigma.shape[-1] != self.ld:
             raise ValueError("sigma must be a padded grid with the solver's ld")
         self.coef = coef
         if coef is not None and (coef.dim() != 3 or coef.shape[2] != self.ld or coef.dtype != torch.float64
@@ -306,15 +322,18 @@ class Solver:
             raise ValueError("coef must be a contiguous float64 (planes, rows, ld) tensor with the solver's ld")
         self.desc = make_desc(self.dim, self.nx, self.ny, self.ld, stencil.cW, stencil.cE, stencil.cS,
                               stencil.cN, stencil.cD, getattr(stencil, "sigma_const", 0.0), sigma,
-                              HJ_F64 if dtype == torch.float64 else HJ_F32, coef)
+                              HJ_F64 if dtype == torch.float64 else HJ_F32, coef, self.nz,
+                              getattr(stencil, "cB", 0.0), getattr(stencil, "cT", 0.0))
         self.h = hj_create(self.desc, self.params)
 
     def _check(self, t, name):
-        if t.dtype != self.dtype or t.shape[1] != self.ld or not t.is_contiguous():
+        if t.dtype != self.dtype or t.shape[-1] != self.ld or not t.is_contiguous():
             raise ValueError(f"{name} must be a contiguous padded grid of {self.dtype} with ld={self.ld}")
+        if self.dim == 3 and tuple(t.shape[:2]) != (self.nz + 2, self.ny + 2):
+            raise ValueError(f"{name} must have shape (nz + 2, ny + 2, ld)")
 
     def grid(self, fill=0.0):
-        return alloc_grid(self.dim, self.nx, self.ny, self.dtype, fill=fill)
+        return alloc_grid(self.dim, self.nx, self.ny, self.dtype, fill=fill, nz=self.nz)
 
     def solve(self, f, u, stream=None, history: int = 0, check=True):
         """Solve in place (u: initial guess with Dirichlet ghost ring -> solution).

@@ -172,8 +172,8 @@ CycArgs base_args(const hj_handle *h, bool transpose) {
     a.k = h->p.k;
     a.cW = transpose ? h->d.cE : h->d.cW;
     a.cE = transpose ? h->d.cW : h->d.cE;
-    a.cS = h->d.dim == 2 ? (transpose ? h->d.cN : h->d.cS) : 0.0;
-    a.cN = h->d.dim == 2 ? (transpose ? h->d.cS : h->d.cN) : 0.0;
+    a.cS = h->d.dim >= 2 ? (transpose ? h->d.cN : h->d.cS) : 0.0;
+    a.cN = h->d.dim >= 2 ? (transpose ? h->d.cS : h->d.cN) : 0.0;
     a.dconst = h->d.cD + h->d.sigma_const;
     a.invd = 1.0 / a.dconst;
     a.fW = (float)a.cW; a.fE = (float)a.cE; a.fS = (float)a.cS; a.fN = (float)a.cN;
@@ -189,6 +189,14 @@ CycArgs base_args(const hj_handle *h, bool transpose) {
         a.vc = h->fam_outer == FAM_F64 ? (const void *)h->d.coef : (const void *)h->vcf;
         a.vsig = h->d.sigma;
         a.vcs = (long long)h->rows * h->d.ld;
+    }
+    if (h->d.dim == 3) {
+        a.nz = h->d.nz;
+        a.ps = (long long)(h->d.ny + 2) * h->d.ld;
+        a.cB = transpose ? h->d.cT : h->d.cB;
+        a.cT = transpose ? h->d.cB : h->d.cT;
+        a.fB = (float)a.cB; a.fT = (float)a.cT;
+        a.gB = (float)(-a.cB * a.invd); a.gT = (float)(-a.cT * a.invd);
     }
     return a;
 }
@@ -321,6 +329,25 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
     pl->period = 2;
     pl->deferred = false;
     const int nx = h->d.nx, ny = h->d.ny;
+    if (h->d.dim == 3) {
+        // seven-point extension: warp-per-subdomain register kernel, or the
+        // classic thread-per-point sweep
+        if (classic) {
+            pl->fn = classic3d_kernel_of(fam, res);
+            pl->grid = dim3((nx + 31) / 32, (ny + 7) / 8, h->d.nz);
+            pl->block = dim3(32, 8);
+        } else {
+            const Tile3Info *t3 = h->k3;
+            const long long nsub = (long long)((nx + t3->tx - 1) / t3->tx) * ((ny + t3->ty - 1) / t3->ty) *
+                                   ((h->d.nz + t3->tz - 1) / t3->tz);
+            pl->fn = t3->fn[res];
+            pl->grid = dim3((unsigned)((nsub + t3->nw - 1) / t3->nw));
+            pl->block = dim3(t3->threads);
+        }
+        pl->smem = 0;
+        pl->ppc = false;
+        return HJ_OK;
+    }
     if (h->d.coef) {
         // variable coefficients: one thread per point; classic Jacobi is the
         // same kernel with one subiteration (a k = 1 cycle is a classic sweep)
@@ -460,7 +487,8 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, 
         base.red.stall_rtol = 1e-3;
     }
     // binary32 kernels with a constant diagonal accumulate (u' - u)^2; r = d (u' - u)
-    if (fam != FAM_F64 && !sig) base.red.scale = base.dconst * base.dconst;
+    // (the variable-coefficient kernels scale by their own d_p)
+    if (fam != FAM_F64 && !sig && !h->d.coef) base.red.scale = base.dconst * base.dconst;
     if (max_cycles <= 0) {
         // no cycle may run: the residual of u_0 is all there is
         ro->c = 0;
@@ -564,7 +592,7 @@ int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int
             const CycArgs &base, void *b0, void *b1, ThirdBuffer third, double tol, long long max_cycles,
             long long fixed, cudaStream_t s, RunOut *ro, double *hist_out, long long hist_cap, long long *hist_len,
             int *used_persistent) {
-    if (h->d.coef) {   // variable coefficients: graph-captured launches only
+    if (h->d.coef || h->d.dim == 3) {   // variable coefficients and 3D: graph-captured launches only
         if (used_persistent) *used_persistent = 0;
         return run_cycles(h, ki, pi, fam, classic, sig, base, b0, b1, third, tol, max_cycles, fixed, s, ro,
                           hist_out, hist_cap, hist_len);
@@ -638,9 +666,13 @@ int iterate(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, int
 int residual_of(hj_handle *h, const void *f, const void *u, bool transpose, double *rr, double *ff, cudaStream_t s) {
     const CycArgs a = base_args(h, transpose);
     const RedArgs red = red_args(h, RED_STORE, 0.0, 0);
-    CKR(launch_residual_ex(h->d.dim, h->d.dtype == HJ_F64, f, u, h->d.sigma, h->d.ld, h->d.ld, h->d.nx, h->d.ny,
-                           a.cW, a.cE, a.cS, a.cN, a.dconst, 1, nullptr, red, s, h->d.coef,
-                           (long long)h->rows * h->d.ld));
+    if (h->d.dim == 3)
+        CKR(launch_residual3d(h->d.dtype == HJ_F64, f, u, h->d.ld, a.ps, h->d.nx, h->d.ny, h->d.nz, a.cW, a.cE,
+                              a.cS, a.cN, a.cB, a.cT, a.dconst, 1, red, s));
+    else
+        CKR(launch_residual_ex(h->d.dim, h->d.dtype == HJ_F64, f, u, h->d.sigma, h->d.ld, h->d.ld, h->d.nx,
+                               h->d.ny, a.cW, a.cE, a.cS, a.cN, a.dconst, 1, nullptr, red, s, h->d.coef,
+                               (long long)h->rows * h->d.ld));
     CKR(cudaMemcpyAsync(h->h_rstore, h->rstore, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CKR(cudaEventRecord(h->ev, s));
     CKR(cudaEventSynchronize(h->ev));
@@ -802,7 +834,9 @@ void fill_stats_config(const hj_handle *h, hj_stats *st, double t0) {
     st->k = h->p.k;
     const TileKernelInfo *tk = h->ir ? h->k_inner : h->k_outer;
     st->tile_threads = tk ? tk->threads / tk->tiles_per_cta
-                          : h->d.coef ? h->p.tile_x * (h->d.dim == 2 ? h->p.tile_y : 1) : 0;
+                          : h->d.coef ? h->p.tile_x * (h->d.dim == 2 ? h->p.tile_y : 1) : h->k3 ? 32 : 0;
+    st->tile_y = h->d.dim >= 2 ? h->p.tile_y : 1;
+    st->tile_z = h->d.dim == 3 ? h->p.tile_z : 1;
     const PpcKernelInfo *pk = h->ir ? h->p_inner : h->p_outer;
     const bool ppc = want_ppc(h, pk, h->p.method == HJ_METHOD_CLASSIC);
     st->pipeline_stages = ppc ? pk->stages : 0;
@@ -891,6 +925,18 @@ int hj_tile_shapes(int dim, int precision, int *xy, int cap) {
     return m;
 }
 
+int hj_tile_shapes3d(int precision, int *xyz, int cap) {
+    if (precision != HJ_PREC_F64 && precision != HJ_PREC_F32) return 0;
+    int n = 0;
+    const Tile3Info *k = precision == HJ_PREC_F64 ? tiles3d_f64(&n) : tiles3d_f32(&n);
+    for (int i = 0; i < n && xyz && i < cap; ++i) {
+        xyz[3 * i] = k[i].tx;
+        xyz[3 * i + 1] = k[i].ty;
+        xyz[3 * i + 2] = k[i].tz;
+    }
+    return n;
+}
+
 void hj_destroy(hj_handle *h) {
     if (!h) return;
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
@@ -916,14 +962,14 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     if (params) p = *params;
     else hj_default_params(&p);
     const hj_desc &d = *desc;
-    if (d.dim != 1 && d.dim != 2) return seterr(HJ_ERR_INVALID_ARG, "dim must be 1 or 2 (got %d)", d.dim);
+    if (d.dim < 1 || d.dim > 3) return seterr(HJ_ERR_INVALID_ARG, "dim must be 1, 2 or 3 (got %d)", d.dim);
     if (d.nx < 1 || d.ny < 1) return seterr(HJ_ERR_INVALID_ARG, "nx, ny must be >= 1 (got %d, %d)", d.nx, d.ny);
     if (d.dtype != HJ_F64 && d.dtype != HJ_F32) return seterr(HJ_ERR_INVALID_ARG, "dtype must be HJ_F64 or HJ_F32");
     const size_t esz = d.dtype == HJ_F64 ? 8 : 4;
     if (d.ld < (long long)d.nx + 2) return seterr(HJ_ERR_INVALID_ARG, "ld (%lld) < nx + 2", d.ld);
     if ((d.ld * (long long)esz) % 16) return seterr(HJ_ERR_INVALID_ARG, "ld * element size must be a multiple of 16 bytes");
     if (d.dim == 1 && d.ny > 65535) return seterr(HJ_ERR_INVALID_ARG, "1D: at most 65535 rows");
-    if (d.dim == 2 && (d.ny + 7) / 8 > 65535) return seterr(HJ_ERR_INVALID_ARG, "2D: ny must be <= 524280");
+    if (d.dim >= 2 && (d.ny + 7) / 8 > 65535) return seterr(HJ_ERR_INVALID_ARG, "2D/3D: ny must be <= 524280");
     if (p.precision < HJ_PREC_F64 || p.precision > HJ_PREC_BF16CORR_IR)
         return seterr(HJ_ERR_INVALID_ARG, "unknown precision %d", p.precision);
     const bool ir = p.precision == HJ_PREC_F32_IR || p.precision == HJ_PREC_BF16CORR_IR;
@@ -939,6 +985,38 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     if (p.inner_stall < 0) return seterr(HJ_ERR_INVALID_ARG, "inner_stall must be >= 0");
     if (p.ctas_per_sm < 0) return seterr(HJ_ERR_INVALID_ARG, "ctas_per_sm must be >= 0");
     if (p.in_place != 0 && p.in_place != 1) return seterr(HJ_ERR_INVALID_ARG, "in_place must be 0 or 1");
+    // 3D seven-point extension: constant coefficients, graphs, F64 / F32
+    const Tile3Info *k3 = nullptr;
+    if (d.dim == 3) {
+        if (d.nz < 1 || d.nz > 65535) return seterr(HJ_ERR_INVALID_ARG, "3D: nz must be in [1, 65535] (got %d)", d.nz);
+        if (d.sigma || d.coef)
+            return seterr(HJ_ERR_UNSUPPORTED, "3D takes constant coefficients and sigma_const (sigma, coef NULL)");
+        if (ir) return seterr(HJ_ERR_UNSUPPORTED, "3D: HJ_PREC_F64 or HJ_PREC_F32");
+        if (p.overlap_x > 0 || p.overlap_y > 0) return seterr(HJ_ERR_UNSUPPORTED, "3D: no overlapping subdomains");
+        if (p.in_place) return seterr(HJ_ERR_UNSUPPORTED, "3D: no in-place variant");
+        if (p.persistent == 1 || p.pipeline == 1)
+            return seterr(HJ_ERR_UNSUPPORTED, "3D runs on graphs (persistent and pipeline must not be 1)");
+        if (p.autotune != 0) return seterr(HJ_ERR_UNSUPPORTED, "3D: no autotuner");
+        const double off = fabs(d.cW) + fabs(d.cE) + fabs(d.cS) + fabs(d.cN) + fabs(d.cB) + fabs(d.cT);
+        const double dc = d.cD + d.sigma_const;
+        if (!(dc > 0.0) || dc < off)
+            return seterr(HJ_ERR_NOT_DIAG_DOMINANT, "diagonal %g < sum |off-diagonal| %g", dc, off);
+        if (p.method == HJ_METHOD_HIER) {
+            int n3 = 0;
+            const Tile3Info *t3 = p.precision == HJ_PREC_F64 ? tiles3d_f64(&n3) : tiles3d_f32(&n3);
+            if (p.tile_z == 0) k3 = &t3[0];
+            for (int i = 0; i < n3 && !k3; ++i)
+                if (t3[i].tx == p.tile_x && t3[i].ty == p.tile_y && t3[i].tz == p.tile_z) k3 = &t3[i];
+            if (!k3)
+                return seterr(HJ_ERR_UNSUPPORTED, "3D subdomain %dx%dx%d not built for this precision (hj_tile_shapes3d)",
+                              p.tile_x, p.tile_y, p.tile_z);
+            p.tile_x = k3->tx;
+            p.tile_y = k3->ty;
+            p.tile_z = k3->tz;
+        }
+    } else {
+        p.tile_z = 1;
+    }
     if (d.dim == 1) p.overlap_y = 0;
     if (p.overlap_x < 0 || p.overlap_y < 0) return seterr(HJ_ERR_INVALID_ARG, "overlaps must be >= 0");
     if (p.overlap_x > 0 || p.overlap_y > 0) {
@@ -969,7 +1047,7 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
         return seterr(HJ_ERR_INVALID_ARG, "overlap (%d, %d) must be smaller than the subdomain (%d, %d)", p.overlap_x,
                       p.overlap_y, p.tile_x, p.tile_y);
 
-    const int rows = d.dim == 2 ? d.ny + 2 : d.ny;
+    const int rows = d.dim >= 2 ? d.ny + 2 : d.ny;
     if (d.coef) {
         if (ir) return seterr(HJ_ERR_UNSUPPORTED, "variable coefficients: HJ_PREC_F64 or HJ_PREC_F32 only");
         if (p.overlap_x > 0 || p.overlap_y > 0)
@@ -981,7 +1059,8 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
             return seterr(HJ_ERR_UNSUPPORTED, "variable coefficients: one thread per point, at most 1024 per subdomain");
     }
     // diagonal dominance (Section 2.1): d_p >= |cW| + |cE| + |cS| + |cN|, d_p > 0
-    {
+    // (3D: checked above)
+    if (d.dim != 3) {
         const int r0 = d.dim == 2 ? 1 : 0, r1 = d.dim == 2 ? d.ny : d.ny - 1;
         std::vector<double> hs, hc;
         if (d.sigma) {
@@ -1023,7 +1102,8 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     h->ir = ir;
     h->rows = rows;
     h->esz = esz;
-    h->grid_elems = (size_t)rows * d.ld;
+    h->grid_elems = (size_t)rows * d.ld * (d.dim == 3 ? (size_t)d.nz + 2 : 1);
+    h->k3 = k3;
     h->grid_bytes = h->grid_elems * esz;
     h->fam_outer = p.precision == HJ_PREC_F32 ? FAM_F32 : FAM_F64;
     h->fam_inner = p.precision == HJ_PREC_BF16CORR_IR ? FAM_BF16 : FAM_F32;
@@ -1060,7 +1140,9 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
             h->p.tile_threads = best;
         }
     }
-    if (ir) {
+    if (d.dim == 3) {
+        // kernels picked above (k3) or the classic seven-point sweep
+    } else if (ir) {
         h->k_inner = find_tile(h->fam_inner, d.dim, p.tile_x, p.tile_y, p.tile_threads);
         if (!h->k_inner)
             HJ_FAIL(HJ_ERR_UNSUPPORTED, "tile %dx%d (%d threads) not built for this precision", p.tile_x, p.tile_y,
@@ -1090,6 +1172,16 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
             dim3 g, b;
             geometry(h, &k[i], false, &g, &b);
             maxb = std::max(maxb, (size_t)g.x * g.y);
+        }
+    }
+    if (d.dim == 3) {
+        const long long gx = (d.nx + 31) / 32, gy = (d.ny + 7) / 8;
+        maxb = std::max(maxb, (size_t)aux_max_blocks3(d.nx, d.ny, d.nz));
+        maxb = std::max(maxb, (size_t)(gx * gy * d.nz));   // classic sweep
+        if (k3) {
+            const long long nsub = (long long)((d.nx + k3->tx - 1) / k3->tx) * ((d.ny + k3->ty - 1) / k3->ty) *
+                                   ((d.nz + k3->tz - 1) / k3->tz);
+            maxb = std::max(maxb, (size_t)((nsub + k3->nw - 1) / k3->nw));
         }
     }
     if (d.coef) {   // thread-per-point kernel: one block per subdomain
@@ -1214,6 +1306,7 @@ int hj_solve_adjoint(hj_handle *h, const void *g, const void *u, void *dl_df, vo
                      hj_stats *stats) {
     if (!h) return seterr(HJ_ERR_INVALID_ARG, "handle is NULL");
     if (h->d.coef) return seterr(HJ_ERR_UNSUPPORTED, "the adjoint is built for constant neighbour coefficients");
+    if (h->d.dim == 3) return seterr(HJ_ERR_UNSUPPORTED, "the adjoint is built for 1D and 2D");
     CKS(check_ptr(h, g, "g"));
     CKS(check_ptr(h, u, "u"));
     CKS(check_ptr(h, dl_df, "dl_df"));

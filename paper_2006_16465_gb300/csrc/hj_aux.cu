@@ -287,6 +287,65 @@ cudaError_t launch_vc_prep(int dim, const double *coef, const double *sigma, dou
     return cudaGetLastError();
 }
 
+namespace {
+// ||f - A u||^2 (and ||f||^2) of the seven-point operator over the interior:
+// blocks of 32 x 8 points of one plane, grid-stride, deterministic reduction
+// (binary64 accumulation in a fixed order per CTA, fixed-order grid fold).
+template <typename T, bool WITH_F>
+__global__ void __launch_bounds__(256) residual3d_kernel(const T *f, const T *u, long long ld, long long ps, int nx,
+                                                        int ny, int nz, double cW, double cE, double cS, double cN,
+                                                        double cB, double cT, double dconst, RedArgs red) {
+    const int bxn = (nx + 31) / 32, byn = (ny + 7) / 8;
+    const long long nb = (long long)bxn * byn * nz;
+    double rr = 0.0, ff = 0.0;
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int i = 1 + (int)(b % bxn) * 32 + (int)threadIdx.x;
+        const int j = 1 + (int)((b / bxn) % byn) * 8 + (int)threadIdx.y;
+        const int z = 1 + (int)(b / ((long long)bxn * byn));
+        if (i > nx || j > ny) continue;
+        const long long q = (long long)z * ps + (long long)j * ld + i;
+        const double fv = (double)f[q];
+        double r = fma(-dconst, (double)u[q], fv);
+        r = fma(-cW, (double)u[q - 1], r);
+        r = fma(-cE, (double)u[q + 1], r);
+        r = fma(-cS, (double)u[q - ld], r);
+        r = fma(-cN, (double)u[q + ld], r);
+        r = fma(-cB, (double)u[q - ps], r);
+        r = fma(-cT, (double)u[q + ps], r);
+        rr += r * r;
+        ff += fv * fv;
+    }
+    if (WITH_F) {
+        const double vals[2] = {rr, ff};
+        reduce_grid<2>(red, vals);
+    } else {
+        const double vals[1] = {rr};
+        reduce_grid<1>(red, vals);
+    }
+}
+
+dim3 aux_grid3(int nx, int ny, int nz) {
+    const long long nb = (long long)((nx + 31) / 32) * ((ny + 7) / 8) * nz;
+    return dim3((unsigned)std::min<long long>(nb, 8LL * sm_count()));
+}
+}  // namespace
+
+cudaError_t launch_residual3d(int user_f64, const void *f, const void *u, long long ld, long long ps, int nx,
+                              int ny, int nz, double cW, double cE, double cS, double cN, double cB, double cT,
+                              double dconst, int with_fnorm, RedArgs red, cudaStream_t s) {
+    const dim3 g = aux_grid3(nx, ny, nz), b(32, 8);
+#define HJ_R3(T, F)                                                                                                residual3d_kernel<T, F><<<g, b, 0, s>>>((const T *)f, (const T *)u, ld, ps, nx, ny, nz, cW, cE, cS, cN, cB,                                             cT, dconst, red)
+    if (user_f64) {
+        if (with_fnorm) HJ_R3(double, true); else HJ_R3(double, false);
+    } else {
+        if (with_fnorm) HJ_R3(float, true); else HJ_R3(float, false);
+    }
+#undef HJ_R3
+    return cudaGetLastError();
+}
+
+int aux_max_blocks3(int nx, int ny, int nz) { return (int)aux_grid3(nx, ny, nz).x; }
+
 int aux_max_blocks(int dim, int nx, int ny) {
     const dim3 g = aux_grid(dim, nx, ny);
     return (int)(g.x * g.y);

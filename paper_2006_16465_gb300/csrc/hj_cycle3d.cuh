@@ -1,0 +1,237 @@
+// hj_cycle3d.cuh -- the 3D seven-point extension of the hierarchical cycle
+// (the paper's 2D stencil of Section 4 plus a bottom (z - 1) and a top (z + 1)
+// neighbour; subdomains of TX x TY x TZ points, Section 4.1 carried to 3D).
+//
+// Layout of one subdomain in a warp (no shared-memory containers):
+//   * LX lanes span x (TX = LX), LY = 32 / LX lane groups span y, and every
+//     lane holds RY consecutive rows x RZ planes of its x column in registers:
+//     TY = LY * RY, TZ = RZ;
+//   * x neighbours come from lane shuffles within the LX-lane segment, the
+//     two x-halo columns from a small shared buffer (read by the edge lanes);
+//   * y neighbours are registers of the same lane, or the neighbouring lane
+//     group's edge row (one shuffle pair per plane), or the frozen y-halo rows;
+//   * z neighbours are registers: the sweep walks the planes in order and keeps
+//     the old values of the previous plane, the z-halo planes are frozen.
+// Each warp owns one subdomain; a CTA holds NW independent warps.  Points
+// beyond the grid (ragged last subdomains) keep their staged values, so the
+// ghost value at nx + 1 (ny + 1, nz + 1) is the frozen neighbour of the last
+// interior point, as in the oracle's truncated subdomain.
+//
+// Arithmetic per point update:
+//   binary64: acc = cW*W; acc += cE*E; acc += cS*S; acc += cN*N; acc += cB*B;
+//             acc += cT*T; u' = (f - acc) * (1/d), each operation rounded once
+//             (the oracle's order, so the GPU matches it bitwise);
+//   binary32: u' = f/d + bT T + bB B + bN N + bS S + bE E + bW W (b = -c/d) as a
+//             fused chain.
+#pragma once
+
+#include "hj_cycle.cuh"
+
+namespace hj {
+
+template <typename T>
+struct Coef3 {
+    T cW, cE, cS, cN, cB, cT;   // stencil (exact path)
+    T bW, bE, bS, bN, bB, bT;   // -c/d (binary32 path)
+    T invd, dconst;
+};
+
+template <typename T>
+__device__ __forceinline__ Coef3<T> make_coef3(const CycArgs &a);
+template <>
+__device__ __forceinline__ Coef3<double> make_coef3<double>(const CycArgs &a) {
+    Coef3<double> k;
+    k.cW = a.cW; k.cE = a.cE; k.cS = a.cS; k.cN = a.cN; k.cB = a.cB; k.cT = a.cT;
+    k.bW = k.bE = k.bS = k.bN = k.bB = k.bT = 0.0;
+    k.invd = a.invd;
+    k.dconst = a.dconst;
+    return k;
+}
+template <>
+__device__ __forceinline__ Coef3<float> make_coef3<float>(const CycArgs &a) {
+    Coef3<float> k;
+    k.cW = a.fW; k.cE = a.fE; k.cS = a.fS; k.cN = a.fN; k.cB = a.fB; k.cT = a.fT;
+    k.bW = a.gW; k.bE = a.gE; k.bS = a.gS; k.bN = a.gN; k.bB = a.gB; k.bT = a.gT;
+    k.invd = a.finvd;
+    k.dconst = a.fdconst;
+    return k;
+}
+
+// One seven-point update.  g: f (binary64) or f/d (binary32).  res receives
+// f - (A u)_p of the old value (binary32: divided by d; the caller scales the
+// reduced sum by d^2).
+template <typename T, bool EXACT, bool WANT_RES>
+__device__ __forceinline__ T point_update3(const Coef3<T> &k, T g, T W, T E, T S, T N, T B, T Tp, T old,
+                                           T &res) {
+    if constexpr (EXACT) {
+        double acc = __dmul_rn(k.cW, W);
+        acc = __dadd_rn(acc, __dmul_rn(k.cE, E));
+        acc = __dadd_rn(acc, __dmul_rn(k.cS, S));
+        acc = __dadd_rn(acc, __dmul_rn(k.cN, N));
+        acc = __dadd_rn(acc, __dmul_rn(k.cB, B));
+        acc = __dadd_rn(acc, __dmul_rn(k.cT, Tp));
+        const double t = __dsub_rn(g, acc);
+        if constexpr (WANT_RES) res = (T)__dsub_rn(t, __dmul_rn(k.dconst, old));
+        return (T)__dmul_rn(t, k.invd);
+    } else {
+        T t = g;
+        t = fma(k.bT, Tp, t);
+        t = fma(k.bB, B, t);
+        t = fma(k.bN, N, t);
+        t = fma(k.bS, S, t);
+        t = fma(k.bE, E, t);
+        t = fma(k.bW, W, t);
+        if constexpr (WANT_RES) res = t - old;
+        return t;
+    }
+}
+
+template <typename S, typename T, int LX, int RY, int RZ, int NW, bool EXACT, bool RES>
+__global__ void __launch_bounds__(32 * NW) hier3d_kernel(const CycArgs a) {
+    constexpr int LY = 32 / LX, TX = LX, TY = LY * RY, TZ = RZ;
+    constexpr unsigned FULL = 0xffffffffu;
+    static_assert(LX == 8 || LX == 16 || LX == 32, "LX lanes per x segment");
+    if constexpr (RES) {
+        if (*(volatile int *)&a.red.ctl->done >= 0) return;
+    }
+    __shared__ T xhalo[NW][2][TY * TZ];   // x-halo columns (x0 - 1, x0 + TX), index y + TY * z
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lx = lane % LX, gy = lane / LX;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int nbx = (nx + TX - 1) / TX, nby = (ny + TY - 1) / TY, nbz = (nz + TZ - 1) / TZ;
+    const long long nsub = (long long)nbx * nby * nbz;
+    const long long sub = (long long)blockIdx.x * NW + warp;
+    typedef typename std::conditional<EXACT, double, T>::type Acc;
+    Acc acc = 0;
+    if (sub < nsub) {   // warp-uniform
+        const int bx = (int)(sub % nbx);
+        const int by = (int)((sub / nbx) % nby);
+        const int bz = (int)(sub / ((long long)nbx * nby));
+        const int x0 = 1 + bx * TX, y0 = 1 + by * TY, z0 = 1 + bz * TZ;
+        const int x = x0 + lx, yl = y0 + gy * RY;   // this lane's column and first row
+        const long long ld = a.ld, ps = a.ps;
+        const S *__restrict__ uin = (const S *)a.uin;
+        const T *__restrict__ f = (const T *)a.f;
+        auto ld_u = [&](int xx, int yy, int zz) -> T {
+            const bool ok = xx <= nx + 1 && yy <= ny + 1 && zz <= nz + 1;
+            return ok ? ld_s<S, T>(uin + (long long)zz * ps + (long long)yy * ld + xx) : (T)0;
+        };
+        const Coef3<T> kc = make_coef3<T>(a);
+        // stage: every global load of this lane, then the x-halo columns
+        T u[RY][RZ], g[RY][RZ], sS[RZ], sN[RZ], hB[RY], hT[RY];
+#pragma unroll
+        for (int z = 0; z < RZ; ++z) {
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                const int yy = yl + r, zz = z0 + z;
+                u[r][z] = ld_u(x, yy, zz);
+                const bool in = x <= nx && yy <= ny && zz <= nz;
+                const T fv = in ? __ldg(f + (long long)zz * ps + (long long)yy * ld + x) : (T)0;
+                g[r][z] = EXACT ? fv : fv * kc.invd;
+            }
+            sS[z] = gy == 0 ? ld_u(x, y0 - 1, z0 + z) : (T)0;
+            sN[z] = gy == LY - 1 ? ld_u(x, y0 + TY, z0 + z) : (T)0;
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            hB[r] = ld_u(x, yl + r, z0 - 1);
+            hT[r] = ld_u(x, yl + r, z0 + TZ);
+        }
+        for (int t = lane; t < TY * TZ; t += 32) {
+            const int yy = y0 + t % TY, zz = z0 + t / TY;
+            xhalo[warp][0][t] = ld_u(x0 - 1, yy, zz);
+            xhalo[warp][1][t] = ld_u(x0 + TX, yy, zz);
+        }
+        __syncwarp();
+        const bool full = x0 + TX - 1 <= nx && y0 + TY - 1 <= ny && z0 + TZ - 1 <= nz;   // warp-uniform
+        for (int s = 0; s < a.k; ++s) {
+            T prev[RY];   // old values of the plane below
+#pragma unroll
+            for (int r = 0; r < RY; ++r) prev[r] = hB[r];
+#pragma unroll
+            for (int z = 0; z < RZ; ++z) {
+                T up = sS[z], dn = sN[z];
+                if constexpr (LY > 1) {
+                    const T a_up = __shfl_up_sync(FULL, u[RY - 1][z], LX);
+                    const T a_dn = __shfl_down_sync(FULL, u[0][z], LX);
+                    if (gy > 0) up = a_up;
+                    if (gy < LY - 1) dn = a_dn;
+                }
+                T nv[RY];
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                    const T c = u[r][z];
+                    T Wv = __shfl_up_sync(FULL, c, 1, LX);
+                    T Ev = __shfl_down_sync(FULL, c, 1, LX);
+                    const int hy = gy * RY + r + TY * z;
+                    if (lx == 0) Wv = xhalo[warp][0][hy];
+                    if (lx == LX - 1) Ev = xhalo[warp][1][hy];
+                    const T Sv = r > 0 ? u[r - 1][z] : up;
+                    const T Nv = r < RY - 1 ? u[r + 1][z] : dn;
+                    const T Tv = z < RZ - 1 ? u[r][z + 1] : hT[r];
+                    T res = 0;
+                    const T v = point_update3<T, EXACT, RES>(kc, g[r][z], Wv, Ev, Sv, Nv, prev[r], Tv, c, res);
+                    const bool in = full || (x <= nx && yl + r <= ny && z0 + z <= nz);
+                    nv[r] = in ? v : c;
+                    if constexpr (RES) {
+                        if (s == 0 && in) acc += (Acc)res * (Acc)res;
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                    prev[r] = u[r][z];
+                    u[r][z] = nv[r];
+                }
+            }
+        }
+        // write back this lane's interior points
+        S *uo = (S *)a.uout;
+#pragma unroll
+        for (int z = 0; z < RZ; ++z)
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                const int yy = yl + r, zz = z0 + z;
+                if (x <= nx && yy <= ny && zz <= nz) st_s<S, T>(uo + (long long)zz * ps + (long long)yy * ld + x, u[r][z]);
+            }
+    }
+    if constexpr (RES) reduce_grid_acc(a.red, acc);
+}
+
+// Classic global-memory Jacobi in 3D (Section 3.2's comparator with the
+// seven-point stencil): one thread per point, block (32, 8), one z plane per
+// blockIdx.z.  Same update arithmetic and fused residual as hier3d_kernel.
+template <typename S, typename T, bool EXACT, bool RES>
+__global__ void __launch_bounds__(256) classic3d_kernel(const CycArgs a) {
+    if constexpr (RES) {
+        if (*(volatile int *)&a.red.ctl->done >= 0) return;
+    }
+    const int x = 1 + blockIdx.x * 32 + threadIdx.x;
+    const int y = 1 + blockIdx.y * 8 + threadIdx.y;
+    const int z = 1 + blockIdx.z;
+    typedef typename std::conditional<EXACT, double, T>::type Acc;
+    Acc acc = 0;
+    if (x <= a.nx && y <= a.ny) {
+        const long long ld = a.ld, ps = a.ps;
+        const long long q = (long long)z * ps + (long long)y * ld + x;
+        const S *__restrict__ uin = (const S *)a.uin;
+        const Coef3<T> kc = make_coef3<T>(a);
+        const T old = ld_s<S, T>(uin + q);
+        const T W = ld_s<S, T>(uin + q - 1), E = ld_s<S, T>(uin + q + 1);
+        const T Sv = ld_s<S, T>(uin + q - ld), Nv = ld_s<S, T>(uin + q + ld);
+        const T B = ld_s<S, T>(uin + q - ps), Tv = ld_s<S, T>(uin + q + ps);
+        const T fv = __ldg((const T *)a.f + q);
+        const T g = EXACT ? fv : fv * kc.invd;
+        T res = 0;
+        const T nv = point_update3<T, EXACT, RES>(kc, g, W, E, Sv, Nv, B, Tv, old, res);
+        st_s<S, T>((S *)a.uout + q, nv);
+        acc += (Acc)res * (Acc)res;
+    }
+    if constexpr (RES) reduce_grid_acc(a.red, acc);
+}
+
+}  // namespace hj
+
+// registry entry: tile (TX, TY, TZ), threads, kernels without / with the fused residual
+#define HJ_K3D(S, T, LX, RY, RZ, NW, EX)                                                        \
+    {(LX), (32 / (LX)) * (RY), (RZ), 32 * (NW), (NW),                                         \
+     {hj::hier3d_kernel<S, T, LX, RY, RZ, NW, EX, false>, hj::hier3d_kernel<S, T, LX, RY, RZ, NW, EX, true>}}

@@ -84,6 +84,12 @@ struct CycArgs {
     const void *vc;
     const double *vsig;
     long long vcs;
+    // 3D seven-point extension: interior planes, plane pitch (elements) and
+    // the bottom (z - 1) / top (z + 1) coefficients with their binary32 copies
+    int nz;
+    long long ps;
+    double cB, cT;
+    float fB, fT, gB, gT;
 };
 
 // Subdomain j of J along one dimension of n interior points, T points each,
@@ -340,6 +346,21 @@ struct VcKernelInfo {
 };
 const VcKernelInfo *vc_kernels_f64();
 const VcKernelInfo *vc_kernels_f32();
+
+// 3D seven-point kernels: one warp per TX x TY x TZ subdomain, NW subdomains
+// per CTA of 32 * NW threads, grid ceil(subdomains / NW) CTAs; fn[res].
+struct Tile3Info {
+    int tx, ty, tz, threads, nw;
+    CycKernel fn[2];
+};
+const Tile3Info *tiles3d_f64(int *n);
+const Tile3Info *tiles3d_f32(int *n);
+// classic seven-point sweep: block (32, 8), grid (ceil(nx/32), ceil(ny/8), nz); fn[res]
+CycKernel classic3d_kernel_of(int fam, int res);
+cudaError_t launch_residual3d(int user_f64, const void *f, const void *u, long long ld, long long ps, int nx,
+                              int ny, int nz, double cW, double cE, double cS, double cN, double cB, double cT,
+                              double dconst, int with_fnorm, RedArgs red, cudaStream_t s);
+int aux_max_blocks3(int nx, int ny, int nz);
 
 // Kernel registries (one per storage/compute combination).
 enum KernelFamily { FAM_F64 = 0, FAM_F32 = 1, FAM_BF16 = 2 };

@@ -64,6 +64,7 @@ struct hj_handle {
     bool ir = false;
     const hj::TileKernelInfo *k_outer = nullptr, *k_inner = nullptr, *k_classic = nullptr, *k_classic_inner = nullptr;
     const hj::PpcKernelInfo *p_outer = nullptr, *p_inner = nullptr;   // TMA-pipelined variants (2D)
+    const hj::Tile3Info *k3 = nullptr;                                 // 3D seven-point kernel (hierarchical)
     long long ld_in = 0;          // row pitch of the refinement's binary32 / bfloat16 arrays
     void *ubuf = nullptr;
     void *ubuf2 = nullptr;        // third iterate buffer (pipelined kernel, deferred residual fold)

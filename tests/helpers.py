@@ -29,7 +29,7 @@ def to_dev(a, dim, dtype):
 
 
 def to_host(t, nx):
-    return t[:, :nx + 2].double().cpu().numpy()
+    return t[..., :nx + 2].double().cpu().numpy()
 
 
 def rel_max(a, b):

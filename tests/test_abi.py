@@ -60,10 +60,23 @@ def test_tile_shapes(hj):
 
 def test_create_rejects_bad_descriptors_without_touching_the_gpu(hj):
     # argument validation happens before any CUDA call
-    d = hj.make_desc(3, 10, 10, 32, -1, -1, -1, -1, 4)
+    d = hj.make_desc(4, 10, 10, 32, -1, -1, -1, -1, 4)
     with pytest.raises(hj.HJError) as e:
         hj.hj_create(d, hj.make_params())
     assert e.value.code == hj.HJ_ERR_INVALID_ARG
+    # 3D seven-point extension: planes, dominance over six neighbours, scope
+    for kw, prm, code in [(dict(nz=0), {}, hj.HJ_ERR_INVALID_ARG),
+                          (dict(nz=5, cB=-1, cT=-1), {}, hj.HJ_ERR_NOT_DIAG_DOMINANT),
+                          (dict(nz=5, cB=-1, cT=-1, cD=6.0), dict(precision="f32_ir"), hj.HJ_ERR_UNSUPPORTED),
+                          (dict(nz=5, cB=-1, cT=-1, cD=6.0), dict(overlap_x=2), hj.HJ_ERR_UNSUPPORTED),
+                          (dict(nz=5, cB=-1, cT=-1, cD=6.0), dict(persistent=1), hj.HJ_ERR_UNSUPPORTED),
+                          (dict(nz=5, cB=-1, cT=-1, cD=6.0), dict(tile_x=32, tile_y=32, tile_z=32),
+                           hj.HJ_ERR_UNSUPPORTED)]:
+        cD = kw.pop("cD", 4.0)
+        d = hj.make_desc(3, 10, 10, 32, -1, -1, -1, -1, cD, **kw)
+        with pytest.raises(hj.HJError) as e:
+            hj.hj_create(d, hj.make_params(**prm))
+        assert e.value.code == code, (kw, prm)
     d = hj.make_desc(2, 10, 10, 11, -1, -1, -1, -1, 4)     # ld < nx + 2
     with pytest.raises(hj.HJError) as e:
         hj.hj_create(d, hj.make_params())
