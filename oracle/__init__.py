@@ -25,7 +25,7 @@ from pathlib import Path
 import numpy as np
 
 _HERE = Path(__file__).resolve().parent
-_SRCS = [_HERE / "hj_oracle.c", _HERE / "hj_oracle3d.c"]
+_SRCS = [_HERE / "hj_oracle.c", _HERE / "hj_oracle3d.c", _HERE / "hj_oracle_mg.c"]
 _LIB = _HERE / "libhj_oracle.so"
 
 
@@ -52,6 +52,11 @@ class _Problem3(C.Structure):
                 ("cW", C.c_double), ("cE", C.c_double), ("cS", C.c_double), ("cN", C.c_double),
                 ("cB", C.c_double), ("cT", C.c_double), ("cD", C.c_double),
                 ("sigma_const", C.c_double), ("sigma", C.c_void_p)]
+
+
+class _MgProblem(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("cW", C.c_double), ("cE", C.c_double),
+                ("cS", C.c_double), ("cN", C.c_double), ("cD", C.c_double), ("sigma_const", C.c_double)]
 
 
 _lib = None
@@ -101,6 +106,18 @@ def lib():
                                  C.c_long, _D, C.c_long, C.POINTER(C.c_int)]
         L.hjo3_solve.restype = C.c_long
         L.hjo3_run_fixed.argtypes = [P3, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_long]
+        PM = C.POINTER(_MgProblem)
+        L.hjo_mg_wcycle.argtypes = [PM, _D, _D, _D, C.c_int, C.c_int, C.c_int, C.c_double]
+        L.hjo_mg_restrict.argtypes = [PM, _D, _D, _D]
+        L.hjo_mg_prolong_add.argtypes = [PM, _D, _D]
+        L.hjo_mg_max_levels.argtypes = [C.c_int, C.c_int]
+        L.hjo_mg_max_levels.restype = C.c_int
+        L.hjo_mg_vcycle.argtypes = [PM, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                    C.c_double, C.c_int, C.c_int]
+        L.hjo_mg_solve.argtypes = [PM, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.c_double, C.c_int, C.c_int, C.c_double, C.c_long, _D, C.c_long,
+                                   C.POINTER(C.c_int)]
+        L.hjo_mg_solve.restype = C.c_long
         L.hjo_paper_smem_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
         L.hjo_paper_smem_bytes.restype = C.c_long
         _lib = L
@@ -286,3 +303,70 @@ def adjoint(st, g, u, tol=1e-13, max_cycles=10_000_000, tx=32, ty=32, k=16):
 
 def paper_smem_bytes(dim, tx, ty, esize) -> int:
     return int(lib().hjo_paper_smem_bytes(dim, tx, ty, esize))
+
+
+# ---------------------------------------------------------------------------
+# hierarchical Jacobi as a multigrid smoother (hj_oracle_mg.c): 2D, constant
+# coefficients and sigma_const
+# ---------------------------------------------------------------------------
+
+def _mgp(st) -> _MgProblem:
+    if st.dim != 2 or st.sigma is not None or getattr(st, "coef", None) is not None:
+        raise ValueError("the multigrid oracle takes 2D constant-coefficient problems (sigma_const only)")
+    return _MgProblem(st.nx, st.ny, st.cW, st.cE, st.cS, st.cN, st.cD, float(st.sigma_const))
+
+
+def mg_coarse_stencil(st):
+    """The rediscretised operator one level down: every h^-2 term / 4."""
+    import dataclasses
+    return dataclasses.replace(st, nx=(st.nx - 1) // 2, ny=(st.ny - 1) // 2, cW=st.cW / 4, cE=st.cE / 4,
+                               cS=st.cS / 4, cN=st.cN / 4, cD=st.cD / 4)
+
+
+def mg_wcycle(st, f, u, tx, ty, k, omega):
+    """One weighted hierarchical cycle (damped Jacobi subiterations)."""
+    p = _mgp(st)
+    out = np.zeros((st.ny + 2, st.nx + 2))
+    lib().hjo_mg_wcycle(C.byref(p), _dp(_grid(f)), _dp(_grid(u)), _dp(out), tx, ty, k, float(omega))
+    return out
+
+
+def mg_restrict(st, f, u):
+    """Full weighting of f - A u onto the next coarser grid."""
+    p = _mgp(st)
+    fc = np.zeros(((st.ny - 1) // 2 + 2, (st.nx - 1) // 2 + 2))
+    lib().hjo_mg_restrict(C.byref(p), _dp(_grid(f)), _dp(_grid(u)), _dp(fc))
+    return fc
+
+
+def mg_prolong_add(st, e, u):
+    """u + bilinear interpolation of the coarse correction e."""
+    p = _mgp(st)
+    out = _grid(u).copy()
+    lib().hjo_mg_prolong_add(C.byref(p), _dp(_grid(e)), _dp(out))
+    return out
+
+
+def mg_max_levels(nx, ny) -> int:
+    return int(lib().hjo_mg_max_levels(nx, ny))
+
+
+def mg_vcycle(st, f, u, levels, pre=1, post=1, tx=32, ty=32, k=4, omega=0.8, coarse_k=64, coarse_cycles=4):
+    p = _mgp(st)
+    out = _grid(u).copy()
+    lib().hjo_mg_vcycle(C.byref(p), _dp(_grid(f)), _dp(out), int(levels), int(pre), int(post), tx, ty, k,
+                        float(omega), int(coarse_k), int(coarse_cycles))
+    return out
+
+
+def mg_solve(st, f, u0, tol, max_vcycles, levels, pre=1, post=1, tx=32, ty=32, k=4, omega=0.8, coarse_k=64,
+             coarse_cycles=4, hist_cap=0):
+    """V-cycles to ||r_c|| <= tol ||r_0||.  Returns (u, c, status, hist)."""
+    p = _mgp(st)
+    u = _grid(u0).copy()
+    hist = np.zeros(max(hist_cap, 1))
+    status = C.c_int(0)
+    c = lib().hjo_mg_solve(C.byref(p), _dp(_grid(f)), _dp(u), int(levels), int(pre), int(post), tx, ty, k,
+                           float(omega), int(coarse_k), int(coarse_cycles), float(tol), int(max_vcycles),
+                           _dp(hist), int(hist_cap), C.byref(status))
+    return u, int(c), int(status.value), hist[:min(hist_cap, c + 1)]
