@@ -453,6 +453,75 @@ def three_d(torch, hj, W, n=512, hbm_peak=None):
     return out
 
 
+def multigrid(torch, hj, W, n=4095, hbm_peak=None):
+    """Hierarchical Jacobi as a multigrid smoother (V-cycles, damped
+    subiterations, full weighting, bilinear prolongation): per-V-cycle time
+    at n^2 with its algorithmic bytes, time to 1e-10 (binary64) at n^2, and
+    time to 1e-8 at 511^2 against the hierarchical Jacobi solver alone
+    (binary32 inner cycles, binary64 refinement).
+
+    Algorithmic bytes per V(pre, post)-cycle, binary32, per fine point: each
+    level moves 12 (pre + post) + 19 B per own point (smoothing 12 B a cycle;
+    restriction reads u, f and writes the coarse f and correction; the
+    prolongation reads and writes u and reads the correction), levels add up
+    to 4/3 of the fine level, and the residual check reads u and f (8 B)."""
+    out = {}
+    q = W.poisson2d_uniform(n, n, seed=1)
+    for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        f = hj.grid_from(q.f, 2, dt)
+        for pre, post, k, tile in ((1, 1, 2, (32, 8)), (2, 2, 2, (32, 32))):
+            s = hj.Solver(q.st, method="mg", precision=prec, tile_x=tile[0], tile_y=tile[1], k=k, mg_pre=pre,
+                          mg_post=post, fixed_cycles=10)
+            u = hj.grid_from(q.u0, 2, dt)
+            s.solve(f, u)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.solve(f, u)
+            e1.record()
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) / 10 * 1e3
+            s.close()
+            row = {"us_per_vcycle": us}
+            if prec == "f32":
+                bpp = (12 * (pre + post) + 19) * 4.0 / 3.0 + 8
+                row["algorithmic_bytes_per_point"] = bpp
+                row["hbm_gbs"] = bpp * n * n / (us / 1e6) / 1e9
+                row["hbm_frac"] = row["hbm_gbs"] / hbm_peak if hbm_peak else None
+            out[f"{prec}_V{pre}{post}_k{k}_{tile[0]}x{tile[1]}"] = row
+        if prec == "f64":
+            s = hj.Solver(q.st, method="mg", precision="f64", tile_x=32, tile_y=8, k=2, tol=1e-10, max_cycles=100)
+            u = hj.grid_from(q.u0, 2, dt)
+            s.solve(f, u.clone())
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = s.solve(f, u)
+            torch.cuda.synchronize()
+            out["f64_to_1e-10"] = {"seconds": time.perf_counter() - t0, "vcycles": r["cycles"],
+                                   "rel_final": r["rel_final"], "status": r["status"]}
+            s.close()
+        del f
+    p = W.poisson2d_uniform(511, 511, seed=1)
+    f = hj.grid_from(p.f, 2, torch.float64)
+    ttr = {}
+    for name, kw in [("mg_f64_V11_k2", dict(method="mg", precision="f64", tile_x=32, tile_y=8, k=2, max_cycles=100)),
+                     ("hier_f32_ir_32x32_k32", dict(tile_x=32, tile_y=32, k=32, precision="f32_ir", inner_tol=1e-4,
+                                                    check_every=256))]:
+        s = hj.Solver(p.st, tol=1e-8, **kw)
+        u = hj.grid_from(p.u0, 2, torch.float64)
+        s.solve(f, u.clone())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = s.solve(f, u)
+        torch.cuda.synchronize()
+        ttr[name] = {"seconds": time.perf_counter() - t0, "cycles": r["cycles"], "status": r["status"]}
+        s.close()
+    ttr["speedup_mg_vs_hier"] = ttr["hier_f32_ir_32x32_k32"]["seconds"] / ttr["mg_f64_V11_k2"]["seconds"]
+    out["time_to_1e-8_511"] = ttr
+    return out
+
+
 def paper_replicas(torch, hj, W, precision="f64"):
     """Context: the paper's timing problems (Sections 3.5 and 4.2), residual
     reduced by 1e-4 from x0 = 1 with b = 1: best classic vs hierarchical
@@ -590,11 +659,22 @@ def main():
                          "(profiling runs: keeps the tuner's launches out of the capture)")
     ap.add_argument("--paper-replicas", action="store_true",
                     help="also time the paper's Section 3.5 / 4.2 problems (binary64, minutes)")
+    ap.add_argument("--only", default="", choices=["", "variable_coefficients", "three_d", "multigrid"],
+                    help="run one extras section alone and print its JSON (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        import torch
+        import paper_2006_16465_gb300 as hj
+        import workloads as W
+        torch.cuda.set_device(0)
+        hbm_peak, _ = _peaks()
+        section = {"variable_coefficients": variable_coefficients, "three_d": three_d, "multigrid": multigrid}
+        print(json.dumps({args.only: section[args.only](torch, hj, W, hbm_peak=hbm_peak)}), flush=True)
+        return 0
 
     import torch
     rank, world, local = dist_env()
@@ -697,6 +777,7 @@ def main():
         extras["inner_sweep_roofline_k16"] = inner_roofline(torch, hj, W, n)
         extras["variable_coefficients_4096"] = variable_coefficients(torch, hj, W, hbm_peak=hbm_peak)
         extras["three_d_512"] = three_d(torch, hj, W, hbm_peak=hbm_peak)
+        extras["multigrid_4095"] = multigrid(torch, hj, W, hbm_peak=hbm_peak)
     if args.paper_replicas and rank == 0:
         extras["paper_replicas"] = paper_replicas(torch, hj, W)
         extras["paper_replicas_f32"] = paper_replicas(torch, hj, W, "f32")

@@ -103,8 +103,19 @@ enum hj_precision { HJ_PREC_F64 = 0, HJ_PREC_F32 = 1, HJ_PREC_F32_IR = 2, HJ_PRE
 
 /* HJ_METHOD_HIER: hierarchical cycles (Sections 3.3, 4.1).
  * HJ_METHOD_CLASSIC: one global-memory Jacobi sweep per step (Section 3.2);
- * every point reads the previous iterate only (a true grid-wide step). */
-enum hj_method { HJ_METHOD_HIER = 0, HJ_METHOD_CLASSIC = 1 };
+ * every point reads the previous iterate only (a true grid-wide step).
+ * HJ_METHOD_MG: geometric multigrid V-cycles whose smoother is the
+ * hierarchical cycle with damped Jacobi subiterations (the use the paper's
+ * conclusion names).  2D, constant coefficients, sigma_const only, odd nx and
+ * ny; level l + 1 has (n_l - 1) / 2 points per axis (coarse point I on fine
+ * point 2I), its operator rediscretises the stencil (cW..cN and cD divided by
+ * 4, sigma_const kept); full-weighting restriction of the residual, bilinear
+ * prolongation, the coarsest level solved by mg_coarse_cycles undamped
+ * cycles of mg_coarse_k subiterations on one subdomain.  A "cycle" in
+ * hj_stats and max_cycles / fixed_cycles is one V-cycle; a solve also ends
+ * (HJ_ERR_NOT_CONVERGED) when ||r|| fell by less than 1 % over 4 V-cycles,
+ * the floor that the storage precision sets. */
+enum hj_method { HJ_METHOD_HIER = 0, HJ_METHOD_CLASSIC = 1, HJ_METHOD_MG = 2 };
 
 typedef struct {
     int dim;              /* 1, 2 or 3 (3: the seven-point extension, see nz)    */
@@ -208,6 +219,17 @@ typedef struct {
                              the precision (binary32 16 x 8 x 8, binary64
                              16 x 4 x 8), which replaces tile_x and tile_y.
                              Built shapes are listed by hj_tile_shapes3d()    */
+    int mg_levels;        /* HJ_METHOD_MG: levels including the given grid (>= 2;
+                             0 = as many as the sizes allow).  The coarsest
+                             level must hold at most 1024 points             */
+    int mg_pre, mg_post;  /* HJ_METHOD_MG: smoothing cycles before and after the
+                             coarse correction (>= 0); each cycle runs k damped
+                             subiterations on tile_x x tile_y subdomains
+                             (tile_x * tile_y <= 1024)                       */
+    double mg_omega;      /* HJ_METHOD_MG: Jacobi damping, 0 < omega <= 1
+                             (u' = u + omega (jac - u))                       */
+    int mg_coarse_k;      /* HJ_METHOD_MG: subiterations per coarsest-level cycle */
+    int mg_coarse_cycles; /* HJ_METHOD_MG: cycles on the coarsest level        */
 } hj_params;
 
 typedef struct {
@@ -237,7 +259,8 @@ typedef struct {
  * inner_tol = 1e-4, inner_max_cycles = 10^6, max_outer = 60, persistent = -1,
  * autotune = 0, pipeline = -1, tile_threads = 0, pipeline_stages = 0,
  * inner_stall = 32, ctas_per_sm = 0, overlap_x = overlap_y = 0, in_place = 0,
- * tile_z = 0. */
+ * tile_z = 0, mg_levels = 0, mg_pre = mg_post = 1, mg_omega = 0.8,
+ * mg_coarse_k = 64, mg_coarse_cycles = 4. */
 HJ_API void hj_default_params(hj_params *p);
 
 /* Create a solver for one problem shape.  Validates the descriptor and

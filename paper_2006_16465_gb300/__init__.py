@@ -31,7 +31,7 @@ HJ_ERR_NO_MEMORY = 8
 
 HJ_F64, HJ_F32 = 0, 1
 HJ_PREC_F64, HJ_PREC_F32, HJ_PREC_F32_IR, HJ_PREC_BF16CORR_IR = 0, 1, 2, 3
-HJ_METHOD_HIER, HJ_METHOD_CLASSIC = 0, 1
+HJ_METHOD_HIER, HJ_METHOD_CLASSIC, HJ_METHOD_MG = 0, 1, 2
 
 PRECISIONS = {"f64": HJ_PREC_F64, "f32": HJ_PREC_F32, "f32_ir": HJ_PREC_F32_IR, "bf16corr_ir": HJ_PREC_BF16CORR_IR}
 
@@ -51,7 +51,9 @@ class hj_params(C.Structure):
                 ("inner_max_cycles", C.c_longlong), ("max_outer", C.c_int), ("persistent", C.c_int),
                 ("autotune", C.c_int), ("pipeline", C.c_int), ("tile_threads", C.c_int),
                 ("pipeline_stages", C.c_int), ("inner_stall", C.c_int), ("ctas_per_sm", C.c_int),
-                ("overlap_x", C.c_int), ("overlap_y", C.c_int), ("in_place", C.c_int), ("tile_z", C.c_int)]
+                ("overlap_x", C.c_int), ("overlap_y", C.c_int), ("in_place", C.c_int), ("tile_z", C.c_int),
+                ("mg_levels", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int), ("mg_omega", C.c_double),
+                ("mg_coarse_k", C.c_int), ("mg_coarse_cycles", C.c_int)]
 
 
 class hj_stats(C.Structure):
@@ -290,7 +292,7 @@ def make_params(**kw) -> hj_params:
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
         if k == "method" and isinstance(v, str):
-            v = {"hier": HJ_METHOD_HIER, "classic": HJ_METHOD_CLASSIC}[v]
+            v = {"hier": HJ_METHOD_HIER, "classic": HJ_METHOD_CLASSIC, "mg": HJ_METHOD_MG}[v]
         setattr(p, k, v)
     return p
 

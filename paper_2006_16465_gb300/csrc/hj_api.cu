@@ -834,7 +834,9 @@ void fill_stats_config(const hj_handle *h, hj_stats *st, double t0) {
     st->k = h->p.k;
     const TileKernelInfo *tk = h->ir ? h->k_inner : h->k_outer;
     st->tile_threads = tk ? tk->threads / tk->tiles_per_cta
-                          : h->d.coef ? h->p.tile_x * (h->d.dim == 2 ? h->p.tile_y : 1) : h->k3 ? 32 : 0;
+                          : (h->d.coef || h->p.method == HJ_METHOD_MG) ? h->p.tile_x * (h->d.dim == 2 ? h->p.tile_y : 1)
+                          : h->k3                                      ? 32
+                                                                       : 0;
     st->tile_y = h->d.dim >= 2 ? h->p.tile_y : 1;
     st->tile_z = h->d.dim == 3 ? h->p.tile_z : 1;
     const PpcKernelInfo *pk = h->ir ? h->p_inner : h->p_outer;
@@ -872,6 +874,12 @@ void hj_default_params(hj_params *p) {
     p->pipeline = -1;
     p->inner_stall = 32;
     p->ctas_per_sm = 0;
+    p->mg_levels = 0;
+    p->mg_pre = 1;
+    p->mg_post = 1;
+    p->mg_omega = 0.8;
+    p->mg_coarse_k = 64;
+    p->mg_coarse_cycles = 4;
 }
 
 const char *hj_error_string(int s) {
@@ -940,6 +948,8 @@ int hj_tile_shapes3d(int precision, int *xyz, int cap) {
 void hj_destroy(hj_handle *h) {
     if (!h) return;
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    if (h->mg_exec) cudaGraphExecDestroy(h->mg_exec);
+    if (h->mg_arena) cudaFree(h->mg_arena);
     void *dev[] = {h->ubuf, h->ubuf2, h->dC, h->vcf, h->dinv_outer, h->dinv32, h->r32, h->dA, h->dB, h->hf, h->hu, h->partials, h->gpart,
                    h->hist, h->rstore, h->gcnt, h->fcnt, h->ctl, h->pscratch, h->barena, h->rs};
     for (void *p : dev)
@@ -975,8 +985,38 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     const bool ir = p.precision == HJ_PREC_F32_IR || p.precision == HJ_PREC_BF16CORR_IR;
     if ((p.precision == HJ_PREC_F32) != (d.dtype == HJ_F32))
         return seterr(HJ_ERR_INVALID_ARG, "dtype HJ_F32 goes with precision HJ_PREC_F32 only (binary64 arrays otherwise)");
-    if (p.method != HJ_METHOD_HIER && p.method != HJ_METHOD_CLASSIC)
+    if (p.method != HJ_METHOD_HIER && p.method != HJ_METHOD_CLASSIC && p.method != HJ_METHOD_MG)
         return seterr(HJ_ERR_INVALID_ARG, "unknown method %d", p.method);
+    int mg_levels = 0;
+    if (p.method == HJ_METHOD_MG) {
+        if (d.dim != 2) return seterr(HJ_ERR_UNSUPPORTED, "multigrid: 2D only");
+        if (d.sigma || d.coef)
+            return seterr(HJ_ERR_UNSUPPORTED, "multigrid: constant coefficients and sigma_const (sigma, coef NULL)");
+        if (p.precision != HJ_PREC_F64 && p.precision != HJ_PREC_F32)
+            return seterr(HJ_ERR_UNSUPPORTED, "multigrid: HJ_PREC_F64 or HJ_PREC_F32");
+        if (p.overlap_x > 0 || p.overlap_y > 0 || p.in_place || p.persistent == 1 || p.pipeline == 1 ||
+            p.autotune != 0)
+            return seterr(HJ_ERR_UNSUPPORTED, "multigrid: no overlap, in-place, persistent, pipeline or autotune");
+        if (p.tile_x < 1 || p.tile_y < 1 || (long long)p.tile_x * p.tile_y > 1024)
+            return seterr(HJ_ERR_INVALID_ARG, "multigrid: smoother subdomain of 1 to 1024 points");
+        if (p.mg_pre < 0 || p.mg_post < 0 || p.mg_coarse_k < 1 || p.mg_coarse_cycles < 1)
+            return seterr(HJ_ERR_INVALID_ARG, "multigrid: mg_pre, mg_post >= 0, mg_coarse_k, mg_coarse_cycles >= 1");
+        if (!(p.mg_omega > 0.0 && p.mg_omega <= 1.0))
+            return seterr(HJ_ERR_INVALID_ARG, "multigrid: 0 < mg_omega <= 1");
+        const int avail = mg_levels_of(d.nx, d.ny);
+        if (avail < 2) return seterr(HJ_ERR_INVALID_ARG, "multigrid needs odd nx, ny > 1 (got %d x %d)", d.nx, d.ny);
+        if (p.mg_levels < 0 || p.mg_levels == 1 || p.mg_levels > avail)
+            return seterr(HJ_ERR_INVALID_ARG, "multigrid: mg_levels must be 0 or in [2, %d]", avail);
+        mg_levels = p.mg_levels ? p.mg_levels : avail;
+        int cx = d.nx, cy = d.ny;
+        for (int l = 1; l < mg_levels; ++l) {
+            cx = (cx - 1) / 2;
+            cy = (cy - 1) / 2;
+        }
+        if ((long long)cx * cy > 1024)
+            return seterr(HJ_ERR_UNSUPPORTED, "multigrid: coarsest level %d x %d exceeds 1024 points (add levels)", cx, cy);
+        p.mg_levels = mg_levels;
+    }
     if (p.k < 1) return seterr(HJ_ERR_INVALID_ARG, "k must be >= 1");
     if (!(p.tol >= 0.0)) return seterr(HJ_ERR_INVALID_ARG, "tol must be >= 0");
     if (p.max_cycles < 0) return seterr(HJ_ERR_INVALID_ARG, "max_cycles must be >= 0");
@@ -1150,6 +1190,8 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
         if (d.dim == 2) h->p_inner = find_ppc(h->fam_inner, p.tile_x, p.tile_y, h->k_inner->threads, p.pipeline_stages);
     } else if (p.method == HJ_METHOD_CLASSIC) {
         h->k_classic = family_classic(h->fam_outer, d.dim);
+    } else if (p.method == HJ_METHOD_MG) {
+        // smoother, transfer and residual kernels live in hj_mg.cu
     } else {
         // (variable coefficients run their own thread-per-point kernel: any
         // subdomain of at most 1024 points)
@@ -1223,6 +1265,13 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
         cudaEventCreateWithFlags(&h->evs[1], cudaEventDisableTiming) != cudaSuccess)
         HJ_FAIL(HJ_ERR_CUDA, "stream/event creation failed");
 
+    if (p.method == HJ_METHOD_MG) {
+        st = mg_setup(h, mg_levels);
+        if (st != HJ_OK) {
+            hj_destroy(h);
+            return st;
+        }
+    }
     const double dconst = d.cD + d.sigma_const;
     const int r0 = d.dim == 2 ? 1 : 0;
     if (ir) {
@@ -1280,8 +1329,9 @@ int hj_solve(hj_handle *h, const void *f, void *u, hj_stream stream, hj_stats *s
     }
     CKS(check_ptr(h, fd, "f"));
     CKS(check_ptr(h, ud, "u"));
-    int st = h->ir ? solve_ir(h, (const double *)fd, (double *)ud, false, s, stats)
-                   : solve_plain(h, fd, ud, false, s, stats);
+    int st = h->ir                          ? solve_ir(h, (const double *)fd, (double *)ud, false, s, stats)
+             : h->p.method == HJ_METHOD_MG ? solve_mg(h, fd, ud, s, stats)
+                                           : solve_plain(h, fd, ud, false, s, stats);
     if (!udev && (st == HJ_OK || st == HJ_ERR_NOT_CONVERGED || st == HJ_ERR_DIVERGED)) {
         CKR(cudaMemcpyAsync(u, ud, h->grid_bytes, cudaMemcpyDeviceToHost, s));
         CKR(cudaStreamSynchronize(s));
@@ -1307,6 +1357,7 @@ int hj_solve_adjoint(hj_handle *h, const void *g, const void *u, void *dl_df, vo
     if (!h) return seterr(HJ_ERR_INVALID_ARG, "handle is NULL");
     if (h->d.coef) return seterr(HJ_ERR_UNSUPPORTED, "the adjoint is built for constant neighbour coefficients");
     if (h->d.dim == 3) return seterr(HJ_ERR_UNSUPPORTED, "the adjoint is built for 1D and 2D");
+    if (h->p.method == HJ_METHOD_MG) return seterr(HJ_ERR_UNSUPPORTED, "the adjoint runs hierarchical cycles, not V-cycles");
     CKS(check_ptr(h, g, "g"));
     CKS(check_ptr(h, u, "u"));
     CKS(check_ptr(h, dl_df, "dl_df"));

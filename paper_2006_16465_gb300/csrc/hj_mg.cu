@@ -1,0 +1,446 @@
+// hj_mg.cu -- hierarchical Jacobi as the smoother of a geometric multigrid
+// V-cycle (the use the paper's conclusion names; the V-cycle is the textbook
+// one of the multigrid tutorial it cites).
+//
+// Levels: level 0 is the caller's 2D grid; level l + 1 halves the interior
+// ((n - 1) / 2 points per axis, coarse point (I, J) on fine point (2I, 2J)),
+// and its operator rediscretises the stencil on the doubled spacing (every
+// h^-2 coefficient divided by 4, sigma_const kept).
+//
+// Kernels (one launch each, all captured in one CUDA graph per handle):
+//   * mg_smooth_kernel: one weighted hierarchical cycle, one thread per point,
+//     the subdomain plus halo in two shared-memory containers, k damped
+//     Jacobi subiterations u' = u + omega (jac - u) with the halo frozen;
+//   * mg_restrict_kernel: the fine residual f - A u at the nine fine points
+//     around each coarse point, full-weighted into the coarse right-hand side
+//     (fused, no residual array), and the coarse correction set to zero;
+//   * mg_prolong_kernel: u + bilinear interpolation of the coarse correction.
+// The graph also holds the residual norm of the level-0 iterate and its copy
+// to pinned host memory, so a V-cycle costs one graph launch and one wait.
+//
+// Binary64 evaluates every sum in the oracle's order with separately rounded
+// operations (no fused multiply-add), so the GPU V-cycle equals the oracle's
+// bit for bit; binary32 uses fused chains.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "hj_runtime.cuh"
+
+namespace hj {
+
+namespace {
+
+struct MgSmoothArgs {
+    const void *f;
+    const void *uin;
+    void *uout;
+    long long ld;
+    int nx, ny, k;
+    double cW, cE, cS, cN, invd, omega;
+    float fW, fE, fS, fN, finvd, fomega;   // binary32: -c/d, 1/d, omega
+};
+
+struct MgXferArgs {
+    const void *f;       // fine right-hand side (restriction)
+    const void *u;       // fine iterate (restriction: input; prolongation: u_in)
+    void *uout;          // prolongation output (may equal u)
+    void *fc;            // coarse right-hand side (restriction output)
+    void *ec;            // coarse correction (restriction: zeroed; prolongation: input)
+    long long ld, ldc;
+    int nx, ny, ncx, ncy;
+    double d, cW, cE, cS, cN;
+};
+
+template <typename T>
+__device__ __forceinline__ T ld_g(const T *p) {
+    return __ldg(p);
+}
+
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(1024, 2) mg_smooth_kernel(const MgSmoothArgs a) {
+    extern __shared__ __align__(16) unsigned char mg_smem[];
+    const int TX = blockDim.x, TY = blockDim.y, lw = TX + 2, lh = TY + 2;
+    T *buf0 = (T *)mg_smem, *buf1 = buf0 + lw * lh;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = 1 + blockIdx.x * TX + tx, j = 1 + blockIdx.y * TY + ty;
+    const int nx = a.nx, ny = a.ny;
+    const long long ld = a.ld;
+    const bool in = i <= nx && j <= ny;
+    const T *__restrict__ u = (const T *)a.uin;
+    auto ld_u = [&](int jj, int ii) -> T {
+        return (ii <= nx + 1 && jj <= ny + 1) ? ld_g(u + (long long)jj * ld + ii) : (T)0;
+    };
+    // every global load first, then the shared-memory stores
+    const T v0 = ld_u(j, i);
+    const T hw = tx == 0 ? ld_u(j, i - 1) : (T)0;
+    const T he = tx == TX - 1 ? ld_u(j, i + 1) : (T)0;
+    const T hs = ty == 0 ? ld_u(j - 1, i) : (T)0;
+    const T hn = ty == TY - 1 ? ld_u(j + 1, i) : (T)0;
+    const long long q = (long long)j * ld + i;
+    const T fv = in ? ld_g((const T *)a.f + q) : (T)0;
+    const int me = (ty + 1) * lw + tx + 1;
+    buf0[me] = v0;
+    buf1[me] = v0;
+    if (tx == 0) { buf0[me - 1] = hw; buf1[me - 1] = hw; }
+    if (tx == TX - 1) { buf0[me + 1] = he; buf1[me + 1] = he; }
+    if (ty == 0) { buf0[me - lw] = hs; buf1[me - lw] = hs; }
+    if (ty == TY - 1) { buf0[me + lw] = hn; buf1[me + lw] = hn; }
+    const T g = EXACT ? fv : fv * (T)a.finvd;
+    __syncthreads();
+    for (int s = 0; s < a.k; ++s) {
+        const T *src = (s & 1) ? buf1 : buf0;
+        T *dst = (s & 1) ? buf0 : buf1;
+        if (in) {
+            const T old = src[me];
+            const T W = src[me - 1], E = src[me + 1], Sv = src[me - lw], Nv = src[me + lw];
+            T nv;
+            if constexpr (EXACT) {
+                double acc = __dmul_rn(a.cW, W);
+                acc = __dadd_rn(acc, __dmul_rn(a.cE, E));
+                acc = __dadd_rn(acc, __dmul_rn(a.cS, Sv));
+                acc = __dadd_rn(acc, __dmul_rn(a.cN, Nv));
+                const double jac = __dmul_rn(__dsub_rn(g, acc), a.invd);
+                nv = __dadd_rn(old, __dmul_rn(a.omega, __dsub_rn(jac, old)));
+            } else {
+                T t = g;
+                t = fmaf(a.fN, Nv, t);
+                t = fmaf(a.fS, Sv, t);
+                t = fmaf(a.fE, E, t);
+                t = fmaf(a.fW, W, t);
+                nv = fmaf(a.fomega, t - old, old);
+            }
+            dst[me] = nv;
+        }
+        __syncthreads();
+    }
+    if (in) ((T *)a.uout)[q] = ((a.k & 1) ? buf1 : buf0)[me];
+}
+
+// f - A u at fine index q, in the oracle's order (binary64) or fused (binary32)
+template <typename T, bool EXACT>
+__device__ __forceinline__ T mg_resid(const MgXferArgs &x, const T *u, const T *f, long long q) {
+    if constexpr (EXACT) {
+        double au = __dmul_rn(x.d, u[q]);
+        au = __dadd_rn(au, __dmul_rn(x.cW, u[q - 1]));
+        au = __dadd_rn(au, __dmul_rn(x.cE, u[q + 1]));
+        au = __dadd_rn(au, __dmul_rn(x.cS, u[q - x.ld]));
+        au = __dadd_rn(au, __dmul_rn(x.cN, u[q + x.ld]));
+        return __dsub_rn(f[q], au);
+    } else {
+        T r = fmaf(-(T)x.d, u[q], f[q]);
+        r = fmaf(-(T)x.cW, u[q - 1], r);
+        r = fmaf(-(T)x.cE, u[q + 1], r);
+        r = fmaf(-(T)x.cS, u[q - x.ld], r);
+        r = fmaf(-(T)x.cN, u[q + x.ld], r);
+        return r;
+    }
+}
+
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(256) mg_restrict_kernel(const MgXferArgs x) {
+    const int I = 1 + blockIdx.x * 32 + threadIdx.x, J = 1 + blockIdx.y * 8 + threadIdx.y;
+    if (I > x.ncx || J > x.ncy) return;
+    const T *u = (const T *)x.u, *f = (const T *)x.f;
+    const long long q = 2LL * J * x.ld + 2LL * I, ld = x.ld;
+    const T r00 = mg_resid<T, EXACT>(x, u, f, q);
+    T fcv;
+    if constexpr (EXACT) {
+        double s1 = __dadd_rn(mg_resid<T, EXACT>(x, u, f, q - 1), mg_resid<T, EXACT>(x, u, f, q + 1));
+        s1 = __dadd_rn(s1, mg_resid<T, EXACT>(x, u, f, q - ld));
+        s1 = __dadd_rn(s1, mg_resid<T, EXACT>(x, u, f, q + ld));
+        double s2 = __dadd_rn(mg_resid<T, EXACT>(x, u, f, q - ld - 1), mg_resid<T, EXACT>(x, u, f, q - ld + 1));
+        s2 = __dadd_rn(s2, mg_resid<T, EXACT>(x, u, f, q + ld - 1));
+        s2 = __dadd_rn(s2, mg_resid<T, EXACT>(x, u, f, q + ld + 1));
+        double t = __dmul_rn(4.0, r00);
+        t = __dadd_rn(t, __dmul_rn(2.0, s1));
+        t = __dadd_rn(t, s2);
+        fcv = __dmul_rn(t, 0.0625);
+    } else {
+        const T s1 = (mg_resid<T, EXACT>(x, u, f, q - 1) + mg_resid<T, EXACT>(x, u, f, q + 1)) +
+                     (mg_resid<T, EXACT>(x, u, f, q - ld) + mg_resid<T, EXACT>(x, u, f, q + ld));
+        const T s2 = (mg_resid<T, EXACT>(x, u, f, q - ld - 1) + mg_resid<T, EXACT>(x, u, f, q - ld + 1)) +
+                     (mg_resid<T, EXACT>(x, u, f, q + ld - 1) + mg_resid<T, EXACT>(x, u, f, q + ld + 1));
+        fcv = (4.0f * r00 + 2.0f * s1 + s2) * 0.0625f;
+    }
+    const long long qc = (long long)J * x.ldc + I;
+    ((T *)x.fc)[qc] = fcv;
+    ((T *)x.ec)[qc] = (T)0;
+}
+
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(256) mg_prolong_kernel(const MgXferArgs x) {
+    const int i = 1 + blockIdx.x * 32 + threadIdx.x, j = 1 + blockIdx.y * 8 + threadIdx.y;
+    if (i > x.nx || j > x.ny) return;
+    const T *e = (const T *)x.ec;
+    const long long ldc = x.ldc;
+    const int a = (i - 1) / 2, b = (j - 1) / 2;
+    T v;
+    if (!(i & 1) && !(j & 1)) {
+        v = e[(long long)(j / 2) * ldc + i / 2];
+    } else if (!(j & 1)) {
+        const long long r = (long long)(j / 2) * ldc;
+        v = EXACT ? (T)__dmul_rn(__dadd_rn(e[r + a], e[r + a + 1]), 0.5) : (e[r + a] + e[r + a + 1]) * (T)0.5;
+    } else if (!(i & 1)) {
+        const long long r0 = (long long)b * ldc, r1 = r0 + ldc;
+        v = EXACT ? (T)__dmul_rn(__dadd_rn(e[r0 + i / 2], e[r1 + i / 2]), 0.5)
+                  : (e[r0 + i / 2] + e[r1 + i / 2]) * (T)0.5;
+    } else {
+        const long long r0 = (long long)b * ldc, r1 = r0 + ldc;
+        if constexpr (EXACT) {
+            double s = __dadd_rn(e[r0 + a], e[r0 + a + 1]);
+            s = __dadd_rn(s, e[r1 + a]);
+            s = __dadd_rn(s, e[r1 + a + 1]);
+            v = __dmul_rn(s, 0.25);
+        } else {
+            v = ((e[r0 + a] + e[r0 + a + 1]) + (e[r1 + a] + e[r1 + a + 1])) * (T)0.25;
+        }
+    }
+    const long long q = (long long)j * x.ld + i;
+    const T un = ((const T *)x.u)[q];
+    ((T *)x.uout)[q] = EXACT ? (T)__dadd_rn(un, v) : un + v;
+}
+
+MgSmoothArgs smooth_args(const MgLevel &L, const void *f, const void *uin, void *uout, int k, double omega,
+                         double sigma_const) {
+    MgSmoothArgs a;
+    memset(&a, 0, sizeof(a));
+    a.f = f;
+    a.uin = uin;
+    a.uout = uout;
+    a.ld = L.ld;
+    a.nx = L.nx;
+    a.ny = L.ny;
+    a.k = k;
+    a.cW = L.cW; a.cE = L.cE; a.cS = L.cS; a.cN = L.cN;
+    a.invd = 1.0 / (L.cD + sigma_const);
+    a.omega = omega;
+    a.fW = (float)(-L.cW * a.invd); a.fE = (float)(-L.cE * a.invd);
+    a.fS = (float)(-L.cS * a.invd); a.fN = (float)(-L.cN * a.invd);
+    a.finvd = (float)a.invd;
+    a.fomega = (float)omega;
+    return a;
+}
+
+// Launch one smoothing cycle on level l (buffer cur -> 1 - cur); tile tx x ty.
+void launch_smooth(hj_handle *h, int l, int cur, int tx, int ty, int k, double omega, cudaStream_t s) {
+    const MgLevel &L = h->mg[l];
+    void *buf[2] = {L.a, L.b};
+    const MgSmoothArgs a = smooth_args(L, L.f, buf[cur], buf[1 - cur], k, omega, h->d.sigma_const);
+    const dim3 block(tx, ty), grid((L.nx + tx - 1) / tx, (L.ny + ty - 1) / ty);
+    const bool f64 = h->fam_outer == FAM_F64;
+    const int smem = 2 * (tx + 2) * (ty + 2) * (f64 ? 8 : 4);
+    if (f64) mg_smooth_kernel<double, true><<<grid, block, smem, s>>>(a);
+    else mg_smooth_kernel<float, false><<<grid, block, smem, s>>>(a);
+}
+
+MgXferArgs xfer_args(const hj_handle *h, int l) {
+    const MgLevel &F = h->mg[l], &Cc = h->mg[l + 1];
+    MgXferArgs x;
+    memset(&x, 0, sizeof(x));
+    x.ld = F.ld;
+    x.ldc = Cc.ld;
+    x.nx = F.nx; x.ny = F.ny;
+    x.ncx = Cc.nx; x.ncy = Cc.ny;
+    x.d = F.cD + h->d.sigma_const;
+    x.cW = F.cW; x.cE = F.cE; x.cS = F.cS; x.cN = F.cN;
+    return x;
+}
+
+// The V-cycle below level l, starting from buffer cur of level l; returns the
+// buffer that holds the level's result.
+int record_level(hj_handle *h, int l, int cur, cudaStream_t s) {
+    const hj_params &p = h->p;
+    const int levels = (int)h->mg.size();
+    const MgLevel &L = h->mg[l];
+    if (l == levels - 1) {
+        for (int c = 0; c < p.mg_coarse_cycles; ++c) {
+            launch_smooth(h, l, cur, L.nx, L.ny, p.mg_coarse_k, 1.0, s);
+            cur ^= 1;
+        }
+        return cur;
+    }
+    for (int c = 0; c < p.mg_pre; ++c) {
+        launch_smooth(h, l, cur, p.tile_x, p.tile_y, p.k, p.mg_omega, s);
+        cur ^= 1;
+    }
+    const bool f64 = h->fam_outer == FAM_F64;
+    MgXferArgs x = xfer_args(h, l);
+    const MgLevel &Cc = h->mg[l + 1];
+    x.f = L.f;
+    x.u = cur ? L.b : L.a;
+    x.fc = Cc.f;
+    x.ec = Cc.a;
+    {
+        const dim3 g((Cc.nx + 31) / 32, (Cc.ny + 7) / 8), b(32, 8);
+        if (f64) mg_restrict_kernel<double, true><<<g, b, 0, s>>>(x);
+        else mg_restrict_kernel<float, false><<<g, b, 0, s>>>(x);
+    }
+    const int ce = record_level(h, l + 1, 0, s);
+    // level 0 must end in buffer a (the graph is replayed from there): when
+    // pre + post is odd, the prolongation writes the other buffer
+    const bool flip = l == 0 && ((p.mg_pre + p.mg_post) & 1);
+    x.ec = ce ? Cc.b : Cc.a;
+    x.u = cur ? L.b : L.a;
+    x.uout = flip ? (cur ? L.a : L.b) : const_cast<void *>(x.u);
+    {
+        const dim3 g((L.nx + 31) / 32, (L.ny + 7) / 8), b(32, 8);
+        if (f64) mg_prolong_kernel<double, true><<<g, b, 0, s>>>(x);
+        else mg_prolong_kernel<float, false><<<g, b, 0, s>>>(x);
+    }
+    if (flip) cur ^= 1;
+    for (int c = 0; c < p.mg_post; ++c) {
+        launch_smooth(h, l, cur, p.tile_x, p.tile_y, p.k, p.mg_omega, s);
+        cur ^= 1;
+    }
+    return cur;
+}
+
+RedArgs store_red(const hj_handle *h) {
+    RedArgs r;
+    memset(&r, 0, sizeof(r));
+    r.partials = h->partials;
+    r.gpart = h->gpart;
+    r.gcnt = h->gcnt;
+    r.fcnt = h->fcnt;
+    r.hist = h->hist;
+    r.out = h->rstore;
+    r.ctl = h->ctl;
+    r.mode = RED_STORE;
+    r.scale = 1.0;
+    return r;
+}
+
+// ||f - A u||^2 of the level-0 buffer a into pinned host memory (h_rstore).
+cudaError_t record_residual(hj_handle *h, cudaStream_t s) {
+    const MgLevel &L = h->mg[0];
+    const hj_desc &d = h->d;
+    cudaError_t e = launch_residual_ex(2, d.dtype == HJ_F64, L.f, L.a, nullptr, d.ld, d.ld, d.nx, d.ny, d.cW, d.cE,
+                                       d.cS, d.cN, d.cD + d.sigma_const, 0, nullptr, store_red(h), s);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(h->h_rstore, h->rstore, sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+}  // namespace
+
+int mg_levels_of(int nx, int ny) {
+    int L = 1;
+    while (nx > 1 && ny > 1 && (nx & 1) && (ny & 1)) {
+        nx = (nx - 1) / 2;
+        ny = (ny - 1) / 2;
+        ++L;
+    }
+    return L;
+}
+
+int mg_setup(hj_handle *h, int levels) {
+    const hj_desc &d = h->d;
+    const size_t esz = h->esz;
+    h->mg.resize(levels);
+    int nx = d.nx, ny = d.ny;
+    double cW = d.cW, cE = d.cE, cS = d.cS, cN = d.cN, cD = d.cD;
+    size_t total = 0;
+    for (int l = 0; l < levels; ++l) {
+        MgLevel &L = h->mg[l];
+        L.nx = nx;
+        L.ny = ny;
+        L.ld = l == 0 ? d.ld : ((long long)nx + 2 + 31) / 32 * 32;
+        L.cW = cW; L.cE = cE; L.cS = cS; L.cN = cN; L.cD = cD;
+        total += 3 * (size_t)(ny + 2) * L.ld * esz;
+        nx = (nx - 1) / 2;
+        ny = (ny - 1) / 2;
+        cW /= 4.0; cE /= 4.0; cS /= 4.0; cN /= 4.0; cD /= 4.0;
+    }
+    if (cudaMalloc(&h->mg_arena, total) != cudaSuccess) {
+        cudaGetLastError();
+        return seterr(HJ_ERR_NO_MEMORY, "cudaMalloc of %zu bytes failed (multigrid levels)", total);
+    }
+    CKR(cudaMemset(h->mg_arena, 0, total));
+    unsigned char *p = (unsigned char *)h->mg_arena;
+    for (int l = 0; l < levels; ++l) {
+        MgLevel &L = h->mg[l];
+        const size_t b = (size_t)(L.ny + 2) * L.ld * esz;
+        L.a = p; p += b;
+        L.b = p; p += b;
+        L.f = p; p += b;
+    }
+    return HJ_OK;
+}
+
+// V-cycles until ||r_c|| <= tol ||r_0|| (or fixed_cycles V-cycles), u in/out.
+int solve_mg(hj_handle *h, const void *f, void *u, cudaStream_t s, hj_stats *st) {
+    const MgLevel &L0 = h->mg[0];
+    CKR(cudaMemcpyAsync(L0.a, u, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+    CKR(cudaMemcpyAsync(L0.b, u, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+    CKR(cudaMemcpyAsync(L0.f, f, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+    if (!h->mg_exec) {
+        cudaGraph_t graph;
+        CKR(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        const int fin = record_level(h, 0, 0, h->cap);
+        cudaError_t le = cudaGetLastError();
+        if (le == cudaSuccess) le = record_residual(h, h->cap);
+        cudaError_t ee = cudaStreamEndCapture(h->cap, &graph);
+        if (le != cudaSuccess) return seterr(HJ_ERR_CUDA, "multigrid capture: %s", cudaGetErrorString(le));
+        if (ee != cudaSuccess) return seterr(HJ_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ee));
+        if (fin != 0) {
+            cudaGraphDestroy(graph);
+            return seterr(HJ_ERR_CUDA, "internal: V-cycle does not end in the level-0 buffer");
+        }
+        cudaError_t ie = cudaGraphInstantiate(&h->mg_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            h->mg_exec = nullptr;
+            return seterr(HJ_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+        }
+    }
+    const long long fixed = h->p.fixed_cycles;
+    long long c = 0, hl = 0;
+    bool stalled = false;
+    int status = HJ_OK;
+    double r0 = -1.0, rc = -1.0;
+    if (fixed > 0) {
+        for (c = 0; c < fixed; ++c) CKR(cudaGraphLaunch(h->mg_exec, s));
+    } else {
+        CKR(record_residual(h, s));
+        CKR(cudaStreamSynchronize(s));
+        r0 = rc = sqrt(std::max(h->h_rstore[0], 0.0));
+        status = HJ_ERR_NOT_CONVERGED;
+        // the last kStall + 1 residuals: a V-cycle contracts by a fixed factor
+        // until the storage precision's floor (binary32 u: about eps |u| / h^2
+        // relative), so a drop of less than 1 % over kStall V-cycles ends the solve
+        constexpr int kStall = 4;
+        double ring[kStall + 1];
+        for (;;) {
+            if (st && st->history && hl < st->history_cap) st->history[hl++] = rc;
+            ring[c % (kStall + 1)] = rc;
+            if (!std::isfinite(rc)) { status = HJ_ERR_DIVERGED; break; }
+            if (rc <= h->p.tol * r0) { status = HJ_OK; break; }
+            if (c >= h->p.max_cycles) break;
+            if (c >= kStall && rc > 0.99 * ring[(c - kStall) % (kStall + 1)]) { stalled = true; break; }
+            CKR(cudaGraphLaunch(h->mg_exec, s));
+            CKR(cudaStreamSynchronize(s));
+            rc = sqrt(std::max(h->h_rstore[0], 0.0));
+            ++c;
+        }
+    }
+    CKR(cudaMemcpyAsync(u, L0.a, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+    CKR(cudaStreamSynchronize(s));
+    if (st) {
+        st->cycles = c;
+        st->cycles_launched = c;
+        st->inner_cycles = 0;
+        st->outer_steps = 0;
+        st->res0 = r0;
+        st->res_final = rc;
+        st->rel_final = r0 > 0 ? rc / r0 : 0.0;
+        st->history_len = hl;
+        st->persistent = 0;
+    }
+    if (status == HJ_ERR_DIVERGED) return seterr(HJ_ERR_DIVERGED, "residual became non-finite at V-cycle %lld", c);
+    if (status == HJ_ERR_NOT_CONVERGED)
+        return seterr(HJ_ERR_NOT_CONVERGED, "tolerance %g not met after %lld V-cycles (rel %g%s)", h->p.tol, c,
+                      r0 > 0 ? rc / r0 : 0.0, stalled ? "; the residual stopped falling" : "");
+    return HJ_OK;
+}
+
+}  // namespace hj

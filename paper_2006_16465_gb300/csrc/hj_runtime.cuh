@@ -52,6 +52,15 @@ const PersistClassicInfo *persist_classic_f64();
 const PersistClassicInfo *persist_classic_f32();
 const PersistClassicInfo *persist_classic_bf16();
 
+// One multigrid level: sizes, pitch, the two iterate buffers and the
+// right-hand side, and the rediscretised stencil (sigma_const is shared).
+struct MgLevel {
+    int nx = 0, ny = 0;
+    long long ld = 0;
+    void *a = nullptr, *b = nullptr, *f = nullptr;
+    double cW = 0, cE = 0, cS = 0, cN = 0, cD = 0;
+};
+
 }  // namespace hj
 
 struct hj_handle {
@@ -95,7 +104,17 @@ struct hj_handle {
     size_t barena_bytes = 0;
     double *rs = nullptr, *h_rs = nullptr;
     size_t nrs = 0;
+    // multigrid (HJ_METHOD_MG): levels, their buffers and the V-cycle graph
+    std::vector<hj::MgLevel> mg;
+    void *mg_arena = nullptr;
+    cudaGraphExec_t mg_exec = nullptr;
 };
+
+namespace hj {
+int mg_levels_of(int nx, int ny);
+int mg_setup(hj_handle *h, int levels);
+int solve_mg(hj_handle *h, const void *f, void *u, cudaStream_t s, hj_stats *st);
+}  // namespace hj
 
 namespace hj {
 

@@ -98,3 +98,34 @@ def test_no_cpu_fallback(tmp_path, monkeypatch, hj):
     monkeypatch.setattr(hj, "_lib", None)
     with pytest.raises(RuntimeError):
         hj.lib()
+
+
+def test_struct_layouts_match_the_header(tmp_path, hj):
+    """Every field of hj_desc, hj_params and hj_stats sits at the same offset
+    (and every struct has the same size) in the ctypes mirrors as in
+    include/hj.h compiled by the C compiler."""
+    import ctypes as C
+    import subprocess
+    from pathlib import Path
+    root = Path(__file__).resolve().parents[1]
+    structs = [hj.hj_desc, hj.hj_params, hj.hj_stats]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hj.h"', "int main(void) {"]
+    for S in structs:
+        lines.append(f'printf("{S.__name__} size %zu\\n", sizeof({S.__name__}));')
+        for name, _ in S._fields_:
+            lines.append(f'printf("{S.__name__} {name} %zu\\n", offsetof({S.__name__}, {name}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", str(root / "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            s, f, v = line.split()
+            got[(s, f)] = int(v)
+    for S in structs:
+        assert got[(S.__name__, "size")] == C.sizeof(S), S.__name__
+        for name, _ in S._fields_:
+            assert got[(S.__name__, name)] == getattr(S, name).offset, (S.__name__, name)
