@@ -8,13 +8,15 @@
 // h^-2 coefficient divided by 4, sigma_const kept).
 //
 // Kernels (one launch each, all captured in one CUDA graph per handle):
-//   * mg_smooth_kernel: one weighted hierarchical cycle, one thread per point,
-//     the subdomain plus halo in two shared-memory containers, k damped
-//     Jacobi subiterations u' = u + omega (jac - u) with the halo frozen;
+//   * mg_smooth_kernel: one weighted hierarchical cycle, a thread per point of
+//     up to four rows, the subdomain plus halo in two shared-memory
+//     containers, k damped Jacobi subiterations u' = u + omega (jac - u)
+//     with the halo frozen;
 //   * mg_restrict_kernel: the fine residual f - A u at the nine fine points
 //     around each coarse point, full-weighted into the coarse right-hand side
 //     (fused, no residual array), and the coarse correction set to zero;
-//   * mg_prolong_kernel: u + bilinear interpolation of the coarse correction.
+//   * mg_prolong_kernel: u + bilinear interpolation of the coarse correction,
+//     one thread per coarse cell writing the 2 x 2 fine points inside it.
 // The graph also holds the residual norm of the level-0 iterate and its copy
 // to pinned host memory, so a V-cycle costs one graph launch and one wait.
 //
@@ -57,41 +59,56 @@ __device__ __forceinline__ T ld_g(const T *p) {
     return __ldg(p);
 }
 
-template <typename T, bool EXACT>
-__global__ void __launch_bounds__(1024, 2) mg_smooth_kernel(const MgSmoothArgs a) {
+// RPT rows per thread: thread (tx, ty) of a (TX, BY) block owns rows
+// ty + m BY (m < RPT) of a TX x (BY RPT) subdomain, so each thread keeps RPT
+// independent loads of u and f in flight (one point per thread leaves too
+// few bytes in flight per SM to cover HBM latency).
+template <typename T, bool EXACT, int RPT>
+__global__ void __launch_bounds__(1024 / RPT, RPT == 1 ? 2 : 1) mg_smooth_kernel(const MgSmoothArgs a) {
     extern __shared__ __align__(16) unsigned char mg_smem[];
-    const int TX = blockDim.x, TY = blockDim.y, lw = TX + 2, lh = TY + 2;
+    const int TX = blockDim.x, BY = blockDim.y, TY = BY * RPT, lw = TX + 2, lh = TY + 2;
     T *buf0 = (T *)mg_smem, *buf1 = buf0 + lw * lh;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i = 1 + blockIdx.x * TX + tx, j = 1 + blockIdx.y * TY + ty;
+    const int i = 1 + blockIdx.x * TX + tx, j0 = 1 + blockIdx.y * TY;
     const int nx = a.nx, ny = a.ny;
     const long long ld = a.ld;
-    const bool in = i <= nx && j <= ny;
     const T *__restrict__ u = (const T *)a.uin;
     auto ld_u = [&](int jj, int ii) -> T {
         return (ii <= nx + 1 && jj <= ny + 1) ? ld_g(u + (long long)jj * ld + ii) : (T)0;
     };
     // every global load first, then the shared-memory stores
-    const T v0 = ld_u(j, i);
-    const T hw = tx == 0 ? ld_u(j, i - 1) : (T)0;
-    const T he = tx == TX - 1 ? ld_u(j, i + 1) : (T)0;
-    const T hs = ty == 0 ? ld_u(j - 1, i) : (T)0;
-    const T hn = ty == TY - 1 ? ld_u(j + 1, i) : (T)0;
-    const long long q = (long long)j * ld + i;
-    const T fv = in ? ld_g((const T *)a.f + q) : (T)0;
-    const int me = (ty + 1) * lw + tx + 1;
-    buf0[me] = v0;
-    buf1[me] = v0;
-    if (tx == 0) { buf0[me - 1] = hw; buf1[me - 1] = hw; }
-    if (tx == TX - 1) { buf0[me + 1] = he; buf1[me + 1] = he; }
-    if (ty == 0) { buf0[me - lw] = hs; buf1[me - lw] = hs; }
-    if (ty == TY - 1) { buf0[me + lw] = hn; buf1[me + lw] = hn; }
-    const T g = EXACT ? fv : fv * (T)a.finvd;
+    T v0[RPT], hw[RPT], he[RPT], g[RPT];
+    bool in[RPT];
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+        const int j = j0 + ty + m * BY;
+        in[m] = i <= nx && j <= ny;
+        v0[m] = ld_u(j, i);
+        hw[m] = tx == 0 ? ld_u(j, i - 1) : (T)0;
+        he[m] = tx == TX - 1 ? ld_u(j, i + 1) : (T)0;
+        const T fv = in[m] ? ld_g((const T *)a.f + (long long)j * ld + i) : (T)0;
+        g[m] = EXACT ? fv : fv * (T)a.finvd;
+    }
+    const T hs = ty == 0 ? ld_u(j0 - 1, i) : (T)0;
+    const T hn = ty == BY - 1 ? ld_u(j0 + TY, i) : (T)0;
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+        const int me = (ty + m * BY + 1) * lw + tx + 1;
+        buf0[me] = v0[m];
+        buf1[me] = v0[m];
+        if (tx == 0) { buf0[me - 1] = hw[m]; buf1[me - 1] = hw[m]; }
+        if (tx == TX - 1) { buf0[me + 1] = he[m]; buf1[me + 1] = he[m]; }
+    }
+    if (ty == 0) { buf0[tx + 1] = hs; buf1[tx + 1] = hs; }
+    if (ty == BY - 1) { buf0[(TY + 1) * lw + tx + 1] = hn; buf1[(TY + 1) * lw + tx + 1] = hn; }
     __syncthreads();
     for (int s = 0; s < a.k; ++s) {
         const T *src = (s & 1) ? buf1 : buf0;
         T *dst = (s & 1) ? buf0 : buf1;
-        if (in) {
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+            if (!in[m]) continue;
+            const int me = (ty + m * BY + 1) * lw + tx + 1;
             const T old = src[me];
             const T W = src[me - 1], E = src[me + 1], Sv = src[me - lw], Nv = src[me + lw];
             T nv;
@@ -100,10 +117,10 @@ __global__ void __launch_bounds__(1024, 2) mg_smooth_kernel(const MgSmoothArgs a
                 acc = __dadd_rn(acc, __dmul_rn(a.cE, E));
                 acc = __dadd_rn(acc, __dmul_rn(a.cS, Sv));
                 acc = __dadd_rn(acc, __dmul_rn(a.cN, Nv));
-                const double jac = __dmul_rn(__dsub_rn(g, acc), a.invd);
+                const double jac = __dmul_rn(__dsub_rn(g[m], acc), a.invd);
                 nv = __dadd_rn(old, __dmul_rn(a.omega, __dsub_rn(jac, old)));
             } else {
-                T t = g;
+                T t = g[m];
                 t = fmaf(a.fN, Nv, t);
                 t = fmaf(a.fS, Sv, t);
                 t = fmaf(a.fE, E, t);
@@ -114,7 +131,12 @@ __global__ void __launch_bounds__(1024, 2) mg_smooth_kernel(const MgSmoothArgs a
         }
         __syncthreads();
     }
-    if (in) ((T *)a.uout)[q] = ((a.k & 1) ? buf1 : buf0)[me];
+    const T *fin = (a.k & 1) ? buf1 : buf0;
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+        const int j = j0 + ty + m * BY;
+        if (in[m]) ((T *)a.uout)[(long long)j * ld + i] = fin[(ty + m * BY + 1) * lw + tx + 1];
+    }
 }
 
 // f - A u at fine index q, in the oracle's order (binary64) or fused (binary32)
@@ -168,37 +190,45 @@ __global__ void __launch_bounds__(256) mg_restrict_kernel(const MgXferArgs x) {
     ((T *)x.ec)[qc] = (T)0;
 }
 
+// One thread per coarse cell (a, b), a in [0, ncx], b in [0, ncy]: the fine
+// points (2a+1 | 2a+2, 2b+1 | 2b+2) inside it, each with the oracle's formula
+// for its parity; a warp writes coalesced pairs of every fine row.
+template <typename T, bool EXACT>
+__device__ __forceinline__ T avg2(T x, T y) {
+    if constexpr (EXACT) return __dmul_rn(__dadd_rn(x, y), 0.5);
+    else return (x + y) * (T)0.5;
+}
+
 template <typename T, bool EXACT>
 __global__ void __launch_bounds__(256) mg_prolong_kernel(const MgXferArgs x) {
-    const int i = 1 + blockIdx.x * 32 + threadIdx.x, j = 1 + blockIdx.y * 8 + threadIdx.y;
-    if (i > x.nx || j > x.ny) return;
+    const int ca = blockIdx.x * 32 + threadIdx.x, cb = blockIdx.y * 8 + threadIdx.y;
+    if (ca > x.ncx || cb > x.ncy) return;
     const T *e = (const T *)x.ec;
-    const long long ldc = x.ldc;
-    const int a = (i - 1) / 2, b = (j - 1) / 2;
-    T v;
-    if (!(i & 1) && !(j & 1)) {
-        v = e[(long long)(j / 2) * ldc + i / 2];
-    } else if (!(j & 1)) {
-        const long long r = (long long)(j / 2) * ldc;
-        v = EXACT ? (T)__dmul_rn(__dadd_rn(e[r + a], e[r + a + 1]), 0.5) : (e[r + a] + e[r + a + 1]) * (T)0.5;
-    } else if (!(i & 1)) {
-        const long long r0 = (long long)b * ldc, r1 = r0 + ldc;
-        v = EXACT ? (T)__dmul_rn(__dadd_rn(e[r0 + i / 2], e[r1 + i / 2]), 0.5)
-                  : (e[r0 + i / 2] + e[r1 + i / 2]) * (T)0.5;
+    const long long r0 = (long long)cb * x.ldc, r1 = r0 + x.ldc;
+    const T e00 = e[r0 + ca], e10 = e[r0 + ca + 1], e01 = e[r1 + ca], e11 = e[r1 + ca + 1];
+    const int i1 = 2 * ca + 1, j1 = 2 * cb + 1;
+    const bool xe = ca < x.ncx, ye = cb < x.ncy;   // the even column / row exists
+    const T *ui = (const T *)x.u;
+    T *uo = (T *)x.uout;
+    auto put = [&](int ii, int jj, T v) {
+        const long long q = (long long)jj * x.ld + ii;
+        const T un = ui[q];
+        uo[q] = EXACT ? (T)__dadd_rn(un, v) : un + v;
+    };
+    // (odd, odd)
+    T s;
+    if constexpr (EXACT) {
+        double t = __dadd_rn(e00, e10);
+        t = __dadd_rn(t, e01);
+        t = __dadd_rn(t, e11);
+        s = __dmul_rn(t, 0.25);
     } else {
-        const long long r0 = (long long)b * ldc, r1 = r0 + ldc;
-        if constexpr (EXACT) {
-            double s = __dadd_rn(e[r0 + a], e[r0 + a + 1]);
-            s = __dadd_rn(s, e[r1 + a]);
-            s = __dadd_rn(s, e[r1 + a + 1]);
-            v = __dmul_rn(s, 0.25);
-        } else {
-            v = ((e[r0 + a] + e[r0 + a + 1]) + (e[r1 + a] + e[r1 + a + 1])) * (T)0.25;
-        }
+        s = ((e00 + e10) + (e01 + e11)) * (T)0.25;
     }
-    const long long q = (long long)j * x.ld + i;
-    const T un = ((const T *)x.u)[q];
-    ((T *)x.uout)[q] = EXACT ? (T)__dadd_rn(un, v) : un + v;
+    put(i1, j1, s);
+    if (xe) put(i1 + 1, j1, avg2<T, EXACT>(e10, e11));          // (even, odd)
+    if (ye) put(i1, j1 + 1, avg2<T, EXACT>(e01, e11));          // (odd, even)
+    if (xe && ye) put(i1 + 1, j1 + 1, e11);                     // (even, even)
 }
 
 MgSmoothArgs smooth_args(const MgLevel &L, const void *f, const void *uin, void *uout, int k, double omega,
@@ -227,11 +257,20 @@ void launch_smooth(hj_handle *h, int l, int cur, int tx, int ty, int k, double o
     const MgLevel &L = h->mg[l];
     void *buf[2] = {L.a, L.b};
     const MgSmoothArgs a = smooth_args(L, L.f, buf[cur], buf[1 - cur], k, omega, h->d.sigma_const);
-    const dim3 block(tx, ty), grid((L.nx + tx - 1) / tx, (L.ny + ty - 1) / ty);
+    // rows per thread: 4 (or 2) when the subdomain height allows, 1 otherwise
+    const int rpt = (ty % 4 == 0 && ty >= 8) ? 4 : (ty % 2 == 0 && ty >= 4) ? 2 : 1;
+    const dim3 block(tx, ty / rpt), grid((L.nx + tx - 1) / tx, (L.ny + ty - 1) / ty);
     const bool f64 = h->fam_outer == FAM_F64;
     const int smem = 2 * (tx + 2) * (ty + 2) * (f64 ? 8 : 4);
-    if (f64) mg_smooth_kernel<double, true><<<grid, block, smem, s>>>(a);
-    else mg_smooth_kernel<float, false><<<grid, block, smem, s>>>(a);
+#define HJ_MG_SMOOTH(T, EX)                                                            \
+    do {                                                                               \
+        if (rpt == 4) mg_smooth_kernel<T, EX, 4><<<grid, block, smem, s>>>(a);         \
+        else if (rpt == 2) mg_smooth_kernel<T, EX, 2><<<grid, block, smem, s>>>(a);    \
+        else mg_smooth_kernel<T, EX, 1><<<grid, block, smem, s>>>(a);                  \
+    } while (0)
+    if (f64) HJ_MG_SMOOTH(double, true);
+    else HJ_MG_SMOOTH(float, false);
+#undef HJ_MG_SMOOTH
 }
 
 MgXferArgs xfer_args(const hj_handle *h, int l) {
@@ -284,7 +323,7 @@ int record_level(hj_handle *h, int l, int cur, cudaStream_t s) {
     x.u = cur ? L.b : L.a;
     x.uout = flip ? (cur ? L.a : L.b) : const_cast<void *>(x.u);
     {
-        const dim3 g((L.nx + 31) / 32, (L.ny + 7) / 8), b(32, 8);
+        const dim3 g((Cc.nx + 1 + 31) / 32, (Cc.ny + 1 + 7) / 8), b(32, 8);   // coarse cells 0..ncx x 0..ncy
         if (f64) mg_prolong_kernel<double, true><<<g, b, 0, s>>>(x);
         else mg_prolong_kernel<float, false><<<g, b, 0, s>>>(x);
     }
