@@ -178,7 +178,10 @@ typedef struct {
                              k per size class                                   */
     int pipeline;         /* 2D cycles: 1 = TMA-pipelined kernel (CTAs walk tile
                              lists, next tile staged while the current one
-                             sweeps), 0 = one CTA per tile, -1 = automatic      */
+                             sweeps), 0 = one CTA per tile, -1 = automatic.
+                             3D: 1 = persistent warps that prefetch the next
+                             subdomain with cp.async; 0 and -1 = one warp per
+                             subdomain                                        */
     int tile_threads;     /* threads per subdomain (one warp per band of rows);
                              0 = the default for the tile shape; the built
                              combinations are listed by hj_tile_variants()      */

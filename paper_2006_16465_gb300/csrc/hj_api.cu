@@ -308,6 +308,13 @@ struct Plan {
     PpcArgs p[kPpcPeriod];
 };
 
+// 3D: whether the prefetching (persistent-warp, cp.async) kernel runs.  Only
+// on request (pipeline = 1): measured at 512^3 binary32 it is slower than the
+// one-warp-per-subdomain kernel (755 against 625 us a cycle at k = 1).
+bool use_pf3(const hj_handle *h) {
+    return h->k3 && h->d.dim == 3 && h->p.method == HJ_METHOD_HIER && h->p.pipeline == 1;
+}
+
 // Whether the TMA-pipelined kernel runs this plan's cycles.
 bool want_ppc(const hj_handle *h, const PpcKernelInfo *pi, bool classic) {
     if (classic || !pi || h->d.dim != 2 || overlapped(h) || h->d.coef) return false;
@@ -340,11 +347,25 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
             const Tile3Info *t3 = h->k3;
             const long long nsub = (long long)((nx + t3->tx - 1) / t3->tx) * ((ny + t3->ty - 1) / t3->ty) *
                                    ((h->d.nz + t3->tz - 1) / t3->tz);
-            pl->fn = t3->fn[res];
-            pl->grid = dim3((unsigned)((nsub + t3->nw - 1) / t3->nw));
+            const long long nblk = (nsub + t3->nw - 1) / t3->nw;
             pl->block = dim3(t3->threads);
+            pl->smem = 0;
+            if (use_pf3(h)) {
+                // persistent warps: at most the resident CTAs, each walking subdomains
+                pl->fn = t3->pf[res];
+                pl->smem = t3->pf_smem;
+                if (pl->smem > 48 * 1024)
+                    CKR(cudaFuncSetAttribute(pl->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->smem));
+                int occ = 0;
+                CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pl->fn, t3->threads, pl->smem));
+                if (occ < 1) return seterr(HJ_ERR_UNSUPPORTED, "3D prefetching kernel does not fit on an SM");
+                pl->grid = dim3((unsigned)std::min<long long>(nblk, (long long)occ * h->nsm));
+            } else {
+                pl->fn = t3->fn[res];
+                pl->grid = dim3((unsigned)nblk);
+            }
         }
-        pl->smem = 0;
+        if (classic) pl->smem = 0;
         pl->ppc = false;
         return HJ_OK;
     }
@@ -841,7 +862,7 @@ void fill_stats_config(const hj_handle *h, hj_stats *st, double t0) {
     st->tile_z = h->d.dim == 3 ? h->p.tile_z : 1;
     const PpcKernelInfo *pk = h->ir ? h->p_inner : h->p_outer;
     const bool ppc = want_ppc(h, pk, h->p.method == HJ_METHOD_CLASSIC);
-    st->pipeline_stages = ppc ? pk->stages : 0;
+    st->pipeline_stages = ppc ? pk->stages : use_pf3(h) ? 1 : 0;
     st->ctas_per_sm = ppc ? h->p.ctas_per_sm : 0;
     st->overlap_x = h->p.overlap_x;
     st->overlap_y = h->d.dim == 2 ? h->p.overlap_y : 0;
@@ -1034,8 +1055,7 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
         if (ir) return seterr(HJ_ERR_UNSUPPORTED, "3D: HJ_PREC_F64 or HJ_PREC_F32");
         if (p.overlap_x > 0 || p.overlap_y > 0) return seterr(HJ_ERR_UNSUPPORTED, "3D: no overlapping subdomains");
         if (p.in_place) return seterr(HJ_ERR_UNSUPPORTED, "3D: no in-place variant");
-        if (p.persistent == 1 || p.pipeline == 1)
-            return seterr(HJ_ERR_UNSUPPORTED, "3D runs on graphs (persistent and pipeline must not be 1)");
+        if (p.persistent == 1) return seterr(HJ_ERR_UNSUPPORTED, "3D runs on graphs (persistent must not be 1)");
         if (p.autotune != 0) return seterr(HJ_ERR_UNSUPPORTED, "3D: no autotuner");
         const double off = fabs(d.cW) + fabs(d.cE) + fabs(d.cS) + fabs(d.cN) + fabs(d.cB) + fabs(d.cT);
         const double dc = d.cD + d.sigma_const;

@@ -197,6 +197,203 @@ __global__ void __launch_bounds__(32 * NW) hier3d_kernel(const CycArgs a) {
     if constexpr (RES) reduce_grid_acc(a.red, acc);
 }
 
+// ---------------------------------------------------------------------------
+// Prefetching variant: persistent warps walk subdomains (warp g takes
+// g, g + G, g + 2G, ... for G warps in the grid), and while a warp sweeps one
+// subdomain in registers, cp.async copies the next one's box (subdomain +
+// halo, (TX+2) x (TY+2) x (TZ+2) values) and its f (TX x TY x TZ) into the
+// warp's shared buffers.  The sweep and its arithmetic are those of
+// hier3d_kernel, so the iterates are identical.  A box row starts at
+// x0 - 1 = bx TX, a multiple of 8 elements, in a row of pitch ld (a multiple
+// of 32 elements), so each row is copied as 16-byte chunks plus one chunk
+// for its last two elements; the part of a chunk beyond the ghost shell is
+// zero-filled without being read (cp.async's source size).
+// ---------------------------------------------------------------------------
+// copy `bytes` (<= BYTES) of src and zero-fill the rest of the BYTES at dst
+template <int BYTES>
+__device__ __forceinline__ void cp_async_part(void *dst, const void *src, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(BYTES), "r"(bytes)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <typename T, int LX, int RY, int RZ>
+struct Pf3Layout {
+    static constexpr int LY = 32 / LX, TX = LX, TY = LY * RY, TZ = RZ;
+    static constexpr int EPC = 16 / (int)sizeof(T);            // elements per 16-byte chunk
+    static constexpr int BX = TX + 2 * (EPC > 2 ? 2 : 1);      // box row pitch: 16-byte multiple, >= TX + 2
+    static constexpr int BYR = TY + 2, BZ = TZ + 2;
+    static constexpr int BOX = BX * BYR * BZ, FBOX = (TX + EPC) * TY * TZ, XH = 2 * TY * TZ;
+    static constexpr int PER_WARP = BOX + FBOX + XH;           // elements (a 16-byte multiple)
+    static constexpr int RCH = TX / EPC;                       // full chunks per row
+    static_assert(TX % EPC == 0 && (BX * (int)sizeof(T)) % 16 == 0 && (PER_WARP * (int)sizeof(T)) % 16 == 0,
+                  "16-byte rows");
+};
+
+template <typename S, typename T, int LX, int RY, int RZ, int NW, bool EXACT, bool RES>
+__global__ void __launch_bounds__(32 * NW) hier3d_pf_kernel(const CycArgs a) {
+    using L = Pf3Layout<T, LX, RY, RZ>;
+    constexpr int LY = L::LY, TX = L::TX, TY = L::TY, TZ = L::TZ, BX = L::BX, BYR = L::BYR;
+    constexpr unsigned FULL = 0xffffffffu;
+    static_assert(sizeof(S) == sizeof(T), "binary32 or binary64 storage");
+    if constexpr (RES) {
+        if (*(volatile int *)&a.red.ctl->done >= 0) return;
+    }
+    extern __shared__ __align__(16) unsigned char pf3_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *box = (T *)pf3_smem + (size_t)warp * L::PER_WARP;
+    T *fbox = box + L::BOX;
+    T *xh = fbox + L::FBOX;
+    const int lx = lane % LX, gy = lane / LX;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int nbx = (nx + TX - 1) / TX, nby = (ny + TY - 1) / TY, nbz = (nz + TZ - 1) / TZ;
+    const long long nsub = (long long)nbx * nby * nbz;
+    const long long G = (long long)gridDim.x * NW;
+    const long long ld = a.ld, ps = a.ps;
+    const S *__restrict__ uin = (const S *)a.uin;
+    const T *__restrict__ f = (const T *)a.f;
+    const Coef3<T> kc = make_coef3<T>(a);
+    typedef typename std::conditional<EXACT, double, T>::type Acc;
+    Acc acc = 0;
+    // origin (x0 - 1, y0 - 1, z0 - 1) of subdomain sub's box
+    auto origin = [&](long long sub, int &bx0, int &by0, int &bz0) {
+        bx0 = (int)(sub % nbx) * TX;
+        by0 = (int)((sub / nbx) % nby) * TY;
+        bz0 = (int)(sub / ((long long)nbx * nby)) * TZ;
+    };
+    constexpr int EPC = L::EPC, RCH = L::RCH, ES = (int)sizeof(T);
+    // bytes of a chunk of EPC elements starting at global x = gx that lie
+    // at or below x = xmax (0 if none)
+    auto part = [&](int gx, int n, int xmax) -> int {
+        const int m = xmax - gx + 1;
+        return (m <= 0 ? 0 : (m >= n ? n : m)) * ES;
+    };
+    auto prefetch = [&](long long sub) {
+        int bx0, by0, bz0;
+        origin(sub, bx0, by0, bz0);
+        // u box: rows (yy, zz) of TX + 2 elements from x = bx0: RCH 16-byte
+        // chunks and a tail chunk holding x = bx0 + TX and bx0 + TX + 1
+        constexpr int RQ = RCH + 1, NQ = BYR * L::BZ * RQ;
+        for (int q = lane; q < NQ; q += 32) {
+            const int j = q % RQ, rho = q / RQ, yy = rho % BYR, zz = rho / BYR;
+            const int gyy = by0 + yy, gz = bz0 + zz, gx = bx0 + j * EPC;
+            const bool row_ok = gyy <= ny + 1 && gz <= nz + 1;
+            const int bytes = row_ok ? part(gx, j < RCH ? EPC : 2, nx + 1) : 0;
+            const S *src = uin + (bytes ? (long long)gz * ps + (long long)gyy * ld + gx : 0);
+            T *dst = box + rho * BX + j * EPC;
+            if (j < RCH) cp_async_part<16>(dst, src, bytes);
+            else cp_async_part<2 * sizeof(T)>(dst, src, bytes);
+        }
+        // f box: TX x TY x TZ interior values, RCH chunks per row from x0 = bx0 + 1
+        // (not 16-byte aligned: element-sized copies would be too many, so the
+        // row is fetched from bx0, whose chunk 0 carries x0 - 1 .. x0 + EPC - 2,
+        // into a scratch row pitch of TX + EPC and read at offset 1)
+        for (int q = lane; q < TY * TZ * (RCH + 1); q += 32) {
+            const int j = q % (RCH + 1), rho = q / (RCH + 1), yy = rho % TY, zz = rho / TY;
+            const int gyy = by0 + 1 + yy, gz = bz0 + 1 + zz, gx = bx0 + j * EPC;
+            const bool row_ok = gyy <= ny && gz <= nz;
+            const int bytes = row_ok ? part(gx, EPC, nx) : 0;
+            const T *src = f + (bytes ? (long long)gz * ps + (long long)gyy * ld + gx : 0);
+            cp_async_part<16>(fbox + rho * (TX + EPC) + j * EPC, src, bytes);
+        }
+        cp_async_commit();
+    };
+    long long sub = (long long)blockIdx.x * NW + warp;
+    if (sub < nsub) prefetch(sub);
+    for (; sub < nsub; sub += G) {   // warp-uniform
+        cp_async_wait_all();
+        __syncwarp();
+        int bx0, by0, bz0;
+        origin(sub, bx0, by0, bz0);
+        const int x0 = bx0 + 1, y0 = by0 + 1, z0 = bz0 + 1;
+        const int x = x0 + lx, yl = y0 + gy * RY;
+        T u[RY][RZ], g[RY][RZ], sS[RZ], sN[RZ], hB[RY], hT[RY];
+        auto B = [&](int zz, int yy, int xx) -> T { return box[(zz * BYR + yy) * BX + xx]; };
+#pragma unroll
+        for (int z = 0; z < RZ; ++z) {
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                u[r][z] = B(z + 1, gy * RY + r + 1, lx + 1);
+                const T fv = fbox[(z * TY + gy * RY + r) * (TX + EPC) + lx + 1];
+                g[r][z] = EXACT ? fv : fv * kc.invd;
+            }
+            sS[z] = B(z + 1, 0, lx + 1);
+            sN[z] = B(z + 1, TY + 1, lx + 1);
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            hB[r] = B(0, gy * RY + r + 1, lx + 1);
+            hT[r] = B(TZ + 1, gy * RY + r + 1, lx + 1);
+        }
+        for (int t = lane; t < TY * TZ; t += 32) {
+            const int yy = t % TY, zz = t / TY;
+            xh[t] = B(zz + 1, yy + 1, 0);
+            xh[TY * TZ + t] = B(zz + 1, yy + 1, TX + 1);
+        }
+        __syncwarp();
+        // the box is in registers (and xh): copy the next subdomain in
+        if (sub + G < nsub) prefetch(sub + G);
+        const bool full = x0 + TX - 1 <= nx && y0 + TY - 1 <= ny && z0 + TZ - 1 <= nz;
+        for (int s = 0; s < a.k; ++s) {
+            T prev[RY];
+#pragma unroll
+            for (int r = 0; r < RY; ++r) prev[r] = hB[r];
+#pragma unroll
+            for (int z = 0; z < RZ; ++z) {
+                T up = sS[z], dn = sN[z];
+                if constexpr (LY > 1) {
+                    const T a_up = __shfl_up_sync(FULL, u[RY - 1][z], LX);
+                    const T a_dn = __shfl_down_sync(FULL, u[0][z], LX);
+                    if (gy > 0) up = a_up;
+                    if (gy < LY - 1) dn = a_dn;
+                }
+                T nv[RY];
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                    const T c = u[r][z];
+                    T Wv = __shfl_up_sync(FULL, c, 1, LX);
+                    T Ev = __shfl_down_sync(FULL, c, 1, LX);
+                    const int hy = gy * RY + r + TY * z;
+                    if (lx == 0) Wv = xh[hy];
+                    if (lx == LX - 1) Ev = xh[TY * TZ + hy];
+                    const T Sv = r > 0 ? u[r - 1][z] : up;
+                    const T Nv = r < RY - 1 ? u[r + 1][z] : dn;
+                    const T Tv = z < RZ - 1 ? u[r][z + 1] : hT[r];
+                    T res = 0;
+                    const T v = point_update3<T, EXACT, RES>(kc, g[r][z], Wv, Ev, Sv, Nv, prev[r], Tv, c, res);
+                    const bool in = full || (x <= nx && yl + r <= ny && z0 + z <= nz);
+                    nv[r] = in ? v : c;
+                    if constexpr (RES) {
+                        if (s == 0 && in) acc += (Acc)res * (Acc)res;
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                    prev[r] = u[r][z];
+                    u[r][z] = nv[r];
+                }
+            }
+        }
+        S *uo = (S *)a.uout;
+#pragma unroll
+        for (int z = 0; z < RZ; ++z)
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                const int yy = yl + r, zz = z0 + z;
+                if (x <= nx && yy <= ny && zz <= nz)
+                    st_s<S, T>(uo + (long long)zz * ps + (long long)yy * ld + x, u[r][z]);
+            }
+        __syncwarp();   // every lane is done with xh before the next staging
+    }
+    cp_async_wait_all();
+    if constexpr (RES) reduce_grid_acc(a.red, acc);
+}
+
 // Classic global-memory Jacobi in 3D (Section 3.2's comparator with the
 // seven-point stencil): one thread per point, block (32, 8), one z plane per
 // blockIdx.z.  Same update arithmetic and fused residual as hier3d_kernel.
@@ -231,7 +428,11 @@ __global__ void __launch_bounds__(256) classic3d_kernel(const CycArgs a) {
 
 }  // namespace hj
 
-// registry entry: tile (TX, TY, TZ), threads, kernels without / with the fused residual
-#define HJ_K3D(S, T, LX, RY, RZ, NW, EX)                                                        \
-    {(LX), (32 / (LX)) * (RY), (RZ), 32 * (NW), (NW),                                         \
-     {hj::hier3d_kernel<S, T, LX, RY, RZ, NW, EX, false>, hj::hier3d_kernel<S, T, LX, RY, RZ, NW, EX, true>}}
+// registry entry: tile (TX, TY, TZ), threads, warps per CTA, kernels without /
+// with the fused residual, the prefetching kernels and their shared memory
+#define HJ_K3D(S, T, LX, RY, RZ, NW, EX)                                                              \
+    {(LX), (32 / (LX)) * (RY), (RZ), 32 * (NW), (NW),                                               \
+     {hj::hier3d_kernel<S, T, LX, RY, RZ, NW, EX, false>, hj::hier3d_kernel<S, T, LX, RY, RZ, NW, EX, true>}, \
+     {hj::hier3d_pf_kernel<S, T, LX, RY, RZ, NW, EX, false>,                                         \
+      hj::hier3d_pf_kernel<S, T, LX, RY, RZ, NW, EX, true>},                                         \
+     (int)((NW) * hj::Pf3Layout<T, LX, RY, RZ>::PER_WARP * sizeof(T))}

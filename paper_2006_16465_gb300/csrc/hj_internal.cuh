@@ -352,6 +352,8 @@ const VcKernelInfo *vc_kernels_f32();
 struct Tile3Info {
     int tx, ty, tz, threads, nw;
     CycKernel fn[2];
+    CycKernel pf[2];   // prefetching persistent variant: grid <= resident CTAs, dynamic smem pf_smem
+    int pf_smem;
 };
 const Tile3Info *tiles3d_f64(int *n);
 const Tile3Info *tiles3d_f32(int *n);

@@ -33,16 +33,20 @@ def _shapes(prec):
     return hj.hj_tile_shapes3d(hj.PRECISIONS[prec])
 
 
+@pytest.mark.parametrize("pipeline", [0, 1])
 @pytest.mark.parametrize("shape,sigma,asym", [((37, 21, 13), "none", True), ((32, 16, 16), "const", False),
                                                ((50, 9, 20), "const", True)])
-def test_f64_3d_cycles_match_oracle(shape, sigma, asym):
+def test_f64_3d_cycles_match_oracle(shape, sigma, asym, pipeline):
+    """pipeline = 1: persistent warps prefetching the next subdomain's box
+    with cp.async (small grids: a warp walks several subdomains); 0: one
+    warp per subdomain, loads issued directly."""
     torch = _torch()
     nx, ny, nz = shape
     p = W.random_bc_problem3d(nx, ny, nz, seed=nx + ny + nz, sigma_kind=sigma, asym=asym)
     for tile in _shapes("f64"):
         for k, ncyc in [(1, 3), (5, 2), (16, 2)]:
             s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], tile_z=tile[2], k=k, precision="f64",
-                           fixed_cycles=ncyc)
+                           fixed_cycles=ncyc, pipeline=pipeline)
             u = to_dev(p.u0, 3, torch.float64)
             s.solve(to_dev(p.f, 3, torch.float64), u)
             ref = oracle.run_fixed(p.st, p.f, p.u0, ncyc, tile[0], tile[1], k, tz=tile[2])
@@ -62,15 +66,15 @@ def test_f64_3d_classic_sweeps_match_oracle():
     s.close()
 
 
-@pytest.mark.parametrize("method,k", [("hier", 8), ("hier", 32), ("classic", 1)])
-def test_f64_3d_convergence_matches_oracle(method, k):
+@pytest.mark.parametrize("method,k,pipeline", [("hier", 8, 0), ("hier", 32, 0), ("hier", 8, 1), ("classic", 1, 0)])
+def test_f64_3d_convergence_matches_oracle(method, k, pipeline):
     """Same stopping cycle, iterate and residual history as the oracle."""
     torch = _torch()
     p = W.random_bc_problem3d(40, 24, 18, seed=9, sigma_kind="const", asym=True)
     tol = 1e-8
     tile = (16, 4, 8)
     s = gpu_solver(p, method=method, tile_x=tile[0], tile_y=tile[1], tile_z=tile[2], k=k, precision="f64",
-                   tol=tol, check_every=16)
+                   tol=tol, check_every=16, pipeline=pipeline, max_cycles=100000)
     u = to_dev(p.u0, 3, torch.float64)
     out = s.solve(to_dev(p.f, 3, torch.float64), u, history=100000)
     uo, c, status, hist = oracle.solve(p.st, p.f, p.u0, tol, 10 ** 7, tile[0], tile[1], k,
@@ -88,14 +92,16 @@ def test_f32_3d_cycles_close_to_oracle_and_solve_converges():
     torch = _torch()
     p = W.random_bc_problem3d(70, 33, 21, seed=23, sigma_kind="const", asym=True)
     for tile in _shapes("f32"):
-        s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], tile_z=tile[2], k=6, precision="f32", fixed_cycles=4)
-        u = to_dev(p.u0, 3, torch.float32)
-        s.solve(to_dev(p.f, 3, torch.float32), u)
-        ref = oracle.run_fixed(p.st, p.f, p.u0, 4, tile[0], tile[1], 6, tz=tile[2])
-        assert rel_max(to_host(u, 70), ref) <= 1e-5, tile
-        s.close()
+        for pipeline in (0, 1):
+            s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], tile_z=tile[2], k=6, precision="f32", fixed_cycles=4,
+                           pipeline=pipeline)
+            u = to_dev(p.u0, 3, torch.float32)
+            s.solve(to_dev(p.f, 3, torch.float32), u)
+            ref = oracle.run_fixed(p.st, p.f, p.u0, 4, tile[0], tile[1], 6, tz=tile[2])
+            assert rel_max(to_host(u, 70), ref) <= 1e-5, (tile, pipeline)
+            s.close()
     q = W.poisson3d_uniform(48, 40, 36, seed=3)
-    s = gpu_solver(q, precision="f32", k=8, tol=1e-4, check_every=8)
+    s = gpu_solver(q, precision="f32", k=8, tol=1e-4, check_every=8, max_cycles=100000)
     u = to_dev(q.u0, 3, torch.float32)
     out = s.solve(to_dev(q.f, 3, torch.float32), u)
     assert out["status"] == 0 and (out["tile_x"], out["tile_y"], out["tile_z"]) == _shapes("f32")[0]
