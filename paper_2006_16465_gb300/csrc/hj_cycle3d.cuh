@@ -6,8 +6,8 @@
 //   * LX lanes span x (TX = LX), LY = 32 / LX lane groups span y, and every
 //     lane holds RY consecutive rows x RZ planes of its x column in registers:
 //     TY = LY * RY, TZ = RZ;
-//   * x neighbours come from lane shuffles within the LX-lane segment, the
-//     two x-halo columns from a small shared buffer (read by the edge lanes);
+//   * x neighbours come from lane shuffles within the LX-lane segment; the
+//     two edge lanes of a segment hold the x-halo column in registers;
 //   * y neighbours are registers of the same lane, or the neighbouring lane
 //     group's edge row (one shuffle pair per plane), or the frozen y-halo rows;
 //   * z neighbours are registers: the sweep walks the planes in order and keeps
@@ -94,7 +94,6 @@ __global__ void __launch_bounds__(32 * NW) hier3d_kernel(const CycArgs a) {
     if constexpr (RES) {
         if (*(volatile int *)&a.red.ctl->done >= 0) return;
     }
-    __shared__ T xhalo[NW][2][TY * TZ];   // x-halo columns (x0 - 1, x0 + TX), index y + TY * z
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lx = lane % LX, gy = lane / LX;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -112,38 +111,61 @@ __global__ void __launch_bounds__(32 * NW) hier3d_kernel(const CycArgs a) {
         const long long ld = a.ld, ps = a.ps;
         const S *__restrict__ uin = (const S *)a.uin;
         const T *__restrict__ f = (const T *)a.f;
-        auto ld_u = [&](int xx, int yy, int zz) -> T {
-            const bool ok = xx <= nx + 1 && yy <= ny + 1 && zz <= nz + 1;
-            return ok ? ld_s<S, T>(uin + (long long)zz * ps + (long long)yy * ld + xx) : (T)0;
-        };
         const Coef3<T> kc = make_coef3<T>(a);
-        // stage: every global load of this lane, then the x-halo columns
-        T u[RY][RZ], g[RY][RZ], sS[RZ], sN[RZ], hB[RY], hT[RY];
+        // every point of the subdomain inside the grid (so its halo is inside
+        // the ghost shell): one base pointer, fixed offsets, no checks
+        const bool full = x0 + TX - 1 <= nx && y0 + TY - 1 <= ny && z0 + TZ - 1 <= nz;   // warp-uniform
+        // stage: u, f/d, the y- and z-halo values and, on the two edge lanes of
+        // each x segment, the x-halo column (xh: W on lane 0, E on lane LX-1)
+        T u[RY][RZ], g[RY][RZ], sS[RZ], sN[RZ], hB[RY], hT[RY], xh[RY][RZ];
+        const int xo = lx == 0 ? -1 : (lx == LX - 1 ? 1 : 0);   // x-halo offset of this lane (0: none)
+        if (full) {
+            const long long o = (long long)z0 * ps + (long long)yl * ld + x;
+            const S *bu = uin + o;
+            const T *bf = f + o;
 #pragma unroll
-        for (int z = 0; z < RZ; ++z) {
+            for (int z = 0; z < RZ; ++z) {
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                    const long long d = z * ps + r * ld;
+                    u[r][z] = ld_s<S, T>(bu + d);
+                    const T fv = __ldg(bf + d);
+                    g[r][z] = EXACT ? fv : fv * kc.invd;
+                    xh[r][z] = xo ? ld_s<S, T>(bu + d + xo) : (T)0;
+                }
+                sS[z] = gy == 0 ? ld_s<S, T>(bu + z * ps - ld) : (T)0;
+                sN[z] = gy == LY - 1 ? ld_s<S, T>(bu + z * ps + RY * ld) : (T)0;
+            }
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
-                const int yy = yl + r, zz = z0 + z;
-                u[r][z] = ld_u(x, yy, zz);
-                const bool in = x <= nx && yy <= ny && zz <= nz;
-                const T fv = in ? __ldg(f + (long long)zz * ps + (long long)yy * ld + x) : (T)0;
-                g[r][z] = EXACT ? fv : fv * kc.invd;
+                hB[r] = ld_s<S, T>(bu - ps + r * ld);
+                hT[r] = ld_s<S, T>(bu + TZ * ps + r * ld);
             }
-            sS[z] = gy == 0 ? ld_u(x, y0 - 1, z0 + z) : (T)0;
-            sN[z] = gy == LY - 1 ? ld_u(x, y0 + TY, z0 + z) : (T)0;
-        }
+        } else {
+            auto ld_u = [&](int xx, int yy, int zz) -> T {
+                const bool ok = xx <= nx + 1 && yy <= ny + 1 && zz <= nz + 1;
+                return ok ? ld_s<S, T>(uin + (long long)zz * ps + (long long)yy * ld + xx) : (T)0;
+            };
 #pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            hB[r] = ld_u(x, yl + r, z0 - 1);
-            hT[r] = ld_u(x, yl + r, z0 + TZ);
+            for (int z = 0; z < RZ; ++z) {
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                    const int yy = yl + r, zz = z0 + z;
+                    u[r][z] = ld_u(x, yy, zz);
+                    const bool in = x <= nx && yy <= ny && zz <= nz;
+                    const T fv = in ? __ldg(f + (long long)zz * ps + (long long)yy * ld + x) : (T)0;
+                    g[r][z] = EXACT ? fv : fv * kc.invd;
+                    xh[r][z] = xo ? ld_u(x + xo, yy, zz) : (T)0;
+                }
+                sS[z] = gy == 0 ? ld_u(x, y0 - 1, z0 + z) : (T)0;
+                sN[z] = gy == LY - 1 ? ld_u(x, y0 + TY, z0 + z) : (T)0;
+            }
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                hB[r] = ld_u(x, yl + r, z0 - 1);
+                hT[r] = ld_u(x, yl + r, z0 + TZ);
+            }
         }
-        for (int t = lane; t < TY * TZ; t += 32) {
-            const int yy = y0 + t % TY, zz = z0 + t / TY;
-            xhalo[warp][0][t] = ld_u(x0 - 1, yy, zz);
-            xhalo[warp][1][t] = ld_u(x0 + TX, yy, zz);
-        }
-        __syncwarp();
-        const bool full = x0 + TX - 1 <= nx && y0 + TY - 1 <= ny && z0 + TZ - 1 <= nz;   // warp-uniform
         for (int s = 0; s < a.k; ++s) {
             T prev[RY];   // old values of the plane below
 #pragma unroll
@@ -163,9 +185,8 @@ __global__ void __launch_bounds__(32 * NW) hier3d_kernel(const CycArgs a) {
                     const T c = u[r][z];
                     T Wv = __shfl_up_sync(FULL, c, 1, LX);
                     T Ev = __shfl_down_sync(FULL, c, 1, LX);
-                    const int hy = gy * RY + r + TY * z;
-                    if (lx == 0) Wv = xhalo[warp][0][hy];
-                    if (lx == LX - 1) Ev = xhalo[warp][1][hy];
+                    if (lx == 0) Wv = xh[r][z];
+                    if (lx == LX - 1) Ev = xh[r][z];
                     const T Sv = r > 0 ? u[r - 1][z] : up;
                     const T Nv = r < RY - 1 ? u[r + 1][z] : dn;
                     const T Tv = z < RZ - 1 ? u[r][z + 1] : hT[r];
@@ -186,13 +207,22 @@ __global__ void __launch_bounds__(32 * NW) hier3d_kernel(const CycArgs a) {
         }
         // write back this lane's interior points
         S *uo = (S *)a.uout;
+        if (full) {
+            S *bo = uo + (long long)z0 * ps + (long long)yl * ld + x;
 #pragma unroll
-        for (int z = 0; z < RZ; ++z)
+            for (int z = 0; z < RZ; ++z)
 #pragma unroll
-            for (int r = 0; r < RY; ++r) {
-                const int yy = yl + r, zz = z0 + z;
-                if (x <= nx && yy <= ny && zz <= nz) st_s<S, T>(uo + (long long)zz * ps + (long long)yy * ld + x, u[r][z]);
-            }
+                for (int r = 0; r < RY; ++r) st_s<S, T>(bo + z * ps + r * ld, u[r][z]);
+        } else {
+#pragma unroll
+            for (int z = 0; z < RZ; ++z)
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                    const int yy = yl + r, zz = z0 + z;
+                    if (x <= nx && yy <= ny && zz <= nz)
+                        st_s<S, T>(uo + (long long)zz * ps + (long long)yy * ld + x, u[r][z]);
+                }
+        }
     }
     if constexpr (RES) reduce_grid_acc(a.red, acc);
 }
