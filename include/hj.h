@@ -345,7 +345,9 @@ HJ_API const char *hj_last_error(void);
  * 8 subdomains per SM, or pipeline = 1), every mode then measures its launch
  * shapes for the chosen subdomain and k (threads per subdomain, copy stages,
  * CTAs per SM) and writes the fastest into tile_threads, pipeline_stages and
- * ctas_per_sm; params->autotune = 3 does only that. */
+ * ctas_per_sm; params->autotune = 3 does only that.  1D and 2D grids with
+ * constant coefficients and hierarchical cycles only: a 3D descriptor, per-point
+ * coefficients or HJ_METHOD_MG give HJ_ERR_UNSUPPORTED before any GPU work. */
 HJ_API int hj_autotune(const hj_desc *desc, hj_params *params, double *predicted_ms);
 
 /* Runs params->fixed_cycles cycles (hierarchical, or classic sweeps with

@@ -338,6 +338,9 @@ int tune_launch(const hj_desc &d, hj_params *p) {
 extern "C" int hj_autotune(const hj_desc *desc, hj_params *params, double *predicted_ms) {
     if (!desc || !params) return seterr(HJ_ERR_INVALID_ARG, "desc and params must be non-NULL");
     const hj_desc &d = *desc;
+    if (d.dim != 1 && d.dim != 2) return seterr(HJ_ERR_UNSUPPORTED, "the autotuner covers 1D and 2D grids");
+    if (d.coef) return seterr(HJ_ERR_UNSUPPORTED, "the autotuner covers constant neighbour coefficients");
+    if (params->method == HJ_METHOD_MG) return seterr(HJ_ERR_UNSUPPORTED, "the autotuner tunes hierarchical cycles");
     if (params->autotune == 3) {
         // launch shape only: tile_x, tile_y and k are the caller's
         if (predicted_ms) *predicted_ms = -1.0;

@@ -129,3 +129,16 @@ def test_struct_layouts_match_the_header(tmp_path, hj):
         assert got[(S.__name__, "size")] == C.sizeof(S), S.__name__
         for name, _ in S._fields_:
             assert got[(S.__name__, name)] == getattr(S, name).offset, (S.__name__, name)
+
+
+def test_autotune_refuses_what_it_does_not_tune(hj):
+    """3D descriptors, per-point coefficients and multigrid are refused
+    before any GPU work."""
+    import ctypes as C
+    d3 = hj.make_desc(3, 16, 16, 32, -1, -1, -1, -1, 6.0, nz=8, cB=-1, cT=-1)
+    dc = hj.make_desc(2, 16, 16, 32, -1, -1, -1, -1, 4.0)
+    dc.coef = 4096   # never dereferenced: the refusal comes first
+    d2 = hj.make_desc(2, 15, 15, 32, -1, -1, -1, -1, 4.0)
+    for d, prm in [(d3, hj.make_params(autotune=1)), (dc, hj.make_params(autotune=1)),
+                   (d2, hj.make_params(autotune=1, method="mg"))]:
+        assert hj.lib().hj_autotune(C.byref(d), C.byref(prm), None) == hj.HJ_ERR_UNSUPPORTED
