@@ -380,6 +380,21 @@ class Solver:
             pass
 
 
+def solve(stencil, f, u, sigma=None, coef=None, stream=None, history: int = 0, **params):
+    """One call: create a handle for this stencil and parameters, solve A u = f
+    in place (u: initial guess with the Dirichlet ghost ring -> solution),
+    destroy the handle, return the hj_stats fields as a dict (plus 'status').
+    f and u are padded device grids (``grid_from``); sigma / coef as for
+    ``Solver``.  For repeated solves keep a ``Solver``: creation validates the
+    problem, allocates the workspace and captures graphs once."""
+    dtype = f.dtype
+    s = Solver(stencil, sigma=sigma, coef=coef, dtype=dtype, **params)
+    try:
+        return s.solve(f, u, stream=stream, history=history)
+    finally:
+        s.close()
+
+
 def _stats_dict(st: hj_stats, hbuf):
     d = {k: getattr(st, k) for k, _ in hj_stats._fields_ if k != "history"}
     if hbuf is not None:

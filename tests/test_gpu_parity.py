@@ -796,3 +796,19 @@ def test_in_place_refinement_and_1d():
     assert out["status"] == 0
     assert oracle.residual(p.st, p.f, to_host(u, 512)) <= 1e-6 * oracle.residual(p.st, p.f, p.u0) * 1.0001
     s.close()
+
+
+def test_one_call_solve_equals_solver():
+    """hj.solve (create, solve, destroy) gives the Solver's iterate."""
+    import paper_2006_16465_gb300 as hj
+    torch = _torch()
+    p = W.random_bc_problem(2, 70, 45, seed=31, sigma_kind="const", asym=True)
+    f = to_dev(p.f, 2, torch.float64)
+    u1 = to_dev(p.u0, 2, torch.float64)
+    out = hj.solve(p.st, f, u1, precision="f64", tile_x=32, tile_y=32, k=8, tol=1e-9, max_cycles=100000)
+    s = gpu_solver(p, precision="f64", tile_x=32, tile_y=32, k=8, tol=1e-9, max_cycles=100000)
+    u2 = to_dev(p.u0, 2, torch.float64)
+    out2 = s.solve(f, u2)
+    s.close()
+    assert out["status"] == 0 and out["cycles"] == out2["cycles"]
+    assert torch.equal(u1, u2)
