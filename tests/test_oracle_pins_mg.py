@@ -96,18 +96,22 @@ def test_weighted_cycle_with_omega_one_is_the_plain_cycle():
     np.testing.assert_allclose(a, b, rtol=0, atol=1e-13 * np.abs(b).max())
 
 
+@pytest.mark.parametrize("shape", [(7, 7), (11, 5), (5, 9)])
 @pytest.mark.parametrize("pre,post,k,omega", [(1, 1, 2, 0.8), (2, 1, 3, 0.6), (0, 2, 1, 0.8)])
-def test_two_level_cycle_is_the_dense_affine_map(pre, post, k, omega):
+def test_two_level_cycle_is_the_dense_affine_map(pre, post, k, omega, shape):
     """Smooth (damped Jacobi on one subdomain), restrict the residual with
     R = P^T / 4, solve the rediscretised coarse system exactly, prolongate,
-    smooth again."""
-    p = W.random_bc_problem(2, 7, 7, seed=6, sigma_kind="const", asym=True)
+    smooth again.  Rectangular grids with a non-symmetric stencil catch an x/y
+    or W/E mix-up in any step."""
+    nx, ny = shape
+    p = W.random_bc_problem(2, nx, ny, seed=6 + nx, sigma_kind="const", asym=True)
     st = p.st
     A, b = dense2d(st, p.f, p.u0)
     d = np.diag(A)
-    P = dense_prolongation(7, 7)
+    P = dense_prolongation(nx, ny)
     cst = oracle.mg_coarse_stencil(st)
-    Ac, _ = dense2d(cst, np.zeros((5, 5)), np.zeros((5, 5)))
+    ncx, ncy = (nx - 1) // 2, (ny - 1) // 2
+    Ac, _ = dense2d(cst, np.zeros((ncy + 2, ncx + 2)), np.zeros((ncy + 2, ncx + 2)))
 
     def smooth(x, cycles):
         for _ in range(cycles * k):
@@ -117,7 +121,7 @@ def test_two_level_cycle_is_the_dense_affine_map(pre, post, k, omega):
     x = smooth(interior(p.u0), pre)
     ec = np.linalg.solve(Ac, 0.25 * P.T @ (b - A @ x))
     x = smooth(x + P @ ec, post)
-    got = oracle.mg_vcycle(st, p.f, p.u0, 2, pre, post, 7, 7, k, omega, coarse_k=200, coarse_cycles=2)
+    got = oracle.mg_vcycle(st, p.f, p.u0, 2, pre, post, nx, ny, k, omega, coarse_k=400, coarse_cycles=2)
     np.testing.assert_allclose(interior(got), x, rtol=0, atol=1e-12 * np.abs(x).max())
     assert np.array_equal(got[0], p.u0[0]) and np.array_equal(got[:, -1], p.u0[:, -1])
 
@@ -140,3 +144,32 @@ def test_vcycle_contracts_poisson_and_reaches_the_dense_solution():
     _, c2, s2, h2 = oracle.mg_solve(q.st, q.f, q.u0, 1e-10, 100, oracle.mg_max_levels(127, 127), 2, 2, 32, 32,
                                     2, 0.8, hist_cap=100)
     assert s2 == 0 and (h2[1:c2 + 1] / h2[:c2]).max() < 0.15
+
+
+def test_two_level_cycle_with_tiles_equals_dense_blockwise_smoothing():
+    """With 4 x 3 subdomains the smoothing cycle is damped Jacobi on each
+    block with its halo frozen at the cycle start: built densely here block
+    by block, then the same two-level map."""
+    nx, ny, tx, ty, k, omega = 9, 7, 4, 3, 3, 0.7
+    p = W.random_bc_problem(2, nx, ny, seed=21, sigma_kind="const", asym=True)
+    st = p.st
+    A, b = dense2d(st, p.f, p.u0)
+    d = np.diag(A)
+    P = dense_prolongation(nx, ny)
+    cst = oracle.mg_coarse_stencil(st)
+    Ac, _ = dense2d(cst, np.zeros((5, 6)), np.zeros((5, 6)))
+    blk = np.array([((j // ty) * 100 + (i // tx)) for j in range(ny) for i in range(nx)])
+    same = blk[:, None] == blk[None, :]
+    Ain, Aout = np.where(same, A, 0.0), np.where(same, 0.0, A)
+
+    def cycle(x):
+        x0 = x.copy()
+        for _ in range(k):   # neighbours in other blocks stay at x0
+            x = x + omega * (b - Ain @ x - Aout @ x0) / d
+        return x
+
+    x = cycle(interior(p.u0))
+    ec = np.linalg.solve(Ac, 0.25 * P.T @ (b - A @ x))
+    x = cycle(x + P @ ec)
+    got = oracle.mg_vcycle(st, p.f, p.u0, 2, 1, 1, tx, ty, k, omega, coarse_k=400, coarse_cycles=2)
+    np.testing.assert_allclose(interior(got), x, rtol=0, atol=1e-12 * np.abs(x).max())
