@@ -145,3 +145,26 @@ def test_3d_discrete_solution_is_a_fixed_point_and_solve_reaches_it():
     np.testing.assert_allclose(u, us, rtol=0, atol=1e-9 * np.abs(us).max())
     # the history is the residual of every iterate
     assert hist[0] == pytest.approx(oracle.residual(p.st, p.f, p.u0), rel=1e-15)
+
+
+@pytest.mark.parametrize("tile,k", [((3, 2, 2), 3), ((4, 3, 5), 2), ((2, 5, 1), 4)])
+def test_3d_cycle_at_finite_k_is_blockwise_jacobi_with_frozen_halos(tile, k):
+    """A cycle is k Jacobi steps on every subdomain, its neighbours in other
+    subdomains (and the ghost shell) held at the cycle's input: built densely
+    here block by block (ragged last blocks included)."""
+    nx, ny, nz = 7, 5, 6
+    tx, ty, tz = tile
+    p = W.random_bc_problem3d(nx, ny, nz, seed=30 + k, sigma_kind="field", asym=True)
+    A, b = dense_system3d(p.st, p.f, p.u0)
+    d = np.diag(A)
+    blk = np.array([((z // tz) * 10000 + (y // ty) * 100 + x // tx)
+                    for z in range(nz) for y in range(ny) for x in range(nx)])
+    same = blk[:, None] == blk[None, :]
+    off_in = np.where(same, A, 0.0) - np.diag(d)
+    off_out = np.where(same, 0.0, A)
+    x0 = interior_vec(p.u0)
+    x = x0.copy()
+    for _ in range(k):
+        x = (b - off_in @ x - off_out @ x0) / d
+    got = oracle.hier_cycle(p.st, p.f, p.u0, tx, ty, k, tz=tz)
+    np.testing.assert_allclose(interior_vec(got), x, rtol=0, atol=1e-12 * np.abs(x).max())
