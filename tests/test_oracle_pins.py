@@ -601,3 +601,30 @@ def test_variable_coefficients_large_k_and_fixed_point_2d():
     ex = u0.copy()
     ex[1:-1, 1:-1] = np.linalg.solve(A, b).reshape(st.ny, st.nx)
     np.testing.assert_allclose(oracle.hier_cycle(st, f, ex, 5, 4, 6), ex, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim,nx,ny,tx,ty,k,vc", [(2, 11, 7, 4, 3, 3, False), (2, 9, 10, 5, 4, 2, True),
+                                                  (1, 23, 2, 6, 1, 4, False), (1, 17, 3, 5, 1, 3, True)])
+def test_cycle_at_finite_k_is_blockwise_jacobi_with_frozen_halos(dim, nx, ny, tx, ty, k, vc):
+    """A hierarchical cycle is k Jacobi steps on every subdomain with its
+    neighbours in other subdomains (and the ghost ring) held at the cycle's
+    input (Sections 3.3, 4.1): built densely here block by block, ragged last
+    blocks included, for constant and per-point coefficients."""
+    if vc:
+        p = W.variable_coef_problem(dim, nx, ny, seed=40 + nx, contrast=6.0, screening=2.0)
+    else:
+        p = W.random_bc_problem(dim, nx, ny, seed=40 + nx, sigma_kind="field", asym=True)
+    A, b = dense_system(p.st, p.f, p.u0)
+    d = np.diag(A)
+    # block id per interior unknown, in the dense system's order (1D: every
+    # row is its own problem)
+    blk = np.array([(j * 1000 if dim == 1 else (j // ty) * 1000) + i // tx for j in range(ny) for i in range(nx)])
+    same = blk[:, None] == blk[None, :]
+    off_in = np.where(same, A, 0.0) - np.diag(d)
+    off_out = np.where(same, 0.0, A)
+    x0 = W.interior(p.u0, dim).reshape(-1)
+    x = x0.copy()
+    for _ in range(k):
+        x = (b - off_in @ x - off_out @ x0) / d
+    got = oracle.hier_cycle(p.st, p.f, p.u0, tx, ty, k)
+    np.testing.assert_allclose(W.interior(got, dim).reshape(-1), x, rtol=0, atol=1e-12 * np.abs(x).max())
