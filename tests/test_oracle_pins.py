@@ -628,3 +628,36 @@ def test_cycle_at_finite_k_is_blockwise_jacobi_with_frozen_halos(dim, nx, ny, tx
         x = (b - off_in @ x - off_out @ x0) / d
     got = oracle.hier_cycle(p.st, p.f, p.u0, tx, ty, k)
     np.testing.assert_allclose(W.interior(got, dim).reshape(-1), x, rtol=0, atol=1e-12 * np.abs(x).max())
+
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_overlap_finite_k_is_local_jacobi_then_owner_selection(k):
+    """Each overlapping subdomain runs k Jacobi steps on its own span with the
+    halo frozen at u_in (its local dense system), and every point takes the
+    value of its owner (Sections 3.4, 4.3).  11 x 10 grid, 4 x 4 subdomains
+    overlapping by 2 (x) and 1 (y), clamped last subdomains."""
+    p = W.random_bc_problem(2, 11, 10, seed=13 + k, sigma_kind="field", asym=True)
+    st, f, u0 = p.st, p.f, p.u0
+    T, ox, oy = 4, 2, 1
+    sx, sy = _starts(st.nx, T, ox), _starts(st.ny, T, oy)
+    ownx, owny = _owner_by_distance(st.nx, T, sx), _owner_by_distance(st.ny, T, sy)
+    out = oracle.hier_cycle_ovl(st, f, u0, T, T, k, ox, oy)
+    ref = u0.copy()
+    for jy, y0 in enumerate(sy):
+        for jx, x0 in enumerate(sx):
+            x1, y1 = min(x0 + T - 1, st.nx), min(y0 + T - 1, st.ny)
+            loc = W.poisson_stencil(2, x1 - x0 + 1, y1 - y0 + 1)
+            loc.cW, loc.cE, loc.cS, loc.cN, loc.cD = st.cW, st.cE, st.cS, st.cN, st.cD
+            loc.sigma = st.sigma[y0 - 1:y1 + 2, x0 - 1:x1 + 2]
+            A, b = dense_system(loc, f[y0 - 1:y1 + 2, x0 - 1:x1 + 2], u0[y0 - 1:y1 + 2, x0 - 1:x1 + 2])
+            d = np.diag(A)
+            off = A - np.diag(d)
+            x = u0[y0:y1 + 1, x0:x1 + 1].reshape(-1).copy()
+            for _ in range(k):
+                x = (b - off @ x) / d
+            x = x.reshape(y1 - y0 + 1, x1 - x0 + 1)
+            for j in range(y0, y1 + 1):
+                for i in range(x0, x1 + 1):
+                    if ownx[i] == jx and owny[j] == jy:
+                        ref[j, i] = x[j - y0, i - x0]
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
