@@ -255,7 +255,9 @@ static void ovl_span(long j, long J, long n, long T, long o, long *start, long *
  * only the points it owns (ovl_span) to u_out.  ox = oy = 0 is the cycle of
  * hjo_hier_cycle.  Parity: pinned (ox = oy = 0 equals hjo_hier_cycle; k = 1
  * equals a classic sweep for any overlap; large k equals restricted additive
- * Schwarz with dense subdomain solves; the overlap count of SURVEY's probe). */
+ * Schwarz with dense subdomain solves; k steps of local Jacobi then owner
+ * selection at finite k; the cycle count of an independent probe of the
+ * Section 3.5 problem). */
 void hjo_hier_cycle_ovl(const hjo_problem *p, const double *f, const double *uin, double *uout,
                         int tx, int ty, int k, int ox, int oy)
 {

@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (called through the C ABI) against the CPU oracle
 on the same seeded inputs.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (written here; each follows from the arithmetic on both sides):
   * binary64 cycles use the oracle's evaluation order without fused
     multiply-add: max |u_gpu - u_oracle| <= 1e-12 max |u_oracle| at equal cycle
     counts (bitwise equality is expected and reported);

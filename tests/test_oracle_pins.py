@@ -528,8 +528,8 @@ def test_overlap_keeps_the_exact_solution_fixed():
 def test_overlap_cycle_count_of_the_paper_1d_problem():
     """Section 3.4's best case, k = 16 with 4 overlapping points (tpb 32) on
     the Section 3.5 problem (N = 1024, b = 1, x0 = 1, residual reduced by
-    1e-4): 8,093 cycles, the count SURVEY's independent numpy probe found
-    under this reading of the subdomain layout; without overlap 19,555."""
+    1e-4): 8,093 cycles, the count an independent numpy implementation of
+    this reading of the subdomain layout found; without overlap 19,555."""
     p = W.paper_replica(1, 1024, copies=1)
     _, c4, s4, _ = oracle.solve(p.st, p.f, p.u0, 1e-4, 10 ** 7, 32, 1, 16, overlap=(4, 0))
     _, c0, s0, _ = oracle.solve(p.st, p.f, p.u0, 1e-4, 10 ** 7, 32, 1, 16)
