@@ -363,7 +363,10 @@ HJ_API int hj_autotune(const hj_desc *desc, hj_params *params, double *predicted
  * match desc->dtype; tile_x, tile_y, k, method as for hj_create.  f and u are
  * device pointers (same layout rules).  Stream-ordered; does not wait.  The
  * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * (cudaGetSymbolAddress) and should come before any stream capture; after
+ * cudaDeviceReset the next call on that device looks it up again (the same
+ * rule applies to it).  in_place, persistent = 1, pipeline = 1 and autotune
+ * give HJ_ERR_UNSUPPORTED (they need a handle's workspace).  All
  * calls share the array: calls whose work overlaps on the GPU (other streams,
  * other host threads) race and corrupt each other's results. */
 HJ_API int hj_cycles_noalloc(const hj_desc *desc, const hj_params *params, const void *f, void *u,

@@ -391,13 +391,13 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
     if (res && !b2) return seterr(HJ_ERR_CUDA, "internal: pipelined residual runs need a third iterate buffer");
     PpcKernel fn = pi->fn[sig][res];
     const int smem = pi->smem[sig];
-    static thread_local const void *configured[64];
-    static thread_local int nconf = 0;
-    bool done_attr = false;
-    for (int i = 0; i < nconf; ++i) done_attr |= configured[i] == (const void *)fn;
-    if (!done_attr) {
+    // the shared-memory limit is a per-device attribute of the function: set
+    // it once per (device, function) pair this thread has launched
+    static thread_local std::vector<std::pair<int, const void *>> configured;
+    const std::pair<int, const void *> key(h->dev, (const void *)fn);
+    if (std::find(configured.begin(), configured.end(), key) == configured.end()) {
         CKR(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        if (nconf < 64) configured[nconf++] = (const void *)fn;
+        configured.push_back(key);
     }
     int occ = 0;
     CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, pi->threads, smem));

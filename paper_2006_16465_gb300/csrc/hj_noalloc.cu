@@ -19,7 +19,10 @@
 // cudaGetSymbolAddress the first time the entry point runs on a device, with
 // that device current, so that first call should come before any stream
 // capture; in host code the array's name is only a host-side stand-in and
-// must never be passed to a kernel.  Every call shares the array
+// must never be passed to a kernel.  The address is cached per device
+// together with the id of the CUDA context it belongs to: after
+// cudaDeviceReset (a new primary context) the next call looks it up again,
+// and that call too should come before any stream capture.  Every call shares the array
 // and it keeps the last call's contents: each call first copies the caller's
 // u (ghost ring included) into it, so nothing stale is ever read.  Calls
 // whose work overlaps on the GPU (different streams, or different host
@@ -28,6 +31,8 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+
+#include <cudaTypedefs.h>
 
 #include "hj_runtime.cuh"
 
@@ -40,24 +45,59 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_mu;
 constexpr int kMaxDevices = 256;
-void *g_addr[kMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id;   // id of the context the address belongs to (0: none yet)
+    void *addr;
+};
+ScratchSlot g_slot[kMaxDevices] = {};
 
-// Device address of the static scratch array on the current device (set up on
-// the first call per device).
+// Unique id of the calling thread's current CUDA context (cuCtxGetId, through
+// the runtime's driver entry points: the library does not link libcuda), or 0
+// if no context is current yet.  Ids are never reused within a process, so a
+// context created after cudaDeviceReset never matches a cached address.
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool queried = false;
+    if (!queried) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = (PFN_cuCtxGetCurrent_v4000)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PFN_cuCtxGetId_v12000)p;
+        queried = true;
+    }
+    CUcontext c = nullptr;
+    if (!get_cur || get_cur(&c) != CUDA_SUCCESS || !c) return 0;
+    unsigned long long id = 0;
+    if (!get_id || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id + 1;   // keep 0 for "no context"
+}
+
+// Device address of the static scratch array on the current device: looked up
+// on the first call per device, and again whenever the device's context has
+// changed since (cudaDeviceReset).
 int scratch_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return seterr(HJ_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return seterr(HJ_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    ScratchSlot &sl = g_slot[dev];
+    const unsigned long long id = current_context_id();
+    if (!sl.addr || id == 0 || sl.ctx_id != id) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // makes the device's context current if none is
         if (e != cudaSuccess || !p)
             return seterr(HJ_ERR_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
-        g_addr[dev] = p;
+        sl.addr = p;
+        sl.ctx_id = current_context_id();
     }
-    *out = g_addr[dev];
+    *out = sl.addr;
     return HJ_OK;
 }
 
@@ -94,6 +134,11 @@ extern "C" int hj_cycles_noalloc(const hj_desc *desc, const hj_params *params, c
     if (p.k < 1) return seterr(HJ_ERR_INVALID_ARG, "k must be >= 1");
     if (p.overlap_x > 0 || (d.dim == 2 && p.overlap_y > 0))
         return seterr(HJ_ERR_UNSUPPORTED, "hj_cycles_noalloc does not take overlapping subdomains");
+    // the engines below need workspace or a handle: refuse them rather than ignore them
+    if (p.in_place != 0) return seterr(HJ_ERR_UNSUPPORTED, "hj_cycles_noalloc: in_place must be 0");
+    if (p.persistent == 1) return seterr(HJ_ERR_UNSUPPORTED, "hj_cycles_noalloc: persistent must not be 1");
+    if (p.pipeline == 1) return seterr(HJ_ERR_UNSUPPORTED, "hj_cycles_noalloc: pipeline must not be 1");
+    if (p.autotune != 0) return seterr(HJ_ERR_UNSUPPORTED, "hj_cycles_noalloc: autotune must be 0");
     if (p.fixed_cycles < 0) return seterr(HJ_ERR_INVALID_ARG, "fixed_cycles (the cycle count) must be >= 0");
     const double off = fabs(d.cW) + fabs(d.cE) + (d.dim == 2 ? fabs(d.cS) + fabs(d.cN) : 0.0);
     const double dc = d.cD + d.sigma_const;

@@ -142,3 +142,15 @@ def test_autotune_refuses_what_it_does_not_tune(hj):
     for d, prm in [(d3, hj.make_params(autotune=1)), (dc, hj.make_params(autotune=1)),
                    (d2, hj.make_params(autotune=1, method="mg"))]:
         assert hj.lib().hj_autotune(C.byref(d), C.byref(prm), None) == hj.HJ_ERR_UNSUPPORTED
+
+
+def test_noalloc_refuses_engines_that_need_workspace(hj):
+    """hj_cycles_noalloc refuses in-place, persistent, pipelined and autotuned
+    runs instead of ignoring them (the refusal comes before any CUDA call, so
+    the fake pointers are never used)."""
+    import ctypes as C
+    st_d = hj.make_desc(2, 64, 64, 96, -1, -1, -1, -1, 4.0)
+    for kw in (dict(in_place=1), dict(persistent=1), dict(pipeline=1), dict(autotune=1), dict(overlap_x=2)):
+        prm = hj.make_params(fixed_cycles=1, precision="f64", **kw)
+        code = hj.lib().hj_cycles_noalloc(C.byref(st_d), C.byref(prm), C.c_void_p(4096), C.c_void_p(8192), None)
+        assert code == hj.HJ_ERR_UNSUPPORTED, kw
