@@ -30,12 +30,18 @@ _LIB = _HERE / "libhj_oracle.so"
 
 
 def build(force: bool = False) -> Path:
-    """Compile the oracle with gcc (-O2, no FMA contraction, no fast-math)."""
-    newest = max(s.stat().st_mtime for s in _SRCS)
+    """Compile the oracle with gcc (-O2, no FMA contraction, no fast-math),
+    with OpenMP where the compiler has it (the subdomain loop of a cycle and
+    the row loop of a classic sweep; results do not depend on the thread
+    count, which stays 1 unless set_threads asks for more)."""
+    newest = max(s.stat().st_mtime for s in _SRCS + [Path(__file__)])
     if force or not _LIB.exists() or _LIB.stat().st_mtime < newest:
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared"] + [str(s) for s in _SRCS] + ["-o", str(_LIB) + ".tmp", "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+        srcs = [str(s) for s in _SRCS]
+        out = ["-o", str(_LIB) + ".tmp", "-lm"]
+        r = subprocess.run(base + ["-fopenmp"] + srcs + out, capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.run(base + srcs + out, check=True)
         os.replace(str(_LIB) + ".tmp", _LIB)
     return _LIB
 
@@ -120,8 +126,18 @@ def lib():
         L.hjo_mg_solve.restype = C.c_long
         L.hjo_paper_smem_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
         L.hjo_paper_smem_bytes.restype = C.c_long
+        L.hjo_set_threads.argtypes = [C.c_int]
+        L.hjo_set_threads.restype = C.c_int
+        L.hjo_set_threads(1)
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads for the subdomain loop of a cycle and the row loop of a classic
+    sweep (OpenMP build; results are bitwise the same for every count).
+    Returns the count in effect (1 without OpenMP)."""
+    return int(lib().hjo_set_threads(int(n)))
 
 
 def _grid(a, dtype=np.float64) -> np.ndarray:

@@ -37,6 +37,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     int dim;            /* 1 or 2 */
@@ -144,6 +147,9 @@ void hjo_jacobi_sweep(const hjo_problem *p, const double *f, const double *uin, 
 {
     const long W = width_of(p);
     copy_ghosts(p, uin, uout);
+    /* rows are independent (every point reads u_in only): an OpenMP build
+     * may split them over threads with the same result bit for bit */
+#pragma omp parallel for schedule(static)
     for (long j = first_row(p); j <= last_row(p); ++j)
         for (long i = 1; i <= p->nx; ++i) {
             const long q = j * W + i;
@@ -170,14 +176,23 @@ void hjo_hier_cycle(const hjo_problem *p, const double *f, const double *uin, do
     if (p->dim == 1) ty = 1;
     copy_ghosts(p, uin, uout);
     const long lw = tx + 2, lh = (p->dim == 2) ? ty + 2 : 1;
-    double *L[2];
-    L[0] = (double *)malloc(sizeof(double) * (size_t)(lw * lh));
-    L[1] = (double *)malloc(sizeof(double) * (size_t)(lw * lh));
     const long jlo = first_row(p), jhi = last_row(p);
     const long jstep = (p->dim == 2) ? ty : 1;
-    for (long j0 = jlo; j0 <= jhi; j0 += jstep) {
-        const long j1 = (p->dim == 2) ? (j0 + ty - 1 < jhi ? j0 + ty - 1 : jhi) : j0;
-        for (long i0 = 1; i0 <= p->nx; i0 += tx) {
+    const long nbx = (p->nx + tx - 1) / tx;                 /* subdomains along x */
+    const long nby = (jhi - jlo + jstep) / jstep;           /* subdomain rows (1D: copies) */
+    /* Subdomains are independent within a cycle (each reads u_in only and
+     * writes its own interior of u_out), so an OpenMP build may run them on
+     * several threads; the result is the same bit for bit. */
+#pragma omp parallel
+    {
+        double *L[2];
+        L[0] = (double *)malloc(sizeof(double) * (size_t)(lw * lh));
+        L[1] = (double *)malloc(sizeof(double) * (size_t)(lw * lh));
+#pragma omp for schedule(static)
+        for (long t = 0; t < nbx * nby; ++t) {
+            const long j0 = jlo + (t / nbx) * jstep;
+            const long j1 = (p->dim == 2) ? (j0 + ty - 1 < jhi ? j0 + ty - 1 : jhi) : j0;
+            const long i0 = 1 + (t % nbx) * tx;
             const long i1 = (i0 + tx - 1 < p->nx) ? i0 + tx - 1 : p->nx;
             const long hj0 = (p->dim == 2) ? j0 - 1 : j0;   /* first staged row */
             const long hj1 = (p->dim == 2) ? j1 + 1 : j1;   /* last staged row  */
@@ -207,9 +222,9 @@ void hjo_hier_cycle(const hjo_problem *p, const double *f, const double *uin, do
                 for (long i = i0; i <= i1; ++i)
                     uout[j * W + i] = fin[(j - hj0) * lw + (i - (i0 - 1))];
         }
+        free(L[0]);
+        free(L[1]);
     }
-    free(L[0]);
-    free(L[1]);
 }
 
 /* Subdomains along one dimension with overlap (Sections 3.4 and 4.3).
@@ -406,6 +421,20 @@ void hjo_run_fixed_ovl(const hjo_problem *p, const double *f, double *u, int tx,
     }
     if (cur != u) memcpy(u, cur, sizeof(double) * n);
     free(v);
+}
+
+/* Threads the subdomain loop of hjo_hier_cycle and the row loop of
+ * hjo_jacobi_sweep may use (an OpenMP build; 1 otherwise).  Results do not
+ * depend on it.  Returns the count in effect. */
+int hjo_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------------- */

@@ -661,3 +661,26 @@ def test_overlap_finite_k_is_local_jacobi_then_owner_selection(k):
                     if ownx[i] == jx and owny[j] == jy:
                         ref[j, i] = x[j - y0, i - x0]
     np.testing.assert_allclose(out, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+# ---------------------------------------------------------------------------
+# the OpenMP build: subdomains (and classic rows) on several threads give the
+# single-thread result bit for bit (each reads u_c only and writes its own points)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,nx,ny,tx,ty,sigma", [(2, 203, 131, 32, 32, "field"), (2, 96, 64, 64, 16, "const"),
+                                                    (1, 777, 9, 128, 1, "field")])
+def test_threaded_oracle_is_bitwise_the_single_thread_oracle(dim, nx, ny, tx, ty, sigma):
+    p = W.random_bc_problem(dim, nx, ny, seed=nx, sigma_kind=sigma, asym=True)
+    try:
+        ref_h = oracle.run_fixed(p.st, p.f, p.u0, 3, tx, ty, 5)
+        ref_c = oracle.run_fixed(p.st, p.f, p.u0, 4, classic=True)
+        ref_s = oracle.solve(p.st, p.f, p.u0, 1e-2, 10 ** 5, tx, ty, 5)
+        for th in (2, 3, 8):
+            got = oracle.set_threads(th)
+            assert np.array_equal(oracle.run_fixed(p.st, p.f, p.u0, 3, tx, ty, 5), ref_h), got
+            assert np.array_equal(oracle.run_fixed(p.st, p.f, p.u0, 4, classic=True), ref_c), got
+            u, c, status, _ = oracle.solve(p.st, p.f, p.u0, 1e-2, 10 ** 5, tx, ty, 5)
+            assert c == ref_s[1] and status == ref_s[2] and np.array_equal(u, ref_s[0])
+    finally:
+        oracle.set_threads(1)
