@@ -42,6 +42,51 @@ sys.path.insert(0, ROOT)
 METRIC = "2D Poisson time-to-1e-8 residual, GLUP/s vs global-mem Jacobi; % HBM roofline"
 N_BENCH = 8192
 BYTES_PER_POINT_CYCLE = 12  # read u, read f, write u (binary32)
+EXTRAS_OUT = os.path.join(ROOT, "gpurun_out", "bench_extras.json")
+
+
+def _r(x, digits=4):
+    """x rounded to a few significant digits (keeps the JSON line short)."""
+    if isinstance(x, float) and math.isfinite(x) and x != 0.0:
+        return float(f"{x:.{digits}g}")
+    return x
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def host_rel_residual(st, f, u) -> float:
+    """||f - A u|| / ||f|| over interior points, recomputed on the host in
+    binary64 numpy (constant five-point stencil, ghost ring = Dirichlet data;
+    with u0 = 0 this is the solver's relative residual)."""
+    import numpy as np
+    f = np.asarray(f, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    au = (st.cD + st.sigma_const) * u[1:-1, 1:-1] + st.cW * u[1:-1, :-2] + st.cE * u[1:-1, 2:] \
+        + st.cS * u[:-2, 1:-1] + st.cN * u[2:, 1:-1]
+    r = f[1:-1, 1:-1] - au
+    return float(np.linalg.norm(r) / np.linalg.norm(f[1:-1, 1:-1]))
+
+
+def dst_solution(st, f):
+    """The exact solution of the discrete 2D Poisson system (constant
+    stencil, zero Dirichlet data) by the type-I sine transform, which
+    diagonalises the five-point operator."""
+    import numpy as np
+    import scipy.fft
+    nx, ny = st.nx, st.ny
+    p = np.arange(1, nx + 1)
+    q = np.arange(1, ny + 1)
+    lam = (st.cD + st.sigma_const) + 2 * st.cW * np.cos(np.pi * p / (nx + 1))[None, :] \
+        + 2 * st.cS * np.cos(np.pi * q / (ny + 1))[:, None]
+    fh = scipy.fft.dstn(np.asarray(f, dtype=np.float64)[1:-1, 1:-1], type=1)
+    u = np.zeros((ny + 2, nx + 2))
+    u[1:-1, 1:-1] = scipy.fft.idstn(fh / lam, type=1)
+    return u
 
 
 # Sources that define the cycle kernel; the DRAM traffic recorded under
@@ -182,37 +227,45 @@ def make_problem(n, seed=1):
     return st, f, u0
 
 
-def run_reference(args):
-    """The oracle (plain C, binary64, one core) timed on the host on a bounded
-    sample of the same workload: one hierarchical cycle of the 8192^2 grid per
-    step."""
-    rank, world, _ = dist_env()
-    if rank != 0:
-        return 0
-    import oracle
-    import workloads as W
-    n = args.n
+def _oracle_rhs_8192(W, n):
     st = W.poisson_stencil(2, n, n)
     f = W.zeros_grid(st)
     rows = 512
     for j0 in range(0, n, rows):
         r = min(rows, n - j0)
         f[1 + j0:1 + j0 + r, 1:n + 1] = W.uniform(1, r * n, -1.0, 1.0, offset=j0 * n).reshape(r, n)
+    return st, f
+
+
+def run_reference(args):
+    """The oracle (plain C, binary64; its subdomain loop on every host core
+    through OpenMP, bitwise the single-thread result) timed on the host on a
+    bounded sample of the same workload: one hierarchical cycle of the
+    n x n grid per step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import workloads as W
+    n = args.n
+    st, f = _oracle_rhs_8192(W, n)
     u = W.zeros_grid(st)
-    prob = oracle.Problem(st)
+    cores = oracle.set_threads(host_cores())
     for _ in range(args.warmup):
-        u = oracle.run_fixed(prob, f, u, 1, 32, 32, args.k)
+        u = oracle.run_fixed(st, f, u, 1, 32, 32, args.k)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        u = oracle.run_fixed(prob, f, u, 1, 32, 32, args.k)
+        u = oracle.run_fixed(st, f, u, 1, 32, 32, args.k)
     dt = time.perf_counter() - t0
+    oracle.set_threads(1)
     glups = n * n * args.k * args.steps / dt / 1e9
-    sample = f"{args.steps} hierarchical cycles (k={args.k}, 32x32 subdomains) of the {n}x{n} grid, binary64"
+    sample = (f"{args.steps} hierarchical cycles (k={args.k}, 32x32 subdomains) of the {n}x{n} grid, binary64, "
+              f"{cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(args, world),
-            "cpu_baseline": {"value": glups, "unit": "GLUP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": glups, "unit": "GLUP/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": glups, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -227,68 +280,281 @@ def _config(args, world):
             "parallelism": f"replicas x{world}"}
 
 
-def cpu_baseline(k):
-    """Oracle timed on host cores on a bounded sample (~10 s): hierarchical
-    cycles of the full 8192^2 grid in binary64 until 10 s have passed."""
-    import oracle
-    import workloads as W
-    n = N_BENCH
-    st = W.poisson_stencil(2, n, n)
-    f = W.zeros_grid(st)
-    rows = 512
-    for j0 in range(0, n, rows):
-        r = min(rows, n - j0)
-        f[1 + j0:1 + j0 + r, 1:n + 1] = W.uniform(1, r * n, -1.0, 1.0, offset=j0 * n).reshape(r, n)
-    u = W.zeros_grid(st)
-    prob = oracle.Problem(st)
+def _oracle_rate(oracle, st, f, k, seconds):
+    u = f * 0.0
     t0 = time.perf_counter()
     cyc = 0
     while True:
-        u = oracle.run_fixed(prob, f, u, 1, 32, 32, k)
+        u = oracle.run_fixed(st, f, u, 1, 32, 32, k)
         cyc += 1
-        if time.perf_counter() - t0 >= 10.0:
+        if time.perf_counter() - t0 >= seconds:
             break
-    dt = time.perf_counter() - t0
-    return {"value": n * n * k * cyc / dt / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
-            "sample": f"{cyc} hierarchical cycles (k={k}, 32x32) of the {n}x{n} grid, binary64, one thread"}
+    return st.nx * st.ny * k * cyc / (time.perf_counter() - t0) / 1e9, cyc
+
+
+def cpu_baseline(k, gpu_counts=None):
+    """The oracle on the host cores, bounded (about 30 s in all):
+      * value: hierarchical cycles of the full 8192^2 grid (binary64, k, 32x32
+        subdomains), subdomains spread over every host core by OpenMP (the
+        result is bitwise the single-thread one), and on one core;
+      * time to a 1e-6 residual reduction: the 1D workload (N = 512, sum of
+        8 sine modes, 128-point subdomains, k = 32, and classic sweeps) run
+        to the end; the 2D 512^2 binary64 workload (f ~ U[-1,1]) projected
+        from a bounded sample of cycles (the per-cycle time includes the
+        residual check the oracle's solve makes every cycle) times the sweep
+        count: classic from the closed form of Jacobi's decay on the sine
+        modes, hierarchical (32x32, k = 16) from the GPU's binary64 solve,
+        whose cycles are bitwise the oracle's."""
+    import numpy as np
+    import oracle
+    import workloads as W
+    cores = host_cores()
+    st, f = _oracle_rhs_8192(W, N_BENCH)
+    used = oracle.set_threads(cores)
+    glups_all, cyc_all = _oracle_rate(oracle, st, f, k, 6.0)
+    oracle.set_threads(1)
+    glups_one, cyc_one = _oracle_rate(oracle, st, f, k, 4.0)
+    del f
+    out = {"value": glups_all, "unit": "GLUP/s", "cores": used, "kind": "oracle",
+           "sample": f"{cyc_all} hierarchical cycles (k={k}, 32x32) of the 8192^2 grid, binary64, {used} threads",
+           "single_core_glups": glups_one}
+    oracle.set_threads(used)
+    try:
+        q = W.poisson1d_sine(512, seed=0)
+        ttr = {}
+        for name, kw in (("hier_128_k32", dict(tx=128, ty=1, k=32)), ("classic", dict(classic=True))):
+            t0 = time.perf_counter()
+            _, c, status, _ = oracle.solve(q.st, q.f, q.u0, 1e-6, 10 ** 7, **kw)
+            ttr[name] = {"s": time.perf_counter() - t0, "cycles": c, "status": status}
+        out["cfg1_1d_to_1e-6"] = ttr
+        p = W.poisson2d_uniform(512, 512, seed=1)
+        proj = {}
+        # classic: per-sweep time over a bounded sample, sweeps from the closed form
+        t0 = time.perf_counter()
+        oracle.solve(p.st, p.f, p.u0, 1e-6, 3000, classic=True)
+        per = (time.perf_counter() - t0) / 3000
+        n_cl = classic_sweeps_closed_form(p.st, p.f, 1e-6)
+        proj["classic"] = {"s_projected": per * n_cl, "sweeps_closed_form": n_cl, "s_per_sweep": per}
+        t0 = time.perf_counter()
+        oracle.solve(p.st, p.f, p.u0, 1e-6, 200, 32, 32, 16)
+        per = (time.perf_counter() - t0) / 200
+        n_h = (gpu_counts or {}).get("f64_k16")
+        proj["hier_32x32_k16"] = {"s_per_cycle": per, "cycles_gpu_f64": n_h,
+                                  "s_projected": per * n_h if n_h else None}
+        out["cfg2_512_f64_to_1e-6"] = proj
+    finally:
+        oracle.set_threads(1)
+    return out
+
+
+def classic_sweeps_closed_form(st, f, factor):
+    """Classic Jacobi sweeps from u0 = 0 until ||r_n|| <= factor ||r_0|| for a
+    constant five-point stencil with zero Dirichlet data: in the sine basis
+    every mode decays by mu = 1 - lam / d per sweep, so the residual norm
+    after n sweeps is a closed-form sum over the transformed right-hand side."""
+    import numpy as np
+    import scipy.fft
+    nx, ny = st.nx, st.ny
+    d = st.cD + st.sigma_const
+    lam = d + 2 * st.cW * np.cos(np.pi * np.arange(1, nx + 1) / (nx + 1))[None, :] \
+        + 2 * st.cS * np.cos(np.pi * np.arange(1, ny + 1) / (ny + 1))[:, None]
+    mu = np.abs(1.0 - lam / d).ravel()
+    w = (scipy.fft.dstn(np.asarray(f, dtype=np.float64)[1:-1, 1:-1], type=1) ** 2).ravel()
+    w0 = w.sum()
+    lmu = np.log(np.maximum(mu, 1e-300))
+
+    def ratio2(n):
+        return float((w * np.exp(2 * n * lmu)).sum() / w0)
+
+    lo, hi = 0, 1
+    while ratio2(hi) > factor ** 2:
+        hi *= 2
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if ratio2(mid) > factor ** 2:
+            lo = mid
+        else:
+            hi = mid
+    return hi
+
+
+def _timed_solve(torch, hj, st, f, u0, dim=2, warm=True, **kw):
+    """Create, warm (graphs, caches, tuning), solve from u0 and time it; the
+    relative residual of the returned u is recomputed on the host."""
+    dt_ = torch.float32 if kw.get("precision") == "f32" else torch.float64
+    s = hj.Solver(st, **kw)
+    fd = hj.grid_from(f, dim, dt_)
+    if warm:
+        s.solve(fd, hj.grid_from(u0, dim, dt_), check=False)
+    u = hj.grid_from(u0, dim, dt_)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = s.solve(fd, u, check=False)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    s.close()
+    uh = u[..., :st.nx + 2].double().cpu().numpy()
+    out = {"s": sec, "cycles": r["cycles"], "outer": r["outer_steps"], "inner": r["inner_cycles"],
+           "status": r["status"], "tile": [r["tile_x"], r["tile_y"]], "k": r["k"],
+           "overlap": [r["overlap_x"], r["overlap_y"]]}
+    if dim == 2:
+        out["rel"] = host_rel_residual(st, f, uh)
+    return out, uh
 
 
 def time_to_residual(torch, hj, W, tol=1e-8):
-    """512^2 Poisson, f ~ U[-1,1]: binary32-inner / binary64-refinement
-    hierarchical solve vs binary64 global-memory Jacobi, both to tol."""
+    """The metric's first clause: 512^2 Poisson, f ~ U[-1,1], u0 = 0, to a
+    1e-8 relative residual.  Hierarchical cycles in binary32 with binary64
+    refinement (autotuned; 32x32, k = 32; and with 4 overlapping points)
+    against the fastest of three binary64 global-memory Jacobi variants
+    (one launch per sweep in graphs, one grid-synchronised persistent launch,
+    the tile kernel with k = 1, which is one classic sweep bit for bit).
+    'rel' is the relative residual of the returned u recomputed on the host."""
     p = W.poisson2d_uniform(512, 512, seed=1)
-    f = hj.grid_from(p.f, 2, torch.float64)
     out = {}
-    for name, kw in [("hier_f32_ir_32x32_k32", dict(tile_x=32, tile_y=32, k=32, precision="f32_ir", inner_tol=1e-4,
-                                                    check_every=256)),
-                     ("hier_f32_ir_32x32_k32_overlap4", dict(tile_x=32, tile_y=32, k=32, overlap_x=4, overlap_y=4,
-                                                             precision="f32_ir", inner_tol=1e-4, check_every=256)),
-                     ("hier_f32_ir_autotuned", dict(precision="f32_ir", inner_tol=1e-4, autotune=1, check_every=256)),
-                     ("classic_f64_graphs", dict(method="classic", precision="f64", check_every=1024, persistent=0)),
-                     ("classic_f64_gridsync", dict(method="classic", precision="f64", persistent=1)),
-                     # a hierarchical cycle with k = 1 is one classic sweep (bitwise): classic
-                     # Jacobi run by the tile kernels
-                     ("classic_f64_tile_k1", dict(tile_x=32, tile_y=32, k=1, precision="f64", check_every=1024))]:
-        s = hj.Solver(p.st, tol=tol, max_cycles=5_000_000, **kw)
-        u = hj.grid_from(p.u0, 2, torch.float64)
-        s.solve(f, u.clone())  # warm (graphs, caches)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = s.solve(f, u)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        a, rel = s.residual(f, u)
-        out[name] = {"seconds": dt, "cycles": r["cycles"], "outer_steps": r["outer_steps"],
-                     "rel_residual": a / r["res0"] if r["res0"] else 0.0, "status": r["status"],
-                     "tile": [r["tile_x"], r["tile_y"], r["tile_threads"]], "k": r["k"],
-                     "overlap": [r["overlap_x"], r["overlap_y"]]}
-        s.close()
-    # the fastest classic variant is the baseline (the paper takes the best classic configuration)
-    best = min(out[k]["seconds"] for k in ("classic_f64_graphs", "classic_f64_gridsync", "classic_f64_tile_k1"))
-    out["speedup_32x32_vs_best_classic"] = best / out["hier_f32_ir_32x32_k32"]["seconds"]
-    out["speedup_autotuned_vs_best_classic"] = best / out["hier_f32_ir_autotuned"]["seconds"]
-    out["speedup_32x32_overlap4_vs_best_classic"] = best / out["hier_f32_ir_32x32_k32_overlap4"]["seconds"]
+    runs = [("hj_f32ir_autotuned", dict(precision="f32_ir", inner_tol=1e-4, autotune=1, check_every=256)),
+            ("hj_f32ir_32x32_k32", dict(tile_x=32, tile_y=32, k=32, precision="f32_ir", inner_tol=1e-4,
+                                        check_every=256)),
+            ("hj_f32ir_32x32_k32_o4", dict(tile_x=32, tile_y=32, k=32, overlap_x=4, overlap_y=4,
+                                           precision="f32_ir", inner_tol=1e-4, check_every=256)),
+            ("classic_f64_graphs", dict(method="classic", precision="f64", check_every=1024, persistent=0)),
+            ("classic_f64_gridsync", dict(method="classic", precision="f64", persistent=1)),
+            ("classic_f64_tile_k1", dict(tile_x=32, tile_y=32, k=1, precision="f64", check_every=1024))]
+    for name, kw in runs:
+        out[name], _ = _timed_solve(torch, hj, p.st, p.f, p.u0, tol=tol, max_cycles=5_000_000, **kw)
+    classic = min((k for k in out if k.startswith("classic")), key=lambda k: out[k]["s"])
+    out["classic_best"] = classic
+    out["speedup_autotuned_vs_classic"] = out[classic]["s"] / out["hj_f32ir_autotuned"]["s"]
+    out["speedup_32x32_k32_vs_classic"] = out[classic]["s"] / out["hj_f32ir_32x32_k32"]["s"]
     return out
+
+
+def cfg2_k_sweep(torch, hj, W):
+    """The k sweep on the 512^2 Poisson problem (f ~ U[-1,1], u0 = 0, 32x32
+    subdomains): binary64 to a 1e-6 relative residual and binary32 to 1e-5
+    (binary32 storage floors near 2e-6 here), k in {1, 4, 16, 64}, beside
+    classic Jacobi in the same precision.  Inner GLUP/s = points x k x cycles
+    / time (the analogue of the paper's k tables)."""
+    p = W.poisson2d_uniform(512, 512, seed=1)
+    n2 = 512 * 512
+    out = {}
+    for prec, tol in (("f64", 1e-6), ("f32", 1e-5)):
+        row = {}
+        for k in (1, 4, 16, 64):
+            r, _ = _timed_solve(torch, hj, p.st, p.f, p.u0, warm=False, tile_x=32, tile_y=32, k=k, precision=prec,
+                                tol=tol, max_cycles=10_000_000, check_every=1024 if k == 1 else 256)
+            r["inner_glups"] = n2 * k * r["cycles"] / r["s"] / 1e9
+            row[f"k{k}"] = r
+        r, _ = _timed_solve(torch, hj, p.st, p.f, p.u0, warm=False, method="classic", precision=prec, tol=tol,
+                            max_cycles=10_000_000, check_every=1024, persistent=0)
+        row["classic"] = r
+        out[f"{prec}_to_{tol:g}"] = row
+    return out
+
+
+def cfg3_precision(torch, hj, W):
+    """Mixed precision on 512^2 Poisson with f = sin(pi x) sin(pi y) + 1e-3
+    U[-1,1]: refinement to a 1e-10 relative residual with binary32 inner
+    cycles and with a bfloat16-stored correction, beside all-binary64
+    hierarchical cycles to the same tolerance.  Each result's error is
+    measured against the exact discrete solution (sine-transform solve) and
+    against the binary64 result."""
+    import numpy as np
+    p = W.poisson2d_sin_noise(512, seed=2)
+    ue = dst_solution(p.st, p.f)
+    out = {}
+    sols = {}
+    runs = [("f32_ir", dict(precision="f32_ir", tile_x=32, tile_y=32, k=32, inner_tol=1e-4, check_every=256)),
+            ("bf16corr_ir", dict(precision="bf16corr_ir", tile_x=32, tile_y=32, k=32, inner_tol=1e-4,
+                                 check_every=256)),
+            ("f64", dict(precision="f64", tile_x=32, tile_y=32, k=32, check_every=256))]
+    for name, kw in runs:
+        r, uh = _timed_solve(torch, hj, p.st, p.f, p.u0, warm=False, tol=1e-10, max_cycles=10_000_000,
+                             max_outer=200, **kw)
+        r["err_vs_exact"] = float(np.linalg.norm(uh - ue) / np.linalg.norm(ue))
+        out[name] = r
+        sols[name] = uh
+    for name in ("f32_ir", "bf16corr_ir"):
+        out[name]["err_vs_f64"] = float(np.linalg.norm(sols[name] - sols["f64"]) / np.linalg.norm(sols["f64"]))
+    return out
+
+
+def fd_check(torch, hj, W, n=1024, entries=32, rel_step=1e-6, seed=7, tol=1e-12, du_tol=1e-9):
+    """Central differences of L(sigma) = 0.5 ||u(sigma) - u*||^2 against the
+    implicit-adjoint gradient dL/dsigma_p = -lambda_p u_p, at `entries`
+    random interior points of the differentiation workload (Fourier sigma
+    field, first right-hand side), binary64 solutions.
+
+    With step delta = rel_step * sigma_p, the loss changes by ~1e-14 of itself
+    at 1024^2: two losses of separately re-solved problems cannot resolve
+    that.  So each perturbed solution is u + du, with du the correction a
+    solve warm-started from u computes: A(sigma +- delta e_p) du = -+ delta u_p
+    e_p (the base residual, common to both and near rounding level, left
+    out), solved to a relative residual of du_tol by binary32 cycles with
+    binary64 refinement, all 2 x entries corrections in one batched call.
+    Then L(u + du) - L(u) = sum du (u - u*) + 0.5 sum du^2, exactly.  The
+    base solve and the adjoint run to tol (binary64 refinement)."""
+    import numpy as np
+    st, fs, ustar = W.differentiation_problem(n, 1, seed=seed)
+    sig = st.sigma
+    f = hj.grid_from(fs[0], 2, torch.float64)
+    sigma = hj.grid_from(sig, 2, torch.float64)
+    target = hj.grid_from(ustar, 2, torch.float64)
+    prm = dict(tile_x=64, tile_y=64, k=32, precision="f32_ir", inner_tol=1e-4)
+    t0 = time.perf_counter()
+    s = hj.Solver(st, sigma=sigma, tol=tol, **prm)
+    u = hj.alloc_grid(2, n, n, torch.float64)
+    s.solve(f, u)
+    g = u - target
+    g[0, :] = 0
+    g[-1, :] = 0
+    g[:, 0] = 0
+    g[:, n + 1:] = 0
+    dl_df = torch.zeros_like(u)
+    dl_dsig = torch.zeros_like(u)
+    s.adjoint(g, u, dl_df, dl_dsig)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    s.close()
+    idx = (W.uniform01(seed + 1000, 2 * entries) * n).astype(np.int64) + 1
+    pts = [(int(idx[2 * e]), int(idx[2 * e + 1])) for e in range(entries)]   # (row j, column i)
+    # 2 x entries perturbed problems, one batched refinement solve
+    sigs, rhs, dus, descs = [], [], [], []
+    for (j, i) in pts:
+        for sgn in (1.0, -1.0):
+            dlt = rel_step * float(sig[j, i])
+            sp = sigma.clone()
+            sp[j, i] += sgn * dlt
+            b = torch.zeros_like(u)
+            b[j, i] = -sgn * dlt * u[j, i]
+            sigs.append(sp)
+            rhs.append(b)
+            dus.append(torch.zeros_like(u))
+            descs.append(hj.make_desc(2, n, n, u.shape[1], st.cW, st.cE, st.cS, st.cN, st.cD, 0.0, sp))
+    sb = hj.Solver(st, sigma=sigma, tol=du_tol, **prm)
+    stats = hj.hj_stats()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    code = hj.hj_solve_batched(sb.h, descs, [b.data_ptr() for b in rhs], [d.data_ptr() for d in dus],
+                               hj._stream_handle(None), stats)
+    torch.cuda.synchronize()
+    t_fd = time.perf_counter() - t1
+    sb.close()
+    w = (u - target)[1:n + 1, 1:n + 1]
+    fd, adj, rel = [], [], []
+    for e, (j, i) in enumerate(pts):
+        dp, dm = dus[2 * e][1:n + 1, 1:n + 1], dus[2 * e + 1][1:n + 1, 1:n + 1]
+        lp = float((dp * w).sum() + 0.5 * (dp * dp).sum())
+        lm = float((dm * w).sum() + 0.5 * (dm * dm).sum())
+        dlt = rel_step * float(sig[j, i])
+        fd.append((lp - lm) / (2 * dlt))
+        adj.append(float(dl_dsig[j, i]))
+        rel.append(abs(fd[-1] - adj[-1]) / abs(adj[-1]))
+    scale = max(abs(a) for a in adj)
+    return {"grid": [n, n], "entries": entries, "rel_step": rel_step, "status": code,
+            "batched_rel_final": stats.rel_final, "max_rel_err": max(rel), "median_rel_err": float(np.median(rel)),
+            "max_err_over_max_grad": max(abs(a - b) for a, b in zip(fd, adj)) / scale,
+            "forward_adjoint_s": t_adj, "fd_solves_s": t_fd, "points": pts, "fd": fd, "adjoint": adj}
 
 
 def inner_roofline(torch, hj, W, n, k=16, cycles=100):
@@ -659,8 +925,13 @@ def main():
                          "(profiling runs: keeps the tuner's launches out of the capture)")
     ap.add_argument("--paper-replicas", action="store_true",
                     help="also time the paper's Section 3.5 / 4.2 problems (binary64, minutes)")
-    ap.add_argument("--only", default="", choices=["", "variable_coefficients", "three_d", "multigrid"],
+    ap.add_argument("--only", default="", choices=["", "variable_coefficients", "three_d", "multigrid",
+                                                    "time_to_residual", "cfg2_k_sweep", "cfg3_precision",
+                                                    "fd_check", "cpu_baseline"],
                     help="run one extras section alone and print its JSON (profiling runs)")
+    ap.add_argument("--fd-n", type=int, default=1024, help="grid side of the finite-difference check")
+    ap.add_argument("--fd-entries", type=int, default=32, help="sigma entries the finite-difference check perturbs")
+    ap.add_argument("--extras-out", default=EXTRAS_OUT, help="where the full record of the extra legs goes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -672,8 +943,15 @@ def main():
         import workloads as W
         torch.cuda.set_device(0)
         hbm_peak, _ = _peaks()
-        section = {"variable_coefficients": variable_coefficients, "three_d": three_d, "multigrid": multigrid}
-        print(json.dumps({args.only: section[args.only](torch, hj, W, hbm_peak=hbm_peak)}), flush=True)
+        section = {"variable_coefficients": lambda: variable_coefficients(torch, hj, W, hbm_peak=hbm_peak),
+                   "three_d": lambda: three_d(torch, hj, W, hbm_peak=hbm_peak),
+                   "multigrid": lambda: multigrid(torch, hj, W, hbm_peak=hbm_peak),
+                   "time_to_residual": lambda: time_to_residual(torch, hj, W),
+                   "cfg2_k_sweep": lambda: cfg2_k_sweep(torch, hj, W),
+                   "cfg3_precision": lambda: cfg3_precision(torch, hj, W),
+                   "fd_check": lambda: fd_check(torch, hj, W, n=args.fd_n, entries=args.fd_entries),
+                   "cpu_baseline": lambda: cpu_baseline(args.k)}
+        print(json.dumps({args.only: section[args.only]()}), flush=True)
         return 0
 
     import torch
@@ -753,7 +1031,8 @@ def main():
         torch.cuda.synchronize()
         cms = e0.elapsed_time(e1) / 1000
         extras["classic_global_jacobi"] = {"glups": n * n / (cms / 1e3) / 1e9, "us_per_sweep": cms * 1e3,
-                                           "hbm_gbs": 12 * n * n / (cms / 1e3) / 1e9}
+                                           "hbm_gbs": 12 * n * n / (cms / 1e3) / 1e9,
+                                           "hbm_frac": 12 * n * n / (cms / 1e3) / 1e9 / hbm_peak}
         cl.close()
         # the same sweep through the tile kernels (a hierarchical cycle with k = 1 is one
         # classic sweep, bitwise), launch shape tuned like the headline's
@@ -769,11 +1048,15 @@ def main():
         extras["classic_jacobi_tile_kernel_k1"] = {"glups": n * n / (tms / 1e3) / 1e9, "us_per_sweep": tms * 1e3,
                                                    "hbm_gbs": 12 * n * n / (tms / 1e3) / 1e9}
         cl.close()
+        del uc
         extras["hier_global_cycle_rate_gdofs"] = n * n / (per_launch_ms / 1e3) / 1e9
         extras["time_to_1e-8_512"] = time_to_residual(torch, hj, W)
+        extras["cfg2_k_sweep_512"] = cfg2_k_sweep(torch, hj, W)
+        extras["cfg3_precision_512"] = cfg3_precision(torch, hj, W)
         extras["cfg1_1d_to_1e-6"] = time_1d(torch, hj, W)
         extras["cfg4_batched_256_to_1e-8"] = time_batched(torch, hj, W)
         extras["cfg5_differentiation_1024"] = time_differentiation(torch, hj, W)
+        extras["cfg5_fd_check"] = fd_check(torch, hj, W, n=args.fd_n, entries=args.fd_entries)
         extras["inner_sweep_roofline_k16"] = inner_roofline(torch, hj, W, n)
         extras["variable_coefficients_4096"] = variable_coefficients(torch, hj, W, hbm_peak=hbm_peak)
         extras["three_d_512"] = three_d(torch, hj, W, hbm_peak=hbm_peak)
@@ -784,25 +1067,73 @@ def main():
     launches += args.steps  # one residual launch per step (the final iterate is not converged: tol = 0)
     ntiles = ((n + 31) // 32) ** 2
     pipelined = ntiles >= 8 * torch.cuda.get_device_properties(local).multi_processor_count
-    kernel_name = ("ppc2d_kernel" if pipelined else "hier2d_kernel") + "<float, 32x32 tiles, fused residual>"
-    line = {"metric": METRIC, "value": glups, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+    kernel_name = ("ppc2d_kernel" if pipelined else "hier2d_kernel") + "<float,32x32>"
+    line = {"metric": METRIC, "value": _r(glups), "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": _r(ms / args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(_config(args, world), launch=launch_used),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": recorded_traffic(n),
+            "roofline": {"bound": "hbm", "achieved": _r(achieved), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": _r(achieved / hbm_peak), "traffic": recorded_traffic(n),
                          "algorithmic_bytes_per_launch": BYTES_PER_POINT_CYCLE * n * n,
                          "kernel": kernel_name, "peak_kind": peak_kind},
-            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
-    line.update(extras)
+            "e2e": {k: _r(v) for k, v in e2e.items()}, "gpu_launches": int(launches), "clocks": clk.summary()}
     if rank == 0 and not args.no_extras:
-        line["cpu_baseline"] = cpu_baseline(k)
+        cpu = cpu_baseline(k, gpu_counts={"f64_k16": extras["cfg2_k_sweep_512"]["f64_to_1e-06"]["k16"]["cycles"]})
+        extras["cpu_baseline"] = cpu
+        line["cpu_baseline"] = {"value": _r(cpu["value"]), "unit": "GLUP/s", "cores": cpu["cores"], "kind": "oracle",
+                                "sample": cpu["sample"], "single_core": _r(cpu["single_core_glups"]),
+                                "cfg1_to_1e-6_s": {a: _r(b["s"], 3) for a, b in cpu["cfg1_1d_to_1e-6"].items()},
+                                "cfg2_f64_to_1e-6_s_projected": {
+                                    a: _r(b["s_projected"], 3) for a, b in cpu["cfg2_512_f64_to_1e-6"].items()}}
+        line.update(compact_summary(extras))
+        try:
+            os.makedirs(os.path.dirname(args.extras_out), exist_ok=True)
+            with open(args.extras_out, "w") as fh:
+                json.dump(dict(line, extras=extras), fh, indent=1)
+        except OSError:
+            pass
     solver.close()
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def compact_summary(x):
+    """The legs' key numbers for the JSON line (the full record goes to the
+    extras file): [seconds, cycles, outer steps, host-recomputed relative
+    residual] per solve, errors against the exact discrete solution."""
+    t = x["time_to_1e-8_512"]
+
+    def solve_row(r, err=False):
+        row = [_r(r["s"], 3), r["cycles"], r["outer"], _r(r.get("rel", 0.0), 2)]
+        if err:
+            row.append(_r(r["err_vs_exact"], 2))
+        return row
+
+    out = {"time_to_1e-8_512": {"fields": "s,cycles,outer,rel",
+                                "hj_f32ir_autotuned": solve_row(t["hj_f32ir_autotuned"]),
+                                "hj_f32ir_32x32_k32": solve_row(t["hj_f32ir_32x32_k32"]),
+                                "classic_f64_best": solve_row(t[t["classic_best"]]),
+                                "classic_variant": t["classic_best"][12:],
+                                "speedup": _r(t["speedup_autotuned_vs_classic"], 3)}}
+    c3 = x["cfg3_precision_512"]
+    out["cfg3_ir_to_1e-10_512"] = {"fields": "s,cycles,outer,rel,err_vs_exact",
+                                   **{k: solve_row(v, True) for k, v in c3.items()}}
+    sw = x["cfg2_k_sweep_512"]
+    out["cfg2_k_sweep_512"] = {"fields": "s,cycles", **{p: {k: [_r(v["s"], 3), v["cycles"]] for k, v in row.items()}
+                                                         for p, row in sw.items()}}
+    fd = x["cfg5_fd_check"]
+    out["cfg5_fd"] = {"grid": fd["grid"][0], "entries": fd["entries"], "step": fd["rel_step"],
+                      "max_rel_err": _r(fd["max_rel_err"], 2), "s": _r(fd["fd_solves_s"], 3)}
+    out["legs"] = {"classic_kernel_hbm_frac": _r(x["classic_global_jacobi"]["hbm_frac"], 3),
+                   "inner_k16_alu_frac": _r(x["inner_sweep_roofline_k16"]["frac"], 3),
+                   "cfg1_gpu_speedup": _r(x["cfg1_1d_to_1e-6"]["speedup"], 3),
+                   "cfg4_s": _r(x["cfg4_batched_256_to_1e-8"]["seconds"], 3),
+                   "cfg5_fwd_bwd_s": [_r(x["cfg5_differentiation_1024"]["forward_seconds"], 3),
+                                      _r(x["cfg5_differentiation_1024"]["backward_seconds"], 3)]}
+    return out
 
 
 if __name__ == "__main__":
