@@ -223,10 +223,10 @@ RedArgs red_args(const hj_handle *h, int mode, double tol, long long max_cycles)
 void geometry(const hj_handle *h, const TileKernelInfo *ki, bool classic, dim3 *grid, dim3 *block) {
     const int nx = h->d.nx, ny = h->d.ny;
     if (classic) {
-        // grid-stride kernels over blocks of 32 x 8 (2D) or 256 (1D) points,
-        // bounded to 8 CTAs per SM so the residual is reduced once per CTA
-        const long long nb = h->d.dim == 2 ? (long long)((nx + 31) / 32) * ((ny + 7) / 8)
-                                           : (long long)((nx + 255) / 256) * ny;
+        // grid-stride kernels over blocks of points (2D: classic2d_blocks; an
+        // upper bound for every storage type) or 256 (1D) points, bounded to 8
+        // CTAs per SM so the residual is reduced once per CTA
+        const long long nb = h->d.dim == 2 ? classic2d_blocks(nx, ny, 8) : (long long)((nx + 255) / 256) * ny;
         *grid = dim3((unsigned)std::min<long long>(nb, 8LL * h->nsm));
         *block = h->d.dim == 2 ? dim3(32, 8) : dim3(256);
         return;
@@ -385,6 +385,13 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
     if (!want_ppc(h, pi, classic)) {
         geometry(h, ki, classic, &pl->grid, &pl->block);
         pl->fn = (!classic && overlapped(h)) ? ki->ovl[sig][res] : ki->fn[sig][res];
+        if (classic && h->d.dim == 2) {
+            // one wave of resident CTAs: every CTA of the grid-stride sweep gets
+            // the same share of blocks, so a partial last wave would idle SMs
+            int occ = 0;
+            CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pl->fn, pl->block.x * pl->block.y, 0));
+            pl->grid.x = (unsigned)std::max(1, std::min<int>((int)pl->grid.x, std::max(occ, 1) * h->nsm));
+        }
         pl->ppc = false;
         return HJ_OK;
     }

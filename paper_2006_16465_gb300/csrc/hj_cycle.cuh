@@ -112,11 +112,13 @@ __device__ __forceinline__ T point_update(const Coef<T> &k, T g, T iv, T W, T E,
 // shared box), the k subiterations, and the write-back.
 //
 // A CTA of NW warps owns a TX x TY tile with TX = L*C, L = 32/H lanes per row,
-// TY = R*NW*H.  Each warp holds H bands of R rows (H = 1 or 2): lane l belongs
+// TY = R*NW*H.  Each warp holds H bands of R rows (H = 1, 2 or 4): lane l belongs
 // to band hb = l / L of its warp and owns the C consecutive columns
 // x0 + (l % L)*C ... of that band's rows; band b = w*H + hb starts at row
-// y0 + b*R.  Two bands per warp let a 32-wide tile give every lane two
-// neighbouring columns, whose updates then run as packed binary32 pairs.
+// y0 + b*R.  Two (four) bands per warp let a 32-wide tile give every lane two
+// (four) neighbouring columns, whose updates then run as packed binary32
+// pairs; the more columns a lane owns, the fewer shuffles and halo selects
+// each point update carries.
 // ---------------------------------------------------------------------------
 template <typename T, int C, int R, bool SIG>
 struct Tile2D {
@@ -189,11 +191,44 @@ template <> __device__ __forceinline__ float sm_s<__nv_bfloat16, float>(const __
 // iterate starting at (x0-1, y0-1); sf / sd: TY rows of f / (1/d) starting at
 // (x0-1, y0); all with row pitch bw elements.  Out-of-bounds box elements
 // were zero-filled by the copy engine, exactly like the predicated path.
+// Four binary32 columns per lane: the lane's columns 1 + 4 li .. 4 + 4 li of a
+// box row straddle the 16-byte chunks at 4 li and 4 li + 4, so two 16-byte
+// shared loads give them together with the W and E neighbours (the halo
+// column for the first and last lane of a row).  The L = 8 lanes of a band
+// read 8 consecutive chunks, one bank each: no conflicts.
+__device__ __forceinline__ void lds_row4(const float *row, const int li, float (&v)[4], float &w, float &e) {
+    const float4 a = *(const float4 *)(row + 4 * li);
+    const float4 b = *(const float4 *)(row + 4 * li + 4);
+    w = a.x;
+    v[0] = a.y;
+    v[1] = a.z;
+    v[2] = a.w;
+    v[3] = b.x;
+    e = b.y;
+}
+
 template <typename S, typename T, int C, int R, int H, bool EXACT, bool SIG>
 __device__ __forceinline__ void stage2d_smem(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const S *su, const T *sf,
                                              const T *sd, const int bwu, const int bwf, const int band_row0) {
     constexpr int L = 32 / H, TX = L * C;
     const int li = (threadIdx.x & 31) % L;
+    if constexpr (C == 4 && std::is_same<S, float>::value && std::is_same<T, float>::value) {
+        // box pitches are multiples of 16 bytes and the boxes 128-byte aligned
+        float w, e, tmp[4];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int sr = band_row0 + r;
+            lds_row4(su + (sr + 1) * bwu, li, t.v[r], w, e);
+            t.hx[r] = (li == 0) ? w : e;
+            lds_row4(sf + sr * bwf, li, tmp, w, e);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) t.g[r][c] = rhs_term<T, EXACT, SIG>(kc, tmp[c]);
+            if constexpr (SIG) lds_row4(sd + sr * bwf, li, t.dv[SIG ? r : 0], w, e);
+        }
+        lds_row4(su + band_row0 * bwu, li, t.top, w, e);
+        lds_row4(su + (band_row0 + R + 1) * bwu, li, t.bot, w, e);
+        return;
+    }
     const int xc = 1 + li * C;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -270,7 +305,7 @@ template <typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RE
 __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type
 sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, const int yb, const int nx,
          const int ny, T *xbuf, const Own own = Own{0, 0, 0, 0}) {
-    static_assert(H == 1 || H == 2, "one or two bands per warp");
+    static_assert(H == 1 || H == 2 || H == 4, "one, two or four bands per warp");
     constexpr int L = 32 / H, TX = L * C;
     constexpr bool PACK = std::is_same<T, float>::value && !EXACT && (C % 2 == 0) && !PART;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -361,6 +396,16 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
                 const T recv = __shfl_xor_sync(FULL, send, 16);
                 if (hb) t.top[c] = recv;
                 else t.bot[c] = recv;
+            }
+        } else if constexpr (H == 4) {
+            // band hb's top row is band hb-1's last row (L lanes down), its
+            // bottom row band hb+1's first row (L lanes up)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const T up = __shfl_up_sync(FULL, t.v[R - 1][c], L);
+                const T dn = __shfl_down_sync(FULL, t.v[0][c], L);
+                if (hb > 0) t.top[c] = up;
+                if (hb < H - 1) t.bot[c] = dn;
             }
         }
         if constexpr (NW > 1) {
@@ -713,37 +758,135 @@ __global__ void __launch_bounds__(1024, 2) vc_kernel(const CycArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Classic global-memory Jacobi (Section 3.2): one sweep per launch, one thread
-// per point, every point reads u_c only and writes u_{c+1}.  Same update
-// arithmetic and fused residual as the cycle kernels.
+// Classic global-memory Jacobi (Section 3.2): one sweep per launch, every
+// point reads u_c only and writes u_{c+1}.  Same update arithmetic and fused
+// residual as the cycle kernels.
+//
+// HBM-bound (12 B per point in binary32, 24 B in binary64), so the layout is
+// chosen for bytes in flight: a CTA of 32 x 8 threads covers a block of
+// 32*V columns x 8*R rows (classic2d_block_cols/rows); a thread owns one
+// 16-byte vector of V = 16 / sizeof(S) columns (ghost columns included, so
+// every vector starts on a 16-byte boundary) for R consecutive rows, issues
+// the R + 2 iterate rows and R right-hand-side rows as vector loads before it
+// computes anything, keeps the vertical neighbours in registers, and takes the
+// horizontal ones from its neighbouring lanes by shuffle (the two columns just
+// outside the warp's segment by scalar loads).  Ghost and padding columns in
+// a vector are stored back unchanged.
 // ---------------------------------------------------------------------------
+template <typename S, typename T>
+__device__ __forceinline__ void ld_vec16(const S *p, T (&out)[16 / sizeof(S)]) {
+    constexpr int V = 16 / (int)sizeof(S);
+    const uint4 raw = __ldg((const uint4 *)p);
+    S tmp[V];
+    memcpy(tmp, &raw, 16);
+#pragma unroll
+    for (int c = 0; c < V; ++c) out[c] = sm_s<S, T>(&tmp[c]);
+}
+
+// V values of the compute type (16 bytes or, for bfloat16 storage, 32)
+template <typename T, int V>
+__device__ __forceinline__ void ld_vecT(const T *p, T (&out)[V]) {
+    static_assert((V * sizeof(T)) % 16 == 0, "whole 16-byte chunks");
+#pragma unroll
+    for (int q = 0; q < (int)(V * sizeof(T)) / 16; ++q) {
+        const uint4 raw = __ldg((const uint4 *)p + q);
+        memcpy(&out[q * 16 / sizeof(T)], &raw, 16);
+    }
+}
+
+template <typename S, typename T>
+__device__ __forceinline__ void st_vec16(S *p, const T (&v)[16 / sizeof(S)]) {
+    constexpr int V = 16 / (int)sizeof(S);
+    S tmp[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) st_s<S, T>(&tmp[c], v[c]);
+    uint4 raw;
+    memcpy(&raw, tmp, 16);
+    *(uint4 *)p = raw;
+}
+
 template <typename S, typename T, bool EXACT, bool SIG, bool RES>
 __global__ void __launch_bounds__(256) classic2d_kernel(const CycArgs a) {
     if constexpr (RES) {
         if (*(volatile int *)&a.red.ctl->done >= 0) return;
     }
+    constexpr int V = 16 / (int)sizeof(S);
+    constexpr int R = kClassicRows;
+    constexpr int BX = 32 * V, BY = 8 * R;
     const long long ld = a.ld;
-    const int bxn = (a.nx + 31) / 32;
-    const long long nb = (long long)bxn * ((a.ny + 7) / 8);
+    const int nx = a.nx, ny = a.ny;
+    const int bxn = (nx + 2 + BX - 1) / BX;
+    const long long nb = (long long)bxn * ((ny + BY - 1) / BY);
     const Coef<T> kc = make_coef<T>(a);
     const S *__restrict__ uin = (const S *)a.uin;
+    const T *__restrict__ f = (const T *)a.f;
+    const T *__restrict__ dinv = (const T *)a.dinv;
+    S *__restrict__ uout = (S *)a.uout;
+    const int lane = threadIdx.x;
     typedef typename std::conditional<EXACT, double, T>::type Acc;
     Acc acc = 0;
     for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
-        const int i = 1 + (int)(b % bxn) * 32 + threadIdx.x;
-        const int j = 1 + (int)(b / bxn) * 8 + threadIdx.y;
-        if (i > a.nx || j > a.ny) continue;
-        const long long q = (long long)j * ld + i;
-        const T old = ld_s<S, T>(uin + q);
-        const T W = ld_s<S, T>(uin + q - 1), E = ld_s<S, T>(uin + q + 1);
-        const T Sv = ld_s<S, T>(uin + q - ld), Nv = ld_s<S, T>(uin + q + ld);
-        const T fv = __ldg((const T *)a.f + q);
-        const T iv = SIG ? __ldg((const T *)a.dinv + q) : (T)0;
-        const T g = (EXACT || SIG) ? fv : fv * kc.invd;
-        T res = 0;
-        const T nv = point_update<T, EXACT, SIG, true, RES>(kc, g, iv, W, E, Sv, Nv, old, res);
-        st_s<S, T>((S *)a.uout + q, nv);
-        acc += (Acc)res * (Acc)res;
+        const int c0 = (int)(b % bxn) * BX + lane * V;               // first column of this lane's vector
+        const int j0 = 1 + (int)(b / bxn) * BY + (int)threadIdx.y * R;   // first row (warp-uniform)
+        if (j0 > ny) continue;
+        const bool colok = c0 <= nx + 1;
+        T u[R + 2][V], g[R][V];
+        T dv[SIG ? R : 1][SIG ? V : 1];
+        T hw[R], he[R];
+        // every load first: iterate rows j0-1 .. j0+R, RHS (and 1/d) rows j0 .. j0+R-1,
+        // and the columns just outside the warp's segment
+#pragma unroll
+        for (int r = 0; r < R + 2; ++r) {
+            const int row = j0 - 1 + r;
+            if (colok && row <= ny + 1) {
+                ld_vec16<S, T>(uin + (long long)row * ld + c0, u[r]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < V; ++c) u[r][c] = (T)0;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = j0 + r;
+            const long long q = (long long)row * ld + c0;
+            if (colok && row <= ny) {
+                ld_vecT<T, V>(f + q, g[r]);
+                if constexpr (SIG) ld_vecT<T, V>(dinv + q, dv[r]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < V; ++c) {
+                    g[r][c] = (T)0;
+                    if constexpr (SIG) dv[r][c] = (T)0;
+                }
+            }
+            hw[r] = (lane == 0 && c0 >= 1 && row <= ny) ? ld_s<S, T>(uin + q - 1) : (T)0;
+            he[r] = (lane == 31 && c0 + V <= nx + 1 && row <= ny) ? ld_s<S, T>(uin + q + V) : (T)0;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = j0 + r;
+            T left = __shfl_up_sync(FULL, u[r + 1][V - 1], 1);
+            T right = __shfl_down_sync(FULL, u[r + 1][0], 1);
+            if (lane == 0) left = hw[r];
+            if (lane == 31) right = he[r];
+            T out[V];
+#pragma unroll
+            for (int c = 0; c < V; ++c) {
+                const int col = c0 + c;
+                const T W = c == 0 ? left : u[r + 1][c > 0 ? c - 1 : 0];
+                const T E = c == V - 1 ? right : u[r + 1][c < V - 1 ? c + 1 : 0];
+                const T gv = (EXACT || SIG) ? g[r][c] : g[r][c] * kc.invd;
+                T res = 0;
+                const T nv = point_update<T, EXACT, SIG, true, RES>(kc, gv, SIG ? dv[SIG ? r : 0][SIG ? c : 0] : (T)0,
+                                                                    W, E, u[r][c], u[r + 2][c], u[r + 1][c], res);
+                const bool in = col >= 1 && col <= nx;
+                out[c] = in ? nv : u[r + 1][c];
+                if constexpr (RES) {
+                    if (in) acc += (Acc)res * (Acc)res;
+                }
+            }
+            if (colok && row <= ny) st_vec16<S, T>(uout + (long long)row * ld + c0, out);
+        }
     }
     if constexpr (RES) reduce_grid_acc(a.red, acc);
 }

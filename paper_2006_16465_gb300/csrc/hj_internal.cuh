@@ -57,6 +57,17 @@ struct RedArgs {
 };
 
 // Arguments of one cycle (or one classic sweep).
+// Classic 2D sweep (classic2d_kernel): rows per thread, and the block of
+// points one CTA of 32 x 8 threads covers per step of its grid-stride loop
+// (columns counted from the ghost column 0, 16 bytes of storage per thread).
+constexpr int kClassicRows = 4;
+inline int classic2d_block_cols(int storage_bytes) { return 32 * (16 / storage_bytes); }
+inline int classic2d_block_rows() { return 8 * kClassicRows; }
+inline long long classic2d_blocks(int nx, int ny, int storage_bytes) {
+    const int bx = classic2d_block_cols(storage_bytes), by = classic2d_block_rows();
+    return (long long)((nx + 2 + bx - 1) / bx) * ((ny + by - 1) / by);
+}
+
 struct CycArgs {
     const void *f;       // right-hand side, compute type (grid layout)
     const void *uin;     // iterate u_c, storage type

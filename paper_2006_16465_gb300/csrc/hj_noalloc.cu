@@ -187,7 +187,7 @@ extern "C" int hj_cycles_noalloc(const hj_desc *desc, const hj_params *params, c
         int dev = 0, nsm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const long long nb = d.dim == 2 ? (long long)((d.nx + 31) / 32) * ((d.ny + 7) / 8)
+        const long long nb = d.dim == 2 ? classic2d_blocks(d.nx, d.ny, (int)esz)
                                         : (long long)((d.nx + 255) / 256) * d.ny;
         grid = dim3((unsigned)std::min<long long>(nb, 8LL * nsm));
         block = d.dim == 2 ? dim3(32, 8) : dim3(256);

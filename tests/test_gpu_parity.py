@@ -94,6 +94,32 @@ def test_f64_classic_sweeps_match_oracle(dim):
     assert np.array_equal(to_host(u, p.st.nx), ref)
 
 
+@pytest.mark.parametrize("prec,shape,sigma", [("f64", (2000, 1500), "field"), ("f64", (1031, 97), "none"),
+                                              ("f32", (4100, 3000), "field"), ("f32", (130, 7), "const")])
+def test_classic_sweeps_on_large_ragged_grids(prec, shape, sigma):
+    """The vectorised classic sweep walks many blocks per CTA (grid-stride),
+    with ragged edges in x (vectors holding ghost and padding columns) and y:
+    binary64 bitwise against the oracle, binary32 within 1e-5."""
+    torch = _torch()
+    nx, ny = shape
+    p = W.random_bc_problem(2, nx, ny, seed=nx + 1, sigma_kind=sigma, asym=True)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    s = gpu_solver(p, method="classic", precision=prec, fixed_cycles=4)
+    u = to_dev(p.u0, 2, dt)
+    s.solve(to_dev(p.f, 2, dt), u)
+    got = to_host(u, nx)
+    ref = oracle.run_fixed(p.st, p.f, p.u0, 4, classic=True)
+    if prec == "f64":
+        assert np.array_equal(got, ref)
+    else:
+        assert rel_max(got, ref) <= 1e-5
+    # the ghost ring (Dirichlet data) is untouched
+    ghost = p.u0.astype(np.float32).astype(np.float64) if prec == "f32" else p.u0
+    for sl in (np.s_[0, :], np.s_[-1, :], np.s_[:, 0], np.s_[:, -1]):
+        assert np.array_equal(got[sl], ghost[sl])
+    s.close()
+
+
 # ---------------------------------------------------------------------------
 # converging solves: same stopping cycle, same iterate, same residual history
 # ---------------------------------------------------------------------------
