@@ -851,26 +851,50 @@ def time_1d(torch, hj, W):
 
 def time_batched(torch, hj, W):
     """cfg4: 256 screened problems, sides from {64..512}, binary32 inner cycles
-    with binary64 refinement to 1e-8, one persistent launch per inner phase,
-    autotuned tile and per-size-class k (second call timed: tuning is cached)."""
+    with binary64 refinement to 1e-8: every refinement step one replay of a
+    captured graph around one persistent launch fed by the device work queue;
+    autotuned tile and per-size-class k (second call timed: tuning is cached).
+    The per-batch-cycle log gives the time against the points still active:
+    inner point updates per second against the binary32 FMA bound (SMs x 128
+    lanes x max SM clock / 4 FMA per update), and the time of the cycles with
+    fewer than 1M active points (the tail)."""
+    import ctypes as C
+    import numpy as np
     probs = W.batched_screened(256, seed=3)
     s = hj.Solver(probs[0].st, tile_x=32, tile_y=32, k=16, precision="f32_ir", tol=1e-8, autotune=1)
     fs = [hj.grid_from(q.f, 2, torch.float64) for q in probs]
     descs = [hj.make_desc(2, q.st.nx, q.st.ny, f.shape[1], q.st.cW, q.st.cE, q.st.cS, q.st.cN, q.st.cD,
                           q.st.sigma_const) for q, f in zip(probs, fs)]
+    cap = 1 << 20
+    ms = (C.c_double * cap)()
+    pts = (C.c_longlong * cap)()
     res = {}
     for rep in range(2):
         us = [hj.grid_from(q.u0, 2, torch.float64) for q in probs]
         st = hj.hj_stats()
+        st.cycle_ms = C.cast(ms, C.POINTER(C.c_double))
+        st.cycle_points = C.cast(pts, C.POINTER(C.c_longlong))
+        st.cycle_cap = cap
         cyc = (hj.C.c_longlong * len(probs))()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         code = hj.hj_solve_batched(s.h, descs, [f.data_ptr() for f in fs], [u.data_ptr() for u in us], 0, st, cyc)
         torch.cuda.synchronize()
-        res = {"seconds": time.perf_counter() - t0, "status": code, "worst_rel_residual": st.rel_final,
-               "outer_steps": st.outer_steps, "inner_cycles_total": st.inner_cycles,
-               "inner_cycles_max": max(cyc), "unknowns": sum(q.st.nx * q.st.ny for q in probs),
-               "tile": [st.tile_x, st.tile_y]}
+        n = st.cycle_len
+        m = np.array(ms[:n])
+        p = np.array(pts[:n], dtype=np.float64)
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        alu_peak = props.multi_processor_count * 128 * 2070e6 / 4
+        upd = float((p * st.k).sum()) if st.k else 0.0
+        res = {"seconds": time.perf_counter() - t0, "status": code, "graphed": st.graphed,
+               "worst_rel_residual": st.rel_final, "outer_steps": st.outer_steps,
+               "inner_cycles_total": st.inner_cycles, "inner_cycles_max": max(cyc),
+               "unknowns": sum(q.st.nx * q.st.ny for q in probs), "tile": [st.tile_x, st.tile_y], "k_max": st.k,
+               "batch_cycles": n, "batch_cycle_seconds": float(m.sum()),
+               "us_per_cycle_all_active": float(m[p >= p.max()].mean() * 1e3) if n else None,
+               "tail_cycles_lt_1M_points": int((p < 1e6).sum()), "tail_seconds": float(m[p < 1e6].sum()),
+               "inner_updates_per_s_at_k_max": upd / float(m.sum()) if n else None,
+               "inner_alu_frac_at_k_max": upd / float(m.sum()) / alu_peak if n else None}
     s.close()
     return res
 
@@ -1139,6 +1163,8 @@ def compact_summary(x):
                    "inner_k16_alu_frac": _r(x["inner_sweep_roofline_k16"]["frac"], 3),
                    "cfg1_gpu_speedup": _r(x["cfg1_1d_to_1e-6"]["speedup"], 3),
                    "cfg4_s": _r(x["cfg4_batched_256_to_1e-8"]["seconds"], 3),
+                   "cfg4_graphed": x["cfg4_batched_256_to_1e-8"]["graphed"],
+                   "cfg4_tail_s": _r(x["cfg4_batched_256_to_1e-8"]["tail_seconds"], 3),
                    "cfg5_fwd_bwd_s": [_r(x["cfg5_differentiation_1024"]["forward_seconds"], 3),
                                       _r(x["cfg5_differentiation_1024"]["backward_seconds"], 3)]}
     return out

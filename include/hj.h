@@ -255,6 +255,19 @@ typedef struct {
     int ctas_per_sm;          /* its CTAs-per-SM cap (0 = as many as fit)         */
     int overlap_x, overlap_y; /* overlapping points used (Sections 3.4, 4.3)      */
     int tile_z;               /* 3D: subdomain depth used (1 otherwise)           */
+    /* hj_solve_batched / hj_solve_adjoint_batched: */
+    int graphed;              /* 1 if every refinement step ran as a replay of one
+                                 captured CUDA graph (zero the corrections, the
+                                 persistent inner launch, the binary64 update and
+                                 residual, the retirement decisions)              */
+    double *cycle_ms;         /* caller-owned host array (nullable): duration of
+                                 each batch cycle (every active problem advances
+                                 one inner cycle), refinement steps one after
+                                 another                                          */
+    long long *cycle_points;  /* caller-owned host array (nullable): interior
+                                 points of the problems active in that cycle      */
+    long long cycle_cap;      /* capacity of cycle_ms and cycle_points            */
+    long long cycle_len;      /* batch cycles recorded (at most cycle_cap)        */
 } hj_stats;
 
 /* Fill p with defaults: hierarchical, 32 x 32 tiles, k = 16, HJ_PREC_F64,

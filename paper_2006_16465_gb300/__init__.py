@@ -64,7 +64,9 @@ class hj_stats(C.Structure):
                 ("history_len", C.c_longlong), ("wall_ms", C.c_double), ("tile_x", C.c_int),
                 ("tile_y", C.c_int), ("k", C.c_int), ("tile_threads", C.c_int), ("persistent", C.c_int),
                 ("pipeline_stages", C.c_int), ("ctas_per_sm", C.c_int), ("overlap_x", C.c_int),
-                ("overlap_y", C.c_int), ("tile_z", C.c_int)]
+                ("overlap_y", C.c_int), ("tile_z", C.c_int), ("graphed", C.c_int),
+                ("cycle_ms", C.POINTER(C.c_double)), ("cycle_points", C.POINTER(C.c_longlong)),
+                ("cycle_cap", C.c_longlong), ("cycle_len", C.c_longlong)]
 
 
 class HJError(RuntimeError):
@@ -396,7 +398,7 @@ def solve(stencil, f, u, sigma=None, coef=None, stream=None, history: int = 0, *
 
 
 def _stats_dict(st: hj_stats, hbuf):
-    d = {k: getattr(st, k) for k, _ in hj_stats._fields_ if k != "history"}
+    d = {k: getattr(st, k) for k, _ in hj_stats._fields_ if k not in ("history", "cycle_ms", "cycle_points")}
     if hbuf is not None:
         d["history"] = [hbuf[i] for i in range(st.history_len)]
     return d

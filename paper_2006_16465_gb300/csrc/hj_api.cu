@@ -979,10 +979,10 @@ void hj_destroy(hj_handle *h) {
     if (h->mg_exec) cudaGraphExecDestroy(h->mg_exec);
     if (h->mg_arena) cudaFree(h->mg_arena);
     void *dev[] = {h->ubuf, h->ubuf2, h->dC, h->vcf, h->dinv_outer, h->dinv32, h->r32, h->dA, h->dB, h->hf, h->hu, h->partials, h->gpart,
-                   h->hist, h->rstore, h->gcnt, h->fcnt, h->ctl, h->pscratch, h->barena, h->rs};
+                   h->hist, h->rstore, h->gcnt, h->fcnt, h->ctl, h->pscratch, h->barena, h->rs, h->bmeta};
     for (void *p : dev)
         if (p) cudaFree(p);
-    void *pin[] = {h->h_ctl, h->h_ctl_init, h->h_hist, h->h_rstore, h->h_pstage, h->h_rs};
+    void *pin[] = {h->h_ctl, h->h_ctl_init, h->h_hist, h->h_rstore, h->h_pstage, h->h_rs, h->h_bmeta};
     for (void *p : pin)
         if (p) cudaFreeHost(p);
     if (h->cap) cudaStreamDestroy(h->cap);

@@ -88,8 +88,22 @@ long long env_ll(const char *name, long long dflt) {
 }
 }  // namespace
 
-int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vector<PersistProblem> &probs,
-                   cudaStream_t s, std::vector<ProbState> *out, PersistKernel classic, int fam) {
+// One persistent launch: its arguments, staged in the handle's persistent
+// scratch (pinned host copy hb, device copy db), and the kernel's shape.
+struct PersistLaunch {
+    PersistArgs P;
+    const void *fn = nullptr;
+    int grid = 0, threads = 256, smem = 0;
+    unsigned char *hb = nullptr, *db = nullptr;
+    size_t o_state = 0, o_bar = 0, total = 0;
+};
+
+// Lay out and upload the arguments of a persistent launch over probs: the
+// per-problem cycle arguments and state, the (problem, block) items, the
+// partials, the barrier words, the work queue (rebuilt by the first barrier
+// of a multi-problem launch) and, for TMA staging, each problem's tensor maps.
+int persist_setup(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vector<PersistProblem> &probs,
+                  cudaStream_t s, PersistKernel classic, int fam, PersistLaunch *L) {
     const int nprob = (int)probs.size();
     bool tma = !classic && fam >= 0 && persist_uses_tma(h, ki, sig);
     // tensor maps of each problem's two iterate buffers, RHS and 1/d; arrays
@@ -127,7 +141,11 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
     const size_t o_ptx = al(o_pn + nprob * sizeof(int));
     const size_t o_part = al(o_ptx + nprob * sizeof(int));
     const size_t o_bar = al(o_part + 2 * nitems * sizeof(double));
-    const size_t o_maps = al(o_bar + 4 * sizeof(unsigned));
+    const size_t o_q = al(o_bar + 4 * sizeof(unsigned));          // head, count, changed, (pad)
+    const size_t o_qitems = al(o_q + 4 * sizeof(int) + 2 * sizeof(long long));
+    const size_t o_qoff = al(o_qitems + nitems * sizeof(int));
+    const size_t o_ppts = al(o_qoff + nprob * sizeof(int));
+    const size_t o_maps = al(o_ppts + nprob * sizeof(long long));
     const size_t total = al(o_maps + (tma ? nprob * sizeof(PersistMaps) : 0));
     CKS(ensure_scratch(h, total));
     unsigned char *hb = h->h_pstage;
@@ -136,6 +154,7 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
     ProbState *hs = (ProbState *)(hb + o_state);
     int *hip = (int *)(hb + o_iprob), *hib = (int *)(hb + o_iblk);
     int *hp0 = (int *)(hb + o_p0), *hpn = (int *)(hb + o_pn), *hptx = (int *)(hb + o_ptx);
+    long long *hpts = (long long *)(hb + o_ppts);
     long long it = 0;
     for (int p = 0; p < nprob; ++p) {
         hp[p] = probs[p].a;
@@ -143,6 +162,7 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
         hp0[p] = (int)it;
         hpn[p] = probs[p].blocks;
         hptx[p] = probs[p].blocks_x;
+        hpts[p] = (long long)probs[p].a.nx * probs[p].a.ny;
         for (int b = 0; b < probs[p].blocks; ++b, ++it) {
             hip[it] = p;
             hib[it] = b;
@@ -153,8 +173,13 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
     hbar[0] = hbar[1] = 0u;
     ((int *)hbar)[2] = nprob;   // active
     ((int *)hbar)[3] = 0;       // err
+    int *hq = (int *)(hb + o_q);
+    hq[0] = 0;                  // head
+    hq[1] = 0;                  // count
+    hq[2] = 1;                  // changed: the first barrier builds the queue
+    hq[3] = 0;
     CKR(cudaMemcpyAsync(db, hb, total, cudaMemcpyHostToDevice, s));
-    PersistArgs P;
+    PersistArgs &P = L->P;
     memset(&P, 0, sizeof(P));
     P.probs = (const CycArgs *)(db + o_probs);
     P.state = (ProbState *)(db + o_state);
@@ -176,6 +201,13 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
     P.skip_barrier_cta = (int)env_ll("HJ_TEST_SKIP_BARRIER_CTA", -1);
     P.maps = tma ? (const PersistMaps *)(db + o_maps) : nullptr;
     P.spin_limit = 1LL << 26;
+    P.q_head = (int *)(db + o_q);
+    P.q_count = (int *)(db + o_q) + 1;
+    P.q_changed = (int *)(db + o_q) + 2;
+    P.q_points = (long long *)(db + o_q + 4 * sizeof(int));
+    P.q_items = (int *)(db + o_qitems);
+    P.q_off = (int *)(db + o_qoff);
+    P.prob_points = (const long long *)(db + o_ppts);
     int cap = 0, threads = 256;
     if (classic) {
         int occ = 0;
@@ -186,18 +218,40 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
         threads = ki->threads;
     }
     if (cap < 1) return seterr(HJ_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
-    const int grid = (int)std::min<long long>(nitems, cap);
-    void *args[] = {&P};
-    // one problem: one grid barrier per cycle; several: two (reduce, then retire)
-    const void *fn = classic ? (const void *)classic
-                     : tma ? (nprob == 1 ? (const void *)ki->tma_one[sig] : (const void *)ki->tma_fn[sig])
-                           : (nprob == 1 ? (const void *)ki->one[sig] : (const void *)ki->fn[sig]);
-    CKR(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, tma ? ki->tma_smem[sig] : 0, s));
-    CKR(cudaMemcpyAsync(hb + o_state, db + o_state, nprob * sizeof(ProbState), cudaMemcpyDeviceToHost, s));
-    CKR(cudaMemcpyAsync(hb + o_bar, db + o_bar, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    L->grid = (int)std::min<long long>(nitems, cap);
+    L->threads = threads;
+    L->smem = tma ? ki->tma_smem[sig] : 0;
+    // one problem: one grid barrier per cycle; several: two (reduce, then
+    // retire and rebuild the work queue)
+    L->fn = classic ? (const void *)classic
+            : tma ? (nprob == 1 ? (const void *)ki->tma_one[sig] : (const void *)ki->tma_fn[sig])
+                  : (nprob == 1 ? (const void *)ki->one[sig] : (const void *)ki->fn[sig]);
+    L->hb = hb;
+    L->db = db;
+    L->o_state = o_state;
+    L->o_bar = o_bar;
+    L->total = total;
+    return HJ_OK;
+}
+
+int persist_launch(const PersistLaunch &L, cudaStream_t s) {
+    void *args[] = {const_cast<PersistArgs *>(&L.P)};
+    CKR(cudaLaunchCooperativeKernel(L.fn, dim3(L.grid), dim3(L.threads), args, L.smem, s));
+    return HJ_OK;
+}
+
+int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vector<PersistProblem> &probs,
+                   cudaStream_t s, std::vector<ProbState> *out, PersistKernel classic, int fam) {
+    PersistLaunch L;
+    CKS(persist_setup(h, ki, sig, probs, s, classic, fam, &L));
+    const int nprob = (int)probs.size();
+    CKS(persist_launch(L, s));
+    CKR(cudaMemcpyAsync(L.hb + L.o_state, L.db + L.o_state, nprob * sizeof(ProbState), cudaMemcpyDeviceToHost, s));
+    CKR(cudaMemcpyAsync(L.hb + L.o_bar, L.db + L.o_bar, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CKR(cudaEventRecord(h->ev, s));
     CKR(cudaEventSynchronize(h->ev));
-    if (((int *)hbar)[3]) return seterr(HJ_ERR_TIMEOUT, "a bounded grid-barrier wait expired");
+    if (((int *)(L.hb + L.o_bar))[3]) return seterr(HJ_ERR_TIMEOUT, "a bounded grid-barrier wait expired");
+    const ProbState *hs = (const ProbState *)(L.hb + L.o_state);
     out->assign(hs, hs + nprob);
     for (int p = 0; p < nprob; ++p)
         if ((*out)[p].done < 0) return seterr(HJ_ERR_CUDA, "persistent launch ended with problem %d active", p);
@@ -209,13 +263,178 @@ int run_persistent(hj_handle *h, const PersistKernelInfo *ki, bool sig, std::vec
 // ===========================================================================
 // hj_solve_batched
 // ===========================================================================
-namespace {
+namespace hj {
+namespace bsched {
 
-struct BProb;
+// ---------------------------------------------------------------------------
+// Device side of the refinement loop over a batch.  Every problem has binary64
+// iterate buffers u[0] (the caller's) and u[1], a binary32 residual r32 (the
+// inner right-hand side), two correction buffers d[0], d[1] and an outer state.
+// One refinement step is, for the problems still refining:
+//   zero d[0]; inner cycles A d = r32 (the persistent launch, d[0] -> d[1] ...);
+//   u[cur ^ 1] = u[cur] + d, r = f - A u[cur ^ 1] (binary64), ||r||;
+//   retire the problem once ||r|| <= tol ||r_0|| (or if it diverged).
+// The same kernels run every step (problems that retired return at once), so
+// a step is one CUDA graph.
+// ---------------------------------------------------------------------------
+struct BDev {
+    const double *f;
+    double *u[2];
+    float *r32;
+    void *d[2];
+    const double *sigma;
+    long long ld, ld_in;      // pitch of f, u, sigma; pitch of r32 and d
+    int nx, ny;
+    double cW, cE, cS, cN, dconst;
+    int aux0, naux;           // first aux item (block of 32 x 8 interior points) and count
+};
 
-}  // namespace
+struct BOuter {
+    double r0, rn;            // ||f - A u_0||, ||f - A u|| of the current iterate
+    long long inner;          // inner cycles so far
+    int active;               // still refining
+    int cur;                  // buffer holding the iterate
+    int status;               // HJ_OK / HJ_ERR_DIVERGED
+    int outer;                // refinement steps taken
+};
 
-namespace {
+struct BatchArgs {
+    const BDev *prob;
+    BOuter *outer;
+    ProbState *state;         // the inner engine's per-problem state
+    int *inner_active;        // the inner engine's count of active problems
+    int *q_changed;           // the inner engine's queue: rebuild at the next launch
+    const int *aux_prob;      // per aux item: its problem
+    double *aux_part;         // per aux item: its share of ||r||^2
+    int *count;               // problems still refining (read by the host)
+    int nprob, naux;
+    double tol;
+};
+
+__device__ __forceinline__ bool aux_point(const BDev &b, int a, int &i, int &j) {
+    const int bxn = (b.nx + 31) / 32;
+    const int blk = a - b.aux0;
+    i = 1 + (blk % bxn) * 32 + (int)threadIdx.x;
+    j = 1 + (blk / bxn) * 8 + (int)threadIdx.y;
+    return i <= b.nx && j <= b.ny;
+}
+
+// zero d[0] on the interior of every refining problem (the ghost ring of the
+// corrections is zero from the start and never written)
+template <typename DS>
+__global__ void __launch_bounds__(256) batch_zero_kernel(const BatchArgs A) {
+    for (int a = blockIdx.x; a < A.naux; a += gridDim.x) {
+        const int p = A.aux_prob[a];
+        if (!A.outer[p].active) continue;
+        const BDev b = A.prob[p];
+        int i, j;
+        if (aux_point(b, a, i, j)) ((DS *)b.d[0])[(long long)j * b.ld_in + i] = DS(0.0f);
+    }
+}
+
+template <typename DS>
+__device__ __forceinline__ double corr(const DS *p) { return (double)(float)*p; }
+
+// INIT: r = f - A u[cur] for every problem; else u[cur ^ 1] = u[cur] + d and
+// r = f - A u[cur ^ 1] for the refining problems (d = the inner solve's last
+// buffer, by the parity of its cycle count).  r goes to r32 and each aux
+// item's ||r||^2 share to aux_part (fixed order within the item).
+template <typename DS, bool INIT>
+__global__ void __launch_bounds__(256) batch_residual_kernel(const BatchArgs A) {
+    __shared__ double s_w[8];
+    for (int a = blockIdx.x; a < A.naux; a += gridDim.x) {
+        const int p = A.aux_prob[a];
+        const BOuter o = A.outer[p];
+        if (!INIT && !o.active) continue;
+        const BDev b = A.prob[p];
+        int i, j;
+        double rr = 0.0;
+        if (aux_point(b, a, i, j)) {
+            const double *u = b.u[o.cur];
+            const long long q = (long long)j * b.ld + i, q2 = (long long)j * b.ld_in + i;
+            double uc = u[q], uW = u[q - 1], uE = u[q + 1], uS = u[q - b.ld], uN = u[q + b.ld];
+            if constexpr (!INIT) {
+                const DS *d = (const DS *)b.d[A.state[p].done & 1];
+                uc = __dadd_rn(uc, corr(d + q2));
+                uW = __dadd_rn(uW, corr(d + q2 - 1));
+                uE = __dadd_rn(uE, corr(d + q2 + 1));
+                uS = __dadd_rn(uS, corr(d + q2 - b.ld_in));
+                uN = __dadd_rn(uN, corr(d + q2 + b.ld_in));
+                b.u[o.cur ^ 1][q] = uc;
+            }
+            const double dg = b.sigma ? __dadd_rn(b.dconst, b.sigma[q]) : b.dconst;
+            double r = fma(-dg, uc, b.f[q]);
+            r = fma(-b.cW, uW, r);
+            r = fma(-b.cE, uE, r);
+            r = fma(-b.cS, uS, r);
+            r = fma(-b.cN, uN, r);
+            b.r32[q2] = (float)r;
+            rr = r * r;
+        }
+        rr = warp_sum(rr);
+        const int w = (threadIdx.y * 32 + threadIdx.x) >> 5;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) s_w[w] = rr;
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t += s_w[k];
+            A.aux_part[a] = t;
+        }
+    }
+}
+
+// One CTA: ||r|| of every refining problem (its aux shares in a fixed order),
+// retirement, and the inner engine's state for the next step.
+template <bool INIT>
+__global__ void __launch_bounds__(1024) batch_finalize_kernel(const BatchArgs A) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int mine = 0;
+    for (int p = w; p < A.nprob; p += nw) {
+        BOuter o = A.outer[p];
+        if (o.active) {
+            const BDev &b = A.prob[p];
+            double s = 0.0;
+            for (int k = lane; k < b.naux; k += 32) s += A.aux_part[b.aux0 + k];
+            s = warp_sum(s);
+            const double rn = sqrt(s);
+            if (INIT) {
+                o.r0 = rn;
+            } else {
+                o.inner += A.state[p].done;
+                o.cur ^= 1;
+                o.outer += 1;
+            }
+            o.rn = rn;
+            if (!isfinite(rn)) {
+                o.status = HJ_ERR_DIVERGED;
+                o.active = 0;
+            } else if (rn <= A.tol * o.r0) {
+                o.active = 0;
+            }
+        }
+        if (lane == 0) {
+            A.outer[p] = o;
+            // the inner engine's state: refining problems start afresh,
+            // the others are left out of the work queue
+            ProbState &st = A.state[p];
+            st = ProbState{o.active ? -1 : 0, HJ_OK, 0, 0.0, 0.0, 0.0, 0};
+            mine += o.active;
+        }
+    }
+    __shared__ int s_n[32];
+    mine = __reduce_add_sync(0xffffffffu, mine);
+    if (lane == 0) s_n[w] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int n = 0;
+        for (int k = 0; k < nw; ++k) n += s_n[k];
+        *A.count = n;
+        *A.inner_active = n;
+        *A.q_changed = 1;
+    }
+}
 
 struct BProb {
     hj_desc d;
@@ -227,11 +446,7 @@ struct BProb {
     double *u2;              // second binary64 buffer
     float *r32;              // binary32 residual (inner RHS)
     void *dA, *dB;           // correction buffers
-    double *cur, *other;
     float *dinv;             // per-point 1/d in binary32 (some problem of the batch has sigma)
-    double r0, rn;
-    bool active;
-    long long inner_cycles;
 };
 
 // transpose: the adjoint operator A^T (cW <-> cE, cS <-> cN)
@@ -285,7 +500,13 @@ int validate_desc(const hj_desc &d, int i) {
     return HJ_OK;
 }
 
-}  // namespace
+// grid-stride launch shape of the batch kernels
+dim3 batch_grid(int naux, int nsm) { return dim3((unsigned)std::max(1, std::min(naux, 8 * nsm))); }
+
+}  // namespace bsched
+}  // namespace hj
+
+using namespace hj::bsched;
 
 int batched_core(hj_handle *h, int nprob, const hj_desc *descs, const void *const *f, void *const *u,
                  hj_stream stream, hj_stats *stats, long long *cycles_out, bool transpose) {
@@ -316,7 +537,7 @@ int batched_core(hj_handle *h, int nprob, const hj_desc *descs, const void *cons
     bool sig_any = false;
     for (int i = 0; i < nprob; ++i) sig_any |= descs[i].sigma != nullptr;
     std::vector<BProb> P(nprob);
-    size_t arena = 0, maxaux = 0;
+    size_t arena = 0;
     for (int i = 0; i < nprob; ++i) {
         if (!f[i] || !u[i] || ((uintptr_t)f[i] & 15) || ((uintptr_t)u[i] & 15))
             return seterr(HJ_ERR_INVALID_ARG, "problem %d: f/u NULL or not 16-byte aligned", i);
@@ -331,9 +552,7 @@ int batched_core(hj_handle *h, int nprob, const hj_desc *descs, const void *cons
         arena += (b.nin * 4 + 255) / 256 * 256;                       // r32
         arena += 2 * ((b.nin * dsz + 255) / 256 * 256);               // dA, dB
         if (sig_any) arena += (b.nin * 4 + 255) / 256 * 256;          // per-point 1/d (binary32)
-        maxaux = std::max(maxaux, (size_t)aux_max_blocks(2, b.d.nx, b.d.ny));
     }
-    CKS(ensure_reduction(h, maxaux));
     if (arena > h->barena_bytes) {
         CKR(cudaDeviceSynchronize());
         if (h->barena) cudaFree(h->barena);
@@ -344,19 +563,6 @@ int batched_core(hj_handle *h, int nprob, const hj_desc *descs, const void *cons
             return seterr(HJ_ERR_NO_MEMORY, "batched workspace of %zu bytes", arena);
         }
         h->barena_bytes = arena;
-    }
-    if (h->nrs < (size_t)nprob) {
-        if (h->rs) cudaFree(h->rs);
-        if (h->h_rs) cudaFreeHost(h->h_rs);
-        h->rs = nullptr;
-        h->h_rs = nullptr;
-        h->nrs = 0;
-        if (cudaMalloc((void **)&h->rs, nprob * sizeof(double)) != cudaSuccess ||
-            cudaMallocHost((void **)&h->h_rs, nprob * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            return seterr(HJ_ERR_NO_MEMORY, "batched norms");
-        }
-        h->nrs = nprob;
     }
     unsigned char *ap = (unsigned char *)h->barena;
     for (auto &b : P) {
@@ -373,113 +579,218 @@ int batched_core(hj_handle *h, int nprob, const hj_desc *descs, const void *cons
         }
         CKR(cudaMemcpyAsync(b.u2, b.u, (size_t)b.rows * b.d.ld * 8, cudaMemcpyDeviceToDevice, s));
         CKR(cudaMemsetAsync(b.r32, 0, b.nin * 4, s));
+        CKR(cudaMemsetAsync(b.dA, 0, b.nin * dsz, s));
         CKR(cudaMemsetAsync(b.dB, 0, b.nin * dsz, s));
-        b.cur = b.u;
-        b.other = b.u2;
-        b.active = true;
-        b.inner_cycles = 0;
     }
-    auto norms = [&](bool update, const std::vector<int> &act, const std::vector<ProbState> *st) -> int {
-        for (size_t j = 0; j < act.size(); ++j) {
-            BProb &b = P[act[j]];
-            const CycArgs g = prob_args(b.d, par, transpose);
-            RedArgs red;
-            memset(&red, 0, sizeof(red));
-            red.partials = h->partials; red.gpart = h->gpart; red.gcnt = h->gcnt; red.fcnt = h->fcnt;
-            red.out = h->rs + act[j];
-            red.mode = RED_STORE;
-            red.scale = 1.0;
-            if (!update) {
-                CKR(launch_residual_ex(2, 1, b.f, b.cur, b.d.sigma, b.d.ld, b.ld_in, b.d.nx, b.d.ny, g.cW, g.cE,
-                                       g.cS, g.cN, g.dconst, 0, b.r32, red, s));
-            } else {
-                const void *dsel = ((*st)[j].done & 1) ? b.dB : b.dA;
-                CKR(launch_update_residual_ex(2, b.f, b.cur, dsel, bf16 ? 1 : 0, b.other, b.d.sigma, b.r32, b.d.ld,
-                                              b.ld_in, b.d.nx, b.d.ny, g.cW, g.cE, g.cS, g.cN, g.dconst, red, s));
-                std::swap(b.cur, b.other);
-            }
+    // the inner engine over every problem of the batch (its work queue holds
+    // the items of the problems still refining)
+    std::vector<PersistProblem> pp(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        BProb &b = P[i];
+        PersistProblem &q = pp[i];
+        q.a = prob_args(b.d, par, transpose);
+        q.a.k = kprob[i];
+        q.a.ld = b.ld_in;
+        q.a.f = b.r32;
+        q.a.uin = b.dA;
+        q.a.uout = b.dB;
+        q.a.dinv = b.dinv;
+        q.a.red.tol = par.inner_tol;
+        q.a.red.max_cycles = par.inner_max_cycles;
+        // the per-point-diagonal kernel forms r itself; the constant-diagonal one forms (u' - u)
+        q.a.red.scale = sig_any ? 1.0 : q.a.dconst * q.a.dconst;
+        q.a.red.stall_window = par.inner_stall;
+        q.a.red.stall_rtol = 1e-3;
+        q.blocks_x = (b.d.nx + ki->tx - 1) / ki->tx;
+        q.blocks = q.blocks_x * ((b.d.ny + ki->ty - 1) / ki->ty);
+    }
+    PersistLaunch L;
+    CKS(persist_setup(h, ki, sig_any, pp, s, nullptr, fam, &L));
+    // batch metadata: per-problem buffers, outer state, aux items, the host
+    // word and the per-cycle log
+    const long long logcap = (stats && (stats->cycle_ms || stats->cycle_points)) ? std::max(0LL, stats->cycle_cap) : 0;
+    long long naux = 0;
+    std::vector<BDev> hd(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        const BProb &b = P[i];
+        const CycArgs g = prob_args(b.d, par, transpose);
+        BDev &x = hd[i];
+        x.f = b.f;
+        x.u[0] = b.u;
+        x.u[1] = b.u2;
+        x.r32 = b.r32;
+        x.d[0] = b.dA;
+        x.d[1] = b.dB;
+        x.sigma = b.d.sigma;
+        x.ld = b.d.ld;
+        x.ld_in = b.ld_in;
+        x.nx = b.d.nx;
+        x.ny = b.d.ny;
+        x.cW = g.cW; x.cE = g.cE; x.cS = g.cS; x.cN = g.cN; x.dconst = g.dconst;
+        x.aux0 = (int)naux;
+        x.naux = ((b.d.nx + 31) / 32) * ((b.d.ny + 7) / 8);
+        naux += x.naux;
+    }
+    if (naux > (1LL << 30)) return seterr(HJ_ERR_INVALID_ARG, "batch too large");
+    const size_t m_prob = 0;
+    const size_t m_outer = al(m_prob + nprob * sizeof(BDev));
+    const size_t m_auxp = al(m_outer + nprob * sizeof(BOuter));
+    const size_t m_part = al(m_auxp + naux * sizeof(int));
+    const size_t m_word = al(m_part + naux * sizeof(double));
+    const size_t m_tlog = al(m_word + 4 * sizeof(long long));
+    const size_t m_total = al(m_tlog + (logcap > 0 ? 2 * (logcap + 1) * sizeof(unsigned long long) : 0));
+    if (m_total > h->bmeta_bytes) {
+        CKR(cudaDeviceSynchronize());
+        if (h->bmeta) cudaFree(h->bmeta);
+        if (h->h_bmeta) cudaFreeHost(h->h_bmeta);
+        h->bmeta = nullptr;
+        h->h_bmeta = nullptr;
+        h->bmeta_bytes = 0;
+        if (cudaMalloc(&h->bmeta, m_total) != cudaSuccess ||
+            cudaMallocHost((void **)&h->h_bmeta, m_total) != cudaSuccess) {
+            cudaGetLastError();
+            return seterr(HJ_ERR_NO_MEMORY, "batch metadata of %zu bytes", m_total);
         }
-        CKR(cudaMemcpyAsync(h->h_rs, h->rs, nprob * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CKR(cudaEventRecord(h->ev, s));
-        CKR(cudaEventSynchronize(h->ev));
-        for (int i : act) P[i].rn = sqrt(h->h_rs[i]);
+        h->bmeta_bytes = m_total;
+    }
+    unsigned char *hm = h->h_bmeta, *dm = (unsigned char *)h->bmeta;
+    memcpy(hm + m_prob, hd.data(), nprob * sizeof(BDev));
+    BOuter *ho = (BOuter *)(hm + m_outer);
+    for (int i = 0; i < nprob; ++i) ho[i] = BOuter{0.0, 0.0, 0, 1, 0, HJ_OK, 0};
+    int *hauxp = (int *)(hm + m_auxp);
+    for (int i = 0; i < nprob; ++i)
+        for (int a = 0; a < hd[i].naux; ++a) hauxp[hd[i].aux0 + a] = i;
+    long long *hword = (long long *)(hm + m_word);
+    hword[0] = hword[1] = hword[2] = hword[3] = 0;
+    CKR(cudaMemcpyAsync(dm, hm, m_word + 4 * sizeof(long long), cudaMemcpyHostToDevice, s));
+    if (logcap > 0) {
+        L.P.tlog = (unsigned long long *)(dm + m_tlog);
+        L.P.tlog_n = (long long *)(dm + m_word) + 1;
+        L.P.tlog_cap = logcap + 1;
+    }
+    BatchArgs B;
+    memset(&B, 0, sizeof(B));
+    B.prob = (const BDev *)(dm + m_prob);
+    B.outer = (BOuter *)(dm + m_outer);
+    B.state = L.P.state;
+    B.inner_active = L.P.active;
+    B.q_changed = L.P.q_changed;
+    B.aux_prob = (const int *)(dm + m_auxp);
+    B.aux_part = (double *)(dm + m_part);
+    B.count = (int *)(dm + m_word);
+    B.nprob = nprob;
+    B.naux = (int)naux;
+    B.tol = par.tol;
+    const dim3 bg = batch_grid((int)naux, h->nsm), bb(32, 8);
+    int *hcount = (int *)hword;
+    // ||r_0|| of every problem, r32 = r_0; the problems already within tol retire
+    batch_residual_kernel<float, true><<<bg, bb, 0, s>>>(B);
+    batch_finalize_kernel<true><<<1, 1024, 0, s>>>(B);
+    CKR(cudaGetLastError());
+    CKR(cudaMemcpyAsync(hcount, B.count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKR(cudaEventRecord(h->ev, s));
+    CKR(cudaEventSynchronize(h->ev));
+    // one refinement step: zero the corrections, the persistent inner launch,
+    // the binary64 update and residual, the retirement decisions, the count
+    auto step = [&](cudaStream_t st) -> int {
+        if (bf16) batch_zero_kernel<__nv_bfloat16><<<bg, bb, 0, st>>>(B);
+        else batch_zero_kernel<float><<<bg, bb, 0, st>>>(B);
+        CKS(persist_launch(L, st));
+        if (bf16) batch_residual_kernel<__nv_bfloat16, false><<<bg, bb, 0, st>>>(B);
+        else batch_residual_kernel<float, false><<<bg, bb, 0, st>>>(B);
+        batch_finalize_kernel<false><<<1, 1024, 0, st>>>(B);
+        CKR(cudaGetLastError());
+        CKR(cudaMemcpyAsync(hcount, B.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CKR(cudaMemcpyAsync(hcount + 1, L.P.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         return HJ_OK;
     };
-    std::vector<int> act;
-    for (int i = 0; i < nprob; ++i) act.push_back(i);
-    CKS(norms(false, act, nullptr));
-    for (auto &b : P) b.r0 = b.rn;
-    int o = 0, status = HJ_OK;
-    long long total_inner = 0;
-    for (;; ++o) {
-        std::vector<int> next;
-        for (int i : act) {
-            BProb &b = P[i];
-            if (!std::isfinite(b.rn)) { status = HJ_ERR_DIVERGED; b.active = false; continue; }
-            if (b.rn <= par.tol * b.r0) { b.active = false; continue; }
-            next.push_back(i);
+    int o = 0, graphed = 0;
+    hcount[1] = 0;
+    cudaGraphExec_t gexec = nullptr;
+    if (hcount[0] > 0) {
+        // capture the step once; replay it while problems are refining
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const int cs = step(h->cap);
+            const cudaError_t ee = cudaStreamEndCapture(h->cap, &graph);
+            if (cs == HJ_OK && ee == cudaSuccess && graph &&
+                cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess)
+                graphed = 1;
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
         }
-        act.swap(next);
-        if (act.empty()) break;
-        if (o >= par.max_outer) { status = HJ_ERR_NOT_CONVERGED; break; }
-        std::vector<PersistProblem> pp;
-        for (int i : act) {
-            BProb &b = P[i];
-            CKR(cudaMemsetAsync(b.dA, 0, b.nin * dsz, s));
-            PersistProblem q;
-            q.a = prob_args(b.d, par, transpose);
-            q.a.k = kprob[i];
-            q.a.ld = b.ld_in;
-            q.a.f = b.r32;
-            q.a.uin = b.dA;
-            q.a.uout = b.dB;
-            q.a.dinv = b.dinv;
-            q.a.red.tol = par.inner_tol;
-            q.a.red.max_cycles = par.inner_max_cycles;
-            // the per-point-diagonal kernel forms r itself; the constant-diagonal one forms (u' - u)
-            q.a.red.scale = sig_any ? 1.0 : q.a.dconst * q.a.dconst;
-            q.a.red.stall_window = par.inner_stall;
-            q.a.red.stall_rtol = 1e-3;
-            q.blocks_x = (b.d.nx + ki->tx - 1) / ki->tx;
-            q.blocks = q.blocks_x * ((b.d.ny + ki->ty - 1) / ki->ty);
-            pp.push_back(q);
-        }
-        std::vector<ProbState> st;
-        CKS(run_persistent(h, ki, sig_any, pp, s, &st, nullptr, fam));
-        for (size_t j = 0; j < act.size(); ++j) {
-            P[act[j]].inner_cycles += st[j].done;
-            total_inner += st[j].done;
-        }
-        CKS(norms(true, act, &st));
     }
-    for (auto &b : P)
-        if (b.cur != b.u) CKR(cudaMemcpyAsync(b.u, b.cur, (size_t)b.rows * b.d.ld * 8, cudaMemcpyDeviceToDevice, s));
-    CKR(cudaStreamSynchronize(s));
-    if (cycles_out)
-        for (int i = 0; i < nprob; ++i) cycles_out[i] = P[i].inner_cycles;
-    if (stats) {
-        double r0 = 0, rn = 0;
-        for (auto &b : P) {
-            r0 = std::max(r0, b.r0 > 0 ? 1.0 : 0.0);
-            rn = std::max(rn, b.r0 > 0 ? b.rn / b.r0 : 0.0);
+    while (hcount[0] > 0 && o < par.max_outer) {
+        if (graphed) CKR(cudaGraphLaunch(gexec, s));
+        else CKS(step(s));
+        CKR(cudaEventRecord(h->ev, s));
+        CKR(cudaEventSynchronize(h->ev));
+        ++o;
+        if (hcount[1]) {
+            if (gexec) cudaGraphExecDestroy(gexec);
+            return seterr(HJ_ERR_TIMEOUT, "a bounded grid-barrier wait expired");
         }
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    // results: iterates held in the second buffer go back to the caller's
+    CKR(cudaMemcpyAsync(hm, dm, m_word + 4 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    if (logcap > 0)
+        CKR(cudaMemcpyAsync(hm + m_tlog, dm + m_tlog, 2 * (logcap + 1) * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s));
+    CKR(cudaEventRecord(h->ev, s));
+    CKR(cudaEventSynchronize(h->ev));
+    int status = HJ_OK, left = 0;
+    long long total_inner = 0;
+    double worst = 0.0, any_r0 = 0.0;
+    for (int i = 0; i < nprob; ++i) {
+        const BOuter &x = ho[i];
+        if (x.r0 > 0) any_r0 = 1.0;
+        if (x.cur) CKR(cudaMemcpyAsync(P[i].u, P[i].u2, (size_t)P[i].rows * P[i].d.ld * 8, cudaMemcpyDeviceToDevice, s));
+        if (x.status == HJ_ERR_DIVERGED) status = HJ_ERR_DIVERGED;
+        left += x.active;
+        total_inner += x.inner;
+        worst = std::max(worst, x.r0 > 0 ? x.rn / x.r0 : 0.0);
+        if (cycles_out) cycles_out[i] = x.inner;
+    }
+    if (status == HJ_OK && left > 0) status = HJ_ERR_NOT_CONVERGED;
+    CKR(cudaStreamSynchronize(s));
+    if (stats) {
         stats->cycles = total_inner;
         stats->cycles_launched = total_inner;
         stats->inner_cycles = total_inner;
         stats->outer_steps = o;
-        stats->res0 = r0;
-        stats->res_final = rn;
-        stats->rel_final = rn;   // worst relative residual over the batch
+        stats->res0 = any_r0;
+        stats->res_final = worst;
+        stats->rel_final = worst;   // worst relative residual over the batch
         stats->history_len = 0;
         stats->tile_x = ki->tx;
         stats->tile_y = ki->ty;
         stats->tile_threads = ki->threads;
         stats->k = *std::max_element(kprob.begin(), kprob.end());
         stats->persistent = 1;
+        stats->graphed = graphed;
+        stats->cycle_len = 0;
+        if (logcap > 0) {
+            // entry n: the time a barrier released (a launch's first barrier, or
+            // the one ending a batch cycle) and the points active in the cycle
+            // that follows it; a launch's last entry has none active, and the
+            // interval after it (the binary64 step between launches) is skipped
+            const unsigned long long *tl = (const unsigned long long *)(hm + m_tlog);
+            const long long nlog = std::min<long long>(hword[1], logcap + 1);
+            long long out = 0;
+            for (long long n = 0; n + 1 < nlog && out < logcap; ++n) {
+                if (tl[2 * n + 1] == 0) continue;
+                const double ms = (double)(tl[2 * (n + 1)] - tl[2 * n]) * 1e-6;
+                if (stats->cycle_ms) stats->cycle_ms[out] = ms;
+                if (stats->cycle_points) stats->cycle_points[out] = (long long)tl[2 * n + 1];
+                ++out;
+            }
+            stats->cycle_len = out;
+        }
     }
     if (status == HJ_ERR_DIVERGED) return seterr(HJ_ERR_DIVERGED, "a problem of the batch diverged");
     if (status == HJ_ERR_NOT_CONVERGED)
-        return seterr(HJ_ERR_NOT_CONVERGED, "%zu problems not converged after %d outer steps", act.size(), o);
+        return seterr(HJ_ERR_NOT_CONVERGED, "%d problems not converged after %d outer steps", left, o);
     return HJ_OK;
 }
 

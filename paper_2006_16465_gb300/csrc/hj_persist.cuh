@@ -1,18 +1,25 @@
 // hj_persist.cuh -- persistent multi-cycle kernel: one cooperative launch runs
 // the cycles of one or many problems until each meets its tolerance.
 //
-// Work items are (problem, block) pairs in a flat list; every CTA walks the
-// list with a static stride.  A cycle is:
-//   phase A  every item of an active problem runs one hierarchical cycle of
-//            its tile(s) (stage u_c + halo, k subiterations, write u_{c+1})
-//            and stores its share of ||f - A u_c||^2;
+// Work items are (problem, block) pairs, numbered problem by problem.  With
+// many problems (the batched scheduler) the CTAs are fed by a device work
+// queue: a compacted list of the items of the problems still active, handed
+// out by an atomic head, so a CTA never visits an item of a retired problem
+// and uneven item costs balance themselves.  A cycle is:
+//   phase A  CTAs take items from the queue; each runs one hierarchical cycle
+//            of its tile (stage u_c + halo, k subiterations, write u_{c+1})
+//            and stores its share of ||f - A u_c||^2 under the item's own
+//            number (so the sums below do not depend on which CTA ran it);
 //   barrier  (grid-wide, bounded)
 //   phase B  CTA b reduces problems b, b + G, ... in a fixed order, records
 //            ||r_c||, and retires the problem when it meets its tolerance
 //            (its iterate u_c is still intact in buffer c mod 2), diverges, or
 //            reaches its cycle cap;
-//   barrier  (grid-wide, bounded); stop when no problem is active.
+//   barrier  (grid-wide, bounded): the last CTA to arrive rebuilds the queue
+//            if a problem retired, resets its head and logs the cycle's end
+//            time; stop when no problem is active.
 // Problems of different sizes, stencils, k and tolerances share the launch.
+// Single-problem launches keep a static stride over the problem's items.
 // Every barrier wait is bounded by wall time (%globaltimer); on expiry the
 // kernel records HJ_ERR_TIMEOUT in the error word and every CTA returns.
 #pragma once
@@ -52,6 +59,18 @@ struct PersistArgs {
     int skip_barrier_cta;    // test hook: this CTA leaves before the first barrier (-1 = none)
     const PersistMaps *maps; // per problem (TMA-staging kernels only)
     long long spin_limit;    // polls of an mbarrier before giving up (TMA-staging kernels)
+    // work queue of the multi-problem kernels
+    int *q_head;             // next queue entry to hand out this cycle
+    int *q_items;            // [nitems] item numbers of the active problems, problem by problem
+    int *q_count;            // entries in q_items
+    int *q_changed;          // a problem retired: rebuild before the next cycle
+    int *q_off;              // [nprob] scratch of the rebuild: first entry of each problem, -1 if retired
+    const long long *prob_points;   // per problem: interior points
+    long long *q_points;     // interior points of the active problems
+    // per-cycle log (nullable): [2 * n] = end time (ns), [2 * n + 1] = active points of the next cycle
+    unsigned long long *tlog;
+    long long *tlog_n;
+    long long tlog_cap;
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -87,6 +106,106 @@ __device__ __forceinline__ bool grid_barrier(const PersistArgs &P) {
                 __nanosleep(64);
             }
         }
+        __threadfence();
+        s_ok = ok && (*(volatile int *)P.err == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Rebuild the work queue from the problems still active (whole CTA; run by
+// the last CTA to reach a grid barrier while the others wait in it), reset
+// the head and log the time.  Problems keep their order and each problem's
+// items stay contiguous, so consecutive CTAs take neighbouring subdomains.
+__device__ __forceinline__ void queue_rebuild(const PersistArgs &P) {
+    // every thread takes the same branch: the flag is read once, before warp 0 clears it
+    __shared__ int s_changed;
+    if (threadIdx.x == 0) s_changed = *(volatile int *)P.q_changed;
+    __syncthreads();
+    if (s_changed) {
+        const int lane = threadIdx.x & 31;
+        if (threadIdx.x < 32) {
+            int base = 0;
+            long long pts = 0;
+            for (int p0 = 0; p0 < P.nprob; p0 += 32) {
+                const int p = p0 + lane;
+                const bool act = p < P.nprob && ((volatile ProbState *)P.state + p)->done < 0;
+                const int n = act ? P.prob_nitems[p] : 0;
+                int x = n;   // inclusive scan over the warp
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (p < P.nprob) P.q_off[p] = act ? base + x - n : -1;
+                double dp = act ? (double)P.prob_points[p] : 0.0;
+                pts += (long long)warp_sum(dp);
+                base += __shfl_sync(0xffffffffu, x, 31);
+            }
+            if (lane == 0) {
+                *P.q_count = base;
+                *P.q_points = pts;
+                *(volatile int *)P.q_changed = 0;
+            }
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < P.nprob; p += blockDim.x) {
+            const int off = P.q_off[p];
+            if (off < 0) continue;
+            const int i0 = P.prob_item0[p], n = P.prob_nitems[p];
+            for (int b = 0; b < n; ++b) P.q_items[off + b] = i0 + b;
+        }
+    }
+    if (threadIdx.x == 0) {
+        *P.q_head = 0;
+        if (P.tlog) {
+            const long long n = *P.tlog_n;
+            if (n < P.tlog_cap) {
+                P.tlog[2 * n] = global_ns();
+                P.tlog[2 * n + 1] = (unsigned long long)*P.q_points;
+            }
+            *P.tlog_n = n + 1;
+        }
+    }
+}
+
+// Grid barrier whose last CTA to arrive rebuilds the work queue before it
+// releases the others (same bounded waits and error word as grid_barrier).
+__device__ __forceinline__ bool grid_barrier_queue(const PersistArgs &P) {
+    __syncthreads();
+    __shared__ int s_last, s_ok;
+    __shared__ unsigned s_gen;
+    if (threadIdx.x == 0) {
+        s_gen = *(volatile unsigned *)(P.bar + 1);
+        __threadfence();
+        s_last = atomicAdd(P.bar, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    int ok = 1;
+    if (s_last) {
+        __threadfence();
+        queue_rebuild(P);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(P.bar, 0u);
+            __threadfence();
+            atomicAdd(P.bar + 1, 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        volatile unsigned *vgen = P.bar + 1;
+        const unsigned long long t0 = global_ns();
+        while (*vgen == s_gen) {
+            if (*(volatile int *)P.err) { ok = 0; break; }
+            if (global_ns() - t0 > P.timeout_ns) {
+                atomicExch(P.err, HJ_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    if (threadIdx.x == 0) {
         __threadfence();
         s_ok = ok && (*(volatile int *)P.err == 0);
     }
@@ -142,7 +261,10 @@ __device__ __forceinline__ void retire_check(const PersistArgs &P, int p, int pa
             retire = 0;
         }
         st->cycle = c + 1;
-        if (retire) atomicSub(P.active, 1);
+        if (retire) {
+            atomicSub(P.active, 1);
+            if (P.q_changed) *(volatile int *)P.q_changed = 1;
+        }
     }
 }
 
@@ -151,13 +273,21 @@ __global__ void __launch_bounds__(32 * NW) persist2d_kernel(const PersistArgs P)
     constexpr int TX = 32 * C / H, TY = R * NW * H;
     constexpr int XB = NW > 1 ? 2 * NW * 2 * TX : 1;
     __shared__ T xbuf[XB];
+    __shared__ int s_take;
+    // the queue of the first cycle is built behind a barrier
+    if (!grid_barrier_queue(P)) return;
     for (long long it = 0; it < P.max_iters; ++it) {
         const int parity = (int)(it & 1);
-        for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
+        const int cnt = *(volatile int *)P.q_count;
+        for (;;) {
+            if (threadIdx.x == 0) s_take = atomicAdd(P.q_head, 1);
+            __syncthreads();
+            const int qi = s_take;
+            if (qi >= cnt) break;
+            const int item = __ldcg(P.q_items + qi);
             const int p = P.item_prob[item];
-            volatile ProbState *st = P.state + p;
-            if (st->done >= 0) continue;
             CycArgs a = P.probs[p];
+            volatile ProbState *st = P.state + p;
             if (st->cycle & 1) {
                 const void *t = a.uin;
                 a.uin = a.uout;
@@ -179,7 +309,7 @@ __global__ void __launch_bounds__(32 * NW) persist2d_kernel(const PersistArgs P)
             for (int p = blockIdx.x; p < P.nprob; p += gridDim.x)
                 if (((volatile ProbState *)P.state + p)->done < 0) retire_check(P, p, parity);
         }
-        if (!grid_barrier(P)) return;
+        if (!grid_barrier_queue(P)) return;
         if (*(volatile int *)P.active <= 0) return;
     }
 }

@@ -59,12 +59,19 @@ __global__ void __launch_bounds__(32 * NW) persist2d_tma_kernel(const PersistArg
         if constexpr (ONE) return ls.cycle;
         else return ((volatile ProbState *)P.state + p)->cycle;
     };
-    auto next_item = [&](int i) -> int {
-        if constexpr (!ONE) {
-            for (; i < P.nitems; i += gridDim.x)
-                if (((volatile ProbState *)P.state + P.item_prob[i])->done < 0) break;
-        }
-        return i < P.nitems ? i : P.nitems;
+    // Items: ONE walks the problem's items with a static stride; otherwise
+    // the work queue hands them out (qi = queue entry, item = its number),
+    // one ahead, so that the next box is in flight while the current one
+    // sweeps.  An entry at or beyond the cycle's count means no more work.
+    __shared__ int s_first, s_next;
+    int cnt = P.nitems;
+    auto take = [&](int from_static) -> int {
+        if constexpr (ONE) return from_static < P.nitems ? from_static : P.nitems;
+        else return atomicAdd(P.q_head, 1);
+    };
+    auto item_of = [&](int qi) -> int {
+        if constexpr (ONE) return qi;
+        else return __ldcg(P.q_items + qi);
     };
     auto issue = [&](int item) {
         const int p = P.item_prob[item];
@@ -76,15 +83,22 @@ __global__ void __launch_bounds__(32 * NW) persist2d_tma_kernel(const PersistArg
         tma_load_2d(sf, &m.mf, bar, bx * TX, by * TY + 1);
         if constexpr (SIG) tma_load_2d(sd, &m.md, bar, bx * TX, by * TY + 1);
     };
+    if constexpr (!ONE) {
+        // the queue of the first cycle is built behind a barrier
+        if (!grid_barrier_queue(P)) return;
+    }
     for (long long it = 0; it < P.max_iters; ++it) {
         const int parity = (int)(it & 1);
-        int i = next_item(blockIdx.x);
-        if (tid == 0 && i < P.nitems) {
+        if constexpr (!ONE) cnt = *(volatile int *)P.q_count;
+        if (tid == 0) s_first = take(blockIdx.x);
+        __syncthreads();
+        int i = s_first;
+        if (tid == 0 && i < cnt) {
             fence_proxy_async_global();
-            issue(i);
+            issue(item_of(i));
         }
-        while (i < P.nitems) {
-            const int nxt = next_item(i + gridDim.x);
+        while (i < cnt) {
+            if (tid == 0) s_next = take(i + gridDim.x);
             bool ok = true;
             long long spins = 0;
             while (!mbar_try_wait(bar, nwait & 1u)) {
@@ -101,22 +115,24 @@ __global__ void __launch_bounds__(32 * NW) persist2d_tma_kernel(const PersistArg
                 return;
             }
             ++nwait;
-            const int p = P.item_prob[i];
+            const int item = item_of(i);
+            const int p = P.item_prob[item];
             CycArgs a = P.probs[p];
             if (cycle_of(p) & 1) {
                 const void *t = a.uin;
                 a.uin = a.uout;
                 a.uout = const_cast<void *>(t);
             }
-            const int blk = P.item_blk[i], tx = P.prob_tiles_x[p];
+            const int blk = P.item_blk[item], tx = P.prob_tiles_x[p];
             const int x0 = 1 + (blk % tx) * TX, y0 = 1 + (blk / tx) * TY, yb = y0 + band * R;
             const Coef<T> kc = make_coef<T>(a);
             Tile2D<T, C, R, SIG> t;
             stage2d_smem<S, T, C, R, H, EXACT, SIG>(t, kc, su, sf, sd, L::BWU, L::BWF, band * R);
-            __syncthreads();   // every thread is done with the boxes
-            if (tid == 0 && nxt < P.nitems) {
+            __syncthreads();   // every thread is done with the boxes (and s_next is published)
+            const int nxt = s_next;
+            if (tid == 0 && nxt < cnt) {
                 fence_proxy_async_smem();
-                issue(nxt);
+                issue(item_of(nxt));
             }
             typename std::conditional<EXACT, double, T>::type acc;
             if (x0 + TX - 1 <= a.nx && y0 + TY - 1 <= a.ny) {
@@ -127,7 +143,7 @@ __global__ void __launch_bounds__(32 * NW) persist2d_tma_kernel(const PersistArg
                 store2d<S, T, C, R, H, SIG, true>(t, a, x0, yb);
             }
             const double s = cta_sum(acc);
-            if (tid == 0) P.partial[(size_t)parity * P.nitems + i] = s;
+            if (tid == 0) P.partial[(size_t)parity * P.nitems + item] = s;
             i = nxt;
         }
         fence_proxy_async_global();   // this cycle's stores, before the next cycle's copies
@@ -140,7 +156,7 @@ __global__ void __launch_bounds__(32 * NW) persist2d_tma_kernel(const PersistArg
                 for (int p = blockIdx.x; p < P.nprob; p += gridDim.x)
                     if (((volatile ProbState *)P.state + p)->done < 0) retire_check(P, p, parity);
             }
-            if (!grid_barrier(P)) return;
+            if (!grid_barrier_queue(P)) return;
             if (*(volatile int *)P.active <= 0) return;
         }
     }

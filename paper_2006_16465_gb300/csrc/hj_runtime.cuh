@@ -104,6 +104,11 @@ struct hj_handle {
     size_t barena_bytes = 0;
     double *rs = nullptr, *h_rs = nullptr;
     size_t nrs = 0;
+    // batched solves: device metadata of the batch (per-problem buffers and
+    // refinement state, residual shares, the per-cycle log) and its pinned copy
+    void *bmeta = nullptr;
+    unsigned char *h_bmeta = nullptr;
+    size_t bmeta_bytes = 0;
     // multigrid (HJ_METHOD_MG): levels, their buffers and the V-cycle graph
     std::vector<hj::MgLevel> mg;
     void *mg_arena = nullptr;

@@ -838,3 +838,42 @@ def test_one_call_solve_equals_solver():
     s.close()
     assert out["status"] == 0 and out["cycles"] == out2["cycles"]
     assert torch.equal(u1, u2)
+
+
+def test_batched_steps_replay_one_graph_and_log_batch_cycles():
+    """The batched scheduler runs every refinement step as a replay of one
+    captured graph, feeds the persistent launch from the device work queue
+    (the results equal per-problem solves, test above) and records each
+    batch cycle's duration with the interior points still active in it."""
+    torch = _torch()
+    import ctypes as C
+    import paper_2006_16465_gb300 as hj
+    probs = _batch()
+    s = gpu_solver(probs[0], tile_x=32, tile_y=32, k=16, precision="f32_ir", tol=1e-8, inner_tol=1e-4)
+    fs = [to_dev(q.f, 2, torch.float64) for q in probs]
+    us = [to_dev(q.u0, 2, torch.float64) for q in probs]
+    descs = [hj.make_desc(2, q.st.nx, q.st.ny, f.shape[1], q.st.cW, q.st.cE, q.st.cS, q.st.cN, q.st.cD,
+                          q.st.sigma_const) for q, f in zip(probs, fs)]
+    cap = 1 << 16
+    ms = (C.c_double * cap)()
+    pts = (C.c_longlong * cap)()
+    st = hj.hj_stats()
+    st.cycle_ms = C.cast(ms, C.POINTER(C.c_double))
+    st.cycle_points = C.cast(pts, C.POINTER(C.c_longlong))
+    st.cycle_cap = cap
+    cyc = (C.c_longlong * len(probs))()
+    code = hj.hj_solve_batched(s.h, descs, [f.data_ptr() for f in fs], [u.data_ptr() for u in us], 0, st, cyc)
+    assert code == 0, hj.hj_last_error()
+    assert st.graphed == 1
+    n = st.cycle_len
+    sizes = [q.st.nx * q.st.ny for q in probs]
+    # one entry per batch cycle: as many as the longest problem's inner cycles
+    # in every refinement step together, at least as many as any one problem's
+    assert max(cyc) <= n <= sum(cyc)
+    assert pts[0] == sum(sizes)
+    assert all(0 < pts[i] <= sum(sizes) for i in range(n))
+    assert all(ms[i] > 0 for i in range(n))
+    # the active points only shrink within a step and start afresh with the next
+    drops = sum(1 for i in range(1, n) if pts[i] < pts[i - 1])
+    assert drops >= 1
+    s.close()
