@@ -385,7 +385,14 @@ def test_refinement_reaches_tolerance_and_matches_oracle(prec, engine):
     h = 1 / (n + 1)
     kappa = (8 / h ** 2) / (2 * np.pi ** 2)
     assert np.abs(ug - uo).max() <= kappa * tol * np.abs(uo).max()
+    # the step counts follow the oracle's refinement: the binary64 outer steps
+    # are the same computation (within one step: the inner binary32 cycles fuse
+    # multiply-adds on the GPU and do not in the oracle, so each inner solve
+    # ends within a few cycles of the oracle's), and ||r_0|| is the same number
     assert out["outer_steps"] >= 2
+    assert abs(out["outer_steps"] - outer) <= 1, (out["outer_steps"], outer)
+    assert abs(out["inner_cycles"] - inner) <= 0.1 * inner + 32, (out["inner_cycles"], inner)
+    assert out["history"][0] == pytest.approx(hist[0], rel=1e-12)
     s.close()
 
 

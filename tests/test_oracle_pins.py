@@ -684,3 +684,46 @@ def test_threaded_oracle_is_bitwise_the_single_thread_oracle(dim, nx, ny, tx, ty
             assert c == ref_s[1] and status == ref_s[2] and np.array_equal(u, ref_s[0])
     finally:
         oracle.set_threads(1)
+
+
+def test_refinement_stagnation_rule_stops_at_the_bf16_fixed_point():
+    """The inner solve of the refinement stops when ||r|| moved by at most
+    1e-3 (relative) over a window of cycles.  With the correction stored in
+    bfloat16 the cycles reach a bitwise fixed point (found here by brute force:
+    iterate until a cycle changes nothing); the rule must stop the inner solve
+    no later than the first window check after it, and at a residual within
+    1e-3 of the fixed point's."""
+    p = W.poisson2d_sin_noise(48, seed=2)
+    st = p.st
+    W_ = st.nx + 2
+    u0 = np.zeros_like(p.f)
+    r = (p.f - oracle.apply(st, u0)).astype(np.float32)
+    r[0, :] = r[-1, :] = 0
+    r[:, 0] = r[:, -1] = 0
+    d = np.zeros_like(r)
+    c_fp = None
+    for c in range(20000):
+        nd = oracle.hier_cycle_f32(st, r, d, 16, 16, 8, bf16=True)
+        if np.array_equal(nd, d):
+            c_fp = c
+            break
+        d = nd
+    assert c_fp is not None and c_fp > 0
+    r_fp = oracle.residual_f32(st, r, d)
+    window = 32
+    m = 1
+    while (m - 1) * window < c_fp:
+        m += 1
+    bound = m * window
+    _, outer, inner, status, hist = oracle.ir_solve(st, p.f, u0, 1e-30, 16, 16, 8, inner_tol=0.0, inner_max=10 ** 6,
+                                                    max_outer=1, bf16=True, stall_window=window, stall_rtol=1e-3)
+    assert outer == 1 and status == 1
+    assert window <= inner <= bound, (inner, c_fp, bound)
+    # here the residual keeps moving until the fixed point, so the rule fires
+    # exactly at that first check (cycle 352 for a fixed point at cycle 297)
+    assert inner == bound
+    # the correction it stopped with sits at the fixed point's residual (to the rule's 1e-3)
+    dd = np.zeros_like(r)
+    for _ in range(inner):
+        dd = oracle.hier_cycle_f32(st, r, dd, 16, 16, 8, bf16=True)
+    assert abs(oracle.residual_f32(st, r, dd) - r_fp) <= 2e-3 * r_fp
