@@ -80,7 +80,9 @@ enum hj_status {
     HJ_ERR_NOT_CONVERGED = 5,    /* max_cycles reached; u holds the last iterate   */
     HJ_ERR_DIVERGED = 6,         /* residual became NaN or Inf                     */
     HJ_ERR_TIMEOUT = 7,          /* a bounded device-side wait gave up             */
-    HJ_ERR_NO_MEMORY = 8         /* workspace allocation failed                    */
+    HJ_ERR_NO_MEMORY = 8,        /* workspace allocation failed                    */
+    HJ_ERR_BOUNDS = 9            /* debug builds: an index check or guard band
+                                    failed (hj_debug_check)                       */
 };
 
 enum hj_dtype { HJ_F64 = 0, HJ_F32 = 1 };
@@ -384,6 +386,30 @@ HJ_API int hj_autotune(const hj_desc *desc, hj_params *params, double *predicted
  * other host threads) race and corrupt each other's results. */
 HJ_API int hj_cycles_noalloc(const hj_desc *desc, const hj_params *params, const void *f, void *u,
                              hj_stream stream);
+
+/* Memory checks of debug builds (the library compiled with -DHJ_DEBUG, see
+ * the package's build script), a stand-in for an external memory checker; no
+ * counterpart in the paper.  In such builds the cycle kernels (2D and 1D
+ * subdomain kernels, the pipelined and persistent engines, the classic sweep)
+ * check every staging, exchange and write-back index against the extent of
+ * the array or shared box it addresses, skip an access that fails and record
+ * the first failure in a device word; every device allocation of the library
+ * is surrounded by guard bands of a fixed byte pattern.  hj_debug_check waits
+ * for the device, then reports the first recorded failure: *site = the kernel
+ * site (> 0) and *index = the failing index, or *site = -2 and *index = the
+ * byte offset (from the start of the allocation) of an overwritten guard byte;
+ * it returns HJ_ERR_BOUNDS for either and clears it (so each is reported
+ * once), HJ_OK with *site = 0 when clean.  Release builds return HJ_OK with
+ * *site = -1: no checks are compiled in.  Either pointer may be NULL.  The
+ * device word lives on the device current at the first debug-build call. */
+HJ_API int hj_debug_check(long long *site, long long *index);
+
+/* Debug builds: shows that both checks catch what they are for, without any
+ * access out of bounds: a kernel checks one index outside its range (no
+ * memory is addressed), and the host overwrites one byte of a fresh
+ * allocation's trailing guard band with cudaMemset.  HJ_OK if both were
+ * reported, HJ_ERR_BOUNDS if not; HJ_ERR_UNSUPPORTED in release builds. */
+HJ_API int hj_debug_selftest(void);
 
 /* Built (tile_x, tile_y, threads) combinations for (dim, precision): writes
  * up to cap triples into txt[3*i .. 3*i+2] and returns how many exist. */

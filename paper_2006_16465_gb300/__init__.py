@@ -13,10 +13,12 @@ tensors).  PyTorch is used only for device memory and streams.
 from __future__ import annotations
 
 import ctypes as C
+import os
 from pathlib import Path
 
 _PKG = Path(__file__).resolve().parent
-LIB_PATH = _PKG / "libhj.so"
+# HJ_LIBRARY=debug selects the debug build (index checks, guard bands; see _build.py)
+LIB_PATH = _PKG / ("libhj_debug.so" if os.environ.get("HJ_LIBRARY") == "debug" else "libhj.so")
 
 # status codes (include/hj.h)
 HJ_OK = 0
@@ -28,6 +30,7 @@ HJ_ERR_NOT_CONVERGED = 5
 HJ_ERR_DIVERGED = 6
 HJ_ERR_TIMEOUT = 7
 HJ_ERR_NO_MEMORY = 8
+HJ_ERR_BOUNDS = 9
 
 HJ_F64, HJ_F32 = 0, 1
 HJ_PREC_F64, HJ_PREC_F32, HJ_PREC_F32_IR, HJ_PREC_BF16CORR_IR = 0, 1, 2, 3
@@ -119,9 +122,12 @@ def lib():
         L.hj_autotune.argtypes = [C.POINTER(hj_desc), C.POINTER(hj_params), C.POINTER(C.c_double)]
         L.hj_cycles_noalloc.argtypes = [C.POINTER(hj_desc), C.POINTER(hj_params), C.c_void_p, C.c_void_p,
                                         C.c_void_p]
+        L.hj_debug_check.argtypes = [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+        L.hj_debug_selftest.argtypes = []
         for name in ("hj_create", "hj_solve", "hj_residual", "hj_solve_adjoint", "hj_solve_batched",
                      "hj_solve_adjoint_batched",
-                     "hj_tile_shapes", "hj_tile_variants", "hj_autotune", "hj_cycles_noalloc"):
+                     "hj_tile_shapes", "hj_tile_variants", "hj_autotune", "hj_cycles_noalloc", "hj_debug_check",
+                     "hj_debug_selftest"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -214,6 +220,18 @@ def hj_cycles_noalloc(desc: hj_desc, params: hj_params, f_ptr: int, u_ptr: int, 
     second iterate buffer is a static 16 MiB array in the library)."""
     return lib().hj_cycles_noalloc(C.byref(desc), C.byref(params), C.c_void_p(f_ptr), C.c_void_p(u_ptr),
                                    C.c_void_p(stream))
+
+
+def hj_debug_check():
+    """(status, site, index) of the debug build's memory checks (see hj.h);
+    site -1: the library has no checks compiled in."""
+    site, index = C.c_longlong(0), C.c_longlong(0)
+    code = lib().hj_debug_check(C.byref(site), C.byref(index))
+    return code, site.value, index.value
+
+
+def hj_debug_selftest() -> int:
+    return lib().hj_debug_selftest()
 
 
 def hj_tile_variants(dim: int, precision: int):

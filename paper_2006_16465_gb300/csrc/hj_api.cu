@@ -181,6 +181,7 @@ CycArgs base_args(const hj_handle *h, bool transpose) {
     a.gS = (float)(-a.cS * a.invd); a.gN = (float)(-a.cN * a.invd);
     a.finvd = (float)a.invd;
     a.fdconst = (float)a.dconst;
+    a.dbg = debug_word();
     a.ox = h->p.overlap_x;
     a.oy = h->d.dim == 2 ? h->p.overlap_y : 0;
     a.jx = subdomain_count(h->d.nx, h->p.tile_x, a.ox);
@@ -533,7 +534,7 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, 
     } else if (want_ppc(h, pi, classic)) {
         if (!third.slot) return seterr(HJ_ERR_CUDA, "internal: no slot for the third iterate buffer");
         if (!*third.slot) {
-            if (cudaMalloc(third.slot, third.bytes) != cudaSuccess) {
+            if (dmalloc(third.slot, third.bytes) != cudaSuccess) {
                 cudaGetLastError();
                 *third.slot = nullptr;
                 return seterr(HJ_ERR_NO_MEMORY, "third iterate buffer (%zu bytes)", third.bytes);
@@ -921,6 +922,7 @@ const char *hj_error_string(int s) {
     case HJ_ERR_DIVERGED: return "diverged";
     case HJ_ERR_TIMEOUT: return "device wait timed out";
     case HJ_ERR_NO_MEMORY: return "out of device memory";
+    case HJ_ERR_BOUNDS: return "debug check failed (index out of range or guard band overwritten)";
     default: return "unknown status";
     }
 }
@@ -977,11 +979,11 @@ void hj_destroy(hj_handle *h) {
     if (!h) return;
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     if (h->mg_exec) cudaGraphExecDestroy(h->mg_exec);
-    if (h->mg_arena) cudaFree(h->mg_arena);
+    if (h->mg_arena) dfree(h->mg_arena);
     void *dev[] = {h->ubuf, h->ubuf2, h->dC, h->vcf, h->dinv_outer, h->dinv32, h->r32, h->dA, h->dB, h->hf, h->hu, h->partials, h->gpart,
                    h->hist, h->rstore, h->gcnt, h->fcnt, h->ctl, h->pscratch, h->barena, h->rs, h->bmeta};
     for (void *p : dev)
-        if (p) cudaFree(p);
+        if (p) dfree(p);
     void *pin[] = {h->h_ctl, h->h_ctl_init, h->h_hist, h->h_rstore, h->h_pstage, h->h_rs, h->h_bmeta};
     for (void *p : pin)
         if (p) cudaFreeHost(p);
@@ -1183,7 +1185,7 @@ int hj_create(hj_handle **out, const hj_desc *desc, const hj_params *params) {
     } while (0)
 #define HJ_ALLOC(ptr, bytes)                                                               \
     do {                                                                                   \
-        if (cudaMalloc((void **)&(ptr), (bytes)) != cudaSuccess) {                         \
+        if (dmalloc((void **)&(ptr), (bytes)) != cudaSuccess) {                         \
             cudaGetLastError();                                                            \
             HJ_FAIL(HJ_ERR_NO_MEMORY, "cudaMalloc of %zu bytes failed", (size_t)(bytes)); \
         }                                                                                  \
@@ -1343,8 +1345,8 @@ int hj_solve(hj_handle *h, const void *f, void *u, hj_stream stream, hj_stats *s
     const void *fd = f;
     void *ud = u;
     if (!fdev || !udev) {
-        if (!h->hf) CKR(cudaMalloc(&h->hf, h->grid_bytes));
-        if (!h->hu) CKR(cudaMalloc(&h->hu, h->grid_bytes));
+        if (!h->hf) CKR(dmalloc(&h->hf, h->grid_bytes));
+        if (!h->hu) CKR(dmalloc(&h->hu, h->grid_bytes));
         if (!fdev) {
             CKR(cudaMemcpyAsync(h->hf, f, h->grid_bytes, cudaMemcpyHostToDevice, s));
             fd = h->hf;

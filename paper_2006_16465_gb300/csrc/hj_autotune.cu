@@ -98,16 +98,16 @@ struct Scratch {
     long long ld = 0;
     int esz = 4;
     ~Scratch() {
-        if (u) cudaFree(u);
-        if (f) cudaFree(f);
-        if (sig) cudaFree(sig);
+        if (u) dfree(u);
+        if (f) dfree(f);
+        if (sig) dfree(sig);
     }
     int init(const hj_desc &d, int prec) {
         esz = prec == HJ_PREC_F64 ? 8 : 4;
         ld = ((long long)d.nx + 2 + 31) / 32 * 32;
         const int rows = d.dim == 2 ? d.ny + 2 : d.ny;
         const size_t bytes = (size_t)rows * ld * esz;
-        if (cudaMalloc(&u, bytes) != cudaSuccess || cudaMalloc(&f, bytes) != cudaSuccess) {
+        if (dmalloc(&u, bytes) != cudaSuccess || dmalloc(&f, bytes) != cudaSuccess) {
             cudaGetLastError();
             return seterr(HJ_ERR_NO_MEMORY, "autotune scratch");
         }
@@ -115,7 +115,7 @@ struct Scratch {
         td.ld = ld;
         td.dtype = prec == HJ_PREC_F64 ? HJ_F64 : HJ_F32;
         if (d.sigma) {
-            if (cudaMalloc((void **)&sig, (size_t)rows * ld * 8) != cudaSuccess ||
+            if (dmalloc((void **)&sig, (size_t)rows * ld * 8) != cudaSuccess ||
                 cudaMemcpy2D(sig, ld * 8, d.sigma, d.ld * 8, (size_t)(d.nx + 2) * 8, rows, cudaMemcpyDeviceToDevice) !=
                     cudaSuccess) {
                 cudaGetLastError();

@@ -17,16 +17,16 @@ namespace hj {
 int ensure_reduction(hj_handle *h, size_t blocks) {
     if (blocks <= h->max_blocks) return HJ_OK;
     const size_t groups = (blocks + kGroup - 1) / kGroup;
-    cudaFree(h->partials);
-    cudaFree(h->gpart);
-    cudaFree(h->gcnt);
+    dfree(h->partials);
+    dfree(h->gpart);
+    dfree(h->gcnt);
     h->partials = nullptr;
     h->gpart = nullptr;
     h->gcnt = nullptr;
     h->max_blocks = h->max_groups = 0;
-    if (cudaMalloc((void **)&h->partials, 2 * blocks * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void **)&h->gpart, 2 * groups * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void **)&h->gcnt, groups * sizeof(unsigned)) != cudaSuccess) {
+    if (dmalloc((void **)&h->partials, 2 * blocks * sizeof(double)) != cudaSuccess ||
+        dmalloc((void **)&h->gpart, 2 * groups * sizeof(double)) != cudaSuccess ||
+        dmalloc((void **)&h->gcnt, groups * sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         return seterr(HJ_ERR_NO_MEMORY, "reduction workspace for %zu blocks", blocks);
     }
@@ -39,12 +39,12 @@ int ensure_reduction(hj_handle *h, size_t blocks) {
 int ensure_scratch(hj_handle *h, size_t bytes) {
     if (bytes <= h->pscratch_bytes) return HJ_OK;
     CKR(cudaDeviceSynchronize());
-    if (h->pscratch) cudaFree(h->pscratch);
+    if (h->pscratch) dfree(h->pscratch);
     if (h->h_pstage) cudaFreeHost(h->h_pstage);
     h->pscratch = nullptr;
     h->h_pstage = nullptr;
     h->pscratch_bytes = 0;
-    if (cudaMalloc(&h->pscratch, bytes) != cudaSuccess || cudaMallocHost((void **)&h->h_pstage, bytes) != cudaSuccess) {
+    if (dmalloc(&h->pscratch, bytes) != cudaSuccess || cudaMallocHost((void **)&h->h_pstage, bytes) != cudaSuccess) {
         cudaGetLastError();
         return seterr(HJ_ERR_NO_MEMORY, "persistent scratch of %zu bytes", bytes);
     }
@@ -309,6 +309,7 @@ struct BatchArgs {
     int *count;               // problems still refining (read by the host)
     int nprob, naux;
     double tol;
+    DbgWord *dbg;             // debug builds: the index-check word
 };
 
 __device__ __forceinline__ bool aux_point(const BDev &b, int a, int &i, int &j) {
@@ -328,7 +329,9 @@ __global__ void __launch_bounds__(256) batch_zero_kernel(const BatchArgs A) {
         if (!A.outer[p].active) continue;
         const BDev b = A.prob[p];
         int i, j;
-        if (aux_point(b, a, i, j)) ((DS *)b.d[0])[(long long)j * b.ld_in + i] = DS(0.0f);
+        const bool pt = aux_point(b, a, i, j);
+        const long long q2 = (long long)j * b.ld_in + i;
+        if (pt && HJ_IN(A.dbg, q2, (long long)(b.ny + 2) * b.ld_in, 60)) ((DS *)b.d[0])[q2] = DS(0.0f);
     }
 }
 
@@ -349,9 +352,13 @@ __global__ void __launch_bounds__(256) batch_residual_kernel(const BatchArgs A) 
         const BDev b = A.prob[p];
         int i, j;
         double rr = 0.0;
-        if (aux_point(b, a, i, j)) {
+        const bool pt = aux_point(b, a, i, j);
+        const long long q = (long long)j * b.ld + i, q2 = (long long)j * b.ld_in + i;
+        if (pt && HJ_IN(A.dbg, q + b.ld, (long long)(b.ny + 2) * b.ld, 61) &&
+            HJ_IN(A.dbg, q - b.ld, (long long)(b.ny + 2) * b.ld, 61) &&
+            HJ_IN(A.dbg, q2 + b.ld_in, (long long)(b.ny + 2) * b.ld_in, 62) &&
+            HJ_IN(A.dbg, q2 - b.ld_in, (long long)(b.ny + 2) * b.ld_in, 62)) {
             const double *u = b.u[o.cur];
-            const long long q = (long long)j * b.ld + i, q2 = (long long)j * b.ld_in + i;
             double uc = u[q], uW = u[q - 1], uE = u[q + 1], uS = u[q - b.ld], uN = u[q + b.ld];
             if constexpr (!INIT) {
                 const DS *d = (const DS *)b.d[A.state[p].done & 1];
@@ -468,6 +475,7 @@ CycArgs prob_args(const hj_desc &d, const hj_params &p, bool transpose = false) 
     a.gS = (float)(-a.cS * a.invd); a.gN = (float)(-a.cN * a.invd);
     a.finvd = (float)a.invd;
     a.fdconst = (float)a.dconst;
+    a.dbg = debug_word();
     return a;
 }
 
@@ -555,10 +563,10 @@ int batched_core(hj_handle *h, int nprob, const hj_desc *descs, const void *cons
     }
     if (arena > h->barena_bytes) {
         CKR(cudaDeviceSynchronize());
-        if (h->barena) cudaFree(h->barena);
+        if (h->barena) dfree(h->barena);
         h->barena = nullptr;
         h->barena_bytes = 0;
-        if (cudaMalloc(&h->barena, arena) != cudaSuccess) {
+        if (dmalloc(&h->barena, arena) != cudaSuccess) {
             cudaGetLastError();
             return seterr(HJ_ERR_NO_MEMORY, "batched workspace of %zu bytes", arena);
         }
@@ -641,12 +649,12 @@ int batched_core(hj_handle *h, int nprob, const hj_desc *descs, const void *cons
     const size_t m_total = al(m_tlog + (logcap > 0 ? 2 * (logcap + 1) * sizeof(unsigned long long) : 0));
     if (m_total > h->bmeta_bytes) {
         CKR(cudaDeviceSynchronize());
-        if (h->bmeta) cudaFree(h->bmeta);
+        if (h->bmeta) dfree(h->bmeta);
         if (h->h_bmeta) cudaFreeHost(h->h_bmeta);
         h->bmeta = nullptr;
         h->h_bmeta = nullptr;
         h->bmeta_bytes = 0;
-        if (cudaMalloc(&h->bmeta, m_total) != cudaSuccess ||
+        if (dmalloc(&h->bmeta, m_total) != cudaSuccess ||
             cudaMallocHost((void **)&h->h_bmeta, m_total) != cudaSuccess) {
             cudaGetLastError();
             return seterr(HJ_ERR_NO_MEMORY, "batch metadata of %zu bytes", m_total);
@@ -681,6 +689,7 @@ int batched_core(hj_handle *h, int nprob, const hj_desc *descs, const void *cons
     B.nprob = nprob;
     B.naux = (int)naux;
     B.tol = par.tol;
+    B.dbg = debug_word();
     const dim3 bg = batch_grid((int)naux, h->nsm), bb(32, 8);
     int *hcount = (int *)hword;
     // ||r_0|| of every problem, r32 = r_0; the problems already within tol retire

@@ -162,23 +162,26 @@ __device__ __forceinline__ void stage2d_global(Tile2D<T, C, R, SIG> &t, const Cy
         for (int c = 0; c < C; ++c) {
             const int col = xl + c;
             const long long q = (long long)row * ld + col;
-            const bool ok = rowok && (!PART || col <= nx + 1);
-            const bool in = rowin && (!PART || col <= nx);
+            const bool ok = rowok && (!PART || col <= nx + 1) && HJ_IN(a.dbg, q, grid_elems2d(a), 1);
+            const bool in = rowin && (!PART || col <= nx) && HJ_IN(a.dbg, q, grid_elems2d(a), 2);
             t.v[r][c] = ok ? ld_s<S, T>(uin + q) : (T)0;
             t.g[r][c] = rhs_term<T, EXACT, SIG>(kc, in ? __ldg(f + q) : (T)0);
             if constexpr (SIG) t.dv[r][c] = in ? __ldg(dinv + q) : (T)0;
         }
         const int hcol = (li == 0) ? x0 - 1 : x0 + TX;
-        const bool hok = (li == 0 || li == L - 1) && rowok && (!PART || hcol <= nx + 1);
-        t.hx[r] = hok ? ld_s<S, T>(uin + (long long)row * ld + hcol) : (T)0;
+        const long long hq = (long long)row * ld + hcol;
+        const bool hok = (li == 0 || li == L - 1) && rowok && (!PART || hcol <= nx + 1) &&
+                         HJ_IN(a.dbg, hq, grid_elems2d(a), 3);
+        t.hx[r] = hok ? ld_s<S, T>(uin + hq) : (T)0;
     }
     const int rt = yb - 1, rb = yb + R;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int col = xl + c;
         const bool okc = !PART || col <= nx + 1;
-        t.top[c] = (okc && (!PART || rt <= ny + 1)) ? ld_s<S, T>(uin + (long long)rt * ld + col) : (T)0;
-        t.bot[c] = (okc && (!PART || rb <= ny + 1)) ? ld_s<S, T>(uin + (long long)rb * ld + col) : (T)0;
+        const long long qt = (long long)rt * ld + col, qb = (long long)rb * ld + col;
+        t.top[c] = (okc && (!PART || rt <= ny + 1) && HJ_IN(a.dbg, qt, grid_elems2d(a), 4)) ? ld_s<S, T>(uin + qt) : (T)0;
+        t.bot[c] = (okc && (!PART || rb <= ny + 1) && HJ_IN(a.dbg, qb, grid_elems2d(a), 5)) ? ld_s<S, T>(uin + qb) : (T)0;
     }
 }
 
@@ -207,26 +210,34 @@ __device__ __forceinline__ void lds_row4(const float *row, const int li, float (
     e = b.y;
 }
 
+// nu, nf: elements of the iterate box and of the RHS (1/d) box, for the
+// index checks of debug builds (dbg: their device word)
 template <typename S, typename T, int C, int R, int H, bool EXACT, bool SIG>
 __device__ __forceinline__ void stage2d_smem(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const S *su, const T *sf,
-                                             const T *sd, const int bwu, const int bwf, const int band_row0) {
+                                             const T *sd, const int bwu, const int bwf, const int band_row0,
+                                             const int nu = 1 << 30, const int nf = 1 << 30,
+                                             DbgWord *dbg = nullptr) {
     constexpr int L = 32 / H, TX = L * C;
     const int li = (threadIdx.x & 31) % L;
+    (void)nu; (void)nf; (void)dbg;
     if constexpr (C == 4 && std::is_same<S, float>::value && std::is_same<T, float>::value) {
         // box pitches are multiples of 16 bytes and the boxes 128-byte aligned
-        float w, e, tmp[4];
+        float w = 0.f, e = 0.f, tmp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int sr = band_row0 + r;
-            lds_row4(su + (sr + 1) * bwu, li, t.v[r], w, e);
+            if (HJ_IN(dbg, (sr + 1) * bwu + 4 * li + 7, nu, 11)) lds_row4(su + (sr + 1) * bwu, li, t.v[r], w, e);
             t.hx[r] = (li == 0) ? w : e;
-            lds_row4(sf + sr * bwf, li, tmp, w, e);
+            if (HJ_IN(dbg, sr * bwf + 4 * li + 7, nf, 12)) lds_row4(sf + sr * bwf, li, tmp, w, e);
 #pragma unroll
             for (int c = 0; c < 4; ++c) t.g[r][c] = rhs_term<T, EXACT, SIG>(kc, tmp[c]);
-            if constexpr (SIG) lds_row4(sd + sr * bwf, li, t.dv[SIG ? r : 0], w, e);
+            if constexpr (SIG) {
+                if (HJ_IN(dbg, sr * bwf + 4 * li + 7, nf, 13)) lds_row4(sd + sr * bwf, li, t.dv[SIG ? r : 0], w, e);
+            }
         }
-        lds_row4(su + band_row0 * bwu, li, t.top, w, e);
-        lds_row4(su + (band_row0 + R + 1) * bwu, li, t.bot, w, e);
+        if (HJ_IN(dbg, band_row0 * bwu + 4 * li + 7, nu, 14)) lds_row4(su + band_row0 * bwu, li, t.top, w, e);
+        if (HJ_IN(dbg, (band_row0 + R + 1) * bwu + 4 * li + 7, nu, 15))
+            lds_row4(su + (band_row0 + R + 1) * bwu, li, t.bot, w, e);
         return;
     }
     const int xc = 1 + li * C;
@@ -235,17 +246,19 @@ __device__ __forceinline__ void stage2d_smem(Tile2D<T, C, R, SIG> &t, const Coef
         const int sr = band_row0 + r;   // tile-interior row index
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            t.v[r][c] = sm_s<S, T>(su + (sr + 1) * bwu + xc + c);
-            t.g[r][c] = rhs_term<T, EXACT, SIG>(kc, sf[sr * bwf + xc + c]);
-            if constexpr (SIG) t.dv[r][c] = sd[sr * bwf + xc + c];
+            const int iu = (sr + 1) * bwu + xc + c, jf = sr * bwf + xc + c;
+            t.v[r][c] = HJ_IN(dbg, iu, nu, 11) ? sm_s<S, T>(su + iu) : (T)0;
+            t.g[r][c] = rhs_term<T, EXACT, SIG>(kc, HJ_IN(dbg, jf, nf, 12) ? sf[jf] : (T)0);
+            if constexpr (SIG) t.dv[r][c] = HJ_IN(dbg, jf, nf, 13) ? sd[jf] : (T)0;
         }
-        const int hcol = (li == 0) ? 0 : TX + 1;
-        t.hx[r] = sm_s<S, T>(su + (sr + 1) * bwu + hcol);
+        const int ih = (sr + 1) * bwu + ((li == 0) ? 0 : TX + 1);
+        t.hx[r] = HJ_IN(dbg, ih, nu, 14) ? sm_s<S, T>(su + ih) : (T)0;
     }
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-        t.top[c] = sm_s<S, T>(su + band_row0 * bwu + xc + c);
-        t.bot[c] = sm_s<S, T>(su + (band_row0 + R + 1) * bwu + xc + c);
+        const int it = band_row0 * bwu + xc + c, ib = (band_row0 + R + 1) * bwu + xc + c;
+        t.top[c] = HJ_IN(dbg, it, nu, 15) ? sm_s<S, T>(su + it) : (T)0;
+        t.bot[c] = HJ_IN(dbg, ib, nu, 15) ? sm_s<S, T>(su + ib) : (T)0;
     }
 }
 
@@ -304,7 +317,8 @@ struct Own {
 template <typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES, bool PART, bool OVL = false>
 __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type
 sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, const int yb, const int nx,
-         const int ny, T *xbuf, const Own own = Own{0, 0, 0, 0}) {
+         const int ny, T *xbuf, const Own own = Own{0, 0, 0, 0}, DbgWord *dbg = nullptr) {
+    (void)dbg;
     static_assert(H == 1 || H == 2 || H == 4, "one, two or four bands per warp");
     constexpr int L = 32 / H, TX = L * C;
     constexpr bool PACK = std::is_same<T, float>::value && !EXACT && (C % 2 == 0) && !PART;
@@ -409,20 +423,30 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
             }
         }
         if constexpr (NW > 1) {
-            T *buf = xbuf + par * (NW * 2 * TX);
+            // two parities of NW x 2 edge rows of TX points
+            constexpr int NX = 2 * NW * 2 * TX;
+            const int o = par * (NW * 2 * TX);
+            T *buf = xbuf + o;
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                if (hb == 0) buf[(w * 2 + 0) * TX + li * C + c] = t.v[0][c];
-                if (hb == H - 1) buf[(w * 2 + 1) * TX + li * C + c] = t.v[R - 1][c];
+                const int i0 = (w * 2 + 0) * TX + li * C + c, i1 = (w * 2 + 1) * TX + li * C + c;
+                if (hb == 0 && HJ_IN(dbg, o + i0, NX, 16)) buf[i0] = t.v[0][c];
+                if (hb == H - 1 && HJ_IN(dbg, o + i1, NX, 16)) buf[i1] = t.v[R - 1][c];
             }
             __syncthreads();
             if (w > 0 && hb == 0) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) t.top[c] = buf[((w - 1) * 2 + 1) * TX + li * C + c];
+                for (int c = 0; c < C; ++c) {
+                    const int i = ((w - 1) * 2 + 1) * TX + li * C + c;
+                    if (HJ_IN(dbg, o + i, NX, 17)) t.top[c] = buf[i];
+                }
             }
             if (w < NW - 1 && hb == H - 1) {
 #pragma unroll
-                for (int c = 0; c < C; ++c) t.bot[c] = buf[((w + 1) * 2 + 0) * TX + li * C + c];
+                for (int c = 0; c < C; ++c) {
+                    const int i = ((w + 1) * 2 + 0) * TX + li * C + c;
+                    if (HJ_IN(dbg, o + i, NX, 17)) t.bot[c] = buf[i];
+                }
             }
             par ^= 1;
         }
@@ -450,7 +474,8 @@ __device__ __forceinline__ void store2d(const Tile2D<T, C, R, SIG> &t, const Cyc
             const int col = xl + c;
             bool w = !PART || (row <= a.ny && col <= a.nx);
             if constexpr (OVL) w = w && row >= own.ylo && row <= own.yhi && col >= own.xlo && col <= own.xhi;
-            if (w) st_s<S, T>(uout + (long long)row * a.ld + col, t.v[r][c]);
+            const long long q = (long long)row * a.ld + col;
+            if (w && HJ_IN(a.dbg, q, grid_elems2d(a), 10)) st_s<S, T>(uout + q, t.v[r][c]);
         }
     }
 }
@@ -463,7 +488,7 @@ tile2d(const CycArgs &a, const int x0, const int y0, T *xbuf, const Own own = Ow
     const Coef<T> kc = make_coef<T>(a);
     Tile2D<T, C, R, SIG> t;
     stage2d_global<S, T, C, R, H, EXACT, SIG, PART>(t, a, kc, x0, yb);
-    auto acc = sweeps2d<T, C, R, NW, H, EXACT, SIG, RES, PART, OVL>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf, own);
+    auto acc = sweeps2d<T, C, R, NW, H, EXACT, SIG, RES, PART, OVL>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf, own, a.dbg);
     store2d<S, T, C, R, H, SIG, PART, OVL>(t, a, x0, yb, own);
     return acc;
 }
@@ -526,8 +551,8 @@ tile1d(const CycArgs &a, const int x0, const int row, Xchg1D<T, WPT> &xb, const 
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int col = xl + c;
-        const bool ok = !PART || col <= nx + 1;
-        const bool in = !PART || col <= nx;
+        const bool ok = (!PART || col <= nx + 1) && HJ_IN(a.dbg, rb + col, grid_elems1d(a), 30);
+        const bool in = (!PART || col <= nx) && HJ_IN(a.dbg, rb + col, grid_elems1d(a), 31);
         v[c] = ok ? ld_s<S, T>(uin + rb + col) : (T)0;
         const T fv = in ? __ldg(f + rb + col) : (T)0;
         if constexpr (SIG) {
@@ -542,7 +567,7 @@ tile1d(const CycArgs &a, const int x0, const int row, Xchg1D<T, WPT> &xb, const 
     // frozen halo: first lane of warp 0 (W) and last lane of the last warp (E)
     const bool wl = lane == 0 && q == 0, el = lane == 31 && q == WPT - 1;
     const int hcol = wl ? x0 - 1 : x0 + TX;
-    const bool hok = (wl || el) && (!PART || hcol <= nx + 1);
+    const bool hok = (wl || el) && (!PART || hcol <= nx + 1) && HJ_IN(a.dbg, rb + hcol, grid_elems1d(a), 32);
     const T hx = hok ? ld_s<S, T>(uin + rb + hcol) : (T)0;
 
     typedef typename std::conditional<EXACT, double, T>::type Acc;
@@ -594,7 +619,7 @@ tile1d(const CycArgs &a, const int x0, const int row, Xchg1D<T, WPT> &xb, const 
         const int col = xl + c;
         bool w = !PART || col <= nx;
         if constexpr (OVL) w = w && col >= own_lo && col <= own_hi;
-        if (w) st_s<S, T>(uout + rb + col, v[c]);
+        if (w && HJ_IN(a.dbg, rb + col, grid_elems1d(a), 33)) st_s<S, T>(uout + rb + col, v[c]);
     }
     return acc;
 }
@@ -838,7 +863,7 @@ __global__ void __launch_bounds__(256) classic2d_kernel(const CycArgs a) {
 #pragma unroll
         for (int r = 0; r < R + 2; ++r) {
             const int row = j0 - 1 + r;
-            if (colok && row <= ny + 1) {
+            if (colok && row <= ny + 1 && HJ_IN(a.dbg, (long long)row * ld + c0 + V - 1, grid_elems2d(a), 20)) {
                 ld_vec16<S, T>(uin + (long long)row * ld + c0, u[r]);
             } else {
 #pragma unroll
@@ -849,7 +874,7 @@ __global__ void __launch_bounds__(256) classic2d_kernel(const CycArgs a) {
         for (int r = 0; r < R; ++r) {
             const int row = j0 + r;
             const long long q = (long long)row * ld + c0;
-            if (colok && row <= ny) {
+            if (colok && row <= ny && HJ_IN(a.dbg, q + V - 1, grid_elems2d(a), 21)) {
                 ld_vecT<T, V>(f + q, g[r]);
                 if constexpr (SIG) ld_vecT<T, V>(dinv + q, dv[r]);
             } else {
@@ -859,8 +884,10 @@ __global__ void __launch_bounds__(256) classic2d_kernel(const CycArgs a) {
                     if constexpr (SIG) dv[r][c] = (T)0;
                 }
             }
-            hw[r] = (lane == 0 && c0 >= 1 && row <= ny) ? ld_s<S, T>(uin + q - 1) : (T)0;
-            he[r] = (lane == 31 && c0 + V <= nx + 1 && row <= ny) ? ld_s<S, T>(uin + q + V) : (T)0;
+            hw[r] = (lane == 0 && c0 >= 1 && row <= ny && HJ_IN(a.dbg, q - 1, grid_elems2d(a), 22)) ? ld_s<S, T>(uin + q - 1)
+                                                                                            : (T)0;
+            he[r] = (lane == 31 && c0 + V <= nx + 1 && row <= ny && HJ_IN(a.dbg, q + V, grid_elems2d(a), 23))
+                        ? ld_s<S, T>(uin + q + V) : (T)0;
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -885,7 +912,8 @@ __global__ void __launch_bounds__(256) classic2d_kernel(const CycArgs a) {
                     if (in) acc += (Acc)res * (Acc)res;
                 }
             }
-            if (colok && row <= ny) st_vec16<S, T>(uout + (long long)row * ld + c0, out);
+            if (colok && row <= ny && HJ_IN(a.dbg, (long long)row * ld + c0 + V - 1, grid_elems2d(a), 24))
+                st_vec16<S, T>(uout + (long long)row * ld + c0, out);
         }
     }
     if constexpr (RES) reduce_grid_acc(a.red, acc);

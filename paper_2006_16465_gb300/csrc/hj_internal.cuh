@@ -57,6 +57,27 @@ struct RedArgs {
 };
 
 // Arguments of one cycle (or one classic sweep).
+// Debug builds (compiled with -DHJ_DEBUG) stand in for a memory checker:
+// every staging, exchange and write-back index of the cycle kernels is
+// checked against the extent of the array it addresses; a failure records
+// the first (site, index) in a device word and skips the access instead of
+// trapping, and hj_debug_check reports it.  Release builds compile the
+// checks away (HJ_IN is the constant true).
+struct DbgWord {
+    unsigned long long site;   // 0 = clean
+    long long index;
+};
+#ifdef HJ_DEBUG
+__device__ __forceinline__ bool dbg_in(DbgWord *w, long long i, long long n, int site) {
+    if (i >= 0 && i < n) return true;
+    if (w && atomicCAS(&w->site, 0ull, (unsigned long long)site) == 0ull) w->index = i;
+    return false;
+}
+#define HJ_IN(w, i, n, site) ::hj::dbg_in((w), (long long)(i), (long long)(n), (site))
+#else
+#define HJ_IN(w, i, n, site) true
+#endif
+
 // Classic 2D sweep (classic2d_kernel): rows per thread, and the block of
 // points one CTA of 32 x 8 threads covers per step of its grid-stride loop
 // (columns counted from the ghost column 0, 16 bytes of storage per thread).
@@ -95,6 +116,8 @@ struct CycArgs {
     const void *vc;
     const double *vsig;
     long long vcs;
+    // debug builds: the device word of failed index checks (nullable)
+    DbgWord *dbg;
     // 3D seven-point extension: interior planes, plane pitch (elements) and
     // the bottom (z - 1) / top (z + 1) coefficients with their binary32 copies
     int nz;
@@ -102,6 +125,11 @@ struct CycArgs {
     double cB, cT;
     float fB, fT, gB, gT;
 };
+
+// Elements of one grid array of a 2D problem ((ny + 2) rows) and of a 1D one
+// (ny independent rows), at the pitch the arguments carry.
+__device__ __forceinline__ long long grid_elems2d(const CycArgs &a) { return (long long)(a.ny + 2) * a.ld; }
+__device__ __forceinline__ long long grid_elems1d(const CycArgs &a) { return (long long)a.ny * a.ld; }
 
 // Subdomain j of J along one dimension of n interior points, T points each,
 // overlapping its neighbours by o points: it spans [start, end] and owns

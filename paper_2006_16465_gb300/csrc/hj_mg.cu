@@ -390,7 +390,7 @@ int mg_setup(hj_handle *h, int levels) {
         ny = (ny - 1) / 2;
         cW /= 4.0; cE /= 4.0; cS /= 4.0; cN /= 4.0; cD /= 4.0;
     }
-    if (cudaMalloc(&h->mg_arena, total) != cudaSuccess) {
+    if (dmalloc(&h->mg_arena, total) != cudaSuccess) {
         cudaGetLastError();
         return seterr(HJ_ERR_NO_MEMORY, "cudaMalloc of %zu bytes failed (multigrid levels)", total);
     }

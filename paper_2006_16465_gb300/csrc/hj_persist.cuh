@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(32 * NW) persist2d_kernel(const PersistArgs P)
             const int qi = s_take;
             if (qi >= cnt) break;
             const int item = __ldcg(P.q_items + qi);
+            if (!HJ_IN(P.probs[0].dbg, item, P.nitems, 51)) break;
             const int p = P.item_prob[item];
             CycArgs a = P.probs[p];
             volatile ProbState *st = P.state + p;

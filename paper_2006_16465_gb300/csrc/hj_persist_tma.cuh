@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(32 * NW) persist2d_tma_kernel(const PersistArg
             }
             ++nwait;
             const int item = item_of(i);
+            if (!HJ_IN(P.probs[0].dbg, item, P.nitems, 51)) break;
             const int p = P.item_prob[item];
             CycArgs a = P.probs[p];
             if (cycle_of(p) & 1) {
@@ -127,7 +128,8 @@ __global__ void __launch_bounds__(32 * NW) persist2d_tma_kernel(const PersistArg
             const int x0 = 1 + (blk % tx) * TX, y0 = 1 + (blk / tx) * TY, yb = y0 + band * R;
             const Coef<T> kc = make_coef<T>(a);
             Tile2D<T, C, R, SIG> t;
-            stage2d_smem<S, T, C, R, H, EXACT, SIG>(t, kc, su, sf, sd, L::BWU, L::BWF, band * R);
+            stage2d_smem<S, T, C, R, H, EXACT, SIG>(t, kc, su, sf, sd, L::BWU, L::BWF, band * R,
+                                                    L::UB / (int)sizeof(S), L::FB / (int)sizeof(T), a.dbg);
             __syncthreads();   // every thread is done with the boxes (and s_next is published)
             const int nxt = s_next;
             if (tid == 0 && nxt < cnt) {
@@ -136,14 +138,17 @@ __global__ void __launch_bounds__(32 * NW) persist2d_tma_kernel(const PersistArg
             }
             typename std::conditional<EXACT, double, T>::type acc;
             if (x0 + TX - 1 <= a.nx && y0 + TY - 1 <= a.ny) {
-                acc = sweeps2d<T, C, R, NW, H, EXACT, SIG, true, false>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
+                acc = sweeps2d<T, C, R, NW, H, EXACT, SIG, true, false>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf,
+                                                                        Own{0, 0, 0, 0}, a.dbg);
                 store2d<S, T, C, R, H, SIG, false>(t, a, x0, yb);
             } else {
-                acc = sweeps2d<T, C, R, NW, H, EXACT, SIG, true, true>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
+                acc = sweeps2d<T, C, R, NW, H, EXACT, SIG, true, true>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf,
+                                                                       Own{0, 0, 0, 0}, a.dbg);
                 store2d<S, T, C, R, H, SIG, true>(t, a, x0, yb);
             }
             const double s = cta_sum(acc);
-            if (tid == 0) P.partial[(size_t)parity * P.nitems + item] = s;
+            const size_t pi = (size_t)parity * P.nitems + item;
+            if (tid == 0 && HJ_IN(a.dbg, pi, 2 * (long long)P.nitems, 50)) P.partial[pi] = s;
             i = nxt;
         }
         fence_proxy_async_global();   // this cycle's stores, before the next cycle's copies

@@ -14,6 +14,14 @@
 namespace hj {
 
 int seterr(int code, const char *fmt, ...);
+
+// Device allocations of the library (handle workspaces): plain cudaMalloc /
+// cudaFree in release builds; debug builds add guard bands around each one
+// (hj_debug.cu, checked by hj_debug_check).
+cudaError_t dmalloc(void **p, size_t bytes);
+cudaError_t dfree(void *p);
+// Device word of the index checks of debug builds (nullptr in release builds).
+DbgWord *debug_word();
 const char *last_error_text();
 
 #define CKR(call)                                                                                           \

@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ 
         const int bx = tile % P.tiles_x, by = tile / P.tiles_x;
         const int x0 = 1 + bx * TX, y0 = 1 + by * TY, yb = y0 + band * R;
         Tile2D<T, C, R, SIG> t;
-        stage2d_smem<S, T, C, R, H, EXACT, SIG>(t, kc, su(s), sf(s), sd(s), L::BWU, L::BWF, band * R);
+        stage2d_smem<S, T, C, R, H, EXACT, SIG>(t, kc, su(s), sf(s), sd(s), L::BWU, L::BWF, band * R,
+                                                L::UB / (int)sizeof(S), L::FB / (int)sizeof(T), a.dbg);
         __syncthreads();   // every thread is done with stage s
         if (tid == 0 && i + NST < mine) {
             fence_proxy_async_smem();
@@ -202,10 +203,12 @@ __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ 
         }
         const bool full = (x0 + TX - 1 <= a.nx) && (y0 + TY - 1 <= a.ny);
         if (full) {
-            acc += sweeps2d<T, C, R, NW, H, EXACT, SIG, RES, false>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
+            acc += sweeps2d<T, C, R, NW, H, EXACT, SIG, RES, false>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf, Own{0, 0, 0, 0},
+                                                                    a.dbg);
             store2d<S, T, C, R, H, SIG, false>(t, a, x0, yb);
         } else {
-            acc += sweeps2d<T, C, R, NW, H, EXACT, SIG, RES, true>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf);
+            acc += sweeps2d<T, C, R, NW, H, EXACT, SIG, RES, true>(t, kc, a.k, x0, yb, a.nx, a.ny, xbuf, Own{0, 0, 0, 0},
+                                                                   a.dbg);
             store2d<S, T, C, R, H, SIG, true>(t, a, x0, yb);
         }
     }

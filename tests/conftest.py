@@ -25,3 +25,16 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _debug_build_checks(request):
+    """With the debug library (HJ_LIBRARY=debug), every GPU test ends with the
+    library's memory checks: no index out of range in a kernel, no guard band
+    of a device allocation overwritten."""
+    yield
+    if os.environ.get("HJ_LIBRARY") != "debug" or "gpu" not in request.keywords:
+        return
+    import paper_2006_16465_gb300 as hj
+    code, site, index = hj.hj_debug_check()
+    assert code == hj.HJ_OK, f"debug check after {request.node.name}: site {site}, index {index}"

@@ -45,7 +45,7 @@ def test_default_params_and_strings(hj):
     p = hj.hj_default_params()
     assert (p.tile_x, p.tile_y, p.k, p.precision, p.check_every) == (32, 32, 16, hj.HJ_PREC_F64, 64)
     assert p.tol == 1e-6 and p.max_outer == 60 and p.persistent == -1
-    for code in range(0, 9):
+    for code in range(0, 10):
         assert hj.hj_error_string(code) != "unknown status"
     assert hj.hj_error_string(99) == "unknown status"
 
@@ -154,3 +154,11 @@ def test_noalloc_refuses_engines_that_need_workspace(hj):
         prm = hj.make_params(fixed_cycles=1, precision="f64", **kw)
         code = hj.lib().hj_cycles_noalloc(C.byref(st_d), C.byref(prm), C.c_void_p(4096), C.c_void_p(8192), None)
         assert code == hj.HJ_ERR_UNSUPPORTED, kw
+
+
+def test_release_build_reports_no_debug_checks(hj):
+    """The release library compiles the memory checks away: hj_debug_check
+    says so (site -1) and the self-test is refused; no GPU work either way."""
+    code, site, _ = hj.hj_debug_check()
+    assert code == hj.HJ_OK and site == -1
+    assert hj.hj_debug_selftest() == hj.HJ_ERR_UNSUPPORTED
