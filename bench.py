@@ -557,6 +557,34 @@ def fd_check(torch, hj, W, n=1024, entries=32, rel_step=1e-6, seed=7, tol=1e-12,
             "forward_adjoint_s": t_adj, "fd_solves_s": t_fd, "points": pts, "fd": fd, "adjoint": adj}
 
 
+def classic_rate(torch, hj, n, cycles=200):
+    """Plain global-memory Jacobi (Section 3.2) on the n x n bench grid,
+    binary32: the sweep kernel alone (fixed sweeps) against its 12 B per
+    point (read u and f, write u), and with the fused residual every sweep."""
+    st, f, u0 = make_problem(n)
+    uc = u0.clone()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    rates = {}
+    for name, kw in (("sweep", dict(fixed_cycles=cycles)),
+                     ("sweep_and_residual", dict(tol=0.0, max_cycles=cycles, check_every=100))):
+        cl = hj.Solver(st, method="classic", precision="f32", **kw)
+        cl.solve(f, uc, check=False)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cl.solve(f, uc, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rates[name] = e0.elapsed_time(e1) / cycles
+        cl.close()
+    hbm_peak, _ = _peaks()
+    cms = rates["sweep"]
+    return {"glups": n * n / (cms / 1e3) / 1e9, "us_per_sweep": cms * 1e3,
+            "hbm_gbs": 12 * n * n / (cms / 1e3) / 1e9, "hbm_frac": 12 * n * n / (cms / 1e3) / 1e9 / hbm_peak,
+            "us_per_sweep_with_fused_residual": rates["sweep_and_residual"] * 1e3}
+
+
 def inner_roofline(torch, hj, W, n, k=16, cycles=100):
     """Inner sweeps bound by the binary32 FMA pipe: 4 FMAs per point update, so
     peak = SMs x 128 lanes x max SM clock / 4 point updates per second."""
@@ -881,7 +909,7 @@ def time_batched(torch, hj, W):
         code = hj.hj_solve_batched(s.h, descs, [f.data_ptr() for f in fs], [u.data_ptr() for u in us], 0, st, cyc)
         torch.cuda.synchronize()
         n = st.cycle_len
-        m = np.array(ms[:n])
+        m = np.array(ms[:n]) * 1e-3   # seconds per batch cycle
         p = np.array(pts[:n], dtype=np.float64)
         props = torch.cuda.get_device_properties(torch.cuda.current_device())
         alu_peak = props.multi_processor_count * 128 * 2070e6 / 4
@@ -891,7 +919,8 @@ def time_batched(torch, hj, W):
                "inner_cycles_total": st.inner_cycles, "inner_cycles_max": max(cyc),
                "unknowns": sum(q.st.nx * q.st.ny for q in probs), "tile": [st.tile_x, st.tile_y], "k_max": st.k,
                "batch_cycles": n, "batch_cycle_seconds": float(m.sum()),
-               "us_per_cycle_all_active": float(m[p >= p.max()].mean() * 1e3) if n else None,
+               "us_per_cycle_all_active": float(m[p >= p.max()].mean() * 1e6) if n else None,
+               "us_per_cycle_tail": float(m[p < 1e6].mean() * 1e6) if (p < 1e6).any() else None,
                "tail_cycles_lt_1M_points": int((p < 1e6).sum()), "tail_seconds": float(m[p < 1e6].sum()),
                "inner_updates_per_s_at_k_max": upd / float(m.sum()) if n else None,
                "inner_alu_frac_at_k_max": upd / float(m.sum()) / alu_peak if n else None}
@@ -951,7 +980,7 @@ def main():
                     help="also time the paper's Section 3.5 / 4.2 problems (binary64, minutes)")
     ap.add_argument("--only", default="", choices=["", "variable_coefficients", "three_d", "multigrid",
                                                     "time_to_residual", "cfg2_k_sweep", "cfg3_precision",
-                                                    "fd_check", "cpu_baseline"],
+                                                    "fd_check", "cpu_baseline", "classic"],
                     help="run one extras section alone and print its JSON (profiling runs)")
     ap.add_argument("--fd-n", type=int, default=1024, help="grid side of the finite-difference check")
     ap.add_argument("--fd-entries", type=int, default=32, help="sigma entries the finite-difference check perturbs")
@@ -974,7 +1003,8 @@ def main():
                    "cfg2_k_sweep": lambda: cfg2_k_sweep(torch, hj, W),
                    "cfg3_precision": lambda: cfg3_precision(torch, hj, W),
                    "fd_check": lambda: fd_check(torch, hj, W, n=args.fd_n, entries=args.fd_entries),
-                   "cpu_baseline": lambda: cpu_baseline(args.k)}
+                   "cpu_baseline": lambda: cpu_baseline(args.k),
+                   "classic": lambda: classic_rate(torch, hj, args.n)}
         print(json.dumps({args.only: section[args.only]()}), flush=True)
         return 0
 
@@ -1047,25 +1077,9 @@ def main():
         # plain global-memory Jacobi on the same grid: the sweep kernel alone
         # (fixed sweeps: its HBM roofline) and with the fused residual every
         # sweep (as the converging solves run it)
+        extras["classic_global_jacobi"] = classic_rate(torch, hj, n, cycles=1000)
         uc = u0.clone()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        rates = {}
-        for name, kw in (("sweep", dict(fixed_cycles=1000)),
-                         ("sweep_and_residual", dict(tol=0.0, max_cycles=1000, check_every=100))):
-            cl = hj.Solver(st, method="classic", precision="f32", **kw)
-            cl.solve(f, uc, check=False)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            cl.solve(f, uc, check=False)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            rates[name] = e0.elapsed_time(e1) / 1000
-            cl.close()
-        cms = rates["sweep"]
-        extras["classic_global_jacobi"] = {"glups": n * n / (cms / 1e3) / 1e9, "us_per_sweep": cms * 1e3,
-                                           "hbm_gbs": 12 * n * n / (cms / 1e3) / 1e9,
-                                           "hbm_frac": 12 * n * n / (cms / 1e3) / 1e9 / hbm_peak,
-                                           "us_per_sweep_with_fused_residual": rates["sweep_and_residual"] * 1e3}
         # the same sweep through the tile kernels (a hierarchical cycle with k = 1 is one
         # classic sweep, bitwise), launch shape tuned like the headline's
         cl = hj.Solver(st, tile_x=32, tile_y=32, k=1, precision="f32", tol=0.0, max_cycles=1000, check_every=100,

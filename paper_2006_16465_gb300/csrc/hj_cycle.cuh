@@ -262,6 +262,19 @@ __device__ __forceinline__ void stage2d_smem(Tile2D<T, C, R, SIG> &t, const Coef
     }
 }
 
+// m ? x : y for a per-lane mask m (all ones or zero), as bitwise operations:
+// the halo and band selects below differ between the lanes of a warp on
+// every row, and as masks they stay single instructions, never branches.
+__device__ __forceinline__ float mask_sel(unsigned m, float x, float y) {
+    return __uint_as_float((__float_as_uint(x) & m) | (__float_as_uint(y) & ~m));
+}
+__device__ __forceinline__ double mask_sel(unsigned m, double x, double y) {
+    const unsigned long long mm = (unsigned long long)(int)m;   // sign-extended: all ones or zero
+    return __longlong_as_double((long long)(((unsigned long long)__double_as_longlong(x) & mm) |
+                                            ((unsigned long long)__double_as_longlong(y) & ~mm)));
+}
+__device__ __forceinline__ unsigned lane_mask(bool b) { return b ? 0xffffffffu : 0u; }
+
 // Packed binary32 pairs (fma/mul .f32x2: two independent round-to-nearest
 // operations, so a pair gives exactly the two scalar results).
 __device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
@@ -325,6 +338,8 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int li = lane % L, hb = lane / L;
     const int xl = x0 + li * C;
+    const unsigned m_first = lane_mask(li == 0), m_last = lane_mask(li == L - 1);   // halo lanes of a row
+    const unsigned m_top = lane_mask(hb > 0), m_bot = lane_mask(hb < H - 1);         // bands with a band above / below
     typedef typename std::conditional<EXACT, double, T>::type Acc;
     Acc acc = 0;
     auto sweep = [&](auto first_tag) {
@@ -337,10 +352,8 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
             T cur[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) cur[c] = t.v[r][c];
-            T left = __shfl_up_sync(FULL, cur[C - 1], 1);
-            T right = __shfl_down_sync(FULL, cur[0], 1);
-            if (li == 0) left = t.hx[r];
-            if (li == L - 1) right = t.hx[r];
+            const T left = mask_sel(m_first, t.hx[r], __shfl_up_sync(FULL, cur[C - 1], 1));
+            const T right = mask_sel(m_last, t.hx[r], __shfl_down_sync(FULL, cur[0], 1));
             if constexpr (PACK) {
 #pragma unroll
                 for (int c = 0; c < C; c += 2) {
@@ -402,24 +415,25 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
     int par = 0;
     // before each subiteration after the first: the rows next to each band
     // become the neighbouring bands' values of the previous subiteration
-    auto exchange = [&]() {
+    // (v: the registers holding that subiteration's values)
+    auto exchange = [&](T (&v)[R][C]) {
         if constexpr (H == 2) {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                const T send = hb ? t.v[0][c] : t.v[R - 1][c];
+                const T send = mask_sel(m_top, v[0][c], v[R - 1][c]);
                 const T recv = __shfl_xor_sync(FULL, send, 16);
-                if (hb) t.top[c] = recv;
-                else t.bot[c] = recv;
+                t.top[c] = mask_sel(m_top, recv, t.top[c]);
+                t.bot[c] = mask_sel(m_bot, recv, t.bot[c]);
             }
         } else if constexpr (H == 4) {
             // band hb's top row is band hb-1's last row (L lanes down), its
             // bottom row band hb+1's first row (L lanes up)
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                const T up = __shfl_up_sync(FULL, t.v[R - 1][c], L);
-                const T dn = __shfl_down_sync(FULL, t.v[0][c], L);
-                if (hb > 0) t.top[c] = up;
-                if (hb < H - 1) t.bot[c] = dn;
+                const T up = __shfl_up_sync(FULL, v[R - 1][c], L);
+                const T dn = __shfl_down_sync(FULL, v[0][c], L);
+                t.top[c] = mask_sel(m_top, up, t.top[c]);
+                t.bot[c] = mask_sel(m_bot, dn, t.bot[c]);
             }
         }
         if constexpr (NW > 1) {
@@ -430,8 +444,8 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 const int i0 = (w * 2 + 0) * TX + li * C + c, i1 = (w * 2 + 1) * TX + li * C + c;
-                if (hb == 0 && HJ_IN(dbg, o + i0, NX, 16)) buf[i0] = t.v[0][c];
-                if (hb == H - 1 && HJ_IN(dbg, o + i1, NX, 16)) buf[i1] = t.v[R - 1][c];
+                if (hb == 0 && HJ_IN(dbg, o + i0, NX, 16)) buf[i0] = v[0][c];
+                if (hb == H - 1 && HJ_IN(dbg, o + i1, NX, 16)) buf[i1] = v[R - 1][c];
             }
             __syncthreads();
             if (w > 0 && hb == 0) {
@@ -453,7 +467,7 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
     };
     sweep(std::integral_constant<bool, true>());
     for (int s = 1; s < k; ++s) {
-        exchange();
+        exchange(t.v);
         sweep(std::integral_constant<bool, false>());
     }
     return acc;
