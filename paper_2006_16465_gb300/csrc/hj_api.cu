@@ -299,15 +299,20 @@ constexpr int kPpcPeriod = 6;
 
 struct Plan {
     bool ppc = false;
-    bool deferred = false;   // pipelined kernel with deferred residual fold
+    bool deferred = false;   // fused residual with the deferred fold (three iterate buffers)
     int period = 2;          // argument blocks launches cycle through
     CycKernel fn = nullptr;
     PpcKernel pfn = nullptr;
     dim3 grid, block;
     int smem = 0;
-    CycArgs a[2];
+    CycArgs a[kPpcPeriod];
     PpcArgs p[kPpcPeriod];
 };
+
+// Largest grid of the one-CTA-per-subdomain kernels that folds its residual
+// in the next launch (one warp sums one partial per CTA; larger grids keep the
+// grid reduction at the launch's end).
+constexpr long long kDeferMaxBlocks = 4096;
 
 // 3D: whether the prefetching (persistent-warp, cp.async) kernel runs.  Only
 // on request (pipeline = 1): measured at 512^3 binary32 it is slower than the
@@ -323,6 +328,22 @@ bool want_ppc(const hj_handle *h, const PpcKernelInfo *pi, bool classic) {
     if (h->p.pipeline != -1) return false;
     const long long ntiles = (long long)((h->d.nx + pi->tx - 1) / pi->tx) * ((h->d.ny + pi->ty - 1) / pi->ty);
     return ntiles >= 8LL * h->nsm;
+}
+
+// Whether a converging run of the one-CTA-per-subdomain 2D kernels folds its
+// residual in the next launch (as the pipelined kernel always does): 2D
+// hierarchical cycles with constant coefficients on grids of at most
+// kDeferMaxBlocks subdomains.
+bool defer_hier(const hj_handle *h, const TileKernelInfo *ki, bool classic) {
+    if (classic || !ki || h->d.dim != 2 || h->d.coef) return false;
+    dim3 g, b;
+    geometry(h, ki, false, &g, &b);
+    return (long long)g.x * g.y <= kDeferMaxBlocks;
+}
+
+// Whether a converging run of this plan needs the third iterate buffer.
+bool deferred_run(const hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, bool classic) {
+    return want_ppc(h, pi, classic) || defer_hier(h, ki, classic);
 }
 
 
@@ -375,9 +396,13 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
         // same kernel with one subiteration (a k = 1 cycle is a classic sweep)
         const VcKernelInfo *vk = fam == FAM_F64 ? vc_kernels_f64() : vc_kernels_f32();
         const int tx = h->p.tile_x, ty = h->d.dim == 2 ? h->p.tile_y : 1;
-        pl->fn = vk->fn[h->d.dim - 1][res];
+        // 2D subdomains of 512 or more points whose height divides by 4 run
+        // with four rows per thread (smaller CTAs, more of them per SM;
+        // measured faster at 32 x 32, slower at 32 x 8)
+        const bool r4 = h->d.dim == 2 && ty % 4 == 0 && tx * ty >= 512;
+        pl->fn = r4 ? vk->fn4[res] : vk->fn[h->d.dim - 1][res];
         pl->grid = h->d.dim == 2 ? dim3((nx + tx - 1) / tx, (ny + ty - 1) / ty) : dim3((nx + tx - 1) / tx, ny);
-        pl->block = h->d.dim == 2 ? dim3(tx, ty) : dim3(tx);
+        pl->block = h->d.dim == 2 ? dim3(tx, r4 ? ty / 4 : ty) : dim3(tx);
         pl->smem = 2 * (tx + 2) * (h->d.dim == 2 ? ty + 2 : 1) * (fam == FAM_F64 ? 8 : 4);
         if (classic) pl->a[0].k = pl->a[1].k = 1;
         pl->ppc = false;
@@ -386,6 +411,25 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
     if (!want_ppc(h, pi, classic)) {
         geometry(h, ki, classic, &pl->grid, &pl->block);
         pl->fn = (!classic && overlapped(h)) ? ki->ovl[sig][res] : ki->fn[sig][res];
+        if (res && defer_hier(h, ki, classic)) {
+            // deferred fold: launch c reads B[c % 3], writes B[(c+1) % 3] and
+            // its per-CTA partials to slot c % 2, folded by launch c + 1
+            if (!b2) return seterr(HJ_ERR_CUDA, "internal: deferred residual runs need a third iterate buffer");
+            const long long nb = (long long)pl->grid.x * pl->grid.y;
+            CKS(ensure_reduction(h, (size_t)nb));
+            void *bufs[3] = {b0, b1, b2};
+            pl->deferred = true;
+            pl->period = kPpcPeriod;
+            for (int j = 0; j < kPpcPeriod; ++j) {
+                CycArgs &A = pl->a[j];
+                A = base;
+                A.uin = bufs[j % 3];
+                A.uout = bufs[(j + 1) % 3];
+                A.part_w = h->partials + (size_t)(j & 1) * nb;
+                A.part_r = h->partials + (size_t)((j + 1) & 1) * nb;
+                A.parity = j & 1;
+            }
+        }
         if (classic && h->d.dim == 2) {
             // one wave of resident CTAs: every CTA of the grid-stride sweep gets
             // the same share of blocks, so a partial last wave would idle SMs
@@ -449,12 +493,12 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
 
 int plan_graph(hj_handle *h, const Plan &pl, int M, cudaGraphExec_t *ex) {
     if (pl.ppc) return get_graph<PpcArgs>(h, pl.pfn, pl.grid, pl.block, pl.smem, pl.p, pl.period, M, ex);
-    return get_graph<CycArgs>(h, pl.fn, pl.grid, pl.block, pl.smem, pl.a, 2, M, ex);
+    return get_graph<CycArgs>(h, pl.fn, pl.grid, pl.block, pl.smem, pl.a, pl.period, M, ex);
 }
 
 void plan_launch(const Plan &pl, long long c, cudaStream_t s) {
     if (pl.ppc) pl.pfn<<<pl.grid, pl.block, pl.smem, s>>>(pl.p[c % pl.period]);
-    else pl.fn<<<pl.grid, pl.block, pl.smem, s>>>(pl.a[c & 1]);
+    else pl.fn<<<pl.grid, pl.block, pl.smem, s>>>(pl.a[c % pl.period]);
 }
 
 struct RunOut {
@@ -531,7 +575,7 @@ int run_cycles(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, 
     void *b2 = nullptr;
     if (third.alias) {
         b2 = third.alias;
-    } else if (want_ppc(h, pi, classic)) {
+    } else if (deferred_run(h, ki, pi, classic)) {
         if (!third.slot) return seterr(HJ_ERR_CUDA, "internal: no slot for the third iterate buffer");
         if (!*third.slot) {
             if (dmalloc(third.slot, third.bytes) != cudaSuccess) {

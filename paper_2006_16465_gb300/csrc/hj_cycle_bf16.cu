@@ -6,6 +6,8 @@ namespace hj {
 static const TileKernelInfo k_tiles[] = {
     HJ_K2D(__nv_bfloat16, float, 2, 16, 1, 2, false),    // 32 x 32
     HJ_K2D(__nv_bfloat16, float, 2, 8, 2, 2, false),     // 32 x 32, two warps
+    HJ_K2D(__nv_bfloat16, float, 2, 4, 4, 2, false),     // 32 x 32, four warps
+    HJ_K2D(__nv_bfloat16, float, 2, 2, 8, 2, false),     // 32 x 32, eight warps
     HJ_K2D(__nv_bfloat16, float, 2, 8, 1, 2, false),     // 32 x 16
     HJ_K2D(__nv_bfloat16, float, 2, 4, 1, 2, false),     // 32 x 8
     HJ_K2D(__nv_bfloat16, float, 2, 16, 2, 2, false),    // 32 x 64

@@ -118,6 +118,13 @@ struct CycArgs {
     long long vcs;
     // debug builds: the device word of failed index checks (nullable)
     DbgWord *dbg;
+    // fused residual with a deferred fold (part_w non-null): this launch
+    // writes one partial of ||f - A u_c||^2 per CTA into part_w; the last CTA
+    // of the next launch folds them (part_r there) into the control block;
+    // parity = launch index mod 2 selects the launch's fold_only flag
+    double *part_w;
+    const double *part_r;
+    int parity;
     // 3D seven-point extension: interior planes, plane pitch (elements) and
     // the bottom (z - 1) / top (z + 1) coefficients with their binary32 copies
     int nz;
@@ -334,6 +341,22 @@ __device__ __forceinline__ void fold_partials(const RedArgs &r, const double *pa
     if (lane == 0) finish_cycle(r, s * r.scale);
 }
 
+// Deferred fold, run by one warp of the last CTA of a launch: fold the
+// previous launch's partials (nparts of them: the residual of the iterate that
+// launch staged), then decide whether the next launch only folds (its iterate
+// would lie beyond max_cycles).  The launch counter and the flags are touched
+// by this warp only, one launch after another.
+__device__ __forceinline__ void deferred_fold_parts(const RedArgs &red, const double *part_r, int nparts,
+                                                    int parity) {
+    volatile Ctl *ctl = red.ctl;
+    const long long l = ctl->launch;
+    if (l >= 1) fold_partials(red, part_r, nparts);
+    if ((threadIdx.x & 31) == 0) {
+        ctl->fold_only[parity ^ 1] = (l + 1 >= red.max_cycles) ? 1 : 0;
+        ctl->launch = l + 1;
+    }
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
@@ -381,7 +404,8 @@ struct TileKernelInfo {
 // Variable-coefficient kernels: [dim - 1][res], one thread per point, dynamic
 // shared memory 2 * (tile_x + 2) * (tile_y + 2) elements of the compute type.
 struct VcKernelInfo {
-    CycKernel fn[2][2];
+    CycKernel fn[2][2];   // [dim - 1][res]: one point per thread
+    CycKernel fn4[2];     // [res]: 2D, four rows per thread (subdomain heights that are multiples of 4)
 };
 const VcKernelInfo *vc_kernels_f64();
 const VcKernelInfo *vc_kernels_f32();

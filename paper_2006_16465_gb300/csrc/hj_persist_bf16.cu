@@ -9,6 +9,8 @@ namespace hj {
 static const PersistKernelInfo k_persist[] = {
     HJ_KP2D(__nv_bfloat16, float, 2, 16, 1, 2, false),
     HJ_KP2D(__nv_bfloat16, float, 2, 8, 2, 2, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 4, 4, 2, false),
+    HJ_KP2D(__nv_bfloat16, float, 2, 2, 8, 2, false),
     HJ_KP2D(__nv_bfloat16, float, 2, 8, 1, 2, false),
     HJ_KP2D(__nv_bfloat16, float, 2, 4, 1, 2, false),
     HJ_KP2D(__nv_bfloat16, float, 2, 16, 2, 1, false),

@@ -93,41 +93,10 @@ struct PpcLayout {
     static constexpr int SMEM = XB_OFF + XB_BYTES + 128;   // + room to align the base to 128 bytes
 };
 
-// Deferred fold, run by one warp of the last CTA of a launch: fold the
-// previous launch's partials (residual of the iterate that launch staged),
-// then decide whether the next launch only folds (its iterate would lie
-// beyond max_cycles).  The launch counter and the flags are touched by this
-// warp only, one launch after another.
+// Deferred fold of the pipelined kernel's residual (deferred_fold_parts over
+// the previous launch's one partial per CTA).
 __device__ __forceinline__ void deferred_fold(const PpcArgs &P) {
-    volatile Ctl *ctl = P.a.red.ctl;
-    const long long l = ctl->launch;
-    if (l >= 1) fold_partials(P.a.red, P.part_r, (int)gridDim.x);
-    if ((threadIdx.x & 31) == 0) {
-        ctl->fold_only[P.parity ^ 1] = (l + 1 >= P.a.red.max_cycles) ? 1 : 0;
-        ctl->launch = l + 1;
-    }
-}
-
-// One partial of the CTA's residual share, written without atomics: the next
-// launch reads it after this kernel has completed.
-template <int NW, typename A>
-__device__ __forceinline__ void write_cta_partial(double *out, A acc) {
-    double v;
-    if constexpr (std::is_same<A, float>::value) v = (double)warp_sum_f(acc);
-    else v = warp_sum((double)acc);
-    if constexpr (NW == 1) {
-        if (threadIdx.x == 0) out[blockIdx.x] = v;
-    } else {
-        __shared__ double s_w[NW];
-        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) t += s_w[w];
-            out[blockIdx.x] = t;
-        }
-    }
+    deferred_fold_parts(P.a.red, P.part_r, (int)gridDim.x, P.parity);
 }
 
 template <typename S, typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES, int NST>
@@ -227,7 +196,7 @@ __global__ void __launch_bounds__(32 * NW) ppc2d_kernel(const __grid_constant__ 
         __syncthreads();
         return;
     }
-    if constexpr (RES) write_cta_partial<NW>(P.part_w, acc);
+    if constexpr (RES) write_cta_partial<NW>(P.part_w + blockIdx.x, acc);
 }
 
 }  // namespace hj

@@ -884,3 +884,64 @@ def test_batched_steps_replay_one_graph_and_log_batch_cycles():
     drops = sum(1 for i in range(1, n) if pts[i] < pts[i - 1])
     assert drops >= 1
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16corr_ir"])
+def test_every_threads_variant_gives_the_same_iterates(prec):
+    """A subdomain swept by one, two, four or eight warps (band edges through
+    shared memory) computes the same values: every built (tile, threads)
+    variant equals the default one bit for bit, in graph launches (with and
+    without overlapping subdomains) and in the persistent engine's solve.
+    (Binary64 builds one threads variant per 2D shape; the bfloat16-stored
+    correction family shares the binary32 kernels' shapes and is run here in
+    its refinement.)"""
+    torch = _torch()
+    import paper_2006_16465_gb300 as hj
+    dt = torch.float32 if prec == "f32" else torch.float64
+    shapes = {}
+    for tx, ty, th in hj.hj_tile_variants(2, hj.PRECISIONS[prec]):
+        shapes.setdefault((tx, ty), []).append(th)
+    checked = 0
+    for (tx, ty), threads in shapes.items():
+        if len(threads) < 2:
+            continue
+        p = W.random_bc_problem(2, 150, 97, seed=tx + ty, sigma_kind="field", asym=True)
+        if prec != "f32":
+            # refinement: binary64 iterate, inner cycles on bfloat16-stored corrections
+            outs = []
+            for th in threads:
+                s = gpu_solver(p, tile_x=tx, tile_y=ty, k=6, precision=prec, tol=1e-8, inner_tol=1e-2,
+                               tile_threads=th, persistent=1, pipeline=0)
+                u = to_dev(p.u0, 2, dt)
+                out = s.solve(to_dev(p.f, 2, dt), u)
+                assert out["status"] == 0
+                outs.append((out["inner_cycles"], to_host(u, 150)))
+                s.close()
+            for th, (c, u) in zip(threads[1:], outs[1:]):
+                assert c == outs[0][0] and np.array_equal(u, outs[0][1]), (tx, ty, th)
+            checked += 1
+            continue
+        for extra in (dict(), dict(overlap_x=4, overlap_y=2)):
+            outs = []
+            for th in threads:
+                s = gpu_solver(p, tile_x=tx, tile_y=ty, k=5, precision=prec, fixed_cycles=4, tile_threads=th,
+                               pipeline=0, **extra)
+                u = to_dev(p.u0, 2, dt)
+                s.solve(to_dev(p.f, 2, dt), u)
+                outs.append(to_host(u, 150))
+                s.close()
+            for th, o in zip(threads[1:], outs[1:]):
+                assert np.array_equal(o, outs[0]), (tx, ty, th, extra)
+        sols = []
+        for th in threads:
+            s = gpu_solver(p, tile_x=tx, tile_y=ty, k=6, precision=prec, tol=1e-5, check_every=8, tile_threads=th,
+                           persistent=1, pipeline=0)
+            u = to_dev(p.u0, 2, dt)
+            out = s.solve(to_dev(p.f, 2, dt), u)
+            assert out["status"] == 0 and out["persistent"] == 1
+            sols.append((out["cycles"], to_host(u, 150)))
+            s.close()
+        for th, (c, u) in zip(threads[1:], sols[1:]):
+            assert c == sols[0][0] and np.array_equal(u, sols[0][1]), (tx, ty, th)
+        checked += 1
+    assert checked >= 1
