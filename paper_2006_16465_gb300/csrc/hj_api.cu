@@ -396,13 +396,9 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
         // same kernel with one subiteration (a k = 1 cycle is a classic sweep)
         const VcKernelInfo *vk = fam == FAM_F64 ? vc_kernels_f64() : vc_kernels_f32();
         const int tx = h->p.tile_x, ty = h->d.dim == 2 ? h->p.tile_y : 1;
-        // 2D subdomains of 512 or more points whose height divides by 4 run
-        // with four rows per thread (smaller CTAs, more of them per SM;
-        // measured faster at 32 x 32, slower at 32 x 8)
-        const bool r4 = h->d.dim == 2 && ty % 4 == 0 && tx * ty >= 512;
-        pl->fn = r4 ? vk->fn4[res] : vk->fn[h->d.dim - 1][res];
+        pl->fn = vk->fn[h->d.dim - 1][res];
         pl->grid = h->d.dim == 2 ? dim3((nx + tx - 1) / tx, (ny + ty - 1) / ty) : dim3((nx + tx - 1) / tx, ny);
-        pl->block = h->d.dim == 2 ? dim3(tx, r4 ? ty / 4 : ty) : dim3(tx);
+        pl->block = h->d.dim == 2 ? dim3(tx, ty) : dim3(tx);
         pl->smem = 2 * (tx + 2) * (h->d.dim == 2 ? ty + 2 : 1) * (fam == FAM_F64 ? 8 : 4);
         if (classic) pl->a[0].k = pl->a[1].k = 1;
         pl->ppc = false;

@@ -708,14 +708,11 @@ __global__ void __launch_bounds__(32 * WPT * WPB) hier1d_kernel(const CycArgs a)
 
 // ---------------------------------------------------------------------------
 // Variable neighbour coefficients (the general tridiagonal a_i, d_i, c_i of
-// Section 3 and its 2D analogue): the subdomain plus its halo in two
-// shared-memory containers used in turn (the paper's own kernel layout,
-// Appendix A), one barrier per subiteration.  A thread owns RPT points of a
-// column of the subdomain (rows ty, ty + blockDim.y, ...: a warp's loads and
-// stores stay one row wide) and keeps their coefficients in registers;
-// RPT > 1 lets a 32 x 32 subdomain run as a CTA of 256 threads, so that more
-// CTAs fit on an SM.  blockDim = (tile_x, tile_y / RPT) in 2D, (tile_x) in 1D
-// with one copy per blockIdx.y.
+// Section 3 and its 2D analogue): one thread per point, the subdomain plus its
+// halo in two shared-memory containers used in turn (the paper's own kernel
+// layout, Appendix A), one barrier per subiteration.  A thread keeps its
+// point's coefficients in registers.  blockDim = (tile_x, tile_y) in 2D,
+// (tile_x) in 1D with one copy per blockIdx.y.
 //   binary64: acc = cW*uW; acc += cE*uE; [acc += cS*uS; acc += cN*uN;]
 //             u' = (f - acc) * (1/d_p), d_p = dconst + sigma_p, each operation
 //             rounded separately (the oracle's order); 1/d_p comes from the
@@ -723,92 +720,78 @@ __global__ void __launch_bounds__(32 * WPT * WPB) hier1d_kernel(const CycArgs a)
 //   binary32: u' = f/d + (-cN/d) uN + (-cS/d) uS + (-cE/d) uE + (-cW/d) uW as a
 //             fused chain from precomputed per-point factors.
 // ---------------------------------------------------------------------------
-template <typename S, typename T, int DIM, int RPT, bool EXACT, bool RES>
-__global__ void __launch_bounds__(RPT > 1 ? 256 : 1024, RPT > 1 ? (sizeof(T) == 8 ? 2 : 4) : 2) vc_kernel(const CycArgs a) {
-    static_assert(DIM == 2 || RPT == 1, "1D subdomains: one point per thread");
+template <typename S, typename T, int DIM, bool EXACT, bool RES>
+__global__ void __launch_bounds__(1024, 2) vc_kernel(const CycArgs a) {
     if constexpr (RES) {
         if (*(volatile int *)&a.red.ctl->done >= 0) return;
     }
     extern __shared__ __align__(16) unsigned char vc_smem[];
-    const int BY = DIM == 2 ? blockDim.y : 1;
-    const int TX = blockDim.x, TY = BY * RPT;
+    const int TX = blockDim.x, TY = DIM == 2 ? blockDim.y : 1;
     const int lw = TX + 2, lh = DIM == 2 ? TY + 2 : 1;
     T *buf0 = (T *)vc_smem, *buf1 = buf0 + lw * lh;
     const int tx = threadIdx.x, ty = DIM == 2 ? threadIdx.y : 0;
     const int i = 1 + blockIdx.x * TX + tx;
+    const int j = DIM == 2 ? 1 + blockIdx.y * TY + ty : blockIdx.y;
     const int nx = a.nx, ny = a.ny;
     const long long ld = a.ld;
+    const bool in = i <= nx && (DIM == 1 || j <= ny);
     const S *__restrict__ uin = (const S *)a.uin;
     const T *__restrict__ f = (const T *)a.f;
-    const long long ps = a.vcs;
+    const int me = (ty + (DIM == 2 ? 1 : 0)) * lw + tx + 1;
     auto ld_u = [&](int jj, int ii) -> T {
         const bool ok = ii <= nx + 1 && (DIM == 1 || jj <= ny + 1);
         return ok ? ld_s<S, T>(uin + (long long)jj * ld + ii) : (T)0;
     };
-    // Every global load first (the points, the halo cells next to them, f and
-    // the points' factors), then the shared-memory stores: one round of
+    // Every global load first (the point, the halo cells next to it, f and
+    // the point's factors), then the shared-memory stores: one round of
     // memory latency per subdomain instead of one per kind of operand.
-    int jm[RPT], me[RPT];
-    bool in[RPT];
-    T v0[RPT], hw[RPT], he[RPT];
-    T cw[RPT], ce[RPT], cs[RPT], cn[RPT], g[RPT], dpt[RPT], iv[RPT];
-    long long q[RPT];
-#pragma unroll
-    for (int m = 0; m < RPT; ++m) {
-        const int ly = ty + m * BY;   // row within the subdomain
-        jm[m] = DIM == 2 ? 1 + blockIdx.y * TY + ly : blockIdx.y;
-        me[m] = (ly + (DIM == 2 ? 1 : 0)) * lw + tx + 1;
-        in[m] = i <= nx && (DIM == 1 || jm[m] <= ny);
-        q[m] = (long long)jm[m] * ld + i;
-        v0[m] = ld_u(jm[m], i);
-        hw[m] = tx == 0 ? ld_u(jm[m], i - 1) : (T)0;
-        he[m] = tx == TX - 1 ? ld_u(jm[m], i + 1) : (T)0;
-        cw[m] = ce[m] = cs[m] = cn[m] = g[m] = dpt[m] = iv[m] = (T)0;
-        if (in[m]) {
-            if constexpr (EXACT) {
-                const double *__restrict__ c = (const double *)a.vc;
-                cw[m] = __ldg(c + q[m]);
-                ce[m] = __ldg(c + ps + q[m]);
-                if constexpr (DIM == 2) {
-                    cs[m] = __ldg(c + 2 * ps + q[m]);
-                    cn[m] = __ldg(c + 3 * ps + q[m]);
-                }
-                // 1/d_p from the handle's plane (the same correctly rounded
-                // reciprocal of dconst + sigma_p): binary64 arithmetic is the
-                // scarce resource here, bytes are not
-                if constexpr (RES) dpt[m] = a.vsig ? __dadd_rn(a.dconst, __ldg(a.vsig + q[m])) : a.dconst;
-                iv[m] = a.dinv ? __ldg((const double *)a.dinv + q[m]) : __drcp_rn(a.dconst);
-                g[m] = __ldg(f + q[m]);
-            } else {
-                const float *__restrict__ c = (const float *)a.vc;
-                constexpr int NP = DIM == 2 ? 4 : 2;   // planes before 1/d and d
-                cw[m] = __ldg(c + q[m]);
-                ce[m] = __ldg(c + ps + q[m]);
-                if constexpr (DIM == 2) {
-                    cs[m] = __ldg(c + 2 * ps + q[m]);
-                    cn[m] = __ldg(c + 3 * ps + q[m]);
-                }
-                iv[m] = __ldg(c + NP * ps + q[m]);
-                if constexpr (RES) dpt[m] = __ldg(c + (NP + 1) * ps + q[m]);
-                g[m] = __ldg(f + q[m]) * iv[m];
-            }
-        }
-    }
+    const T v0 = ld_u(j, i);
+    const T hw = tx == 0 ? ld_u(j, i - 1) : (T)0;
+    const T he = tx == TX - 1 ? ld_u(j, i + 1) : (T)0;
     T hs = 0, hn = 0;
     if constexpr (DIM == 2) {
-        hs = ty == 0 ? ld_u(jm[0] - 1, i) : (T)0;
-        hn = ty == BY - 1 ? ld_u(jm[RPT - 1] + 1, i) : (T)0;
+        hs = ty == 0 ? ld_u(j - 1, i) : (T)0;
+        hn = ty == TY - 1 ? ld_u(j + 1, i) : (T)0;
     }
-#pragma unroll
-    for (int m = 0; m < RPT; ++m) {
-        buf0[me[m]] = v0[m];
-        buf1[me[m]] = v0[m];
-        if (tx == 0) { buf0[me[m] - 1] = hw[m]; buf1[me[m] - 1] = hw[m]; }
-        if (tx == TX - 1) { buf0[me[m] + 1] = he[m]; buf1[me[m] + 1] = he[m]; }
+    const long long q = (long long)j * ld + i;
+    const long long ps = a.vcs;
+    T cw = 0, ce = 0, cs = 0, cn = 0, g = 0, dpt = 0, iv = 0;
+    if (in) {
+        if constexpr (EXACT) {
+            const double *__restrict__ c = (const double *)a.vc;
+            cw = __ldg(c + q);
+            ce = __ldg(c + ps + q);
+            if constexpr (DIM == 2) {
+                cs = __ldg(c + 2 * ps + q);
+                cn = __ldg(c + 3 * ps + q);
+            }
+            // 1/d_p from the handle's plane (the same correctly rounded
+            // reciprocal of dconst + sigma_p): binary64 arithmetic is the
+            // scarce resource here, bytes are not
+            if constexpr (RES) dpt = a.vsig ? __dadd_rn(a.dconst, __ldg(a.vsig + q)) : a.dconst;
+            iv = a.dinv ? __ldg((const double *)a.dinv + q) : __drcp_rn(a.dconst);
+            g = __ldg(f + q);
+        } else {
+            const float *__restrict__ c = (const float *)a.vc;
+            constexpr int NP = DIM == 2 ? 4 : 2;   // planes before 1/d and d
+            cw = __ldg(c + q);
+            ce = __ldg(c + ps + q);
+            if constexpr (DIM == 2) {
+                cs = __ldg(c + 2 * ps + q);
+                cn = __ldg(c + 3 * ps + q);
+            }
+            iv = __ldg(c + NP * ps + q);
+            if constexpr (RES) dpt = __ldg(c + (NP + 1) * ps + q);
+            g = __ldg(f + q) * iv;
+        }
     }
+    buf0[me] = v0;
+    buf1[me] = v0;
+    if (tx == 0) { buf0[me - 1] = hw; buf1[me - 1] = hw; }
+    if (tx == TX - 1) { buf0[me + 1] = he; buf1[me + 1] = he; }
     if constexpr (DIM == 2) {
-        if (ty == 0) { buf0[me[0] - lw] = hs; buf1[me[0] - lw] = hs; }
-        if (ty == BY - 1) { buf0[me[RPT - 1] + lw] = hn; buf1[me[RPT - 1] + lw] = hn; }
+        if (ty == 0) { buf0[me - lw] = hs; buf1[me - lw] = hs; }
+        if (ty == TY - 1) { buf0[me + lw] = hn; buf1[me + lw] = hn; }
     }
     __syncthreads();
     typedef typename std::conditional<EXACT, double, T>::type Acc;
@@ -816,42 +799,37 @@ __global__ void __launch_bounds__(RPT > 1 ? 256 : 1024, RPT > 1 ? (sizeof(T) == 
     for (int s = 0; s < a.k; ++s) {
         const T *src = (s & 1) ? buf1 : buf0;
         T *dst = (s & 1) ? buf0 : buf1;
-#pragma unroll
-        for (int m = 0; m < RPT; ++m) {
-            if (!in[m]) continue;
-            const int e = me[m];
-            const T old = src[e], W = src[e - 1], E = src[e + 1];
-            const T Sv = DIM == 2 ? src[e - lw] : (T)0, Nv = DIM == 2 ? src[e + lw] : (T)0;
+        if (in) {
+            const T old = src[me], W = src[me - 1], E = src[me + 1];
+            const T Sv = DIM == 2 ? src[me - lw] : (T)0, Nv = DIM == 2 ? src[me + lw] : (T)0;
             T nv, res = 0;
             if constexpr (EXACT) {
-                double t = __dmul_rn(cw[m], W);
-                t = __dadd_rn(t, __dmul_rn(ce[m], E));
+                double t = __dmul_rn(cw, W);
+                t = __dadd_rn(t, __dmul_rn(ce, E));
                 if constexpr (DIM == 2) {
-                    t = __dadd_rn(t, __dmul_rn(cs[m], Sv));
-                    t = __dadd_rn(t, __dmul_rn(cn[m], Nv));
+                    t = __dadd_rn(t, __dmul_rn(cs, Sv));
+                    t = __dadd_rn(t, __dmul_rn(cn, Nv));
                 }
-                const double tt = __dsub_rn(g[m], t);
-                nv = __dmul_rn(tt, iv[m]);
-                if (RES && s == 0) res = __dsub_rn(tt, __dmul_rn(dpt[m], old));
+                const double tt = __dsub_rn(g, t);
+                nv = __dmul_rn(tt, iv);
+                if (RES && s == 0) res = __dsub_rn(tt, __dmul_rn(dpt, old));
             } else {
-                T t = g[m];
+                T t = g;
                 if constexpr (DIM == 2) {
-                    t = fma(cn[m], Nv, t);
-                    t = fma(cs[m], Sv, t);
+                    t = fma(cn, Nv, t);
+                    t = fma(cs, Sv, t);
                 }
-                t = fma(ce[m], E, t);
-                t = fma(cw[m], W, t);
+                t = fma(ce, E, t);
+                t = fma(cw, W, t);
                 nv = t;
-                if (RES && s == 0) res = (t - old) * dpt[m];
+                if (RES && s == 0) res = (t - old) * dpt;
             }
             if constexpr (RES) acc += (Acc)res * (Acc)res;
-            dst[e] = nv;
+            dst[me] = nv;
         }
         __syncthreads();
     }
-#pragma unroll
-    for (int m = 0; m < RPT; ++m)
-        if (in[m]) st_s<S, T>((S *)a.uout + q[m], ((a.k & 1) ? buf1 : buf0)[me[m]]);
+    if (in) st_s<S, T>((S *)a.uout + q, ((a.k & 1) ? buf1 : buf0)[me]);
     if constexpr (RES) reduce_grid_acc(a.red, acc);
 }
 
@@ -1053,6 +1031,5 @@ __global__ void __launch_bounds__(256) classic1d_kernel(const CycArgs a) {
       {hj::classic1d_kernel<S, T, EX, true, false>, hj::classic1d_kernel<S, T, EX, true, true>}},     \
      {{nullptr, nullptr}, {nullptr, nullptr}}}
 #define HJ_KVC(S, T, EX)                                                                              \
-    {{{hj::vc_kernel<S, T, 1, 1, EX, false>, hj::vc_kernel<S, T, 1, 1, EX, true>},                    \
-      {hj::vc_kernel<S, T, 2, 1, EX, false>, hj::vc_kernel<S, T, 2, 1, EX, true>}},                   \
-     {hj::vc_kernel<S, T, 2, 4, EX, false>, hj::vc_kernel<S, T, 2, 4, EX, true>}}
+    {{{hj::vc_kernel<S, T, 1, EX, false>, hj::vc_kernel<S, T, 1, EX, true>},                          \
+      {hj::vc_kernel<S, T, 2, EX, false>, hj::vc_kernel<S, T, 2, EX, true>}}}

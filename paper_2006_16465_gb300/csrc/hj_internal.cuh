@@ -404,8 +404,7 @@ struct TileKernelInfo {
 // Variable-coefficient kernels: [dim - 1][res], one thread per point, dynamic
 // shared memory 2 * (tile_x + 2) * (tile_y + 2) elements of the compute type.
 struct VcKernelInfo {
-    CycKernel fn[2][2];   // [dim - 1][res]: one point per thread
-    CycKernel fn4[2];     // [res]: 2D, four rows per thread (subdomain heights that are multiples of 4)
+    CycKernel fn[2][2];
 };
 const VcKernelInfo *vc_kernels_f64();
 const VcKernelInfo *vc_kernels_f32();
