@@ -17,8 +17,10 @@
 //     the two bands of a warp swap their edge rows by shuffle, and only the
 //     edge rows of each warp go through a ping-pong shared-memory buffer (one
 //     barrier per subiteration, none when NW = 1);
-//   * binary32 lanes with an even number of columns update them in packed
-//     pairs (fma.rn.f32x2), which gives the scalar results exactly;
+//   * binary32 lanes with an even number of columns update them partly in
+//     packed pairs (fma.rn.f32x2: two independent round-to-nearest operations)
+//     and fold the frozen halo's contribution into the right-hand-side term
+//     once per cycle, so their sweeps carry no halo selects;
 //   * the residual ||f - A u_c||^2 of the staged input is formed in the first
 //     subiteration (r_p = d_p (u'_p - u_p)) and reduced deterministically
 //     (warp butterfly, CTA, two-level grid) inside the same launch.
@@ -297,28 +299,6 @@ __device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsign
     return d;
 }
 
-// Two neighbouring points of one row (binary32 fast or per-point-d path), in
-// the scalar chain's order: point_update gives the same two values.
-template <bool SIG>
-__device__ __forceinline__ void point_update_pair(const Coef<float> &k, float g0, float g1, float iv0, float iv1,
-                                                  float W0, float W1, float E0, float E1, float S0, float S1,
-                                                  float N0, float N1, float &n0, float &n1) {
-    unsigned long long t = pk2(g0, g1);
-    if constexpr (SIG) {
-        t = ffma2(pk2(-k.cW, -k.cW), pk2(W0, W1), t);
-        t = ffma2(pk2(-k.cE, -k.cE), pk2(E0, E1), t);
-        t = ffma2(pk2(-k.cS, -k.cS), pk2(S0, S1), t);
-        t = ffma2(pk2(-k.cN, -k.cN), pk2(N0, N1), t);
-        t = fmul2(t, pk2(iv0, iv1));
-    } else {
-        t = ffma2(pk2(k.bN, k.bN), pk2(N0, N1), t);
-        t = ffma2(pk2(k.bS, k.bS), pk2(S0, S1), t);
-        t = ffma2(pk2(k.bE, k.bE), pk2(E0, E1), t);
-        t = ffma2(pk2(k.bW, k.bW), pk2(W0, W1), t);
-    }
-    upk2(t, n0, n1);
-}
-
 // k subiterations on registers.  Returns this thread's share of
 // ||f - A u_c||^2 (unscaled by d^2 on the fast constant-diagonal path).
 // Points a subdomain owns (overlapping subdomains write back and count in the
@@ -326,6 +306,170 @@ __device__ __forceinline__ void point_update_pair(const Coef<float> &k, float g0
 struct Own {
     int xlo, xhi, ylo, yhi;
 };
+
+// Binary32 path for lanes of an even number of columns (constant or per-point
+// diagonal, full tiles), with the frozen halo folded into the right-hand-side
+// term.  Within a cycle the halo of a subdomain does not change, so its
+// weighted contribution to the updates along the subdomain's edge is a
+// constant: it is added to g once, before the first subiteration, and the
+// edge lanes then weight what they receive by shuffle (a point of another row,
+// or their own) with a zero coefficient.  No halo select is left in the sweeps.
+// A point update is the sum g + kW W + kE E + kS S + kN N (times 1/d_p on the
+// per-point path) taken in a fixed order: the two horizontal neighbours first
+// (E then W in even columns of the subdomain, W then E in odd ones), then S,
+// then N; the last two steps are packed pairs (fma.rn.f32x2: two independent
+// round-to-nearest operations) whose results are the next pair of iterate
+// registers.  The order depends only on the point's place in the subdomain, so
+// every lane layout of a subdomain (two columns per lane in two bands, four in
+// four bands, one to eight warps) gives the same values bit for bit.  Per row
+// and lane of two columns: two shuffles, two scalar and three packed
+// multiply-adds.
+template <int C, int R, int NW, int H, bool SIG, bool RES, bool OVL>
+__device__ __forceinline__ float sweeps2d_fold(Tile2D<float, C, R, SIG> &t, const Coef<float> &kc, const int k,
+                                               const int x0, const int yb, float *xbuf, const Own own,
+                                               DbgWord *dbg) {
+    (void)dbg; (void)own; (void)x0; (void)yb;
+    static_assert(C % 2 == 0, "packed pairs of columns");
+    constexpr int L = 32 / H, TX = L * C;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int li = lane % L, hb = lane / L, band = w * H + hb;
+    const int xl = x0 + li * C;
+    // neighbour weights: -c_X / d (constant diagonal) or -c_X (per-point 1/d, applied last)
+    const float kW = SIG ? -kc.cW : kc.bW, kE = SIG ? -kc.cE : kc.bE;
+    const float kS = SIG ? -kc.cS : kc.bS, kN = SIG ? -kc.cN : kc.bN;
+    const bool wl = li == 0, el = li == L - 1, tb = band == 0, bb = band == NW * H - 1;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        t.g[r][0] = fmaf(wl ? kW : 0.f, t.hx[r], t.g[r][0]);
+        t.g[r][C - 1] = fmaf(el ? kE : 0.f, t.hx[r], t.g[r][C - 1]);
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        t.g[0][c] = fmaf(tb ? kS : 0.f, t.top[c], t.g[0][c]);
+        t.g[R - 1][c] = fmaf(bb ? kN : 0.f, t.bot[c], t.g[R - 1][c]);
+    }
+    // weights of the shuffled W / E values and of the band's outer rows
+    const float kWs = wl ? 0.f : kW, kEs = el ? 0.f : kE;
+    const float kS0 = tb ? 0.f : kS, kNR = bb ? 0.f : kN;
+    const unsigned long long kS2 = pk2(kS, kS), kN2 = pk2(kN, kN), kS02 = pk2(kS0, kS0), kNR2 = pk2(kNR, kNR);
+    const unsigned long long kWE = pk2(kWs, kEs);
+    const unsigned m_top = lane_mask(hb > 0);
+    float acc = 0.f;
+    auto sweep = [&](auto first_tag) {
+        constexpr bool FIRST = decltype(first_tag)::value;
+        float prev[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) prev[c] = t.top[c];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float cur[C], a[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) cur[c] = t.v[r][c];
+            const float sW = __shfl_up_sync(FULL, cur[C - 1], 1);
+            const float sE = __shfl_down_sync(FULL, cur[0], 1);
+            const unsigned long long cN2 = (r == R - 1) ? kNR2 : kN2, cS2 = (r == 0) ? kS02 : kS2;
+            // horizontal neighbours: even column E then W, odd column W then E
+            if constexpr (C == 2) {
+                a[0] = fmaf(kE, cur[1], t.g[r][0]);
+                a[1] = fmaf(kW, cur[0], t.g[r][1]);
+                upk2(ffma2(kWE, pk2(sW, sE), pk2(a[0], a[1])), a[0], a[1]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < C; c += 2) {
+                    a[c] = fmaf(kE, cur[c + 1], t.g[r][c]);
+                    a[c] = (c == 0) ? fmaf(kWs, sW, a[c]) : fmaf(kW, cur[c > 0 ? c - 1 : 0], a[c]);
+                    a[c + 1] = fmaf(kW, cur[c], t.g[r][c + 1]);
+                    a[c + 1] = (c + 2 == C) ? fmaf(kEs, sE, a[c + 1]) : fmaf(kE, cur[c + 2 < C ? c + 2 : 0], a[c + 1]);
+                }
+            }
+            // then S and N as packed pairs
+#pragma unroll
+            for (int c = 0; c < C; c += 2) {
+                const float N0 = (r == R - 1) ? t.bot[c] : t.v[r < R - 1 ? r + 1 : 0][c];
+                const float N1 = (r == R - 1) ? t.bot[c + 1] : t.v[r < R - 1 ? r + 1 : 0][c + 1];
+                unsigned long long p = ffma2(cS2, pk2(prev[c], prev[c + 1]), pk2(a[c], a[c + 1]));
+                p = ffma2(cN2, pk2(N0, N1), p);
+                upk2(p, a[c], a[c + 1]);
+            }
+            if constexpr (SIG) {
+#pragma unroll
+                for (int c = 0; c < C; c += 2)
+                    upk2(fmul2(pk2(a[c], a[c + 1]), pk2(t.dv[SIG ? r : 0][SIG ? c : 0], t.dv[SIG ? r : 0][SIG ? c + 1 : 0])),
+                         a[c], a[c + 1]);
+            }
+            if constexpr (FIRST && RES) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    float rc = a[c] - cur[c];
+                    if constexpr (SIG) rc = rc * (1.f / t.dv[SIG ? r : 0][SIG ? c : 0]);
+                    if constexpr (OVL) {
+                        if (!(yb + r >= own.ylo && yb + r <= own.yhi && xl + c >= own.xlo && xl + c <= own.xhi))
+                            rc = 0.f;
+                    }
+                    acc += rc * rc;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                t.v[r][c] = a[c];
+                prev[c] = cur[c];
+            }
+        }
+    };
+    int par = 0;
+    // the rows next to each band become the neighbouring bands' values of the
+    // previous subiteration; the frozen edges of the subdomain carry zero
+    // weights, so what lands there does not matter
+    auto exchange = [&]() {
+        if constexpr (H == 2) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float recv = __shfl_xor_sync(FULL, mask_sel(m_top, t.v[0][c], t.v[R - 1][c]), 16);
+                t.top[c] = recv;
+                t.bot[c] = recv;
+            }
+        } else if constexpr (H == 4) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                t.top[c] = __shfl_up_sync(FULL, t.v[R - 1][c], L);
+                t.bot[c] = __shfl_down_sync(FULL, t.v[0][c], L);
+            }
+        }
+        if constexpr (NW > 1) {
+            constexpr int NX = 2 * NW * 2 * TX;
+            const int o = par * (NW * 2 * TX);
+            float *buf = xbuf + o;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int i0 = (w * 2 + 0) * TX + li * C + c, i1 = (w * 2 + 1) * TX + li * C + c;
+                if (hb == 0 && HJ_IN(dbg, o + i0, NX, 16)) buf[i0] = t.v[0][c];
+                if (hb == H - 1 && HJ_IN(dbg, o + i1, NX, 16)) buf[i1] = t.v[R - 1][c];
+            }
+            __syncthreads();
+            if (w > 0 && hb == 0) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const int i = ((w - 1) * 2 + 1) * TX + li * C + c;
+                    if (HJ_IN(dbg, o + i, NX, 17)) t.top[c] = buf[i];
+                }
+            }
+            if (w < NW - 1 && hb == H - 1) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const int i = ((w + 1) * 2 + 0) * TX + li * C + c;
+                    if (HJ_IN(dbg, o + i, NX, 17)) t.bot[c] = buf[i];
+                }
+            }
+            par ^= 1;
+        }
+    };
+    sweep(std::integral_constant<bool, true>());
+    for (int s = 1; s < k; ++s) {
+        exchange();
+        sweep(std::integral_constant<bool, false>());
+    }
+    return acc;
+}
 
 template <typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool RES, bool PART, bool OVL = false>
 __device__ __forceinline__ typename std::conditional<EXACT, double, T>::type
@@ -335,6 +479,9 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
     static_assert(H == 1 || H == 2 || H == 4, "one, two or four bands per warp");
     constexpr int L = 32 / H, TX = L * C;
     constexpr bool PACK = std::is_same<T, float>::value && !EXACT && (C % 2 == 0) && !PART;
+    if constexpr (PACK) {
+        return sweeps2d_fold<C, R, NW, H, SIG, RES, OVL>(t, kc, k, x0, yb, xbuf, own, dbg);
+    } else {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int li = lane % L, hb = lane / L;
     const int xl = x0 + li * C;
@@ -354,38 +501,7 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
             for (int c = 0; c < C; ++c) cur[c] = t.v[r][c];
             const T left = mask_sel(m_first, t.hx[r], __shfl_up_sync(FULL, cur[C - 1], 1));
             const T right = mask_sel(m_last, t.hx[r], __shfl_down_sync(FULL, cur[0], 1));
-            if constexpr (PACK) {
-#pragma unroll
-                for (int c = 0; c < C; c += 2) {
-                    const T W0 = (c == 0) ? left : cur[c > 0 ? c - 1 : 0];
-                    const T E1 = (c + 2 == C) ? right : cur[c + 2 < C ? c + 2 : 0];
-                    const T N0 = (r == R - 1) ? t.bot[c] : t.v[r < R - 1 ? r + 1 : 0][c];
-                    const T N1 = (r == R - 1) ? t.bot[c + 1] : t.v[r < R - 1 ? r + 1 : 0][c + 1];
-                    T n0, n1;
-                    point_update_pair<SIG>(kc, t.g[r][c], t.g[r][c + 1], SIG ? t.dv[SIG ? r : 0][SIG ? c : 0] : 0.f,
-                                           SIG ? t.dv[SIG ? r : 0][SIG ? c + 1 : 0] : 0.f, W0, cur[c], cur[c + 1],
-                                           E1, prev[c], prev[c + 1], N0, N1, n0, n1);
-                    if constexpr (FIRST && RES) {
-                        T r0, r1;
-                        if constexpr (SIG) {
-                            r0 = (n0 - cur[c]) * ((T)1 / t.dv[SIG ? r : 0][SIG ? c : 0]);
-                            r1 = (n1 - cur[c + 1]) * ((T)1 / t.dv[SIG ? r : 0][SIG ? c + 1 : 0]);
-                        } else {
-                            r0 = n0 - cur[c];
-                            r1 = n1 - cur[c + 1];
-                        }
-                        if constexpr (OVL) {
-                            const bool orow = yb + r >= own.ylo && yb + r <= own.yhi;
-                            if (!(orow && xl + c >= own.xlo && xl + c <= own.xhi)) r0 = 0;
-                            if (!(orow && xl + c + 1 >= own.xlo && xl + c + 1 <= own.xhi)) r1 = 0;
-                        }
-                        acc += (Acc)r0 * (Acc)r0;
-                        acc += (Acc)r1 * (Acc)r1;
-                    }
-                    t.v[r][c] = n0;
-                    t.v[r][c + 1] = n1;
-                }
-            } else {
+            {
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     const T W = (c == 0) ? left : cur[c > 0 ? c - 1 : 0];
@@ -471,6 +587,7 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
         sweep(std::integral_constant<bool, false>());
     }
     return acc;
+    }
 }
 
 // Write the band's interior points into u_{c+1}.
