@@ -1,7 +1,9 @@
 // hj_cycle3d.cu -- registries of the 3D seven-point kernels (hj_cycle3d.cuh).
 //
 // Shapes: LX lanes along x, 32 / LX lane groups along y with RY rows each,
-// RZ planes per lane, four warps (four subdomains) per CTA.
+// RZ planes per lane, four warps (four subdomains) per CTA.  Binary32 runs the
+// same shapes with two columns per lane (LX / 2 lanes along x, RY / 2 rows
+// per lane group); its prefetching variant keeps one column per lane.
 //   binary32: 16 x 8 x 8 (default), 32 x 4 x 8, 8 x 8 x 8, 16 x 8 x 4, 32 x 8 x 4
 //   binary64: 16 x 4 x 8 (default), 8 x 8 x 8, 32 x 2 x 8, 16 x 8 x 4
 #include "hj_cycle3d.cuh"
@@ -10,11 +12,11 @@ namespace hj {
 
 namespace {
 const Tile3Info k3_f32[] = {
-    HJ_K3D(float, float, 16, 4, 8, 4, false),
-    HJ_K3D(float, float, 32, 4, 8, 4, false),
-    HJ_K3D(float, float, 8, 2, 8, 4, false),
-    HJ_K3D(float, float, 16, 4, 4, 4, false),
-    HJ_K3D(float, float, 32, 8, 4, 4, false),
+    HJ_K3D_F32(16, 4, 8, 4),
+    HJ_K3D_F32(32, 4, 8, 4),
+    HJ_K3D_F32(8, 2, 8, 4),
+    HJ_K3D_F32(16, 4, 4, 4),
+    HJ_K3D_F32(32, 8, 4, 4),
 };
 const Tile3Info k3_f64[] = {
     HJ_K3D(double, double, 16, 2, 8, 4, true),

@@ -228,6 +228,211 @@ __global__ void __launch_bounds__(32 * NW) hier3d_kernel(const CycArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Binary32 variant with two x columns per lane (LX lanes span TX = 2 LX
+// columns, LY = 32 / LX lane groups span y with RY rows each, RZ planes per
+// lane): half the x shuffles of the one-column kernel, and the frozen halo
+// folded into the right-hand-side term once per cycle, as in the 2D binary32
+// sweeps.  Within a cycle the halo does not change, so its weighted
+// contribution to the updates next to the subdomain's faces is added to
+// g = f/d before the first subiteration; the lanes on an x or y face then
+// weight what they receive by shuffle (their own value) with zero, and the
+// first and last planes drop their B and T terms.  A point update is
+// g + bW W + bE E + bS S + bN N + bB B + bT T in the order: the horizontal
+// pair (E then W in even columns of the subdomain, W then E in odd ones), then
+// S, N, B, T as packed pairs (fma.rn.f32x2, two independent round-to-nearest
+// operations).  Per pair of points: two x shuffles, two scalar and five packed
+// multiply-adds.
+// ---------------------------------------------------------------------------
+template <int LX, int RY, int RZ, int NW, bool RES>
+__global__ void __launch_bounds__(32 * NW, 3) hier3d_pk_kernel(const CycArgs a) {
+    constexpr int LY = 32 / LX, TX = 2 * LX, TY = LY * RY, TZ = RZ;
+    constexpr unsigned FULL = 0xffffffffu;
+    static_assert(LX == 4 || LX == 8 || LX == 16, "LX lanes of two columns per x segment");
+    if constexpr (RES) {
+        if (*(volatile int *)&a.red.ctl->done >= 0) return;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lx = lane % LX, gy = lane / LX;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int nbx = (nx + TX - 1) / TX, nby = (ny + TY - 1) / TY, nbz = (nz + TZ - 1) / TZ;
+    const long long nsub = (long long)nbx * nby * nbz;
+    const long long sub = (long long)blockIdx.x * NW + warp;
+    float acc = 0.f;
+    if (sub < nsub) {   // warp-uniform
+        const int bx = (int)(sub % nbx);
+        const int by = (int)((sub / nbx) % nby);
+        const int bz = (int)(sub / ((long long)nbx * nby));
+        const int x0 = 1 + bx * TX, y0 = 1 + by * TY, z0 = 1 + bz * TZ;
+        const int x = x0 + 2 * lx, yl = y0 + gy * RY;   // this lane's first column and first row
+        const long long ld = a.ld, ps = a.ps;
+        const float *__restrict__ uin = (const float *)a.uin;
+        const float *__restrict__ f = (const float *)a.f;
+        const Coef3<float> kc = make_coef3<float>(a);
+        const bool full = x0 + TX - 1 <= nx && y0 + TY - 1 <= ny && z0 + TZ - 1 <= nz;   // warp-uniform
+        const bool wl = lx == 0, el = lx == LX - 1, sl = gy == 0, nl = gy == LY - 1;
+        // iterate and f/d of the lane's points, with the halo folded into g.
+        // A subdomain inside the grid loads from one base pointer at fixed
+        // offsets; a ragged one checks every load: points beyond the grid read
+        // the ghost value (x, y or z = n + 1) or zero, and keep it.
+        float u[RY][RZ][2], g[RY][RZ][2];
+        auto stage = [&](auto part_tag) {
+            constexpr bool PART = decltype(part_tag)::value;
+            const long long o = (long long)z0 * ps + (long long)yl * ld + x;
+            const float *bu = uin + o, *bf = f + o;
+            // offset (dx, row dy, plane dz) from this lane's first point; inside
+            // the grid every such address within one point of the subdomain is
+            // in the ghost shell, so the loads need no lane conditions and all
+            // of them are in flight before the first use
+            auto ldu = [&](int dx, int dy, int dz) -> float {
+                if constexpr (PART) {
+                    if (x + dx > nx + 1 || yl + dy > ny + 1 || z0 + dz > nz + 1) return 0.f;
+                }
+                return ld_s<float, float>(bu + (long long)dz * ps + (long long)dy * ld + dx);
+            };
+            const int xo = wl ? -1 : 2;   // x-halo column: W on the first lane of a segment, else E
+            float xh[RY][RZ], hs[RZ][2], hn[RZ][2], hb[RY][2], ht[RY][2];
+#pragma unroll
+            for (int z = 0; z < RZ; ++z) {
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        u[r][z][c] = ldu(c, r, z);
+                        const bool in = !PART || (x + c <= nx && yl + r <= ny && z0 + z <= nz);
+                        g[r][z][c] = in ? __ldg(bf + (long long)z * ps + (long long)r * ld + c) : 0.f;
+                    }
+                    xh[r][z] = ldu(xo, r, z);
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    hs[z][c] = ldu(c, -1, z);
+                    hn[z][c] = ldu(c, RY, z);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    hb[r][c] = ldu(c, r, -1);
+                    ht[r][c] = ldu(c, r, TZ);
+                }
+            }
+            // g = f/d plus the weighted frozen halo: x faces (the first lane of a
+            // segment holds W, the last E), y faces (first and last lane
+            // groups), z faces
+#pragma unroll
+            for (int z = 0; z < RZ; ++z) {
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) g[r][z][c] *= kc.invd;
+                    g[r][z][0] = fmaf(wl ? kc.bW : 0.f, xh[r][z], g[r][z][0]);
+                    g[r][z][1] = fmaf(el ? kc.bE : 0.f, xh[r][z], g[r][z][1]);
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    g[0][z][c] = fmaf(sl ? kc.bS : 0.f, hs[z][c], g[0][z][c]);
+                    g[RY - 1][z][c] = fmaf(nl ? kc.bN : 0.f, hn[z][c], g[RY - 1][z][c]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    g[r][0][c] = fmaf(kc.bB, hb[r][c], g[r][0][c]);
+                    g[r][RZ - 1][c] = fmaf(kc.bT, ht[r][c], g[r][RZ - 1][c]);
+                }
+            }
+        };
+        if (full) stage(std::integral_constant<bool, false>());
+        else stage(std::integral_constant<bool, true>());
+        const unsigned long long kWE = pk2(wl ? 0.f : kc.bW, el ? 0.f : kc.bE);
+        const unsigned long long kS2 = pk2(kc.bS, kc.bS), kN2 = pk2(kc.bN, kc.bN);
+        const unsigned long long kS02 = pk2(sl ? 0.f : kc.bS, sl ? 0.f : kc.bS);
+        const unsigned long long kNl2 = pk2(nl ? 0.f : kc.bN, nl ? 0.f : kc.bN);
+        const unsigned long long kB2 = pk2(kc.bB, kc.bB), kT2 = pk2(kc.bT, kc.bT);
+        auto sweeps = [&](auto part_tag) {
+            constexpr bool PART = decltype(part_tag)::value;
+#pragma unroll 1
+            for (int s = 0; s < a.k; ++s) {
+                float prev[RY][2];   // old values of the plane below
+#pragma unroll
+                for (int z = 0; z < RZ; ++z) {
+                    float up[2] = {0.f, 0.f}, dn[2] = {0.f, 0.f};
+                    if constexpr (LY > 1) {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            up[c] = __shfl_up_sync(FULL, u[RY - 1][z][c], LX);
+                            dn[c] = __shfl_down_sync(FULL, u[0][z][c], LX);
+                        }
+                    }
+                    float nv[RY][2];
+#pragma unroll
+                    for (int r = 0; r < RY; ++r) {
+                        const float c0 = u[r][z][0], c1 = u[r][z][1];
+                        const float sW = __shfl_up_sync(FULL, c1, 1, LX);
+                        const float sE = __shfl_down_sync(FULL, c0, 1, LX);
+                        float a0 = fmaf(kc.bE, c1, g[r][z][0]);
+                        float a1 = fmaf(kc.bW, c0, g[r][z][1]);
+                        unsigned long long p = ffma2(kWE, pk2(sW, sE), pk2(a0, a1));
+                        if (r > 0) p = ffma2(kS2, pk2(u[r > 0 ? r - 1 : 0][z][0], u[r > 0 ? r - 1 : 0][z][1]), p);
+                        else if (LY > 1) p = ffma2(kS02, pk2(up[0], up[1]), p);
+                        if (r < RY - 1)
+                            p = ffma2(kN2, pk2(u[r < RY - 1 ? r + 1 : 0][z][0], u[r < RY - 1 ? r + 1 : 0][z][1]), p);
+                        else if (LY > 1) p = ffma2(kNl2, pk2(dn[0], dn[1]), p);
+                        if (z > 0) p = ffma2(kB2, pk2(prev[r][0], prev[r][1]), p);
+                        if (z < RZ - 1)
+                            p = ffma2(kT2, pk2(u[r][z < RZ - 1 ? z + 1 : 0][0], u[r][z < RZ - 1 ? z + 1 : 0][1]), p);
+                        float n0, n1;
+                        upk2(p, n0, n1);
+                        bool in0 = true, in1 = true;
+                        if constexpr (PART) {
+                            const bool iyz = yl + r <= ny && z0 + z <= nz;
+                            in0 = iyz && x <= nx;
+                            in1 = iyz && x + 1 <= nx;
+                            n0 = in0 ? n0 : c0;
+                            n1 = in1 ? n1 : c1;
+                        }
+                        if constexpr (RES) {
+                            if (s == 0) {
+                                const float r0 = in0 ? n0 - c0 : 0.f, r1 = in1 ? n1 - c1 : 0.f;
+                                acc += r0 * r0;
+                                acc += r1 * r1;
+                            }
+                        }
+                        nv[r][0] = n0;
+                        nv[r][1] = n1;
+                    }
+#pragma unroll
+                    for (int r = 0; r < RY; ++r) {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            prev[r][c] = u[r][z][c];
+                            u[r][z][c] = nv[r][c];
+                        }
+                    }
+                }
+            }
+        };
+        if (full) sweeps(std::integral_constant<bool, false>());
+        else sweeps(std::integral_constant<bool, true>());
+        // write back this lane's interior points
+        float *uo = (float *)a.uout;
+#pragma unroll
+        for (int z = 0; z < RZ; ++z)
+#pragma unroll
+            for (int r = 0; r < RY; ++r)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int yy = yl + r, zz = z0 + z;
+                    if (full || (x + c <= nx && yy <= ny && zz <= nz))
+                        uo[(long long)zz * ps + (long long)yy * ld + x + c] = u[r][z][c];
+                }
+    }
+    if constexpr (RES) reduce_grid_acc(a.red, acc);
+}
+
+// ---------------------------------------------------------------------------
 // Prefetching variant: persistent warps walk subdomains (warp g takes
 // g, g + G, g + 2G, ... for G warps in the grid), and while a warp sweeps one
 // subdomain in registers, cp.async copies the next one's box (subdomain +
@@ -466,3 +671,13 @@ __global__ void __launch_bounds__(256) classic3d_kernel(const CycArgs a) {
      {hj::hier3d_pf_kernel<S, T, LX, RY, RZ, NW, EX, false>,                                         \
       hj::hier3d_pf_kernel<S, T, LX, RY, RZ, NW, EX, true>},                                         \
      (int)((NW) * hj::Pf3Layout<T, LX, RY, RZ>::PER_WARP * sizeof(T))}
+
+// binary32 entry of the same TX x TY x TZ shape: the two-column kernel, whose
+// LX / 2 lanes span x with RY / 2 rows per lane group, and the one-column
+// prefetching kernel
+#define HJ_K3D_F32(LX, RY, RZ, NW)                                                                   \
+    {(LX), (32 / (LX)) * (RY), (RZ), 32 * (NW), (NW),                                               \
+     {hj::hier3d_pk_kernel<(LX) / 2, (RY) / 2, RZ, NW, false>, hj::hier3d_pk_kernel<(LX) / 2, (RY) / 2, RZ, NW, true>}, \
+     {hj::hier3d_pf_kernel<float, float, LX, RY, RZ, NW, false, false>,                              \
+      hj::hier3d_pf_kernel<float, float, LX, RY, RZ, NW, false, true>},                              \
+     (int)((NW) * hj::Pf3Layout<float, LX, RY, RZ>::PER_WARP * sizeof(float))}
