@@ -1019,6 +1019,7 @@ void hj_destroy(hj_handle *h) {
     if (!h) return;
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     if (h->mg_exec) cudaGraphExecDestroy(h->mg_exec);
+    if (h->mg_exec_fixed) cudaGraphExecDestroy(h->mg_exec_fixed);
     if (h->mg_arena) dfree(h->mg_arena);
     void *dev[] = {h->ubuf, h->ubuf2, h->dC, h->vcf, h->dinv_outer, h->dinv32, h->r32, h->dA, h->dB, h->hf, h->hu, h->partials, h->gpart,
                    h->hist, h->rstore, h->gcnt, h->fcnt, h->ctl, h->pscratch, h->barena, h->rs, h->bmeta};

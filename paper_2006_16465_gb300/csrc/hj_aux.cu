@@ -26,6 +26,23 @@ __device__ __forceinline__ double resid_exact(double f, double d, double u, doub
     return r;
 }
 
+// Binary32 -> binary64 by integer operations: the conversion instruction runs
+// on this part's narrow FP64 pipe, which the residual's multiply-adds already
+// saturate.  A normal binary32 value becomes the binary64 value with the same
+// sign, the exponent re-biased (127 -> 1023) and the 23 fraction bits at the
+// top of the 52 (exact, like the conversion); zeros keep their sign; subnormal,
+// infinite and NaN inputs (rare) take the conversion instruction.
+__device__ __forceinline__ double f32_to_f64(float x) {
+    const unsigned b = __float_as_uint(x), a = b & 0x7fffffffu;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    if (a - 0x00800000u < 0x7f000000u)   // exponent field in [1, 254]
+        return __longlong_as_double((long long)(sign | ((unsigned long long)a + (896ull << 23)) << 29));
+    if (a == 0) return __longlong_as_double((long long)sign);
+    return (double)x;
+}
+template <typename T> __device__ __forceinline__ double to_f64(T x) { return (double)x; }
+template <> __device__ __forceinline__ double to_f64<float>(float x) { return f32_to_f64(x); }
+
 struct AuxArgs {
     const void *f;        // user dtype
     const void *u;        // user dtype
@@ -76,7 +93,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const AuxArgs a) {
         if (!AuxGeom<D>::idx(a.nx, a.ny, b, i, j)) continue;
         const T *u = (const T *)a.u;
         const long long q = (long long)j * a.ld + i;
-        const double fv = (double)((const T *)a.f)[q];
+        const double fv = to_f64<T>(((const T *)a.f)[q]);
         const double d = a.sigma ? __dadd_rn(a.dconst, a.sigma[q]) : a.dconst;
         double cW = a.cW, cE = a.cE, cS = a.cS, cN = a.cN;
         if (a.coef) {
@@ -87,9 +104,9 @@ __global__ void __launch_bounds__(256) residual_kernel(const AuxArgs a) {
                 cN = a.coef[3 * a.cps + q];
             }
         }
-        const double r = resid_exact<D == 2>(fv, d, (double)u[q], (double)u[q - 1], (double)u[q + 1],
-                                             D == 2 ? (double)u[q - a.ld] : 0.0,
-                                             D == 2 ? (double)u[q + a.ld] : 0.0, cW, cE, cS, cN);
+        const double r = resid_exact<D == 2>(fv, d, to_f64<T>(u[q]), to_f64<T>(u[q - 1]), to_f64<T>(u[q + 1]),
+                                             D == 2 ? to_f64<T>(u[q - a.ld]) : 0.0,
+                                             D == 2 ? to_f64<T>(u[q + a.ld]) : 0.0, cW, cE, cS, cN);
         rr += r * r;
         ff += fv * fv;
         if (a.r32) a.r32[(long long)j * a.ld2 + i] = (float)r;
@@ -124,10 +141,10 @@ __global__ void __launch_bounds__(256) vc_prep_kernel(const double *coef, const 
 }
 
 template <typename DS>
-__device__ __forceinline__ double ld_corr(const DS *p) { return (double)__ldg(p); }
+__device__ __forceinline__ double ld_corr(const DS *p) { return f32_to_f64(__ldg(p)); }
 template <>
 __device__ __forceinline__ double ld_corr<__nv_bfloat16>(const __nv_bfloat16 *p) {
-    return (double)__bfloat162float(__ldg(p));
+    return f32_to_f64(__bfloat162float(__ldg(p)));
 }
 
 // u_out = u_in + d on interior points, and r = f - A u_out (binary64) with its
@@ -304,14 +321,14 @@ __global__ void __launch_bounds__(256) residual3d_kernel(const T *f, const T *u,
         const int z = 1 + (int)(b / ((long long)bxn * byn));
         if (i > nx || j > ny) continue;
         const long long q = (long long)z * ps + (long long)j * ld + i;
-        const double fv = (double)f[q];
-        double r = fma(-dconst, (double)u[q], fv);
-        r = fma(-cW, (double)u[q - 1], r);
-        r = fma(-cE, (double)u[q + 1], r);
-        r = fma(-cS, (double)u[q - ld], r);
-        r = fma(-cN, (double)u[q + ld], r);
-        r = fma(-cB, (double)u[q - ps], r);
-        r = fma(-cT, (double)u[q + ps], r);
+        const double fv = to_f64<T>(f[q]);
+        double r = fma(-dconst, to_f64<T>(u[q]), fv);
+        r = fma(-cW, to_f64<T>(u[q - 1]), r);
+        r = fma(-cE, to_f64<T>(u[q + 1]), r);
+        r = fma(-cS, to_f64<T>(u[q - ld]), r);
+        r = fma(-cN, to_f64<T>(u[q + ld]), r);
+        r = fma(-cB, to_f64<T>(u[q - ps]), r);
+        r = fma(-cT, to_f64<T>(u[q + ps]), r);
         rr += r * r;
         ff += fv * fv;
     }

@@ -120,7 +120,8 @@ struct hj_handle {
     // multigrid (HJ_METHOD_MG): levels, their buffers and the V-cycle graph
     std::vector<hj::MgLevel> mg;
     void *mg_arena = nullptr;
-    cudaGraphExec_t mg_exec = nullptr;
+    cudaGraphExec_t mg_exec = nullptr;         // V-cycle + level-0 residual (converging runs)
+    cudaGraphExec_t mg_exec_fixed = nullptr;   // V-cycle alone (fixed-cycle runs)
 };
 
 namespace hj {

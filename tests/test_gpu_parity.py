@@ -298,6 +298,33 @@ def test_residual_api_matches_oracle():
         s.close()
 
 
+def test_f32_residual_is_the_binary64_residual_of_the_stored_values():
+    """Binary32 grids: the residual is formed in binary64 from the exact
+    binary64 values of the stored binary32 numbers (converted by integer
+    operations on the GPU, by the instruction for subnormals), so it equals
+    the oracle's binary64 residual of the upcast arrays.  The grids carry
+    signed zeros, subnormals and large values in the iterate, the RHS and the
+    boundary ring (2D with a sigma field, 1D, 3D)."""
+    torch = _torch()
+    rng = np.random.default_rng(17)
+    cases = [(2, W.random_bc_problem(2, 77, 53, seed=6, sigma_kind="field", asym=True), 77),
+             (1, W.random_bc_problem(1, 301, 2, seed=7, sigma_kind="const", asym=True), 301),
+             (3, W.random_bc_problem3d(23, 17, 11, seed=8, sigma_kind="const", asym=True), 23)]
+    specials = np.array([0.0, -0.0, 1e-40, -3e-42, 1.4e-45, 3.0e38, -2.5e37, 1.17549435e-38], np.float32)
+    for dim, p, nx in cases:
+        f32 = p.f.astype(np.float32)
+        u32 = p.u0.astype(np.float32)
+        for a in (f32, u32):
+            flat = a.reshape(-1)
+            idx = rng.choice(flat.size, size=min(40, flat.size // 4), replace=False)
+            flat[idx] = specials[rng.integers(0, specials.size, idx.size)]
+        s = gpu_solver(p, precision="f32")
+        got, _ = s.residual(to_dev(f32, dim, torch.float32), to_dev(u32, dim, torch.float32))
+        ref = oracle.residual(p.st, f32.astype(np.float64), u32.astype(np.float64))
+        assert np.isfinite(ref) and got == pytest.approx(ref, rel=1e-12), (dim, got, ref)
+        s.close()
+
+
 # ---------------------------------------------------------------------------
 # binary32 cycles
 # ---------------------------------------------------------------------------
