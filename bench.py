@@ -982,7 +982,8 @@ def main():
                     help="also time the paper's Section 3.5 / 4.2 problems (binary64, minutes)")
     ap.add_argument("--only", default="", choices=["", "variable_coefficients", "three_d", "multigrid",
                                                     "time_to_residual", "cfg2_k_sweep", "cfg3_precision",
-                                                    "fd_check", "cpu_baseline", "classic"],
+                                                    "fd_check", "cpu_baseline", "classic", "batched",
+                                                    "differentiation"],
                     help="run one extras section alone and print its JSON (profiling runs)")
     ap.add_argument("--fd-n", type=int, default=1024, help="grid side of the finite-difference check")
     ap.add_argument("--fd-entries", type=int, default=32, help="sigma entries the finite-difference check perturbs")
@@ -1006,7 +1007,9 @@ def main():
                    "cfg3_precision": lambda: cfg3_precision(torch, hj, W),
                    "fd_check": lambda: fd_check(torch, hj, W, n=args.fd_n, entries=args.fd_entries),
                    "cpu_baseline": lambda: cpu_baseline(args.k),
-                   "classic": lambda: classic_rate(torch, hj, args.n)}
+                   "classic": lambda: classic_rate(torch, hj, args.n),
+                   "batched": lambda: time_batched(torch, hj, W),
+                   "differentiation": lambda: time_differentiation(torch, hj, W)}
         print(json.dumps({args.only: section[args.only]()}), flush=True)
         return 0
 

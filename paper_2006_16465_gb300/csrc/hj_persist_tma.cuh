@@ -34,8 +34,14 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 
 // ONE: single problem (one barrier per cycle, every CTA reduces all partials
 // itself, as persist2d_one_kernel); else many problems (reduce, then retire).
+// Batched four-warp kernels with a sigma field are held to three CTAs per SM
+// (at most 168 registers instead of about 220): measured 3.5 % faster on 16
+// 1024^2 sigma-field problems.  The others keep the compiler's choice (a
+// minimum of 0 CTAs leaves it as without one; an explicit 1 let the compiler
+// take more registers, and the constant-sigma batched kernel held to three
+// CTAs was slower).
 template <typename S, typename T, int C, int R, int NW, int H, bool EXACT, bool SIG, bool ONE>
-__global__ void __launch_bounds__(32 * NW) persist2d_tma_kernel(const PersistArgs P) {
+__global__ void __launch_bounds__(32 * NW, (NW == 4 && SIG && !ONE) ? 3 : 0) persist2d_tma_kernel(const PersistArgs P) {
     using L = PpcLayout<S, T, C, R, NW, H, SIG, 1>;
     constexpr int TX = L::TX, TY = L::TY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
