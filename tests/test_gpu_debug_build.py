@@ -40,6 +40,20 @@ def test_debug_build_catches_what_it_checks(debug_env):
     assert clean[1:3] == ["0", "0"], r.stdout
 
 
+def test_3d_and_multigrid_suites_pass_the_debug_checks(debug_env):
+    """The 3D kernels (binary64 one column per lane, binary32 two columns per
+    lane with the halo folded into f/d, the prefetching variant) and the
+    multigrid V-cycles (smoothing launches that form the coarse RHS or stage
+    the prolongation themselves) under the guard bands of every device
+    allocation, checked after each test."""
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_gpu_3d.py", "tests/test_gpu_mg.py",
+                        "-m", "gpu", "-q", "-p", "no:cacheprovider", "-x"],
+                       cwd=ROOT, env=debug_env, capture_output=True, text=True, timeout=1800)
+    tail = "\n".join(r.stdout.splitlines()[-15:])
+    assert r.returncode == 0, tail + r.stderr[-2000:]
+    assert " passed" in tail
+
+
 def test_parity_suites_pass_the_debug_checks(debug_env):
     sel = ("tile_walk or classic or batched or pipelined or persistent or refinement or f64_cycles_match_oracle_1d "
            "or launch_shapes")
