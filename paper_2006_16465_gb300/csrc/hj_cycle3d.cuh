@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(32 * NW, 3) hier3d_pk_kernel(const CycArgs a) 
     constexpr int LY = 32 / LX, TX = 2 * LX, TY = LY * RY, TZ = RZ;
     constexpr unsigned FULL = 0xffffffffu;
     static_assert(LX == 4 || LX == 8 || LX == 16, "LX lanes of two columns per x segment");
+    static_assert(LY > 1, "the first and last lane groups are different groups");
     if constexpr (RES) {
         if (*(volatile int *)&a.red.ctl->done >= 0) return;
     }
@@ -289,8 +290,26 @@ __global__ void __launch_bounds__(32 * NW, 3) hier3d_pk_kernel(const CycArgs a) 
                 }
                 return ld_s<float, float>(bu + (long long)dz * ps + (long long)dy * ld + dx);
             };
+            // the same load where p holds, zero elsewhere, as a predicated
+            // instruction (no branch, so it is issued with the others)
+            auto ld_pred = [&](bool p, int dx, int dy, int dz) -> float {
+                if constexpr (PART) {
+                    if (x + dx > nx + 1 || yl + dy > ny + 1 || z0 + dz > nz + 1) p = false;
+                }
+                float v = 0.f;
+                const float *q = bu + (long long)dz * ps + (long long)dy * ld + dx;
+                asm volatile("{\n\t.reg .pred pp;\n\tsetp.ne.b32 pp, %2, 0;\n\t@pp ld.global.nc.f32 %0, [%1];\n\t}"
+                             : "+f"(v)
+                             : "l"(q), "r"((int)p));
+                return v;
+            };
             const int xo = wl ? -1 : 2;   // x-halo column: W on the first lane of a segment, else E
-            float xh[RY][RZ], hs[RZ][2], hn[RZ][2], hb[RY][2], ht[RY][2];
+            // y-halo row: S for the first lane group, N for the last (one row each;
+            // the other groups load nothing, which keeps the rows an instruction
+            // touches, and so its L1 wavefronts, to the two that are needed)
+            const int yo = sl ? -1 : RY;
+            const bool yh = sl || nl;
+            float xh[RY][RZ], hy[RZ][2], hb[RY][2], ht[RY][2];
 #pragma unroll
             for (int z = 0; z < RZ; ++z) {
 #pragma unroll
@@ -301,13 +320,10 @@ __global__ void __launch_bounds__(32 * NW, 3) hier3d_pk_kernel(const CycArgs a) 
                         const bool in = !PART || (x + c <= nx && yl + r <= ny && z0 + z <= nz);
                         g[r][z][c] = in ? __ldg(bf + (long long)z * ps + (long long)r * ld + c) : 0.f;
                     }
-                    xh[r][z] = ldu(xo, r, z);
+                    xh[r][z] = ld_pred(wl || el, xo, r, z);
                 }
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    hs[z][c] = ldu(c, -1, z);
-                    hn[z][c] = ldu(c, RY, z);
-                }
+                for (int c = 0; c < 2; ++c) hy[z][c] = ld_pred(yh, c, yo, z);
             }
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
@@ -331,8 +347,8 @@ __global__ void __launch_bounds__(32 * NW, 3) hier3d_pk_kernel(const CycArgs a) 
                 }
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    g[0][z][c] = fmaf(sl ? kc.bS : 0.f, hs[z][c], g[0][z][c]);
-                    g[RY - 1][z][c] = fmaf(nl ? kc.bN : 0.f, hn[z][c], g[RY - 1][z][c]);
+                    g[0][z][c] = fmaf(sl ? kc.bS : 0.f, hy[z][c], g[0][z][c]);
+                    g[RY - 1][z][c] = fmaf(nl ? kc.bN : 0.f, hy[z][c], g[RY - 1][z][c]);
                 }
             }
 #pragma unroll
