@@ -687,14 +687,15 @@ def variable_coefficients(torch, hj, W, n=4096, hbm_peak=None):
 
 def three_d(torch, hj, W, n=512, hbm_peak=None):
     """3D seven-point extension: cycle rate and HBM roofline of the
-    warp-per-subdomain kernel and of the classic sweep at n^3 (binary32: 12 B
+    subdomain kernels (binary32 at this size: the TMA-pipelined kernel) and of
+    the classic sweep at n^3 (binary32: 12 B
     per point and cycle, u in/out and f; binary64 is bound by the FP64 pipe,
     13 separately rounded operations per update), and time to a 1e-5
     residual reduction at 128^3 (binary32), hierarchical vs classic."""
     out = {}
     st = W.poisson_stencil3d(n, n, n)
-    runs = [("f32", (16, 8, 4), 1), ("f32", (16, 8, 4), 4), ("f32", (16, 8, 8), 4), ("f32", None, 1),
-            ("f64", (16, 4, 8), 1), ("f64", (16, 4, 8), 4)]
+    runs = [("f32", (16, 8, 4), 1), ("f32", (16, 8, 4), 4), ("f32", (16, 8, 8), 4), ("f32", (32, 4, 8), 1),
+            ("f32", (32, 4, 8), 4), ("f32", None, 1), ("f64", (16, 4, 8), 1), ("f64", (16, 4, 8), 4)]
     for prec, tile, k in runs:
         dt = torch.float32 if prec == "f32" else torch.float64
         bpp = 12 if prec == "f32" else 24

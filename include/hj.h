@@ -182,7 +182,11 @@ typedef struct {
                              lists, next tile staged while the current one
                              sweeps), 0 = one CTA per tile, -1 = automatic.
                              3D: 1 = persistent warps that prefetch the next
-                             subdomain with cp.async; 0 and -1 = one warp per
+                             subdomain with cp.async; 0 = one warp per
+                             subdomain; -1 = automatic: binary32 grids of at
+                             least 8 subdomains per SM (subdomains at least 16
+                             wide) run the TMA-pipelined kernel (one warp per
+                             CTA walking subdomains), others one warp per
                              subdomain                                        */
     int tile_threads;     /* threads per subdomain (one warp per band of rows);
                              0 = the default for the tile shape; the built

@@ -70,6 +70,23 @@ bool make_tmap(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int esz
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 3D tiled map over a grid array: dims (cols, rows, planes), row stride
+// ld*esz and plane stride ps*esz bytes, box (bw, bh, bd); out-of-bounds
+// elements read as zero.
+bool make_tmap3(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int esz, long long ld, long long ps,
+                int cols, int rows, int planes, int bw, int bh, int bd) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)(ld * esz), (cuuint64_t)(ps * esz)};
+    cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)bd};
+    cuuint32_t estr[3] = {1, 1, 1};
+    memset(m, 0, sizeof(*m));
+    return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 CUtensorMapDataType tmap_type(int fam, bool storage) {
     if (fam == FAM_F64) return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
     if (fam == FAM_BF16 && storage) return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
@@ -321,6 +338,17 @@ bool use_pf3(const hj_handle *h) {
     return h->k3 && h->d.dim == 3 && h->p.method == HJ_METHOD_HIER && h->p.pipeline == 1;
 }
 
+// 3D: whether the TMA-pipelined kernel runs the hierarchical cycles (binary32,
+// automatic pipeline choice, at least 8 subdomains per SM, as in 2D).
+bool want_ppc3(const hj_handle *h, bool classic) {
+    if (classic || !h->k3 || h->d.dim != 3 || h->p.method != HJ_METHOD_HIER || !h->k3->ppc[0]) return false;
+    if (h->p.pipeline != -1) return false;
+    const Tile3Info *t3 = h->k3;
+    const long long nsub = (long long)((h->d.nx + t3->tx - 1) / t3->tx) * ((h->d.ny + t3->ty - 1) / t3->ty) *
+                           ((h->d.nz + t3->tz - 1) / t3->tz);
+    return nsub >= 8LL * h->nsm;
+}
+
 // Whether the TMA-pipelined kernel runs this plan's cycles.
 bool want_ppc(const hj_handle *h, const PpcKernelInfo *pi, bool classic) {
     if (classic || !pi || h->d.dim != 2 || overlapped(h) || h->d.coef) return false;
@@ -343,7 +371,7 @@ bool defer_hier(const hj_handle *h, const TileKernelInfo *ki, bool classic) {
 
 // Whether a converging run of this plan needs the third iterate buffer.
 bool deferred_run(const hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, bool classic) {
-    return want_ppc(h, pi, classic) || defer_hier(h, ki, classic);
+    return want_ppc(h, pi, classic) || defer_hier(h, ki, classic) || want_ppc3(h, classic);
 }
 
 
@@ -361,6 +389,60 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
     if (h->d.dim == 3) {
         // seven-point extension: warp-per-subdomain register kernel, or the
         // classic thread-per-point sweep
+        if (want_ppc3(h, classic)) {
+            // TMA-pipelined: one warp per CTA walks subdomains, the next one's
+            // boxes copied in while the current one sweeps; residual folded by
+            // the next launch over three rotating iterate buffers
+            if (res && !b2) return seterr(HJ_ERR_CUDA, "internal: pipelined residual runs need a third iterate buffer");
+            const Tile3Info *t3 = h->k3;
+            PpcKernel fn = t3->ppc[res];
+            const int smem = t3->ppc_smem;
+            static thread_local std::vector<std::pair<int, const void *>> configured3;
+            const std::pair<int, const void *> key(h->dev, (const void *)fn);
+            if (std::find(configured3.begin(), configured3.end(), key) == configured3.end()) {
+                CKR(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                configured3.push_back(key);
+            }
+            int occ = 0;
+            CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32, smem));
+            if (occ < 1) return seterr(HJ_ERR_UNSUPPORTED, "3D pipelined kernel does not fit on an SM");
+            if (h->p.ctas_per_sm > 0) occ = std::min(occ, h->p.ctas_per_sm);
+            else if (t3->ppc_cps > 0) occ = std::min(occ, t3->ppc_cps);
+            const int tiles_x = (nx + t3->tx - 1) / t3->tx, tiles_y = (ny + t3->ty - 1) / t3->ty;
+            const int ntiles = tiles_x * tiles_y * ((h->d.nz + t3->tz - 1) / t3->tz);
+            const int grid = std::min(ntiles, occ * h->nsm);
+            const int bw = (t3->tx + 2 + 3) / 4 * 4;   // box width: the kernel's BX
+            void *bufs[3] = {b0, b1, b2};
+            pl->deferred = res;
+            pl->period = res ? kPpcPeriod : 2;
+            if (res) CKS(ensure_reduction(h, (size_t)grid));
+            for (int j = 0; j < pl->period; ++j) {
+                PpcArgs &P = pl->p[j];
+                memset(&P, 0, sizeof(P));
+                P.a = base;
+                P.a.uin = res ? bufs[j % 3] : bufs[j & 1];
+                P.a.uout = res ? bufs[(j + 1) % 3] : bufs[(j + 1) & 1];
+                P.tiles_x = tiles_x;
+                P.tiles_y = tiles_y;
+                P.ntiles = ntiles;
+                P.spin_limit = 1LL << 26;
+                P.parity = j & 1;
+                P.part_w = h->partials + (size_t)(j & 1) * grid;
+                P.part_r = h->partials + (size_t)((j + 1) & 1) * grid;
+                const long long ld = base.ld, ps = base.ps;
+                if (!make_tmap3(&P.mu, P.a.uin, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, ps, nx + 2, ny + 2, h->d.nz + 2,
+                                bw, t3->ty + 2, t3->tz + 2) ||
+                    !make_tmap3(&P.mf, P.a.f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ld, ps, nx + 2, ny + 2, h->d.nz + 2,
+                                bw, t3->ty, t3->tz))
+                    return seterr(HJ_ERR_CUDA, "cuTensorMapEncodeTiled failed (3D map: pointer alignment or pitch)");
+            }
+            pl->ppc = true;
+            pl->pfn = fn;
+            pl->smem = smem;
+            pl->grid = dim3(grid);
+            pl->block = dim3(32);
+            return HJ_OK;
+        }
         if (classic) {
             pl->fn = classic3d_kernel_of(fam, res);
             pl->grid = dim3((nx + 31) / 32, (ny + 7) / 8, h->d.nz);
@@ -910,7 +992,7 @@ void fill_stats_config(const hj_handle *h, hj_stats *st, double t0) {
     st->tile_z = h->d.dim == 3 ? h->p.tile_z : 1;
     const PpcKernelInfo *pk = h->ir ? h->p_inner : h->p_outer;
     const bool ppc = want_ppc(h, pk, h->p.method == HJ_METHOD_CLASSIC);
-    st->pipeline_stages = ppc ? pk->stages : use_pf3(h) ? 1 : 0;
+    st->pipeline_stages = ppc ? pk->stages : (use_pf3(h) || want_ppc3(h, h->p.method == HJ_METHOD_CLASSIC)) ? 1 : 0;
     st->ctas_per_sm = ppc ? h->p.ctas_per_sm : 0;
     st->overlap_x = h->p.overlap_x;
     st->overlap_y = h->d.dim == 2 ? h->p.overlap_y : 0;

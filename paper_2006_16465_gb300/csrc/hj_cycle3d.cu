@@ -12,11 +12,11 @@ namespace hj {
 
 namespace {
 const Tile3Info k3_f32[] = {
-    HJ_K3D_F32(16, 4, 8, 4),
-    HJ_K3D_F32(32, 4, 8, 4),
-    HJ_K3D_F32(8, 2, 8, 4),
-    HJ_K3D_F32(16, 4, 4, 4),
-    HJ_K3D_F32(32, 8, 4, 4),
+    HJ_K3D_F32(16, 4, 8, 4, 8),    // 16 x 8 x 8
+    HJ_K3D_F32(32, 4, 8, 4, 0),    // 32 x 4 x 8
+    HJ_K3D_F32_NOPPC(8, 2, 8, 4),  // 8 x 8 x 8
+    HJ_K3D_F32(16, 4, 4, 4, 12),   // 16 x 8 x 4
+    HJ_K3D_F32(32, 8, 4, 4, 0),    // 32 x 8 x 4
 };
 const Tile3Info k3_f64[] = {
     HJ_K3D(double, double, 16, 2, 8, 4, true),

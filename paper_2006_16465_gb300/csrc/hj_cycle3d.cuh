@@ -25,7 +25,7 @@
 //             fused chain.
 #pragma once
 
-#include "hj_cycle.cuh"
+#include "hj_tma.cuh"
 
 namespace hj {
 
@@ -243,10 +243,142 @@ __global__ void __launch_bounds__(32 * NW) hier3d_kernel(const CycArgs a) {
 // operations).  Per pair of points: two x shuffles, two scalar and five packed
 // multiply-adds.
 // ---------------------------------------------------------------------------
+// Register state of one subdomain in the two-column layout, and the steps
+// every binary32 3D kernel applies to it once a stager has filled it: u and
+// f (in g), and the frozen halo values the lane needs (x column: W on the
+// first lane of a segment, E on the last; y row: S on the first lane group,
+// N on the last; the planes below and above).
+template <int LX, int RY, int RZ>
+struct Pk3 {
+    static constexpr int LY = 32 / LX, TX = 2 * LX, TY = LY * RY, TZ = RZ;
+    float u[RY][RZ][2], g[RY][RZ][2];
+    float xh[RY][RZ], hy[RZ][2], hb[RY][2], ht[RY][2];
+};
+
+// g = f/d plus the weighted frozen halo: x faces, y faces, z faces.
+template <int LX, int RY, int RZ>
+__device__ __forceinline__ void pk3_fold(Pk3<LX, RY, RZ> &t, const Coef3<float> &kc, bool wl, bool el, bool sl,
+                                         bool nl) {
+#pragma unroll
+    for (int z = 0; z < RZ; ++z) {
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) t.g[r][z][c] *= kc.invd;
+            t.g[r][z][0] = fmaf(wl ? kc.bW : 0.f, t.xh[r][z], t.g[r][z][0]);
+            t.g[r][z][1] = fmaf(el ? kc.bE : 0.f, t.xh[r][z], t.g[r][z][1]);
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            t.g[0][z][c] = fmaf(sl ? kc.bS : 0.f, t.hy[z][c], t.g[0][z][c]);
+            t.g[RY - 1][z][c] = fmaf(nl ? kc.bN : 0.f, t.hy[z][c], t.g[RY - 1][z][c]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            t.g[r][0][c] = fmaf(kc.bB, t.hb[r][c], t.g[r][0][c]);
+            t.g[r][RZ - 1][c] = fmaf(kc.bT, t.ht[r][c], t.g[r][RZ - 1][c]);
+        }
+    }
+}
+
+// k subiterations; returns the lane's share of ||f - A u||^2 / d^2 of the
+// staged iterate (RES).  PART: points beyond the grid keep their values.
+template <int LX, int RY, int RZ, bool RES, bool PART>
+__device__ __forceinline__ float pk3_sweeps(Pk3<LX, RY, RZ> &t, const Coef3<float> &kc, int k, bool wl, bool el,
+                                            bool sl, bool nl, int x, int yl, int z0, int nx, int ny, int nz) {
+    constexpr int LY = 32 / LX;
+    constexpr unsigned FULL = 0xffffffffu;
+    const unsigned long long kWE = pk2(wl ? 0.f : kc.bW, el ? 0.f : kc.bE);
+    const unsigned long long kS2 = pk2(kc.bS, kc.bS), kN2 = pk2(kc.bN, kc.bN);
+    const unsigned long long kS02 = pk2(sl ? 0.f : kc.bS, sl ? 0.f : kc.bS);
+    const unsigned long long kNl2 = pk2(nl ? 0.f : kc.bN, nl ? 0.f : kc.bN);
+    const unsigned long long kB2 = pk2(kc.bB, kc.bB), kT2 = pk2(kc.bT, kc.bT);
+    float acc = 0.f;
+#pragma unroll 1
+    for (int s = 0; s < k; ++s) {
+        float prev[RY][2];   // old values of the plane below
+#pragma unroll
+        for (int z = 0; z < RZ; ++z) {
+            float up[2], dn[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                up[c] = __shfl_up_sync(FULL, t.u[RY - 1][z][c], LX);
+                dn[c] = __shfl_down_sync(FULL, t.u[0][z][c], LX);
+            }
+            float nv[RY][2];
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                const float c0 = t.u[r][z][0], c1 = t.u[r][z][1];
+                const float sW = __shfl_up_sync(FULL, c1, 1, LX);
+                const float sE = __shfl_down_sync(FULL, c0, 1, LX);
+                const float a0 = fmaf(kc.bE, c1, t.g[r][z][0]);
+                const float a1 = fmaf(kc.bW, c0, t.g[r][z][1]);
+                unsigned long long p = ffma2(kWE, pk2(sW, sE), pk2(a0, a1));
+                if (r > 0) p = ffma2(kS2, pk2(t.u[r > 0 ? r - 1 : 0][z][0], t.u[r > 0 ? r - 1 : 0][z][1]), p);
+                else p = ffma2(kS02, pk2(up[0], up[1]), p);
+                if (r < RY - 1)
+                    p = ffma2(kN2, pk2(t.u[r < RY - 1 ? r + 1 : 0][z][0], t.u[r < RY - 1 ? r + 1 : 0][z][1]), p);
+                else p = ffma2(kNl2, pk2(dn[0], dn[1]), p);
+                if (z > 0) p = ffma2(kB2, pk2(prev[r][0], prev[r][1]), p);
+                if (z < RZ - 1)
+                    p = ffma2(kT2, pk2(t.u[r][z < RZ - 1 ? z + 1 : 0][0], t.u[r][z < RZ - 1 ? z + 1 : 0][1]), p);
+                float n0, n1;
+                upk2(p, n0, n1);
+                bool in0 = true, in1 = true;
+                if constexpr (PART) {
+                    const bool iyz = yl + r <= ny && z0 + z <= nz;
+                    in0 = iyz && x <= nx;
+                    in1 = iyz && x + 1 <= nx;
+                    n0 = in0 ? n0 : c0;
+                    n1 = in1 ? n1 : c1;
+                }
+                if constexpr (RES) {
+                    if (s == 0) {
+                        const float r0 = in0 ? n0 - c0 : 0.f, r1 = in1 ? n1 - c1 : 0.f;
+                        acc += r0 * r0;
+                        acc += r1 * r1;
+                    }
+                }
+                nv[r][0] = n0;
+                nv[r][1] = n1;
+            }
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    prev[r][c] = t.u[r][z][c];
+                    t.u[r][z][c] = nv[r][c];
+                }
+            }
+        }
+    }
+    (void)LY;
+    return acc;
+}
+
+// Write back the lane's interior points.
+template <int LX, int RY, int RZ>
+__device__ __forceinline__ void pk3_store(const Pk3<LX, RY, RZ> &t, float *uo, long long ld, long long ps, bool full,
+                                          int x, int yl, int z0, int nx, int ny, int nz) {
+#pragma unroll
+    for (int z = 0; z < RZ; ++z)
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int yy = yl + r, zz = z0 + z;
+                if (full || (x + c <= nx && yy <= ny && zz <= nz))
+                    uo[(long long)zz * ps + (long long)yy * ld + x + c] = t.u[r][z][c];
+            }
+}
+
 template <int LX, int RY, int RZ, int NW, bool RES>
 __global__ void __launch_bounds__(32 * NW, 3) hier3d_pk_kernel(const CycArgs a) {
-    constexpr int LY = 32 / LX, TX = 2 * LX, TY = LY * RY, TZ = RZ;
-    constexpr unsigned FULL = 0xffffffffu;
+    using P3 = Pk3<LX, RY, RZ>;
+    constexpr int LY = P3::LY, TX = P3::TX, TY = P3::TY, TZ = P3::TZ;
     static_assert(LX == 4 || LX == 8 || LX == 16, "LX lanes of two columns per x segment");
     static_assert(LY > 1, "the first and last lane groups are different groups");
     if constexpr (RES) {
@@ -271,19 +403,18 @@ __global__ void __launch_bounds__(32 * NW, 3) hier3d_pk_kernel(const CycArgs a) 
         const Coef3<float> kc = make_coef3<float>(a);
         const bool full = x0 + TX - 1 <= nx && y0 + TY - 1 <= ny && z0 + TZ - 1 <= nz;   // warp-uniform
         const bool wl = lx == 0, el = lx == LX - 1, sl = gy == 0, nl = gy == LY - 1;
-        // iterate and f/d of the lane's points, with the halo folded into g.
-        // A subdomain inside the grid loads from one base pointer at fixed
-        // offsets; a ragged one checks every load: points beyond the grid read
-        // the ghost value (x, y or z = n + 1) or zero, and keep it.
-        float u[RY][RZ][2], g[RY][RZ][2];
+        P3 t;
+        // stage from global memory.  A subdomain inside the grid loads from one
+        // base pointer at fixed offsets; a ragged one checks every load: points
+        // beyond the grid read the ghost value (x, y or z = n + 1) or zero, and
+        // keep it.  Inside the grid every address within one point of the
+        // subdomain is in the ghost shell, so no load needs a lane condition
+        // and all of them are in flight before the first use.
         auto stage = [&](auto part_tag) {
             constexpr bool PART = decltype(part_tag)::value;
             const long long o = (long long)z0 * ps + (long long)yl * ld + x;
             const float *bu = uin + o, *bf = f + o;
-            // offset (dx, row dy, plane dz) from this lane's first point; inside
-            // the grid every such address within one point of the subdomain is
-            // in the ghost shell, so the loads need no lane conditions and all
-            // of them are in flight before the first use
+            // offset (dx, row dy, plane dz) from this lane's first point
             auto ldu = [&](int dx, int dy, int dz) -> float {
                 if constexpr (PART) {
                     if (x + dx > nx + 1 || yl + dy > ny + 1 || z0 + dz > nz + 1) return 0.f;
@@ -291,7 +422,9 @@ __global__ void __launch_bounds__(32 * NW, 3) hier3d_pk_kernel(const CycArgs a) 
                 return ld_s<float, float>(bu + (long long)dz * ps + (long long)dy * ld + dx);
             };
             // the same load where p holds, zero elsewhere, as a predicated
-            // instruction (no branch, so it is issued with the others)
+            // instruction (no branch, so it is issued with the others; the
+            // lanes that skip it keep the rows it touches, and so its L1
+            // wavefronts, to the ones that are needed)
             auto ld_pred = [&](bool p, int dx, int dy, int dz) -> float {
                 if constexpr (PART) {
                     if (x + dx > nx + 1 || yl + dy > ny + 1 || z0 + dz > nz + 1) p = false;
@@ -303,149 +436,180 @@ __global__ void __launch_bounds__(32 * NW, 3) hier3d_pk_kernel(const CycArgs a) 
                              : "l"(q), "r"((int)p));
                 return v;
             };
-            const int xo = wl ? -1 : 2;   // x-halo column: W on the first lane of a segment, else E
-            // y-halo row: S for the first lane group, N for the last (one row each;
-            // the other groups load nothing, which keeps the rows an instruction
-            // touches, and so its L1 wavefronts, to the two that are needed)
-            const int yo = sl ? -1 : RY;
-            const bool yh = sl || nl;
-            float xh[RY][RZ], hy[RZ][2], hb[RY][2], ht[RY][2];
+            const int xo = wl ? -1 : 2, yo = sl ? -1 : RY;
 #pragma unroll
             for (int z = 0; z < RZ; ++z) {
 #pragma unroll
                 for (int r = 0; r < RY; ++r) {
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
-                        u[r][z][c] = ldu(c, r, z);
+                        t.u[r][z][c] = ldu(c, r, z);
                         const bool in = !PART || (x + c <= nx && yl + r <= ny && z0 + z <= nz);
-                        g[r][z][c] = in ? __ldg(bf + (long long)z * ps + (long long)r * ld + c) : 0.f;
+                        t.g[r][z][c] = in ? __ldg(bf + (long long)z * ps + (long long)r * ld + c) : 0.f;
                     }
-                    xh[r][z] = ld_pred(wl || el, xo, r, z);
+                    t.xh[r][z] = ld_pred(wl || el, xo, r, z);
                 }
 #pragma unroll
-                for (int c = 0; c < 2; ++c) hy[z][c] = ld_pred(yh, c, yo, z);
+                for (int c = 0; c < 2; ++c) t.hy[z][c] = ld_pred(sl || nl, c, yo, z);
             }
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    hb[r][c] = ldu(c, r, -1);
-                    ht[r][c] = ldu(c, r, TZ);
-                }
-            }
-            // g = f/d plus the weighted frozen halo: x faces (the first lane of a
-            // segment holds W, the last E), y faces (first and last lane
-            // groups), z faces
-#pragma unroll
-            for (int z = 0; z < RZ; ++z) {
-#pragma unroll
-                for (int r = 0; r < RY; ++r) {
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) g[r][z][c] *= kc.invd;
-                    g[r][z][0] = fmaf(wl ? kc.bW : 0.f, xh[r][z], g[r][z][0]);
-                    g[r][z][1] = fmaf(el ? kc.bE : 0.f, xh[r][z], g[r][z][1]);
-                }
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    g[0][z][c] = fmaf(sl ? kc.bS : 0.f, hy[z][c], g[0][z][c]);
-                    g[RY - 1][z][c] = fmaf(nl ? kc.bN : 0.f, hy[z][c], g[RY - 1][z][c]);
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < RY; ++r) {
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    g[r][0][c] = fmaf(kc.bB, hb[r][c], g[r][0][c]);
-                    g[r][RZ - 1][c] = fmaf(kc.bT, ht[r][c], g[r][RZ - 1][c]);
+                    t.hb[r][c] = ldu(c, r, -1);
+                    t.ht[r][c] = ldu(c, r, TZ);
                 }
             }
         };
         if (full) stage(std::integral_constant<bool, false>());
         else stage(std::integral_constant<bool, true>());
-        const unsigned long long kWE = pk2(wl ? 0.f : kc.bW, el ? 0.f : kc.bE);
-        const unsigned long long kS2 = pk2(kc.bS, kc.bS), kN2 = pk2(kc.bN, kc.bN);
-        const unsigned long long kS02 = pk2(sl ? 0.f : kc.bS, sl ? 0.f : kc.bS);
-        const unsigned long long kNl2 = pk2(nl ? 0.f : kc.bN, nl ? 0.f : kc.bN);
-        const unsigned long long kB2 = pk2(kc.bB, kc.bB), kT2 = pk2(kc.bT, kc.bT);
-        auto sweeps = [&](auto part_tag) {
-            constexpr bool PART = decltype(part_tag)::value;
-#pragma unroll 1
-            for (int s = 0; s < a.k; ++s) {
-                float prev[RY][2];   // old values of the plane below
-#pragma unroll
-                for (int z = 0; z < RZ; ++z) {
-                    float up[2] = {0.f, 0.f}, dn[2] = {0.f, 0.f};
-                    if constexpr (LY > 1) {
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            up[c] = __shfl_up_sync(FULL, u[RY - 1][z][c], LX);
-                            dn[c] = __shfl_down_sync(FULL, u[0][z][c], LX);
-                        }
-                    }
-                    float nv[RY][2];
-#pragma unroll
-                    for (int r = 0; r < RY; ++r) {
-                        const float c0 = u[r][z][0], c1 = u[r][z][1];
-                        const float sW = __shfl_up_sync(FULL, c1, 1, LX);
-                        const float sE = __shfl_down_sync(FULL, c0, 1, LX);
-                        float a0 = fmaf(kc.bE, c1, g[r][z][0]);
-                        float a1 = fmaf(kc.bW, c0, g[r][z][1]);
-                        unsigned long long p = ffma2(kWE, pk2(sW, sE), pk2(a0, a1));
-                        if (r > 0) p = ffma2(kS2, pk2(u[r > 0 ? r - 1 : 0][z][0], u[r > 0 ? r - 1 : 0][z][1]), p);
-                        else if (LY > 1) p = ffma2(kS02, pk2(up[0], up[1]), p);
-                        if (r < RY - 1)
-                            p = ffma2(kN2, pk2(u[r < RY - 1 ? r + 1 : 0][z][0], u[r < RY - 1 ? r + 1 : 0][z][1]), p);
-                        else if (LY > 1) p = ffma2(kNl2, pk2(dn[0], dn[1]), p);
-                        if (z > 0) p = ffma2(kB2, pk2(prev[r][0], prev[r][1]), p);
-                        if (z < RZ - 1)
-                            p = ffma2(kT2, pk2(u[r][z < RZ - 1 ? z + 1 : 0][0], u[r][z < RZ - 1 ? z + 1 : 0][1]), p);
-                        float n0, n1;
-                        upk2(p, n0, n1);
-                        bool in0 = true, in1 = true;
-                        if constexpr (PART) {
-                            const bool iyz = yl + r <= ny && z0 + z <= nz;
-                            in0 = iyz && x <= nx;
-                            in1 = iyz && x + 1 <= nx;
-                            n0 = in0 ? n0 : c0;
-                            n1 = in1 ? n1 : c1;
-                        }
-                        if constexpr (RES) {
-                            if (s == 0) {
-                                const float r0 = in0 ? n0 - c0 : 0.f, r1 = in1 ? n1 - c1 : 0.f;
-                                acc += r0 * r0;
-                                acc += r1 * r1;
-                            }
-                        }
-                        nv[r][0] = n0;
-                        nv[r][1] = n1;
-                    }
-#pragma unroll
-                    for (int r = 0; r < RY; ++r) {
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            prev[r][c] = u[r][z][c];
-                            u[r][z][c] = nv[r][c];
-                        }
-                    }
-                }
-            }
-        };
-        if (full) sweeps(std::integral_constant<bool, false>());
-        else sweeps(std::integral_constant<bool, true>());
-        // write back this lane's interior points
-        float *uo = (float *)a.uout;
-#pragma unroll
-        for (int z = 0; z < RZ; ++z)
-#pragma unroll
-            for (int r = 0; r < RY; ++r)
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int yy = yl + r, zz = z0 + z;
-                    if (full || (x + c <= nx && yy <= ny && zz <= nz))
-                        uo[(long long)zz * ps + (long long)yy * ld + x + c] = u[r][z][c];
-                }
+        pk3_fold<LX, RY, RZ>(t, kc, wl, el, sl, nl);
+        if (full) acc = pk3_sweeps<LX, RY, RZ, RES, false>(t, kc, a.k, wl, el, sl, nl, x, yl, z0, nx, ny, nz);
+        else acc = pk3_sweeps<LX, RY, RZ, RES, true>(t, kc, a.k, wl, el, sl, nl, x, yl, z0, nx, ny, nz);
+        pk3_store<LX, RY, RZ>(t, (float *)a.uout, ld, ps, full, x, yl, z0, nx, ny, nz);
     }
     if constexpr (RES) reduce_grid_acc(a.red, acc);
+}
+
+// ---------------------------------------------------------------------------
+// TMA-pipelined binary32 variant for grids much larger than the resident CTAs
+// (the 3D counterpart of ppc2d_kernel).  One warp per CTA walks a static list
+// of subdomains (t = blockIdx.x + i gridDim.x, x fastest); one lane issues
+// cp.async.bulk.tensor copies of the next subdomain's iterate box (subdomain
+// + halo) and RHS box into shared memory, completing on an mbarrier, while
+// the warp sweeps the current one in registers (the two-column layout of
+// hier3d_pk_kernel, from the same steps).  The boxes start at x0 - 1 = bx TX,
+// a 16-byte boundary, and are BX = TX + 2 rounded up to four values wide;
+// elements beyond the tensor (the ghost shell) read as zero, as the checked
+// loads of the one-warp kernel do.  The residual is one partial per CTA,
+// folded by the next launch (the deferred fold of the 2D pipelined kernel).
+// Every wait on the mbarrier is bounded; on expiry the kernel records the
+// error, waits (bounded) for its copy in flight and returns.
+// ---------------------------------------------------------------------------
+template <int LX, int RY, int RZ>
+struct Ppc3Layout {
+    static constexpr int LY = 32 / LX, TX = 2 * LX, TY = LY * RY, TZ = RZ;
+    static constexpr int BX = round_up(TX + 2, 4);   // box width (iterate and RHS), 16-byte multiple
+    static constexpr int UB = BX * (TY + 2) * (TZ + 2) * 4, FB = BX * TY * TZ * 4;
+    static constexpr int UB_AL = round_up(UB, 128), FB_AL = round_up(FB, 128);
+    static constexpr int TX_BYTES = UB + FB;
+    static constexpr int BAR_OFF = UB_AL + FB_AL;
+    static constexpr int SMEM = BAR_OFF + 8 + 128;   // + room to align the base to 128 bytes
+};
+
+template <int LX, int RY, int RZ, bool RES>
+__global__ void __launch_bounds__(32) ppc3d_kernel(const __grid_constant__ PpcArgs P) {
+    using L = Ppc3Layout<LX, RY, RZ>;
+    using P3 = Pk3<LX, RY, RZ>;
+    constexpr int LY = L::LY, TX = L::TX, TY = L::TY, TZ = L::TZ, BX = L::BX;
+    static_assert(LY > 1, "the first and last lane groups are different groups");
+    const CycArgs &a = P.a;
+    const bool reducer = blockIdx.x == gridDim.x - 1;
+    if constexpr (RES) {
+        volatile Ctl *ctl = a.red.ctl;
+        if (ctl->done >= 0) return;
+        if (ctl->fold_only[P.parity]) {
+            if (reducer) deferred_fold(P);
+            return;
+        }
+    }
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    float *su = (float *)smem, *sf = (float *)(smem + L::UB_AL);
+    uint64_t *bar = (uint64_t *)(smem + L::BAR_OFF);
+    const int lane = threadIdx.x;
+    const int lx = lane % LX, gy = lane / LX;
+    const bool wl = lx == 0, el = lx == LX - 1, sl = gy == 0, nl = gy == LY - 1;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int txs = P.tiles_x, tys = P.tiles_y;
+    const int mine = (P.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    auto issue = [&](int tile) {
+        const int bx = tile % txs, by = (tile / txs) % tys, bz = tile / (txs * tys);
+        mbar_expect_tx(bar, L::TX_BYTES);
+        tma_load_3d(su, &P.mu, bar, bx * TX, by * TY, bz * TZ);
+        tma_load_3d(sf, &P.mf, bar, bx * TX, by * TY + 1, bz * TZ + 1);
+    };
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (lane == 0 && mine > 0) issue(blockIdx.x);
+    // the last CTA has the fewest subdomains when the grid does not divide
+    // them: it folds the previous launch's residual while its first copy lands
+    if constexpr (RES) {
+        if (reducer) deferred_fold(P);
+    }
+    const Coef3<float> kc = make_coef3<float>(a);
+    const long long ld = a.ld, ps = a.ps;
+    float acc = 0.f;
+    int i = 0;
+    bool failed = false;
+    for (; i < mine; ++i) {
+        bool ok = true;
+        long long spins = 0;
+        while (!mbar_try_wait(bar, (unsigned)i & 1u)) {
+            if (++spins > P.spin_limit) { ok = false; break; }
+        }
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        const int tile = blockIdx.x + i * gridDim.x;
+        const int bx = tile % txs, by = (tile / txs) % tys, bz = tile / (txs * tys);
+        const int x0 = 1 + bx * TX, y0 = 1 + by * TY, z0 = 1 + bz * TZ;
+        const int x = x0 + 2 * lx, yl = y0 + gy * RY;
+        const bool full = x0 + TX - 1 <= nx && y0 + TY - 1 <= ny && z0 + TZ - 1 <= nz;
+        // stage from the boxes: iterate box element (X, Y, Z) relative to
+        // (x0 - 1, y0 - 1, z0 - 1), RHS box element relative to (x0 - 1, y0, z0)
+        P3 t;
+        {
+            const int cx = 1 + 2 * lx, ry = gy * RY;
+            auto U = [&](int X, int Y, int Z) -> float { return su[(Z * (TY + 2) + Y) * BX + X]; };
+            const int xo = wl ? 0 : cx + 2, yo = sl ? 0 : ry + RY + 1;
+#pragma unroll
+            for (int z = 0; z < RZ; ++z) {
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        t.u[r][z][c] = U(cx + c, ry + r + 1, z + 1);
+                        const bool in = full || (x + c <= nx && yl + r <= ny && z0 + z <= nz);
+                        t.g[r][z][c] = in ? sf[(z * TY + ry + r) * BX + cx + c] : 0.f;
+                    }
+                    t.xh[r][z] = U(xo, ry + r + 1, z + 1);
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c) t.hy[z][c] = U(cx + c, yo, z + 1);
+            }
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    t.hb[r][c] = U(cx + c, ry + r + 1, 0);
+                    t.ht[r][c] = U(cx + c, ry + r + 1, TZ + 1);
+                }
+            }
+        }
+        __syncthreads();   // every lane is done with the boxes
+        if (lane == 0 && i + 1 < mine) {
+            fence_proxy_async_smem();
+            issue(blockIdx.x + (i + 1) * gridDim.x);
+        }
+        pk3_fold<LX, RY, RZ>(t, kc, wl, el, sl, nl);
+        if (full) acc += pk3_sweeps<LX, RY, RZ, RES, false>(t, kc, a.k, wl, el, sl, nl, x, yl, z0, nx, ny, nz);
+        else acc += pk3_sweeps<LX, RY, RZ, RES, true>(t, kc, a.k, wl, el, sl, nl, x, yl, z0, nx, ny, nz);
+        pk3_store<LX, RY, RZ>(t, (float *)a.uout, ld, ps, full, x, yl, z0, nx, ny, nz);
+    }
+    if (failed) {
+        // record the expiry, wait (bounded) for the copy in flight, return
+        if (lane == 0) {
+            atomicExch(a.err, HJ_ERR_TIMEOUT);
+            long long spins = 0;
+            while (!mbar_try_wait(bar, (unsigned)i & 1u) && ++spins <= P.spin_limit) {
+            }
+        }
+        __syncthreads();
+        return;
+    }
+    if constexpr (RES) write_cta_partial<1>(P.part_w + blockIdx.x, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -686,14 +850,27 @@ __global__ void __launch_bounds__(256) classic3d_kernel(const CycArgs a) {
      {hj::hier3d_kernel<S, T, LX, RY, RZ, NW, EX, false>, hj::hier3d_kernel<S, T, LX, RY, RZ, NW, EX, true>}, \
      {hj::hier3d_pf_kernel<S, T, LX, RY, RZ, NW, EX, false>,                                         \
       hj::hier3d_pf_kernel<S, T, LX, RY, RZ, NW, EX, true>},                                         \
-     (int)((NW) * hj::Pf3Layout<T, LX, RY, RZ>::PER_WARP * sizeof(T))}
+     (int)((NW) * hj::Pf3Layout<T, LX, RY, RZ>::PER_WARP * sizeof(T)), {nullptr, nullptr}, 0, 0}
 
 // binary32 entry of the same TX x TY x TZ shape: the two-column kernel, whose
-// LX / 2 lanes span x with RY / 2 rows per lane group, and the one-column
-// prefetching kernel
-#define HJ_K3D_F32(LX, RY, RZ, NW)                                                                   \
+// LX / 2 lanes span x with RY / 2 rows per lane group, the one-column
+// prefetching kernel, and the TMA-pipelined two-column kernel with its
+// resident CTAs per SM (CPS, measured per shape: more copies in flight slowed
+// the 16-wide boxes sharply)
+#define HJ_K3D_F32(LX, RY, RZ, NW, CPS)                                                              \
     {(LX), (32 / (LX)) * (RY), (RZ), 32 * (NW), (NW),                                               \
      {hj::hier3d_pk_kernel<(LX) / 2, (RY) / 2, RZ, NW, false>, hj::hier3d_pk_kernel<(LX) / 2, (RY) / 2, RZ, NW, true>}, \
      {hj::hier3d_pf_kernel<float, float, LX, RY, RZ, NW, false, false>,                              \
       hj::hier3d_pf_kernel<float, float, LX, RY, RZ, NW, false, true>},                              \
-     (int)((NW) * hj::Pf3Layout<float, LX, RY, RZ>::PER_WARP * sizeof(float))}
+     (int)((NW) * hj::Pf3Layout<float, LX, RY, RZ>::PER_WARP * sizeof(float)),                       \
+     {hj::ppc3d_kernel<(LX) / 2, (RY) / 2, RZ, false>, hj::ppc3d_kernel<(LX) / 2, (RY) / 2, RZ, true>},  \
+     hj::Ppc3Layout<(LX) / 2, (RY) / 2, RZ>::SMEM, (CPS)}
+
+// the same without the pipelined kernel (8-wide boxes: 48-byte rows, which
+// the copy engine moves too slowly to gain on the one-warp kernel)
+#define HJ_K3D_F32_NOPPC(LX, RY, RZ, NW)                                                             \
+    {(LX), (32 / (LX)) * (RY), (RZ), 32 * (NW), (NW),                                               \
+     {hj::hier3d_pk_kernel<(LX) / 2, (RY) / 2, RZ, NW, false>, hj::hier3d_pk_kernel<(LX) / 2, (RY) / 2, RZ, NW, true>}, \
+     {hj::hier3d_pf_kernel<float, float, LX, RY, RZ, NW, false, false>,                              \
+      hj::hier3d_pf_kernel<float, float, LX, RY, RZ, NW, false, true>},                              \
+     (int)((NW) * hj::Pf3Layout<float, LX, RY, RZ>::PER_WARP * sizeof(float)), {nullptr, nullptr}, 0, 0}

@@ -416,6 +416,9 @@ struct Tile3Info {
     CycKernel fn[2];
     CycKernel pf[2];   // prefetching persistent variant: grid <= resident CTAs, dynamic smem pf_smem
     int pf_smem;
+    PpcKernel ppc[2];  // TMA-pipelined variant (binary32; null otherwise): one warp per CTA, dynamic smem ppc_smem
+    int ppc_smem;
+    int ppc_cps;       // its resident CTAs per SM unless the caller sets ctas_per_sm (0: as many as fit)
 };
 const Tile3Info *tiles3d_f64(int *n);
 const Tile3Info *tiles3d_f32(int *n);

@@ -25,6 +25,7 @@ struct PpcArgs {
     CUtensorMap md;   // per-point 1/d (compute type), box (bwf, TY); sigma only
     CycArgs a;
     int tiles_x, ntiles;
+    int tiles_y;            // 3D kernel: subdomains along y (the tile index is x fastest, then y, then z)
     long long spin_limit;   // polls of an mbarrier before giving up
     // Fused residual (deferred fold): this launch writes one partial of
     // ||f - A u_c||^2 per CTA into part_w; the last CTA of the next launch
@@ -72,6 +73,14 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
         ::"r"(smem_addr(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
         : "memory");
 }
 

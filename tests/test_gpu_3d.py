@@ -148,3 +148,63 @@ def test_3d_host_pointer_solve_equals_device_solve():
     assert code == hj.HJ_OK
     assert torch.equal(uh, u.cpu())
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# binary32 TMA-pipelined kernel (grids of at least 8 subdomains per SM with
+# the automatic pipeline choice): one warp per CTA walks subdomains, the next
+# one's boxes copied in while the current one sweeps.  It stages the same
+# values (the copy engine's zero fill beyond the ghost shell for the one-warp
+# kernel's checked loads) and runs the same sweep steps, so its iterates equal
+# the one-warp kernel's bit for bit; both stay within 1e-5 of the oracle.
+# ---------------------------------------------------------------------------
+
+BIG3 = (200, 100, 60)   # 1,352 to 2,600 subdomains for the built binary32 shapes
+
+
+@pytest.mark.parametrize("ctas_per_sm", [0, 1, 2])
+def test_f32_3d_pipelined_walk_equals_one_warp_kernel_and_oracle(ctas_per_sm):
+    """ctas_per_sm 1 and 2 make every CTA walk many subdomains (stage reuse,
+    mbarrier phase flips, refills after the proxy fence); 0 = full residency."""
+    torch = _torch()
+    nx, ny, nz = BIG3
+    p = W.random_bc_problem3d(nx, ny, nz, seed=31, sigma_kind="const", asym=True)
+    shapes = _shapes("f32") if ctas_per_sm == 1 else _shapes("f32")[:1]
+    for tile in shapes:
+        outs = []
+        for pipeline in (-1, 0):
+            s = gpu_solver(p, tile_x=tile[0], tile_y=tile[1], tile_z=tile[2], k=5, precision="f32", fixed_cycles=3,
+                           pipeline=pipeline, ctas_per_sm=ctas_per_sm)
+            u = to_dev(p.u0, 3, torch.float32)
+            out = s.solve(to_dev(p.f, 3, torch.float32), u)
+            # every shape at least 16 wide has the pipelined kernel (8-wide boxes do not)
+            want = 1 if (pipeline == -1 and tile[0] >= 16) else 0
+            assert out["pipeline_stages"] == want, (tile, pipeline, out["pipeline_stages"])
+            outs.append(to_host(u, nx))
+            s.close()
+        assert np.array_equal(outs[0], outs[1]), (tile, rel_max(outs[0], outs[1]))
+        ref = oracle.run_fixed(p.st, p.f, p.u0, 3, tile[0], tile[1], 5, tz=tile[2])
+        assert rel_max(outs[0], ref) <= 1e-5, (tile, rel_max(outs[0], ref))
+
+
+def test_f32_3d_pipelined_converging_solve_equals_one_warp_kernel():
+    """The deferred residual fold (one partial per CTA, folded by the next
+    launch over three rotating iterate buffers) stops at the one-warp
+    kernel's cycle with the same iterate; the oracle's residual of the
+    returned iterate meets the tolerance."""
+    torch = _torch()
+    nx, ny, nz = BIG3
+    q = W.poisson3d_uniform(nx, ny, nz, seed=5)
+    res = []
+    for pipeline in (-1, 0):
+        s = gpu_solver(q, precision="f32", k=8, tol=1e-3, check_every=8, max_cycles=100000, pipeline=pipeline,
+                       ctas_per_sm=2)
+        u = to_dev(q.u0, 3, torch.float32)
+        out = s.solve(to_dev(q.f, 3, torch.float32), u)
+        assert out["status"] == 0
+        res.append((out["cycles"], to_host(u, nx)))
+        s.close()
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1])
+    r = oracle.residual(q.st, q.f, res[0][1])
+    assert r <= 1.01e-3 * oracle.residual(q.st, q.f, q.u0)
