@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -338,6 +339,26 @@ bool use_pf3(const hj_handle *h) {
     return h->k3 && h->d.dim == 3 && h->p.method == HJ_METHOD_HIER && h->p.pipeline == 1;
 }
 
+// Raise a kernel's dynamic shared-memory limit (a per-device attribute of the
+// function) to at least `bytes`, never lowering it: a kernel whose shared
+// memory depends on the subdomain shape may serve several handles, and graphs
+// built earlier keep launching with their own sizes.
+cudaError_t ensure_dyn_smem(int dev, const void *fn, int bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<int, const void *>, int>> set;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &e : set)
+        if (e.first.first == dev && e.first.second == fn) {
+            if (bytes <= e.second) return cudaSuccess;
+            const cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (r == cudaSuccess) e.second = bytes;
+            return r;
+        }
+    const cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (r == cudaSuccess) set.push_back({{dev, fn}, bytes});
+    return r;
+}
+
 // 3D: whether the TMA-pipelined kernel runs the hierarchical cycles (binary32,
 // automatic pipeline choice, at least 8 subdomains per SM, as in 2D).
 bool want_ppc3(const hj_handle *h, bool classic) {
@@ -397,12 +418,7 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
             const Tile3Info *t3 = h->k3;
             PpcKernel fn = t3->ppc[res];
             const int smem = t3->ppc_smem;
-            static thread_local std::vector<std::pair<int, const void *>> configured3;
-            const std::pair<int, const void *> key(h->dev, (const void *)fn);
-            if (std::find(configured3.begin(), configured3.end(), key) == configured3.end()) {
-                CKR(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-                configured3.push_back(key);
-            }
+            CKR(ensure_dyn_smem(h->dev, (const void *)fn, smem));
             int occ = 0;
             CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32, smem));
             if (occ < 1) return seterr(HJ_ERR_UNSUPPORTED, "3D pipelined kernel does not fit on an SM");
@@ -521,14 +537,7 @@ int make_plan(hj_handle *h, const TileKernelInfo *ki, const PpcKernelInfo *pi, i
     if (res && !b2) return seterr(HJ_ERR_CUDA, "internal: pipelined residual runs need a third iterate buffer");
     PpcKernel fn = pi->fn[sig][res];
     const int smem = pi->smem[sig];
-    // the shared-memory limit is a per-device attribute of the function: set
-    // it once per (device, function) pair this thread has launched
-    static thread_local std::vector<std::pair<int, const void *>> configured;
-    const std::pair<int, const void *> key(h->dev, (const void *)fn);
-    if (std::find(configured.begin(), configured.end(), key) == configured.end()) {
-        CKR(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        configured.push_back(key);
-    }
+    CKR(ensure_dyn_smem(h->dev, (const void *)fn, smem));
     int occ = 0;
     CKR(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, pi->threads, smem));
     if (occ < 1) return seterr(HJ_ERR_UNSUPPORTED, "pipelined kernel does not fit on an SM");

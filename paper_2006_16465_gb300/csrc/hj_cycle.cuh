@@ -437,6 +437,7 @@ __device__ __forceinline__ float sweeps2d_fold(Tile2D<float, C, R, SIG> &t, cons
         }
         if constexpr (NW > 1) {
             constexpr int NX = 2 * NW * 2 * TX;
+            (void)NX;   // read by the index checks of debug builds
             const int o = par * (NW * 2 * TX);
             float *buf = xbuf + o;
 #pragma unroll
@@ -555,6 +556,7 @@ sweeps2d(Tile2D<T, C, R, SIG> &t, const Coef<T> &kc, const int k, const int x0, 
         if constexpr (NW > 1) {
             // two parities of NW x 2 edge rows of TX points
             constexpr int NX = 2 * NW * 2 * TX;
+            (void)NX;   // read by the index checks of debug builds
             const int o = par * (NW * 2 * TX);
             T *buf = xbuf + o;
 #pragma unroll

@@ -84,7 +84,7 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
+__host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 template <typename S, typename T, int C, int R, int NW, int H, bool SIG, int NST>
 struct PpcLayout {
