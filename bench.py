@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 METRIC = "2D Poisson time-to-1e-8 residual, GLUP/s vs global-mem Jacobi; % HBM roofline"
 N_BENCH = 8192
 BYTES_PER_POINT_CYCLE = 12  # read u, read f, write u (binary32)
-EXTRAS_OUT = os.path.join(ROOT, "gpurun_out", "bench_extras.json")
+EXTRAS_OUT = os.path.join(ROOT, "bench_extras.json")   # full record of the extra legs (not tracked)
 
 
 def _r(x, digits=4):
