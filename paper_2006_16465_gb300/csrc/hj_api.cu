@@ -339,23 +339,52 @@ bool use_pf3(const hj_handle *h) {
     return h->k3 && h->d.dim == 3 && h->p.method == HJ_METHOD_HIER && h->p.pipeline == 1;
 }
 
-// Raise a kernel's dynamic shared-memory limit (a per-device attribute of the
-// function) to at least `bytes`, never lowering it: a kernel whose shared
-// memory depends on the subdomain shape may serve several handles, and graphs
-// built earlier keep launching with their own sizes.
+// Id of the calling thread's current CUDA context (cuCtxGetId through the
+// runtime's driver entry points), or 0 if it cannot be had.  A context made
+// after cudaDeviceReset gets a new id, so settings recorded for the old one
+// are not taken for it.
+unsigned long long context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = (PFN_cuCtxGetCurrent_v4000)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PFN_cuCtxGetId_v12000)p;
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id + 1;
+}
+
+// Raise a kernel's dynamic shared-memory limit (an attribute of the function
+// in the current context) to at least `bytes`, never lowering it: a kernel
+// whose shared memory depends on the subdomain shape may serve several
+// handles, and graphs built earlier keep launching with their own sizes.
+// Recorded per (context, device, function); without a context id it is set
+// every time.
 cudaError_t ensure_dyn_smem(int dev, const void *fn, int bytes) {
     static std::mutex mu;
-    static std::vector<std::pair<std::pair<int, const void *>, int>> set;
+    static std::vector<std::pair<std::pair<unsigned long long, const void *>, std::pair<int, int>>> set;
+    const unsigned long long ctx = context_id();
+    if (ctx == 0) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     std::lock_guard<std::mutex> lk(mu);
     for (auto &e : set)
-        if (e.first.first == dev && e.first.second == fn) {
-            if (bytes <= e.second) return cudaSuccess;
+        if (e.first.first == ctx && e.first.second == fn && e.second.first == dev) {
+            if (bytes <= e.second.second) return cudaSuccess;
             const cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            if (r == cudaSuccess) e.second = bytes;
+            if (r == cudaSuccess) e.second.second = bytes;
             return r;
         }
     const cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (r == cudaSuccess) set.push_back({{dev, fn}, bytes});
+    if (r == cudaSuccess) set.push_back({{ctx, fn}, {dev, bytes}});
     return r;
 }
 
