@@ -610,8 +610,17 @@ def inner_roofline(torch, hj, W, n, k=16, cycles=100):
         pass
     peak = props.multi_processor_count * 128 * sm_max_mhz * 1e6 / 4 / 1e9
     achieved = n * n * k * cycles / (ms / 1e3) / 1e9
+    # the on-chip data path of the sweeps: their east/west neighbours and band
+    # edges move by warp shuffle, which goes through the SM's shared-memory
+    # data pipe at one warp-wide shuffle per clock; a 32x32 subdomain (one
+    # warp, two bands of 16 rows, two columns per lane) issues 2 x 16 row
+    # shuffles and 2 band-exchange shuffles per subiteration
+    smem_bound = props.multi_processor_count * sm_max_mhz * 1e6 * 1024 / 34 / 1e9
     return {"bound": "alu", "k": k, "achieved": achieved, "peak": peak, "unit": "GLUP/s", "frac": achieved / peak,
-            "peak_basis": "SMs x 128 FP32 lanes x max SM clock / 4 FMA per point update"}
+            "peak_basis": "SMs x 128 FP32 lanes x max SM clock / 4 FMA per point update",
+            "smem_path_bound": smem_bound, "smem_path_frac": achieved / smem_bound,
+            "smem_path_basis": "SMs x max SM clock x 1024 point updates / 34 warp shuffles (shared-memory data pipe, "
+                               "one warp-wide shuffle per clock)"}
 
 
 def variable_coefficients(torch, hj, W, n=4096, hbm_peak=None):
@@ -1181,6 +1190,7 @@ def compact_summary(x):
                       "max_rel_err": _r(fd["max_rel_err"], 2), "s": _r(fd["fd_solves_s"], 3)}
     out["legs"] = {"classic_kernel_hbm_frac": _r(x["classic_global_jacobi"]["hbm_frac"], 3),
                    "inner_k16_alu_frac": _r(x["inner_sweep_roofline_k16"]["frac"], 3),
+                   "inner_k16_smem_frac": _r(x["inner_sweep_roofline_k16"]["smem_path_frac"], 3),
                    "cfg1_gpu_speedup": _r(x["cfg1_1d_to_1e-6"]["speedup"], 3),
                    "cfg4_s": _r(x["cfg4_batched_256_to_1e-8"]["seconds"], 3),
                    "cfg4_graphed": x["cfg4_batched_256_to_1e-8"]["graphed"],
