@@ -76,3 +76,30 @@ def test_closed_form_sweep_count_and_sine_solve_of_the_bench():
     assert bench.host_rel_residual(p.st, p.f, u) < 1e-12
     assert bench.host_rel_residual(p.st, p.f, p.u0) == 1.0
     assert np.allclose(bench.host_rel_residual(p.st, p.f, u * 0.5), 0.5)
+
+
+def test_compact_summary_fits_the_line_and_carries_every_leg():
+    """The JSON line's summary of the extra legs, from a synthetic record with
+    the keys the legs write: every leg present, rows rounded, and the whole
+    line well inside the few kilobytes the bench's output tail keeps."""
+    sys.path.insert(0, ROOT)
+    import bench
+    row = {"s": 0.123456, "cycles": 1234, "outer": 3, "rel": 2.5e-10, "err_vs_exact": 6.4e-12}
+    sweep = {"k1": {"s": 1.0, "cycles": 10}, "k4": {"s": 0.5, "cycles": 5}, "classic": {"s": 2.0, "cycles": 20}}
+    x = {"time_to_1e-8_512": {"hj_f32ir_autotuned": row, "hj_f32ir_32x32_k32": row, "classic_f64_tile_k1": row,
+                              "classic_best": "classic_f64_tile_k1", "speedup_autotuned_vs_classic": 46.8},
+         "cfg3_precision_512": {"f32_ir": row, "bf16corr_ir": row, "f64": row},
+         "cfg2_k_sweep_512": {"f64_to_1e-06": sweep, "f32_to_1e-05": sweep},
+         "cfg5_fd_check": {"grid": [1024, 1024], "entries": 32, "rel_step": 1e-6, "max_rel_err": 5.4e-6,
+                           "fd_solves_s": 36.2},
+         "classic_global_jacobi": {"hbm_frac": 0.9123},
+         "inner_sweep_roofline_k16": {"frac": 0.4834, "smem_path_frac": 0.5118},
+         "cfg1_1d_to_1e-6": {"speedup": 9.37},
+         "cfg4_batched_256_to_1e-8": {"seconds": 2.66, "graphed": 1, "tail_seconds": 0.544},
+         "cfg5_differentiation_1024": {"forward_seconds": 14.1, "backward_seconds": 14.6}}
+    out = bench.compact_summary(x)
+    assert out["time_to_1e-8_512"]["hj_f32ir_autotuned"] == [0.123, 1234, 3, 2.5e-10]
+    assert out["cfg3_ir_to_1e-10_512"]["f32_ir"] == [0.123, 1234, 3, 2.5e-10, 6.4e-12]
+    assert out["legs"]["inner_k16_smem_frac"] == 0.512 and out["legs"]["inner_k16_alu_frac"] == 0.483
+    assert out["cfg5_fd"]["entries"] == 32 and out["cfg2_k_sweep_512"]["f32_to_1e-05"]["k4"] == [0.5, 5]
+    assert len(json.dumps(out, separators=(",", ":"))) < 1500
